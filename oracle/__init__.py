@@ -1,0 +1,221 @@
+"""ctypes binding of the plain FP64 CPU oracle.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
+the CPU-baseline / reference leg of ``bench.py``.  The product package never
+imports it, and the oracle shares no code with the CUDA path.
+
+A run is described by a plain dict (see ``lbm_workloads``) with the keys
+``lattice`` ("D2Q9" | "D2Q37"), ``nx``, ``ny``, ``tau``, ``rho0``, ``sides``
+(four of "periodic" | "cbc" | "inflow" | "zg", order W, E, S, N),
+``schemes`` (four of "lodi" | "lodi_relax" | "cbc" | "cbc_relax"),
+``viscous`` ("meso" | "fd" | "off"), ``dirichlet`` ("eq" | "neep"), ``alpha_T``, ``beta_P``,
+``t_inf``, ``p_inf`` (four values) and ``inflow`` (rho, ux, uy, T).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LATTICES = {"D2Q9": 0, "D2Q37": 1}
+SIDES = {"periodic": 0, "cbc": 1, "inflow": 2, "zg": 3}
+SCHEMES = {"lodi": 0, "lodi_relax": 1, "cbc": 2, "cbc_relax": 3}
+DIRICHLET = {"eq": 0, "neep": 1}
+VISCOUS = {"meso": 0, "fd": 1, "off": 2}
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+        ("tau", C.c_double), ("rho0", C.c_double),
+        ("side", C.c_int * 4), ("scheme", C.c_int * 4),
+        ("viscous", C.c_int), ("dirichlet", C.c_int),
+        ("alpha_T", C.c_double), ("beta_P", C.c_double), ("t_inf", C.c_double),
+        ("p_inf", C.c_double * 4), ("inflow", C.c_double * 4),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int)
+        L.orc_lattice_info.argtypes = [C.c_int, ip, ip, dp, ip, dp]
+        L.orc_feq.argtypes = [C.c_int, C.c_double, dp, dp]
+        L.orc_moments.argtypes = [C.c_int, C.c_double, dp, dp]
+        L.orc_char_matrices.argtypes = [C.c_int, C.c_double, dp, dp, dp, dp]
+        L.orc_char_rhs.argtypes = [C.POINTER(Params), dp, dp, dp, dp, C.c_int, C.c_double, C.c_int, dp]
+        L.orc_rk4_scalar.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
+        L.orc_rk4_scalar.restype = C.c_double
+        L.orc_create.argtypes = [C.POINTER(Params)]
+        L.orc_create.restype = C.c_void_p
+        L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_init.argtypes = [C.c_void_p, dp, dp, dp, dp]
+        L.orc_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc_macros.argtypes = [C.c_void_p, dp, dp, dp, dp]
+        L.orc_populations.argtypes = [C.c_void_p, dp]
+        L.orc_neq_moments.argtypes = [C.c_void_p, C.c_int, C.c_int, dp]
+        L.orc_vis_meso_at.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, dp]
+        L.orc_boundary_state.argtypes = [C.c_void_p, dp]
+        L.orc_steps_done.argtypes = [C.c_void_p]
+        L.orc_steps_done.restype = C.c_long
+        L.orc_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_params(cfg) -> Params:
+    p = Params()
+    p.lattice = LATTICES[cfg["lattice"]]
+    p.nx, p.ny = int(cfg["nx"]), int(cfg["ny"])
+    p.tau = float(cfg["tau"])
+    p.rho0 = float(cfg.get("rho0", 1.0))
+    for i, s in enumerate(cfg.get("sides", ["periodic"] * 4)):
+        p.side[i] = SIDES[s]
+    for i, s in enumerate(cfg.get("schemes", ["cbc"] * 4)):
+        p.scheme[i] = SCHEMES[s]
+    p.viscous = VISCOUS[cfg.get("viscous", "meso")]
+    p.dirichlet = DIRICHLET[cfg.get("dirichlet", "eq")]
+    p.alpha_T = float(cfg.get("alpha_T", 0.0))
+    p.beta_P = float(cfg.get("beta_P", 0.0))
+    p.t_inf = float(cfg.get("t_inf", 0.0))
+    cs2 = lattice_info(cfg["lattice"])["cs2"]
+    pinf = cfg.get("p_inf", [cs2 * p.rho0] * 4)
+    for i in range(4):
+        p.p_inf[i] = float(pinf[i])
+    inflow = cfg.get("inflow", [p.rho0, 0.0, 0.0, 1.0])
+    for i in range(4):
+        p.inflow[i] = float(inflow[i])
+    return p
+
+
+def lattice_info(name):
+    L = lib()
+    q = C.c_int()
+    M = C.c_int()
+    cs2 = C.c_double()
+    c = (C.c_int * 74)()
+    w = (C.c_double * 37)()
+    if L.orc_lattice_info(LATTICES[name], C.byref(q), C.byref(M), C.byref(cs2), c, w):
+        raise ValueError(name)
+    n = q.value
+    return {"q": n, "M": M.value, "cs2": cs2.value,
+            "c": np.array(c[: 2 * n], dtype=np.int64).reshape(n, 2),
+            "w": np.array(w[:n], dtype=np.float64)}
+
+
+def feq(lattice, rho0, U):
+    """Shifted equilibrium f^eq - w rho0 at U = (drho, ux, uy, dT)."""
+    info = lattice_info(lattice)
+    g = np.zeros(info["q"])
+    u = _f64(U)
+    lib().orc_feq(LATTICES[lattice], rho0, _dp(u), _dp(g))
+    return g
+
+
+def moments(lattice, rho0, g):
+    """(drho, ux, uy, dT) of shifted populations g."""
+    g = _f64(g)
+    U = np.zeros(4)
+    lib().orc_moments(LATTICES[lattice], rho0, _dp(g), _dp(U))
+    return U
+
+
+def char_matrices(lattice, rho0, Ul):
+    S = np.zeros(16)
+    Si = np.zeros(16)
+    lam = np.zeros(4)
+    u = _f64(Ul)
+    lib().orc_char_matrices(LATTICES[lattice], rho0, _dp(u), _dp(S), _dp(Si), _dp(lam))
+    n = 4 if lattice == "D2Q37" else 3
+    return S.reshape(4, 4)[:n, :n], Si.reshape(4, 4)[:n, :n], lam[:n]
+
+
+def char_rhs(cfg, Ul, dUn, TT, VV, mask, dP, scheme):
+    p = make_params(cfg)
+    k = np.zeros(4)
+    args = [_f64(a) for a in (Ul, dUn, TT, VV)]
+    lib().orc_char_rhs(C.byref(p), *[_dp(a) for a in args], int(mask), float(dP),
+                       SCHEMES[scheme], _dp(k))
+    return k
+
+
+def rk4_scalar(lam, y0, h, nsteps):
+    return lib().orc_rk4_scalar(lam, y0, h, nsteps)
+
+
+def threads():
+    return lib().orc_threads()
+
+
+class Sim:
+    """One oracle run: ``Sim(cfg).init(rho, ux, uy, T).step(n).macros()``."""
+
+    def __init__(self, cfg):
+        self.cfg = dict(cfg)
+        self._p = make_params(cfg)
+        self._h = lib().orc_create(C.byref(self._p))
+        if not self._h:
+            raise ValueError("oracle rejected the configuration")
+        self.nx, self.ny = self._p.nx, self._p.ny
+        self.q = lattice_info(cfg["lattice"])["q"]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_destroy(h)
+            self._h = None
+
+    def init(self, rho, ux, uy, T):
+        shape = (self.ny, self.nx)
+        arrs = [_f64(np.broadcast_to(a, shape)) for a in (rho, ux, uy, T)]
+        lib().orc_init(self._h, *[_dp(a) for a in arrs])
+        return self
+
+    def step(self, n=1):
+        lib().orc_step(self._h, int(n))
+        return self
+
+    @property
+    def steps_done(self):
+        return lib().orc_steps_done(self._h)
+
+    def macros(self):
+        """(rho, ux, uy, T), each [ny, nx] float64."""
+        out = [np.zeros((self.ny, self.nx)) for _ in range(4)]
+        lib().orc_macros(self._h, *[_dp(a) for a in out])
+        return tuple(out)
+
+    def populations(self):
+        g = np.zeros((self.ny, self.nx, self.q))
+        lib().orc_populations(self._h, _dp(g))
+        return g
+
+    def neq_moments(self, x, y):
+        out = np.zeros(5)
+        lib().orc_neq_moments(self._h, int(x), int(y), _dp(out))
+        return out
+
+    def vis_meso_at(self, side, x, y):
+        V = np.zeros(4)
+        lib().orc_vis_meso_at(self._h, int(side), int(x), int(y), _dp(V))
+        return V
+
+    def boundary_state(self):
+        U = np.zeros((self.ny, self.nx, 4))
+        lib().orc_boundary_state(self._h, _dp(U))
+        return U
