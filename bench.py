@@ -1,0 +1,339 @@
+"""Benchmark: MLUPS and fraction of the HBM roofline of the thermal LBM step
+with the characteristic boundary condition, on the D2Q37 isentropic-vortex
+workload (1024 x 512, inflow | CBC-RELAX outlet, periodic y).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage f32|f64|f16]
+                  [--impl gb300|reference]
+
+Prints one JSON line.  Timing: W untimed warm-up steps, then K steps, each
+bracketed by CUDA events on the solver's stream with an L2 flush (a write of
+a buffer larger than L2) between timed steps; barrier + synchronize around the
+timed region; the max over ranks is reported.  N > 1 runs independent
+replicas, one per GPU (weak scaling; the method has no cross-GPU exchange in
+this configuration).  The reference arm times the FP64 CPU oracle on this
+host on the same workload and metric.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lbm_workloads as W  # noqa: E402
+
+METRIC = "MLUPS (lattice updates/s / 1e6), D2Q37 thermal LBM + CBC step"
+BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f64", "f16"])
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=512)
+    ap.add_argument("--no-fp64-leg", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(nx, ny, storage, steps):
+    cfg, fields = W.vortex_d2q37(nx, ny, Ma=0.1, steps=steps, storage=storage)
+    return cfg, fields
+
+
+def workload_config(cfg, extra=None):
+    d = {"workload": cfg["name"], "lattice": cfg["lattice"], "nx": cfg["nx"], "ny": cfg["ny"],
+         "tau": cfg["tau"], "sides": cfg["sides"], "scheme_outlet": cfg["schemes"][1],
+         "viscous": cfg["viscous"], "storage": cfg["storage"], "l2": "flushed between timed steps"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ------------------------------------------------------------ clocks ---
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- peaks ---
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def bulk_traffic(storage, nx, ny):
+    """DRAM bytes per bulk-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (scaled by bulk nodes)."""
+    src = os.path.join(ROOT, "paper_2307_16766_gb300", "csrc", "bulk.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+    path = os.path.join(ROOT, "profiles", "k_bulk_d2q37_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        m = re.match(r"traffic\s+storage=(\w+)\s+nodes=(\d+)\s+bytes=(\d+)\s+src=(\w+)", line.strip())
+        if m and m.group(1) == storage and m.group(4) == sha:
+            nodes = int(m.group(2))
+            return int(m.group(3)) * ((nx - 6) * ny) / nodes
+    return None
+
+
+# -------------------------------------------------------- GPU measurement ---
+
+def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
+    import torch
+    import paper_2307_16766_gb300 as lbm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cfg, fields = workload(args.nx, args.ny, storage, args.steps)
+    sim = lbm.Simulation(cfg, device=dev)
+    sim.init_fields(*fields)
+    stream = sim.stream
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            flush.fill_(float(k))                       # evict L2 between timed steps
+            ev[k][0].record(stream)
+            sim.step_phase(0)                           # bulk stream-collide
+            ev[k][1].record(stream)
+            sim.step_phase(1)                           # boundary conditions
+            ev[k][2].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = np.array([ev[k][0].elapsed_time(ev[k][2]) for k in range(K)])
+    bulk_ms = np.array([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)])
+    bnd_ms = np.array([ev[k][1].elapsed_time(ev[k][2]) for k in range(K)])
+    rho, ux, uy, T = sim.macros()
+    finite = bool(np.all(np.isfinite(rho)) and np.all(np.isfinite(ux)))
+
+    res = {"step_ms_total": float(step_ms.sum()), "bulk_ms_mean": float(bulk_ms.mean()),
+           "boundary_ms_mean": float(bnd_ms.mean()), "wall_s": wall, "clocks": clocks,
+           "finite": finite, "cfg": cfg, "bulk_nodes": (sim.nx - 6) * sim.ny}
+
+    if want_e2e:
+        # End to end through the C ABI with pinned host buffers: every segment
+        # copies the initial fields in, runs S steps and reads the macros back.
+        S = 100
+        n = sim.nx * sim.ny
+        host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in fields]
+        host_out = [torch.empty((sim.ny, sim.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+        segs = max(1, min(5, K // S))
+        lbm.lbm_init_fields(sim.handle, n, *[t.numpy() for t in host_in])
+        lbm.lbm_step(sim.handle, S)
+        lbm.lbm_get_macros(sim.handle, *[t.data_ptr() for t in host_out], 0)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        for _ in range(segs):
+            lbm.lbm_init_fields(sim.handle, n, *[t.numpy() for t in host_in])
+            lbm.lbm_step(sim.handle, S)
+            lbm.lbm_get_macros(sim.handle, *[t.data_ptr() for t in host_out], 0)
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t1
+        res["e2e"] = {"value": n * S * segs / e2e_s / 1e6, "unit": "MLUPS",
+                      "h2d_bytes_per_step": 4 * 8 * n / S, "d2h_bytes_per_step": 4 * 8 * n / S,
+                      "segment_steps": S, "segments": segs}
+    sim.close()
+    return res
+
+
+def cpu_baseline(cfg, fields, seconds=15.0):
+    import oracle
+    s = oracle.Sim(cfg).init(*fields)
+    t = time.perf_counter()
+    s.step(1)
+    one = time.perf_counter() - t
+    n = max(1, int(seconds / max(one, 1e-3)))
+    t = time.perf_counter()
+    s.step(n)
+    dt = time.perf_counter() - t
+    mlups = cfg["nx"] * cfg["ny"] * n / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d FP64 oracle steps of the %dx%d workload after one warm-up step (%.1f s)"
+                      % (n, cfg["nx"], cfg["ny"], dt)}
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo" if args.impl == "reference" else "nccl")
+
+    if args.impl == "reference":
+        if rank == 0:
+            cfg, fields = workload(args.nx, args.ny, "f64", args.steps)
+            import oracle
+            s = oracle.Sim(cfg).init(*fields)
+            for _ in range(min(args.warmup, 1)):
+                s.step(1)
+            t = time.perf_counter()
+            s.step(1)
+            one = time.perf_counter() - t
+            n = max(1, min(args.steps, int(120.0 / max(one, 1e-3))))
+            t = time.perf_counter()
+            s.step(n)
+            dt = time.perf_counter() - t
+            v = cfg["nx"] * cfg["ny"] * n / dt / 1e6
+            line = {"metric": METRIC, "value": v, "unit": "MLUPS", "impl": "reference",
+                    "n_gpus": args.gpus, "steps": n, "warmup": args.warmup,
+                    "ms_per_step": dt / n * 1e3, "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                    "config": workload_config(cfg, {"l2": "n/a (CPU)"}),
+                    "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.threads(),
+                                     "kind": "oracle",
+                                     "sample": "%d of %d requested steps of the full grid" % (n, args.steps)},
+                    "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                    "gpu_launches": 0}
+            print(json.dumps(line))
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+    res = run_gpu(args, rank, world, local_rank, args.storage)
+    fp64 = None
+    if not args.no_fp64_leg and args.storage != "f64":
+        a2 = argparse.Namespace(**vars(args))
+        a2.steps = min(args.steps, 50)
+        fp64 = run_gpu(a2, rank, world, local_rank, "f64", want_e2e=False)
+
+    K = args.steps
+    nodes = args.nx * args.ny
+    step_s = res["step_ms_total"] / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([step_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_s = float(t.item())
+    value = nodes * K * world / step_s / 1e6
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        Q, b = 37, BYTES_PER_VALUE[args.storage]
+        alg_bytes = 2 * Q * b * res["bulk_nodes"]
+        achieved = alg_bytes / (res["bulk_ms_mean"] / 1e3) / 1e9
+        traffic = bulk_traffic(args.storage, args.nx, args.ny)
+        launches_per_step = 1 + 4 + 1    # bulk, 4 RK4 stages, inflow nodes
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": res["step_ms_total"] / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f32": "f32", "f64": "f64", "f16": "f16-storage/f32"}[args.storage],
+            "data": "synthetic", "config": workload_config(res["cfg"]),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_bulk (stream+collide)", "peak_kind": peak_kind,
+                         "bytes_per_launch": alg_bytes,
+                         "bulk_ms": res["bulk_ms_mean"], "boundary_ms": res["boundary_ms_mean"]},
+            "e2e": res.get("e2e"),
+            "gpu_launches": launches_per_step * K,
+            "clocks": res["clocks"],
+            "finite": res["finite"],
+        }
+        if fp64 is not None:
+            line["fp64"] = {"value": nodes / (fp64["step_ms_total"] / 1e3 / min(K, 50)) / 1e6,
+                            "unit": "MLUPS", "bulk_ms": fp64["bulk_ms_mean"],
+                            "boundary_ms": fp64["boundary_ms_mean"],
+                            "bulk_GBps": 2 * Q * 8 * fp64["bulk_nodes"] / (fp64["bulk_ms_mean"] / 1e3) / 1e9}
+        if not args.no_cpu_baseline and world == 1:
+            cfg, fields = workload(args.nx, args.ny, "f64", 1)
+            line["cpu_baseline"] = cpu_baseline(cfg, fields)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * lbm_cbc.h -- C ABI of the GB300 (sm_103a) thermal lattice Boltzmann solver
+ * with the layer-wise characteristic boundary condition of Klass, Gabbana &
+ * Bartel, "Characteristic Boundary Condition for Thermal Lattice Boltzmann
+ * Methods" (arXiv 2307.16766).
+ *
+ * One time step (Fig. flowchart-lbm-algo) is a fused pull-stream + BGK
+ * collide over the bulk (Eqs. lbe, bgk, macro, feq-3/feq-4) followed by the
+ * boundary solver of Sec. 3: characteristic analysis on each of the M boundary
+ * layers (Eq. thermal_WAV), incoming amplitudes by Eqs. PNR / LODI-Relax /
+ * CBC-PNR / CBC-Relax (Tab. CBCs), RK4 in time (Sec. 3.3) and a mesoscopic
+ * Dirichlet write (equilibrium or Eq. NEEP).  Zero gradient (Eq. zg-bc) and a
+ * fixed inflow equilibrium are available per side; corners use LODI along the
+ * outward diagonal (Sec. 3.3, Fig. Layer-Multispeed-BC).
+ *
+ * Conventions
+ *  - Every function returns LBM_OK (0) or a negative LBM_ERR_* code; the text
+ *    of the last error of a handle is available from lbm_last_error().
+ *  - Grid arrays are row-major [ny][nx], x fastest, double precision.
+ *  - Sides are indexed W (-x) = 0, E (+x) = 1, S (-y) = 2, N (+y) = 3.
+ *  - T is the dimensionless temperature (T~ = c_s^2 T, reference T0 = 1).
+ *  - The library owns every device buffer it allocates; with lbm_create_in()
+ *    the caller owns the workspace and must keep it alive until
+ *    lbm_destroy().  Caller arrays passed to a call are only borrowed for the
+ *    duration of that call.
+ *  - Work is issued on the handle's CUDA stream (default: the legacy default
+ *    stream; see lbm_set_stream()).  lbm_step() is asynchronous; the calls
+ *    that return data to the caller synchronise the stream.
+ *  - A handle must not be used from two threads at once.
+ */
+#ifndef LBM_CBC_H
+#define LBM_CBC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK              0
+#define LBM_ERR_ARG        -1   /* invalid argument or configuration            */
+#define LBM_ERR_ALLOC      -2   /* device or host allocation failed             */
+#define LBM_ERR_CUDA       -3   /* a CUDA call failed (message has the reason)  */
+#define LBM_ERR_NUMERICAL  -4   /* non-finite macroscopic values were produced  */
+#define LBM_ERR_STATE      -5   /* call out of order (e.g. step before init)    */
+
+/* Velocity sets (Appendix B): D2Q9 (M = 1, isothermal, second-order
+ * equilibrium) and D2Q37 (M = 3, fourth-order Hermite equilibrium, Eq. feq-4). */
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D2Q37 = 1 };
+
+/* Storage of the populations, always shifted by the rest state,
+ * g_i = f_i - w_i rho0.  F64: double, FP64 arithmetic.  F32: float, FP32
+ * arithmetic.  F16: half holding g_i / w_i, FP32 arithmetic.  The boundary
+ * solver always runs in FP64. */
+enum lbm_storage { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2 };
+
+enum lbm_side_kind {
+    LBM_SIDE_PERIODIC = 0,   /* both sides of an axis must be periodic or neither */
+    LBM_SIDE_CBC      = 1,   /* characteristic boundary condition (Sec. 3)       */
+    LBM_SIDE_INFLOW   = 2,   /* equilibrium of the fixed inflow state            */
+    LBM_SIDE_ZG       = 3    /* zero gradient, Eq. zg-bc                         */
+};
+
+/* Incoming-wave treatment of a CBC side (Tab. CBCs). */
+enum lbm_scheme { LBM_LODI = 0, LBM_LODI_RELAX = 1, LBM_CBC = 2, LBM_CBC_RELAX = 3 };
+
+/* Viscous vector V of the CBC schemes: mesoscopic (Eqs. LaplaceU, LaplaceT,
+ * evaluated at the bulk node next to the boundary), finite differences of the
+ * macros ("-FD" of Sec. 4.2), or none. */
+enum lbm_viscous { LBM_VISCOUS_MESO = 0, LBM_VISCOUS_FD = 1, LBM_VISCOUS_OFF = 2 };
+
+/* Mesoscopic Dirichlet condition (Sec. 3.3): equilibrium, or Eq. NEEP. */
+enum lbm_dirichlet { LBM_DIRICHLET_EQ = 0, LBM_DIRICHLET_NEEP = 1 };
+
+typedef struct lbm_cbc_params {
+    int    side[4];     /* enum lbm_side_kind per side (W, E, S, N)                   */
+    int    scheme[4];   /* enum lbm_scheme per CBC side                                */
+    int    viscous;     /* enum lbm_viscous                                            */
+    int    dirichlet;   /* enum lbm_dirichlet                                          */
+    double alpha_T;     /* alpha of Eqs. CBC-Relax / LODI-Relax: transversal relaxation */
+    double beta_P;      /* beta of Eqs. CBC-Relax / LODI-Relax: pressure relaxation     */
+    double t_inf;       /* target transversal amplitude T^inf (the paper uses 0)        */
+    double p_inf[4];    /* target pressure Z_inf = P_inf per side, P = rho c_s^2 T      */
+    double inflow[4];   /* rho, ux, uy, T imposed on LBM_SIDE_INFLOW sides              */
+    int    storage;     /* enum lbm_storage                                             */
+    double rho0;        /* reference density of the population shift                   */
+} lbm_cbc_params;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Fill p with defaults: all sides periodic, CBC-RELAX, mesoscopic viscous
+ * terms, equilibrium Dirichlet, alpha_T = beta_P = t_inf = 0,
+ * p_inf = rho0 c_s^2 (set per lattice by lbm_create when left at 0),
+ * inflow = (1, 0, 0, 1), F32 storage, rho0 = 1. */
+int lbm_params_default(lbm_cbc_params* p);
+
+/* Bytes of device workspace a configuration needs (for lbm_create_in). */
+int lbm_workspace_bytes(int lattice, int nx, int ny, const lbm_cbc_params* p, size_t* bytes);
+
+/* Create a solver for an nx x ny grid with BGK relaxation time tau > 1/2
+ * (Eq. bgk).  Non-periodic axes need at least 2M + 3 nodes; when both axes
+ * are non-periodic, either all four sides are CBC or none is.  Allocates its
+ * device memory with cudaMalloc on the current device. */
+int lbm_create(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p,
+               lbm_handle** out);
+
+/* As lbm_create, but carves every device buffer out of the caller's
+ * workspace (device pointer, 256-byte aligned, at least
+ * lbm_workspace_bytes()).  No device memory is allocated. */
+int lbm_create_in(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p,
+                  void* dev_workspace, size_t workspace_bytes, lbm_handle** out);
+
+/* Issue all further work on stream (a cudaStream_t; NULL = legacy default). */
+int lbm_set_stream(lbm_handle* h, void* stream);
+
+/* Initialise f = f^eq(rho, u, T) on every node (Sec. 2) and the boundary
+ * state from the same fields.  Arrays are [ny][nx] doubles, on the device
+ * when on_device != 0, else in host memory (copied in on the handle's stream).
+ * For D2Q9, T is ignored (isothermal).  Resets the step counter. */
+int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
+                    const double* uy, const double* T, int on_device);
+
+/* Advance n time steps (asynchronous on the handle's stream). */
+int lbm_step(lbm_handle* h, int n);
+
+/* Issue one phase of one step: 0 = bulk stream-collide, 1 = boundary
+ * conditions (ends the step).  Used to time the phases separately; a step
+ * is phase 0 then phase 1. */
+int lbm_step_phase(lbm_handle* h, int phase);
+
+/* Macroscopic fields of the current populations (Eq. macro): absolute rho,
+ * ux, uy and T ([ny][nx] doubles; T = 1 for D2Q9).  Device or host arrays as
+ * on_device says.  Synchronises the stream.  Returns LBM_ERR_NUMERICAL (after
+ * filling the arrays) if any value is not finite. */
+int lbm_get_macros(lbm_handle* h, double* rho, double* ux, double* uy, double* T,
+                   int on_device);
+
+/* Checkpoint / resume: the populations, the boundary state and the step
+ * counter, as an opaque host buffer of lbm_state_bytes() bytes.  Restoring a
+ * state reproduces the continuation bit for bit. */
+int lbm_state_bytes(const lbm_handle* h, size_t* bytes);
+int lbm_get_state(lbm_handle* h, void* host_buf, size_t bytes);
+int lbm_set_state(lbm_handle* h, const void* host_buf, size_t bytes);
+
+/* Steps taken since lbm_init_fields (or restored with lbm_set_state). */
+long long lbm_steps_done(const lbm_handle* h);
+
+/* Text of the last error on h (never NULL; empty when none). */
+const char* lbm_last_error(const lbm_handle* h);
+
+/* Free everything the handle owns.  NULL is ignored. */
+void lbm_destroy(lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_CBC_H */

@@ -1,0 +1,302 @@
+"""GB300 (sm_103a) thermal lattice Boltzmann solver with the layer-wise
+characteristic boundary condition of Klass, Gabbana & Bartel (arXiv 2307.16766).
+
+A thin ctypes binding of the C ABI declared in ``include/lbm_cbc.h``: the
+functions below carry the C names and only marshal arguments; every step of
+the method runs in the CUDA kernels of ``csrc/``.  PyTorch is used only to
+provide device memory (the solver workspace) and the CUDA stream.
+
+Quick use::
+
+    import lbm_workloads as W, paper_2307_16766_gb300 as lbm
+    cfg, fields = W.pulse_d2q37(256, alpha_T=0.5, steps=100)
+    sim = lbm.Simulation(cfg)          # workspace from torch, torch's stream
+    sim.init_fields(*fields)
+    sim.step(100)
+    rho, ux, uy, T = sim.macros()      # numpy [ny, nx] arrays
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "LbmCbcParams", "LBM_D2Q9", "LBM_D2Q37", "LBM_F64", "LBM_F32", "LBM_F16",
+    "lbm_params_default", "lbm_workspace_bytes", "lbm_create", "lbm_create_in",
+    "lbm_set_stream", "lbm_init_fields", "lbm_step", "lbm_step_phase", "lbm_get_macros",
+    "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_steps_done",
+    "lbm_last_error", "lbm_destroy", "Simulation", "params_from_run", "LbmError",
+]
+
+LBM_D2Q9, LBM_D2Q37 = 0, 1
+LBM_F64, LBM_F32, LBM_F16 = 0, 1, 2
+LATTICES = {"D2Q9": LBM_D2Q9, "D2Q37": LBM_D2Q37}
+STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16}
+SIDES = {"periodic": 0, "cbc": 1, "inflow": 2, "zg": 3}
+SCHEMES = {"lodi": 0, "lodi_relax": 1, "cbc": 2, "cbc_relax": 3}
+VISCOUS = {"meso": 0, "fd": 1, "off": 2}
+DIRICHLET = {"eq": 0, "neep": 1}
+ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_ALLOC", -3: "LBM_ERR_CUDA",
+          -4: "LBM_ERR_NUMERICAL", -5: "LBM_ERR_STATE"}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "error"), code, msg))
+        self.code = code
+
+
+class LbmCbcParams(C.Structure):
+    """Mirror of ``lbm_cbc_params``."""
+    _fields_ = [
+        ("side", C.c_int * 4), ("scheme", C.c_int * 4), ("viscous", C.c_int),
+        ("dirichlet", C.c_int), ("alpha_T", C.c_double), ("beta_P", C.c_double),
+        ("t_inf", C.c_double), ("p_inf", C.c_double * 4), ("inflow", C.c_double * 4),
+        ("storage", C.c_int), ("rho0", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library, building it in-tree if needed.  There is no
+    fallback: without the library nothing in this package runs."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            path = _build.build()
+        L = C.CDLL(path)
+        vp, dp, sz = C.c_void_p, C.POINTER(C.c_double), C.c_size_t
+        pp = C.POINTER(LbmCbcParams)
+        sig = {
+            "lbm_params_default": (C.c_int, [pp]),
+            "lbm_workspace_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, pp, C.POINTER(sz)]),
+            "lbm_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, pp, C.POINTER(vp)]),
+            "lbm_create_in": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, pp, vp, sz, C.POINTER(vp)]),
+            "lbm_set_stream": (C.c_int, [vp, vp]),
+            "lbm_init_fields": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
+            "lbm_step": (C.c_int, [vp, C.c_int]),
+            "lbm_step_phase": (C.c_int, [vp, C.c_int]),
+            "lbm_get_macros": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
+            "lbm_state_bytes": (C.c_int, [vp, C.POINTER(sz)]),
+            "lbm_get_state": (C.c_int, [vp, vp, sz]),
+            "lbm_set_state": (C.c_int, [vp, vp, sz]),
+            "lbm_steps_done": (C.c_longlong, [vp]),
+            "lbm_last_error": (C.c_char_p, [vp]),
+            "lbm_destroy": (None, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        del dp
+        _lib = L
+    return _lib
+
+
+def _check(rc, h=None):
+    if rc != 0:
+        msg = lib().lbm_last_error(h).decode() if h else ""
+        raise LbmError(rc, msg)
+
+
+def params_from_run(cfg) -> LbmCbcParams:
+    """Build ``lbm_cbc_params`` from a run description (see lbm_workloads.run)."""
+    p = LbmCbcParams()
+    _check(lib().lbm_params_default(C.byref(p)))
+    for i, s in enumerate(cfg.get("sides", ["periodic"] * 4)):
+        p.side[i] = SIDES[s]
+    for i, s in enumerate(cfg.get("schemes", ["cbc_relax"] * 4)):
+        p.scheme[i] = SCHEMES[s]
+    p.viscous = VISCOUS[cfg.get("viscous", "meso")]
+    p.dirichlet = DIRICHLET[cfg.get("dirichlet", "eq")]
+    p.alpha_T = float(cfg.get("alpha_T", 0.0))
+    p.beta_P = float(cfg.get("beta_P", 0.0))
+    p.t_inf = float(cfg.get("t_inf", 0.0))
+    for i, v in enumerate(cfg.get("p_inf", [0.0] * 4)):
+        p.p_inf[i] = float(v)
+    for i, v in enumerate(cfg.get("inflow", [1.0, 0.0, 0.0, 1.0])):
+        p.inflow[i] = float(v)
+    p.storage = STORAGES[cfg.get("storage", "f32")]
+    p.rho0 = float(cfg.get("rho0", 1.0))
+    return p
+
+
+# ----------------------------------------------------------- C ABI names ---
+
+def lbm_params_default() -> LbmCbcParams:
+    p = LbmCbcParams()
+    _check(lib().lbm_params_default(C.byref(p)))
+    return p
+
+
+def lbm_workspace_bytes(lattice, nx, ny, params) -> int:
+    n = C.c_size_t()
+    _check(lib().lbm_workspace_bytes(int(lattice), int(nx), int(ny), C.byref(params), C.byref(n)))
+    return n.value
+
+
+def lbm_create(lattice, nx, ny, tau, params):
+    h = C.c_void_p()
+    _check(lib().lbm_create(int(lattice), int(nx), int(ny), float(tau), C.byref(params), C.byref(h)))
+    return h
+
+
+def lbm_create_in(lattice, nx, ny, tau, params, dev_ptr, nbytes):
+    h = C.c_void_p()
+    _check(lib().lbm_create_in(int(lattice), int(nx), int(ny), float(tau), C.byref(params),
+                               C.c_void_p(dev_ptr), C.c_size_t(nbytes), C.byref(h)))
+    return h
+
+
+def lbm_set_stream(h, stream_ptr):
+    _check(lib().lbm_set_stream(h, C.c_void_p(stream_ptr)), h)
+
+
+def _field_ptr(a, n):
+    """(pointer, on_device, keepalive) for a float64 field of n values:
+    a CUDA torch tensor stays on the device, anything else goes through a
+    contiguous host float64 array."""
+    mod = type(a).__module__
+    if mod.startswith("torch") and getattr(a, "is_cuda", False):
+        import torch
+        t = a.detach().to(torch.float64).contiguous()
+        if t.numel() != n:
+            raise ValueError("field has %d values, expected %d" % (t.numel(), n))
+        return t.data_ptr(), 1, t
+    if mod.startswith("torch"):
+        a = a.detach().cpu().numpy()
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if arr.size != n:
+        raise ValueError("field has %d values, expected %d" % (arr.size, n))
+    return arr.ctypes.data, 0, arr
+
+
+def lbm_init_fields(h, n_nodes, rho, ux, uy, T):
+    """Fields as numpy arrays (host) or CUDA torch tensors (device)."""
+    ptrs = [_field_ptr(a, n_nodes) for a in (rho, ux, uy, T)]
+    on_dev = {p[1] for p in ptrs}
+    if len(on_dev) != 1:
+        raise ValueError("all four fields must be on the host or all on the device")
+    _check(lib().lbm_init_fields(h, *[C.c_void_p(p[0]) for p in ptrs], on_dev.pop()), h)
+
+
+def lbm_step(h, n):
+    _check(lib().lbm_step(h, int(n)), h)
+
+
+def lbm_step_phase(h, phase):
+    _check(lib().lbm_step_phase(h, int(phase)), h)
+
+
+def lbm_get_macros(h, rho, ux, uy, T, on_device):
+    """Fill four preallocated outputs (pointers as ints)."""
+    _check(lib().lbm_get_macros(h, C.c_void_p(rho), C.c_void_p(ux), C.c_void_p(uy),
+                                C.c_void_p(T), int(on_device)), h)
+
+
+def lbm_state_bytes(h) -> int:
+    n = C.c_size_t()
+    _check(lib().lbm_state_bytes(h, C.byref(n)), h)
+    return n.value
+
+
+def lbm_get_state(h) -> bytes:
+    n = lbm_state_bytes(h)
+    buf = C.create_string_buffer(n)
+    _check(lib().lbm_get_state(h, buf, n), h)
+    return buf.raw
+
+
+def lbm_set_state(h, state: bytes):
+    buf = C.create_string_buffer(state, len(state))
+    _check(lib().lbm_set_state(h, buf, len(state)), h)
+
+
+def lbm_steps_done(h) -> int:
+    return lib().lbm_steps_done(h)
+
+
+def lbm_last_error(h) -> str:
+    return lib().lbm_last_error(h).decode()
+
+
+def lbm_destroy(h):
+    if h:
+        lib().lbm_destroy(h)
+
+
+# ---------------------------------------------------------- convenience ---
+
+class Simulation:
+    """One solver instance built from a run description.
+
+    The device workspace is a torch uint8 tensor (``lbm_create_in``) and work
+    is issued on torch's current CUDA stream, so torch events and streams
+    order with the solver's kernels.
+    """
+
+    def __init__(self, cfg, device=None):
+        import torch
+        self.cfg = dict(cfg)
+        self.lattice = LATTICES[cfg["lattice"]]
+        self.nx, self.ny = int(cfg["nx"]), int(cfg["ny"])
+        self.tau = float(cfg["tau"])
+        self.params = params_from_run(cfg)
+        self.device = torch.device(device or "cuda")
+        nbytes = lbm_workspace_bytes(self.lattice, self.nx, self.ny, self.params)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        off = (-base) % 256
+        self.handle = lbm_create_in(self.lattice, self.nx, self.ny, self.tau, self.params,
+                                    base + off, nbytes)
+        self.stream = torch.cuda.current_stream(self.device)
+        lbm_set_stream(self.handle, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def steps_done(self):
+        return lbm_steps_done(self.handle)
+
+    def init_fields(self, rho, ux, uy, T):
+        lbm_init_fields(self.handle, self.nx * self.ny, rho, ux, uy, T)
+        return self
+
+    def step(self, n=1):
+        lbm_step(self.handle, n)
+        return self
+
+    def step_phase(self, phase):
+        lbm_step_phase(self.handle, phase)
+
+    def macros(self, device=False):
+        """(rho, ux, uy, T): numpy [ny, nx] arrays, or CUDA tensors if device."""
+        import torch
+        if device:
+            out = [torch.empty((self.ny, self.nx), dtype=torch.float64, device=self.device)
+                   for _ in range(4)]
+            lbm_get_macros(self.handle, *[t.data_ptr() for t in out], 1)
+            return tuple(out)
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        lbm_get_macros(self.handle, *[a.ctypes.data for a in out], 0)
+        return tuple(out)
+
+    def get_state(self) -> bytes:
+        return lbm_get_state(self.handle)
+
+    def set_state(self, state: bytes):
+        lbm_set_state(self.handle, state)

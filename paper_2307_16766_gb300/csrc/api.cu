@@ -1,0 +1,531 @@
+// api.cu -- host runtime behind the C ABI of include/lbm_cbc.h.
+//
+// A handle owns (or borrows, with lbm_create_in) one device workspace carved
+// into: the two population buffers (ping-pong by step parity), the
+// near-boundary strips exported by the bulk kernel, the boundary ODE state
+// and RK4 stage buffers, a macro buffer and a status flag.  Every launch goes
+// to the handle's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbm_cbc.h"
+#include "lbm_internal.cuh"
+
+using namespace lbmgb;
+
+struct lbm_handle {
+    int lattice = 0, nx = 0, ny = 0, M = 0, Q = 0, storage = 0;
+    double tau = 0;
+    lbm_cbc_params P{};
+    Geom G{};
+    Band B{};
+    size_t esize = 0, f_bytes = 0, stripU_n = 0, stripN_n = 0;
+    void* f[2] = {nullptr, nullptr};
+    double* macro = nullptr;
+    int* flag = nullptr;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool owns_ws = false;
+    cudaStream_t stream = nullptr;
+    long long steps = 0;
+    bool initialized = false;
+    bool bulk_pending = false;   // phase 0 issued, phase 1 not yet
+    std::string err;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Plan {
+    Geom G{};
+    Band B{};
+    int Q = 0;
+    size_t esize = 0, f_bytes = 0, stripU_n = 0, stripN_n = 0;
+    size_t off_f0 = 0, off_f1 = 0, off_sU = 0, off_sN = 0, off_Ub = 0, off_Ya = 0, off_Yb = 0,
+           off_acc = 0, off_V = 0, off_mask = 0, off_macro = 0, off_flag = 0, total = 0;
+};
+
+std::string fmt(const char* f, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, f);
+    vsnprintf(buf, sizeof buf, f, ap);
+    va_end(ap);
+    return buf;
+}
+
+double lattice_cs2(int lattice) { return lattice == LBM_D2Q9 ? Lat<D2Q9>::CS2 : Lat<D2Q37>::CS2; }
+
+// Validate a configuration and lay out the workspace.
+int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, Plan& pl,
+              std::string& err)
+{
+    if (!p) { err = "params is NULL"; return LBM_ERR_ARG; }
+    if (lattice != LBM_D2Q9 && lattice != LBM_D2Q37) { err = fmt("unknown lattice %d", lattice); return LBM_ERR_ARG; }
+    if (!(tau > 0.5) || !std::isfinite(tau)) { err = fmt("tau must exceed 1/2 (got %g)", tau); return LBM_ERR_ARG; }
+    if (p->storage < LBM_F64 || p->storage > LBM_F16) { err = fmt("unknown storage %d", p->storage); return LBM_ERR_ARG; }
+    if (!(p->rho0 > 0.0)) { err = "rho0 must be positive"; return LBM_ERR_ARG; }
+    if (p->viscous < 0 || p->viscous > 2) { err = "unknown viscous mode"; return LBM_ERR_ARG; }
+    if (p->dirichlet < 0 || p->dirichlet > 1) { err = "unknown Dirichlet mode"; return LBM_ERR_ARG; }
+    for (int s = 0; s < 4; ++s) {
+        if (p->side[s] < 0 || p->side[s] > 3) { err = fmt("unknown kind %d of side %d", p->side[s], s); return LBM_ERR_ARG; }
+        if (p->scheme[s] < 0 || p->scheme[s] > 3) { err = fmt("unknown scheme of side %d", s); return LBM_ERR_ARG; }
+    }
+    const int perx = p->side[0] == LBM_SIDE_PERIODIC, pery = p->side[2] == LBM_SIDE_PERIODIC;
+    if (perx != (p->side[1] == LBM_SIDE_PERIODIC) || pery != (p->side[3] == LBM_SIDE_PERIODIC)) {
+        err = "a periodic side needs a periodic opposite side";
+        return LBM_ERR_ARG;
+    }
+    const int M = lattice == LBM_D2Q9 ? 1 : 3;
+    const int Q = lattice == LBM_D2Q9 ? 9 : 37;
+    const int nmin_b = 2 * M + 3;
+    if (nx < 1 || ny < 1 || nx > (1 << 20) || ny > 65535) { err = fmt("grid %d x %d out of range", nx, ny); return LBM_ERR_ARG; }
+    if ((!perx && nx < nmin_b) || (!pery && ny < nmin_b)) {
+        err = fmt("non-periodic axes need at least %d nodes", nmin_b);
+        return LBM_ERR_ARG;
+    }
+    if ((perx && nx < M) || (pery && ny < M)) { err = fmt("periodic axes need at least %d nodes", M); return LBM_ERR_ARG; }
+    if (!perx && !pery) {
+        int ncbc = 0;
+        for (int s = 0; s < 4; ++s) ncbc += p->side[s] == LBM_SIDE_CBC;
+        if (ncbc != 0 && ncbc != 4) { err = "with four open sides, either all or none must be CBC"; return LBM_ERR_ARG; }
+    }
+
+    Geom& G = pl.G;
+    G.nx = nx;
+    G.ny = ny;
+    G.M = M;
+    G.nxp = (nx + 63) / 64 * 64;
+    G.perx = perx;
+    G.pery = pery;
+    G.bx0 = perx ? 0 : M;
+    G.bx1 = perx ? nx : nx - M;
+    G.by0 = pery ? 0 : M;
+    G.by1 = pery ? ny : ny - M;
+    G.plane = (long long)ny * G.nxp;
+    G.tau = tau;
+    G.rho0 = p->rho0;
+
+    Band& B = pl.B;
+    std::memset(&B, 0, sizeof B);
+    const double cs2 = lattice_cs2(lattice);
+    size_t totU = 0, totN = 0;
+    for (int s = 0; s < 4; ++s) {
+        Side& S = B.s[s];
+        S.kind = p->side[s];
+        S.scheme = p->scheme[s];
+        S.L = s < 2 ? ny : nx;
+        S.tper = s < 2 ? pery : perx;
+        S.lo = S.tper ? 0 : M;
+        S.hi = S.tper ? S.L - 1 : S.L - 1 - M;
+        if (S.kind == LBM_SIDE_CBC) {
+            S.base = B.n_side_unk;
+            B.n_side_unk += (S.hi - S.lo + 1) * M;
+            S.offU = (long long)totU;
+            S.offN = (long long)totN;
+            totU += 2ull * 3 * S.L * 4;
+            totN += 2ull * 3 * S.L * 5;
+            B.any_cbc = 1;
+        } else if (S.kind == LBM_SIDE_INFLOW || S.kind == LBM_SIDE_ZG) {
+            S.ebase = B.n_extra_side;
+            B.n_extra_side += (S.hi - S.lo + 1) * M;
+        }
+        const double pinf = p->p_inf[s] != 0.0 ? p->p_inf[s] : cs2 * p->rho0;
+        B.pdev[s] = pinf - cs2 * p->rho0;
+    }
+    B.corner_kind = -1;
+    if (!perx && !pery) {
+        if (p->side[0] == LBM_SIDE_CBC) B.corner_kind = SIDE_CBC;
+        else if (p->side[0] == LBM_SIDE_INFLOW || p->side[1] == LBM_SIDE_INFLOW ||
+                 p->side[2] == LBM_SIDE_INFLOW || p->side[3] == LBM_SIDE_INFLOW)
+            B.corner_kind = SIDE_INFLOW;
+        else B.corner_kind = SIDE_ZG;
+    }
+    B.n_unk = B.n_side_unk + (B.corner_kind == SIDE_CBC ? 4 : 0);
+    B.n_extra = B.n_extra_side + ((B.corner_kind == SIDE_ZG || B.corner_kind == SIDE_INFLOW) ? 4 * M * M : 0);
+    B.viscous = p->viscous;
+    B.dirichlet = p->dirichlet;
+    B.alpha_T = p->alpha_T;
+    B.beta_P = p->beta_P;
+    B.t_inf = p->t_inf;
+    B.Uin[0] = p->inflow[0] - p->rho0;
+    B.Uin[1] = p->inflow[1];
+    B.Uin[2] = p->inflow[2];
+    B.Uin[3] = lattice == LBM_D2Q37 ? p->inflow[3] - 1.0 : 0.0;
+
+    pl.Q = Q;
+    pl.esize = p->storage == LBM_F64 ? 8 : (p->storage == LBM_F32 ? 4 : 2);
+    pl.f_bytes = (size_t)Q * (size_t)G.plane * pl.esize;
+    pl.stripU_n = totU;
+    pl.stripN_n = totN;
+    const size_t nu = (size_t)B.n_unk;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes); return at; };
+    pl.off_f0 = take(pl.f_bytes);
+    pl.off_f1 = take(pl.f_bytes);
+    pl.off_sU = take(totU * 8);
+    pl.off_sN = take(totN * 8);
+    pl.off_Ub = take(nu * 32);
+    pl.off_Ya = take(nu * 32);
+    pl.off_Yb = take(nu * 32);
+    pl.off_acc = take(nu * 32);
+    pl.off_V = take(nu * 32);
+    pl.off_mask = take(nu * 4);
+    pl.off_macro = take((size_t)4 * nx * ny * 8);
+    pl.off_flag = take(sizeof(int));
+    pl.total = o;
+    return LBM_OK;
+}
+
+template <typename T>
+T* at(void* base, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(base) + off); }
+
+int cuda_fail(lbm_handle* h, cudaError_t e, const char* what)
+{
+    if (h) h->err = fmt("%s: %s", what, cudaGetErrorString(e));
+    return LBM_ERR_CUDA;
+}
+
+int check_launch(lbm_handle* h, int rc, const char* what)
+{
+    if (rc == 0) return LBM_OK;
+    const cudaError_t e = cudaGetLastError();
+    return cuda_fail(h, e == cudaSuccess ? cudaErrorLaunchFailure : e, what);
+}
+
+int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_params* p,
+          const Plan& pl, void* ws, size_t ws_bytes, bool owns)
+{
+    h->lattice = lattice;
+    h->nx = nx;
+    h->ny = ny;
+    h->M = pl.G.M;
+    h->Q = pl.Q;
+    h->tau = tau;
+    h->P = *p;
+    h->storage = p->storage;
+    h->G = pl.G;
+    h->B = pl.B;
+    h->esize = pl.esize;
+    h->f_bytes = pl.f_bytes;
+    h->stripU_n = pl.stripU_n;
+    h->stripN_n = pl.stripN_n;
+    h->ws = ws;
+    h->ws_bytes = ws_bytes;
+    h->owns_ws = owns;
+    h->f[0] = at<char>(ws, pl.off_f0);
+    h->f[1] = at<char>(ws, pl.off_f1);
+    h->B.stripU = at<double>(ws, pl.off_sU);
+    h->B.stripN = at<double>(ws, pl.off_sN);
+    h->B.Ub = at<double>(ws, pl.off_Ub);
+    h->B.Ya = at<double>(ws, pl.off_Ya);
+    h->B.Yb = at<double>(ws, pl.off_Yb);
+    h->B.acc = at<double>(ws, pl.off_acc);
+    h->B.V = at<double>(ws, pl.off_V);
+    h->B.mask = at<int>(ws, pl.off_mask);
+    h->macro = at<double>(ws, pl.off_macro);
+    h->flag = at<int>(ws, pl.off_flag);
+    // Zero the strips so that padding positions hold finite values.
+    cudaError_t e = cudaMemsetAsync(h->B.stripU, 0, pl.stripU_n * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->B.stripN, 0, pl.stripN_n * 8, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "workspace clear");
+    return LBM_OK;
+}
+
+int create_common(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, void* ws,
+                  size_t ws_bytes, lbm_handle** out)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    Plan pl;
+    std::string err;
+    int rc = make_plan(lattice, nx, ny, tau, p, pl, err);
+    if (rc != LBM_OK) {
+        fprintf(stderr, "lbm_create: %s\n", err.c_str());
+        return rc;
+    }
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_ERR_ALLOC;
+    bool owns = false;
+    if (ws) {
+        if (ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) {
+            fprintf(stderr, "lbm_create_in: workspace of %zu bytes at %p is too small or misaligned (%zu needed)\n",
+                    ws_bytes, ws, pl.total);
+            delete h;
+            return LBM_ERR_ARG;
+        }
+    } else {
+        const cudaError_t e = cudaMalloc(&ws, pl.total);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "lbm_create: cudaMalloc(%zu): %s\n", pl.total, cudaGetErrorString(e));
+            delete h;
+            return LBM_ERR_ALLOC;
+        }
+        ws_bytes = pl.total;
+        owns = true;
+    }
+    rc = setup(h, lattice, nx, ny, tau, p, pl, ws, ws_bytes, owns);
+    if (rc != LBM_OK) {
+        fprintf(stderr, "lbm_create: %s\n", h->err.c_str());
+        if (owns) cudaFree(ws);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_params_default(lbm_cbc_params* p)
+{
+    if (!p) return LBM_ERR_ARG;
+    std::memset(p, 0, sizeof *p);
+    for (int s = 0; s < 4; ++s) {
+        p->side[s] = LBM_SIDE_PERIODIC;
+        p->scheme[s] = LBM_CBC_RELAX;
+        p->p_inf[s] = 0.0;
+    }
+    p->viscous = LBM_VISCOUS_MESO;
+    p->dirichlet = LBM_DIRICHLET_EQ;
+    p->inflow[0] = 1.0;
+    p->inflow[3] = 1.0;
+    p->storage = LBM_F32;
+    p->rho0 = 1.0;
+    return LBM_OK;
+}
+
+int lbm_workspace_bytes(int lattice, int nx, int ny, const lbm_cbc_params* p, size_t* bytes)
+{
+    if (!bytes) return LBM_ERR_ARG;
+    Plan pl;
+    std::string err;
+    const int rc = make_plan(lattice, nx, ny, 0.75, p, pl, err);
+    if (rc != LBM_OK) return rc;
+    *bytes = pl.total;
+    return LBM_OK;
+}
+
+int lbm_create(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, lbm_handle** out)
+{
+    return create_common(lattice, nx, ny, tau, p, nullptr, 0, out);
+}
+
+int lbm_create_in(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p,
+                  void* dev_workspace, size_t workspace_bytes, lbm_handle** out)
+{
+    if (!dev_workspace) return LBM_ERR_ARG;
+    return create_common(lattice, nx, ny, tau, p, dev_workspace, workspace_bytes, out);
+}
+
+int lbm_set_stream(lbm_handle* h, void* stream)
+{
+    if (!h) return LBM_ERR_ARG;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux, const double* uy,
+                    const double* T, int on_device)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (!rho || !ux || !uy || (!T && h->lattice == LBM_D2Q37)) {
+        h->err = "NULL field";
+        return LBM_ERR_ARG;
+    }
+    const size_t n = (size_t)h->nx * h->ny;
+    const double *dr = rho, *du = ux, *dv = uy, *dt = T;
+    if (!on_device) {
+        double* m = h->macro;
+        const double* src[4] = {rho, ux, uy, T ? T : rho};
+        for (int c = 0; c < 4; ++c) {
+            const cudaError_t e = cudaMemcpyAsync(m + c * n, src[c], n * 8, cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy of initial fields");
+        }
+        dr = m;
+        du = m + n;
+        dv = m + 2 * n;
+        dt = m + 3 * n;
+    } else if (!dt) {
+        dt = dr;   // unused by the isothermal lattice
+    }
+    int rc = launch_init(h->lattice, h->storage, h->G, h->B, dr, du, dv, dt, h->f[0], h->stream);
+    if (rc) return check_launch(h, rc, "init kernels");
+    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "init");
+    h->steps = 0;
+    h->initialized = true;
+    h->bulk_pending = false;
+    return LBM_OK;
+}
+
+int lbm_step_phase(lbm_handle* h, int phase)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (!h->initialized) {
+        h->err = "lbm_step before lbm_init_fields";
+        return LBM_ERR_STATE;
+    }
+    const int par = int(h->steps & 1);
+    if (phase == 0) {
+        if (h->bulk_pending) { h->err = "bulk phase issued twice"; return LBM_ERR_STATE; }
+        const int rc = launch_bulk(h->lattice, h->storage, h->G, h->B, h->f[par], h->f[par ^ 1],
+                                   par ^ 1, h->stream);
+        if (rc) return check_launch(h, rc, "bulk kernel");
+        h->bulk_pending = true;
+        return LBM_OK;
+    }
+    if (phase == 1) {
+        if (!h->bulk_pending) { h->err = "boundary phase before bulk phase"; return LBM_ERR_STATE; }
+        const int rc = launch_boundary(h->lattice, h->storage, h->G, h->B, h->f[par ^ 1], par, h->stream);
+        if (rc) return check_launch(h, rc, "boundary kernels");
+        h->bulk_pending = false;
+        h->steps++;
+        return LBM_OK;
+    }
+    h->err = fmt("unknown phase %d", phase);
+    return LBM_ERR_ARG;
+}
+
+int lbm_step(lbm_handle* h, int n)
+{
+    if (!h || n < 0) return LBM_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        int rc = lbm_step_phase(h, 0);
+        if (rc == LBM_OK) rc = lbm_step_phase(h, 1);
+        if (rc != LBM_OK) return rc;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_macros(lbm_handle* h, double* rho, double* ux, double* uy, double* T, int on_device)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (!h->initialized) { h->err = "lbm_get_macros before lbm_init_fields"; return LBM_ERR_STATE; }
+    if (h->bulk_pending) { h->err = "lbm_get_macros in the middle of a step"; return LBM_ERR_STATE; }
+    if (!rho || !ux || !uy || !T) { h->err = "NULL output"; return LBM_ERR_ARG; }
+    const size_t n = (size_t)h->nx * h->ny;
+    double* d[4];
+    if (on_device) {
+        d[0] = rho; d[1] = ux; d[2] = uy; d[3] = T;
+    } else {
+        for (int c = 0; c < 4; ++c) d[c] = h->macro + c * n;
+    }
+    cudaError_t e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "flag reset");
+    const int rc = launch_macros(h->lattice, h->storage, h->G, h->f[h->steps & 1], d[0], d[1], d[2], d[3],
+                                 h->flag, h->stream);
+    if (rc) return check_launch(h, rc, "macros kernel");
+    if (!on_device) {
+        double* dst[4] = {rho, ux, uy, T};
+        for (int c = 0; c < 4; ++c) {
+            e = cudaMemcpyAsync(dst[c], d[c], n * 8, cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy of macros");
+        }
+    }
+    int flag = 0;
+    e = cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "macros");
+    if (flag) {
+        h->err = "non-finite macroscopic values";
+        return LBM_ERR_NUMERICAL;
+    }
+    return LBM_OK;
+}
+
+namespace {
+struct StateHeader {
+    char magic[8];
+    int lattice, nx, ny, storage, n_unk;
+    long long steps;
+    unsigned long long f_bytes, stripU_n, stripN_n;
+};
+}  // namespace
+
+int lbm_state_bytes(const lbm_handle* h, size_t* bytes)
+{
+    if (!h || !bytes) return LBM_ERR_ARG;
+    *bytes = sizeof(StateHeader) + h->f_bytes + (h->stripU_n + h->stripN_n + 4ull * h->B.n_unk) * 8;
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_handle* h, void* buf, size_t bytes)
+{
+    size_t need = 0;
+    if (lbm_state_bytes(h, &need) != LBM_OK || !buf) return LBM_ERR_ARG;
+    if (bytes < need) { h->err = fmt("state buffer needs %zu bytes", need); return LBM_ERR_ARG; }
+    if (!h->initialized || h->bulk_pending) { h->err = "no complete state to save"; return LBM_ERR_STATE; }
+    StateHeader hd{};
+    std::memcpy(hd.magic, "LBMCBC01", 8);
+    hd.lattice = h->lattice; hd.nx = h->nx; hd.ny = h->ny; hd.storage = h->storage; hd.n_unk = h->B.n_unk;
+    hd.steps = h->steps; hd.f_bytes = h->f_bytes; hd.stripU_n = h->stripU_n; hd.stripN_n = h->stripN_n;
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    cudaError_t e = cudaMemcpyAsync(p, h->f[h->steps & 1], h->f_bytes, cudaMemcpyDeviceToHost, h->stream);
+    p += h->f_bytes;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->B.stripU, h->stripU_n * 8, cudaMemcpyDeviceToHost, h->stream);
+    p += h->stripU_n * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->B.stripN, h->stripN_n * 8, cudaMemcpyDeviceToHost, h->stream);
+    p += h->stripN_n * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->B.Ub, 32ull * h->B.n_unk, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "state copy");
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes)
+{
+    size_t need = 0;
+    if (lbm_state_bytes(h, &need) != LBM_OK || !buf) return LBM_ERR_ARG;
+    if (bytes < need) { h->err = "state buffer too small"; return LBM_ERR_ARG; }
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (std::memcmp(hd.magic, "LBMCBC01", 8) != 0 || hd.lattice != h->lattice || hd.nx != h->nx ||
+        hd.ny != h->ny || hd.storage != h->storage || hd.n_unk != h->B.n_unk || hd.f_bytes != h->f_bytes ||
+        hd.stripU_n != h->stripU_n || hd.stripN_n != h->stripN_n) {
+        h->err = "state was saved from a different configuration";
+        return LBM_ERR_ARG;
+    }
+    const char* p = static_cast<const char*>(buf) + sizeof hd;
+    cudaError_t e = cudaMemcpyAsync(h->f[hd.steps & 1], p, h->f_bytes, cudaMemcpyHostToDevice, h->stream);
+    p += h->f_bytes;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.stripU, p, h->stripU_n * 8, cudaMemcpyHostToDevice, h->stream);
+    p += h->stripU_n * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.stripN, p, h->stripN_n * 8, cudaMemcpyHostToDevice, h->stream);
+    p += h->stripN_n * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.Ub, p, 32ull * h->B.n_unk, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "state restore");
+    h->steps = hd.steps;
+    h->initialized = true;
+    h->bulk_pending = false;
+    return LBM_OK;
+}
+
+long long lbm_steps_done(const lbm_handle* h) { return h ? h->steps : -1; }
+
+const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+void lbm_destroy(lbm_handle* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    if (h->owns_ws && h->ws) cudaFree(h->ws);
+    delete h;
+}
+
+}  // extern "C"

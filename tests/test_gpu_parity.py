@@ -1,0 +1,262 @@
+"""Parity of the CUDA path with the FP64 CPU oracle, element by element.
+
+Error measure per field (the reading of "relative" used throughout):
+  rel_Z = max |Z_gpu - Z_ref| / max |Z_ref|,  Z in {rho, T};
+  rel_u = max(|ux_gpu - ux_ref|, |uy_gpu - uy_ref|) / max(|ux_ref|, |uy_ref|).
+Bars: FP64 storage 1e-12, FP32 storage 1e-5 after the stated step counts;
+FP16 storage errors are reported per field against a loose bound.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import lbm_workloads as W
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def lbm():
+    import paper_2307_16766_gb300 as m
+    return m
+
+
+def gpu_run(cfg, fields, steps):
+    sim = lbm().Simulation(cfg).init_fields(*fields)
+    sim.step(steps)
+    out = sim.macros()
+    sim.close()
+    return out
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_cached(key):
+    cfg, fields, steps = _ORACLE_ARGS[key]
+    return oracle.Sim(cfg).init(*fields).step(steps).macros()
+
+
+_ORACLE_ARGS = {}
+
+
+def oracle_run(cfg, fields, steps, key=None):
+    if key is None:
+        return oracle.Sim(cfg).init(*fields).step(steps).macros()
+    _ORACLE_ARGS[key] = (cfg, fields, steps)
+    return _oracle_cached(key)
+
+
+def rel_errors(got, ref):
+    rho, ux, uy, T = got
+    r_rho, r_ux, r_uy, r_T = ref
+    umax = max(np.abs(r_ux).max(), np.abs(r_uy).max())
+    return {
+        "rho": np.abs(rho - r_rho).max() / np.abs(r_rho).max(),
+        "u": max(np.abs(ux - r_ux).max(), np.abs(uy - r_uy).max()) / umax,
+        "T": np.abs(T - r_T).max() / np.abs(r_T).max(),
+    }
+
+
+def assert_parity(cfg, fields, steps, storage="f64", key=None):
+    c = dict(cfg)
+    c["storage"] = storage
+    got = gpu_run(c, fields, steps)
+    ref = oracle_run(cfg, fields, steps, key)
+    for a in got:
+        assert np.all(np.isfinite(a))
+    e = rel_errors(got, ref)
+    tol = TOL[storage]
+    assert max(e.values()) < tol, (storage, e)
+    return e
+
+
+# ------------------------------------------------------------ D2Q9 cases ---
+
+def test_d2q9_pulse_64_full_200_steps():
+    """64 x 64 D2Q9 density pulse, CBC on four sides (-FD viscous), 200 steps."""
+    cfg, f = W.pulse_d2q9(64, 200)
+    assert_parity(cfg, f, 200)
+
+
+@pytest.mark.parametrize("scheme", ["lodi", "lodi_relax", "cbc", "cbc_relax"])
+@pytest.mark.parametrize("vis,dirichlet", [("meso", "eq"), ("fd", "neep"), ("off", "eq")])
+def test_d2q9_schemes(scheme, vis, dirichlet):
+    n, m = 45, 38
+    cfg = W.run("D2Q9", n, m, 0.65, sides=("cbc",) * 4, schemes=(scheme,) * 4, viscous=vis,
+                dirichlet=dirichlet, alpha_T=0.4, beta_P=0.3, p_inf=[W.CS2["D2Q9"] * 1.0005] * 4)
+    f = W.gaussian_pulse(n, m, 1e-3, 0.0, 4.0, center=(20.3, 17.6), u=(0.01, -0.02))
+    assert_parity(cfg, f, 90)
+
+
+@pytest.mark.parametrize("sides", [("zg",) * 4, ("inflow", "zg", "periodic", "periodic"),
+                                   ("periodic",) * 4, ("cbc", "cbc", "periodic", "periodic")])
+def test_d2q9_side_kinds(sides):
+    n, m = 70, 33
+    cfg = W.run("D2Q9", n, m, 0.7, sides=sides, schemes=("cbc_relax",) * 4, alpha_T=0.2,
+                inflow=(1.0, 0.03, 0.0, 1.0))
+    f = W.smooth_random(n, m, seed=5, amp=1e-3, lattice="D2Q9", u0=(0.02, 0.0))
+    assert_parity(cfg, f, 120)
+
+
+# ----------------------------------------------------------- D2Q37 cases ---
+
+def test_d2q37_pulse_ragged_grid():
+    """150 x 70 (two bulk tiles plus a ragged tail per row), CBC-RELAX with
+    mesoscopic viscous terms on four sides, 120 steps."""
+    cfg = W.run("D2Q37", 150, 70, 0.8, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4,
+                alpha_T=0.5, beta_P=0.1)
+    f = W.gaussian_pulse(150, 70, 1e-3, 1e-3, 6.0, center=(70.2, 33.9))
+    assert_parity(cfg, f, 120)
+
+
+@pytest.mark.parametrize("scheme", ["lodi", "lodi_relax", "cbc", "cbc_relax"])
+@pytest.mark.parametrize("vis", ["meso", "fd", "off"])
+@pytest.mark.parametrize("dirichlet", ["eq", "neep"])
+def test_d2q37_schemes(scheme, vis, dirichlet):
+    n, m = 37, 29
+    cs2 = W.CS2["D2Q37"]
+    cfg = W.run("D2Q37", n, m, 0.75, sides=("cbc",) * 4, schemes=(scheme,) * 4, viscous=vis,
+                dirichlet=dirichlet, alpha_T=0.3, beta_P=0.2, p_inf=[cs2 * 1.0002] * 4)
+    f = W.gaussian_pulse(n, m, 1e-3, 1e-3, 3.5, center=(17.4, 13.1), u=(0.01, 0.005))
+    assert_parity(cfg, f, 60)
+
+
+@pytest.mark.parametrize("sides", [("zg",) * 4, ("inflow", "zg", "zg", "zg"),
+                                   ("periodic",) * 4, ("periodic", "periodic", "cbc", "cbc")])
+def test_d2q37_side_kinds(sides):
+    n, m = 66, 40
+    cfg = W.run("D2Q37", n, m, 0.8, sides=sides, schemes=("cbc_relax",) * 4, alpha_T=0.5,
+                inflow=(1.0, 0.04, 0.0, 1.0))
+    f = W.smooth_random(n, m, seed=9, amp=1e-3, u0=(0.01, 0.0))
+    assert_parity(cfg, f, 100)
+
+
+def test_d2q37_vortex_through_outlet_small():
+    """Isentropic vortex convected through a CBC outlet (inflow left,
+    periodic y) on a reduced grid, Ma = 0.3, 400 steps."""
+    cfg, f = W.vortex_d2q37(160, 48, Ma=0.3, steps=400, storage="f64", radius=8.0)
+    assert_parity(cfg, f, 400)
+
+
+def test_d2q37_minimal_grid():
+    """Smallest admissible grid (2M + 3 = 9 nodes per open axis)."""
+    cfg = W.run("D2Q37", 9, 9, 0.9, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4, alpha_T=0.5)
+    f = W.gaussian_pulse(9, 9, 1e-3, 1e-3, 2.0)
+    assert_parity(cfg, f, 50)
+
+
+# -------------------------------------------------- full-size workloads ---
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0])
+def test_d2q37_pulse_256_full_2000_steps_f64_and_f32(alpha):
+    """D2Q37 256 x 256 rho+T pulse, CBC-RELAX on four sides, 2000 steps: FP64
+    storage to 1e-12 and FP32 storage to 1e-5 of the oracle."""
+    cfg, f = W.pulse_d2q37(256, alpha_T=alpha, steps=2000, storage="f64")
+    cfg["viscous"] = "off"
+    key = ("pulse256", alpha)
+    assert_parity(cfg, f, 2000, "f64", key)
+    assert_parity(cfg, f, 2000, "f32", key)
+
+
+def test_d2q37_pulse_256_meso_viscous_prefix():
+    """The same workload with mesoscopic viscous terms and alpha_T = 0 over
+    the first 300 steps (the scheme grows from a boundary at rest later)."""
+    cfg, f = W.pulse_d2q37(256, alpha_T=0.0, steps=300, storage="f64")
+    assert_parity(cfg, f, 300)
+
+
+def test_d2q37_vortex_1024x512_full_grid_short():
+    """The benchmark grid (1024 x 512 vortex, inflow | CBC, periodic y) in the
+    launch configuration the benchmark times, checked on every node after 20
+    steps in FP64 and FP32."""
+    cfg, f = W.vortex_d2q37(1024, 512, Ma=0.1, steps=20, storage="f64")
+    assert_parity(cfg, f, 20, "f64", "vortex1024")
+    assert_parity(cfg, f, 20, "f32", "vortex1024")
+
+
+def test_f16_storage_error_per_field(capsys):
+    """FP16 storage (g / w in half precision, FP32 arithmetic): errors against
+    the oracle are reported per field; they stay at the half-precision level."""
+    cfg = W.run("D2Q37", 128, 96, 0.8, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4,
+                alpha_T=0.5, viscous="off")
+    f = W.gaussian_pulse(128, 96, 1e-3, 1e-3, 6.0)
+    c = dict(cfg)
+    c["storage"] = "f16"
+    got = gpu_run(c, f, 300)
+    ref = oracle_run(cfg, f, 300)
+    e = rel_errors(got, ref)
+    with capsys.disabled():
+        print("\nFP16 storage, D2Q37 128x96, 300 steps: rel errors", {k: "%.2e" % v for k, v in e.items()})
+    assert e["rho"] < 1e-5 and e["T"] < 1e-5 and e["u"] < 5e-2
+
+
+# ---------------------------------------------------------- API behaviour ---
+
+def test_checkpoint_resume_is_bit_exact():
+    cfg, f = W.pulse_d2q37(64, alpha_T=0.5, steps=100, storage="f32", width=5.0, offset=3.0)
+    sim = lbm().Simulation(cfg).init_fields(*f)
+    sim.step(40)
+    state = sim.get_state()
+    sim.step(35)
+    a = sim.macros()
+    sim.set_state(state)
+    assert sim.steps_done == 40
+    sim.step(35)
+    b = sim.macros()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    sim.close()
+
+
+def test_zero_steps_and_device_fields():
+    import torch
+    cfg, f = W.pulse_d2q37(48, alpha_T=0.5, steps=0, storage="f64", width=4.0, offset=2.0)
+    sim = lbm().Simulation(cfg).init_fields(*f)
+    sim.step(0)
+    got = sim.macros()
+    for g, r in zip(got, f):
+        assert np.abs(g - r).max() < 1e-15
+    dev = [torch.tensor(a, device="cuda") for a in f]
+    sim.init_fields(*dev)
+    sim.step(10)
+    a = sim.macros(device=True)
+    sim.init_fields(*f)
+    sim.step(10)
+    b = sim.macros()
+    for x, y in zip(a, b):
+        assert np.array_equal(x.cpu().numpy(), y)
+    sim.close()
+
+
+def test_non_finite_fields_are_reported():
+    m = lbm()
+    cfg = W.run("D2Q9", 16, 16, 0.7)
+    f = list(W.uniform(16, 16))
+    f[0] = f[0].copy()
+    f[0][3, 4] = np.nan
+    sim = m.Simulation(cfg).init_fields(*f)
+    sim.step(2)
+    with pytest.raises(m.LbmError) as e:
+        sim.macros()
+    assert e.value.code == -4
+    sim.close()
+
+
+def test_phase_order_is_enforced():
+    m = lbm()
+    cfg = W.run("D2Q9", 16, 16, 0.7)
+    sim = m.Simulation(cfg)
+    with pytest.raises(m.LbmError) as e:
+        sim.step(1)
+    assert e.value.code == -5
+    sim.init_fields(*W.uniform(16, 16))
+    with pytest.raises(m.LbmError):
+        sim.step_phase(1)
+    sim.step_phase(0)
+    with pytest.raises(m.LbmError):
+        sim.macros()
+    sim.step_phase(1)
+    assert sim.steps_done == 1
+    sim.close()
