@@ -11,6 +11,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "lbm_cbc.h"
 #include "lbm_internal.cuh"
@@ -22,9 +23,15 @@ struct lbm_handle {
     double tau = 0;
     lbm_cbc_params P{};
     Geom G{};
+    Offsets O{};
+    Export E{};
     Band B{};
-    size_t esize = 0, f_bytes = 0, stripU_n = 0, stripN_n = 0;
+    size_t esize = 0, f_bytes = 0;
     void* f[2] = {nullptr, nullptr};
+    int* inflow_nodes = nullptr;
+    int n_inflow = 0;
+    bool inflow_done[2] = {false, false};   // buffer already holds the inflow equilibrium
+    double Uin[4] = {0, 0, 0, 0};
     double* macro = nullptr;
     int* flag = nullptr;
     void* ws = nullptr;
@@ -45,11 +52,18 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Plan {
     Geom G{};
+    Offsets O{};
+    Export E{};
     Band B{};
     int Q = 0;
     size_t esize = 0, f_bytes = 0, stripU_n = 0, stripN_n = 0;
+    std::vector<UDesc> ud;
+    std::vector<int2> zg;
+    std::vector<int> inflow;
+    double Uin[4] = {0, 0, 0, 0};
     size_t off_f0 = 0, off_f1 = 0, off_sU = 0, off_sN = 0, off_Ub = 0, off_Ya = 0, off_Yb = 0,
-           off_acc = 0, off_V = 0, off_mask = 0, off_macro = 0, off_flag = 0, total = 0;
+           off_acc = 0, off_V = 0, off_mask = 0, off_ud = 0, off_zg = 0, off_in = 0, off_macro = 0,
+           off_flag = 0, total = 0;
 };
 
 std::string fmt(const char* f, ...)
@@ -64,7 +78,23 @@ std::string fmt(const char* f, ...)
 
 double lattice_cs2(int lattice) { return lattice == LBM_D2Q9 ? Lat<D2Q9>::CS2 : Lat<D2Q37>::CS2; }
 
-// Validate a configuration and lay out the workspace.
+int lattice_cx(int lattice, int i) { return lattice == LBM_D2Q9 ? Lat<D2Q9>::cx(i) : Lat<D2Q37>::cx(i); }
+int lattice_cy(int lattice, int i) { return lattice == LBM_D2Q9 ? Lat<D2Q9>::cy(i) : Lat<D2Q37>::cy(i); }
+
+// Side geometry (W = 0, E = 1, S = 2, N = 3): outward normal and the layer-0
+// node x_f at tangential position p (Fig. Layer-Multispeed-BC).
+const int kSN[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+
+void side_xf(int s, int p, int nx, int ny, int M, int& x, int& y)
+{
+    if (s == 0) { x = M; y = p; }
+    else if (s == 1) { x = nx - 1 - M; y = p; }
+    else if (s == 2) { x = p; y = M; }
+    else { x = p; y = ny - 1 - M; }
+}
+
+// Validate a configuration, lay out the workspace and resolve the boundary
+// descriptors.
 int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, Plan& pl,
               std::string& err)
 {
@@ -98,12 +128,14 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
         for (int s = 0; s < 4; ++s) ncbc += p->side[s] == LBM_SIDE_CBC;
         if (ncbc != 0 && ncbc != 4) { err = "with four open sides, either all or none must be CBC"; return LBM_ERR_ARG; }
     }
+    const int nxp = (nx + 63) / 64 * 64;
+    if ((double)Q * ny * nxp >= 2147483647.0) { err = "grid too large (more than 2^31 population values)"; return LBM_ERR_ARG; }
 
     Geom& G = pl.G;
     G.nx = nx;
     G.ny = ny;
     G.M = M;
-    G.nxp = (nx + 63) / 64 * 64;
+    G.nxp = nxp;
     G.perx = perx;
     G.pery = pery;
     G.bx0 = perx ? 0 : M;
@@ -113,72 +145,169 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     G.plane = (long long)ny * G.nxp;
     G.tau = tau;
     G.rho0 = p->rho0;
+    G.omega = 1.0 / tau;
+    G.omega_f = float(1.0 / tau);
+    G.rho0_f = float(p->rho0);
+    for (int i = 0; i < Q; ++i) {
+        pl.O.st[i] = int(i * G.plane);
+        pl.O.ld[i] = int(i * G.plane) - lattice_cy(lattice, i) * nxp - lattice_cx(lattice, i);
+    }
+
+    // strips: slots (side, depth, position) of the characteristic sides
+    Export& E = pl.E;
+    int L[4], lo[4], hi[4], tper[4];
+    for (int s = 0; s < 4; ++s) {
+        L[s] = s < 2 ? ny : nx;
+        tper[s] = s < 2 ? pery : perx;
+        lo[s] = tper[s] ? 0 : M;
+        hi[s] = tper[s] ? L[s] - 1 : L[s] - 1 - M;
+        E.cbc[s] = p->side[s] == LBM_SIDE_CBC;
+        E.L[s] = L[s];
+        E.offS[s] = E.nslots;
+        if (E.cbc[s]) E.nslots += 3 * L[s];
+    }
+    auto slot = [&](int s, int d, int pp) {
+        if (tper[s]) pp = ((pp % L[s]) + L[s]) % L[s];
+        return E.offS[s] + d * L[s] + pp;
+    };
+    auto goff = [&](int x, int y) { return y * nxp + x; };
 
     Band& B = pl.B;
-    std::memset(&B, 0, sizeof B);
+    B.M = M;
     const double cs2 = lattice_cs2(lattice);
-    size_t totU = 0, totN = 0;
+    int corner_kind = -1;
+    if (!perx && !pery) {
+        if (p->side[0] == LBM_SIDE_CBC) corner_kind = SIDE_CBC;
+        else if (p->side[0] == LBM_SIDE_INFLOW || p->side[1] == LBM_SIDE_INFLOW ||
+                 p->side[2] == LBM_SIDE_INFLOW || p->side[3] == LBM_SIDE_INFLOW)
+            corner_kind = SIDE_INFLOW;
+        else corner_kind = SIDE_ZG;
+    }
+    // unknown index of side s, layer j, position pp (pp already in range)
+    int base[4] = {0, 0, 0, 0}, n_side = 0;
+    for (int s = 0; s < 4; ++s)
+        if (E.cbc[s]) { base[s] = n_side; n_side += (hi[s] - lo[s] + 1) * M; }
+    const int lo_corner[4] = {0, 1, 0, 2}, hi_corner[4] = {2, 3, 1, 3};
+    auto ref = [&](int s, int j, int pp) -> int {
+        if (tper[s]) pp = ((pp % L[s]) + L[s]) % L[s];
+        if (j <= 0) return -(slot(s, -j, pp) + 1);
+        if (pp < lo[s]) return n_side + lo_corner[s];
+        if (pp > hi[s]) return n_side + hi_corner[s];
+        return base[s] + (pp - lo[s]) * M + (j - 1);
+    };
     for (int s = 0; s < 4; ++s) {
-        Side& S = B.s[s];
-        S.kind = p->side[s];
-        S.scheme = p->scheme[s];
-        S.L = s < 2 ? ny : nx;
-        S.tper = s < 2 ? pery : perx;
-        S.lo = S.tper ? 0 : M;
-        S.hi = S.tper ? S.L - 1 : S.L - 1 - M;
-        if (S.kind == LBM_SIDE_CBC) {
-            S.base = B.n_side_unk;
-            B.n_side_unk += (S.hi - S.lo + 1) * M;
-            S.offU = (long long)totU;
-            S.offN = (long long)totN;
-            totU += 2ull * 3 * S.L * 4;
-            totN += 2ull * 3 * S.L * 5;
-            B.any_cbc = 1;
-        } else if (S.kind == LBM_SIDE_INFLOW || S.kind == LBM_SIDE_ZG) {
-            S.ebase = B.n_extra_side;
-            B.n_extra_side += (S.hi - S.lo + 1) * M;
+        if (!E.cbc[s]) continue;
+        for (int pp = lo[s]; pp <= hi[s]; ++pp)
+            for (int j = 1; j <= M; ++j) {
+                UDesc D;
+                std::memset(&D, 0, sizeof D);
+                D.kind = s;
+                D.j = j;
+                D.nb[0] = j < M ? ref(s, j + 1, pp) : 0;
+                D.nb[1] = ref(s, j - 1, pp);
+                D.nb[2] = ref(s, j - 2, pp);
+                D.nb[3] = j - 3 >= -2 ? ref(s, j - 3, pp) : 0;
+                D.nb[4] = ref(s, j, pp + 1);
+                D.nb[5] = ref(s, j, pp - 1);
+                D.tmode = tper[s] ? 0 : (pp == hi[s] ? 1 : (pp == lo[s] ? -1 : 0));
+                D.vs[0] = slot(s, 0, pp);
+                D.vs[1] = slot(s, 1, pp);
+                D.vs[2] = slot(s, 2, pp);
+                if (D.tmode == 0) { D.vs[3] = slot(s, 0, pp + 1); D.vs[4] = slot(s, 0, pp - 1); }
+                else if (D.tmode == 1) { D.vs[3] = slot(s, 0, pp - 1); D.vs[4] = slot(s, 0, pp - 2); }
+                else { D.vs[3] = slot(s, 0, pp + 1); D.vs[4] = slot(s, 0, pp + 2); }
+                int x, y;
+                side_xf(s, pp, nx, ny, M, x, y);
+                D.wsrc = goff(x, y);
+                D.wslot = slot(s, 0, pp);
+                D.wnode = goff(x + j * kSN[s][0], y + j * kSN[s][1]);
+                pl.ud.push_back(D);
+            }
+    }
+    if (corner_kind == SIDE_CBC)
+        for (int c = 0; c < 4; ++c) {
+            UDesc D;
+            std::memset(&D, 0, sizeof D);
+            const int sx = (c & 1) ? 1 : -1, sy = (c & 2) ? 1 : -1;
+            const int sW = sx < 0 ? 0 : 1;
+            const int xc = sx < 0 ? M - 1 : nx - M, yc = sy < 0 ? M - 1 : ny - M;
+            D.kind = 4 + c;
+            D.nb[0] = -(slot(sW, 0, yc - sy) + 1);
+            D.nb[1] = -(slot(sW, 1, yc - 2 * sy) + 1);
+            D.wsrc = goff(xc - sx, yc - sy);
+            D.wslot = slot(sW, 0, yc - sy);
+            D.wnode = goff(sx < 0 ? 0 : nx - 1, sy < 0 ? 0 : ny - 1);
+            D.wdx = sx < 0 ? 1 : -1;
+            D.wdy = (sy < 0 ? 1 : -1) * nxp;
+            pl.ud.push_back(D);
         }
+    // zero-gradient and inflow nodes
+    for (int s = 0; s < 4; ++s) {
+        if (p->side[s] != LBM_SIDE_ZG && p->side[s] != LBM_SIDE_INFLOW) continue;
+        for (int pp = lo[s]; pp <= hi[s]; ++pp)
+            for (int j = 1; j <= M; ++j) {
+                int x, y;
+                side_xf(s, pp, nx, ny, M, x, y);
+                const int node = goff(x + j * kSN[s][0], y + j * kSN[s][1]);
+                if (p->side[s] == LBM_SIDE_ZG) pl.zg.push_back(make_int2(node, goff(x, y)));
+                else pl.inflow.push_back(node);
+            }
+    }
+    if (corner_kind == SIDE_ZG || corner_kind == SIDE_INFLOW)
+        for (int c = 0; c < 4; ++c) {
+            const int sx = (c & 1) ? 1 : -1, sy = (c & 2) ? 1 : -1;
+            const int xc = sx < 0 ? M - 1 : nx - M, yc = sy < 0 ? M - 1 : ny - M;
+            for (int a = 0; a < M; ++a)
+                for (int b = 0; b < M; ++b) {
+                    const int x = sx < 0 ? a : nx - 1 - a, y = sy < 0 ? b : ny - 1 - b;
+                    if (corner_kind == SIDE_ZG) pl.zg.push_back(make_int2(goff(x, y), goff(xc - sx, yc - sy)));
+                    else pl.inflow.push_back(goff(x, y));
+                }
+        }
+    B.n_unk = int(pl.ud.size());
+    B.n_zg = int(pl.zg.size());
+    B.viscous = p->viscous;
+    B.dirichlet = p->dirichlet;
+    for (int s = 0; s < 4; ++s) {
+        B.scheme[s] = p->scheme[s];
         const double pinf = p->p_inf[s] != 0.0 ? p->p_inf[s] : cs2 * p->rho0;
         B.pdev[s] = pinf - cs2 * p->rho0;
     }
-    B.corner_kind = -1;
-    if (!perx && !pery) {
-        if (p->side[0] == LBM_SIDE_CBC) B.corner_kind = SIDE_CBC;
-        else if (p->side[0] == LBM_SIDE_INFLOW || p->side[1] == LBM_SIDE_INFLOW ||
-                 p->side[2] == LBM_SIDE_INFLOW || p->side[3] == LBM_SIDE_INFLOW)
-            B.corner_kind = SIDE_INFLOW;
-        else B.corner_kind = SIDE_ZG;
-    }
-    B.n_unk = B.n_side_unk + (B.corner_kind == SIDE_CBC ? 4 : 0);
-    B.n_extra = B.n_extra_side + ((B.corner_kind == SIDE_ZG || B.corner_kind == SIDE_INFLOW) ? 4 * M * M : 0);
-    B.viscous = p->viscous;
-    B.dirichlet = p->dirichlet;
     B.alpha_T = p->alpha_T;
     B.beta_P = p->beta_P;
     B.t_inf = p->t_inf;
-    B.Uin[0] = p->inflow[0] - p->rho0;
-    B.Uin[1] = p->inflow[1];
-    B.Uin[2] = p->inflow[2];
-    B.Uin[3] = lattice == LBM_D2Q37 ? p->inflow[3] - 1.0 : 0.0;
+    B.kA = 1.0 / std::sqrt(8.0 * cs2);
+    B.kB = std::sqrt(2.0 * cs2);
+    B.kC = 1.0 / (2.0 * std::sqrt(2.0));
+    B.kR = 1.0 / std::sqrt(2.0);
+    B.cs = std::sqrt(cs2);
+    B.ihcs = 0.5 / B.cs;
+    pl.Uin[0] = p->inflow[0] - p->rho0;
+    pl.Uin[1] = p->inflow[1];
+    pl.Uin[2] = p->inflow[2];
+    pl.Uin[3] = lattice == LBM_D2Q37 ? p->inflow[3] - 1.0 : 0.0;
 
     pl.Q = Q;
     pl.esize = p->storage == LBM_F64 ? 8 : (p->storage == LBM_F32 ? 4 : 2);
     pl.f_bytes = (size_t)Q * (size_t)G.plane * pl.esize;
-    pl.stripU_n = totU;
-    pl.stripN_n = totN;
+    pl.stripU_n = 2ull * E.nslots * 4;
+    pl.stripN_n = 2ull * E.nslots * 5;
     const size_t nu = (size_t)B.n_unk;
     size_t o = 0;
     auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes); return at; };
     pl.off_f0 = take(pl.f_bytes);
     pl.off_f1 = take(pl.f_bytes);
-    pl.off_sU = take(totU * 8);
-    pl.off_sN = take(totN * 8);
+    pl.off_sU = take(pl.stripU_n * 8);
+    pl.off_sN = take(pl.stripN_n * 8);
     pl.off_Ub = take(nu * 32);
     pl.off_Ya = take(nu * 32);
     pl.off_Yb = take(nu * 32);
     pl.off_acc = take(nu * 32);
     pl.off_V = take(nu * 32);
     pl.off_mask = take(nu * 4);
+    pl.off_ud = take(nu * sizeof(UDesc));
+    pl.off_zg = take(pl.zg.size() * sizeof(int2));
+    pl.off_in = take(pl.inflow.size() * sizeof(int));
     pl.off_macro = take((size_t)4 * nx * ny * 8);
     pl.off_flag = take(sizeof(int));
     pl.total = o;
@@ -213,31 +342,46 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     h->P = *p;
     h->storage = p->storage;
     h->G = pl.G;
+    h->O = pl.O;
+    h->E = pl.E;
     h->B = pl.B;
     h->esize = pl.esize;
     h->f_bytes = pl.f_bytes;
-    h->stripU_n = pl.stripU_n;
-    h->stripN_n = pl.stripN_n;
     h->ws = ws;
     h->ws_bytes = ws_bytes;
     h->owns_ws = owns;
     h->f[0] = at<char>(ws, pl.off_f0);
     h->f[1] = at<char>(ws, pl.off_f1);
-    h->B.stripU = at<double>(ws, pl.off_sU);
-    h->B.stripN = at<double>(ws, pl.off_sN);
+    h->E.stripU = at<double>(ws, pl.off_sU);
+    h->E.stripN = at<double>(ws, pl.off_sN);
     h->B.Ub = at<double>(ws, pl.off_Ub);
     h->B.Ya = at<double>(ws, pl.off_Ya);
     h->B.Yb = at<double>(ws, pl.off_Yb);
     h->B.acc = at<double>(ws, pl.off_acc);
     h->B.V = at<double>(ws, pl.off_V);
     h->B.mask = at<int>(ws, pl.off_mask);
+    h->B.ud = at<UDesc>(ws, pl.off_ud);
+    h->B.zg = at<int2>(ws, pl.off_zg);
+    h->inflow_nodes = at<int>(ws, pl.off_in);
+    h->n_inflow = int(pl.inflow.size());
+    for (int c = 0; c < 4; ++c) h->Uin[c] = pl.Uin[c];
     h->macro = at<double>(ws, pl.off_macro);
     h->flag = at<int>(ws, pl.off_flag);
-    // Zero the strips so that padding positions hold finite values.
-    cudaError_t e = cudaMemsetAsync(h->B.stripU, 0, pl.stripU_n * 8, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->B.stripN, 0, pl.stripN_n * 8, h->stream);
+    // Zero the strips (positions no kernel writes stay finite) and upload the
+    // boundary tables.
+    cudaError_t e = cudaMemsetAsync(h->E.stripU, 0, pl.stripU_n * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->E.stripN, 0, pl.stripN_n * 8, h->stream);
+    if (e == cudaSuccess && !pl.ud.empty())
+        e = cudaMemcpyAsync(const_cast<UDesc*>(h->B.ud), pl.ud.data(), pl.ud.size() * sizeof(UDesc),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !pl.zg.empty())
+        e = cudaMemcpyAsync(const_cast<int2*>(h->B.zg), pl.zg.data(), pl.zg.size() * sizeof(int2),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !pl.inflow.empty())
+        e = cudaMemcpyAsync(h->inflow_nodes, pl.inflow.data(), pl.inflow.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "workspace clear");
+    if (e != cudaSuccess) return cuda_fail(h, e, "workspace set-up");
     return LBM_OK;
 }
 
@@ -360,8 +504,9 @@ int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux, const do
     } else if (!dt) {
         dt = dr;   // unused by the isothermal lattice
     }
-    int rc = launch_init(h->lattice, h->storage, h->G, h->B, dr, du, dv, dt, h->f[0], h->stream);
+    int rc = launch_init(h->lattice, h->storage, h->G, h->E, h->B, dr, du, dv, dt, h->f[0], h->stream);
     if (rc) return check_launch(h, rc, "init kernels");
+    h->inflow_done[0] = h->inflow_done[1] = false;
     const cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "init");
     h->steps = 0;
@@ -380,7 +525,7 @@ int lbm_step_phase(lbm_handle* h, int phase)
     const int par = int(h->steps & 1);
     if (phase == 0) {
         if (h->bulk_pending) { h->err = "bulk phase issued twice"; return LBM_ERR_STATE; }
-        const int rc = launch_bulk(h->lattice, h->storage, h->G, h->B, h->f[par], h->f[par ^ 1],
+        const int rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->E, h->f[par], h->f[par ^ 1],
                                    par ^ 1, h->stream);
         if (rc) return check_launch(h, rc, "bulk kernel");
         h->bulk_pending = true;
@@ -388,7 +533,17 @@ int lbm_step_phase(lbm_handle* h, int phase)
     }
     if (phase == 1) {
         if (!h->bulk_pending) { h->err = "boundary phase before bulk phase"; return LBM_ERR_STATE; }
-        const int rc = launch_boundary(h->lattice, h->storage, h->G, h->B, h->f[par ^ 1], par, h->stream);
+        // Inflow nodes carry a fixed equilibrium, imposed after streaming
+        // like every boundary condition; each buffer gets it once, the first
+        // time a step writes that buffer.
+        if (h->n_inflow > 0 && !h->inflow_done[par ^ 1]) {
+            const int rc = launch_inflow(h->lattice, h->storage, h->G, h->inflow_nodes, h->n_inflow,
+                                         h->Uin, h->f[par ^ 1], h->stream);
+            if (rc) return check_launch(h, rc, "inflow kernel");
+            h->inflow_done[par ^ 1] = true;
+        }
+        const int rc = launch_boundary(h->lattice, h->storage, h->G, h->E, h->B, h->f[par ^ 1], par,
+                                       h->stream);
         if (rc) return check_launch(h, rc, "boundary kernels");
         h->bulk_pending = false;
         h->steps++;
@@ -457,7 +612,7 @@ struct StateHeader {
 int lbm_state_bytes(const lbm_handle* h, size_t* bytes)
 {
     if (!h || !bytes) return LBM_ERR_ARG;
-    *bytes = sizeof(StateHeader) + h->f_bytes + (h->stripU_n + h->stripN_n + 4ull * h->B.n_unk) * 8;
+    *bytes = sizeof(StateHeader) + h->f_bytes + (18ull * h->E.nslots + 4ull * h->B.n_unk) * 8;
     return LBM_OK;
 }
 
@@ -470,16 +625,16 @@ int lbm_get_state(lbm_handle* h, void* buf, size_t bytes)
     StateHeader hd{};
     std::memcpy(hd.magic, "LBMCBC01", 8);
     hd.lattice = h->lattice; hd.nx = h->nx; hd.ny = h->ny; hd.storage = h->storage; hd.n_unk = h->B.n_unk;
-    hd.steps = h->steps; hd.f_bytes = h->f_bytes; hd.stripU_n = h->stripU_n; hd.stripN_n = h->stripN_n;
+    hd.steps = h->steps; hd.f_bytes = h->f_bytes; hd.stripU_n = 8ull * h->E.nslots; hd.stripN_n = 10ull * h->E.nslots;
     char* p = static_cast<char*>(buf);
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
     cudaError_t e = cudaMemcpyAsync(p, h->f[h->steps & 1], h->f_bytes, cudaMemcpyDeviceToHost, h->stream);
     p += h->f_bytes;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->B.stripU, h->stripU_n * 8, cudaMemcpyDeviceToHost, h->stream);
-    p += h->stripU_n * 8;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->B.stripN, h->stripN_n * 8, cudaMemcpyDeviceToHost, h->stream);
-    p += h->stripN_n * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->E.stripU, 8ull * h->E.nslots * 8, cudaMemcpyDeviceToHost, h->stream);
+    p += 8ull * h->E.nslots * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->E.stripN, 10ull * h->E.nslots * 8, cudaMemcpyDeviceToHost, h->stream);
+    p += 10ull * h->E.nslots * 8;
     if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->B.Ub, 32ull * h->B.n_unk, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "state copy");
@@ -495,23 +650,24 @@ int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes)
     std::memcpy(&hd, buf, sizeof hd);
     if (std::memcmp(hd.magic, "LBMCBC01", 8) != 0 || hd.lattice != h->lattice || hd.nx != h->nx ||
         hd.ny != h->ny || hd.storage != h->storage || hd.n_unk != h->B.n_unk || hd.f_bytes != h->f_bytes ||
-        hd.stripU_n != h->stripU_n || hd.stripN_n != h->stripN_n) {
+        hd.stripU_n != 8ull * h->E.nslots || hd.stripN_n != 10ull * h->E.nslots) {
         h->err = "state was saved from a different configuration";
         return LBM_ERR_ARG;
     }
     const char* p = static_cast<const char*>(buf) + sizeof hd;
     cudaError_t e = cudaMemcpyAsync(h->f[hd.steps & 1], p, h->f_bytes, cudaMemcpyHostToDevice, h->stream);
     p += h->f_bytes;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.stripU, p, h->stripU_n * 8, cudaMemcpyHostToDevice, h->stream);
-    p += h->stripU_n * 8;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.stripN, p, h->stripN_n * 8, cudaMemcpyHostToDevice, h->stream);
-    p += h->stripN_n * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->E.stripU, p, 8ull * h->E.nslots * 8, cudaMemcpyHostToDevice, h->stream);
+    p += 8ull * h->E.nslots * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->E.stripN, p, 10ull * h->E.nslots * 8, cudaMemcpyHostToDevice, h->stream);
+    p += 10ull * h->E.nslots * 8;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.Ub, p, 32ull * h->B.n_unk, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "state restore");
     h->steps = hd.steps;
     h->initialized = true;
     h->bulk_pending = false;
+    h->inflow_done[0] = h->inflow_done[1] = false;
     return LBM_OK;
 }
 

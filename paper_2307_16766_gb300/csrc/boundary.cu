@@ -1,17 +1,18 @@
 // boundary.cu -- boundary conditions of one time step.
 //
-//  k_cbc_stage  one RK4 stage (Sec. 3.3, "Time integration") of the boundary
-//               ODE on every characteristic unknown: each of the M layers of
-//               every CBC side position and the innermost node of each corner
-//               block.  Stage 0 also freezes the viscous vector and the
-//               incoming-wave mask of time t; stage 3 finishes the step and
-//               writes the mesoscopic Dirichlet populations (equilibrium or
-//               Eq. NEEP), post-collision, into the new population buffer.
-//  k_extras     zero gradient (Eq. zg-bc) and inflow-equilibrium nodes.
+//  k_stage   one classical RK4 stage (Sec. 3.3, "Time integration") of the
+//            boundary ODE on every characteristic unknown: layer j = 1..M
+//            of every CBC side position (Sec. 3.3, "Multi-speed LBM") and the
+//            innermost node of every corner block.  Stage 0 freezes the
+//            viscous vector and the incoming-wave mask of time t; stage 3
+//            ends the step, writes the mesoscopic Dirichlet populations
+//            (equilibrium or Eq. NEEP) post-collision into the new buffer,
+//            and copies the zero-gradient nodes (Eq. zg-bc).
 //
-// All boundary arithmetic is FP64: the characteristic decomposition works on
-// small gradients of O(1) states.  Bulk macros at stage times come from the
-// strips the bulk kernel exported (time t and t+1), interpolated linearly.
+// All characteristic arithmetic is FP64.  Every neighbour a right-hand side
+// needs is resolved on the host into a UDesc: another unknown (stage value)
+// or a strip slot holding a bulk node's macros at t and t + 1 (interpolated
+// linearly at the stage time, Sec. 3.3).
 #include "lbm_internal.cuh"
 
 namespace lbmgb {
@@ -20,181 +21,171 @@ namespace {
 
 constexpr int kBandThreads = 32;   // few unknowns: spread them over many SMs
 
-struct Frame {
-    double n0, n1, t0, t1;
-};
-
-__device__ inline Frame frame_of_side(int s)
-{
-    return Frame{double(side_nx(s)), double(side_ny(s)), double(side_tx(s)), double(side_ty(s))};
-}
-
-// Corner blocks: outward diagonal n = (sx, sy)/sqrt(2), t = n rotated by +90.
-__device__ inline Frame frame_of_corner(int c)
-{
-    const double r = 1.0 / sqrt(2.0);
-    const double n0 = corner_sx(c) * r, n1 = corner_sy(c) * r;
-    return Frame{n0, n1, -n1, n0};
-}
-
-__device__ inline void to_local(const double* U, const Frame& F, double* Lc)
+// Lab <-> local frame.  Sides: n the outward normal, t = +y (W, E) or +x
+// (S, N).  Corners: n = (sx, sy)/sqrt(2), t = n rotated by +90 degrees.
+__device__ __forceinline__ void to_local(int kind, double r, const double* U, double* Lc)
 {
     Lc[0] = U[0];
-    Lc[1] = U[1] * F.n0 + U[2] * F.n1;
-    Lc[2] = U[1] * F.t0 + U[2] * F.t1;
     Lc[3] = U[3];
+    switch (kind) {
+    case 0: Lc[1] = -U[1]; Lc[2] = U[2]; break;
+    case 1: Lc[1] = U[1]; Lc[2] = U[2]; break;
+    case 2: Lc[1] = -U[2]; Lc[2] = U[1]; break;
+    case 3: Lc[1] = U[2]; Lc[2] = U[1]; break;
+    default: {
+        const int c = kind - 4;
+        const double n0 = (c & 1) ? r : -r, n1 = (c & 2) ? r : -r;
+        Lc[1] = U[1] * n0 + U[2] * n1;
+        Lc[2] = -U[1] * n1 + U[2] * n0;
+    }
+    }
 }
 
-__device__ inline void to_lab(const double* Lc, const Frame& F, double* U)
+__device__ __forceinline__ void to_lab(int kind, double r, const double* Lc, double* U)
 {
     U[0] = Lc[0];
-    U[1] = Lc[1] * F.n0 + Lc[2] * F.t0;
-    U[2] = Lc[1] * F.n1 + Lc[2] * F.t1;
     U[3] = Lc[3];
+    switch (kind) {
+    case 0: U[1] = -Lc[1]; U[2] = Lc[2]; break;
+    case 1: U[1] = Lc[1]; U[2] = Lc[2]; break;
+    case 2: U[2] = -Lc[1]; U[1] = Lc[2]; break;
+    case 3: U[2] = Lc[1]; U[1] = Lc[2]; break;
+    default: {
+        const int c = kind - 4;
+        const double n0 = (c & 1) ? r : -r, n1 = (c & 2) ? r : -r;
+        U[1] = Lc[1] * n0 - Lc[2] * n1;
+        U[2] = Lc[1] * n1 + Lc[2] * n0;
+    }
+    }
 }
 
-// Corner block met at the low / high tangential end of a side.
-__device__ inline int lo_corner(int s) { return s == 3 ? 2 : (s == 1 ? 1 : 0); }
-__device__ inline int hi_corner(int s) { return s == 2 ? 1 : (s == 0 ? 2 : 3); }
+struct Ctx {
+    const double* Y;     // stage values of the unknowns
+    const double* St;    // strip macros at t
+    const double* St1;   // strip macros at t + 1
+    double frac;         // stage time fraction in [0, 1]
+};
 
-// Stage value of layer j (j >= 1: boundary unknown; j <= 0: bulk node at
-// depth -j, interpolated between t and t+1) at tangential position p.
-__device__ inline void fetch(const Geom& G, const Band& B, const double* Y, int par_t, double frac,
-                             int s, int j, int p, double U[4])
+__device__ __forceinline__ void fetch(const Ctx& X, int ref, double* U)
 {
-    const Side& S = B.s[s];
-    if (S.tper) {
-        p %= S.L;
-        if (p < 0) p += S.L;
-    }
-    if (j >= 1) {
-        const double* src;
-        if (p < S.lo) src = Y + 4LL * (B.n_side_unk + lo_corner(s));
-        else if (p > S.hi) src = Y + 4LL * (B.n_side_unk + hi_corner(s));
-        else src = Y + 4LL * (S.base + (p - S.lo) * G.M + (j - 1));
-#pragma unroll
-        for (int c = 0; c < 4; ++c) U[c] = src[c];
+    if (ref >= 0) {
+        const double2* p = reinterpret_cast<const double2*>(X.Y + 4LL * ref);
+        const double2 a = p[0], b = p[1];
+        U[0] = a.x; U[1] = a.y; U[2] = b.x; U[3] = b.y;
     } else {
-        const double* a = B.stripU + strip_u_index(S, par_t, -j, p);
-        const double* b = B.stripU + strip_u_index(S, par_t ^ 1, -j, p);
+        const long long s = 4LL * (-ref - 1);
+        const double w0 = 1.0 - X.frac, w1 = X.frac;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) U[c] = (1.0 - frac) * a[c] + frac * b[c];
+        for (int c = 0; c < 4; ++c) U[c] = w0 * X.St[s + c] + w1 * X.St1[s + c];
     }
 }
 
-__device__ inline void fetch_local(const Geom& G, const Band& B, const double* Y, int par_t,
-                                   double frac, int s, int j, int p, const Frame& F, double Lc[4])
+__device__ __forceinline__ void fetch_local(const Ctx& X, int ref, int kind, double r, double* Lc)
 {
     double U[4];
-    fetch(G, B, Y, par_t, frac, s, j, p, U);
-    to_local(U, F, Lc);
+    fetch(X, ref, U);
+    to_local(kind, r, U, Lc);
 }
 
 // ---------------------------------------------------------------------------
-// Characteristic right-hand side in the local frame (Sec. 3.1, 3.2)
+// Characteristic system in the local frame (Sec. 3.1)
 // ---------------------------------------------------------------------------
-
-// Thermal system, U = (drho, u_n, u_t, dT), T~ = c_s^2 (1 + dT):
-//   S = [[-T~/(2 rho c_s^2), 0, 0, 1/2], [0, 0, 1, 0],
-//        [T~/(4 rho c_s^2), -sqrt(T~/(8 c_s^4)), 0, 1/4],
-//        [T~/(4 rho c_s^2),  sqrt(T~/(8 c_s^4)), 0, 1/4]],
-//   Lambda = (u_n, u_n, u_n - sqrt(2 T~), u_n + sqrt(2 T~)).
-// The isothermal D2Q9 system for (drho, u_n, u_t) has
-//   S = [[1/2, -rho/(2 c_s), 0], [0, 0, 1], [1/2, rho/(2 c_s), 0]],
+// Thermal, U = (drho, u_n, u_t, dT), theta = 1 + dT, T~ = c_s^2 theta:
+//   S rows: (-r/2, 0, 0, 1/2), (0, 0, 1, 0), (r/4, -a, 0, 1/4), (r/4, a, 0, 1/4)
+//   S^-1 rows: (-1/r, 0, 1/r, 1/r), (0, 0, -b, b), (0, 1, 0, 0), (1, 0, 1, 1)
+//   with r = T~/(rho c_s^2) = theta/rho, a = sqrt(T~/(8 c_s^4)),
+//   b = sqrt(2 c_s^4 / T~) and Lambda = (u_n, u_n, u_n - c, u_n + c),
+//   c = sqrt(2 T~).
+// Isothermal D2Q9, U = (drho, u_n, u_t):
+//   S rows: (1/2, -h, 0), (0, 0, 1), (1/2, h, 0) with h = rho/(2 c_s),
+//   S^-1 rows: (1, 0, 1), (-c_s/rho, 0, c_s/rho), (0, 1, 0),
 //   Lambda = (u_n - c_s, u_n, u_n + c_s).
 struct CharSys {
-    bool th;
-    double r, a, b, cs, rho;
+    double rho, irho, r, ir, a, b, h, csr;
     double lam[4];
 };
 
-__device__ inline CharSys char_sys(bool th, double cs2, double rho0, const double U[4])
+template <bool TH>
+__device__ __forceinline__ CharSys char_sys(const Band& B, double rho0, const double* U)
 {
     CharSys C;
-    C.th = th;
     C.rho = rho0 + U[0];
-    if (th) {
-        const double theta = 1.0 + U[3];
-        C.r = theta / C.rho;                      // T~ / (rho c_s^2)
-        C.a = sqrt(theta / (8.0 * cs2));          // sqrt(T~ / (8 c_s^4))
-        C.b = sqrt(2.0 * cs2 / theta);            // sqrt(2 c_s^4 / T~)
-        const double c = sqrt(2.0 * cs2 * theta); // sqrt(2 T~)
+    C.irho = 1.0 / C.rho;
+    if (TH) {
+        const double th = 1.0 + U[3];
+        const double sth = sqrt(th);
+        const double isth = 1.0 / sth;
+        C.r = th * C.irho;
+        C.ir = C.rho * isth * isth;
+        C.a = sth * B.kA;
+        C.b = isth * B.kB;
+        const double c = sth * B.kB;
         C.lam[0] = U[1];
         C.lam[1] = U[1];
         C.lam[2] = U[1] - c;
         C.lam[3] = U[1] + c;
-        C.cs = 0.0;
+        C.h = C.csr = 0.0;
     } else {
-        C.cs = sqrt(cs2);
-        C.r = C.a = C.b = 0.0;
-        C.lam[0] = U[1] - C.cs;
+        C.h = C.rho * B.ihcs;
+        C.csr = B.cs * C.irho;
+        C.lam[0] = U[1] - B.cs;
         C.lam[1] = U[1];
-        C.lam[2] = U[1] + C.cs;
+        C.lam[2] = U[1] + B.cs;
         C.lam[3] = 0.0;
+        C.r = C.ir = C.a = C.b = 0.0;
     }
     return C;
 }
 
-__device__ inline void apply_S(const CharSys& C, const double v[4], double o[4])
+template <bool TH>
+__device__ __forceinline__ void apply_S(const CharSys& C, const double* v, double* o)
 {
-    if (C.th) {
-        o[0] = -0.5 * C.r * v[0] + 0.5 * v[3];
+    if (TH) {
+        const double rv = 0.25 * C.r * v[0], q = 0.25 * v[3], av = C.a * v[1];
+        o[0] = -2.0 * rv + 2.0 * q;
         o[1] = v[2];
-        o[2] = 0.25 * C.r * v[0] - C.a * v[1] + 0.25 * v[3];
-        o[3] = 0.25 * C.r * v[0] + C.a * v[1] + 0.25 * v[3];
+        o[2] = rv - av + q;
+        o[3] = rv + av + q;
     } else {
-        const double h = C.rho / (2.0 * C.cs);
-        o[0] = 0.5 * v[0] - h * v[1];
+        const double hv = C.h * v[1];
+        o[0] = 0.5 * v[0] - hv;
         o[1] = v[2];
-        o[2] = 0.5 * v[0] + h * v[1];
+        o[2] = 0.5 * v[0] + hv;
         o[3] = 0.0;
     }
 }
 
-__device__ inline void apply_Sinv(const CharSys& C, const double w[4], double o[4])
+template <bool TH>
+__device__ __forceinline__ int incoming_mask(const CharSys& C)
 {
-    if (C.th) {
-        o[0] = (w[2] + w[3] - w[0]) / C.r;
-        o[1] = C.b * (w[3] - w[2]);
-        o[2] = w[1];
-        o[3] = w[0] + w[2] + w[3];
-    } else {
-        o[0] = w[0] + w[2];
-        o[1] = C.cs / C.rho * (w[2] - w[0]);
-        o[2] = w[1];
-        o[3] = 0.0;
-    }
-}
-
-__device__ inline int incoming_mask(const CharSys& C)
-{
-    const int n = C.th ? 4 : 3;
     int m = 0;
-    for (int i = 0; i < n; ++i)
+#pragma unroll
+    for (int i = 0; i < (TH ? 4 : 3); ++i)
         if (C.lam[i] < 0.0) m |= 1 << i;
     return m;
 }
 
-// dU/dt = -S^-1 Lbar (+ T + V for the CBC schemes) with Lbar_i = L_i =
-// Lambda_i (S dU/dn)_i for outgoing waves (Eq. thermal_WAV) and, for
-// incoming waves, Eq. PNR (LODI), Eq. LODI-Relax, Eq. CBC-PNR (CBC) or
-// Eq. CBC-Relax.  beta (Z - Z_inf) acts on incoming acoustic waves.
-__device__ inline void char_rhs(const CharSys& C, const Band& B, const double dUn[4],
-                                const double TT[4], const double VV[4], int mask, double dP,
-                                int scheme, double k[4])
+// dU/dt = -S^-1 Lbar (+ T + V for the CBC schemes): Lbar_i = L_i =
+// Lambda_i (S dU/dn)_i for outgoing waves (Eq. thermal_WAV); for incoming
+// waves Eq. PNR (LODI), Eq. LODI-Relax, Eq. CBC-PNR (CBC) or Eq. CBC-Relax,
+// with beta (Z - Z_inf) on the incoming acoustic waves.
+template <bool TH>
+__device__ __forceinline__ void char_rhs(const CharSys& C, const Band& B, const double* dUn,
+                                         const double* TT, const double* VV, int mask, double dP,
+                                         int scheme, double* k)
 {
     double sd[4], st[4], sv[4], w[4];
-    apply_S(C, dUn, sd);
-    apply_S(C, TT, st);
-    apply_S(C, VV, sv);
-    const int n = C.th ? 4 : 3;
-    for (int i = 0; i < 4; ++i) w[i] = 0.0;
-    for (int i = 0; i < n; ++i) {
+    apply_S<TH>(C, dUn, sd);
+    apply_S<TH>(C, TT, st);
+    apply_S<TH>(C, VV, sv);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (!TH && i == 3) { w[i] = 0.0; continue; }
         if (!((mask >> i) & 1)) {
             w[i] = C.lam[i] * sd[i];
             continue;
         }
-        const bool acoustic = C.th ? (i >= 2) : (i != 1);
+        const bool acoustic = TH ? (i >= 2) : (i != 1);
         const double relaxP = acoustic ? B.beta_P * dP : 0.0;
         if (scheme == SCH_LODI) w[i] = 0.0;
         else if (scheme == SCH_LODI_RELAX) w[i] = B.alpha_T * (B.t_inf - st[i]) + relaxP;
@@ -202,319 +193,289 @@ __device__ inline void char_rhs(const CharSys& C, const Band& B, const double dU
         else w[i] = st[i] + sv[i] + B.alpha_T * (B.t_inf - st[i]) + relaxP;
     }
     double o[4];
-    apply_Sinv(C, w, o);
+    if (TH) {
+        o[0] = (w[2] + w[3] - w[0]) * C.ir;
+        o[1] = C.b * (w[3] - w[2]);
+        o[2] = w[1];
+        o[3] = w[0] + w[2] + w[3];
+    } else {
+        o[0] = w[0] + w[2];
+        o[1] = C.csr * (w[2] - w[0]);
+        o[2] = w[1];
+        o[3] = 0.0;
+    }
     const bool cbc = scheme == SCH_CBC || scheme == SCH_CBC_RELAX;
+#pragma unroll
     for (int m = 0; m < 4; ++m) k[m] = -o[m] + (cbc ? TT[m] + VV[m] : 0.0);
 }
 
 // ---------------------------------------------------------------------------
-// Viscous vectors (frozen at time t)
+// Viscous vectors, frozen at time t
 // ---------------------------------------------------------------------------
 
-// Mesoscopic form at x_f of side s, position p, from the non-equilibrium
-// moments the bulk kernel exported: normal derivatives one-sided into the
-// bulk (Eq. FD-dx-bw), tangential ones central (Eq. FD-dx-center), and
-// one-sided inward where the tangential neighbour is a boundary node.
+// Mesoscopic form at x_f (Eqs. LaplaceU, LaplaceT): normal derivatives
+// one-sided into the bulk (Eq. FD-dx-bw), tangential ones central
+// (Eq. FD-dx-center) or one-sided inward next to a boundary node:
 //   V = (0, (1/rho) d_j s'_jn, (1/rho) d_j s'_jt,
-//        (-div q + heating) / (rho c_s^2)),
-//   heating = rho nu ((d_n u_n - d_t u_t)^2 + (d_n u_t + d_t u_n)^2).
-template <int LAT>
-__device__ void vis_meso(const Geom& G, const Band& B, int par_t, int s, int p, double V[4])
+//        -div q / (rho c_s^2) + (nu / c_s^2) ((d_n u_n - d_t u_t)^2 + (d_n u_t + d_t u_n)^2)).
+template <bool TH>
+__device__ void vis_meso(const Geom& G, const Band& B, const Export& E, int par_t,
+                         const UDesc& D, double cs2, double* V)
 {
-    constexpr double cs2 = Lat<LAT>::CS2;
-    const Side& S = B.s[s];
-    const Frame F = frame_of_side(s);
-    auto H = [&](int d, int pp, double h[7]) {
-        if (S.tper) {
-            pp %= S.L;
-            if (pp < 0) pp += S.L;
-        }
-        const double* n = B.stripN + strip_n_index(S, par_t, d, pp);
-        const double* u = B.stripU + strip_u_index(S, par_t, d, pp);
-        const double sn0 = n[0] * F.n0 + n[1] * F.n1, sn1 = n[1] * F.n0 + n[2] * F.n1;
-        const double st0 = n[0] * F.t0 + n[1] * F.t1, st1 = n[1] * F.t0 + n[2] * F.t1;
-        h[0] = F.n0 * sn0 + F.n1 * sn1;
-        h[1] = F.t0 * sn0 + F.t1 * sn1;
-        h[2] = F.t0 * st0 + F.t1 * st1;
-        h[3] = n[3] * F.n0 + n[4] * F.n1;
-        h[4] = n[3] * F.t0 + n[4] * F.t1;
-        h[5] = u[1] * F.n0 + u[2] * F.n1;
-        h[6] = u[1] * F.t0 + u[2] * F.t1;
-    };
-    int tmode = 0;
-    if (!S.tper) {
-        if (p == S.hi) tmode = 1;
-        else if (p == S.lo) tmode = -1;
-    }
-    double h0[7], h1[7], h2[7], ha[7], hb[7];
-    H(0, p, h0);
-    H(1, p, h1);
-    H(2, p, h2);
-    if (tmode == 0) {
-        H(0, p + 1, ha);
-        H(0, p - 1, hb);
-    } else if (tmode == 1) {
-        H(0, p - 1, ha);
-        H(0, p - 2, hb);
-    } else {
-        H(0, p + 1, ha);
-        H(0, p + 2, hb);
+    const double* SU = E.stripU + (long long)par_t * E.nslots * 4;
+    const double* SN = E.stripN + (long long)par_t * E.nslots * 5;
+    const int s = D.kind;
+    const int an = s < 2 ? 0 : 1, at = 1 - an;     // axes of n and t
+    const double sn = (s == 0 || s == 2) ? -1.0 : 1.0;
+    double h[5][7];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double* n = SN + 5LL * D.vs[k];
+        const double* u = SU + 4LL * D.vs[k];
+        const double sxx = n[0], sxy = n[1], syy = n[2];
+        h[k][0] = an == 0 ? sxx : syy;              // sigma'_nn
+        h[k][1] = sn * sxy;                         // sigma'_nt
+        h[k][2] = an == 0 ? syy : sxx;              // sigma'_tt
+        h[k][3] = sn * n[3 + an];                   // q_n
+        h[k][4] = n[3 + at];                        // q_t
+        h[k][5] = sn * u[1 + an];                   // u_n
+        h[k][6] = u[1 + at];                        // u_t
     }
     double dn[7], dt[7];
+#pragma unroll
     for (int m = 0; m < 7; ++m) {
-        dn[m] = 0.5 * (3.0 * h0[m] - 4.0 * h1[m] + h2[m]);
-        if (tmode == 0) dt[m] = 0.5 * (ha[m] - hb[m]);
-        else if (tmode == 1) dt[m] = 0.5 * (3.0 * h0[m] - 4.0 * ha[m] + hb[m]);
-        else dt[m] = -0.5 * (3.0 * h0[m] - 4.0 * ha[m] + hb[m]);
+        dn[m] = 0.5 * (3.0 * h[0][m] - 4.0 * h[1][m] + h[2][m]);
+        if (D.tmode == 0) dt[m] = 0.5 * (h[3][m] - h[4][m]);
+        else dt[m] = double(D.tmode) * 0.5 * (3.0 * h[0][m] - 4.0 * h[3][m] + h[4][m]);
     }
-    const double rho = G.rho0 + B.stripU[strip_u_index(S, par_t, 0, p)];
+    const double irho = 1.0 / (G.rho0 + SU[4LL * D.vs[0]]);
     V[0] = 0.0;
-    V[1] = (dn[0] + dt[1]) / rho;
-    V[2] = (dn[1] + dt[2]) / rho;
+    V[1] = (dn[0] + dt[1]) * irho;
+    V[2] = (dn[1] + dt[2]) * irho;
     V[3] = 0.0;
-    if (Lat<LAT>::THERMAL) {
+    if (TH) {
         const double nu = (G.tau - 0.5) * cs2;
         const double e1 = dn[5] - dt[6], e2 = dn[6] + dt[5];
-        V[3] = -(dn[3] + dt[4]) / (rho * cs2) + nu / cs2 * (e1 * e1 + e2 * e2);
+        V[3] = -(dn[3] + dt[4]) * irho * (1.0 / cs2) + nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
     }
 }
 
-// "-FD" form (Sec. 4.2) at layer j: second derivatives of the macros of time
-// t, 4-point one-sided at j = M, 3-point central elsewhere and along the side.
-template <int LAT>
-__device__ void vis_fd(const Geom& G, const Band& B, int par_t, int s, int j, int p, double V[4])
+// "-FD" form (Sec. 4.2) at layer j from the macros of time t: 4-point
+// one-sided second derivative at j = M, 3-point central elsewhere.
+template <bool TH>
+__device__ void vis_fd(const Geom& G, const Band& B, const Ctx& X0, const UDesc& D, int u,
+                       double cs2, double* V)
 {
-    constexpr double cs2 = Lat<LAT>::CS2;
-    const Frame F = frame_of_side(s);
-    const double* Y = B.Ub;
-    double U[4], A[4], Bv[4], Cv[4], Tp[4], Tm[4];
-    fetch_local(G, B, Y, par_t, 0.0, s, j, p, F, U);
-    fetch_local(G, B, Y, par_t, 0.0, s, j - 1, p, F, Bv);
-    fetch_local(G, B, Y, par_t, 0.0, s, j, p + 1, F, Tp);
-    fetch_local(G, B, Y, par_t, 0.0, s, j, p - 1, F, Tm);
-    double dnn[4], d1n[4];
-    if (j == G.M) {
-        fetch_local(G, B, Y, par_t, 0.0, s, j - 2, p, F, A);
-        fetch_local(G, B, Y, par_t, 0.0, s, j - 3, p, F, Cv);
+    const int kind = D.kind;
+    double U[4], A[4], Bv[4], Cv[4], Tp[4], Tm[4], dnn[4], d1n[4];
+    fetch_local(X0, u, kind, 0.0, U);
+    fetch_local(X0, D.nb[1], kind, 0.0, Bv);
+    fetch_local(X0, D.nb[4], kind, 0.0, Tp);
+    fetch_local(X0, D.nb[5], kind, 0.0, Tm);
+    if (D.j == B.M) {
+        fetch_local(X0, D.nb[2], kind, 0.0, A);
+        fetch_local(X0, D.nb[3], kind, 0.0, Cv);
+#pragma unroll
         for (int m = 0; m < 4; ++m) {
             dnn[m] = 2.0 * U[m] - 5.0 * Bv[m] + 4.0 * A[m] - Cv[m];
             d1n[m] = 0.5 * (3.0 * U[m] - 4.0 * Bv[m] + A[m]);
         }
     } else {
-        fetch_local(G, B, Y, par_t, 0.0, s, j + 1, p, F, A);
+        fetch_local(X0, D.nb[0], kind, 0.0, A);
+#pragma unroll
         for (int m = 0; m < 4; ++m) {
             dnn[m] = A[m] - 2.0 * U[m] + Bv[m];
             d1n[m] = 0.5 * (A[m] - Bv[m]);
         }
     }
-    double dtt[4], d1t[4];
-    for (int m = 0; m < 4; ++m) {
-        dtt[m] = Tp[m] - 2.0 * U[m] + Tm[m];
-        d1t[m] = 0.5 * (Tp[m] - Tm[m]);
-    }
     const double nu = (G.tau - 0.5) * cs2;
     V[0] = 0.0;
-    V[1] = nu * (dnn[1] + dtt[1]);
-    V[2] = nu * (dnn[2] + dtt[2]);
+    V[1] = nu * (dnn[1] + (Tp[1] - 2.0 * U[1] + Tm[1]));
+    V[2] = nu * (dnn[2] + (Tp[2] - 2.0 * U[2] + Tm[2]));
     V[3] = 0.0;
-    if (Lat<LAT>::THERMAL) {
-        const double e1 = d1n[1] - d1t[2], e2 = d1n[2] + d1t[1];
-        V[3] = 2.0 * nu * (dnn[3] + dtt[3]) + nu / cs2 * (e1 * e1 + e2 * e2);
+    if (TH) {
+        const double d1t1 = 0.5 * (Tp[1] - Tm[1]), d1t2 = 0.5 * (Tp[2] - Tm[2]);
+        const double e1 = d1n[1] - d1t2, e2 = d1n[2] + d1t1;
+        V[3] = 2.0 * nu * (dnn[3] + (Tp[3] - 2.0 * U[3] + Tm[3])) + nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Right-hand sides of the boundary ODE
+// Right-hand side of one unknown
 // ---------------------------------------------------------------------------
 
 template <int LAT>
-__device__ void side_rhs(const Geom& G, const Band& B, const double* Y, int par_t, double frac,
-                         int s, int j, int p, const double V[4], int mask, double k[4])
+__device__ void unknown_rhs(const Geom& G, const Band& B, const Ctx& X, const UDesc& D, int u,
+                            const double* V, int mask, double* k)
 {
     using L = Lat<LAT>;
-    const Frame F = frame_of_side(s);
-    double U[4], A[4], Bv[4], dUn[4], Up[4], Um[4];
-    fetch_local(G, B, Y, par_t, frac, s, j, p, F, U);
-    if (j == G.M) {                 // Eq. FD-dx-bw at the outermost layer
-        fetch_local(G, B, Y, par_t, frac, s, j - 1, p, F, A);
-        fetch_local(G, B, Y, par_t, frac, s, j - 2, p, F, Bv);
+    constexpr bool TH = L::THERMAL;
+    const int kind = D.kind;
+    const double r = B.kR;
+    double U[4], A[4], Bv[4], dUn[4];
+    fetch_local(X, u, kind, r, U);
+    if (kind >= 4) {
+        // Corner: LODI (Eq. PNR) along the outward diagonal, one-sided
+        // difference of spacing sqrt(2) through the two diagonal bulk nodes.
+        fetch_local(X, D.nb[0], kind, r, A);
+        fetch_local(X, D.nb[1], kind, r, Bv);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) dUn[m] = (3.0 * U[m] - 4.0 * A[m] + Bv[m]) * B.kC;
+        const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+        const CharSys C = char_sys<TH>(B, G.rho0, U);
+        double kl[4];
+        char_rhs<TH>(C, B, dUn, zero, zero, mask, 0.0, SCH_LODI, kl);
+        to_lab(kind, r, kl, k);
+        return;
+    }
+    if (D.j == B.M) {            // Eq. FD-dx-bw at the outermost layer
+        fetch_local(X, D.nb[1], kind, r, A);
+        fetch_local(X, D.nb[2], kind, r, Bv);
+#pragma unroll
         for (int m = 0; m < 4; ++m) dUn[m] = 0.5 * (3.0 * U[m] - 4.0 * A[m] + Bv[m]);
-    } else {                        // Eq. FD-dx-center at inner layers
-        fetch_local(G, B, Y, par_t, frac, s, j + 1, p, F, A);
-        fetch_local(G, B, Y, par_t, frac, s, j - 1, p, F, Bv);
+    } else {                     // Eq. FD-dx-center at inner layers
+        fetch_local(X, D.nb[0], kind, r, A);
+        fetch_local(X, D.nb[1], kind, r, Bv);
+#pragma unroll
         for (int m = 0; m < 4; ++m) dUn[m] = 0.5 * (A[m] - Bv[m]);
     }
-    // transversal vector T (Sec. 3.1), central differences along the side
-    fetch_local(G, B, Y, par_t, frac, s, j, p + 1, F, Up);
-    fetch_local(G, B, Y, par_t, frac, s, j, p - 1, F, Um);
+    // transversal vector T (Sec. 3.1) from central differences along the side
+    double Up[4], Um[4];
+    fetch_local(X, D.nb[4], kind, r, Up);
+    fetch_local(X, D.nb[5], kind, r, Um);
     const double rho0 = G.rho0, cs2 = L::CS2;
-    const double rho = rho0 + U[0], ut = U[2];
+    const CharSys C = char_sys<TH>(B, rho0, U);
+    const double ut = U[2];
     const double d_rhout = 0.5 * ((rho0 + Up[0]) * Up[2] - (rho0 + Um[0]) * Um[2]);
     const double d_un = 0.5 * (Up[1] - Um[1]);
     const double d_ut = 0.5 * (Up[2] - Um[2]);
     double TT[4], dP;
-    if (L::THERMAL) {
+    if (TH) {
         // rho T - rho0 = drho + rho0 dT + drho dT
         const double d_rhoT = 0.5 * ((Up[0] + rho0 * Up[3] + Up[0] * Up[3]) -
                                      (Um[0] + rho0 * Um[3] + Um[0] * Um[3]));
         const double d_Tut = 0.5 * ((1.0 + Up[3]) * Up[2] - (1.0 + Um[3]) * Um[2]);
         TT[0] = -d_rhout;
         TT[1] = -ut * d_un;
-        TT[2] = -(cs2 / rho) * d_rhoT - ut * d_ut;
+        TT[2] = -cs2 * C.irho * d_rhoT - ut * d_ut;
         TT[3] = -d_Tut;
-        dP = cs2 * (U[0] + rho0 * U[3] + U[0] * U[3]) - B.pdev[s];
+        dP = cs2 * (U[0] + rho0 * U[3] + U[0] * U[3]) - B.pdev[kind];
     } else {
         TT[0] = -d_rhout;
         TT[1] = -ut * d_un;
-        TT[2] = -(cs2 / rho) * 0.5 * (Up[0] - Um[0]) - ut * d_ut;
+        TT[2] = -cs2 * C.irho * 0.5 * (Up[0] - Um[0]) - ut * d_ut;
         TT[3] = 0.0;
-        dP = cs2 * U[0] - B.pdev[s];
+        dP = cs2 * U[0] - B.pdev[kind];
     }
-    const CharSys C = char_sys(L::THERMAL, cs2, rho0, U);
     double kl[4];
-    char_rhs(C, B, dUn, TT, V, mask, dP, B.s[s].scheme, kl);
-    to_lab(kl, F, k);
-}
-
-// Corner: LODI (Eq. PNR) along the outward diagonal at the innermost corner
-// node, with a one-sided difference of spacing sqrt(2) into the bulk.
-template <int LAT>
-__device__ void corner_rhs(const Geom& G, const Band& B, const double* Y, int par_t, double frac,
-                           int c, int mask, double k[4])
-{
-    using L = Lat<LAT>;
-    const Frame F = frame_of_corner(c);
-    const int sx = corner_sx(c), sy = corner_sy(c);
-    const int sW = sx < 0 ? 0 : 1;
-    const int yc = sy < 0 ? G.M - 1 : G.ny - G.M;
-    double U[4], U1[4], U2[4], dUn[4];
-    to_local(Y + 4LL * (B.n_side_unk + c), F, U);
-    fetch_local(G, B, Y, par_t, frac, sW, 0, yc - sy, F, U1);
-    fetch_local(G, B, Y, par_t, frac, sW, -1, yc - 2 * sy, F, U2);
-    const double h = 2.0 * sqrt(2.0);
-    for (int m = 0; m < 4; ++m) dUn[m] = (3.0 * U[m] - 4.0 * U1[m] + U2[m]) / h;
-    const double zero[4] = {0.0, 0.0, 0.0, 0.0};
-    const CharSys C = char_sys(L::THERMAL, L::CS2, G.rho0, U);
-    double kl[4];
-    char_rhs(C, B, dUn, zero, zero, mask, 0.0, SCH_LODI, kl);
-    to_lab(kl, F, k);
+    char_rhs<TH>(C, B, dUn, TT, V, mask, dP, B.scheme[kind], kl);
+    to_lab(kind, r, kl, k);
 }
 
 // ---------------------------------------------------------------------------
-// Population writes
+// Population writes (stage 3)
 // ---------------------------------------------------------------------------
 
+// Mesoscopic Dirichlet condition for the new boundary state, stored
+// post-collision: f^eq(Unew) and, for Eq. NEEP, the non-equilibrium part of
+// the bulk neighbour after its collision, f*(x_f) - f^eq(U(x_f, t+1)).  Computed
+// in the arithmetic type of the storage.
 template <int LAT, typename S>
-__device__ inline void load_g(const Geom& G, const S* f, int x, int y, double* g)
+__device__ void dirichlet(const Geom& G, const Band& B, const Export& E, S* f, int par_new,
+                          const UDesc& D, const double* Unew)
 {
     using L = Lat<LAT>;
-    const S* in = f + (long long)y * G.nxp + x;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        double v = double(Store<S>::load(in + (long long)i * G.plane));
-        if (Store<S>::SCALED) v *= L::w(i);
-        g[i] = v;
-    }
-}
-
-template <int LAT, typename S>
-__device__ inline void put_g(const Geom& G, S* f, int x, int y, const double* g)
-{
-    using L = Lat<LAT>;
-    S* out = f + (long long)y * G.nxp + x;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        double v = g[i];
-        if (Store<S>::SCALED) v *= 1.0 / L::w(i);
-        Store<S>::put(out + (long long)i * G.plane, typename Store<S>::C(v));
-    }
-}
-
-template <int LAT>
-__device__ inline void geq_of(double rho0, const double U[4], double* ge)
-{
-    Moments<LAT, double> m;
-    m.s0 = U[0];
-    m.rho = rho0 + U[0];
-    m.ux = U[1];
-    m.uy = U[2];
-    m.dT = Lat<LAT>::THERMAL ? U[3] : 0.0;
-    equilibrium<LAT, double>(m, ge);
-}
-
-// Mesoscopic Dirichlet condition for the boundary state Unew, stored
-// post-collision: f^eq(Unew), plus for Eq. NEEP the non-equilibrium part of
-// the bulk neighbour x_f after its collision, f*(x_f) - f^eq(U(x_f)).
-template <int LAT, typename S>
-__device__ void dirichlet(const Geom& G, const Band& B, S* f, int par_new, const double Unew[4],
-                          int xs, int ys, const double* Usrc, int x0, int y0, int nbx, int nby,
-                          int dx, int dy)
-{
-    using L = Lat<LAT>;
-    double ge[L::Q];
-    geq_of<LAT>(G.rho0, Unew, ge);
+    using Cm = typename Store<S>::C;
+    Moments<LAT, Cm> m;
+    m.s0 = Cm(Unew[0]);
+    m.rho = Cm(G.rho0) + m.s0;
+    m.ux = Cm(Unew[1]);
+    m.uy = Cm(Unew[2]);
+    m.dT = Cm(L::THERMAL ? Unew[3] : 0.0);
+    Cm ge[L::Q];
+    equilibrium<LAT, Cm>(m, ge);
     if (B.dirichlet == 1) {
-        double gs[L::Q], gf[L::Q];
-        load_g<LAT, S>(G, f, xs, ys, gs);
-        geq_of<LAT>(G.rho0, Usrc, gf);
+        const double* Us = E.stripU + ((long long)par_new * E.nslots + D.wslot) * 4;
+        Moments<LAT, Cm> ms;
+        ms.s0 = Cm(Us[0]);
+        ms.rho = Cm(G.rho0) + ms.s0;
+        ms.ux = Cm(Us[1]);
+        ms.uy = Cm(Us[2]);
+        ms.dT = Cm(L::THERMAL ? Us[3] : 0.0);
+        Cm gs[L::Q];
+        equilibrium<LAT, Cm>(ms, gs);
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) ge[i] += gs[i] - gf[i];
+        for (int i = 0; i < L::Q; ++i) {
+            Cm v = Cm(Store<S>::load(f + i * G.plane + D.wsrc));
+            if (Store<S>::SCALED) v *= Cm(L::w(i));
+            ge[i] += v - gs[i];
+        }
     }
-    for (int a = 0; a < nbx; ++a)
-        for (int b = 0; b < nby; ++b) put_g<LAT, S>(G, f, x0 + a * dx, y0 + b * dy, ge);
-    (void)par_new;
+    const int nb = D.kind >= 4 ? G.M : 1;
+    for (int a = 0; a < nb; ++a)
+        for (int b = 0; b < nb; ++b) {
+            const long long node = D.wnode + a * D.wdx + b * D.wdy;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                Cm v = ge[i];
+                if (Store<S>::SCALED) v *= Cm(1.0 / L::w(i));
+                Store<S>::put(f + i * G.plane + node, v);
+            }
+        }
 }
 
 template <int LAT, typename S>
 __global__ void __launch_bounds__(kBandThreads)
-    k_cbc_stage(Geom G, Band B, S* __restrict__ f, int par_t, int stage)
+    k_stage(Geom G, Band B, Export E, S* __restrict__ f, int par_t, int stage)
 {
+    using L = Lat<LAT>;
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= B.n_unk) return;
-    const double frac = stage == 0 ? 0.0 : (stage == 3 ? 1.0 : 0.5);
-    const double* Yin = stage == 0 ? B.Ub : (stage == 2 ? B.Yb : B.Ya);
-    double* Yout = stage == 1 ? B.Yb : B.Ya;
-    const bool corner = u >= B.n_side_unk;
-    int s = 0, p = 0, j = 0, c = 0;
-    if (corner) {
-        c = u - B.n_side_unk;
-    } else {
-        while (s < 3 && !(B.s[s].kind == SIDE_CBC && u >= B.s[s].base &&
-                          u < B.s[s].base + (B.s[s].hi - B.s[s].lo + 1) * G.M))
-            ++s;
-        const int r = u - B.s[s].base;
-        p = B.s[s].lo + r / G.M;
-        j = 1 + r % G.M;
+    if (stage == 3 && u >= B.n_unk) {
+        // zero gradient: copy the post-collision populations of x_f
+        const int z = u - B.n_unk;
+        if (z >= B.n_zg) return;
+        const int2 nd = B.zg[z];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) f[i * G.plane + nd.x] = f[i * G.plane + nd.y];
+        return;
     }
+    if (u >= B.n_unk) return;
+    const UDesc D = B.ud[u];
+    Ctx X;
+    X.Y = stage == 0 ? B.Ub : (stage == 2 ? B.Yb : B.Ya);
+    X.St = E.stripU + (long long)par_t * E.nslots * 4;
+    X.St1 = E.stripU + (long long)(par_t ^ 1) * E.nslots * 4;
+    X.frac = stage == 0 ? 0.0 : (stage == 3 ? 1.0 : 0.5);
+    double* Yout = stage == 1 ? B.Yb : B.Ya;
+
     double V[4];
     int mask;
     if (stage == 0) {
-        const Frame F = corner ? frame_of_corner(c) : frame_of_side(s);
         double Ul[4];
-        to_local(B.Ub + 4LL * u, F, Ul);
-        mask = incoming_mask(char_sys(Lat<LAT>::THERMAL, Lat<LAT>::CS2, G.rho0, Ul));
-        if (corner || B.viscous == VIS_OFF) {
-            V[0] = V[1] = V[2] = V[3] = 0.0;
-        } else if (B.viscous == VIS_FD) {
-            vis_fd<LAT>(G, B, par_t, s, j, p, V);
-        } else {
-            vis_meso<LAT>(G, B, par_t, s, p, V);
-        }
-        for (int m = 0; m < 4; ++m) B.V[4LL * u + m] = V[m];
+        to_local(D.kind, B.kR, B.Ub + 4LL * u, Ul);
+        mask = incoming_mask<L::THERMAL>(char_sys<L::THERMAL>(B, G.rho0, Ul));
+        if (D.kind >= 4 || B.viscous == VIS_OFF) V[0] = V[1] = V[2] = V[3] = 0.0;
+        else if (B.viscous == VIS_FD) vis_fd<L::THERMAL>(G, B, X, D, u, L::CS2, V);
+        else vis_meso<L::THERMAL>(G, B, E, par_t, D, L::CS2, V);
+        double2* vo = reinterpret_cast<double2*>(B.V + 4LL * u);
+        vo[0] = make_double2(V[0], V[1]);
+        vo[1] = make_double2(V[2], V[3]);
         B.mask[u] = mask;
     } else {
-        for (int m = 0; m < 4; ++m) V[m] = B.V[4LL * u + m];
+        const double2* vi = reinterpret_cast<const double2*>(B.V + 4LL * u);
+        const double2 v0 = vi[0], v1 = vi[1];
+        V[0] = v0.x; V[1] = v0.y; V[2] = v1.x; V[3] = v1.y;
         mask = B.mask[u];
     }
     double k[4];
-    if (corner) corner_rhs<LAT>(G, B, Yin, par_t, frac, c, mask, k);
-    else side_rhs<LAT>(G, B, Yin, par_t, frac, s, j, p, V, mask, k);
+    unknown_rhs<LAT>(G, B, X, D, u, V, mask, k);
 
     const double* U0 = B.Ub + 4LL * u;
     double* acc = B.acc + 4LL * u;
     if (stage < 3) {
         const double wk = stage == 0 ? 1.0 : 2.0;
         const double hk = stage == 2 ? 1.0 : 0.5;
+#pragma unroll
         for (int m = 0; m < 4; ++m) {
             acc[m] = (stage == 0 ? 0.0 : acc[m]) + wk * k[m];
             Yout[4LL * u + m] = U0[m] + hk * k[m];
@@ -522,91 +483,42 @@ __global__ void __launch_bounds__(kBandThreads)
         return;
     }
     double Unew[4];
-    for (int m = 0; m < 4; ++m) Unew[m] = U0[m] + (acc[m] + k[m]) / 6.0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) Unew[m] = U0[m] + (acc[m] + k[m]) * (1.0 / 6.0);
+#pragma unroll
     for (int m = 0; m < 4; ++m) B.Ub[4LL * u + m] = Unew[m];
-
-    const int par_new = par_t ^ 1;
-    if (corner) {
-        const int sx = corner_sx(c), sy = corner_sy(c);
-        const int sW = sx < 0 ? 0 : 1;
-        const int xc = sx < 0 ? G.M - 1 : G.nx - G.M;
-        const int yc = sy < 0 ? G.M - 1 : G.ny - G.M;
-        const double* Us = B.stripU + strip_u_index(B.s[sW], par_new, 0, yc - sy);
-        const int x0 = sx < 0 ? 0 : G.nx - 1, y0 = sy < 0 ? 0 : G.ny - 1;
-        dirichlet<LAT, S>(G, B, f, par_new, Unew, xc - sx, yc - sy, Us, x0, y0, G.M, G.M,
-                          sx < 0 ? 1 : -1, sy < 0 ? 1 : -1);
-    } else {
-        int xf, yf;
-        side_xf(s, p, G.nx, G.ny, G.M, xf, yf);
-        const double* Us = B.stripU + strip_u_index(B.s[s], par_new, 0, p);
-        dirichlet<LAT, S>(G, B, f, par_new, Unew, xf, yf, Us, xf + j * side_nx(s),
-                          yf + j * side_ny(s), 1, 1, 0, 0);
-    }
-}
-
-// Zero gradient (Eq. zg-bc: copy of the post-collision populations of x_f)
-// and inflow equilibrium nodes; corner blocks copy the diagonal bulk node.
-template <int LAT, typename S>
-__global__ void k_extras(Geom G, Band B, S* __restrict__ f)
-{
-    using L = Lat<LAT>;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= B.n_extra) return;
-    int kind, x, y, xs, ys;
-    if (e < B.n_extra_side) {
-        int s = 0;
-        while (s < 3 && !(B.s[s].kind >= SIDE_INFLOW && e >= B.s[s].ebase &&
-                          e < B.s[s].ebase + (B.s[s].hi - B.s[s].lo + 1) * G.M))
-            ++s;
-        const int r = e - B.s[s].ebase;
-        const int p = B.s[s].lo + r / G.M, j = 1 + r % G.M;
-        side_xf(s, p, G.nx, G.ny, G.M, xs, ys);
-        x = xs + j * side_nx(s);
-        y = ys + j * side_ny(s);
-        kind = B.s[s].kind;
-    } else {
-        const int r = e - B.n_extra_side, MM = G.M * G.M;
-        const int c = r / MM, a = (r % MM) / G.M, b = r % G.M;
-        const int sx = corner_sx(c), sy = corner_sy(c);
-        x = sx < 0 ? a : G.nx - 1 - a;
-        y = sy < 0 ? b : G.ny - 1 - b;
-        const int xc = sx < 0 ? G.M - 1 : G.nx - G.M, yc = sy < 0 ? G.M - 1 : G.ny - G.M;
-        xs = xc - sx;
-        ys = yc - sy;
-        kind = B.corner_kind;
-    }
-    double g[L::Q];
-    if (kind == SIDE_ZG) load_g<LAT, S>(G, f, xs, ys, g);
-    else geq_of<LAT>(G.rho0, B.Uin, g);
-    put_g<LAT, S>(G, f, x, y, g);
+    dirichlet<LAT, S>(G, B, E, f, par_t ^ 1, D, Unew);
 }
 
 template <int LAT, typename S>
-int boundary_t(const Geom& G, const Band& B, void* fnew, int par_t, cudaStream_t st)
+int boundary_t(const Geom& G, const Export& E, const Band& B, void* fnew, int par_t, cudaStream_t st)
 {
     S* f = static_cast<S*>(fnew);
-    if (B.n_extra > 0) k_extras<LAT, S><<<(B.n_extra + 127) / 128, 128, 0, st>>>(G, B, f);
     if (B.n_unk > 0) {
         const int nb = (B.n_unk + kBandThreads - 1) / kBandThreads;
-        for (int stage = 0; stage < 4; ++stage)
-            k_cbc_stage<LAT, S><<<nb, kBandThreads, 0, st>>>(G, B, f, par_t, stage);
+        for (int stage = 0; stage < 3; ++stage)
+            k_stage<LAT, S><<<nb, kBandThreads, 0, st>>>(G, B, E, f, par_t, stage);
     }
+    const int n3 = B.n_unk + B.n_zg;
+    if (n3 > 0)
+        k_stage<LAT, S><<<(n3 + kBandThreads - 1) / kBandThreads, kBandThreads, 0, st>>>(G, B, E, f,
+                                                                                      par_t, 3);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace
 
-int launch_boundary(int lat, int storage, const Geom& G, const Band& B, void* fnew, int par_t,
-                    cudaStream_t st)
+int launch_boundary(int lat, int storage, const Geom& G, const Export& E, const Band& B,
+                    void* fnew, int par_t, cudaStream_t st)
 {
     if (lat == D2Q9) {
-        if (storage == 0) return boundary_t<D2Q9, double>(G, B, fnew, par_t, st);
-        if (storage == 1) return boundary_t<D2Q9, float>(G, B, fnew, par_t, st);
-        if (storage == 2) return boundary_t<D2Q9, __half>(G, B, fnew, par_t, st);
+        if (storage == 0) return boundary_t<D2Q9, double>(G, E, B, fnew, par_t, st);
+        if (storage == 1) return boundary_t<D2Q9, float>(G, E, B, fnew, par_t, st);
+        if (storage == 2) return boundary_t<D2Q9, __half>(G, E, B, fnew, par_t, st);
     } else {
-        if (storage == 0) return boundary_t<D2Q37, double>(G, B, fnew, par_t, st);
-        if (storage == 1) return boundary_t<D2Q37, float>(G, B, fnew, par_t, st);
-        if (storage == 2) return boundary_t<D2Q37, __half>(G, B, fnew, par_t, st);
+        if (storage == 0) return boundary_t<D2Q37, double>(G, E, B, fnew, par_t, st);
+        if (storage == 1) return boundary_t<D2Q37, float>(G, E, B, fnew, par_t, st);
+        if (storage == 2) return boundary_t<D2Q37, __half>(G, E, B, fnew, par_t, st);
     }
     return -1;
 }

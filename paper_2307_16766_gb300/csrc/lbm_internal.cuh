@@ -142,30 +142,52 @@ struct Store<__half> {
 // ---------------------------------------------------------------------------
 
 // Coefficients of the shifted Hermite equilibrium as a polynomial in
-// p = c.u / c_s^2 for one velocity class with xi^2 = |c|^2 / c_s^2:
-//   f^eq / (w rho) - 1 = a0 + a1 p + a2 p^2 + a3 p^3 + a4 p^4.
-// Thermal (Eq. feq-4, fourth-order Hermite in xi = c/c_s, u~ = u/c_s,
-// theta - 1 = dT, with the (xi^2 - 6) coefficient of the (u.c)^2 (T-1)
-// term): a3 = 1/6, a4 = 1/24.  Isothermal D2Q9: second order.
+// p = c.u / c_s^2 for a velocity class with xi^2 = |c|^2 / c_s^2:
+//   f^eq / (w rho) - 1 = a0 + a1 p + a2 p^2 + a3 p^3 + a4 p^4,
+// and each a_k as a polynomial in xi^2:
+//   a0 = A0 + xi^2 (B0 + C0 xi^2),  a1 = A1 + B1 xi^2,  a2 = A2 + B2 xi^2.
+// Thermal lattice: Eq. feq-4, the fourth-order Hermite expansion in
+// xi = c/c_s, u~ = u/c_s, theta - 1 = t, read with the coefficient
+// (xi^2 - 6) in the (u.c)^2 (T-1) term; then a3 = 1/6, a4 = 1/24.
+// Isothermal D2Q9: second order, a0 = -u2/2, a1 = 1, a2 = 1/2.
+template <typename C>
+struct EqPoly {
+    C A0, B0, C0, A1, B1, A2, B2;
+};
+
+template <int LAT, typename C>
+__device__ __forceinline__ EqPoly<C> eq_poly(C u2, C t)
+{
+    EqPoly<C> e;
+    if (Lat<LAT>::THERMAL) {
+        e.A0 = C(-0.5) * u2 - t + C(0.125) * u2 * u2 + t * u2 + t * t;
+        e.B0 = C(0.5) * t - C(0.25) * t * u2 - t * t;
+        e.C0 = C(0.125) * t * t;
+        e.A1 = C(1) - C(0.5) * u2 - C(2) * t;
+        e.B1 = C(0.5) * t;
+        e.A2 = C(0.5) - C(0.25) * u2 - C(1.5) * t;
+        e.B2 = C(0.25) * t;
+    } else {
+        e.A0 = C(-0.5) * u2;
+        e.B0 = e.C0 = e.B1 = e.B2 = C(0);
+        e.A1 = C(1);
+        e.A2 = C(0.5);
+    }
+    return e;
+}
+
 template <int LAT, typename C>
 __device__ __forceinline__ void eq_coef(C u2, C dT, C* a0, C* a1, C* a2)
 {
     using L = Lat<LAT>;
     constexpr C ics2 = C(1.0 / L::CS2);
+    const EqPoly<C> e = eq_poly<LAT, C>(u2, dT);
 #pragma unroll
     for (int k = 0; k < L::NCLS; ++k) {
         const C xi2 = C(L::c2cls(k)) * ics2;
-        if (L::THERMAL) {
-            a0[k] = C(0.5) * (dT * (xi2 - C(2)) - u2) +
-                    C(1.0 / 24.0) * (C(3) * u2 * u2 + C(6) * dT * u2 * (C(4) - xi2) +
-                                     C(3) * dT * dT * (xi2 * xi2 - C(8) * xi2 + C(8)));
-            a1[k] = C(1) - C(0.5) * u2 + C(0.5) * dT * (xi2 - C(4));
-            a2[k] = C(0.5) - C(0.25) * u2 + C(0.25) * dT * (xi2 - C(6));
-        } else {
-            a0[k] = C(-0.5) * u2;
-            a1[k] = C(1);
-            a2[k] = C(0.5);
-        }
+        a0[k] = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
+        a1[k] = e.A1 + e.B1 * xi2;
+        a2[k] = e.A2 + e.B2 * xi2;
     }
 }
 
@@ -233,85 +255,94 @@ enum { SIDE_PERIODIC = 0, SIDE_CBC = 1, SIDE_INFLOW = 2, SIDE_ZG = 3 };
 enum { SCH_LODI = 0, SCH_LODI_RELAX = 1, SCH_CBC = 2, SCH_CBC_RELAX = 3 };
 enum { VIS_MESO = 0, VIS_FD = 1, VIS_OFF = 2 };
 
-// Grid geometry.  Populations are SoA planes f[i][y][x] with row pitch nxp.
+// Grid geometry.  Populations are SoA planes f[i][y][x] with row pitch nxp;
+// a node's offset inside a plane is y * nxp + x.
 struct Geom {
     int nx, ny, nxp, M;
     int perx, pery;
     int bx0, bx1, by0, by1;     // bulk nodes: [bx0, bx1) x [by0, by1)
     long long plane;            // ny * nxp
-    double tau, rho0;
+    double tau, rho0, omega;    // omega = 1 / tau
+    float omega_f, rho0_f;
 };
 
-// One side of the grid (W = 0, E = 1, S = 2, N = 3).
-struct Side {
-    int kind, scheme;
-    int L;                      // nodes along the side (ny for W/E, nx for S/N)
-    int lo, hi;                 // tangential range of the side's own layers
-    int tper;                   // tangential axis periodic
-    int base;                   // first characteristic unknown of the side
-    long long offU, offN;       // offsets of the side's strips (doubles)
-    int ebase;                  // first node of the side in the extras list
+// Offsets (in elements) of the pull sources and of the output planes, used
+// by the bulk kernel away from periodic wrap-around: source of velocity i is
+// node + ld[i] = i * plane - c_iy * nxp - c_ix, its output is node + st[i].
+struct Offsets {
+    int ld[37];
+    int st[37];
 };
 
-// Characteristic boundary state and the near-boundary strips the bulk kernel
-// exports: macros U (4 doubles) and non-equilibrium moments N = sigma'_xx,
-// sigma'_xy, sigma'_yy, q_x, q_y (5 doubles) at depths d = 0, 1, 2 inside
-// the boundary layers, for two time levels (parity of the step).
+// Near-boundary strips exported by the bulk kernel for each characteristic
+// side: macros U = (drho, ux, uy, dT) and non-equilibrium moments
+// N = (sigma'_xx, sigma'_xy, sigma'_yy, q_x, q_y) of the bulk nodes at depths
+// d = 0, 1, 2 inside the boundary layers (x_f, x_f - n, x_f - 2n), for two
+// time levels.  Slot of (side s, depth d, position p) = offS[s] + d L[s] + p;
+// arrays are [parity][slot][4] and [parity][slot][5].
+struct Export {
+    int cbc[4];
+    int offS[4];
+    int L[4];
+    int nslots;
+    double* stripU;
+    double* stripN;
+};
+
+// One unknown of the boundary ODE: layer j of a characteristic side at one
+// tangential position, or the innermost node of a corner block.  Every
+// neighbour the right-hand side needs is resolved when the solver is
+// created: ref >= 0 is another unknown, ref < 0 is strip slot -(ref + 1)
+// (a bulk node, interpolated in time between t and t + 1).
+struct UDesc {
+    int kind;        // side 0..3 (W, E, S, N) or 4 + corner (SW, SE, NW, NE)
+    int j;           // layer 1..M (sides)
+    int tmode;       // tangential stencil of the viscous terms: 0 central, 1 backward, -1 forward
+    int wslot;       // strip slot of the NEEP source node (its macros at t + 1)
+    int nb[6];       // +n, -n, -2n, -3n, +t, -t (corners: nb[0] = c - s, nb[1] = c - 2s)
+    int vs[5];       // strip slots for the viscous terms: d = 0, 1, 2 at p, then two tangential
+    int wsrc;        // grid offset of the NEEP source node
+    int wnode;       // grid offset of the node written (corner: block origin)
+    int wdx, wdy;    // corner block: grid-offset steps along x and y
+    int pad[3];
+};
+
 struct Band {
-    Side s[4];
-    int any_cbc;
-    int n_side_unk, n_unk;      // unknowns of the boundary ODE (sides + corners)
-    int corner_kind;            // kind of the four M x M corner blocks (or -1)
-    int n_extra;                // zero-gradient / inflow nodes (sides, then corners)
-    int n_extra_side;           // of which on the sides
+    int n_unk;       // unknowns of the boundary ODE
+    int n_zg;        // zero-gradient nodes (copied every step)
+    int M;
     int viscous, dirichlet;
+    int scheme[4];
     double alpha_T, beta_P, t_inf;
-    double pdev[4];             // P_inf - c_s^2 rho0 per side
-    double Uin[4];              // inflow state (drho, ux, uy, dT)
+    double pdev[4];  // P_inf - c_s^2 rho0 per side
+    double kA;       // 1 / sqrt(8 c_s^2)
+    double kB;       // sqrt(2 c_s^2)
+    double kC;       // 1 / (2 sqrt 2): one-sided diagonal difference
+    double kR;       // 1 / sqrt 2: corner frame
+    double cs;       // c_s (isothermal system)
+    double ihcs;     // 1 / (2 c_s)
+    const UDesc* ud;
+    const int2* zg;  // (node, source) grid offsets
     double *Ub, *Ya, *Yb, *acc, *V;
     int* mask;
-    double *stripU, *stripN;
 };
-
-// Row-major index of the strip entries.
-__host__ __device__ inline long long strip_u_index(const Side& S, int par, int d, int p)
-{
-    return S.offU + ((long long)(par * 3 + d) * S.L + p) * 4;
-}
-__host__ __device__ inline long long strip_n_index(const Side& S, int par, int d, int p)
-{
-    return S.offN + ((long long)(par * 3 + d) * S.L + p) * 5;
-}
-
-// Outward normal and tangent of each side, and the outward diagonal of each
-// corner block (SW = 0, SE = 1, NW = 2, NE = 3).
-__host__ __device__ inline int side_nx(int s) { return s == 0 ? -1 : (s == 1 ? 1 : 0); }
-__host__ __device__ inline int side_ny(int s) { return s == 2 ? -1 : (s == 3 ? 1 : 0); }
-__host__ __device__ inline int side_tx(int s) { return s < 2 ? 0 : 1; }
-__host__ __device__ inline int side_ty(int s) { return s < 2 ? 1 : 0; }
-__host__ __device__ inline int corner_sx(int c) { return (c & 1) ? 1 : -1; }
-__host__ __device__ inline int corner_sy(int c) { return (c & 2) ? 1 : -1; }
-
-// Node x_f (layer 0) of side s at tangential position p.
-__host__ __device__ inline void side_xf(int s, int p, int nx, int ny, int M, int& x, int& y)
-{
-    if (s == 0) { x = M; y = p; }
-    else if (s == 1) { x = nx - 1 - M; y = p; }
-    else if (s == 2) { x = p; y = M; }
-    else { x = p; y = ny - 1 - M; }
-}
 
 // ---------------------------------------------------------------------------
 // Host-side launchers (defined in bulk.cu / boundary.cu)
 // ---------------------------------------------------------------------------
 
-int launch_init(int lat, int storage, const Geom& G, const Band& B, const double* rho,
-                const double* ux, const double* uy, const double* T, void* f, cudaStream_t st);
-int launch_bulk(int lat, int storage, const Geom& G, const Band& B, const void* fin, void* fout,
-                int par_new, cudaStream_t st);
+// Initial populations f^eq(U0) into f, strips of time 0, boundary state.
+int launch_init(int lat, int storage, const Geom& G, const Export& E, const Band& B,
+                const double* rho, const double* ux, const double* uy, const double* T, void* f,
+                cudaStream_t st);
+// Fixed inflow equilibrium at the listed nodes of one population buffer.
+int launch_inflow(int lat, int storage, const Geom& G, const int* nodes, int n, const double Uin[4],
+                  void* f, cudaStream_t st);
+int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
+                const void* fin, void* fout, int par_new, cudaStream_t st);
 int launch_macros(int lat, int storage, const Geom& G, const void* f, double* rho, double* ux,
                   double* uy, double* T, int* flag, cudaStream_t st);
-int launch_boundary(int lat, int storage, const Geom& G, const Band& B, void* fnew, int par_t,
-                    cudaStream_t st);
+int launch_boundary(int lat, int storage, const Geom& G, const Export& E, const Band& B,
+                    void* fnew, int par_t, cudaStream_t st);
 
 }  // namespace lbmgb
