@@ -152,37 +152,87 @@ __global__ void __launch_bounds__(kBulkThreads)
     const EqPoly<C> e = eq_poly<LAT, C>(m.ux * uxs + m.uy * uys, m.dT);
     const C om = omega_of<C>(G);
     S* out = fout + node;
-    {
-        const C geq = C(L::w(0)) * (m.s0 + m.rho * e.A0);
-        C v = g[0] + om * (geq - g[0]);
-        if (Store<S>::SCALED) v *= C(1.0 / L::w(0));
-        Store<S>::put(out + O.st[0], v);
-    }
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const int k = L::cls(i);
-        const C xi2 = C(L::c2cls(k)) * ics2;
-        const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
-        const C a1 = e.A1 + e.B1 * xi2;
-        const C a2 = e.A2 + e.B2 * xi2;
-        C p;
-        if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
-        else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
-        else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
-        const C p2 = p * p;
-        const C ev = a0 + p2 * (a2 + p2 * a4);
-        const C od = p * (a1 + p2 * a3);
-        const C ws0 = C(L::w(i)) * m.s0, wr = C(L::w(i)) * m.rho;
-        const C gp = ws0 + wr * (ev + od);
-        const C gm = ws0 + wr * (ev - od);
-        C vp = g[i] + om * (gp - g[i]);
-        C vm = g[i + 1] + om * (gm - g[i + 1]);
-        if (Store<S>::SCALED) {
-            vp *= C(1.0 / L::w(i));
-            vm *= C(1.0 / L::w(i));
+    auto put = [&](int i, C v) {
+        if (Store<S>::SCALED) v *= C(1.0 / L::w(i));
+        Store<S>::put(out + O.st[i], v);
+    };
+    if (sizeof(C) == 8) {
+        {
+            const C geq = C(L::w(0)) * (m.s0 + m.rho * e.A0);
+            put(0, g[0] + om * (geq - g[0]));
         }
-        Store<S>::put(out + O.st[i], vp);
-        Store<S>::put(out + O.st[i + 1], vm);
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const int k = L::cls(i);
+            const C xi2 = C(L::c2cls(k)) * ics2;
+            const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
+            const C a1 = e.A1 + e.B1 * xi2;
+            const C a2 = e.A2 + e.B2 * xi2;
+            C p;
+            if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
+            else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
+            else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
+            const C p2 = p * p;
+            const C ev = a0 + p2 * (a2 + p2 * a4);
+            const C od = p * (a1 + p2 * a3);
+            const C ws0 = C(L::w(i)) * m.s0, wr = C(L::w(i)) * m.rho;
+            const C gp = ws0 + wr * (ev + od);
+            const C gm = ws0 + wr * (ev - od);
+            put(i, g[i] + om * (gp - g[i]));
+            put(i + 1, g[i + 1] + om * (gm - g[i + 1]));
+        }
+    } else {
+        // FP32 arithmetic.  Float-rounded weights and c_s^2 miss the discrete
+        // moment identities by ~1e-8, which would make each collision leak
+        // mass, momentum and energy at that relative rate.  The equilibrium
+        // is therefore closed on the conserved moments: the |c| = 1 pairs
+        // take the momentum and energy remainders and the rest velocity the
+        // mass remainder (corrections of float-rounding size).
+        C M0 = 0, Mx = 0, My = 0, Me = 0;
+#pragma unroll
+        for (int i = 5; i < Q; i += 2) {
+            const int k = L::cls(i);
+            const C xi2 = C(L::c2cls(k)) * ics2;
+            const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
+            const C a1 = e.A1 + e.B1 * xi2;
+            const C a2 = e.A2 + e.B2 * xi2;
+            C p;
+            if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
+            else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
+            else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
+            const C p2 = p * p;
+            const C ev = a0 + p2 * (a2 + p2 * a4);
+            const C od = p * (a1 + p2 * a3);
+            const C ws0 = C(L::w(i)) * m.s0, wr = C(L::w(i)) * m.rho;
+            const C gp = ws0 + wr * (ev + od);
+            const C gm = ws0 + wr * (ev - od);
+            const C sum = gp + gm, dif = gp - gm;
+            M0 += sum;
+            if (L::cx(i)) Mx += C(L::cx(i)) * dif;
+            if (L::cy(i)) My += C(L::cy(i)) * dif;
+            if (L::THERMAL) Me += C(L::c2cls(k)) * sum;
+            put(i, g[i] + om * (gp - g[i]));
+            put(i + 1, g[i + 1] + om * (gm - g[i + 1]));
+        }
+        // |c| = 1 class: (1,0) and (-1,0) are velocities 1, 2; (0,1), (0,-1) are 3, 4
+        const C a0 = e.A0 + ics2 * (e.B0 + e.C0 * ics2);
+        const C a2 = e.A2 + e.B2 * ics2;
+        const C px2 = uxs * uxs, py2 = uys * uys;
+        const C ws0 = C(L::w(1)) * m.s0, wr = C(L::w(1)) * m.rho;
+        C ex = ws0 + wr * (a0 + px2 * (a2 + px2 * a4));
+        C ey = ws0 + wr * (a0 + py2 * (a2 + py2 * a4));
+        if (L::THERMAL) {
+            const C d = C(0.25) * (m.se - Me - C(2) * (ex + ey));
+            ex += d;
+            ey += d;
+        }
+        const C ox = C(0.5) * (m.sx - Mx), oy = C(0.5) * (m.sy - My);
+        put(1, g[1] + om * (ex + ox - g[1]));
+        put(2, g[2] + om * (ex - ox - g[2]));
+        put(3, g[3] + om * (ey + oy - g[3]));
+        put(4, g[4] + om * (ey - oy - g[4]));
+        const C geq0 = m.s0 - M0 - C(2) * (ex + ey);
+        put(0, g[0] + om * (geq0 - g[0]));
     }
 
     // Near-boundary export for the characteristic boundary solver.

@@ -194,6 +194,7 @@ __device__ __forceinline__ void eq_coef(C u2, C dT, C* a0, C* a1, C* a2)
 template <int LAT, typename C>
 struct Moments {
     C s0, ux, uy, dT, rho;
+    C sx, sy, se;   // sum g c_x, sum g c_y, sum g |c|^2
 };
 
 // Eq. macro on shifted populations (sum_i w_i c_i = 0, sum_i w_i |c_i|^2 =
@@ -213,6 +214,9 @@ __device__ __forceinline__ Moments<LAT, C> moments(const C* g, C rho0)
     }
     Moments<LAT, C> m;
     m.s0 = s0;
+    m.sx = sx;
+    m.sy = sy;
+    m.se = se;
     m.rho = rho0 + s0;
     const C irho = C(1) / m.rho;
     m.ux = sx * irho;
