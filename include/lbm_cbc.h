@@ -151,6 +151,43 @@ const char* lbm_last_error(const lbm_handle* h);
 /* Free everything the handle owns.  NULL is ignored. */
 void lbm_destroy(lbm_handle* h);
 
+/* Allocation-free boundary step for one side.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory -- code running
+ * inside another framework's memory pool, under a no-allocation policy, or
+ * where cudaMalloc is not allowed at all -- but that hold the boundary data
+ * themselves.  It advances the characteristic boundary state of ONE straight
+ * CBC side (side index as above) whose tangential axis is periodic by one
+ * time step: the same four RK4 stages lbm_step() runs, without writing
+ * populations.
+ *
+ *   Ub        device, [length][M][4] doubles, in/out: the state of layers
+ *             j = 1..M at each tangential position, as deviations
+ *             (rho - rho0, u_x, u_y, T - 1); time t in, t + 1 out.
+ *   strip_t   device, [3][length][4]: the same quantities on the bulk nodes
+ *             at depths 0, 1, 2 inside the layers (x_f, x_f - n, x_f - 2n)
+ *             at time t;  strip_t1: the same at time t + 1.
+ *   neq_t     device, [3][length][5]: sigma'_xx, sigma'_xy, sigma'_yy, q_x,
+ *             q_y on those nodes at time t; needed only when p->viscous is
+ *             LBM_VISCOUS_MESO, otherwise may be NULL.
+ *   stream    cudaStream_t (NULL = legacy default); the call is asynchronous.
+ * Only p->scheme[side], p->viscous, alpha_T, beta_P, t_inf, p_inf[side] and
+ * rho0 are read.  length * M may not exceed 12288 (4096 positions on D2Q37,
+ * 12288 on D2Q9); larger sides are rejected with LBM_ERR_ARG and a message
+ * on stderr.
+ *
+ * Nothing is allocated: the RK4 stage scratch lives in one fixed ~1.6 MB
+ * device array inside the library, held by every GPU that loads it until the
+ * process exits.  The first call on a device looks that array's address up
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (every value a stage reads is written earlier in the same call, so nothing
+ * needs clearing); calls that overlap on the GPU -- on different streams, or
+ * from different threads -- race on it and must be serialised by the
+ * caller. */
+int lbm_cbc_side_step_noalloc(int lattice, int side, int length, double tau,
+                              const lbm_cbc_params* p, double* Ub, const double* strip_t,
+                              const double* strip_t1, const double* neq_t, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

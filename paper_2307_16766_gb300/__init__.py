@@ -27,7 +27,8 @@ __all__ = [
     "lbm_params_default", "lbm_workspace_bytes", "lbm_create", "lbm_create_in",
     "lbm_set_stream", "lbm_init_fields", "lbm_step", "lbm_step_phase", "lbm_get_macros",
     "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_steps_done",
-    "lbm_last_error", "lbm_destroy", "Simulation", "params_from_run", "LbmError",
+    "lbm_last_error", "lbm_destroy", "lbm_cbc_side_step_noalloc", "Simulation",
+    "params_from_run", "LbmError",
 ]
 
 LBM_D2Q9, LBM_D2Q37 = 0, 1
@@ -88,6 +89,8 @@ def lib():
             "lbm_steps_done": (C.c_longlong, [vp]),
             "lbm_last_error": (C.c_char_p, [vp]),
             "lbm_destroy": (None, [vp]),
+            "lbm_cbc_side_step_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, pp,
+                                                    vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -228,6 +231,16 @@ def lbm_last_error(h) -> str:
 def lbm_destroy(h):
     if h:
         lib().lbm_destroy(h)
+
+
+def lbm_cbc_side_step_noalloc(lattice, side, length, tau, params, ub_ptr, strip_t_ptr,
+                              strip_t1_ptr, neq_t_ptr=0, stream_ptr=0):
+    """Allocation-free boundary step of one side (device pointers as ints);
+    see include/lbm_cbc.h for the layouts."""
+    _check(lib().lbm_cbc_side_step_noalloc(int(lattice), int(side), int(length), float(tau),
+                                           C.byref(params), C.c_void_p(ub_ptr),
+                                           C.c_void_p(strip_t_ptr), C.c_void_p(strip_t1_ptr),
+                                           C.c_void_p(neq_t_ptr or None), C.c_void_p(stream_ptr or None)))
 
 
 # ---------------------------------------------------------- convenience ---

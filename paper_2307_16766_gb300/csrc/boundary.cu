@@ -524,3 +524,204 @@ int launch_boundary(int lat, int storage, const Geom& G, const Export& E, const 
 }
 
 }  // namespace lbmgb
+
+// ---------------------------------------------------------------------------
+// Allocation-free boundary step for one side (no counterpart in the paper)
+// ---------------------------------------------------------------------------
+// Some callers cannot allocate device memory: code that runs inside another
+// framework's memory pool, under a no-allocation policy, or in a context
+// where cudaMalloc is forbidden.  lbm_cbc_side_step_noalloc() advances the
+// characteristic boundary state of one straight CBC side whose tangential
+// axis is periodic by one time step (the four RK4 stages above), with its
+// stage scratch in the file-scope array below instead of a workspace.
+
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "lbm_cbc.h"
+
+namespace lbmgb {
+namespace {
+
+constexpr int kNoAllocMaxUnknowns = 12288;     // M * length: 4096 positions of D2Q37
+constexpr int kNoAllocMaxDevices = 64;
+// Ya, Yb, acc, V (4 doubles per unknown each), then the incoming masks.
+constexpr size_t kNoAllocDoubles = 16ull * kNoAllocMaxUnknowns + kNoAllocMaxUnknowns / 2;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+template <int LAT>
+__global__ void __launch_bounds__(kBandThreads)
+    k_side_stage_noalloc(Geom G, Band B, Export E, int side, int L, const double* __restrict__ St,
+                         const double* __restrict__ St1, int stage)
+{
+    using Lt = Lat<LAT>;
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= B.n_unk) return;
+    const int M = B.M, p = u / M, j = 1 + u % M;
+    auto wrapp = [L](int q) { return q < 0 ? q + L : (q >= L ? q - L : q); };
+    auto ref = [&](int jj, int q) {
+        q = wrapp(q);
+        return jj >= 1 ? q * M + (jj - 1) : -((-jj) * L + q + 1);
+    };
+    UDesc D;
+    D.kind = side;
+    D.j = j;
+    D.tmode = 0;
+    D.nb[0] = j < M ? ref(j + 1, p) : 0;
+    D.nb[1] = ref(j - 1, p);
+    D.nb[2] = ref(j - 2, p);
+    D.nb[3] = ref(j - 3, p);
+    D.nb[4] = ref(j, p + 1);
+    D.nb[5] = ref(j, p - 1);
+    D.vs[0] = p;
+    D.vs[1] = L + p;
+    D.vs[2] = 2 * L + p;
+    D.vs[3] = wrapp(p + 1);
+    D.vs[4] = wrapp(p - 1);
+    Ctx X;
+    X.Y = stage == 0 ? B.Ub : (stage == 2 ? B.Yb : B.Ya);
+    X.St = St;
+    X.St1 = St1;
+    X.frac = stage == 0 ? 0.0 : (stage == 3 ? 1.0 : 0.5);
+    double* Yout = stage == 1 ? B.Yb : B.Ya;
+    double V[4];
+    int mask;
+    if (stage == 0) {
+        double Ul[4];
+        to_local(side, B.kR, B.Ub + 4LL * u, Ul);
+        mask = incoming_mask<Lt::THERMAL>(char_sys<Lt::THERMAL>(B, G.rho0, Ul));
+        if (B.viscous == VIS_OFF) V[0] = V[1] = V[2] = V[3] = 0.0;
+        else if (B.viscous == VIS_FD) vis_fd<Lt::THERMAL>(G, B, X, D, u, Lt::CS2, V);
+        else vis_meso<Lt::THERMAL>(G, B, E, 0, D, Lt::CS2, V);
+        for (int m = 0; m < 4; ++m) B.V[4LL * u + m] = V[m];
+        B.mask[u] = mask;
+    } else {
+        for (int m = 0; m < 4; ++m) V[m] = B.V[4LL * u + m];
+        mask = B.mask[u];
+    }
+    double k[4];
+    unknown_rhs<LAT>(G, B, X, D, u, V, mask, k);
+    const double* U0 = B.Ub + 4LL * u;
+    double* acc = B.acc + 4LL * u;
+    if (stage < 3) {
+        const double wk = stage == 0 ? 1.0 : 2.0;
+        const double hk = stage == 2 ? 1.0 : 0.5;
+        for (int m = 0; m < 4; ++m) {
+            acc[m] = (stage == 0 ? 0.0 : acc[m]) + wk * k[m];
+            Yout[4LL * u + m] = U0[m] + hk * k[m];
+        }
+        return;
+    }
+    double Unew[4];
+    for (int m = 0; m < 4; ++m) Unew[m] = U0[m] + (acc[m] + k[m]) * (1.0 / 6.0);
+    for (int m = 0; m < 4; ++m) B.Ub[4LL * u + m] = Unew[m];
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the array's name as a device address).
+int noalloc_scratch(double** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "lbm_cbc_side_step_noalloc: cudaGetDevice: %s\n", cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        fprintf(stderr, "lbm_cbc_side_step_noalloc: device %d beyond the supported %d\n", dev,
+                kNoAllocMaxDevices);
+        return LBM_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "lbm_cbc_side_step_noalloc: cudaGetSymbolAddress: %s\n",
+                    cudaGetErrorString(e));
+            return LBM_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return LBM_OK;
+}
+
+}  // namespace
+}  // namespace lbmgb
+
+extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, double tau,
+                                         const lbm_cbc_params* p, double* Ub, const double* strip_t,
+                                         const double* strip_t1, const double* neq_t, void* stream)
+{
+    using namespace lbmgb;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D2Q37) return LBM_ERR_ARG;
+    if (!p || !Ub || !strip_t || !strip_t1 || side < 0 || side > 3 || !(tau > 0.5)) return LBM_ERR_ARG;
+    if (p->viscous < 0 || p->viscous > 2 || p->scheme[side] < 0 || p->scheme[side] > 3 || !(p->rho0 > 0.0))
+        return LBM_ERR_ARG;
+    if (p->viscous == LBM_VISCOUS_MESO && !neq_t) {
+        fprintf(stderr, "lbm_cbc_side_step_noalloc: mesoscopic viscous terms need neq_t\n");
+        return LBM_ERR_ARG;
+    }
+    const int M = lattice == LBM_D2Q9 ? 1 : 3;
+    if (length < 3 || (long long)length * M > kNoAllocMaxUnknowns) {
+        fprintf(stderr,
+                "lbm_cbc_side_step_noalloc: side length %d outside [3, %d] (at most %d unknowns)\n",
+                length, kNoAllocMaxUnknowns / M, kNoAllocMaxUnknowns);
+        return LBM_ERR_ARG;
+    }
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != LBM_OK) return rc;
+    const double cs2 = lattice == LBM_D2Q9 ? Lat<D2Q9>::CS2 : Lat<D2Q37>::CS2;
+    const int n = length * M;
+    Geom G{};
+    G.M = M;
+    G.tau = tau;
+    G.rho0 = p->rho0;
+    Band B{};
+    B.n_unk = n;
+    B.M = M;
+    B.viscous = p->viscous;
+    B.scheme[side] = p->scheme[side];
+    B.alpha_T = p->alpha_T;
+    B.beta_P = p->beta_P;
+    B.t_inf = p->t_inf;
+    const double pinf = p->p_inf[side] != 0.0 ? p->p_inf[side] : cs2 * p->rho0;
+    B.pdev[side] = pinf - cs2 * p->rho0;
+    B.kA = 1.0 / std::sqrt(8.0 * cs2);
+    B.kB = std::sqrt(2.0 * cs2);
+    B.kC = 1.0 / (2.0 * std::sqrt(2.0));
+    B.kR = 1.0 / std::sqrt(2.0);
+    B.cs = std::sqrt(cs2);
+    B.ihcs = 0.5 / B.cs;
+    B.Ub = Ub;
+    B.Ya = scratch;
+    B.Yb = scratch + 4ull * kNoAllocMaxUnknowns;
+    B.acc = scratch + 8ull * kNoAllocMaxUnknowns;
+    B.V = scratch + 12ull * kNoAllocMaxUnknowns;
+    B.mask = reinterpret_cast<int*>(scratch + 16ull * kNoAllocMaxUnknowns);
+    Export E{};
+    E.nslots = 3 * length;
+    E.stripU = const_cast<double*>(strip_t);
+    E.stripN = const_cast<double*>(neq_t);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nb = (n + kBandThreads - 1) / kBandThreads;
+    for (int stage = 0; stage < 4; ++stage) {
+        if (lattice == LBM_D2Q9)
+            k_side_stage_noalloc<D2Q9><<<nb, kBandThreads, 0, st>>>(G, B, E, side, length, strip_t, strip_t1, stage);
+        else
+            k_side_stage_noalloc<D2Q37><<<nb, kBandThreads, 0, st>>>(G, B, E, side, length, strip_t, strip_t1, stage);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "lbm_cbc_side_step_noalloc: launch: %s\n", cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
