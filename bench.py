@@ -6,8 +6,8 @@ workload (1024 x 512, inflow | CBC-RELAX outlet, periodic y).
                   [--impl gb300|reference]
 
 Prints one JSON line.  Timing: W untimed warm-up steps, then K steps, each
-bracketed by CUDA events on the solver's stream with an L2 flush (a write of
-a buffer larger than L2) between timed steps; barrier + synchronize around the
+bracketed by CUDA events on the solver's stream with an L2 flush (a write,
+then a read, of a 512 MB buffer) between timed steps; barrier + synchronize around the
 timed region; the max over ranks is reported.  N > 1 runs independent
 replicas, one per GPU (weak scaling; the method has no cross-GPU exchange in
 this configuration).  The reference arm times the FP64 CPU oracle on this
@@ -61,7 +61,7 @@ def workload(nx, ny, storage, steps):
 def workload_config(cfg, extra=None):
     d = {"workload": cfg["name"], "lattice": cfg["lattice"], "nx": cfg["nx"], "ny": cfg["ny"],
          "tau": cfg["tau"], "sides": cfg["sides"], "scheme_outlet": cfg["schemes"][1],
-         "viscous": cfg["viscous"], "storage": cfg["storage"], "l2": "flushed between timed steps"}
+         "viscous": cfg["viscous"], "storage": cfg["storage"], "l2": "flushed between timed steps (512 MB write + read)"}
     if extra:
         d.update(extra)
     return d
@@ -164,6 +164,7 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
     sim.init_fields(*fields)
     stream = sim.stream
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush_sum = torch.empty((), dtype=torch.float32, device=dev)
 
     for _ in range(args.warmup):
         sim.step(1)
@@ -179,7 +180,11 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for k in range(K):
-            flush.fill_(float(k))                       # evict L2 between timed steps
+            # Evict L2 between timed steps: write a 512 MB buffer, then read it
+            # back so that the lines left in L2 are clean (no write-back of the
+            # flush lands inside the next timed step).
+            flush.fill_(float(k))
+            torch.sum(flush, dim=0, out=flush_sum)
             ev[k][0].record(stream)
             sim.step_phase(0)                           # bulk stream-collide
             ev[k][1].record(stream)

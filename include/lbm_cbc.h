@@ -43,6 +43,7 @@ extern "C" {
 #define LBM_ERR_CUDA       -3   /* a CUDA call failed (message has the reason)  */
 #define LBM_ERR_NUMERICAL  -4   /* non-finite macroscopic values were produced  */
 #define LBM_ERR_STATE      -5   /* call out of order (e.g. step before init)    */
+#define LBM_ERR_TIMEOUT    -6   /* a bounded device-side wait gave up           */
 
 /* Velocity sets (Appendix B): D2Q9 (M = 1, isothermal, second-order
  * equilibrium) and D2Q37 (M = 3, fourth-order Hermite equilibrium, Eq. feq-4). */

@@ -40,7 +40,7 @@ SCHEMES = {"lodi": 0, "lodi_relax": 1, "cbc": 2, "cbc_relax": 3}
 VISCOUS = {"meso": 0, "fd": 1, "off": 2}
 DIRICHLET = {"eq": 0, "neep": 1}
 ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_ALLOC", -3: "LBM_ERR_CUDA",
-          -4: "LBM_ERR_NUMERICAL", -5: "LBM_ERR_STATE"}
+          -4: "LBM_ERR_NUMERICAL", -5: "LBM_ERR_STATE", -6: "LBM_ERR_TIMEOUT"}
 
 
 class LbmError(RuntimeError):

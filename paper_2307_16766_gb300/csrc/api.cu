@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "lbm_cbc.h"
 #include "lbm_internal.cuh"
 
@@ -33,7 +35,8 @@ struct lbm_handle {
     bool inflow_done[2] = {false, false};   // buffer already holds the inflow equilibrium
     double Uin[4] = {0, 0, 0, 0};
     double* macro = nullptr;
-    int* flag = nullptr;
+    int* flag = nullptr;     // [0]: non-finite macros seen, [1]: kernel status bits
+    CUtensorMap tmap[2][3];  // tensor-copy descriptors of the two buffers, box depths 7, 5, 3
     void* ws = nullptr;
     size_t ws_bytes = 0;
     bool owns_ws = false;
@@ -149,8 +152,9 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     G.omega_f = float(1.0 / tau);
     G.rho0_f = float(p->rho0);
     for (int i = 0; i < Q; ++i) {
-        pl.O.st[i] = int(i * G.plane);
-        pl.O.ld[i] = int(i * G.plane) - lattice_cy(lattice, i) * nxp - lattice_cx(lattice, i);
+        const int plane_i = lattice == LBM_D2Q9 ? Lat<D2Q9>::plane_of(i) : Lat<D2Q37>::plane_of(i);
+        pl.O.st[i] = int(plane_i * G.plane);
+        pl.O.ld[i] = int(plane_i * G.plane) - lattice_cy(lattice, i) * nxp - lattice_cx(lattice, i);
     }
 
     // strips: slots (side, depth, position) of the characteristic sides
@@ -309,7 +313,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     pl.off_zg = take(pl.zg.size() * sizeof(int2));
     pl.off_in = take(pl.inflow.size() * sizeof(int));
     pl.off_macro = take((size_t)4 * nx * ny * 8);
-    pl.off_flag = take(sizeof(int));
+    pl.off_flag = take(2 * sizeof(int));
     pl.total = o;
     return LBM_OK;
 }
@@ -328,6 +332,52 @@ int check_launch(lbm_handle* h, int rc, const char* what)
     if (rc == 0) return LBM_OK;
     const cudaError_t e = cudaGetLastError();
     return cuda_fail(h, e == cudaSuccess ? cudaErrorLaunchFailure : e, what);
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3D view [Q][ny][nxp] of a population buffer; box = one padded row segment
+// of 128 + 2H elements in `depth` consecutive planes (the bulk kernel's
+// tensor copies of one c_y group).
+int encode_population_map(lbm_handle* h, void* base, int depth, CUtensorMap* map)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) {
+        h->err = "cuTensorMapEncodeTiled is not available from the driver";
+        return LBM_ERR_CUDA;
+    }
+    const int es = int(h->esize);
+    const int halo = es == 2 ? 8 : 4;
+    const CUtensorMapDataType dt = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    cuuint64_t dims[3] = {cuuint64_t(h->G.nxp), cuuint64_t(h->ny), cuuint64_t(h->Q)};
+    cuuint64_t strides[2] = {cuuint64_t(h->G.nxp) * es, cuuint64_t(h->G.plane) * es};
+    cuuint32_t box[3] = {cuuint32_t(128 + 2 * halo), 1, cuuint32_t(depth)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        h->err = fmt("cuTensorMapEncodeTiled failed (%d)", int(r));
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
 }
 
 int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_params* p,
@@ -367,9 +417,16 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     for (int c = 0; c < 4; ++c) h->Uin[c] = pl.Uin[c];
     h->macro = at<double>(ws, pl.off_macro);
     h->flag = at<int>(ws, pl.off_flag);
-    // Zero the strips (positions no kernel writes stay finite) and upload the
-    // boundary tables.
+    const int depths[3] = {7, 5, 3};
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 3; ++k) {
+            const int rc = encode_population_map(h, h->f[b], depths[k] <= h->Q ? depths[k] : 1, &h->tmap[b][k]);
+            if (rc != LBM_OK) return rc;
+        }
+    // Zero the strips (positions no kernel writes stay finite) and the
+    // status words, and upload the boundary tables.
     cudaError_t e = cudaMemsetAsync(h->E.stripU, 0, pl.stripU_n * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, 2 * sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->E.stripN, 0, pl.stripN_n * 8, h->stream);
     if (e == cudaSuccess && !pl.ud.empty())
         e = cudaMemcpyAsync(const_cast<UDesc*>(h->B.ud), pl.ud.data(), pl.ud.size() * sizeof(UDesc),
@@ -525,8 +582,8 @@ int lbm_step_phase(lbm_handle* h, int phase)
     const int par = int(h->steps & 1);
     if (phase == 0) {
         if (h->bulk_pending) { h->err = "bulk phase issued twice"; return LBM_ERR_STATE; }
-        const int rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->E, h->f[par], h->f[par ^ 1],
-                                   par ^ 1, h->stream);
+        const int rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->E, h->tmap[par], h->f[par],
+                                   h->f[par ^ 1], par ^ 1, h->flag + 1, h->stream);
         if (rc) return check_launch(h, rc, "bulk kernel");
         h->bulk_pending = true;
         return LBM_OK;
@@ -577,7 +634,7 @@ int lbm_get_macros(lbm_handle* h, double* rho, double* ux, double* uy, double* T
     } else {
         for (int c = 0; c < 4; ++c) d[c] = h->macro + c * n;
     }
-    cudaError_t e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+    cudaError_t e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);   // status word kept
     if (e != cudaSuccess) return cuda_fail(h, e, "flag reset");
     const int rc = launch_macros(h->lattice, h->storage, h->G, h->f[h->steps & 1], d[0], d[1], d[2], d[3],
                                  h->flag, h->stream);
@@ -589,11 +646,15 @@ int lbm_get_macros(lbm_handle* h, double* rho, double* ux, double* uy, double* T
             if (e != cudaSuccess) return cuda_fail(h, e, "copy of macros");
         }
     }
-    int flag = 0;
-    e = cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    int flag[2] = {0, 0};
+    e = cudaMemcpyAsync(flag, h->flag, sizeof flag, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "macros");
-    if (flag) {
+    if (flag[1]) {
+        h->err = "a tensor copy of the bulk kernel did not complete in time";
+        return LBM_ERR_TIMEOUT;
+    }
+    if (flag[0]) {
         h->err = "non-finite macroscopic values";
         return LBM_ERR_NUMERICAL;
     }

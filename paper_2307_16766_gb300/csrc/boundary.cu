@@ -406,7 +406,7 @@ __device__ void dirichlet(const Geom& G, const Band& B, const Export& E, S* f, i
         equilibrium<LAT, Cm>(ms, gs);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            Cm v = Cm(Store<S>::load(f + i * G.plane + D.wsrc));
+            Cm v = Cm(Store<S>::load(f + L::plane_of(i) * G.plane + D.wsrc));
             if (Store<S>::SCALED) v *= Cm(L::w(i));
             ge[i] += v - gs[i];
         }
@@ -419,7 +419,7 @@ __device__ void dirichlet(const Geom& G, const Band& B, const Export& E, S* f, i
             for (int i = 0; i < L::Q; ++i) {
                 Cm v = ge[i];
                 if (Store<S>::SCALED) v *= Cm(1.0 / L::w(i));
-                Store<S>::put(f + i * G.plane + node, v);
+                Store<S>::put(f + L::plane_of(i) * G.plane + node, v);
             }
         }
 }

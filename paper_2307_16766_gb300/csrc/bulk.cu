@@ -12,17 +12,86 @@
 //
 // Populations are stored post-collision and shifted, g = f* - w rho0, in SoA
 // planes [Q][ny][nxp].  A bulk node pulls g*_i(x - c_i) for every i.  Away
-// from periodic wrap-around the pull sources sit at fixed element offsets
-// from the node (Offsets, in the kernel parameter bank), so each load and
-// store needs one address instruction.  The FP32/FP16 paths do all of their
-// arithmetic in FP32; the FP64 path in FP64.
+// from periodic wrap-around the 37 shifted source rows of a 128-node row
+// segment are staged through shared memory by tensor copies (TMA); stores
+// go straight to global memory at fixed plane offsets (Offsets, in the
+// kernel parameter bank).  The FP32/FP16 paths do all of their arithmetic in
+// FP32; the FP64 path in FP64.
 #include "lbm_internal.cuh"
+
+#include <utility>
 
 namespace lbmgb {
 
 namespace {
 
-constexpr int kBulkThreads = 128;
+constexpr int kBulkThreads = 128;   // one CTA = one row segment of 128 nodes
+
+// TMA staging.  For population i a CTA needs the source row segment
+// [x0 - c_ix, x0 + 127 - c_ix] of row y - c_iy.  Planes are stored grouped by
+// c_y, so one 3D tensor copy brings, for every population of a group, the
+// 16-byte-aligned box [x0 - H, x0 + 128 + H) of its source row into shared
+// memory (H = 4 elements for 4- and 8-byte storage, 8 for 2-byte storage,
+// >= max |c_x| = 3); each thread then reads its shifted values there.
+// Group boxes start 128-byte aligned.
+template <int LAT, typename S>
+struct Stage {
+    static constexpr int H = sizeof(S) == 2 ? 8 : 4;
+    static constexpr int W = kBulkThreads + 2 * H;                 // elements per row box
+    static constexpr int ROWB = W * int(sizeof(S));                // bytes per row box
+    __host__ __device__ static constexpr int gbytes(int g) { return Lat<LAT>::gcount(g) * ROWB; }
+    __host__ __device__ static constexpr int gofs(int g)           // byte offset of group g
+    {
+        int o = 0;
+        for (int k = 0; k < g; ++k) o += (gbytes(k) + 127) / 128 * 128;
+        return o;
+    }
+    static constexpr int TOTAL = gofs(Lat<LAT>::NG);
+    static constexpr int TX = Lat<LAT>::Q * ROWB;                  // bytes per tile
+    // element index of velocity i's row box inside the staging buffer
+    __host__ __device__ static constexpr int elem(int i)
+    {
+        return gofs(group_of<LAT>(i)) / int(sizeof(S)) +
+               (Lat<LAT>::plane_of(i) - Lat<LAT>::gstart(group_of<LAT>(i))) * W;
+    }
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the transaction barrier (phase 0) with a 1 s limit; on timeout
+// record it in *status and wait once more (again bounded) for copies still
+// in flight before giving up.
+__device__ bool wait_tx(unsigned long long* bar, int* status)
+{
+    const unsigned a = smem_u32(bar);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+            unsigned ok;
+            asm volatile(
+                "{\n .reg .pred p;\n"
+                " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                " selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(ok)
+                : "r"(a), "r"(0u)
+                : "memory");
+            if (ok) return attempt == 0;
+            if (global_ns() - t0 > 1000000000ull) break;
+        }
+        if (attempt == 0) atomicOr(status, 2);
+    }
+    return false;
+}
 
 template <typename C>
 __device__ __forceinline__ C omega_of(const Geom& G);
@@ -105,29 +174,88 @@ __device__ __noinline__ void export_node(const Geom& G, const Offsets& O, const 
     }
 }
 
+// Tensor maps of the input buffer: box depths 7, 5 and 3 planes.
+struct Maps {
+    CUtensorMap m7, m5, m3;
+};
+
+// One 3D tensor copy per c_y group; every offset, coordinate shift and map
+// choice is a template constant so nothing is looked up at run time.
+template <int LAT, typename S, int GI>
+__device__ __forceinline__ void issue_group(const Maps& tm, unsigned char* smem, int x0, int y,
+                                            unsigned bar)
+{
+    using L = Lat<LAT>;
+    using BX = Stage<LAT, S>;
+    constexpr int cnt = L::gcount(GI);
+    static_assert(cnt == 7 || cnt == 5 || cnt == 3, "group depth without a tensor map");
+    constexpr int ofs = BX::gofs(GI);
+    constexpr int dy = L::gcy(GI);
+    constexpr int z0 = L::gstart(GI);
+    const CUtensorMap* m = cnt == 7 ? &tm.m7 : (cnt == 5 ? &tm.m5 : &tm.m3);
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(smem + ofs)), "l"(m), "r"(x0 - BX::H), "r"(y - dy), "r"(z0), "r"(bar)
+        : "memory");
+}
+
+template <int LAT, typename S, int... GI>
+__device__ __forceinline__ void issue_copies(const Maps& tm, unsigned char* smem, int x0, int y,
+                                             unsigned bar, std::integer_sequence<int, GI...>)
+{
+    (issue_group<LAT, S, GI>(tm, smem, x0, y, bar), ...);
+}
+
+// g_i = staged source row of velocity i at column t - c_ix (offsets folded).
+template <int LAT, typename S, typename C, int... I>
+__device__ __forceinline__ void gather_staged(C* g, const S* sb, int t,
+                                              std::integer_sequence<int, I...>)
+{
+    using BX = Stage<LAT, S>;
+    ((g[I] = C(sb[std::integral_constant<int, BX::elem(I) + BX::H - Lat<LAT>::cx(I)>::value + t])),
+     ...);
+}
+
 template <int LAT, typename S>
 __global__ void __launch_bounds__(kBulkThreads)
-    k_bulk(Geom G, Offsets O, Export E, const S* __restrict__ fin, S* __restrict__ fout,
-           int par_new)
+    k_bulk(const __grid_constant__ Maps tm, Geom G, Offsets O, Export E,
+           const S* __restrict__ fin, S* __restrict__ fout, int par_new, int* status)
 {
     using L = Lat<LAT>;
     using C = typename Store<S>::C;
+    using BX = Stage<LAT, S>;
     constexpr int Q = L::Q;
-    const int x0 = G.bx0 + blockIdx.x * blockDim.x;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar;
+    const int x0 = (G.bx0 / kBulkThreads + blockIdx.x) * kBulkThreads;   // tiles aligned to 128
     const int x = x0 + threadIdx.x;
     const int y = G.by0 + blockIdx.y;
-    if (x >= G.bx1) return;
+    const bool valid = x >= G.bx0 && x < G.bx1;
     const int node = y * G.nxp + x;
 
-    // Pull stream (Eq. lbe): g_i(x) = g*_i(x - c_i).  The block takes the
-    // offset table unless its row or columns wrap around a periodic axis.
+    // Pull stream (Eq. lbe): g_i(x) = g*_i(x - c_i).  Segments whose sources
+    // wrap around a periodic axis use plain loads; all others stage the 37
+    // shifted source rows through shared memory with tensor copies.
     const bool wrap = (G.pery && (y < L::M || y >= G.ny - L::M)) ||
-                      (G.perx && (x0 < L::M || x0 + kBulkThreads > G.nx - L::M));
+                      (G.perx && (x0 - L::M < 0 || x0 + kBulkThreads + L::M > G.nx));
     C g[Q];
     if (!wrap) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = C(Store<S>::load(fin + (node + O.ld[i])));
+        S* sb = reinterpret_cast<S*>(smem_raw);
+        if (threadIdx.x == 0) {
+            const unsigned b = smem_u32(&bar);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         ::"r"(b), "r"(BX::TX) : "memory");
+            issue_copies<LAT, S>(tm, smem_raw, x0, y, b, std::make_integer_sequence<int, L::NG>{});
+        }
+        __syncthreads();
+        if (!wait_tx(&bar, status) || !valid) return;
+        gather_staged<LAT, S, C>(g, sb, threadIdx.x, std::make_integer_sequence<int, Q>{});
     } else {
+        if (!valid) return;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             int xs = x - L::cx(i), ys = y - L::cy(i);
@@ -264,7 +392,7 @@ __global__ void k_init(Geom G, Export E, const double* __restrict__ rho,
     for (int i = 0; i < L::Q; ++i) {
         double v = geq[i];
         if (Store<S>::SCALED) v *= 1.0 / L::w(i);
-        Store<S>::put(out + (long long)i * G.plane, typename Store<S>::C(v));
+        Store<S>::put(out + (long long)L::plane_of(i) * G.plane, typename Store<S>::C(v));
     }
     // strips of time 0 (parity 0): U0 and zero non-equilibrium moments
     const int dd[4] = {x - G.M, G.nx - 1 - G.M - x, y - G.M, G.ny - 1 - G.M - y};
@@ -303,7 +431,7 @@ __global__ void k_inflow(Geom G, const int* __restrict__ nodes, int n, double d0
     for (int i = 0; i < L::Q; ++i) {
         double v = geq[i];
         if (Store<S>::SCALED) v *= 1.0 / L::w(i);
-        Store<S>::put(f + i * G.plane + node, typename Store<S>::C(v));
+        Store<S>::put(f + L::plane_of(i) * G.plane + node, typename Store<S>::C(v));
     }
 }
 
@@ -339,7 +467,7 @@ __global__ void k_macros(Geom G, const S* __restrict__ f, double* __restrict__ r
     double g[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        double v = double(Store<S>::load(in + (long long)i * G.plane));
+        double v = double(Store<S>::load(in + (long long)L::plane_of(i) * G.plane));
         if (Store<S>::SCALED) v *= L::w(i);
         g[i] = v;
     }
@@ -373,14 +501,20 @@ int inflow_t(const Geom& G, const int* nodes, int n, const double U[4], void* f,
 }
 
 template <int LAT, typename S>
-int bulk_t(const Geom& G, const Offsets& O, const Export& E, const void* fin, void* fout,
-           int par_new, cudaStream_t st)
+int bulk_t(const Geom& G, const Offsets& O, const Export& E, const CUtensorMap* tmaps,
+           const void* fin, void* fout, int par_new, int* status, cudaStream_t st)
 {
-    const int w = G.bx1 - G.bx0, h = G.by1 - G.by0;
-    if (w <= 0 || h <= 0) return 0;
-    dim3 blk(kBulkThreads), grd((w + kBulkThreads - 1) / kBulkThreads, h);
-    k_bulk<LAT, S><<<grd, blk, 0, st>>>(G, O, E, static_cast<const S*>(fin), static_cast<S*>(fout),
-                                        par_new);
+    const int h = G.by1 - G.by0;
+    if (G.bx1 <= G.bx0 || h <= 0) return 0;
+    const int t0 = G.bx0 / kBulkThreads, t1 = (G.bx1 + kBulkThreads - 1) / kBulkThreads;
+    const size_t smem = Stage<LAT, S>::TOTAL;
+    Maps tm;
+    tm.m7 = tmaps[0];
+    tm.m5 = tmaps[1];
+    tm.m3 = tmaps[2];
+    dim3 blk(kBulkThreads), grd(t1 - t0, h);
+    k_bulk<LAT, S><<<grd, blk, smem, st>>>(tm, G, O, E, static_cast<const S*>(fin),
+                                           static_cast<S*>(fout), par_new, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -427,9 +561,10 @@ int launch_inflow(int lat, int storage, const Geom& G, const int* nodes, int n, 
 }
 
 int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
-                const void* fin, void* fout, int par_new, cudaStream_t st)
+                const CUtensorMap* tmaps, const void* fin, void* fout, int par_new, int* status,
+                cudaStream_t st)
 {
-#define CALL(L, S) bulk_t<L, S>(G, O, E, fin, fout, par_new, st)
+#define CALL(L, S) bulk_t<L, S>(G, O, E, tmaps, fin, fout, par_new, status, st)
     LBM_DISPATCH(lat, storage, CALL);
 #undef CALL
 }

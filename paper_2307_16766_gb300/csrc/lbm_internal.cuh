@@ -3,6 +3,7 @@
 // api.cu).  Nothing here is visible through the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -50,6 +51,29 @@ struct Lat<D2Q9> {
         return v[k];
     }
     __host__ __device__ static constexpr double w(int i) { return wcls(cls(i)); }
+    // Population planes are stored grouped by c_y (groups c_y = 0, 1, -1)
+    // so that one tensor copy fetches every population with a common source row.
+    static constexpr int NG = 3;
+    __host__ __device__ static constexpr int plane_of(int i)
+    {
+        constexpr int v[9] = {0, 1, 2, 3, 6, 4, 7, 8, 5};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int gcy(int g)
+    {
+        constexpr int v[3] = {0, 1, -1};
+        return v[g];
+    }
+    __host__ __device__ static constexpr int gstart(int g)
+    {
+        constexpr int v[3] = {0, 3, 6};
+        return v[g];
+    }
+    __host__ __device__ static constexpr int gcount(int g)
+    {
+        constexpr int v[3] = {3, 3, 3};
+        return v[g];
+    }
 };
 
 // D2Q37, Tab. d2q37 velocity classes (0,0) (1,0) (1,1) (2,0) (2,1) (2,2) (3,0)
@@ -103,7 +127,42 @@ struct Lat<D2Q37> {
         return v[k];
     }
     __host__ __device__ static constexpr double w(int i) { return wcls(cls(i)); }
+    // planes grouped by c_y = 0, 1, -1, 2, -2, 3, -3
+    static constexpr int NG = 7;
+    __host__ __device__ static constexpr int plane_of(int i)
+    {
+        constexpr int v[37] = {0,  1,  2,  7,  14, 8,  15, 16, 9,  3,  4,  21, 26,
+                               10, 17, 18, 11, 22, 27, 28, 23, 24, 29, 30, 25, 5,
+                               6,  31, 34, 12, 19, 20, 13, 32, 35, 36, 33};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int gcy(int g)
+    {
+        constexpr int v[7] = {0, 1, -1, 2, -2, 3, -3};
+        return v[g];
+    }
+    __host__ __device__ static constexpr int gstart(int g)
+    {
+        constexpr int v[7] = {0, 7, 14, 21, 26, 31, 34};
+        return v[g];
+    }
+    __host__ __device__ static constexpr int gcount(int g)
+    {
+        constexpr int v[7] = {7, 7, 7, 5, 5, 3, 3};
+        return v[g];
+    }
 };
+
+// Group of velocity i (its plane lies in [gstart, gstart + gcount)).
+template <int LAT>
+__host__ __device__ constexpr int group_of(int i)
+{
+    int g = 0;
+    while (!(Lat<LAT>::plane_of(i) >= Lat<LAT>::gstart(g) &&
+             Lat<LAT>::plane_of(i) < Lat<LAT>::gstart(g) + Lat<LAT>::gcount(g)))
+        ++g;
+    return g;
+}
 
 // ---------------------------------------------------------------------------
 // Storage traits.  Populations are stored shifted, g = f - w rho0.  F16 keeps
@@ -342,8 +401,11 @@ int launch_init(int lat, int storage, const Geom& G, const Export& E, const Band
 // Fixed inflow equilibrium at the listed nodes of one population buffer.
 int launch_inflow(int lat, int storage, const Geom& G, const int* nodes, int n, const double Uin[4],
                   void* f, cudaStream_t st);
+// One bulk step fin -> fout; tmaps[0..2] describe fin for the tensor copies
+// (box depths 7, 5, 3 planes); *status gets bit 1 if a copy never completed.
 int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
-                const void* fin, void* fout, int par_new, cudaStream_t st);
+                const CUtensorMap* tmaps, const void* fin, void* fout, int par_new, int* status,
+                cudaStream_t st);
 int launch_macros(int lat, int storage, const Geom& G, const void* f, double* rho, double* ux,
                   double* uy, double* T, int* flag, cudaStream_t st);
 int launch_boundary(int lat, int storage, const Geom& G, const Export& E, const Band& B,
