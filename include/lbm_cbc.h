@@ -25,7 +25,11 @@
  *    duration of that call.
  *  - Work is issued on the handle's CUDA stream (default: the legacy default
  *    stream; see lbm_set_stream()).  lbm_step() is asynchronous; the calls
- *    that return data to the caller synchronise the stream.
+ *    that return data to the caller synchronise the stream.  Each handle
+ *    also owns one internal stream of the highest priority: lbm_step() forks
+ *    onto it from the handle's stream and joins back before returning
+ *    control of the step, so work issued afterwards on the handle's stream
+ *    sees the whole step (and the fork/join is legal under stream capture).
  *  - A handle must not be used from two threads at once.
  */
 #ifndef LBM_CBC_H
@@ -121,13 +125,36 @@ int lbm_set_stream(lbm_handle* h, void* stream);
 int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
                     const double* uy, const double* T, int on_device);
 
-/* Advance n time steps (asynchronous on the handle's stream). */
+/* Advance n time steps (asynchronous on the handle's stream).  Per step, the
+ * bulk nodes within max(M, 3) of a non-periodic side (the rim: their pulls
+ * reach boundary nodes and they feed the boundary solver) are updated first;
+ * then the boundary phase runs on the internal stream while the other bulk
+ * nodes (the interior) are updated on the handle's stream.  The result is
+ * identical to phase 0 followed by phase 1. */
 int lbm_step(lbm_handle* h, int n);
 
-/* Issue one phase of one step: 0 = bulk stream-collide, 1 = boundary
- * conditions (ends the step).  Used to time the phases separately; a step
- * is phase 0 then phase 1. */
+/* Issue one phase of one step on the handle's stream, without overlap:
+ * 0 = bulk stream-collide (rim, then interior), 1 = boundary conditions
+ * (ends the step).  Used to time the phases separately; a step is phase 0
+ * then phase 1. */
 int lbm_step_phase(lbm_handle* h, int phase);
+
+/* Timing hook: record the caller's CUDA events (cudaEvent_t, created by the
+ * caller with timing enabled) around the launches of every following
+ * lbm_step() / lbm_step_phase() call, so that the dominant kernel can be
+ * timed while the boundary phase runs beside it.  n = 0 turns the hook off;
+ * n = 2 or 5:
+ *   events[0], events[1]  before / after the interior bulk launch (handle's
+ *                         stream);
+ *   events[2]             before the rim launch (handle's stream);
+ *   events[3]             before the boundary phase;
+ *   events[4]             after the boundary phase;
+ * events[3..4] are recorded on the internal stream in lbm_step() and on the
+ * handle's stream in lbm_step_phase().  The events stay owned by the
+ * caller, who must keep them alive while the hook is set; with several steps
+ * per call only the last step's records remain.  A NULL entry among the
+ * first n is LBM_ERR_ARG. */
+int lbm_set_kernel_events(lbm_handle* h, void* const* events, int n);
 
 /* Macroscopic fields of the current populations (Eq. macro): absolute rho,
  * ux, uy and T ([ny][nx] doubles; T = 1 for D2Q9).  Device or host arrays as

@@ -25,7 +25,8 @@ from . import build as _build
 __all__ = [
     "LbmCbcParams", "LBM_D2Q9", "LBM_D2Q37", "LBM_F64", "LBM_F32", "LBM_F16",
     "lbm_params_default", "lbm_workspace_bytes", "lbm_create", "lbm_create_in",
-    "lbm_set_stream", "lbm_init_fields", "lbm_step", "lbm_step_phase", "lbm_get_macros",
+    "lbm_set_stream", "lbm_init_fields", "lbm_step", "lbm_step_phase", "lbm_set_kernel_events",
+    "lbm_get_macros",
     "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_steps_done",
     "lbm_last_error", "lbm_destroy", "lbm_cbc_side_step_noalloc", "Simulation",
     "params_from_run", "LbmError",
@@ -82,6 +83,7 @@ def lib():
             "lbm_init_fields": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
             "lbm_step": (C.c_int, [vp, C.c_int]),
             "lbm_step_phase": (C.c_int, [vp, C.c_int]),
+            "lbm_set_kernel_events": (C.c_int, [vp, C.POINTER(C.c_void_p), C.c_int]),
             "lbm_get_macros": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
             "lbm_state_bytes": (C.c_int, [vp, C.POINTER(sz)]),
             "lbm_get_state": (C.c_int, [vp, vp, sz]),
@@ -194,6 +196,15 @@ def lbm_step(h, n):
 
 def lbm_step_phase(h, phase):
     _check(lib().lbm_step_phase(h, int(phase)), h)
+
+
+def lbm_set_kernel_events(h, events):
+    """Timing hook: a sequence of 0, 2 or 5 raw cudaEvent_t handles (ints,
+    e.g. torch.cuda.Event.cuda_event of recorded events); see
+    include/lbm_cbc.h for where each is recorded."""
+    events = list(events or [])
+    arr = (C.c_void_p * max(1, len(events)))(*[C.c_void_p(int(e)) for e in events])
+    _check(lib().lbm_set_kernel_events(h, arr, len(events)), h)
 
 
 def lbm_get_macros(h, rho, ux, uy, T, on_device):

@@ -5,6 +5,7 @@
 // near-boundary strips exported by the bulk kernel, the boundary ODE state
 // and RK4 stage buffers, a macro buffer and a status flag.  Every launch goes
 // to the handle's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -41,6 +42,11 @@ struct lbm_handle {
     size_t ws_bytes = 0;
     bool owns_ws = false;
     cudaStream_t stream = nullptr;
+    Region interior{};       // bulk nodes independent of the boundary phase
+    Rim rim{};               // the other bulk nodes
+    cudaStream_t aux = nullptr;              // high-priority stream: rim + boundary
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t kev[5] = {};  // caller's timing events (see lbm_set_kernel_events)
     long long steps = 0;
     bool initialized = false;
     bool bulk_pending = false;   // phase 0 issued, phase 1 not yet
@@ -60,6 +66,8 @@ struct Plan {
     Band B{};
     int Q = 0;
     size_t esize = 0, f_bytes = 0, stripU_n = 0, stripN_n = 0;
+    Region interior{};
+    Rim rim{};
     std::vector<UDesc> ud;
     std::vector<int2> zg;
     std::vector<int> inflow;
@@ -146,6 +154,42 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     G.by0 = pery ? 0 : M;
     G.by1 = pery ? ny : ny - M;
     G.plane = (long long)ny * G.nxp;
+
+    // Interior / rim split.  A rim of width max(M, 3) along each
+    // non-periodic side holds every bulk node whose pull reaches a boundary
+    // node (distance <= M) and every node the strip export writes (depths
+    // 0..2); the interior reads and writes nothing the boundary phase
+    // touches.
+    {
+        const int R = std::max(M, 3);
+        Region in{G.bx0 + (perx ? 0 : R), G.bx1 - (perx ? 0 : R), G.by0 + (pery ? 0 : R),
+                  G.by1 - (pery ? 0 : R)};
+        Rim& rm = pl.rim;
+        rm = Rim{};
+        auto add = [&](int x0, int x1, int y0, int y1) {
+            if (x1 <= x0 || y1 <= y0) return;
+            rm.r[rm.n] = Region{x0, x1, y0, y1};
+            rm.start[rm.n] = rm.total;
+            rm.total += (x1 - x0) * (y1 - y0);
+            rm.n++;
+        };
+        if (perx && pery) {
+            pl.interior = in;
+        } else if (in.x1 <= in.x0 || in.y1 <= in.y0) {
+            pl.interior = Region{0, 0, 0, 0};       // too small to split: all rim
+            add(G.bx0, G.bx1, G.by0, G.by1);
+        } else {
+            pl.interior = in;
+            if (!perx) {
+                add(G.bx0, in.x0, G.by0, G.by1);
+                add(in.x1, G.bx1, G.by0, G.by1);
+            }
+            if (!pery) {
+                add(in.x0, in.x1, G.by0, in.y0);
+                add(in.x0, in.x1, in.y1, G.by1);
+            }
+        }
+    }
     G.tau = tau;
     G.rho0 = p->rho0;
     G.omega = 1.0 / tau;
@@ -187,22 +231,28 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
             corner_kind = SIDE_INFLOW;
         else corner_kind = SIDE_ZG;
     }
-    // unknown index of side s, layer j, position pp (pp already in range)
-    int base[4] = {0, 0, 0, 0}, n_side = 0;
+    // unknown index of side s, layer j, position pp (pp already in range):
+    // layer-major, so that the threads of a warp share j (one stencil
+    // branch, neighbours of one kind) and the RK4 stages do not diverge
+    int base[4] = {0, 0, 0, 0}, npos[4] = {0, 0, 0, 0}, n_side = 0;
     for (int s = 0; s < 4; ++s)
-        if (E.cbc[s]) { base[s] = n_side; n_side += (hi[s] - lo[s] + 1) * M; }
+        if (E.cbc[s]) {
+            base[s] = n_side;
+            npos[s] = hi[s] - lo[s] + 1;
+            n_side += npos[s] * M;
+        }
     const int lo_corner[4] = {0, 1, 0, 2}, hi_corner[4] = {2, 3, 1, 3};
     auto ref = [&](int s, int j, int pp) -> int {
         if (tper[s]) pp = ((pp % L[s]) + L[s]) % L[s];
         if (j <= 0) return -(slot(s, -j, pp) + 1);
         if (pp < lo[s]) return n_side + lo_corner[s];
         if (pp > hi[s]) return n_side + hi_corner[s];
-        return base[s] + (pp - lo[s]) * M + (j - 1);
+        return base[s] + (j - 1) * npos[s] + (pp - lo[s]);
     };
     for (int s = 0; s < 4; ++s) {
         if (!E.cbc[s]) continue;
-        for (int pp = lo[s]; pp <= hi[s]; ++pp)
-            for (int j = 1; j <= M; ++j) {
+        for (int j = 1; j <= M; ++j)
+            for (int pp = lo[s]; pp <= hi[s]; ++pp) {
                 UDesc D;
                 std::memset(&D, 0, sizeof D);
                 D.kind = s;
@@ -395,6 +445,8 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     h->O = pl.O;
     h->E = pl.E;
     h->B = pl.B;
+    h->interior = pl.interior;
+    h->rim = pl.rim;
     h->esize = pl.esize;
     h->f_bytes = pl.f_bytes;
     h->ws = ws;
@@ -423,9 +475,17 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
             const int rc = encode_population_map(h, h->f[b], depths[k] <= h->Q ? depths[k] : 1, &h->tmap[b][k]);
             if (rc != LBM_OK) return rc;
         }
+    // The rim and the boundary phase run on a stream of the highest
+    // priority so that their few CTAs are scheduled ahead of the interior's.
+    int prio_lo = 0, prio_hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream set-up");
     // Zero the strips (positions no kernel writes stay finite) and the
     // status words, and upload the boundary tables.
-    cudaError_t e = cudaMemsetAsync(h->E.stripU, 0, pl.stripU_n * 8, h->stream);
+    e = cudaMemsetAsync(h->E.stripU, 0, pl.stripU_n * 8, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, 2 * sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->E.stripN, 0, pl.stripN_n * 8, h->stream);
     if (e == cudaSuccess && !pl.ud.empty())
@@ -440,6 +500,65 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "workspace set-up");
     return LBM_OK;
+}
+
+int mark(lbm_handle* h, int k, cudaStream_t st)
+{
+    if (!h->kev[k]) return LBM_OK;
+    const cudaError_t e = cudaEventRecord(h->kev[k], st);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "timing event");
+}
+
+// Interior bulk update of step (parity par) on stream st, bracketed by the
+// caller's timing events when set.
+int interior(lbm_handle* h, int par, cudaStream_t st)
+{
+    int rc = mark(h, 0, st);
+    if (rc != LBM_OK) return rc;
+    rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->E, h->interior, h->tmap[par], h->f[par],
+                     h->f[par ^ 1], par ^ 1, h->flag + 1, st);
+    if (rc) return check_launch(h, rc, "bulk kernel");
+    return mark(h, 1, st);
+}
+
+// Rim bulk update of step (parity par) on stream st, after timing mark 2.
+int rim(lbm_handle* h, int par, cudaStream_t st)
+{
+    int rc = mark(h, 2, st);
+    if (rc != LBM_OK) return rc;
+    rc = launch_rim(h->lattice, h->storage, h->G, h->O, h->E, h->rim, h->f[par], h->f[par ^ 1],
+                    par ^ 1, st);
+    return rc ? check_launch(h, rc, "rim kernel") : LBM_OK;
+}
+
+// Inflow equilibrium (once per buffer) and the characteristic boundary
+// solver of step (parity par) on stream st.
+int boundary_phase(lbm_handle* h, int par, cudaStream_t st)
+{
+    int rc = mark(h, 3, st);
+    if (rc != LBM_OK) return rc;
+    // Inflow nodes carry a fixed equilibrium, imposed after streaming like
+    // every boundary condition; each buffer gets it once, the first time a
+    // step writes that buffer.
+    if (h->n_inflow > 0 && !h->inflow_done[par ^ 1]) {
+        rc = launch_inflow(h->lattice, h->storage, h->G, h->inflow_nodes, h->n_inflow, h->Uin,
+                           h->f[par ^ 1], st);
+        if (rc) return check_launch(h, rc, "inflow kernel");
+        h->inflow_done[par ^ 1] = true;
+    }
+    rc = launch_boundary(h->lattice, h->storage, h->G, h->E, h->B, h->f[par ^ 1], par, st);
+    if (rc) return check_launch(h, rc, "boundary kernels");
+    return mark(h, 4, st);
+}
+
+void release_streams(lbm_handle* h)
+{
+    if (h->aux) cudaStreamSynchronize(h->aux);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    h->aux = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
 }
 
 int create_common(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, void* ws,
@@ -477,6 +596,7 @@ int create_common(int lattice, int nx, int ny, double tau, const lbm_cbc_params*
     rc = setup(h, lattice, nx, ny, tau, p, pl, ws, ws_bytes, owns);
     if (rc != LBM_OK) {
         fprintf(stderr, "lbm_create: %s\n", h->err.c_str());
+        release_streams(h);
         if (owns) cudaFree(ws);
         delete h;
         return rc;
@@ -582,26 +702,16 @@ int lbm_step_phase(lbm_handle* h, int phase)
     const int par = int(h->steps & 1);
     if (phase == 0) {
         if (h->bulk_pending) { h->err = "bulk phase issued twice"; return LBM_ERR_STATE; }
-        const int rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->E, h->tmap[par], h->f[par],
-                                   h->f[par ^ 1], par ^ 1, h->flag + 1, h->stream);
-        if (rc) return check_launch(h, rc, "bulk kernel");
+        int rc = rim(h, par, h->stream);
+        if (rc == LBM_OK) rc = interior(h, par, h->stream);
+        if (rc != LBM_OK) return rc;
         h->bulk_pending = true;
         return LBM_OK;
     }
     if (phase == 1) {
         if (!h->bulk_pending) { h->err = "boundary phase before bulk phase"; return LBM_ERR_STATE; }
-        // Inflow nodes carry a fixed equilibrium, imposed after streaming
-        // like every boundary condition; each buffer gets it once, the first
-        // time a step writes that buffer.
-        if (h->n_inflow > 0 && !h->inflow_done[par ^ 1]) {
-            const int rc = launch_inflow(h->lattice, h->storage, h->G, h->inflow_nodes, h->n_inflow,
-                                         h->Uin, h->f[par ^ 1], h->stream);
-            if (rc) return check_launch(h, rc, "inflow kernel");
-            h->inflow_done[par ^ 1] = true;
-        }
-        const int rc = launch_boundary(h->lattice, h->storage, h->G, h->E, h->B, h->f[par ^ 1], par,
-                                       h->stream);
-        if (rc) return check_launch(h, rc, "boundary kernels");
+        const int rc = boundary_phase(h, par, h->stream);
+        if (rc != LBM_OK) return rc;
         h->bulk_pending = false;
         h->steps++;
         return LBM_OK;
@@ -613,11 +723,51 @@ int lbm_step_phase(lbm_handle* h, int phase)
 int lbm_step(lbm_handle* h, int n)
 {
     if (!h || n < 0) return LBM_ERR_ARG;
-    for (int i = 0; i < n; ++i) {
-        int rc = lbm_step_phase(h, 0);
-        if (rc == LBM_OK) rc = lbm_step_phase(h, 1);
-        if (rc != LBM_OK) return rc;
+    if (!h->initialized) {
+        h->err = "lbm_step before lbm_init_fields";
+        return LBM_ERR_STATE;
     }
+    if (h->bulk_pending) { h->err = "lbm_step in the middle of a phased step"; return LBM_ERR_STATE; }
+    for (int i = 0; i < n; ++i) {
+        const int par = int(h->steps & 1);
+        if (h->rim.total == 0) {
+            // fully periodic: no boundary phase, one launch
+            const int rc = interior(h, par, h->stream);
+            if (rc != LBM_OK) return rc;
+            h->steps++;
+            continue;
+        }
+        // The rim first, alone (launched beside the interior, its few CTAs
+        // would queue behind the interior's); then fork: the boundary phase
+        // on the high-priority stream, the interior on the handle's stream,
+        // concurrently; join before the next step.
+        int rc = rim(h, par, h->stream);
+        if (rc != LBM_OK) return rc;
+        cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "fork");
+        rc = interior(h, par, h->stream);
+        if (rc != LBM_OK) return rc;
+        rc = boundary_phase(h, par, h->aux);
+        if (rc != LBM_OK) return rc;
+        e = cudaEventRecord(h->ev_join, h->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "join");
+        h->steps++;
+    }
+    return LBM_OK;
+}
+
+int lbm_set_kernel_events(lbm_handle* h, void* const* events, int n)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (!(n == 0 || n == 2 || n == 5) || (n > 0 && !events)) {
+        h->err = "lbm_set_kernel_events takes 0, 2 or 5 events";
+        return LBM_ERR_ARG;
+    }
+    for (int k = 0; k < n; ++k)
+        if (!events[k]) { h->err = "NULL event"; return LBM_ERR_ARG; }
+    for (int k = 0; k < 5; ++k) h->kev[k] = k < n ? static_cast<cudaEvent_t>(events[k]) : nullptr;
     return LBM_OK;
 }
 
@@ -741,6 +891,7 @@ void lbm_destroy(lbm_handle* h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    release_streams(h);
     if (h->owns_ws && h->ws) cudaFree(h->ws);
     delete h;
 }

@@ -1,10 +1,15 @@
 // bulk.cu -- bulk kernels of the thermal lattice Boltzmann step.
 //
-//  k_bulk     fused pull-stream + moments + BGK collide on every bulk node
-//             (Eqs. lbe, macro, bgk with the equilibria of Eqs. feq-3/feq-4),
-//             plus the export of macros and non-equilibrium moments on the
-//             three bulk columns/rows next to each characteristic side (used
-//             by the boundary solver of Sec. 3.3).
+//  k_bulk     fused pull-stream + moments + BGK collide on the interior
+//             bulk nodes (Eqs. lbe, macro, bgk with the equilibria of
+//             Eqs. feq-3/feq-4).
+//  k_rim      the same update on the rim: bands of width max(M, 3) next to
+//             the non-periodic sides, whose pulls reach nodes the boundary
+//             phase writes; it also exports the macros and non-equilibrium
+//             moments of the three bulk columns/rows next to each
+//             characteristic side (used by the boundary solver of
+//             Sec. 3.3).  The interior is independent of the boundary phase
+//             of the same step, so the two can run concurrently.
 //  k_init     f = f^eq(U0) on every node and the strips of time 0.
 //  k_inflow   the fixed inflow equilibrium on the inflow nodes of a buffer.
 //  k_init_band  boundary ODE state of time 0.
@@ -140,25 +145,12 @@ __device__ __forceinline__ void neq_moments(const C* g, const Moments<LAT, C>& m
 }
 
 // Strip export of one bulk node next to a characteristic side (a few
-// columns/rows of the grid).  It pulls the node's populations again (they
-// are in L2) so the main path never hands its registers to this call.
-template <int LAT, typename S>
-__device__ __noinline__ void export_node(const Geom& G, const Offsets& O, const Export& E,
-                                         const S* __restrict__ fin, int x, int y, int par_new)
+// columns/rows of the grid): macros and non-equilibrium moments of its
+// pulled (pre-collision) populations g with moments m.
+template <int LAT, typename C>
+__device__ __forceinline__ void export_from(const Geom& G, const Export& E, const C* g,
+                                            const Moments<LAT, C>& m, int x, int y, int par_new)
 {
-    using L = Lat<LAT>;
-    using C = typename Store<S>::C;
-    C g[L::Q];
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        int xs = x - L::cx(i), ys = y - L::cy(i);
-        if (G.perx) xs = xs < 0 ? xs + G.nx : (xs >= G.nx ? xs - G.nx : xs);
-        if (G.pery) ys = ys < 0 ? ys + G.ny : (ys >= G.ny ? ys - G.ny : ys);
-        C v = C(Store<S>::load(fin + (O.st[i] + ys * G.nxp + xs)));
-        if (Store<S>::SCALED) v *= C(L::w(i));
-        g[i] = v;
-    }
-    const Moments<LAT, C> m = moments<LAT, C>(g, rho0_of<C>(G));
     const int dd[4] = {x - G.M, G.nx - 1 - G.M - x, y - G.M, G.ny - 1 - G.M - y};
     double N[5];
     neq_moments<LAT, C>(g, m, 1.0 - 0.5 / G.tau, N);
@@ -217,53 +209,33 @@ __device__ __forceinline__ void gather_staged(C* g, const S* sb, int t,
      ...);
 }
 
-template <int LAT, typename S>
-__global__ void __launch_bounds__(kBulkThreads)
-    k_bulk(const __grid_constant__ Maps tm, Geom G, Offsets O, Export E,
-           const S* __restrict__ fin, S* __restrict__ fout, int par_new, int* status)
+// Plain pull of node (x, y) with periodic wrap-around of the sources.
+template <int LAT, typename S, typename C>
+__device__ __forceinline__ void pull_plain(const Geom& G, const Offsets& O,
+                                           const S* __restrict__ fin, int x, int y, C* g)
 {
     using L = Lat<LAT>;
-    using C = typename Store<S>::C;
-    using BX = Stage<LAT, S>;
-    constexpr int Q = L::Q;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long bar;
-    const int x0 = (G.bx0 / kBulkThreads + blockIdx.x) * kBulkThreads;   // tiles aligned to 128
-    const int x = x0 + threadIdx.x;
-    const int y = G.by0 + blockIdx.y;
-    const bool valid = x >= G.bx0 && x < G.bx1;
-    const int node = y * G.nxp + x;
-
-    // Pull stream (Eq. lbe): g_i(x) = g*_i(x - c_i).  Segments whose sources
-    // wrap around a periodic axis use plain loads; all others stage the 37
-    // shifted source rows through shared memory with tensor copies.
-    const bool wrap = (G.pery && (y < L::M || y >= G.ny - L::M)) ||
-                      (G.perx && (x0 - L::M < 0 || x0 + kBulkThreads + L::M > G.nx));
-    C g[Q];
-    if (!wrap) {
-        S* sb = reinterpret_cast<S*>(smem_raw);
-        if (threadIdx.x == 0) {
-            const unsigned b = smem_u32(&bar);
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         ::"r"(b), "r"(BX::TX) : "memory");
-            issue_copies<LAT, S>(tm, smem_raw, x0, y, b, std::make_integer_sequence<int, L::NG>{});
-        }
-        __syncthreads();
-        if (!wait_tx(&bar, status) || !valid) return;
-        gather_staged<LAT, S, C>(g, sb, threadIdx.x, std::make_integer_sequence<int, Q>{});
-    } else {
-        if (!valid) return;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            int xs = x - L::cx(i), ys = y - L::cy(i);
-            if (L::cx(i) && G.perx) xs = xs < 0 ? xs + G.nx : (xs >= G.nx ? xs - G.nx : xs);
-            if (L::cy(i) && G.pery) ys = ys < 0 ? ys + G.ny : (ys >= G.ny ? ys - G.ny : ys);
-            g[i] = C(Store<S>::load(fin + (O.st[i] + ys * G.nxp + xs)));
-        }
+    for (int i = 0; i < L::Q; ++i) {
+        int xs = x - L::cx(i), ys = y - L::cy(i);
+        if (L::cx(i) && G.perx) xs = xs < 0 ? xs + G.nx : (xs >= G.nx ? xs - G.nx : xs);
+        if (L::cy(i) && G.pery) ys = ys < 0 ? ys + G.ny : (ys >= G.ny ? ys - G.ny : ys);
+        g[i] = C(Store<S>::load(fin + (O.st[i] + ys * G.nxp + xs)));
     }
+}
+
+// Moments, BGK collision (Eq. bgk) and post-collision store of one node
+// whose pulled populations are in g, plus (EXPORT) the strip export next to
+// the characteristic sides.  Only rim nodes export: the interior lies at
+// least max(M, 3) >= 3 nodes inside every characteristic side.
+template <int LAT, typename S, typename C, bool EXPORT>
+__device__ __forceinline__ void collide_store(const Geom& G, const Offsets& O, const Export& E,
+                                              const S* __restrict__ fin, S* __restrict__ fout,
+                                              int x, int y, int par_new, C* g)
+{
+    using L = Lat<LAT>;
+    constexpr int Q = L::Q;
+    const int node = y * G.nxp + x;
     if (Store<S>::SCALED) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) g[i] *= C(L::w(i));
@@ -363,10 +335,80 @@ __global__ void __launch_bounds__(kBulkThreads)
         put(0, g[0] + om * (geq0 - g[0]));
     }
 
-    // Near-boundary export for the characteristic boundary solver.
+    // Strip export for the characteristic boundary solver.
     const bool near = (E.cbc[0] && x - G.M <= 2) || (E.cbc[1] && G.nx - 1 - G.M - x <= 2) ||
                       (E.cbc[2] && y - G.M <= 2) || (E.cbc[3] && G.ny - 1 - G.M - y <= 2);
-    if (near) export_node<LAT, S>(G, O, E, fin, x, y, par_new);
+    if (EXPORT && near) export_from<LAT, C>(G, E, g, m, x, y, par_new);
+}
+
+template <int LAT, typename S>
+__global__ void __launch_bounds__(kBulkThreads)
+    k_bulk(const __grid_constant__ Maps tm, Geom G, Offsets O, Export E, Region R,
+           const S* __restrict__ fin, S* __restrict__ fout, int par_new, int* status)
+{
+    using L = Lat<LAT>;
+    using C = typename Store<S>::C;
+    using BX = Stage<LAT, S>;
+    constexpr int Q = L::Q;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar;
+    const int x0 = (R.x0 / kBulkThreads + blockIdx.x) * kBulkThreads;   // tiles aligned to 128
+    const int x = x0 + threadIdx.x;
+    const int y = R.y0 + blockIdx.y;
+    const bool valid = x >= R.x0 && x < R.x1;
+
+    // Pull stream (Eq. lbe): g_i(x) = g*_i(x - c_i).  Segments whose sources
+    // wrap around a periodic axis use plain loads; all others stage the 37
+    // shifted source rows through shared memory with tensor copies.
+    const bool wrap = (G.pery && (y < L::M || y >= G.ny - L::M)) ||
+                      (G.perx && (x0 - L::M < 0 || x0 + kBulkThreads + L::M > G.nx));
+    C g[Q];
+    if (!wrap) {
+        S* sb = reinterpret_cast<S*>(smem_raw);
+        if (threadIdx.x == 0) {
+            const unsigned b = smem_u32(&bar);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         ::"r"(b), "r"(BX::TX) : "memory");
+            issue_copies<LAT, S>(tm, smem_raw, x0, y, b, std::make_integer_sequence<int, L::NG>{});
+        }
+        __syncthreads();
+        if (!wait_tx(&bar, status) || !valid) return;
+        gather_staged<LAT, S, C>(g, sb, threadIdx.x, std::make_integer_sequence<int, Q>{});
+    } else {
+        if (!valid) return;
+        pull_plain<LAT, S, C>(G, O, fin, x, y, g);
+    }
+    collide_store<LAT, S, C, false>(G, O, E, fin, fout, x, y, par_new, g);   // never near a side
+}
+
+// The rim bands: one thread per node, plain loads (the bands are a few
+// nodes wide, too narrow for row-segment staging).
+template <int LAT, typename S>
+__global__ void __launch_bounds__(kBulkThreads)
+    k_rim(Geom G, Offsets O, Export E, Rim RM, const S* __restrict__ fin, S* __restrict__ fout,
+          int par_new)
+{
+    using C = typename Store<S>::C;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= RM.total) return;
+    // band of node k, selected with constant indices (no local copy of RM)
+    int bx0 = RM.r[0].x0, bw = RM.r[0].x1 - RM.r[0].x0, by0 = RM.r[0].y0, b0 = 0;
+#pragma unroll
+    for (int j = 1; j < 4; ++j)
+        if (j < RM.n && k >= RM.start[j]) {
+            bx0 = RM.r[j].x0;
+            bw = RM.r[j].x1 - RM.r[j].x0;
+            by0 = RM.r[j].y0;
+            b0 = RM.start[j];
+        }
+    const int l = k - b0;
+    const int x = bx0 + l % bw, y = by0 + l / bw;
+    C g[Lat<LAT>::Q];
+    pull_plain<LAT, S, C>(G, O, fin, x, y, g);
+    collide_store<LAT, S, C, true>(G, O, E, fin, fout, x, y, par_new, g);
 }
 
 template <int LAT, typename S>
@@ -501,20 +543,32 @@ int inflow_t(const Geom& G, const int* nodes, int n, const double U[4], void* f,
 }
 
 template <int LAT, typename S>
-int bulk_t(const Geom& G, const Offsets& O, const Export& E, const CUtensorMap* tmaps,
-           const void* fin, void* fout, int par_new, int* status, cudaStream_t st)
+int bulk_t(const Geom& G, const Offsets& O, const Export& E, const Region& R,
+           const CUtensorMap* tmaps, const void* fin, void* fout, int par_new, int* status,
+           cudaStream_t st)
 {
-    const int h = G.by1 - G.by0;
-    if (G.bx1 <= G.bx0 || h <= 0) return 0;
-    const int t0 = G.bx0 / kBulkThreads, t1 = (G.bx1 + kBulkThreads - 1) / kBulkThreads;
+    const int h = R.y1 - R.y0;
+    if (R.x1 <= R.x0 || h <= 0) return 0;
+    const int t0 = R.x0 / kBulkThreads, t1 = (R.x1 + kBulkThreads - 1) / kBulkThreads;
     const size_t smem = Stage<LAT, S>::TOTAL;
     Maps tm;
     tm.m7 = tmaps[0];
     tm.m5 = tmaps[1];
     tm.m3 = tmaps[2];
     dim3 blk(kBulkThreads), grd(t1 - t0, h);
-    k_bulk<LAT, S><<<grd, blk, smem, st>>>(tm, G, O, E, static_cast<const S*>(fin),
+    k_bulk<LAT, S><<<grd, blk, smem, st>>>(tm, G, O, E, R, static_cast<const S*>(fin),
                                            static_cast<S*>(fout), par_new, status);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int LAT, typename S>
+int rim_t(const Geom& G, const Offsets& O, const Export& E, const Rim& RM, const void* fin,
+          void* fout, int par_new, cudaStream_t st)
+{
+    const int n = RM.total;
+    if (n <= 0) return 0;
+    k_rim<LAT, S><<<(n + kBulkThreads - 1) / kBulkThreads, kBulkThreads, 0, st>>>(
+        G, O, E, RM, static_cast<const S*>(fin), static_cast<S*>(fout), par_new);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -561,10 +615,18 @@ int launch_inflow(int lat, int storage, const Geom& G, const int* nodes, int n, 
 }
 
 int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
-                const CUtensorMap* tmaps, const void* fin, void* fout, int par_new, int* status,
-                cudaStream_t st)
+                const Region& R, const CUtensorMap* tmaps, const void* fin, void* fout,
+                int par_new, int* status, cudaStream_t st)
 {
-#define CALL(L, S) bulk_t<L, S>(G, O, E, tmaps, fin, fout, par_new, status, st)
+#define CALL(L, S) bulk_t<L, S>(G, O, E, R, tmaps, fin, fout, par_new, status, st)
+    LBM_DISPATCH(lat, storage, CALL);
+#undef CALL
+}
+
+int launch_rim(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
+               const Rim& RM, const void* fin, void* fout, int par_new, cudaStream_t st)
+{
+#define CALL(L, S) rim_t<L, S>(G, O, E, RM, fin, fout, par_new, st)
     LBM_DISPATCH(lat, storage, CALL);
 #undef CALL
 }

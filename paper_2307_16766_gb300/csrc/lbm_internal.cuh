@@ -329,6 +329,22 @@ struct Geom {
     float omega_f, rho0_f;
 };
 
+// A rectangle of bulk nodes [x0, x1) x [y0, y1).
+struct Region {
+    int x0, x1, y0, y1;
+};
+
+// The rim: bulk nodes whose pull stencil reaches a node the boundary phase
+// writes, or whose macros the boundary solver reads (the strip export).
+// Bands of width max(M, 3) along each non-periodic side, disjoint; start[b]
+// is the first node index of band b in a flat numbering of the n bands,
+// total the number of rim nodes.
+struct Rim {
+    int n, total;
+    Region r[4];
+    int start[4];
+};
+
 // Offsets (in elements) of the pull sources and of the output planes, used
 // by the bulk kernel away from periodic wrap-around: source of velocity i is
 // node + ld[i] = i * plane - c_iy * nxp - c_ix, its output is node + st[i].
@@ -401,11 +417,15 @@ int launch_init(int lat, int storage, const Geom& G, const Export& E, const Band
 // Fixed inflow equilibrium at the listed nodes of one population buffer.
 int launch_inflow(int lat, int storage, const Geom& G, const int* nodes, int n, const double Uin[4],
                   void* f, cudaStream_t st);
-// One bulk step fin -> fout; tmaps[0..2] describe fin for the tensor copies
-// (box depths 7, 5, 3 planes); *status gets bit 1 if a copy never completed.
+// One bulk step fin -> fout over the bulk nodes of region R; tmaps[0..2]
+// describe fin for the tensor copies (box depths 7, 5, 3 planes); *status
+// gets bit 1 if a copy never completed.
 int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
-                const CUtensorMap* tmaps, const void* fin, void* fout, int par_new, int* status,
-                cudaStream_t st);
+                const Region& R, const CUtensorMap* tmaps, const void* fin, void* fout,
+                int par_new, int* status, cudaStream_t st);
+// The same update on the rim bands (plain loads, one thread per node).
+int launch_rim(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
+               const Rim& RM, const void* fin, void* fout, int par_new, cudaStream_t st);
 int launch_macros(int lat, int storage, const Geom& G, const void* f, double* rho, double* ux,
                   double* uy, double* T, int* flag, cudaStream_t st);
 int launch_boundary(int lat, int storage, const Geom& G, const Export& E, const Band& B,

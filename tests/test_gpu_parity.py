@@ -289,3 +289,117 @@ def test_phase_order_is_enforced():
     sim.step_phase(1)
     assert sim.steps_done == 1
     sim.close()
+
+
+# ------------------------------------------- overlapped step schedule ---
+
+def _phased(cfg, fields, steps):
+    sim = lbm().Simulation(cfg).init_fields(*fields)
+    for _ in range(steps):
+        sim.step_phase(0)
+        sim.step_phase(1)
+    state = sim.get_state()
+    sim.close()
+    return state
+
+
+def _overlapped(cfg, fields, steps, chunks=(1, 4)):
+    sim = lbm().Simulation(cfg).init_fields(*fields)
+    done, k = 0, 0
+    while done < steps:
+        n = min(chunks[k % len(chunks)], steps - done)
+        sim.step(n)
+        done += n
+        k += 1
+    state = sim.get_state()
+    sim.close()
+    return state
+
+
+@pytest.mark.parametrize("case", [
+    "vortex_inflow_cbc_periodic_y", "d2q37_four_cbc_f32", "d2q37_cbc_y_periodic_x_f16",
+    "d2q9_four_cbc_f64", "d2q37_zg_x_periodic_y", "d2q37_interior_empty",
+    "d2q37_fully_periodic"])
+def test_overlapped_step_is_bit_identical_to_phased_step(case):
+    """lbm_step runs the rim and the boundary phase on a second stream
+    beside the interior; populations, strips and boundary state must equal
+    those of the sequential phase 0 / phase 1 order bit for bit."""
+    if case == "vortex_inflow_cbc_periodic_y":
+        cfg, f = W.vortex_d2q37(160, 48, Ma=0.3, steps=60, storage="f32", radius=8.0)
+    elif case == "d2q37_four_cbc_f32":
+        cfg, f = W.pulse_d2q37(70, alpha_T=0.5, steps=60, storage="f32", width=5.0, offset=3.0)
+    elif case == "d2q37_cbc_y_periodic_x_f16":
+        cfg = W.run("D2Q37", 64, 40, 0.8, sides=("periodic", "periodic", "cbc", "cbc"),
+                    schemes=("cbc_relax",) * 4, alpha_T=0.5, storage="f16")
+        f = W.gaussian_pulse(64, 40, 1e-3, 1e-3, 4.0)
+    elif case == "d2q9_four_cbc_f64":
+        cfg, f = W.pulse_d2q9(48, steps=60)
+    elif case == "d2q37_zg_x_periodic_y":
+        cfg = W.run("D2Q37", 50, 30, 0.8, sides=("zg", "zg", "periodic", "periodic"), storage="f32")
+        f = W.gaussian_pulse(50, 30, 1e-3, 1e-3, 4.0)
+    elif case == "d2q37_interior_empty":
+        cfg = W.run("D2Q37", 11, 12, 0.9, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4,
+                    alpha_T=0.5, storage="f64")
+        f = W.gaussian_pulse(11, 12, 1e-3, 1e-3, 2.0)
+    else:
+        cfg = W.run("D2Q37", 40, 24, 0.8, storage="f32")
+        f = W.gaussian_pulse(40, 24, 1e-3, 1e-3, 4.0)
+    a = _phased(cfg, f, 23)
+    b = _overlapped(cfg, f, 23)
+    assert a == b
+
+
+def test_kernel_events_time_the_interior_launch():
+    import torch
+    m = lbm()
+    cfg, f = W.vortex_d2q37(256, 64, Ma=0.1, steps=10, storage="f32", radius=8.0)
+    sim = m.Simulation(cfg).init_fields(*f)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    for e in ev:
+        e.record(sim.stream)       # creates the events
+    m.lbm_set_kernel_events(sim.handle, [e.cuda_event for e in ev])
+    sim.step(1)
+    torch.cuda.synchronize()
+    interior = ev[0].elapsed_time(ev[1])
+    rim, boundary = ev[2].elapsed_time(ev[3]), ev[3].elapsed_time(ev[4])
+    assert 0.0 < interior < 50.0 and 0.0 < rim < 50.0 and 0.0 < boundary < 50.0
+    sim.step_phase(0)
+    sim.step_phase(1)              # phased: all five on the solver's stream, in order
+    torch.cuda.synchronize()
+    # order on one stream: rim start (2), interior (0, 1), boundary (3, 4)
+    assert ev[2].elapsed_time(ev[0]) > 0.0 and ev[0].elapsed_time(ev[1]) > 0.0
+    assert ev[1].elapsed_time(ev[3]) >= 0.0 and ev[3].elapsed_time(ev[4]) > 0.0
+    m.lbm_set_kernel_events(sim.handle, [])
+    with pytest.raises(m.LbmError):
+        m.lbm_set_kernel_events(sim.handle, [ev[0].cuda_event])
+    sim.step(2)
+    sim.close()
+
+
+def test_step_replays_under_cuda_graph_capture():
+    """The fork/join of lbm_step is capturable: a graph of two steps,
+    replayed, reproduces eager stepping bit for bit."""
+    import torch
+    m = lbm()
+    cfg, f = W.vortex_d2q37(160, 48, Ma=0.3, steps=30, storage="f32", radius=8.0)
+    ref = m.Simulation(cfg).init_fields(*f)
+    ref.step(2 + 2 * 5)
+    want = ref.macros()
+    ref.close()
+
+    sim = m.Simulation(cfg).init_fields(*f)
+    sim.step(2)                    # both buffers get their inflow nodes eagerly
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        m.lbm_set_stream(sim.handle, s.cuda_stream)
+        m.lbm_step(sim.handle, 2)  # recorded only: the buffers do not advance
+    for _ in range(5):
+        g.replay()
+    torch.cuda.synchronize()
+    m.lbm_set_stream(sim.handle, torch.cuda.current_stream().cuda_stream)
+    got = sim.macros()             # host counter: 4 steps, parity matches 12
+    sim.close()
+    for x, y in zip(want, got):
+        assert np.array_equal(x, y)
