@@ -9,9 +9,9 @@ Prints one JSON line.  Timing: W untimed warm-up steps, then K steps, each
 bracketed by CUDA events on the solver's stream with an L2 flush (a write,
 then a read, of a 512 MB buffer) between timed steps; barrier + synchronize
 around the timed region; the max over ranks is reported.  A step is one
-lbm_step(1): the rim and the boundary phase on the solver's high-priority
-stream beside the interior bulk launch, whose duration (the roofline's
-kernel time) is taken with events the library records around it.  N > 1 runs independent
+lbm_step(1): the band kernel (strip nodes + characteristic boundary solver)
+beside the bulk kernel, whose duration (the roofline's kernel time) is
+taken with events the library records around it.  N > 1 runs independent
 replicas, one per GPU (weak scaling; the method has no cross-GPU exchange in
 this configuration).  The reference arm times the FP64 CPU oracle on this
 host on the same workload and metric.
@@ -168,12 +168,12 @@ def bulk_nodes(cfg):
 
 
 def interior_nodes(cfg):
-    """Nodes of the interior launch: the bulk minus a rim of width max(M, 3)
-    along every non-periodic side (the split lbm_step makes)."""
+    """Nodes of the bulk launch: the bulk minus the three strip columns/rows
+    next to every characteristic side (the band kernel updates those)."""
     per_x, per_y, M = _open_axes(cfg)
-    R = max(M, 3)
-    w = cfg["nx"] - (0 if per_x else 2 * (M + R))
-    h = cfg["ny"] - (0 if per_y else 2 * (M + R))
+    cbc = [k == "cbc" for k in cfg["sides"]]
+    w = cfg["nx"] - (0 if per_x else 2 * M) - 3 * (cbc[0] + cbc[1])
+    h = cfg["ny"] - (0 if per_y else 2 * M) - 3 * (cbc[2] + cbc[3])
     return max(w, 0) * max(h, 0)
 
 
@@ -198,8 +198,8 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
 
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
-    # per step: interior before/after (main stream), rim start, boundary
-    # start, boundary end (the solver's high-priority stream)
+    # per step: bulk before/after (the solver's internal stream), step start,
+    # band before/after (the solver's stream)
     kev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
     with torch.cuda.stream(stream):
         for evs in kev:                # events exist once recorded
@@ -231,7 +231,6 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
     lbm.lbm_set_kernel_events(sim.handle, [])
     step_ms = np.array([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)])
     interior_ms = np.array([kev[k][0].elapsed_time(kev[k][1]) for k in range(K)])
-    rim_ms = np.array([kev[k][2].elapsed_time(kev[k][3]) for k in range(K)])
     chain_ms = np.array([kev[k][3].elapsed_time(kev[k][4]) for k in range(K)])
 
     # Breakdown, not part of the headline: the same steps with the phases in
@@ -254,7 +253,7 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
     finite = bool(np.all(np.isfinite(rho)) and np.all(np.isfinite(ux)))
 
     res = {"step_ms_total": float(step_ms.sum()), "interior_ms_mean": float(interior_ms.mean()),
-           "rim_ms_mean": float(rim_ms.mean()), "boundary_overlapped_ms_mean": float(chain_ms.mean()),
+           "boundary_overlapped_ms_mean": float(chain_ms.mean()),
            "bulk_ms_mean": float(bulk_ms.mean()), "boundary_ms_mean": float(bnd_ms.mean()),
            "wall_s": wall, "clocks": clocks, "finite": finite, "cfg": cfg,
            "bulk_nodes": bulk_nodes(cfg), "interior_nodes": interior_nodes(cfg)}
@@ -360,12 +359,12 @@ def main():
     if rank == 0:
         peak, peak_kind = measured_peaks()
         Q, b = 37, BYTES_PER_VALUE[args.storage]
-        # dominant kernel: the interior k_bulk launch, timed live on its own
-        # stream while the boundary phase runs beside it
+        # dominant kernel: the k_bulk launch, timed live on its own stream
+        # while the band kernel runs beside it
         alg_bytes = 2 * Q * b * res["interior_nodes"]
         achieved = alg_bytes / (res["interior_ms_mean"] / 1e3) / 1e9
         traffic = bulk_traffic(args.storage, res["interior_nodes"])
-        launches_per_step = 2 + 4        # rim, interior, 4 RK4 stages (inflow written once per buffer)
+        launches_per_step = 2            # bulk and band (inflow written once per buffer; no ZG sides)
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": res["step_ms_total"] / K,
@@ -374,10 +373,9 @@ def main():
             "data": "synthetic", "config": workload_config(res["cfg"]),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_bulk interior (stream+collide)", "peak_kind": peak_kind,
+                         "kernel": "k_bulk (stream+collide)", "peak_kind": peak_kind,
                          "bytes_per_launch": alg_bytes, "kernel_ms": res["interior_ms_mean"],
-                         "rim_ms": res["rim_ms_mean"],
-                         "boundary_overlapped_ms": res["boundary_overlapped_ms_mean"],
+                         "band_overlapped_ms": res["boundary_overlapped_ms_mean"],
                          "phased_bulk_ms": res["bulk_ms_mean"],
                          "phased_boundary_ms": res["boundary_ms_mean"]},
             "e2e": res.get("e2e"),

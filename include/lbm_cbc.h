@@ -125,18 +125,19 @@ int lbm_set_stream(lbm_handle* h, void* stream);
 int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
                     const double* uy, const double* T, int on_device);
 
-/* Advance n time steps (asynchronous on the handle's stream).  Per step, the
- * bulk nodes within max(M, 3) of a non-periodic side (the rim: their pulls
- * reach boundary nodes and they feed the boundary solver) are updated first;
- * then the boundary phase runs on the internal stream while the other bulk
- * nodes (the interior) are updated on the handle's stream.  The result is
- * identical to phase 0 followed by phase 1. */
+/* Advance n time steps (asynchronous on the handle's stream).  Per step, one
+ * band kernel on the handle's stream updates the three bulk columns/rows
+ * next to each characteristic side and runs the boundary solver, while the
+ * bulk kernel (every other bulk node) and the zero-gradient copies run on
+ * the internal stream.  The result is identical to phase 0 followed by
+ * phase 1. */
 int lbm_step(lbm_handle* h, int n);
 
 /* Issue one phase of one step on the handle's stream, without overlap:
- * 0 = bulk stream-collide (rim, then interior), 1 = boundary conditions
- * (ends the step).  Used to time the phases separately; a step is phase 0
- * then phase 1. */
+ * 0 = bulk stream-collide (all but the strip nodes next to characteristic
+ * sides), 1 = boundary conditions (band kernel, zero-gradient copies; ends
+ * the step).  Used to time the phases separately; a step is phase 0 then
+ * phase 1. */
 int lbm_step_phase(lbm_handle* h, int phase);
 
 /* Timing hook: record the caller's CUDA events (cudaEvent_t, created by the
@@ -144,13 +145,12 @@ int lbm_step_phase(lbm_handle* h, int phase);
  * lbm_step() / lbm_step_phase() call, so that the dominant kernel can be
  * timed while the boundary phase runs beside it.  n = 0 turns the hook off;
  * n = 2 or 5:
- *   events[0], events[1]  before / after the interior bulk launch (handle's
- *                         stream);
- *   events[2]             before the rim launch (handle's stream);
- *   events[3]             before the boundary phase;
- *   events[4]             after the boundary phase;
- * events[3..4] are recorded on the internal stream in lbm_step() and on the
- * handle's stream in lbm_step_phase().  The events stay owned by the
+ *   events[0], events[1]  before / after the bulk launch;
+ *   events[2]             at the start of the step;
+ *   events[3], events[4]  before / after the band launch (with the inflow
+ *                         write of the first steps);
+ * all on the handle's stream except events[0..1] in lbm_step(), which go
+ * on the internal stream with the bulk launch.  The events stay owned by the
  * caller, who must keep them alive while the hook is set; with several steps
  * per call only the last step's records remain.  A NULL entry among the
  * first n is LBM_ERR_ARG. */

@@ -12,6 +12,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -42,9 +44,9 @@ struct lbm_handle {
     size_t ws_bytes = 0;
     bool owns_ws = false;
     cudaStream_t stream = nullptr;
-    Region interior{};       // bulk nodes independent of the boundary phase
-    Rim rim{};               // the other bulk nodes
-    cudaStream_t aux = nullptr;              // high-priority stream: rim + boundary
+    Region bulk{};           // nodes of the bulk kernel: all but the CBC strip nodes
+    size_t band_pad = 0;     // extra shared memory per band CTA (SM reservation)
+    cudaStream_t aux = nullptr;              // internal stream: the bulk beside the band
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t kev[5] = {};  // caller's timing events (see lbm_set_kernel_events)
     long long steps = 0;
@@ -66,15 +68,18 @@ struct Plan {
     Band B{};
     int Q = 0;
     size_t esize = 0, f_bytes = 0, stripU_n = 0, stripN_n = 0;
-    Region interior{};
-    Rim rim{};
+    Region bulk{};
+    std::vector<StripNode> sn;   // strip nodes of the tiles
+    std::vector<int> sbeg;
     std::vector<UDesc> ud;
+    std::vector<UDesc> ld;       // tile tables of the fused band kernel
+    std::vector<int> tbeg;
     std::vector<int2> zg;
     std::vector<int> inflow;
     double Uin[4] = {0, 0, 0, 0};
-    size_t off_f0 = 0, off_f1 = 0, off_sU = 0, off_sN = 0, off_Ub = 0, off_Ya = 0, off_Yb = 0,
-           off_acc = 0, off_V = 0, off_mask = 0, off_ud = 0, off_zg = 0, off_in = 0, off_macro = 0,
-           off_flag = 0, total = 0;
+    size_t off_f0 = 0, off_f1 = 0, off_sU = 0, off_sN = 0, off_Ub = 0, off_ud = 0, off_ld = 0,
+           off_tb = 0, off_sn = 0, off_sb = 0, off_zg = 0, off_in = 0, off_macro = 0, off_flag = 0,
+           total = 0;
 };
 
 std::string fmt(const char* f, ...)
@@ -155,40 +160,16 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     G.by1 = pery ? ny : ny - M;
     G.plane = (long long)ny * G.nxp;
 
-    // Interior / rim split.  A rim of width max(M, 3) along each
-    // non-periodic side holds every bulk node whose pull reaches a boundary
-    // node (distance <= M) and every node the strip export writes (depths
-    // 0..2); the interior reads and writes nothing the boundary phase
-    // touches.
+    // The bulk kernel updates every bulk node except the three columns/rows
+    // next to each characteristic side (the strip nodes), which the band
+    // kernel of the same step updates itself; so the two touch disjoint
+    // nodes and run concurrently.
     {
-        const int R = std::max(M, 3);
-        Region in{G.bx0 + (perx ? 0 : R), G.bx1 - (perx ? 0 : R), G.by0 + (pery ? 0 : R),
-                  G.by1 - (pery ? 0 : R)};
-        Rim& rm = pl.rim;
-        rm = Rim{};
-        auto add = [&](int x0, int x1, int y0, int y1) {
-            if (x1 <= x0 || y1 <= y0) return;
-            rm.r[rm.n] = Region{x0, x1, y0, y1};
-            rm.start[rm.n] = rm.total;
-            rm.total += (x1 - x0) * (y1 - y0);
-            rm.n++;
-        };
-        if (perx && pery) {
-            pl.interior = in;
-        } else if (in.x1 <= in.x0 || in.y1 <= in.y0) {
-            pl.interior = Region{0, 0, 0, 0};       // too small to split: all rim
-            add(G.bx0, G.bx1, G.by0, G.by1);
-        } else {
-            pl.interior = in;
-            if (!perx) {
-                add(G.bx0, in.x0, G.by0, G.by1);
-                add(in.x1, G.bx1, G.by0, G.by1);
-            }
-            if (!pery) {
-                add(in.x0, in.x1, G.by0, in.y0);
-                add(in.x0, in.x1, in.y1, G.by1);
-            }
-        }
+        const int cW = p->side[0] == LBM_SIDE_CBC, cE = p->side[1] == LBM_SIDE_CBC;
+        const int cS = p->side[2] == LBM_SIDE_CBC, cN = p->side[3] == LBM_SIDE_CBC;
+        pl.bulk = Region{G.bx0 + 3 * cW, G.bx1 - 3 * cE, G.by0 + 3 * cS, G.by1 - 3 * cN};
+        if (pl.bulk.x1 < pl.bulk.x0) pl.bulk.x1 = pl.bulk.x0;
+        if (pl.bulk.y1 < pl.bulk.y0) pl.bulk.y1 = pl.bulk.y0;
     }
     G.tau = tau;
     G.rho0 = p->rho0;
@@ -320,6 +301,141 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
         }
     B.n_unk = int(pl.ud.size());
     B.n_zg = int(pl.zg.size());
+
+    // Tiles of the fused band kernel: runs of P positions of one
+    // characteristic side with all M layers owned (each corner owned by the
+    // W/E tile next to it), closed over the neighbours the RK4 stages read:
+    // level l + 1 holds the unknowns level l reads that are not yet in the
+    // tile, up to level 4 (U(t) only).
+    {
+        const int P = kTileUnknowns / M - 8;
+        auto used_refs = [&](const UDesc& D, int* r) {
+            int n = 0;
+            if (D.kind >= 4) return 0;                  // corners read strips only
+            r[n++] = D.j < M ? D.nb[0] : D.nb[2];       // normal stencil
+            r[n++] = D.nb[1];
+            r[n++] = D.nb[4];                           // tangential stencil
+            r[n++] = D.nb[5];
+            if (p->viscous == LBM_VISCOUS_FD) {
+                if (D.j == M) r[n++] = D.nb[3];
+                else r[n++] = D.nb[0];
+            }
+            return n;
+        };
+        std::vector<int> g2l(pl.ud.size(), -1);
+        std::unordered_set<int> owned_node;     // strip nodes whose populations a tile writes
+        // grid node of strip slot sl: side s, depth d, position pp
+        auto slot_side = [&](int sl) {
+            int s = 0;
+            while (!(E.cbc[s] && sl >= E.offS[s] && sl < E.offS[s] + 3 * L[s])) ++s;
+            return s;
+        };
+        auto slot_x = [&](int sl) {
+            const int s = slot_side(sl), d = (sl - E.offS[s]) / L[s], pp = (sl - E.offS[s]) % L[s];
+            int x, y;
+            side_xf(s, pp, nx, ny, M, x, y);
+            return x - d * kSN[s][0];
+        };
+        auto slot_y = [&](int sl) {
+            const int s = slot_side(sl), d = (sl - E.offS[s]) / L[s], pp = (sl - E.offS[s]) % L[s];
+            int x, y;
+            side_xf(s, pp, nx, ny, M, x, y);
+            return y - d * kSN[s][1];
+        };
+        B.max_nodes = 0;
+        B.max_fx = 0;
+        for (int s = 0; s < 4; ++s) {
+            if (!E.cbc[s]) continue;
+            for (int a = lo[s]; a <= hi[s]; a += P) {
+                const int b = std::min(a + P - 1, hi[s]);
+                std::vector<int> list, level;
+                auto add = [&](int g, int lev) {
+                    if (g2l[g] >= 0) return;
+                    g2l[g] = int(list.size());
+                    list.push_back(g);
+                    level.push_back(lev);
+                };
+                for (int j = 1; j <= M; ++j)
+                    for (int pp = a; pp <= b; ++pp) add(ref(s, j, pp), 0);
+                if (corner_kind == SIDE_CBC && s < 2)
+                    for (int c = s; c < 4; c += 2)           // corners on this W/E side
+                        if ((c < 2 && a == lo[s]) || (c >= 2 && b == hi[s])) add(n_side + c, 0);
+                size_t f0 = 0;
+                for (int lev = 0; lev < 4; ++lev) {
+                    const size_t f1 = list.size();
+                    for (size_t q = f0; q < f1; ++q) {
+                        int r[6];
+                        const int nr = used_refs(pl.ud[list[q]], r);
+                        for (int k = 0; k < nr; ++k)
+                            if (r[k] >= 0) add(r[k], lev + 1);
+                    }
+                    f0 = f1;
+                }
+                if ((int)list.size() > kTileUnknowns) {
+                    err = fmt("internal: boundary tile of %zu unknowns", list.size());
+                    return LBM_ERR_ARG;
+                }
+                // strip nodes the tile reads or owns; node key = grid offset
+                std::vector<StripNode> nodes;
+                std::unordered_map<int, int> n2l, fxl;
+                auto node_of = [&](int sl) {
+                    const int x = slot_x(sl), y = slot_y(sl), key = goff(x, y);
+                    auto it = n2l.find(key);
+                    if (it != n2l.end()) return it->second;
+                    n2l[key] = int(nodes.size());
+                    nodes.push_back(StripNode{x, y, 0, -1, sl, -1});
+                    return int(nodes.size()) - 1;
+                };
+                for (int d = 0; d < 3; ++d)
+                    for (int pp = a; pp <= b; ++pp) {
+                        const int sl = slot(s, d, pp);
+                        StripNode& N = nodes[node_of(sl)];
+                        N.gslot = sl;
+                        const int key = goff(N.x, N.y);
+                        if (!owned_node.count(key)) { owned_node.insert(key); N.own = 1; }
+                    }
+                pl.tbeg.push_back(int(pl.ld.size()));
+                for (size_t q = 0; q < list.size(); ++q) {
+                    UDesc D = pl.ud[list[q]];
+                    const UDesc Dg = D;
+                    const bool comp = level[q] <= 3;
+                    for (int k = 0; k < 6; ++k) {
+                        if (D.nb[k] >= 0) D.nb[k] = g2l[D.nb[k]] >= 0 ? g2l[D.nb[k]] : 0;
+                        else D.nb[k] = comp ? -(node_of(-Dg.nb[k] - 1) + 1) : -1;
+                    }
+                    for (int k = 0; k < 5; ++k)
+                        D.vs[k] = comp && D.kind < 4 && p->viscous == LBM_VISCOUS_MESO ? node_of(Dg.vs[k]) : 0;
+                    if (level[q] == 0 && p->dirichlet == LBM_DIRICHLET_NEEP) {
+                        const int nl = node_of(Dg.wslot);
+                        D.wslot = nl;
+                        auto it = fxl.find(nl);
+                        if (it == fxl.end()) {
+                            const int fi = int(fxl.size());
+                            fxl[nl] = fi;
+                            nodes[nl].fx = fi;
+                            D.wsrc = fi;
+                        } else {
+                            D.wsrc = it->second;
+                        }
+                    } else {
+                        D.wslot = 0;
+                        D.wsrc = 0;
+                    }
+                    D.gid = list[q];
+                    D.level = level[q];
+                    pl.ld.push_back(D);
+                }
+                for (int g : list) g2l[g] = -1;
+                pl.sbeg.push_back(int(pl.sn.size()));
+                pl.sn.insert(pl.sn.end(), nodes.begin(), nodes.end());
+                B.max_nodes = std::max(B.max_nodes, int(nodes.size()));
+                B.max_fx = std::max(B.max_fx, int(fxl.size()));
+            }
+        }
+        pl.tbeg.push_back(int(pl.ld.size()));
+        pl.sbeg.push_back(int(pl.sn.size()));
+        B.n_tiles = int(pl.tbeg.size()) - 1;
+    }
     B.viscous = p->viscous;
     B.dirichlet = p->dirichlet;
     for (int s = 0; s < 4; ++s) {
@@ -353,13 +469,12 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     pl.off_f1 = take(pl.f_bytes);
     pl.off_sU = take(pl.stripU_n * 8);
     pl.off_sN = take(pl.stripN_n * 8);
-    pl.off_Ub = take(nu * 32);
-    pl.off_Ya = take(nu * 32);
-    pl.off_Yb = take(nu * 32);
-    pl.off_acc = take(nu * 32);
-    pl.off_V = take(nu * 32);
-    pl.off_mask = take(nu * 4);
+    pl.off_Ub = take(2 * nu * 32);
     pl.off_ud = take(nu * sizeof(UDesc));
+    pl.off_ld = take(pl.ld.size() * sizeof(UDesc));
+    pl.off_tb = take(pl.tbeg.size() * sizeof(int));
+    pl.off_sn = take(pl.sn.size() * sizeof(StripNode));
+    pl.off_sb = take(pl.sbeg.size() * sizeof(int));
     pl.off_zg = take(pl.zg.size() * sizeof(int2));
     pl.off_in = take(pl.inflow.size() * sizeof(int));
     pl.off_macro = take((size_t)4 * nx * ny * 8);
@@ -445,8 +560,7 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     h->O = pl.O;
     h->E = pl.E;
     h->B = pl.B;
-    h->interior = pl.interior;
-    h->rim = pl.rim;
+    h->bulk = pl.bulk;
     h->esize = pl.esize;
     h->f_bytes = pl.f_bytes;
     h->ws = ws;
@@ -457,12 +571,13 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     h->E.stripU = at<double>(ws, pl.off_sU);
     h->E.stripN = at<double>(ws, pl.off_sN);
     h->B.Ub = at<double>(ws, pl.off_Ub);
-    h->B.Ya = at<double>(ws, pl.off_Ya);
-    h->B.Yb = at<double>(ws, pl.off_Yb);
-    h->B.acc = at<double>(ws, pl.off_acc);
-    h->B.V = at<double>(ws, pl.off_V);
-    h->B.mask = at<int>(ws, pl.off_mask);
+    h->B.Ya = h->B.Yb = h->B.acc = h->B.V = nullptr;
+    h->B.mask = nullptr;
     h->B.ud = at<UDesc>(ws, pl.off_ud);
+    h->B.ld = at<UDesc>(ws, pl.off_ld);
+    h->B.tbeg = at<int>(ws, pl.off_tb);
+    h->B.sn = at<StripNode>(ws, pl.off_sn);
+    h->B.sbeg = at<int>(ws, pl.off_sb);
     h->B.zg = at<int2>(ws, pl.off_zg);
     h->inflow_nodes = at<int>(ws, pl.off_in);
     h->n_inflow = int(pl.inflow.size());
@@ -475,11 +590,14 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
             const int rc = encode_population_map(h, h->f[b], depths[k] <= h->Q ? depths[k] : 1, &h->tmap[b][k]);
             if (rc != LBM_OK) return rc;
         }
-    // The rim and the boundary phase run on a stream of the highest
-    // priority so that their few CTAs are scheduled ahead of the interior's.
-    int prio_lo = 0, prio_hi = 0;
-    cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_hi);
+    // The bulk kernel runs on an internal stream beside the band kernel,
+    // which stays on the handle's stream so that it is queued first.
+    // (Reserving whole SMs for the band through its shared-memory request
+    // measured slower: the bulk loses more than the band gains.)
+    h->band_pad = 0;
+    if (h->B.n_tiles > 0 && prepare_boundary(h->lattice, h->storage, h->B, h->band_pad) != 0)
+        return cuda_fail(h, cudaGetLastError(), "band kernel shared memory");
+    cudaError_t e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(h, e, "stream set-up");
@@ -490,6 +608,18 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     if (e == cudaSuccess) e = cudaMemsetAsync(h->E.stripN, 0, pl.stripN_n * 8, h->stream);
     if (e == cudaSuccess && !pl.ud.empty())
         e = cudaMemcpyAsync(const_cast<UDesc*>(h->B.ud), pl.ud.data(), pl.ud.size() * sizeof(UDesc),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !pl.ld.empty())
+        e = cudaMemcpyAsync(const_cast<UDesc*>(h->B.ld), pl.ld.data(), pl.ld.size() * sizeof(UDesc),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !pl.tbeg.empty())
+        e = cudaMemcpyAsync(const_cast<int*>(h->B.tbeg), pl.tbeg.data(), pl.tbeg.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !pl.sn.empty())
+        e = cudaMemcpyAsync(const_cast<StripNode*>(h->B.sn), pl.sn.data(), pl.sn.size() * sizeof(StripNode),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !pl.sbeg.empty())
+        e = cudaMemcpyAsync(const_cast<int*>(h->B.sbeg), pl.sbeg.data(), pl.sbeg.size() * sizeof(int),
                             cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && !pl.zg.empty())
         e = cudaMemcpyAsync(const_cast<int2*>(h->B.zg), pl.zg.data(), pl.zg.size() * sizeof(int2),
@@ -509,31 +639,21 @@ int mark(lbm_handle* h, int k, cudaStream_t st)
     return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "timing event");
 }
 
-// Interior bulk update of step (parity par) on stream st, bracketed by the
-// caller's timing events when set.
-int interior(lbm_handle* h, int par, cudaStream_t st)
+// Bulk update of step (parity par) on stream st, bracketed by the caller's
+// timing events 0 and 1 when set.
+int bulk(lbm_handle* h, int par, cudaStream_t st)
 {
     int rc = mark(h, 0, st);
     if (rc != LBM_OK) return rc;
-    rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->E, h->interior, h->tmap[par], h->f[par],
-                     h->f[par ^ 1], par ^ 1, h->flag + 1, st);
+    rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->bulk, h->tmap[par], h->f[par],
+                     h->f[par ^ 1], h->flag + 1, st);
     if (rc) return check_launch(h, rc, "bulk kernel");
     return mark(h, 1, st);
 }
 
-// Rim bulk update of step (parity par) on stream st, after timing mark 2.
-int rim(lbm_handle* h, int par, cudaStream_t st)
-{
-    int rc = mark(h, 2, st);
-    if (rc != LBM_OK) return rc;
-    rc = launch_rim(h->lattice, h->storage, h->G, h->O, h->E, h->rim, h->f[par], h->f[par ^ 1],
-                    par ^ 1, st);
-    return rc ? check_launch(h, rc, "rim kernel") : LBM_OK;
-}
-
-// Inflow equilibrium (once per buffer) and the characteristic boundary
-// solver of step (parity par) on stream st.
-int boundary_phase(lbm_handle* h, int par, cudaStream_t st)
+// Inflow equilibrium (once per buffer) and the band kernel of step (parity
+// par) on stream st, bracketed by timing events 3 and 4.
+int band(lbm_handle* h, int par, cudaStream_t st)
 {
     int rc = mark(h, 3, st);
     if (rc != LBM_OK) return rc;
@@ -546,9 +666,17 @@ int boundary_phase(lbm_handle* h, int par, cudaStream_t st)
         if (rc) return check_launch(h, rc, "inflow kernel");
         h->inflow_done[par ^ 1] = true;
     }
-    rc = launch_boundary(h->lattice, h->storage, h->G, h->E, h->B, h->f[par ^ 1], par, st);
-    if (rc) return check_launch(h, rc, "boundary kernels");
+    rc = launch_boundary(h->lattice, h->storage, h->G, h->O, h->E, h->B, h->f[par], h->f[par ^ 1],
+                         par, h->band_pad, st);
+    if (rc) return check_launch(h, rc, "band kernel");
     return mark(h, 4, st);
+}
+
+// Zero-gradient copies of step (parity par), after the bulk update.
+int zero_gradient(lbm_handle* h, int par, cudaStream_t st)
+{
+    const int rc = launch_zg(h->lattice, h->storage, h->G, h->B, h->f[par ^ 1], st);
+    return rc ? check_launch(h, rc, "zero-gradient kernel") : LBM_OK;
 }
 
 void release_streams(lbm_handle* h)
@@ -702,15 +830,16 @@ int lbm_step_phase(lbm_handle* h, int phase)
     const int par = int(h->steps & 1);
     if (phase == 0) {
         if (h->bulk_pending) { h->err = "bulk phase issued twice"; return LBM_ERR_STATE; }
-        int rc = rim(h, par, h->stream);
-        if (rc == LBM_OK) rc = interior(h, par, h->stream);
+        int rc = mark(h, 2, h->stream);
+        if (rc == LBM_OK) rc = bulk(h, par, h->stream);
         if (rc != LBM_OK) return rc;
         h->bulk_pending = true;
         return LBM_OK;
     }
     if (phase == 1) {
         if (!h->bulk_pending) { h->err = "boundary phase before bulk phase"; return LBM_ERR_STATE; }
-        const int rc = boundary_phase(h, par, h->stream);
+        int rc = band(h, par, h->stream);
+        if (rc == LBM_OK) rc = zero_gradient(h, par, h->stream);
         if (rc != LBM_OK) return rc;
         h->bulk_pending = false;
         h->steps++;
@@ -730,25 +859,27 @@ int lbm_step(lbm_handle* h, int n)
     if (h->bulk_pending) { h->err = "lbm_step in the middle of a phased step"; return LBM_ERR_STATE; }
     for (int i = 0; i < n; ++i) {
         const int par = int(h->steps & 1);
-        if (h->rim.total == 0) {
-            // fully periodic: no boundary phase, one launch
-            const int rc = interior(h, par, h->stream);
+        int rc = mark(h, 2, h->stream);
+        if (rc != LBM_OK) return rc;
+        if (h->B.n_tiles == 0) {
+            // no characteristic side: bulk, inflow and zero gradient in order
+            rc = bulk(h, par, h->stream);
+            if (rc == LBM_OK) rc = band(h, par, h->stream);
+            if (rc == LBM_OK) rc = zero_gradient(h, par, h->stream);
             if (rc != LBM_OK) return rc;
             h->steps++;
             continue;
         }
-        // The rim first, alone (launched beside the interior, its few CTAs
-        // would queue behind the interior's); then fork: the boundary phase
-        // on the high-priority stream, the interior on the handle's stream,
-        // concurrently; join before the next step.
-        int rc = rim(h, par, h->stream);
-        if (rc != LBM_OK) return rc;
+        // Fork: the band kernel on the handle's stream (queued first, so its
+        // few CTAs take their SMs before the bulk's), the bulk kernel and the
+        // zero-gradient copies on the internal stream; join before the next
+        // step.  The two kernels write disjoint nodes of the new buffer.
         cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
         if (e != cudaSuccess) return cuda_fail(h, e, "fork");
-        rc = interior(h, par, h->stream);
-        if (rc != LBM_OK) return rc;
-        rc = boundary_phase(h, par, h->aux);
+        rc = band(h, par, h->stream);
+        if (rc == LBM_OK) rc = bulk(h, par, h->aux);
+        if (rc == LBM_OK) rc = zero_gradient(h, par, h->aux);
         if (rc != LBM_OK) return rc;
         e = cudaEventRecord(h->ev_join, h->aux);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
@@ -846,7 +977,9 @@ int lbm_get_state(lbm_handle* h, void* buf, size_t bytes)
     p += 8ull * h->E.nslots * 8;
     if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->E.stripN, 10ull * h->E.nslots * 8, cudaMemcpyDeviceToHost, h->stream);
     p += 10ull * h->E.nslots * 8;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->B.Ub, 32ull * h->B.n_unk, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p, h->B.Ub + (h->steps & 1) * 4ull * h->B.n_unk, 32ull * h->B.n_unk,
+                            cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "state copy");
     return LBM_OK;
@@ -872,7 +1005,9 @@ int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes)
     p += 8ull * h->E.nslots * 8;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->E.stripN, p, 10ull * h->E.nslots * 8, cudaMemcpyHostToDevice, h->stream);
     p += 10ull * h->E.nslots * 8;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.Ub, p, 32ull * h->B.n_unk, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->B.Ub + (hd.steps & 1) * 4ull * h->B.n_unk, p, 32ull * h->B.n_unk,
+                            cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "state restore");
     h->steps = hd.steps;

@@ -1,25 +1,28 @@
 // boundary.cu -- boundary conditions of one time step.
 //
-//  k_stage   one classical RK4 stage (Sec. 3.3, "Time integration") of the
-//            boundary ODE on every characteristic unknown: layer j = 1..M
-//            of every CBC side position (Sec. 3.3, "Multi-speed LBM") and the
-//            innermost node of every corner block.  Stage 0 freezes the
-//            viscous vector and the incoming-wave mask of time t; stage 3
-//            ends the step, writes the mesoscopic Dirichlet populations
-//            (equilibrium or Eq. NEEP) post-collision into the new buffer,
-//            and copies the zero-gradient nodes (Eq. zg-bc).
+//  k_band    the characteristic boundary condition (Sec. 3) of one step in
+//            one launch: each CTA takes a tile of a characteristic side,
+//            updates the strip nodes next to it, integrates the boundary
+//            ODE of its layers j = 1..M (and corner) over the four RK4
+//            stages in shared memory, and writes the mesoscopic Dirichlet
+//            populations (equilibrium or Eq. NEEP) post-collision.
+//  k_zg      zero-gradient copies (Eq. zg-bc), after the bulk update.
 //
 // All characteristic arithmetic is FP64.  Every neighbour a right-hand side
 // needs is resolved on the host into a UDesc: another unknown (stage value)
-// or a strip slot holding a bulk node's macros at t and t + 1 (interpolated
+// or a strip node holding a bulk node's macros at t and t + 1 (interpolated
 // linearly at the stage time, Sec. 3.3).
-#include "lbm_internal.cuh"
+#include "collide.cuh"
 
 namespace lbmgb {
 
 namespace {
 
-constexpr int kBandThreads = 32;   // few unknowns: spread them over many SMs
+constexpr int kBandThreads = 32;   // allocation-free path: one thread per unknown
+// Fused band kernel: at most one warp per SM sub-partition, because FP64
+// issue (one warp instruction per 64 cycles on each sub-partition) bounds
+// the characteristic arithmetic; the host sizes tiles to fit.
+constexpr int kTileThreads = kTileUnknowns;
 
 // Lab <-> local frame.  Sides: n the outward normal, t = +y (W, E) or +x
 // (S, N).  Corners: n = (sx, sy)/sqrt(2), t = n rotated by +90 degrees.
@@ -219,11 +222,11 @@ __device__ __forceinline__ void char_rhs(const CharSys& C, const Band& B, const 
 //   V = (0, (1/rho) d_j s'_jn, (1/rho) d_j s'_jt,
 //        -div q / (rho c_s^2) + (nu / c_s^2) ((d_n u_n - d_t u_t)^2 + (d_n u_t + d_t u_n)^2)).
 template <bool TH>
-__device__ void vis_meso(const Geom& G, const Band& B, const Export& E, int par_t,
-                         const UDesc& D, double cs2, double* V)
+__device__ void vis_meso(const Geom& G, const double* SU, const double* SN, const UDesc& D,
+                         double cs2, double* V)
 {
-    const double* SU = E.stripU + (long long)par_t * E.nslots * 4;
-    const double* SN = E.stripN + (long long)par_t * E.nslots * 5;
+    // SU, SN: macros [.][4] and non-equilibrium moments [.][5] of time t,
+    // indexed by D.vs[]
     const int s = D.kind;
     const int an = s < 2 ? 0 : 1, at = 1 - an;     // axes of n and t
     const double sn = (s == 0 || s == 2) ? -1.0 : 1.0;
@@ -381,9 +384,11 @@ __device__ void unknown_rhs(const Geom& G, const Band& B, const Ctx& X, const UD
 // the bulk neighbour after its collision, f*(x_f) - f^eq(U(x_f, t+1)).  Computed
 // in the arithmetic type of the storage.
 template <int LAT, typename S>
-__device__ void dirichlet(const Geom& G, const Band& B, const Export& E, S* f, int par_new,
+__device__ void dirichlet(const Geom& G, const Band& B, S* f, const double* Us, const S* fsrc,
                           const UDesc& D, const double* Unew)
 {
+    // Us: macros of x_f at t + 1; fsrc: its stored post-collision
+    // populations, indexed by velocity (both read only for Eq. NEEP)
     using L = Lat<LAT>;
     using Cm = typename Store<S>::C;
     Moments<LAT, Cm> m;
@@ -395,7 +400,6 @@ __device__ void dirichlet(const Geom& G, const Band& B, const Export& E, S* f, i
     Cm ge[L::Q];
     equilibrium<LAT, Cm>(m, ge);
     if (B.dirichlet == 1) {
-        const double* Us = E.stripU + ((long long)par_new * E.nslots + D.wslot) * 4;
         Moments<LAT, Cm> ms;
         ms.s0 = Cm(Us[0]);
         ms.rho = Cm(G.rho0) + ms.s0;
@@ -406,7 +410,7 @@ __device__ void dirichlet(const Geom& G, const Band& B, const Export& E, S* f, i
         equilibrium<LAT, Cm>(ms, gs);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            Cm v = Cm(Store<S>::load(f + L::plane_of(i) * G.plane + D.wsrc));
+            Cm v = Cm(Store<S>::value(fsrc[i]));     // fsrc is in shared memory
             if (Store<S>::SCALED) v *= Cm(L::w(i));
             ge[i] += v - gs[i];
         }
@@ -424,101 +428,238 @@ __device__ void dirichlet(const Geom& G, const Band& B, const Export& E, S* f, i
         }
 }
 
+// One tile of the boundary band per CTA: a run of positions of one
+// characteristic side (all M layers, and the corner next to it on a W/E
+// side), plus the halo its four RK4 stages need (Sec. 3.3).
+//
+// 1. Strip nodes: the tile pulls and collides the bulk nodes at depths 0..2
+//    next to the side that its stencils read (Eqs. lbe, bgk), keeps their
+//    macros of t (loaded) and t + 1 (computed) in shared memory, writes the
+//    populations of the nodes it owns and the strips of its own positions
+//    for the next step.
+// 2. RK4 (Sec. 3.3, "Time integration"): the local table lists the tile's
+//    unknowns by level: level 0 are owned, level l computes the first 4 - l
+//    stages, level 4 only supplies U(t); stage values live in shared memory.
+//    Stage 0 freezes the viscous vector and the incoming-wave mask of time
+//    t.  After stage 3 the owners write U(t + 1) and the mesoscopic
+//    Dirichlet populations (equilibrium or Eq. NEEP).
 template <int LAT, typename S>
-__global__ void __launch_bounds__(kBandThreads)
-    k_stage(Geom G, Band B, Export E, S* __restrict__ f, int par_t, int stage)
+__global__ void __launch_bounds__(kTileThreads)
+    k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
+           int par_t)
 {
     using L = Lat<LAT>;
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (stage == 3 && u >= B.n_unk) {
-        // zero gradient: copy the post-collision populations of x_f
-        const int z = u - B.n_unk;
-        if (z >= B.n_zg) return;
-        const int2 nd = B.zg[z];
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) f[i * G.plane + nd.x] = f[i * G.plane + nd.y];
-        return;
-    }
-    if (u >= B.n_unk) return;
-    const UDesc D = B.ud[u];
-    Ctx X;
-    X.Y = stage == 0 ? B.Ub : (stage == 2 ? B.Yb : B.Ya);
-    X.St = E.stripU + (long long)par_t * E.nslots * 4;
-    X.St1 = E.stripU + (long long)(par_t ^ 1) * E.nslots * 4;
-    X.frac = stage == 0 ? 0.0 : (stage == 3 ? 1.0 : 0.5);
-    double* Yout = stage == 1 ? B.Yb : B.Ya;
+    using C = typename Store<S>::C;
+    __shared__ __align__(16) double Ys[kTileThreads * 4];
+    extern __shared__ __align__(16) double dyn[];
+    double* SUt = dyn;                              // [max_nodes][4] macros of t
+    double* SUt1 = SUt + 4 * B.max_nodes;           // [max_nodes][4] macros of t + 1
+    double* SNt = SUt1 + 4 * B.max_nodes;           // [max_nodes][5] moments of t
+    S* Fx = reinterpret_cast<S*>(SNt + 5 * B.max_nodes);   // [max_fx][Q]
+    const int tile = blockIdx.x;
+    const int l = threadIdx.x;
 
-    double V[4];
-    int mask;
-    if (stage == 0) {
-        double Ul[4];
-        to_local(D.kind, B.kR, B.Ub + 4LL * u, Ul);
-        mask = incoming_mask<L::THERMAL>(char_sys<L::THERMAL>(B, G.rho0, Ul));
-        if (D.kind >= 4 || B.viscous == VIS_OFF) V[0] = V[1] = V[2] = V[3] = 0.0;
-        else if (B.viscous == VIS_FD) vis_fd<L::THERMAL>(G, B, X, D, u, L::CS2, V);
-        else vis_meso<L::THERMAL>(G, B, E, par_t, D, L::CS2, V);
-        double2* vo = reinterpret_cast<double2*>(B.V + 4LL * u);
-        vo[0] = make_double2(V[0], V[1]);
-        vo[1] = make_double2(V[2], V[3]);
-        B.mask[u] = mask;
-    } else {
-        const double2* vi = reinterpret_cast<const double2*>(B.V + 4LL * u);
-        const double2 v0 = vi[0], v1 = vi[1];
-        V[0] = v0.x; V[1] = v0.y; V[2] = v1.x; V[3] = v1.y;
-        mask = B.mask[u];
-    }
-    double k[4];
-    unknown_rhs<LAT>(G, B, X, D, u, V, mask, k);
-
-    const double* U0 = B.Ub + 4LL * u;
-    double* acc = B.acc + 4LL * u;
-    if (stage < 3) {
-        const double wk = stage == 0 ? 1.0 : 2.0;
-        const double hk = stage == 2 ? 1.0 : 0.5;
+    // 1. strip nodes
+    {
+        const int sb = B.sbeg[tile], ns = B.sbeg[tile + 1] - sb;
+        const double* gU = E.stripU + (long long)par_t * E.nslots * 4;
+        const double* gN = E.stripN + (long long)par_t * E.nslots * 5;
+        double* wU = E.stripU + (long long)(par_t ^ 1) * E.nslots * 4;
+        double* wN = E.stripN + (long long)(par_t ^ 1) * E.nslots * 5;
+        const double fac = 1.0 - 0.5 / G.tau;
+        for (int k = l; k < ns; k += kTileThreads) {
+            const StripNode N = B.sn[sb + k];
+            C g[L::Q];
+            pull_plain<LAT, S, C>(G, O, fin, N.x, N.y, g);
+            if (Store<S>::SCALED) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            acc[m] = (stage == 0 ? 0.0 : acc[m]) + wk * k[m];
-            Yout[4LL * u + m] = U0[m] + hk * k[m];
+                for (int i = 0; i < L::Q; ++i) g[i] *= C(L::w(i));
+            }
+            S* out = f + (N.y * G.nxp + N.x);
+            S* fx = N.fx >= 0 ? Fx + N.fx * L::Q : nullptr;
+            const Moments<LAT, C> m = collide<LAT, C>(G, g, [&](int i, C v) {
+                if (Store<S>::SCALED) v *= C(1.0 / L::w(i));
+                if (N.own) Store<S>::put(out + O.st[i], v);
+                if (fx) Store<S>::put(fx + i, v);
+            });
+            const double U1[4] = {double(m.s0), double(m.ux), double(m.uy), double(m.dT)};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) SUt1[4 * k + c] = U1[c];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) SUt[4 * k + c] = gU[4LL * N.tslot + c];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) SNt[5 * k + c] = gN[5LL * N.tslot + c];
+            if (N.gslot >= 0) {
+                double N1[5];
+                neq_moments<LAT, C>(g, m, fac, N1);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) wU[4LL * N.gslot + c] = U1[c];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) wN[5LL * N.gslot + c] = N1[c];
+            }
         }
-        return;
     }
+
+    // 2. RK4 of the characteristic boundary state
+    const int beg = B.tbeg[tile], n = B.tbeg[tile + 1] - beg;
+    UDesc D;
+    int lev = 99;                       // > 4: no unknown on this thread
+    double U0[4] = {0.0, 0.0, 0.0, 0.0};
+    if (l < n) {
+        D = B.ld[beg + l];
+        lev = D.level;
+        const double2* p = reinterpret_cast<const double2*>(B.Ub + ((long long)par_t * B.n_unk + D.gid) * 4);
+        const double2 a = p[0], b = p[1];
+        U0[0] = a.x; U0[1] = a.y; U0[2] = b.x; U0[3] = b.y;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) Ys[4 * l + m] = U0[m];
+    }
+    __syncthreads();
+    Ctx X;
+    X.Y = Ys;
+    X.St = SUt;
+    X.St1 = SUt1;
+    double V[4] = {0.0, 0.0, 0.0, 0.0}, acc[4] = {0.0, 0.0, 0.0, 0.0}, k[4];
+    int mask = 0;
+    for (int stage = 0; stage < 4; ++stage) {
+        const bool comp = lev <= 3 - stage;
+        if (comp) {
+            X.frac = stage == 0 ? 0.0 : (stage == 3 ? 1.0 : 0.5);
+            if (stage == 0) {
+                double Ul[4];
+                to_local(D.kind, B.kR, U0, Ul);
+                mask = incoming_mask<L::THERMAL>(char_sys<L::THERMAL>(B, G.rho0, Ul));
+                if (D.kind < 4 && B.viscous == VIS_FD) vis_fd<L::THERMAL>(G, B, X, D, l, L::CS2, V);
+                else if (D.kind < 4 && B.viscous == VIS_MESO) vis_meso<L::THERMAL>(G, SUt, SNt, D, L::CS2, V);
+            }
+            unknown_rhs<LAT>(G, B, X, D, l, V, mask, k);
+            if (stage < 3) {
+                const double wk = stage == 0 ? 1.0 : 2.0;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) acc[m] = (stage == 0 ? 0.0 : acc[m]) + wk * k[m];
+            }
+        }
+        if (stage == 3) break;
+        __syncthreads();                // every stage-s value has been read
+        if (comp) {                     // read at the next stage by neighbours one level in
+            const double hk = stage == 2 ? 1.0 : 0.5;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) Ys[4 * l + m] = U0[m] + hk * k[m];
+        }
+        __syncthreads();
+    }
+    if (lev != 0) return;
+    // RK4: U(t + 1) = U(t) + (k1 + 2 k2 + 2 k3 + k4) / 6, acc = k1 + 2 k2 + 2 k3
     double Unew[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) Unew[m] = U0[m] + (acc[m] + k[m]) * (1.0 / 6.0);
+    double2* q = reinterpret_cast<double2*>(B.Ub + ((long long)(par_t ^ 1) * B.n_unk + D.gid) * 4);
+    q[0] = make_double2(Unew[0], Unew[1]);
+    q[1] = make_double2(Unew[2], Unew[3]);
+    const bool neep = B.dirichlet == 1;
+    dirichlet<LAT, S>(G, B, f, neep ? SUt1 + 4 * D.wslot : nullptr,
+                      neep ? Fx + D.wsrc * L::Q : nullptr, D, Unew);
+}
+
+// Zero gradient (Eq. zg-bc): the post-collision populations of x_f.
+template <int LAT, typename S>
+__global__ void k_zg(Geom G, Band B, S* __restrict__ f)
+{
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= B.n_zg) return;
+    const int2 nd = B.zg[z];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) B.Ub[4LL * u + m] = Unew[m];
-    dirichlet<LAT, S>(G, B, E, f, par_t ^ 1, D, Unew);
+    for (int i = 0; i < Lat<LAT>::Q; ++i) f[i * G.plane + nd.x] = f[i * G.plane + nd.y];
 }
 
 template <int LAT, typename S>
-int boundary_t(const Geom& G, const Export& E, const Band& B, void* fnew, int par_t, cudaStream_t st)
+size_t band_smem(const Band& B)
 {
-    S* f = static_cast<S*>(fnew);
-    if (B.n_unk > 0) {
-        const int nb = (B.n_unk + kBandThreads - 1) / kBandThreads;
-        for (int stage = 0; stage < 3; ++stage)
-            k_stage<LAT, S><<<nb, kBandThreads, 0, st>>>(G, B, E, f, par_t, stage);
-    }
-    const int n3 = B.n_unk + B.n_zg;
-    if (n3 > 0)
-        k_stage<LAT, S><<<(n3 + kBandThreads - 1) / kBandThreads, kBandThreads, 0, st>>>(G, B, E, f,
-                                                                                      par_t, 3);
+    return (size_t)B.max_nodes * 13 * sizeof(double) + (size_t)B.max_fx * Lat<LAT>::Q * sizeof(S);
+}
+
+template <int LAT, typename S>
+int boundary_t(const Geom& G, const Offsets& O, const Export& E, const Band& B, const void* fin,
+               void* fnew, int par_t, size_t smem_pad, cudaStream_t st)
+{
+    if (B.n_tiles == 0) return 0;
+    const size_t smem = band_smem<LAT, S>(B) + smem_pad;
+    k_band<LAT, S><<<B.n_tiles, kTileThreads, smem, st>>>(G, O, B, E, static_cast<const S*>(fin),
+                                                         static_cast<S*>(fnew), par_t);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int LAT, typename S>
+int prepare_t(const Band& B, size_t smem_pad)
+{
+    const size_t smem = band_smem<LAT, S>(B) + smem_pad;
+    if (smem <= 48 * 1024) return 0;
+    return cudaFuncSetAttribute(k_band<LAT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(smem)) == cudaSuccess ? 0 : -1;
+}
+
+template <int LAT, typename S>
+int zg_t(const Geom& G, const Band& B, void* fnew, cudaStream_t st)
+{
+    if (B.n_zg == 0) return 0;
+    k_zg<LAT, S><<<(B.n_zg + 127) / 128, 128, 0, st>>>(G, B, static_cast<S*>(fnew));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace
 
-int launch_boundary(int lat, int storage, const Geom& G, const Export& E, const Band& B,
-                    void* fnew, int par_t, cudaStream_t st)
+int launch_boundary(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
+                    const Band& B, const void* fin, void* fnew, int par_t, size_t smem_pad,
+                    cudaStream_t st)
 {
     if (lat == D2Q9) {
-        if (storage == 0) return boundary_t<D2Q9, double>(G, E, B, fnew, par_t, st);
-        if (storage == 1) return boundary_t<D2Q9, float>(G, E, B, fnew, par_t, st);
-        if (storage == 2) return boundary_t<D2Q9, __half>(G, E, B, fnew, par_t, st);
+        if (storage == 0) return boundary_t<D2Q9, double>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
+        if (storage == 1) return boundary_t<D2Q9, float>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
+        if (storage == 2) return boundary_t<D2Q9, __half>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
     } else {
-        if (storage == 0) return boundary_t<D2Q37, double>(G, E, B, fnew, par_t, st);
-        if (storage == 1) return boundary_t<D2Q37, float>(G, E, B, fnew, par_t, st);
-        if (storage == 2) return boundary_t<D2Q37, __half>(G, E, B, fnew, par_t, st);
+        if (storage == 0) return boundary_t<D2Q37, double>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
+        if (storage == 1) return boundary_t<D2Q37, float>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
+        if (storage == 2) return boundary_t<D2Q37, __half>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
+    }
+    return -1;
+}
+
+size_t band_dynamic_smem(int lat, int storage, const Band& B)
+{
+    if (lat == D2Q9) {
+        if (storage == 0) return band_smem<D2Q9, double>(B);
+        if (storage == 1) return band_smem<D2Q9, float>(B);
+        return band_smem<D2Q9, __half>(B);
+    }
+    if (storage == 0) return band_smem<D2Q37, double>(B);
+    if (storage == 1) return band_smem<D2Q37, float>(B);
+    return band_smem<D2Q37, __half>(B);
+}
+
+int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad)
+{
+    if (lat == D2Q9) {
+        if (storage == 0) return prepare_t<D2Q9, double>(B, smem_pad);
+        if (storage == 1) return prepare_t<D2Q9, float>(B, smem_pad);
+        if (storage == 2) return prepare_t<D2Q9, __half>(B, smem_pad);
+    } else {
+        if (storage == 0) return prepare_t<D2Q37, double>(B, smem_pad);
+        if (storage == 1) return prepare_t<D2Q37, float>(B, smem_pad);
+        if (storage == 2) return prepare_t<D2Q37, __half>(B, smem_pad);
+    }
+    return -1;
+}
+
+int launch_zg(int lat, int storage, const Geom& G, const Band& B, void* fnew, cudaStream_t st)
+{
+    if (lat == D2Q9) {
+        if (storage == 0) return zg_t<D2Q9, double>(G, B, fnew, st);
+        if (storage == 1) return zg_t<D2Q9, float>(G, B, fnew, st);
+        if (storage == 2) return zg_t<D2Q9, __half>(G, B, fnew, st);
+    } else {
+        if (storage == 0) return zg_t<D2Q37, double>(G, B, fnew, st);
+        if (storage == 1) return zg_t<D2Q37, float>(G, B, fnew, st);
+        if (storage == 2) return zg_t<D2Q37, __half>(G, B, fnew, st);
     }
     return -1;
 }
@@ -597,7 +738,7 @@ __global__ void __launch_bounds__(kBandThreads)
         mask = incoming_mask<Lt::THERMAL>(char_sys<Lt::THERMAL>(B, G.rho0, Ul));
         if (B.viscous == VIS_OFF) V[0] = V[1] = V[2] = V[3] = 0.0;
         else if (B.viscous == VIS_FD) vis_fd<Lt::THERMAL>(G, B, X, D, u, Lt::CS2, V);
-        else vis_meso<Lt::THERMAL>(G, B, E, 0, D, Lt::CS2, V);
+        else vis_meso<Lt::THERMAL>(G, E.stripU, E.stripN, D, Lt::CS2, V);
         for (int m = 0; m < 4; ++m) B.V[4LL * u + m] = V[m];
         B.mask[u] = mask;
     } else {

@@ -1,0 +1,170 @@
+// collide.cuh -- the per-node update shared by the bulk kernels (bulk.cu)
+// and the band kernel (boundary.cu): plain pull, moments, BGK collision.
+#pragma once
+#include "lbm_internal.cuh"
+
+namespace lbmgb {
+
+template <typename C>
+__device__ __forceinline__ C omega_of(const Geom& G);
+template <>
+__device__ __forceinline__ float omega_of<float>(const Geom& G) { return G.omega_f; }
+template <>
+__device__ __forceinline__ double omega_of<double>(const Geom& G) { return G.omega; }
+template <typename C>
+__device__ __forceinline__ C rho0_of(const Geom& G);
+template <>
+__device__ __forceinline__ float rho0_of<float>(const Geom& G) { return G.rho0_f; }
+template <>
+__device__ __forceinline__ double rho0_of<double>(const Geom& G) { return G.rho0; }
+
+// Viscous stress sigma' = -(1 - 1/(2 tau)) sum c c (f - f^eq) (Eq. LaplaceU)
+// and heat flux q = (1 - 1/(2 tau)) 1/2 sum (f - f^eq) |c-u|^2 (c-u)
+// (Eqs. heatflux, LaplaceT; the equilibrium part of the central third
+// moment vanishes on D2Q37).
+template <int LAT, typename C>
+__device__ __forceinline__ void neq_moments(const C* g, const Moments<LAT, C>& m, double fac,
+                                         double* N)
+{
+    using L = Lat<LAT>;
+    C geq[L::Q];
+    equilibrium<LAT, C>(m, geq);
+    C pxx = 0, pxy = 0, pyy = 0, qx = 0, qy = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const C d = g[i] - geq[i];
+        const C cx = C(L::cx(i)), cy = C(L::cy(i));
+        pxx += cx * cx * d;
+        pxy += cx * cy * d;
+        pyy += cy * cy * d;
+        if (L::THERMAL) {
+            const C ex = cx - m.ux, ey = cy - m.uy;
+            const C h = C(0.5) * d * (ex * ex + ey * ey);
+            qx += h * ex;
+            qy += h * ey;
+        }
+    }
+    N[0] = -fac * double(pxx);
+    N[1] = -fac * double(pxy);
+    N[2] = -fac * double(pyy);
+    N[3] = fac * double(qx);
+    N[4] = fac * double(qy);
+}
+
+// Plain pull of node (x, y) with periodic wrap-around of the sources.
+template <int LAT, typename S, typename C>
+__device__ __forceinline__ void pull_plain(const Geom& G, const Offsets& O,
+                                           const S* __restrict__ fin, int x, int y, C* g)
+{
+    using L = Lat<LAT>;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        int xs = x - L::cx(i), ys = y - L::cy(i);
+        if (L::cx(i) && G.perx) xs = xs < 0 ? xs + G.nx : (xs >= G.nx ? xs - G.nx : xs);
+        if (L::cy(i) && G.pery) ys = ys < 0 ? ys + G.ny : (ys >= G.ny ? ys - G.ny : ys);
+        g[i] = C(Store<S>::load(fin + (O.st[i] + ys * G.nxp + xs)));
+    }
+}
+
+// Moments (Eq. macro) and BGK collision (Eq. bgk) of one node whose pulled
+// populations are in g (already multiplied by w for scaled storage).  The
+// post-collision value of velocity i goes to put(i, value); the moments of
+// the pulled populations are returned.
+template <int LAT, typename C, typename Put>
+__device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Put&& put)
+{
+    using L = Lat<LAT>;
+    constexpr int Q = L::Q;
+    const Moments<LAT, C> m = moments<LAT, C>(g, rho0_of<C>(G));
+
+    // BGK collide (Eq. bgk), one opposite pair at a time:
+    // g^eq_{+-} = w (rho - rho0) + w rho (even +- odd) in p = c.u / c_s^2.
+    constexpr C ics2 = C(1.0 / L::CS2);
+    constexpr C a3 = L::THERMAL ? C(1.0 / 6.0) : C(0);
+    constexpr C a4 = L::THERMAL ? C(1.0 / 24.0) : C(0);
+    const C uxs = m.ux * ics2, uys = m.uy * ics2;
+    const EqPoly<C> e = eq_poly<LAT, C>(m.ux * uxs + m.uy * uys, m.dT);
+    const C om = omega_of<C>(G);
+    if (sizeof(C) == 8) {
+        {
+            const C geq = C(L::w(0)) * (m.s0 + m.rho * e.A0);
+            put(0, g[0] + om * (geq - g[0]));
+        }
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const int k = L::cls(i);
+            const C xi2 = C(L::c2cls(k)) * ics2;
+            const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
+            const C a1 = e.A1 + e.B1 * xi2;
+            const C a2 = e.A2 + e.B2 * xi2;
+            C p;
+            if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
+            else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
+            else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
+            const C p2 = p * p;
+            const C ev = a0 + p2 * (a2 + p2 * a4);
+            const C od = p * (a1 + p2 * a3);
+            const C ws0 = C(L::w(i)) * m.s0, wr = C(L::w(i)) * m.rho;
+            const C gp = ws0 + wr * (ev + od);
+            const C gm = ws0 + wr * (ev - od);
+            put(i, g[i] + om * (gp - g[i]));
+            put(i + 1, g[i + 1] + om * (gm - g[i + 1]));
+        }
+    } else {
+        // FP32 arithmetic.  Float-rounded weights and c_s^2 miss the discrete
+        // moment identities by ~1e-8, which would make each collision leak
+        // mass, momentum and energy at that relative rate.  The equilibrium
+        // is therefore closed on the conserved moments: the |c| = 1 pairs
+        // take the momentum and energy remainders and the rest velocity the
+        // mass remainder (corrections of float-rounding size).
+        C M0 = 0, Mx = 0, My = 0, Me = 0;
+#pragma unroll
+        for (int i = 5; i < Q; i += 2) {
+            const int k = L::cls(i);
+            const C xi2 = C(L::c2cls(k)) * ics2;
+            const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
+            const C a1 = e.A1 + e.B1 * xi2;
+            const C a2 = e.A2 + e.B2 * xi2;
+            C p;
+            if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
+            else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
+            else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
+            const C p2 = p * p;
+            const C ev = a0 + p2 * (a2 + p2 * a4);
+            const C od = p * (a1 + p2 * a3);
+            const C ws0 = C(L::w(i)) * m.s0, wr = C(L::w(i)) * m.rho;
+            const C gp = ws0 + wr * (ev + od);
+            const C gm = ws0 + wr * (ev - od);
+            const C sum = gp + gm, dif = gp - gm;
+            M0 += sum;
+            if (L::cx(i)) Mx += C(L::cx(i)) * dif;
+            if (L::cy(i)) My += C(L::cy(i)) * dif;
+            if (L::THERMAL) Me += C(L::c2cls(k)) * sum;
+            put(i, g[i] + om * (gp - g[i]));
+            put(i + 1, g[i + 1] + om * (gm - g[i + 1]));
+        }
+        // |c| = 1 class: (1,0) and (-1,0) are velocities 1, 2; (0,1), (0,-1) are 3, 4
+        const C a0 = e.A0 + ics2 * (e.B0 + e.C0 * ics2);
+        const C a2 = e.A2 + e.B2 * ics2;
+        const C px2 = uxs * uxs, py2 = uys * uys;
+        const C ws0 = C(L::w(1)) * m.s0, wr = C(L::w(1)) * m.rho;
+        C ex = ws0 + wr * (a0 + px2 * (a2 + px2 * a4));
+        C ey = ws0 + wr * (a0 + py2 * (a2 + py2 * a4));
+        if (L::THERMAL) {
+            const C d = C(0.25) * (m.se - Me - C(2) * (ex + ey));
+            ex += d;
+            ey += d;
+        }
+        const C ox = C(0.5) * (m.sx - Mx), oy = C(0.5) * (m.sy - My);
+        put(1, g[1] + om * (ex + ox - g[1]));
+        put(2, g[2] + om * (ex - ox - g[2]));
+        put(3, g[3] + om * (ey + oy - g[3]));
+        put(4, g[4] + om * (ey - oy - g[4]));
+        const C geq0 = m.s0 - M0 - C(2) * (ex + ey);
+        put(0, g[0] + om * (geq0 - g[0]));
+    }
+
+    return m;
+}
+
+}  // namespace lbmgb

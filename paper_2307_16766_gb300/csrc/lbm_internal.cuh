@@ -169,6 +169,9 @@ __host__ __device__ constexpr int group_of(int i)
 // g / w so that every velocity uses the same half-precision range.
 // ---------------------------------------------------------------------------
 
+// load(): read-only GLOBAL memory only (the non-coherent load path rejects
+// any other address space); value(): the arithmetic value of a stored
+// element already read (e.g. from shared memory); put(): any address space.
 template <typename S>
 struct Store;
 
@@ -177,6 +180,7 @@ struct Store<double> {
     using C = double;                       // arithmetic type of the bulk kernel
     static constexpr bool SCALED = false;
     __device__ static double load(const double* p) { return __ldg(p); }
+    __device__ static double value(double v) { return v; }
     __device__ static void put(double* p, double v) { *p = v; }
 };
 
@@ -185,6 +189,7 @@ struct Store<float> {
     using C = float;
     static constexpr bool SCALED = false;
     __device__ static float load(const float* p) { return __ldg(p); }
+    __device__ static float value(float v) { return v; }
     __device__ static void put(float* p, float v) { *p = v; }
 };
 
@@ -193,6 +198,7 @@ struct Store<__half> {
     using C = float;
     static constexpr bool SCALED = true;
     __device__ static float load(const __half* p) { return __half2float(__ldg(p)); }
+    __device__ static float value(__half v) { return __half2float(v); }
     __device__ static void put(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
@@ -334,16 +340,6 @@ struct Region {
     int x0, x1, y0, y1;
 };
 
-// The rim: bulk nodes whose pull stencil reaches a node the boundary phase
-// writes, or whose macros the boundary solver reads (the strip export).
-// Bands of width max(M, 3) along each non-periodic side, disjoint; start[b]
-// is the first node index of band b in a flat numbering of the n bands,
-// total the number of rim nodes.
-struct Rim {
-    int n, total;
-    Region r[4];
-    int start[4];
-};
 
 // Offsets (in elements) of the pull sources and of the output planes, used
 // by the bulk kernel away from periodic wrap-around: source of velocity i is
@@ -383,7 +379,23 @@ struct UDesc {
     int wsrc;        // grid offset of the NEEP source node
     int wnode;       // grid offset of the node written (corner: block origin)
     int wdx, wdy;    // corner block: grid-offset steps along x and y
-    int pad[3];
+    int gid;         // tile tables: the unknown's global index (boundary state row)
+    int level;       // tile tables: 0 owned, l > 0 halo computing 4 - l stages
+    int pad;
+};
+
+// Unknowns per tile of the fused band kernel (its block size).
+constexpr int kTileUnknowns = 128;
+
+// A bulk node at depth 0..2 next to a characteristic side (a strip node),
+// which a band tile pulls and collides itself because the tile's RK4 reads
+// its macros at t + 1.
+struct StripNode {
+    int x, y;
+    int own;     // this tile writes the node's post-collision populations
+    int gslot;   // strip slot this tile writes for t + 1 (own side, owned position), or -1
+    int tslot;   // a strip slot of the node: its macros and moments of time t
+    int fx;      // index of its population copy in shared memory (Eq. NEEP source), or -1
 };
 
 struct Band {
@@ -402,7 +414,20 @@ struct Band {
     double ihcs;     // 1 / (2 c_s)
     const UDesc* ud;
     const int2* zg;  // (node, source) grid offsets
-    double *Ub, *Ya, *Yb, *acc, *V;
+    // Tiles of the fused band kernel: tile t holds local descriptors
+    // ld[tbeg[t] .. tbeg[t + 1]) and strip nodes sn[sbeg[t] .. sbeg[t + 1]).
+    // In ld, refs >= 0 index the tile's unknowns and refs < 0 its strip
+    // nodes (-(k + 1)); vs[] and wslot are strip-node indices, wsrc the
+    // strip node's population copy (fx).
+    int n_tiles;
+    int max_nodes, max_fx;   // per tile, to size shared memory
+    const UDesc* ld;
+    const int* tbeg;
+    const StripNode* sn;
+    const int* sbeg;
+    double* Ub;      // boundary state [parity][n_unk][4] (the fused kernel); [n_unk][4]
+                     // in the allocation-free path
+    double *Ya, *Yb, *acc, *V;   // stage scratch of the allocation-free path
     int* mask;
 };
 
@@ -417,18 +442,25 @@ int launch_init(int lat, int storage, const Geom& G, const Export& E, const Band
 // Fixed inflow equilibrium at the listed nodes of one population buffer.
 int launch_inflow(int lat, int storage, const Geom& G, const int* nodes, int n, const double Uin[4],
                   void* f, cudaStream_t st);
-// One bulk step fin -> fout over the bulk nodes of region R; tmaps[0..2]
-// describe fin for the tensor copies (box depths 7, 5, 3 planes); *status
-// gets bit 1 if a copy never completed.
-int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
-                const Region& R, const CUtensorMap* tmaps, const void* fin, void* fout,
-                int par_new, int* status, cudaStream_t st);
-// The same update on the rim bands (plain loads, one thread per node).
-int launch_rim(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
-               const Rim& RM, const void* fin, void* fout, int par_new, cudaStream_t st);
+// One bulk step fin -> fout over the nodes of region R; tmaps[0..2] describe
+// fin for the tensor copies (box depths 7, 5, 3 planes); *status gets bit 1
+// if a copy never completed.
+int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Region& R,
+                const CUtensorMap* tmaps, const void* fin, void* fout, int* status,
+                cudaStream_t st);
 int launch_macros(int lat, int storage, const Geom& G, const void* f, double* rho, double* ux,
                   double* uy, double* T, int* flag, cudaStream_t st);
-int launch_boundary(int lat, int storage, const Geom& G, const Export& E, const Band& B,
-                    void* fnew, int par_t, cudaStream_t st);
+// The band of one step fin -> fnew: strip nodes, RK4 of the characteristic
+// boundary state, Dirichlet populations.  smem_pad: extra dynamic shared
+// memory per CTA (0 = none), which keeps other kernels' CTAs off its SMs.
+int launch_boundary(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
+                    const Band& B, const void* fin, void* fnew, int par_t, size_t smem_pad,
+                    cudaStream_t st);
+// Dynamic shared memory the band kernel needs per CTA (without padding).
+size_t band_dynamic_smem(int lat, int storage, const Band& B);
+// Opt the band kernel in to its dynamic shared memory (once, at creation).
+int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad);
+// Zero-gradient copies (Eq. zg-bc) in fnew, after the bulk update of x_f.
+int launch_zg(int lat, int storage, const Geom& G, const Band& B, void* fnew, cudaStream_t st);
 
 }  // namespace lbmgb
