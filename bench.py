@@ -168,13 +168,8 @@ def bulk_nodes(cfg):
 
 
 def interior_nodes(cfg):
-    """Nodes of the bulk launch: the bulk minus the three strip columns/rows
-    next to every characteristic side (the band kernel updates those)."""
-    per_x, per_y, M = _open_axes(cfg)
-    cbc = [k == "cbc" for k in cfg["sides"]]
-    w = cfg["nx"] - (0 if per_x else 2 * M) - 3 * (cbc[0] + cbc[1])
-    h = cfg["ny"] - (0 if per_y else 2 * M) - 3 * (cbc[2] + cbc[3])
-    return max(w, 0) * max(h, 0)
+    """Nodes of the bulk launch: every bulk node."""
+    return bulk_nodes(cfg)
 
 
 # -------------------------------------------------------- GPU measurement ---

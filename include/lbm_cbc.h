@@ -125,19 +125,17 @@ int lbm_set_stream(lbm_handle* h, void* stream);
 int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
                     const double* uy, const double* T, int on_device);
 
-/* Advance n time steps (asynchronous on the handle's stream).  Per step, one
- * band kernel on the handle's stream updates the three bulk columns/rows
- * next to each characteristic side and runs the boundary solver, while the
- * bulk kernel (every other bulk node) and the zero-gradient copies run on
- * the internal stream.  The result is identical to phase 0 followed by
+/* Advance n time steps (asynchronous on the handle's stream).  Per step, the
+ * band kernel (the boundary solver) runs on the handle's stream while the
+ * bulk kernel (every bulk node) and the zero-gradient copies run on the
+ * internal stream.  The result is identical to phase 0 followed by
  * phase 1. */
 int lbm_step(lbm_handle* h, int n);
 
 /* Issue one phase of one step on the handle's stream, without overlap:
- * 0 = bulk stream-collide (all but the strip nodes next to characteristic
- * sides), 1 = boundary conditions (band kernel, zero-gradient copies; ends
- * the step).  Used to time the phases separately; a step is phase 0 then
- * phase 1. */
+ * 0 = bulk stream-collide, 1 = boundary conditions (band kernel,
+ * zero-gradient copies; ends the step).  Used to time the phases
+ * separately; a step is phase 0 then phase 1. */
 int lbm_step_phase(lbm_handle* h, int phase);
 
 /* Timing hook: record the caller's CUDA events (cudaEvent_t, created by the

@@ -71,6 +71,8 @@ struct Plan {
     Region bulk{};
     std::vector<StripNode> sn;   // strip nodes of the tiles
     std::vector<int> sbeg;
+    std::vector<UDesc> ldp;      // ld and sn at a fixed stride per tile (device copies)
+    std::vector<StripNode> snp;
     std::vector<UDesc> ud;
     std::vector<UDesc> ld;       // tile tables of the fused band kernel
     std::vector<int> tbeg;
@@ -78,7 +80,7 @@ struct Plan {
     std::vector<int> inflow;
     double Uin[4] = {0, 0, 0, 0};
     size_t off_f0 = 0, off_f1 = 0, off_sU = 0, off_sN = 0, off_Ub = 0, off_ud = 0, off_ld = 0,
-           off_tb = 0, off_sn = 0, off_sb = 0, off_zg = 0, off_in = 0, off_macro = 0, off_flag = 0,
+           off_sn = 0, off_zg = 0, off_in = 0, off_macro = 0, off_flag = 0,
            total = 0;
 };
 
@@ -160,17 +162,10 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     G.by1 = pery ? ny : ny - M;
     G.plane = (long long)ny * G.nxp;
 
-    // The bulk kernel updates every bulk node except the three columns/rows
-    // next to each characteristic side (the strip nodes), which the band
-    // kernel of the same step updates itself; so the two touch disjoint
-    // nodes and run concurrently.
-    {
-        const int cW = p->side[0] == LBM_SIDE_CBC, cE = p->side[1] == LBM_SIDE_CBC;
-        const int cS = p->side[2] == LBM_SIDE_CBC, cN = p->side[3] == LBM_SIDE_CBC;
-        pl.bulk = Region{G.bx0 + 3 * cW, G.bx1 - 3 * cE, G.by0 + 3 * cS, G.by1 - 3 * cN};
-        if (pl.bulk.x1 < pl.bulk.x0) pl.bulk.x1 = pl.bulk.x0;
-        if (pl.bulk.y1 < pl.bulk.y0) pl.bulk.y1 = pl.bulk.y0;
-    }
+    // The bulk kernel updates every bulk node; the band kernel of the same
+    // step writes only boundary nodes, reads only the old buffer, so the two
+    // run concurrently.
+    pl.bulk = Region{G.bx0, G.bx1, G.by0, G.by1};
     G.tau = tau;
     G.rho0 = p->rho0;
     G.omega = 1.0 / tau;
@@ -323,7 +318,6 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
             return n;
         };
         std::vector<int> g2l(pl.ud.size(), -1);
-        std::unordered_set<int> owned_node;     // strip nodes whose populations a tile writes
         // grid node of strip slot sl: side s, depth d, position pp
         auto slot_side = [&](int sl) {
             int s = 0;
@@ -383,16 +377,14 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
                     auto it = n2l.find(key);
                     if (it != n2l.end()) return it->second;
                     n2l[key] = int(nodes.size());
-                    nodes.push_back(StripNode{x, y, 0, -1, sl, -1});
+                    nodes.push_back(StripNode{x, y, sl, -1, -1});
                     return int(nodes.size()) - 1;
                 };
+                // the strips of the tile's own positions: written by the tile
                 for (int d = 0; d < 3; ++d)
                     for (int pp = a; pp <= b; ++pp) {
                         const int sl = slot(s, d, pp);
-                        StripNode& N = nodes[node_of(sl)];
-                        N.gslot = sl;
-                        const int key = goff(N.x, N.y);
-                        if (!owned_node.count(key)) { owned_node.insert(key); N.own = 1; }
+                        nodes[node_of(sl)].gslot = sl;
                     }
                 pl.tbeg.push_back(int(pl.ld.size()));
                 for (size_t q = 0; q < list.size(); ++q) {
@@ -435,6 +427,20 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
         pl.tbeg.push_back(int(pl.ld.size()));
         pl.sbeg.push_back(int(pl.sn.size()));
         B.n_tiles = int(pl.tbeg.size()) - 1;
+        // device tables at a fixed stride per tile (kTileUnknowns unknowns,
+        // max_nodes strip nodes), so the kernel reads no offsets first;
+        // padding: level 99 (no unknown), x = -1 (no node)
+        UDesc pad_u;
+        std::memset(&pad_u, 0, sizeof pad_u);
+        pad_u.level = 99;
+        pl.ldp.assign((size_t)B.n_tiles * kTileUnknowns, pad_u);
+        pl.snp.assign((size_t)B.n_tiles * B.max_nodes, StripNode{-1, -1, 0, -1, -1});
+        for (int t = 0; t < B.n_tiles; ++t) {
+            std::copy(pl.ld.begin() + pl.tbeg[t], pl.ld.begin() + pl.tbeg[t + 1],
+                      pl.ldp.begin() + (size_t)t * kTileUnknowns);
+            std::copy(pl.sn.begin() + pl.sbeg[t], pl.sn.begin() + pl.sbeg[t + 1],
+                      pl.snp.begin() + (size_t)t * B.max_nodes);
+        }
     }
     B.viscous = p->viscous;
     B.dirichlet = p->dirichlet;
@@ -471,10 +477,8 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     pl.off_sN = take(pl.stripN_n * 8);
     pl.off_Ub = take(2 * nu * 32);
     pl.off_ud = take(nu * sizeof(UDesc));
-    pl.off_ld = take(pl.ld.size() * sizeof(UDesc));
-    pl.off_tb = take(pl.tbeg.size() * sizeof(int));
-    pl.off_sn = take(pl.sn.size() * sizeof(StripNode));
-    pl.off_sb = take(pl.sbeg.size() * sizeof(int));
+    pl.off_ld = take(pl.ldp.size() * sizeof(UDesc));
+    pl.off_sn = take(pl.snp.size() * sizeof(StripNode));
     pl.off_zg = take(pl.zg.size() * sizeof(int2));
     pl.off_in = take(pl.inflow.size() * sizeof(int));
     pl.off_macro = take((size_t)4 * nx * ny * 8);
@@ -575,9 +579,7 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     h->B.mask = nullptr;
     h->B.ud = at<UDesc>(ws, pl.off_ud);
     h->B.ld = at<UDesc>(ws, pl.off_ld);
-    h->B.tbeg = at<int>(ws, pl.off_tb);
     h->B.sn = at<StripNode>(ws, pl.off_sn);
-    h->B.sbeg = at<int>(ws, pl.off_sb);
     h->B.zg = at<int2>(ws, pl.off_zg);
     h->inflow_nodes = at<int>(ws, pl.off_in);
     h->n_inflow = int(pl.inflow.size());
@@ -609,17 +611,11 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     if (e == cudaSuccess && !pl.ud.empty())
         e = cudaMemcpyAsync(const_cast<UDesc*>(h->B.ud), pl.ud.data(), pl.ud.size() * sizeof(UDesc),
                             cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess && !pl.ld.empty())
-        e = cudaMemcpyAsync(const_cast<UDesc*>(h->B.ld), pl.ld.data(), pl.ld.size() * sizeof(UDesc),
+    if (e == cudaSuccess && !pl.ldp.empty())
+        e = cudaMemcpyAsync(const_cast<UDesc*>(h->B.ld), pl.ldp.data(), pl.ldp.size() * sizeof(UDesc),
                             cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess && !pl.tbeg.empty())
-        e = cudaMemcpyAsync(const_cast<int*>(h->B.tbeg), pl.tbeg.data(), pl.tbeg.size() * sizeof(int),
-                            cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess && !pl.sn.empty())
-        e = cudaMemcpyAsync(const_cast<StripNode*>(h->B.sn), pl.sn.data(), pl.sn.size() * sizeof(StripNode),
-                            cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess && !pl.sbeg.empty())
-        e = cudaMemcpyAsync(const_cast<int*>(h->B.sbeg), pl.sbeg.data(), pl.sbeg.size() * sizeof(int),
+    if (e == cudaSuccess && !pl.snp.empty())
+        e = cudaMemcpyAsync(const_cast<StripNode*>(h->B.sn), pl.snp.data(), pl.snp.size() * sizeof(StripNode),
                             cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && !pl.zg.empty())
         e = cudaMemcpyAsync(const_cast<int2*>(h->B.zg), pl.zg.data(), pl.zg.size() * sizeof(int2),
@@ -671,6 +667,7 @@ int band(lbm_handle* h, int par, cudaStream_t st)
     if (rc) return check_launch(h, rc, "band kernel");
     return mark(h, 4, st);
 }
+
 
 // Zero-gradient copies of step (parity par), after the bulk update.
 int zero_gradient(lbm_handle* h, int par, cudaStream_t st)
@@ -873,7 +870,8 @@ int lbm_step(lbm_handle* h, int n)
         // Fork: the band kernel on the handle's stream (queued first, so its
         // few CTAs take their SMs before the bulk's), the bulk kernel and the
         // zero-gradient copies on the internal stream; join before the next
-        // step.  The two kernels write disjoint nodes of the new buffer.
+        // step.  The kernels write disjoint nodes of the new buffer and read
+        // only the old one.
         cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
         if (e != cudaSuccess) return cuda_fail(h, e, "fork");

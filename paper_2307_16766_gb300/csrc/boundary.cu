@@ -14,6 +14,10 @@
 // linearly at the stage time, Sec. 3.3).
 #include "collide.cuh"
 
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
 namespace lbmgb {
 
 namespace {
@@ -23,6 +27,7 @@ constexpr int kBandThreads = 32;   // allocation-free path: one thread per unkno
 // issue (one warp instruction per 64 cycles on each sub-partition) bounds
 // the characteristic arithmetic; the host sizes tiles to fit.
 constexpr int kTileThreads = kTileUnknowns;
+constexpr int kCluster = 4;         // CTAs per band tile: one per characteristic component
 
 // Lab <-> local frame.  Sides: n the outward normal, t = +y (W, E) or +x
 // (S, N).  Corners: n = (sx, sy)/sqrt(2), t = n rotated by +90 degrees.
@@ -428,137 +433,428 @@ __device__ void dirichlet(const Geom& G, const Band& B, S* f, const double* Us, 
         }
 }
 
-// One tile of the boundary band per CTA: a run of positions of one
+// ---------------------------------------------------------------------------
+// The band kernel: one cluster of four CTAs per tile
+// ---------------------------------------------------------------------------
+// FP64 issues at one warp instruction per 64 cycles on each SM
+// sub-partition, so the characteristic arithmetic of an unknown is split
+// over the four CTAs of a cluster (four SMs): CTA r owns component / wave r
+// of every unknown of the tile, and the CTAs exchange their shares through
+// distributed shared memory between cluster barriers.
+
+// Row i of S (Sec. 3.1) applied to v: thermal rows (-r/2, 0, 0, 1/2),
+// (0, 0, 1, 0), (r/4, -a, 0, 1/4), (r/4, a, 0, 1/4); isothermal rows
+// (1/2, -h, 0), (0, 0, 1), (1/2, h, 0).
+template <bool TH>
+__device__ __forceinline__ double s_row(int i, double rr, double a, double h, const double* v)
+{
+    if (TH) {
+        const double rv = 0.25 * rr * v[0], q = 0.25 * v[3], av = a * v[1];
+        if (i == 0) return -2.0 * rv + 2.0 * q;
+        if (i == 1) return v[2];
+        if (i == 2) return rv - av + q;
+        return rv + av + q;
+    }
+    const double hv = h * v[1];
+    if (i == 0) return 0.5 * v[0] - hv;
+    if (i == 1) return v[2];
+    if (i == 2) return 0.5 * v[0] + hv;
+    return 0.0;
+}
+
+// Amplitude of wave i (Eq. thermal_WAV for outgoing waves; Eqs. PNR,
+// LODI-Relax, CBC-PNR, CBC-Relax for incoming ones).
+template <bool TH>
+__device__ __forceinline__ double wave(int i, const Band& B, int scheme, int mask, double lam,
+                                       double sd, double st, double sv, double dP)
+{
+    if (!TH && i == 3) return 0.0;
+    if (!((mask >> i) & 1)) return lam * sd;
+    const bool acoustic = TH ? (i >= 2) : (i != 1);
+    const double relaxP = acoustic ? B.beta_P * dP : 0.0;
+    if (scheme == SCH_LODI) return 0.0;
+    if (scheme == SCH_LODI_RELAX) return B.alpha_T * (B.t_inf - st) + relaxP;
+    if (scheme == SCH_CBC) return st + sv;
+    return st + sv + B.alpha_T * (B.t_inf - st) + relaxP;
+}
+
+// Share c of the mesoscopic viscous vector (see vis_meso): V1 for c = 1,
+// V2 for c = 2; V3 is split, its conductive part for c = 0 and its
+// viscous-heating part for c = 3 (V0 = 0).
+template <bool TH>
+__device__ double vis_meso_c(int c, const Geom& G, const double* SU, const double* SN,
+                             const UDesc& D, double cs2)
+{
+    if (!TH && (c == 0 || c == 3)) return 0.0;
+    const int s = D.kind;
+    const int an = s < 2 ? 0 : 1, at = 1 - an;
+    const double sn = (s == 0 || s == 2) ? -1.0 : 1.0;
+    auto h = [&](int k, int m) -> double {
+        const double* n = SN + 5LL * D.vs[k];
+        const double* u = SU + 4LL * D.vs[k];
+        switch (m) {
+        case 0: return an == 0 ? n[0] : n[2];
+        case 1: return sn * n[1];
+        case 2: return an == 0 ? n[2] : n[0];
+        case 3: return sn * n[3 + an];
+        case 4: return n[3 + at];
+        case 5: return sn * u[1 + an];
+        default: return u[1 + at];
+        }
+    };
+    auto dn = [&](int m) { return 0.5 * (3.0 * h(0, m) - 4.0 * h(1, m) + h(2, m)); };
+    auto dt = [&](int m) {
+        if (D.tmode == 0) return 0.5 * (h(3, m) - h(4, m));
+        return double(D.tmode) * 0.5 * (3.0 * h(0, m) - 4.0 * h(3, m) + h(4, m));
+    };
+    if (c == 3) {
+        const double nu = (G.tau - 0.5) * cs2;
+        const double e1 = dn(5) - dt(6), e2 = dn(6) + dt(5);
+        return nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
+    }
+    const double irho = 1.0 / (G.rho0 + SU[4LL * D.vs[0]]);
+    if (c == 1) return (dn(0) + dt(1)) * irho;
+    if (c == 2) return (dn(1) + dt(2)) * irho;
+    return -(dn(3) + dt(4)) * irho * (1.0 / cs2);
+}
+
+// Share c of the "-FD" viscous vector (see vis_fd), split as vis_meso_c:
+// V3 = (c = 0 part) + (c = 3 part).
+template <bool TH>
+__device__ double vis_fd_c(int c, const Geom& G, const Band& B, const Ctx& X0, const UDesc& D, int u,
+                           double cs2)
+{
+    if (!TH && (c == 0 || c == 3)) return 0.0;
+    const int kind = D.kind;
+    double U[4], A[4], Bv[4], Cv[4], Tp[4], Tm[4], dnn[4], d1n[4];
+    fetch_local(X0, u, kind, 0.0, U);
+    fetch_local(X0, D.nb[1], kind, 0.0, Bv);
+    fetch_local(X0, D.nb[4], kind, 0.0, Tp);
+    fetch_local(X0, D.nb[5], kind, 0.0, Tm);
+    if (D.j == B.M) {
+        fetch_local(X0, D.nb[2], kind, 0.0, A);
+        fetch_local(X0, D.nb[3], kind, 0.0, Cv);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            dnn[m] = 2.0 * U[m] - 5.0 * Bv[m] + 4.0 * A[m] - Cv[m];
+            d1n[m] = 0.5 * (3.0 * U[m] - 4.0 * Bv[m] + A[m]);
+        }
+    } else {
+        fetch_local(X0, D.nb[0], kind, 0.0, A);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            dnn[m] = A[m] - 2.0 * U[m] + Bv[m];
+            d1n[m] = 0.5 * (A[m] - Bv[m]);
+        }
+    }
+    const double nu = (G.tau - 0.5) * cs2;
+    if (c == 1) return nu * (dnn[1] + (Tp[1] - 2.0 * U[1] + Tm[1]));
+    if (c == 2) return nu * (dnn[2] + (Tp[2] - 2.0 * U[2] + Tm[2]));
+    if (c == 0) return 2.0 * nu * (dnn[3] + (Tp[3] - 2.0 * U[3] + Tm[3]));
+    const double d1t1 = 0.5 * (Tp[1] - Tm[1]), d1t2 = 0.5 * (Tp[2] - Tm[2]);
+    const double e1 = d1n[1] - d1t2, e2 = d1n[2] + d1t1;
+    return nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
+}
+
+// Lab component m of a local-frame vector (m = 1, 2 need k1 and k2).
+__device__ __forceinline__ double lab_component(int m, int kind, double r, double k0, double k1,
+                                                double k2, double k3)
+{
+    if (m == 0) return k0;
+    if (m == 3) return k3;
+    switch (kind) {
+    case 0: return m == 1 ? -k1 : k2;
+    case 1: return m == 1 ? k1 : k2;
+    case 2: return m == 1 ? k2 : -k1;
+    case 3: return m == 1 ? k2 : k1;
+    default: {
+        const int c = kind - 4;
+        const double n0 = (c & 1) ? r : -r, n1 = (c & 2) ? r : -r;
+        return m == 1 ? k1 * n0 - k2 * n1 : k1 * n1 + k2 * n0;
+    }
+    }
+}
+
+// One tile of the boundary band per cluster: a run of positions of one
 // characteristic side (all M layers, and the corner next to it on a W/E
 // side), plus the halo its four RK4 stages need (Sec. 3.3).
 //
-// 1. Strip nodes: the tile pulls and collides the bulk nodes at depths 0..2
-//    next to the side that its stencils read (Eqs. lbe, bgk), keeps their
-//    macros of t (loaded) and t + 1 (computed) in shared memory, writes the
-//    populations of the nodes it owns and the strips of its own positions
-//    for the next step.
+// 1. Strip nodes: the cluster pulls the bulk nodes at depths 0..2 next to
+//    the side that its stencils read (Eq. lbe) for their macros at t + 1
+//    (Eq. macro), and keeps them with the stored macros and moments of t in
+//    every CTA's shared memory; for its own positions it also writes the
+//    macros and non-equilibrium moments of t + 1 for the next step.  (The
+//    bulk kernel updates the populations of these nodes.)
 // 2. RK4 (Sec. 3.3, "Time integration"): the local table lists the tile's
 //    unknowns by level: level 0 are owned, level l computes the first 4 - l
-//    stages, level 4 only supplies U(t); stage values live in shared memory.
+//    stages, level 4 only supplies U(t).  Per stage, CTA r computes its
+//    share of the characteristic system (1/rho, sqrt(theta),
+//    1/sqrt(theta), P - P_inf and the transversal terms), then wave r,
+//    then lab component r of the right-hand side and of the stage value.
 //    Stage 0 freezes the viscous vector and the incoming-wave mask of time
-//    t.  After stage 3 the owners write U(t + 1) and the mesoscopic
-//    Dirichlet populations (equilibrium or Eq. NEEP).
+//    t.
+// 3. The owners write U(t + 1) and the mesoscopic Dirichlet populations
+//    (equilibrium or Eq. NEEP), shared out over the four CTAs.
 template <int LAT, typename S>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads)
     k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
            int par_t)
 {
     using L = Lat<LAT>;
     using C = typename Store<S>::C;
-    __shared__ __align__(16) double Ys[kTileThreads * 4];
+    constexpr bool TH = L::THERMAL;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = int(cl.block_rank());
+    const int tile = blockIdx.x / kCluster;
+    const int l = threadIdx.x;
+    __shared__ __align__(16) double Ys[kTileThreads * 4];   // stage values, lab frame
+    __shared__ __align__(16) double Xp[kTileThreads * 8];   // shares of the characteristic system
+    __shared__ __align__(16) double Xw[kTileThreads * 4];   // wave amplitudes
+    __shared__ __align__(16) double Xv[kTileThreads * 4];   // viscous vector (local frame, frozen)
     extern __shared__ __align__(16) double dyn[];
     double* SUt = dyn;                              // [max_nodes][4] macros of t
     double* SUt1 = SUt + 4 * B.max_nodes;           // [max_nodes][4] macros of t + 1
     double* SNt = SUt1 + 4 * B.max_nodes;           // [max_nodes][5] moments of t
-    S* Fx = reinterpret_cast<S*>(SNt + 5 * B.max_nodes);   // [max_fx][Q]
-    const int tile = blockIdx.x;
-    const int l = threadIdx.x;
+    S* Fx = reinterpret_cast<S*>(SNt + 5 * B.max_nodes);   // [max_fx][Q], node k in CTA k % 4
+    auto bcast = [&](double* p, double v) {
+#pragma unroll
+        for (int q = 0; q < kCluster; ++q) *cl.map_shared_rank(p, q) = v;
+    };
+    // Descriptors first, all at once: under a saturated memory system each
+    // dependent global round trip costs microseconds.
+    const int ns = B.max_nodes;
+    const StripNode* snt = B.sn + (long long)tile * ns;
+    const int kp = rank + kCluster * l;             // the strip node this thread pulls
+    StripNode Na{-1, -1, 0, -1, -1}, Nb{-1, -1, 0, -1, -1};
+    if (l < ns) Na = snt[l];
+    if (kp < ns) Nb = snt[kp];
+    const UDesc D = B.ld[(long long)tile * kTileUnknowns + l];
+    cl.sync();                          // every CTA of the cluster runs before any remote store
 
-    // 1. strip nodes
-    {
-        const int sb = B.sbeg[tile], ns = B.sbeg[tile + 1] - sb;
-        const double* gU = E.stripU + (long long)par_t * E.nslots * 4;
-        const double* gN = E.stripN + (long long)par_t * E.nslots * 5;
-        double* wU = E.stripU + (long long)(par_t ^ 1) * E.nslots * 4;
-        double* wN = E.stripN + (long long)(par_t ^ 1) * E.nslots * 5;
-        const double fac = 1.0 - 0.5 / G.tau;
-        for (int k = l; k < ns; k += kTileThreads) {
-            const StripNode N = B.sn[sb + k];
-            C g[L::Q];
-            pull_plain<LAT, S, C>(G, O, fin, N.x, N.y, g);
-            if (Store<S>::SCALED) {
+    // 1. strip nodes: macros of t and moments of t for every CTA; macros of
+    //    t + 1 (pull and Eq. macro) by CTA k % kCluster for node k, shared
+    //    out; post-collision populations of Eq. NEEP sources kept locally
+    const double* gU = E.stripU + (long long)par_t * E.nslots * 4;
+    const double* gN = E.stripN + (long long)par_t * E.nslots * 5;
+    auto load_t = [&](int k, int ts) {
 #pragma unroll
-                for (int i = 0; i < L::Q; ++i) g[i] *= C(L::w(i));
-            }
-            S* out = f + (N.y * G.nxp + N.x);
-            S* fx = N.fx >= 0 ? Fx + N.fx * L::Q : nullptr;
-            const Moments<LAT, C> m = collide<LAT, C>(G, g, [&](int i, C v) {
-                if (Store<S>::SCALED) v *= C(1.0 / L::w(i));
-                if (N.own) Store<S>::put(out + O.st[i], v);
-                if (fx) Store<S>::put(fx + i, v);
-            });
-            const double U1[4] = {double(m.s0), double(m.ux), double(m.uy), double(m.dT)};
+        for (int c = 0; c < 4; ++c) SUt[4 * k + c] = gU[4LL * ts + c];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) SUt1[4 * k + c] = U1[c];
+        for (int c = 0; c < 5; ++c) SNt[5 * k + c] = gN[5LL * ts + c];
+    };
+    auto pull_t1 = [&](int k, const StripNode& N) {
+        C g[L::Q];
+        pull_plain<LAT, S, C>(G, O, fin, N.x, N.y, g);
+        if (Store<S>::SCALED) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) SUt[4 * k + c] = gU[4LL * N.tslot + c];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) SNt[5 * k + c] = gN[5LL * N.tslot + c];
-            if (N.gslot >= 0) {
-                double N1[5];
-                neq_moments<LAT, C>(g, m, fac, N1);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) wU[4LL * N.gslot + c] = U1[c];
-#pragma unroll
-                for (int c = 0; c < 5; ++c) wN[5LL * N.gslot + c] = N1[c];
-            }
+            for (int i = 0; i < L::Q; ++i) g[i] *= C(L::w(i));
         }
-    }
-
-    // 2. RK4 of the characteristic boundary state
-    const int beg = B.tbeg[tile], n = B.tbeg[tile + 1] - beg;
-    UDesc D;
-    int lev = 99;                       // > 4: no unknown on this thread
+        Moments<LAT, C> m;
+        if (N.fx >= 0) {
+            S* fx = Fx + N.fx * L::Q;
+            m = collide<LAT, C>(G, g, [&](int i, C v) {
+                if (Store<S>::SCALED) v *= C(1.0 / L::w(i));
+                Store<S>::put(fx + i, v);
+            });
+        } else {
+            m = moments<LAT, C>(g, rho0_of<C>(G));
+        }
+        const double U1[4] = {double(m.s0), double(m.ux), double(m.uy), double(m.dT)};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bcast(SUt1 + 4 * k + c, U1[c]);
+        if (N.gslot >= 0) {             // the strips of t + 1, for the next step
+            double N1[5];
+            neq_moments<LAT, C>(g, m, 1.0 - 0.5 / G.tau, N1);
+            double* u = E.stripU + ((long long)(par_t ^ 1) * E.nslots + N.gslot) * 4;
+            double* q = E.stripN + ((long long)(par_t ^ 1) * E.nslots + N.gslot) * 5;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) u[c] = U1[c];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) q[c] = N1[c];
+        }
+    };
+    // U(t) of the tile's unknowns: every CTA loads its own copy
+    const int lev = D.level;            // > 4: no unknown on this thread
     double U0[4] = {0.0, 0.0, 0.0, 0.0};
-    if (l < n) {
-        D = B.ld[beg + l];
-        lev = D.level;
+    if (lev <= 4) {
         const double2* p = reinterpret_cast<const double2*>(B.Ub + ((long long)par_t * B.n_unk + D.gid) * 4);
         const double2 a = p[0], b = p[1];
         U0[0] = a.x; U0[1] = a.y; U0[2] = b.x; U0[3] = b.y;
+    }
+    if (Na.x >= 0) load_t(l, Na.tslot);
+    if (Nb.x >= 0) pull_t1(kp, Nb);
+    for (int k = l + kTileThreads; k < ns; k += kTileThreads) {
+        const StripNode N = snt[k];
+        if (N.x >= 0) load_t(k, N.tslot);
+    }
+    for (int k = kp + kCluster * kTileThreads; k < ns; k += kCluster * kTileThreads) {
+        const StripNode N = snt[k];
+        if (N.x >= 0) pull_t1(k, N);
+    }
+    if (lev <= 4) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) Ys[4 * l + m] = U0[m];
     }
-    __syncthreads();
+    cl.sync();
+
+    // 2. RK4, component rank of every unknown
     Ctx X;
     X.Y = Ys;
     X.St = SUt;
     X.St1 = SUt1;
-    double V[4] = {0.0, 0.0, 0.0, 0.0}, acc[4] = {0.0, 0.0, 0.0, 0.0}, k[4];
+    const double rho0 = G.rho0, cs2 = L::CS2, kr = B.kR;
+    const bool corner = lev <= 4 && D.kind >= 4;
+    const int scheme = corner ? SCH_LODI : (lev <= 4 ? B.scheme[D.kind] : 0);
+    const bool cbc = scheme == SCH_CBC || scheme == SCH_CBC_RELAX;
+    double acc = 0.0, kc = 0.0;         // lab component rank of sum k and of the last k
+    const double u0r = rank == 0 ? U0[0] : rank == 1 ? U0[1] : rank == 2 ? U0[2] : U0[3];
     int mask = 0;
     for (int stage = 0; stage < 4; ++stage) {
         const bool comp = lev <= 3 - stage;
+        X.frac = stage == 0 ? 0.0 : (stage == 3 ? 1.0 : 0.5);
+        double Ul[4] = {0.0, 0.0, 0.0, 0.0}, dUn[4] = {0.0, 0.0, 0.0, 0.0};
+        double Up[4] = {0.0, 0.0, 0.0, 0.0}, Um[4] = {0.0, 0.0, 0.0, 0.0};
+        // A: shares
         if (comp) {
-            X.frac = stage == 0 ? 0.0 : (stage == 3 ? 1.0 : 0.5);
-            if (stage == 0) {
-                double Ul[4];
-                to_local(D.kind, B.kR, U0, Ul);
-                mask = incoming_mask<L::THERMAL>(char_sys<L::THERMAL>(B, G.rho0, Ul));
-                if (D.kind < 4 && B.viscous == VIS_FD) vis_fd<L::THERMAL>(G, B, X, D, l, L::CS2, V);
-                else if (D.kind < 4 && B.viscous == VIS_MESO) vis_meso<L::THERMAL>(G, SUt, SNt, D, L::CS2, V);
+            const int kind = D.kind;
+            double A[4], Bv[4];
+            fetch_local(X, l, kind, kr, Ul);
+            if (corner) {
+                // LODI along the outward diagonal, one-sided difference of
+                // spacing sqrt(2) through the two diagonal bulk nodes
+                fetch_local(X, D.nb[0], kind, kr, A);
+                fetch_local(X, D.nb[1], kind, kr, Bv);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) dUn[m] = (3.0 * Ul[m] - 4.0 * A[m] + Bv[m]) * B.kC;
+            } else {
+                if (D.j == B.M) {        // Eq. FD-dx-bw at the outermost layer
+                    fetch_local(X, D.nb[1], kind, kr, A);
+                    fetch_local(X, D.nb[2], kind, kr, Bv);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) dUn[m] = 0.5 * (3.0 * Ul[m] - 4.0 * A[m] + Bv[m]);
+                } else {                 // Eq. FD-dx-center at inner layers
+                    fetch_local(X, D.nb[0], kind, kr, A);
+                    fetch_local(X, D.nb[1], kind, kr, Bv);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) dUn[m] = 0.5 * (A[m] - Bv[m]);
+                }
+                fetch_local(X, D.nb[4], kind, kr, Up);
+                fetch_local(X, D.nb[5], kind, kr, Um);
             }
-            unknown_rhs<LAT>(G, B, X, D, l, V, mask, k);
+            double* xp = Xp + 8 * l;
+            if (rank == 0) {
+                bcast(xp + 0, 1.0 / (rho0 + Ul[0]));
+                bcast(xp + 1, corner ? 0.0 : -0.5 * ((rho0 + Up[0]) * Up[2] - (rho0 + Um[0]) * Um[2]));
+            } else if (rank == 1) {
+                if (TH) bcast(xp + 2, sqrt(1.0 + Ul[3]));
+                bcast(xp + 3, corner ? 0.0 : -Ul[2] * (0.5 * (Up[1] - Um[1])));
+            } else if (rank == 2) {
+                if (TH) bcast(xp + 4, rsqrt(1.0 + Ul[3]));
+                const double dP = TH ? cs2 * (Ul[0] + rho0 * Ul[3] + Ul[0] * Ul[3]) : cs2 * Ul[0];
+                bcast(xp + 5, corner ? 0.0 : dP - B.pdev[kind]);
+                if (!TH) bcast(xp + 6, 0.5 * (Up[0] - Um[0]));
+            } else if (TH) {
+                // rho T - rho0 = drho + rho0 dT + drho dT
+                bcast(xp + 6, 0.5 * ((Up[0] + rho0 * Up[3] + Up[0] * Up[3]) -
+                                     (Um[0] + rho0 * Um[3] + Um[0] * Um[3])));
+                bcast(xp + 7, corner ? 0.0 : -0.5 * ((1.0 + Up[3]) * Up[2] - (1.0 + Um[3]) * Um[2]));
+            }
+            if (stage == 0) {
+                double v = 0.0;
+                if (!corner && B.viscous == VIS_FD) v = vis_fd_c<TH>(rank, G, B, X, D, l, cs2);
+                else if (!corner && B.viscous == VIS_MESO) v = vis_meso_c<TH>(rank, G, SUt, SNt, D, cs2);
+                bcast(Xv + 4 * l + rank, v);
+            }
+        }
+        cl.sync();
+        // B: wave rank
+        double TT[4] = {0.0, 0.0, 0.0, 0.0}, V[4] = {0.0, 0.0, 0.0, 0.0};
+        double ir = 0.0, bb = 0.0, csr = 0.0;
+        if (comp) {
+            const double* xp = Xp + 8 * l;
+            const double irho = xp[0], rho = rho0 + Ul[0];
+            const double d_ut = 0.5 * (Up[2] - Um[2]);
+            double lam[4], rr = 0.0, a = 0.0, h = 0.0;
+            if (TH) {
+                const double sth = xp[2], isth = xp[4], th = 1.0 + Ul[3];
+                rr = th * irho;
+                ir = rho * isth * isth;
+                a = sth * B.kA;
+                bb = isth * B.kB;
+                const double c = sth * B.kB;
+                lam[0] = Ul[1];
+                lam[1] = Ul[1];
+                lam[2] = Ul[1] - c;
+                lam[3] = Ul[1] + c;
+                if (!corner) {
+                    TT[0] = xp[1];
+                    TT[1] = xp[3];
+                    TT[2] = -cs2 * irho * xp[6] - Ul[2] * d_ut;
+                    TT[3] = xp[7];
+                }
+            } else {
+                h = rho * B.ihcs;
+                csr = B.cs * irho;
+                lam[0] = Ul[1] - B.cs;
+                lam[1] = Ul[1];
+                lam[2] = Ul[1] + B.cs;
+                lam[3] = 0.0;
+                if (!corner) {
+                    TT[0] = xp[1];
+                    TT[1] = xp[3];
+                    TT[2] = -cs2 * irho * xp[6] - Ul[2] * d_ut;
+                }
+            }
+            if (stage == 0)
+                for (int i = 0; i < (TH ? 4 : 3); ++i)
+                    if (lam[i] < 0.0) mask |= 1 << i;
+            V[1] = Xv[4 * l + 1];
+            V[2] = Xv[4 * l + 2];
+            V[3] = TH ? Xv[4 * l + 0] + Xv[4 * l + 3] : 0.0;   // V0 = 0; V3 from two shares
+            const double lr = rank == 0 ? lam[0] : rank == 1 ? lam[1] : rank == 2 ? lam[2] : lam[3];
+            const double w = wave<TH>(rank, B, scheme, mask, lr, s_row<TH>(rank, rr, a, h, dUn),
+                                      s_row<TH>(rank, rr, a, h, TT), s_row<TH>(rank, rr, a, h, V),
+                                      xp[5]);
+            bcast(Xw + 4 * l + rank, w);
+        }
+        cl.sync();
+        // C: lab component rank of the right-hand side; RK4 update
+        if (comp) {
+            const double* w = Xw + 4 * l;
+            double kl[4] = {0.0, 0.0, 0.0, 0.0};
+            if (rank == 0) kl[0] = -(TH ? (w[2] + w[3] - w[0]) * ir : w[0] + w[2]);
+            if (rank == 3) kl[3] = TH ? -(w[0] + w[2] + w[3]) : 0.0;
+            if (rank == 1 || rank == 2) {
+                kl[1] = -(TH ? bb * (w[3] - w[2]) : csr * (w[2] - w[0]));
+                kl[2] = -w[1];
+            }
+            if (cbc)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) kl[m] += TT[m] + V[m];
+            kc = lab_component(rank, D.kind, kr, kl[0], kl[1], kl[2], kl[3]);
             if (stage < 3) {
                 const double wk = stage == 0 ? 1.0 : 2.0;
-#pragma unroll
-                for (int m = 0; m < 4; ++m) acc[m] = (stage == 0 ? 0.0 : acc[m]) + wk * k[m];
+                const double hk = stage == 2 ? 1.0 : 0.5;
+                acc = (stage == 0 ? 0.0 : acc) + wk * kc;
+                bcast(Ys + 4 * l + rank, u0r + hk * kc);
+            } else {
+                // RK4: U(t + 1) = U(t) + (k1 + 2 k2 + 2 k3 + k4) / 6
+                const double un = u0r + (acc + kc) * (1.0 / 6.0);
+                B.Ub[((long long)(par_t ^ 1) * B.n_unk + D.gid) * 4 + rank] = un;
+                bcast(Ys + 4 * l + rank, un);
             }
         }
-        if (stage == 3) break;
-        __syncthreads();                // every stage-s value has been read
-        if (comp) {                     // read at the next stage by neighbours one level in
-            const double hk = stage == 2 ? 1.0 : 0.5;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) Ys[4 * l + m] = U0[m] + hk * k[m];
-        }
-        __syncthreads();
+        cl.sync();
     }
-    if (lev != 0) return;
-    // RK4: U(t + 1) = U(t) + (k1 + 2 k2 + 2 k3 + k4) / 6, acc = k1 + 2 k2 + 2 k3
-    double Unew[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) Unew[m] = U0[m] + (acc[m] + k[m]) * (1.0 / 6.0);
-    double2* q = reinterpret_cast<double2*>(B.Ub + ((long long)(par_t ^ 1) * B.n_unk + D.gid) * 4);
-    q[0] = make_double2(Unew[0], Unew[1]);
-    q[1] = make_double2(Unew[2], Unew[3]);
-    const bool neep = B.dirichlet == 1;
-    dirichlet<LAT, S>(G, B, f, neep ? SUt1 + 4 * D.wslot : nullptr,
-                      neep ? Fx + D.wsrc * L::Q : nullptr, D, Unew);
+
+    // 3. Dirichlet populations of unknown l, on CTA l % kCluster
+    if (lev == 0 && l % kCluster == rank) {
+        const double Unew[4] = {Ys[4 * l], Ys[4 * l + 1], Ys[4 * l + 2], Ys[4 * l + 3]};
+        const bool neep = B.dirichlet == 1;
+        const S* fs = neep ? cl.map_shared_rank(Fx + D.wsrc * L::Q, D.wslot % kCluster) : nullptr;
+        dirichlet<LAT, S>(G, B, f, neep ? SUt1 + 4 * D.wslot : nullptr, fs, D, Unew);
+    }
+    cl.sync();                          // no CTA leaves while its Fx may be read
 }
 
 // Zero gradient (Eq. zg-bc): the post-collision populations of x_f.
@@ -584,16 +880,16 @@ int boundary_t(const Geom& G, const Offsets& O, const Export& E, const Band& B, 
 {
     if (B.n_tiles == 0) return 0;
     const size_t smem = band_smem<LAT, S>(B) + smem_pad;
-    k_band<LAT, S><<<B.n_tiles, kTileThreads, smem, st>>>(G, O, B, E, static_cast<const S*>(fin),
-                                                         static_cast<S*>(fnew), par_t);
+    k_band<LAT, S><<<B.n_tiles * kCluster, kTileThreads, smem, st>>>(
+        G, O, B, E, static_cast<const S*>(fin), static_cast<S*>(fnew), par_t);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <int LAT, typename S>
 int prepare_t(const Band& B, size_t smem_pad)
 {
+    // the 48 KB default covers static + dynamic shared memory: always opt in
     const size_t smem = band_smem<LAT, S>(B) + smem_pad;
-    if (smem <= 48 * 1024) return 0;
     return cudaFuncSetAttribute(k_band<LAT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(smem)) == cudaSuccess ? 0 : -1;
 }

@@ -1,9 +1,7 @@
 // bulk.cu -- bulk kernels of the thermal lattice Boltzmann step.
 //
 //  k_bulk     fused pull-stream + moments + BGK collide (Eqs. lbe, macro,
-//             bgk with the equilibria of Eqs. feq-3/feq-4) on every bulk node
-//             except the three columns/rows next to each characteristic side,
-//             which the band kernel (boundary.cu) updates itself.
+//             bgk with the equilibria of Eqs. feq-3/feq-4) on every bulk node.
 //  k_init     f = f^eq(U0) on every node and the strips of time 0.
 //  k_inflow   the fixed inflow equilibrium on the inflow nodes of a buffer.
 //  k_init_band  boundary ODE state of time 0.

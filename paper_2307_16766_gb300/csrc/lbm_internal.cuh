@@ -387,15 +387,15 @@ struct UDesc {
 // Unknowns per tile of the fused band kernel (its block size).
 constexpr int kTileUnknowns = 128;
 
-// A bulk node at depth 0..2 next to a characteristic side (a strip node),
-// which a band tile pulls and collides itself because the tile's RK4 reads
-// its macros at t + 1.
+// A bulk node at depth 0..2 next to a characteristic side (a strip node)
+// that a band tile reads.  The bulk kernel updates it; the tile pulls it
+// again for its macros and non-equilibrium moments at t + 1 (and, for
+// Eq. NEEP sources, its post-collision populations).
 struct StripNode {
     int x, y;
-    int own;     // this tile writes the node's post-collision populations
-    int gslot;   // strip slot this tile writes for t + 1 (own side, owned position), or -1
     int tslot;   // a strip slot of the node: its macros and moments of time t
     int fx;      // index of its population copy in shared memory (Eq. NEEP source), or -1
+    int gslot;   // strip slot this tile writes for t + 1 (own side, owned position), or -1
 };
 
 struct Band {
@@ -414,17 +414,16 @@ struct Band {
     double ihcs;     // 1 / (2 c_s)
     const UDesc* ud;
     const int2* zg;  // (node, source) grid offsets
-    // Tiles of the fused band kernel: tile t holds local descriptors
-    // ld[tbeg[t] .. tbeg[t + 1]) and strip nodes sn[sbeg[t] .. sbeg[t + 1]).
-    // In ld, refs >= 0 index the tile's unknowns and refs < 0 its strip
-    // nodes (-(k + 1)); vs[] and wslot are strip-node indices, wsrc the
-    // strip node's population copy (fx).
+    // Tiles of the band kernel: tile t holds local descriptors
+    // ld[t * kTileUnknowns + l] (padding: level 99) and strip nodes
+    // sn[t * max_nodes + k] (padding: x = -1).  In ld, refs >= 0 index the
+    // tile's unknowns and refs < 0 its strip nodes (-(k + 1)); vs[] and
+    // wslot are strip-node indices, wsrc the strip node's population copy
+    // (fx).
     int n_tiles;
     int max_nodes, max_fx;   // per tile, to size shared memory
     const UDesc* ld;
-    const int* tbeg;
     const StripNode* sn;
-    const int* sbeg;
     double* Ub;      // boundary state [parity][n_unk][4] (the fused kernel); [n_unk][4]
                      // in the allocation-free path
     double *Ya, *Yb, *acc, *V;   // stage scratch of the allocation-free path
