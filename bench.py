@@ -279,6 +279,23 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
     return res
 
 
+def max_over_ranks(seconds, world):
+    """The slowest rank's timed-region length (replicas run in lock step
+    between the barriers; the job is as fast as its slowest GPU)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes, steps, world, seconds):
+    """Lattice updates of all replicas per second / 1e6 (weak scaling)."""
+    return nodes * steps * world / seconds / 1e6
+
+
 def cpu_baseline(cfg, fields, seconds=15.0):
     import oracle
     s = oracle.Sim(cfg).init(*fields)
@@ -343,13 +360,8 @@ def main():
 
     K = args.steps
     nodes = args.nx * args.ny
-    step_s = res["step_ms_total"] / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([step_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_s = float(t.item())
-    value = nodes * K * world / step_s / 1e6
+    step_s = max_over_ranks(res["step_ms_total"] / 1e3, world)
+    value = whole_job_mlups(nodes, K, world, step_s)
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
