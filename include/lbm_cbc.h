@@ -50,8 +50,9 @@ extern "C" {
 #define LBM_ERR_TIMEOUT    -6   /* a bounded device-side wait gave up           */
 
 /* Velocity sets (Appendix B): D2Q9 (M = 1, isothermal, second-order
- * equilibrium) and D2Q37 (M = 3, fourth-order Hermite equilibrium, Eq. feq-4). */
-enum lbm_lattice { LBM_D2Q9 = 0, LBM_D2Q37 = 1 };
+ * equilibrium), D2Q37 (M = 3, fourth-order Hermite equilibrium, Eq. feq-4)
+ * and D2Q17 (M = 3, third-order equilibrium, Eq. feq-3). */
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D2Q37 = 1, LBM_D2Q17 = 2 };
 
 /* Storage of the populations, always shifted by the rest state,
  * g_i = f_i - w_i rho0.  F64: double, FP64 arithmetic.  F32: float, FP32
@@ -197,8 +198,8 @@ void lbm_destroy(lbm_handle* h);
  *             LBM_VISCOUS_MESO, otherwise may be NULL.
  *   stream    cudaStream_t (NULL = legacy default); the call is asynchronous.
  * Only p->scheme[side], p->viscous, alpha_T, beta_P, t_inf, p_inf[side] and
- * rho0 are read.  length * M may not exceed 12288 (4096 positions on D2Q37,
- * 12288 on D2Q9); larger sides are rejected with LBM_ERR_ARG and a message
+ * rho0 are read.  length * M may not exceed 12288 (4096 positions on D2Q37
+ * and D2Q17, 12288 on D2Q9); larger sides are rejected with LBM_ERR_ARG and a message
  * on stderr.
  *
  * Nothing is allocated: the RK4 stage scratch lives in one fixed ~1.6 MB

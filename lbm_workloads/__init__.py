@@ -17,8 +17,9 @@ import numpy as np
 
 # Lattice sound speeds squared (Appendix B), used only to scale inputs:
 # background velocity Ma * c_s and the default target pressure rho0 c_s^2.
-CS2 = {"D2Q9": 1.0 / 3.0, "D2Q37": 0.6979533220196830882384091}
-M_OF = {"D2Q9": 1, "D2Q37": 3}
+CS2 = {"D2Q9": 1.0 / 3.0, "D2Q37": 0.6979533220196830882384091,
+       "D2Q17": 0.3702518670183398497189151}
+M_OF = {"D2Q9": 1, "D2Q37": 3, "D2Q17": 3}
 
 _MASK64 = (1 << 64) - 1
 

@@ -5,7 +5,7 @@ the CPU-baseline / reference leg of ``bench.py``.  The product package never
 imports it, and the oracle shares no code with the CUDA path.
 
 A run is described by a plain dict (see ``lbm_workloads``) with the keys
-``lattice`` ("D2Q9" | "D2Q37"), ``nx``, ``ny``, ``tau``, ``rho0``, ``sides``
+``lattice`` ("D2Q9" | "D2Q37" | "D2Q17"), ``nx``, ``ny``, ``tau``, ``rho0``, ``sides``
 (four of "periodic" | "cbc" | "inflow" | "zg", order W, E, S, N),
 ``schemes`` (four of "lodi" | "lodi_relax" | "cbc" | "cbc_relax"),
 ``viscous`` ("meso" | "fd" | "off"), ``dirichlet`` ("eq" | "neep"), ``alpha_T``, ``beta_P``,
@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-LATTICES = {"D2Q9": 0, "D2Q37": 1}
+LATTICES = {"D2Q9": 0, "D2Q37": 1, "D2Q17": 2}
 SIDES = {"periodic": 0, "cbc": 1, "inflow": 2, "zg": 3}
 SCHEMES = {"lodi": 0, "lodi_relax": 1, "cbc": 2, "cbc_relax": 3}
 DIRICHLET = {"eq": 0, "neep": 1}
@@ -141,7 +141,7 @@ def char_matrices(lattice, rho0, Ul):
     lam = np.zeros(4)
     u = _f64(Ul)
     lib().orc_char_matrices(LATTICES[lattice], rho0, _dp(u), _dp(S), _dp(Si), _dp(lam))
-    n = 4 if lattice == "D2Q37" else 3
+    n = 3 if lattice == "D2Q9" else 4
     return S.reshape(4, 4)[:n, :n], Si.reshape(4, 4)[:n, :n], lam[:n]
 
 

@@ -41,6 +41,7 @@
 
 typedef struct {
     int q, M, thermal;
+    int order;         /* order of the Hermite expansion of f^eq: 2, 3 or 4 */
     double cs2, cs;
     int c[QMAX][2];
     double w[QMAX];
@@ -72,6 +73,7 @@ static int make_lattice(int lattice, lattice_t* L)
         /* Appendix B, Tab. d2q9: c_s = 1/sqrt(3). */
         L->M = 1;
         L->thermal = 0;
+        L->order = 2;
         L->cs2 = 1.0 / 3.0;
         add_class(L, 0, 0, 4.0 / 9.0);
         add_class(L, 1, 0, 1.0 / 9.0);
@@ -82,6 +84,7 @@ static int make_lattice(int lattice, lattice_t* L)
          * eighth order; they agree with the printed 14-decimal weights. */
         L->M = 3;
         L->thermal = 1;
+        L->order = 4;
         L->cs2 = 0.6979533220196830882384091;
         add_class(L, 0, 0, 0.23315066913235250229);
         add_class(L, 1, 0, 0.10730609154221900241);
@@ -91,6 +94,21 @@ static int make_lattice(int lattice, lattice_t* L)
         add_class(L, 2, 2, 0.0010119375926735754754);
         add_class(L, 3, 0, 0.00024530102775771734547);
         add_class(L, 3, 1, 0.0002834142529941982174);
+    } else if (lattice == ORC_D2Q17) {
+        /* Appendix B, Tab. d2q17: the printed closed-form weights, M = 3,
+         * third-order equilibrium (Eq. feq-3).  c_s^2 = 72 / (5 (25 +
+         * sqrt 193)) = sum_i w_i c_ix^2 of those weights: the printed c_s
+         * formula gives its reciprocal. */
+        const double r = sqrt(193.0);
+        L->M = 3;
+        L->thermal = 1;
+        L->order = 3;
+        L->cs2 = 72.0 / (5.0 * (25.0 + r));
+        add_class(L, 0, 0, (575.0 + 193.0 * r) / 8100.0);
+        add_class(L, 1, 0, (3355.0 - 91.0 * r) / 18000.0);
+        add_class(L, 1, 1, (655.0 + 17.0 * r) / 27000.0);
+        add_class(L, 2, 2, (685.0 - 49.0 * r) / 54000.0);
+        add_class(L, 3, 0, (1445.0 - 101.0 * r) / 162000.0);
     } else {
         return -1;
     }
@@ -119,6 +137,7 @@ int orc_lattice_info(int lattice, int* q, int* M, double* cs2, int* c, double* w
 /* Shifted equilibrium g^eq_i = f^eq_i - w_i rho0 at U = (drho, ux, uy, dT).
  * D2Q37: fourth-order Hermite expansion, Eq. feq-4 (built on Eq. feq-3),
  * written in xi = c/c_s, u~ = u/c_s, theta - 1 = dT.
+ * D2Q17: the third-order expansion, Eq. feq-3, in the same variables.
  * D2Q9: second-order isothermal expansion (the first bracket of Eq. feq-3
  * with T = 1). */
 static void feq_shifted(const lattice_t* L, double rho0, const double U[4], double* g)
@@ -134,8 +153,9 @@ static void feq_shifted(const lattice_t* L, double rho0, const double U[4], doub
         double h1 = xu;
         double h2 = 0.5 * (xu * xu - uu + dT * (xi2 - 2.0));
         double h3 = 0.0, h4 = 0.0;
-        if (L->thermal) {
+        if (L->order >= 3)
             h3 = xu / 6.0 * (xu * xu - 3.0 * uu + 3.0 * dT * (xi2 - 4.0));
+        if (L->order >= 4) {
             h4 = (xu * xu * xu * xu - 6.0 * xu * xu * uu + 3.0 * uu * uu
                   + 6.0 * dT * (xu * xu * (xi2 - 6.0) + uu * (4.0 - xi2))
                   + 3.0 * dT * dT * (xi2 * xi2 - 8.0 * xi2 + 8.0)) / 24.0;
@@ -182,8 +202,9 @@ void orc_moments(int lattice, double rho0, const double* g, double U[4])
 
 /* Viscous stress sigma' (Eq. LaplaceU) and heat flux q (Eqs. heatflux,
  * LaplaceT) from the non-equilibrium part f - f^eq of one node.  The
- * equilibrium part of the central third moment vanishes on D2Q37, so q is
- * taken from f^neq alone.  Both carry the factor (1 - 1/(2 tau)). */
+ * equilibrium part of the central third moment vanishes on D2Q37 and D2Q17
+ * (their equilibria reproduce the Maxwellian moments through third order),
+ * so q is taken from f^neq alone.  Both carry the factor (1 - 1/(2 tau)). */
 static void neq_moments(const lattice_t* L, double tau, double rho0, const double* g, double out[5])
 {
     double U[4], ge[QMAX];

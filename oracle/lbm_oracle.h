@@ -26,13 +26,13 @@
 extern "C" {
 #endif
 
-enum { ORC_D2Q9 = 0, ORC_D2Q37 = 1 };
+enum { ORC_D2Q9 = 0, ORC_D2Q37 = 1, ORC_D2Q17 = 2 };
 enum { ORC_PERIODIC = 0, ORC_SIDE_CBC = 1, ORC_SIDE_INFLOW = 2, ORC_SIDE_ZG = 3 };
 enum { ORC_LODI = 0, ORC_LODI_RELAX = 1, ORC_CBC = 2, ORC_CBC_RELAX = 3 };
 enum { ORC_VIS_MESO = 0, ORC_VIS_FD = 1, ORC_VIS_OFF = 2 };
 
 typedef struct {
-    int lattice;       /* ORC_D2Q9 (isothermal) or ORC_D2Q37 (thermal)        */
+    int lattice;       /* ORC_D2Q9 (isothermal), ORC_D2Q37 or ORC_D2Q17 (thermal) */
     int nx, ny;        /* grid size                                            */
     double tau;        /* BGK relaxation time, Eq. bgk                         */
     double rho0;       /* reference density of the population shift            */

@@ -23,7 +23,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "LbmCbcParams", "LBM_D2Q9", "LBM_D2Q37", "LBM_F64", "LBM_F32", "LBM_F16",
+    "LbmCbcParams", "LBM_D2Q9", "LBM_D2Q37", "LBM_D2Q17", "LBM_F64", "LBM_F32", "LBM_F16",
     "lbm_params_default", "lbm_workspace_bytes", "lbm_create", "lbm_create_in",
     "lbm_set_stream", "lbm_init_fields", "lbm_step", "lbm_step_phase", "lbm_set_kernel_events",
     "lbm_get_macros",
@@ -32,9 +32,9 @@ __all__ = [
     "params_from_run", "LbmError",
 ]
 
-LBM_D2Q9, LBM_D2Q37 = 0, 1
+LBM_D2Q9, LBM_D2Q37, LBM_D2Q17 = 0, 1, 2
 LBM_F64, LBM_F32, LBM_F16 = 0, 1, 2
-LATTICES = {"D2Q9": LBM_D2Q9, "D2Q37": LBM_D2Q37}
+LATTICES = {"D2Q9": LBM_D2Q9, "D2Q37": LBM_D2Q37, "D2Q17": LBM_D2Q17}
 STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16}
 SIDES = {"periodic": 0, "cbc": 1, "inflow": 2, "zg": 3}
 SCHEMES = {"lodi": 0, "lodi_relax": 1, "cbc": 2, "cbc_relax": 3}

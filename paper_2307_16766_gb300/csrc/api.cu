@@ -39,7 +39,7 @@ struct lbm_handle {
     double Uin[4] = {0, 0, 0, 0};
     double* macro = nullptr;
     int* flag = nullptr;     // [0]: non-finite macros seen, [1]: kernel status bits
-    CUtensorMap tmap[2][3];  // tensor-copy descriptors of the two buffers, box depths 7, 5, 3
+    CUtensorMap tmap[2][5];  // tensor-copy descriptors of the two buffers, box depths 7, 5, 3, 2, 1
     void* ws = nullptr;
     size_t ws_bytes = 0;
     bool owns_ws = false;
@@ -94,10 +94,24 @@ std::string fmt(const char* f, ...)
     return buf;
 }
 
-double lattice_cs2(int lattice) { return lattice == LBM_D2Q9 ? Lat<D2Q9>::CS2 : Lat<D2Q37>::CS2; }
+double lattice_cs2(int lattice)
+{
+    return lattice == LBM_D2Q9 ? Lat<D2Q9>::CS2 : lattice == LBM_D2Q17 ? Lat<D2Q17>::CS2 : Lat<D2Q37>::CS2;
+}
 
-int lattice_cx(int lattice, int i) { return lattice == LBM_D2Q9 ? Lat<D2Q9>::cx(i) : Lat<D2Q37>::cx(i); }
-int lattice_cy(int lattice, int i) { return lattice == LBM_D2Q9 ? Lat<D2Q9>::cy(i) : Lat<D2Q37>::cy(i); }
+int lattice_cx(int lattice, int i)
+{
+    return lattice == LBM_D2Q9 ? Lat<D2Q9>::cx(i) : lattice == LBM_D2Q17 ? Lat<D2Q17>::cx(i) : Lat<D2Q37>::cx(i);
+}
+int lattice_cy(int lattice, int i)
+{
+    return lattice == LBM_D2Q9 ? Lat<D2Q9>::cy(i) : lattice == LBM_D2Q17 ? Lat<D2Q17>::cy(i) : Lat<D2Q37>::cy(i);
+}
+int lattice_plane(int lattice, int i)
+{
+    return lattice == LBM_D2Q9 ? Lat<D2Q9>::plane_of(i)
+         : lattice == LBM_D2Q17 ? Lat<D2Q17>::plane_of(i) : Lat<D2Q37>::plane_of(i);
+}
 
 // Side geometry (W = 0, E = 1, S = 2, N = 3): outward normal and the layer-0
 // node x_f at tangential position p (Fig. Layer-Multispeed-BC).
@@ -117,7 +131,10 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
               std::string& err)
 {
     if (!p) { err = "params is NULL"; return LBM_ERR_ARG; }
-    if (lattice != LBM_D2Q9 && lattice != LBM_D2Q37) { err = fmt("unknown lattice %d", lattice); return LBM_ERR_ARG; }
+    if (lattice != LBM_D2Q9 && lattice != LBM_D2Q37 && lattice != LBM_D2Q17) {
+        err = fmt("unknown lattice %d", lattice);
+        return LBM_ERR_ARG;
+    }
     if (!(tau > 0.5) || !std::isfinite(tau)) { err = fmt("tau must exceed 1/2 (got %g)", tau); return LBM_ERR_ARG; }
     if (p->storage < LBM_F64 || p->storage > LBM_F16) { err = fmt("unknown storage %d", p->storage); return LBM_ERR_ARG; }
     if (!(p->rho0 > 0.0)) { err = "rho0 must be positive"; return LBM_ERR_ARG; }
@@ -133,7 +150,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
         return LBM_ERR_ARG;
     }
     const int M = lattice == LBM_D2Q9 ? 1 : 3;
-    const int Q = lattice == LBM_D2Q9 ? 9 : 37;
+    const int Q = lattice == LBM_D2Q9 ? 9 : lattice == LBM_D2Q17 ? 17 : 37;
     const int nmin_b = 2 * M + 3;
     if (nx < 1 || ny < 1 || nx > (1 << 20) || ny > 65535) { err = fmt("grid %d x %d out of range", nx, ny); return LBM_ERR_ARG; }
     if ((!perx && nx < nmin_b) || (!pery && ny < nmin_b)) {
@@ -172,7 +189,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     G.omega_f = float(1.0 / tau);
     G.rho0_f = float(p->rho0);
     for (int i = 0; i < Q; ++i) {
-        const int plane_i = lattice == LBM_D2Q9 ? Lat<D2Q9>::plane_of(i) : Lat<D2Q37>::plane_of(i);
+        const int plane_i = lattice_plane(lattice, i);
         pl.O.st[i] = int(plane_i * G.plane);
         pl.O.ld[i] = int(plane_i * G.plane) - lattice_cy(lattice, i) * nxp - lattice_cx(lattice, i);
     }
@@ -461,7 +478,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     pl.Uin[0] = p->inflow[0] - p->rho0;
     pl.Uin[1] = p->inflow[1];
     pl.Uin[2] = p->inflow[2];
-    pl.Uin[3] = lattice == LBM_D2Q37 ? p->inflow[3] - 1.0 : 0.0;
+    pl.Uin[3] = lattice != LBM_D2Q9 ? p->inflow[3] - 1.0 : 0.0;
 
     pl.Q = Q;
     pl.esize = p->storage == LBM_F64 ? 8 : (p->storage == LBM_F32 ? 4 : 2);
@@ -586,9 +603,9 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     for (int c = 0; c < 4; ++c) h->Uin[c] = pl.Uin[c];
     h->macro = at<double>(ws, pl.off_macro);
     h->flag = at<int>(ws, pl.off_flag);
-    const int depths[3] = {7, 5, 3};
+    const int depths[5] = {7, 5, 3, 2, 1};
     for (int b = 0; b < 2; ++b)
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 5; ++k) {
             const int rc = encode_population_map(h, h->f[b], depths[k] <= h->Q ? depths[k] : 1, &h->tmap[b][k]);
             if (rc != LBM_OK) return rc;
         }
@@ -786,7 +803,7 @@ int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux, const do
                     const double* T, int on_device)
 {
     if (!h) return LBM_ERR_ARG;
-    if (!rho || !ux || !uy || (!T && h->lattice == LBM_D2Q37)) {
+    if (!rho || !ux || !uy || (!T && h->lattice != LBM_D2Q9)) {
         h->err = "NULL field";
         return LBM_ERR_ARG;
     }

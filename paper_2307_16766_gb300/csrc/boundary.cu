@@ -904,59 +904,54 @@ int zg_t(const Geom& G, const Band& B, void* fnew, cudaStream_t st)
 
 }  // namespace
 
+#define BAND_DISPATCH(lat, storage, CALL)                                  \
+    do {                                                                   \
+        if (lat == D2Q9) {                                                 \
+            if (storage == 0) return CALL(D2Q9, double);                   \
+            if (storage == 1) return CALL(D2Q9, float);                    \
+            if (storage == 2) return CALL(D2Q9, __half);                   \
+        } else if (lat == D2Q17) {                                         \
+            if (storage == 0) return CALL(D2Q17, double);                  \
+            if (storage == 1) return CALL(D2Q17, float);                   \
+            if (storage == 2) return CALL(D2Q17, __half);                  \
+        } else {                                                           \
+            if (storage == 0) return CALL(D2Q37, double);                  \
+            if (storage == 1) return CALL(D2Q37, float);                   \
+            if (storage == 2) return CALL(D2Q37, __half);                  \
+        }                                                                  \
+    } while (0)
+
 int launch_boundary(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
                     const Band& B, const void* fin, void* fnew, int par_t, size_t smem_pad,
                     cudaStream_t st)
 {
-    if (lat == D2Q9) {
-        if (storage == 0) return boundary_t<D2Q9, double>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
-        if (storage == 1) return boundary_t<D2Q9, float>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
-        if (storage == 2) return boundary_t<D2Q9, __half>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
-    } else {
-        if (storage == 0) return boundary_t<D2Q37, double>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
-        if (storage == 1) return boundary_t<D2Q37, float>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
-        if (storage == 2) return boundary_t<D2Q37, __half>(G, O, E, B, fin, fnew, par_t, smem_pad, st);
-    }
+#define CALL(L, S) boundary_t<L, S>(G, O, E, B, fin, fnew, par_t, smem_pad, st)
+    BAND_DISPATCH(lat, storage, CALL);
+#undef CALL
     return -1;
 }
 
 size_t band_dynamic_smem(int lat, int storage, const Band& B)
 {
-    if (lat == D2Q9) {
-        if (storage == 0) return band_smem<D2Q9, double>(B);
-        if (storage == 1) return band_smem<D2Q9, float>(B);
-        return band_smem<D2Q9, __half>(B);
-    }
-    if (storage == 0) return band_smem<D2Q37, double>(B);
-    if (storage == 1) return band_smem<D2Q37, float>(B);
-    return band_smem<D2Q37, __half>(B);
+#define CALL(L, S) band_smem<L, S>(B)
+    BAND_DISPATCH(lat, storage, CALL);
+#undef CALL
+    return 0;
 }
 
 int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad)
 {
-    if (lat == D2Q9) {
-        if (storage == 0) return prepare_t<D2Q9, double>(B, smem_pad);
-        if (storage == 1) return prepare_t<D2Q9, float>(B, smem_pad);
-        if (storage == 2) return prepare_t<D2Q9, __half>(B, smem_pad);
-    } else {
-        if (storage == 0) return prepare_t<D2Q37, double>(B, smem_pad);
-        if (storage == 1) return prepare_t<D2Q37, float>(B, smem_pad);
-        if (storage == 2) return prepare_t<D2Q37, __half>(B, smem_pad);
-    }
+#define CALL(L, S) prepare_t<L, S>(B, smem_pad)
+    BAND_DISPATCH(lat, storage, CALL);
+#undef CALL
     return -1;
 }
 
 int launch_zg(int lat, int storage, const Geom& G, const Band& B, void* fnew, cudaStream_t st)
 {
-    if (lat == D2Q9) {
-        if (storage == 0) return zg_t<D2Q9, double>(G, B, fnew, st);
-        if (storage == 1) return zg_t<D2Q9, float>(G, B, fnew, st);
-        if (storage == 2) return zg_t<D2Q9, __half>(G, B, fnew, st);
-    } else {
-        if (storage == 0) return zg_t<D2Q37, double>(G, B, fnew, st);
-        if (storage == 1) return zg_t<D2Q37, float>(G, B, fnew, st);
-        if (storage == 2) return zg_t<D2Q37, __half>(G, B, fnew, st);
-    }
+#define CALL(L, S) zg_t<L, S>(G, B, fnew, st)
+    BAND_DISPATCH(lat, storage, CALL);
+#undef CALL
     return -1;
 }
 
@@ -1097,7 +1092,7 @@ extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, doub
                                          const double* strip_t1, const double* neq_t, void* stream)
 {
     using namespace lbmgb;
-    if (lattice != LBM_D2Q9 && lattice != LBM_D2Q37) return LBM_ERR_ARG;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D2Q37 && lattice != LBM_D2Q17) return LBM_ERR_ARG;
     if (!p || !Ub || !strip_t || !strip_t1 || side < 0 || side > 3 || !(tau > 0.5)) return LBM_ERR_ARG;
     if (p->viscous < 0 || p->viscous > 2 || p->scheme[side] < 0 || p->scheme[side] > 3 || !(p->rho0 > 0.0))
         return LBM_ERR_ARG;
@@ -1115,7 +1110,8 @@ extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, doub
     double* scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc != LBM_OK) return rc;
-    const double cs2 = lattice == LBM_D2Q9 ? Lat<D2Q9>::CS2 : Lat<D2Q37>::CS2;
+    const double cs2 = lattice == LBM_D2Q9 ? Lat<D2Q9>::CS2
+                     : lattice == LBM_D2Q17 ? Lat<D2Q17>::CS2 : Lat<D2Q37>::CS2;
     const int n = length * M;
     Geom G{};
     G.M = M;
@@ -1152,6 +1148,8 @@ extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, doub
     for (int stage = 0; stage < 4; ++stage) {
         if (lattice == LBM_D2Q9)
             k_side_stage_noalloc<D2Q9><<<nb, kBandThreads, 0, st>>>(G, B, E, side, length, strip_t, strip_t1, stage);
+        else if (lattice == LBM_D2Q17)
+            k_side_stage_noalloc<D2Q17><<<nb, kBandThreads, 0, st>>>(G, B, E, side, length, strip_t, strip_t1, stage);
         else
             k_side_stage_noalloc<D2Q37><<<nb, kBandThreads, 0, st>>>(G, B, E, side, length, strip_t, strip_t1, stage);
     }

@@ -90,9 +90,10 @@ __device__ bool wait_tx(unsigned long long* bar, int* status)
     return false;
 }
 
-// Tensor maps of the input buffer: box depths 7, 5 and 3 planes.
+// Tensor maps of the input buffer: box depths 7, 5, 3, 2 and 1 planes
+// (the c_y group sizes of the three lattices).
 struct Maps {
-    CUtensorMap m7, m5, m3;
+    CUtensorMap m7, m5, m3, m2, m1;
 };
 
 // One 3D tensor copy per c_y group; every offset, coordinate shift and map
@@ -104,11 +105,13 @@ __device__ __forceinline__ void issue_group(const Maps& tm, unsigned char* smem,
     using L = Lat<LAT>;
     using BX = Stage<LAT, S>;
     constexpr int cnt = L::gcount(GI);
-    static_assert(cnt == 7 || cnt == 5 || cnt == 3, "group depth without a tensor map");
+    static_assert(cnt == 7 || cnt == 5 || cnt == 3 || cnt == 2 || cnt == 1,
+                  "group depth without a tensor map");
     constexpr int ofs = BX::gofs(GI);
     constexpr int dy = L::gcy(GI);
     constexpr int z0 = L::gstart(GI);
-    const CUtensorMap* m = cnt == 7 ? &tm.m7 : (cnt == 5 ? &tm.m5 : &tm.m3);
+    const CUtensorMap* m = cnt == 7 ? &tm.m7 : cnt == 5 ? &tm.m5 : cnt == 3 ? &tm.m3
+                         : cnt == 2 ? &tm.m2 : &tm.m1;
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4}], [%5];"
@@ -337,6 +340,8 @@ int bulk_t(const Geom& G, const Offsets& O, const Region& R, const CUtensorMap* 
     tm.m7 = tmaps[0];
     tm.m5 = tmaps[1];
     tm.m3 = tmaps[2];
+    tm.m2 = tmaps[3];
+    tm.m1 = tmaps[4];
     dim3 blk(kBulkThreads), grd(t1 - t0, h);
     k_bulk<LAT, S><<<grd, blk, smem, st>>>(tm, G, O, R, static_cast<const S*>(fin),
                                            static_cast<S*>(fout), status);
@@ -360,6 +365,10 @@ int macros_t(const Geom& G, const void* f, double* rho, double* ux, double* uy, 
             if (storage == 0) return CALL(D2Q9, double);                   \
             if (storage == 1) return CALL(D2Q9, float);                    \
             if (storage == 2) return CALL(D2Q9, __half);                   \
+        } else if (lat == D2Q17) {                                         \
+            if (storage == 0) return CALL(D2Q17, double);                  \
+            if (storage == 1) return CALL(D2Q17, float);                   \
+            if (storage == 2) return CALL(D2Q17, __half);                  \
         } else {                                                           \
             if (storage == 0) return CALL(D2Q37, double);                  \
             if (storage == 1) return CALL(D2Q37, float);                   \

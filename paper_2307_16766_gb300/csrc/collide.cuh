@@ -80,8 +80,8 @@ __device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Pu
     // BGK collide (Eq. bgk), one opposite pair at a time:
     // g^eq_{+-} = w (rho - rho0) + w rho (even +- odd) in p = c.u / c_s^2.
     constexpr C ics2 = C(1.0 / L::CS2);
-    constexpr C a3 = L::THERMAL ? C(1.0 / 6.0) : C(0);
-    constexpr C a4 = L::THERMAL ? C(1.0 / 24.0) : C(0);
+    constexpr C a3 = L::ORDER >= 3 ? C(1.0 / 6.0) : C(0);
+    constexpr C a4 = L::ORDER >= 4 ? C(1.0 / 24.0) : C(0);
     const C uxs = m.ux * ics2, uys = m.uy * ics2;
     const EqPoly<C> e = eq_poly<LAT, C>(m.ux * uxs + m.uy * uys, m.dT);
     const C om = omega_of<C>(G);

@@ -17,7 +17,7 @@ namespace lbmgb {
 // can be evaluated once per pair (even and odd parts in c.u).
 // ---------------------------------------------------------------------------
 
-enum { D2Q9 = 0, D2Q37 = 1 };
+enum { D2Q9 = 0, D2Q37 = 1, D2Q17 = 2 };
 
 template <int LAT>
 struct Lat;
@@ -27,6 +27,7 @@ template <>
 struct Lat<D2Q9> {
     static constexpr int Q = 9, M = 1, NCLS = 3;
     static constexpr bool THERMAL = false;
+    static constexpr int ORDER = 2;         // Hermite order of the equilibrium
     static constexpr double CS2 = 1.0 / 3.0;
     __host__ __device__ static constexpr int cx(int i)
     {
@@ -84,6 +85,7 @@ template <>
 struct Lat<D2Q37> {
     static constexpr int Q = 37, M = 3, NCLS = 8;
     static constexpr bool THERMAL = true;
+    static constexpr int ORDER = 4;
     static constexpr double CS2 = 0.6979533220196830882384091;
     __host__ __device__ static constexpr int cx(int i)
     {
@@ -153,6 +155,68 @@ struct Lat<D2Q37> {
     }
 };
 
+// D2Q17, Tab. d2q17 velocity classes (0,0) (1,0) (1,1) (2,2) (3,0); M = 3;
+// third-order equilibrium (Eq. feq-3).  The class weights are the printed
+// closed forms (a + b sqrt 193) / d; c_s^2 = 72 / (5 (25 + sqrt 193)), which
+// is sum_i w_i c_ix^2 of those weights (the printed c_s formula gives its
+// reciprocal).
+template <>
+struct Lat<D2Q17> {
+    static constexpr int Q = 17, M = 3, NCLS = 5;
+    static constexpr bool THERMAL = true;
+    static constexpr int ORDER = 3;
+    static constexpr double CS2 = 0.3702518670183398497189151;
+    __host__ __device__ static constexpr int cx(int i)
+    {
+        constexpr int v[17] = {0, 1, -1, 0, 0, 1, -1, 1, -1, 2, -2, 2, -2, 3, -3, 0, 0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cy(int i)
+    {
+        constexpr int v[17] = {0, 0, 0, 1, -1, 1, -1, -1, 1, 2, -2, -2, 2, 0, 0, 3, -3};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cls(int i)
+    {
+        return i == 0 ? 0 : i < 5 ? 1 : i < 9 ? 2 : i < 13 ? 3 : 4;
+    }
+    __host__ __device__ static constexpr int c2cls(int k)
+    {
+        constexpr int v[5] = {0, 1, 2, 8, 9};
+        return v[k];
+    }
+    __host__ __device__ static constexpr double wcls(int k)
+    {
+        constexpr double v[5] = {0.4020051469091126259416644, 0.1161548664977815438740355,
+                                 0.0330063536229869139497538, 0.0000790786021659181312371,
+                                 0.0002584145497874675595575};
+        return v[k];
+    }
+    __host__ __device__ static constexpr double w(int i) { return wcls(cls(i)); }
+    // planes grouped by c_y = 0, 1, -1, 2, -2, 3, -3
+    static constexpr int NG = 7;
+    __host__ __device__ static constexpr int plane_of(int i)
+    {
+        constexpr int v[17] = {0, 1, 2, 5, 8, 6, 9, 10, 7, 11, 13, 14, 12, 3, 4, 15, 16};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int gcy(int g)
+    {
+        constexpr int v[7] = {0, 1, -1, 2, -2, 3, -3};
+        return v[g];
+    }
+    __host__ __device__ static constexpr int gstart(int g)
+    {
+        constexpr int v[7] = {0, 5, 8, 11, 13, 15, 16};
+        return v[g];
+    }
+    __host__ __device__ static constexpr int gcount(int g)
+    {
+        constexpr int v[7] = {5, 3, 3, 2, 2, 1, 1};
+        return v[g];
+    }
+};
+
 // Group of velocity i (its plane lies in [gstart, gstart + gcount)).
 template <int LAT>
 __host__ __device__ constexpr int group_of(int i)
@@ -211,9 +275,11 @@ struct Store<__half> {
 //   f^eq / (w rho) - 1 = a0 + a1 p + a2 p^2 + a3 p^3 + a4 p^4,
 // and each a_k as a polynomial in xi^2:
 //   a0 = A0 + xi^2 (B0 + C0 xi^2),  a1 = A1 + B1 xi^2,  a2 = A2 + B2 xi^2.
-// Thermal lattice: Eq. feq-4, the fourth-order Hermite expansion in
-// xi = c/c_s, u~ = u/c_s, theta - 1 = t, read with the coefficient
-// (xi^2 - 6) in the (u.c)^2 (T-1) term; then a3 = 1/6, a4 = 1/24.
+// D2Q37: Eq. feq-4, the fourth-order Hermite expansion in xi = c/c_s,
+// u~ = u/c_s, theta - 1 = t, read with the coefficient (xi^2 - 6) in the
+// (u.c)^2 (T-1) term; then a3 = 1/6, a4 = 1/24.
+// D2Q17: Eq. feq-3, the third-order expansion in the same variables;
+// a3 = 1/6, a4 = 0.
 // Isothermal D2Q9: second order, a0 = -u2/2, a1 = 1, a2 = 1/2.
 template <typename C>
 struct EqPoly {
@@ -224,7 +290,17 @@ template <int LAT, typename C>
 __device__ __forceinline__ EqPoly<C> eq_poly(C u2, C t)
 {
     EqPoly<C> e;
-    if (Lat<LAT>::THERMAL) {
+    if (Lat<LAT>::ORDER == 3) {
+        // Eq. feq-3: even part -u2/2 - t + (t/2) xi^2 + p^2/2, odd part
+        // p (1 - u2/2 - 2t + (t/2) xi^2) + p^3/6
+        e.A0 = C(-0.5) * u2 - t;
+        e.B0 = C(0.5) * t;
+        e.C0 = C(0);
+        e.A1 = C(1) - C(0.5) * u2 - C(2) * t;
+        e.B1 = C(0.5) * t;
+        e.A2 = C(0.5);
+        e.B2 = C(0);
+    } else if (Lat<LAT>::THERMAL) {
         e.A0 = C(-0.5) * u2 - t + C(0.125) * u2 * u2 + t * u2 + t * t;
         e.B0 = C(0.5) * t - C(0.25) * t * u2 - t * t;
         e.C0 = C(0.125) * t * t;
@@ -299,8 +375,8 @@ __device__ __forceinline__ void equilibrium(const Moments<LAT, C>& m, C* geq)
 {
     using L = Lat<LAT>;
     constexpr C ics2 = C(1.0 / L::CS2);
-    constexpr C a3 = L::THERMAL ? C(1.0 / 6.0) : C(0);
-    constexpr C a4 = L::THERMAL ? C(1.0 / 24.0) : C(0);
+    constexpr C a3 = L::ORDER >= 3 ? C(1.0 / 6.0) : C(0);
+    constexpr C a4 = L::ORDER >= 4 ? C(1.0 / 24.0) : C(0);
     C a0[L::NCLS], a1[L::NCLS], a2[L::NCLS];
     eq_coef<LAT, C>((m.ux * m.ux + m.uy * m.uy) * ics2, m.dT, a0, a1, a2);
     geq[0] = C(L::w(0)) * (m.s0 + m.rho * a0[0]);
@@ -441,8 +517,8 @@ int launch_init(int lat, int storage, const Geom& G, const Export& E, const Band
 // Fixed inflow equilibrium at the listed nodes of one population buffer.
 int launch_inflow(int lat, int storage, const Geom& G, const int* nodes, int n, const double Uin[4],
                   void* f, cudaStream_t st);
-// One bulk step fin -> fout over the nodes of region R; tmaps[0..2] describe
-// fin for the tensor copies (box depths 7, 5, 3 planes); *status gets bit 1
+// One bulk step fin -> fout over the nodes of region R; tmaps[0..4] describe
+// fin for the tensor copies (box depths 7, 5, 3, 2, 1 planes); *status gets bit 1
 // if a copy never completed.
 int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Region& R,
                 const CUtensorMap* tmaps, const void* fin, void* fout, int* status,

@@ -84,7 +84,10 @@ def test_defaults_and_workspace_size():
     (lbm.LBM_D2Q37, 16, 16, dict(storage=7), False),
     (lbm.LBM_D2Q37, 16, 16, dict(viscous=3), False),
     (lbm.LBM_D2Q37, 16, 16, dict(rho0=0.0), False),
-    (2, 16, 16, dict(), False),
+    (lbm.LBM_D2Q17, 9, 9, dict(side=[1, 1, 1, 1]), True),          # D2Q17: M = 3 as well
+    (lbm.LBM_D2Q17, 9, 8, dict(side=[1, 1, 1, 1]), False),
+    (3, 16, 16, dict(), False),                                    # unknown lattice
+    (-1, 16, 16, dict(), False),
 ])
 def test_configuration_validation(lattice, nx, ny, kw, ok):
     p = cfg_params(**kw)

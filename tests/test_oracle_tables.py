@@ -29,7 +29,8 @@ def class_of(c):
     return (a, b)
 
 
-@pytest.mark.parametrize("lat,q,M,degree", [("D2Q9", 9, 1, 5), ("D2Q37", 37, 3, 9)])
+@pytest.mark.parametrize("lat,q,M,degree", [("D2Q9", 9, 1, 5), ("D2Q37", 37, 3, 9),
+                                            ("D2Q17", 17, 3, 7)])
 def test_quadrature_isotropy(lat, q, M, degree):
     """sum_i w_i xi_x^a xi_y^b equals the standard-normal moments E[Z^a] E[Z^b]
     for every a + b <= degree (a Gauss-Hermite rule of that degree)."""
@@ -72,6 +73,25 @@ def test_d2q37_weights_match_printed_table():
     assert abs(np.sum(L["w"] * xi ** 4) - 3.0) > 0.1
 
 
+def test_d2q17_weights_match_printed_table():
+    """Appendix B, Tab. d2q17 prints the weights as closed forms.  Its printed
+    c_s^2 = 5 (25 + sqrt 193) / 72 fails the second-moment condition with
+    those weights; its reciprocal, which the oracle uses, satisfies it."""
+    L = oracle.lattice_info("D2Q17")
+    rows = np.loadtxt(os.path.join(GOLD, "d2q17_weights_printed.txt"))
+    r = math.sqrt(193.0)
+    printed = {(int(x[0]), int(x[1])): (x[2] + x[3] * r) / x[4] for x in rows}
+    counts = {}
+    for c, w in zip(L["c"], L["w"]):
+        k = class_of(c)
+        assert abs(w - printed[k]) < 1e-16
+        counts[k] = counts.get(k, 0) + 1
+    assert counts == {(0, 0): 1, (1, 0): 4, (1, 1): 4, (2, 2): 4, (3, 0): 4}
+    printed_cs2 = 5.0 * (25.0 + r) / 72.0
+    assert abs(np.sum(L["w"] * L["c"][:, 0] ** 2) - printed_cs2) > 1.0
+    assert abs(L["cs2"] * printed_cs2 - 1.0) < 1e-15
+
+
 def test_d2q9_weights_match_printed_table():
     L = oracle.lattice_info("D2Q9")
     rows = np.loadtxt(os.path.join(GOLD, "d2q9_weights_printed.txt"))
@@ -91,13 +111,14 @@ def random_states(rng, n, thermal):
     return out
 
 
-@pytest.mark.parametrize("lat,order", [("D2Q9", 2), ("D2Q37", 4)])
+@pytest.mark.parametrize("lat,order", [("D2Q9", 2), ("D2Q37", 4), ("D2Q17", 3)])
 def test_equilibrium_reproduces_maxwellian_moments(lat, order):
-    """Eq. feq-4 (D2Q37) / the second-order isothermal expansion (D2Q9) must
-    carry every velocity moment of the Maxwellian through its expansion order:
+    """Eq. feq-4 (D2Q37) / Eq. feq-3 (D2Q17) / the second-order isothermal
+    expansion (D2Q9) must carry every velocity moment of the Maxwellian
+    through its expansion order:
     sum f^eq xi_x^a xi_y^b = rho E[X^a] E[Y^b], X ~ N(u~_x, theta)."""
     L = oracle.lattice_info(lat)
-    thermal = lat == "D2Q37"
+    thermal = lat != "D2Q9"
     xi = L["c"] / math.sqrt(L["cs2"])
     rng = np.random.default_rng(1)
     rho0 = 1.0
@@ -128,22 +149,24 @@ def test_fourth_order_misprint_breaks_mass():
     assert abs(np.sum(delta)) > 1e-4
 
 
-@pytest.mark.parametrize("lat", ["D2Q9", "D2Q37"])
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q37", "D2Q17"])
 def test_moments_invert_equilibrium(lat):
     """U(f^eq(U)) = U (Eq. macro applied to Eqs. feq-3/4)."""
     rng = np.random.default_rng(2)
-    for U in random_states(rng, 30, lat == "D2Q37"):
+    for U in random_states(rng, 30, lat != "D2Q9"):
         got = oracle.moments(lat, 1.0, oracle.feq(lat, 1.0, U))
         assert np.allclose(got, U, rtol=0, atol=2e-15), (got, U)
 
 
-def test_equilibrium_heat_flux_vanishes():
-    """The central third moment of f^eq is zero on D2Q37 (the oracle computes
-    the heat flux of Eq. heatflux from f - f^eq on that basis)."""
-    L = oracle.lattice_info("D2Q37")
+@pytest.mark.parametrize("lat", ["D2Q37", "D2Q17"])
+def test_equilibrium_heat_flux_vanishes(lat):
+    """The central third moment of f^eq is zero on D2Q37 and D2Q17 (the
+    oracle computes the heat flux of Eq. heatflux from f - f^eq on that
+    basis)."""
+    L = oracle.lattice_info(lat)
     rng = np.random.default_rng(3)
     for U in random_states(rng, 10, True):
-        f = oracle.feq("D2Q37", 1.0, U) + L["w"]
+        f = oracle.feq(lat, 1.0, U) + L["w"]
         e = L["c"] - U[1:3]
         q = 0.5 * np.sum(f[:, None] * (e ** 2).sum(1)[:, None] * e, axis=0)
         assert np.abs(q).max() < 1e-14
