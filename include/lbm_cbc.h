@@ -75,8 +75,11 @@ enum lbm_scheme { LBM_LODI = 0, LBM_LODI_RELAX = 1, LBM_CBC = 2, LBM_CBC_RELAX =
  * macros ("-FD" of Sec. 4.2), or none. */
 enum lbm_viscous { LBM_VISCOUS_MESO = 0, LBM_VISCOUS_FD = 1, LBM_VISCOUS_OFF = 2 };
 
-/* Mesoscopic Dirichlet condition (Sec. 3.3): equilibrium, or Eq. NEEP. */
-enum lbm_dirichlet { LBM_DIRICHLET_EQ = 0, LBM_DIRICHLET_NEEP = 1 };
+/* Mesoscopic Dirichlet condition (Sec. 3.3): equilibrium, Eq. NEEP, or NEEP
+ * with the non-equilibrium part of x_f projected onto the Hermite
+ * polynomials of orders 2 (D2Q9) or 2 and 3 (D2Q17, D2Q37) -- a regularised
+ * scheme the paper names for future work (Sec. 5). */
+enum lbm_dirichlet { LBM_DIRICHLET_EQ = 0, LBM_DIRICHLET_NEEP = 1, LBM_DIRICHLET_REG = 2 };
 
 typedef struct lbm_cbc_params {
     int    side[4];     /* enum lbm_side_kind per side (W, E, S, N)                   */

@@ -8,7 +8,7 @@ A run is described by a plain dict (see ``lbm_workloads``) with the keys
 ``lattice`` ("D2Q9" | "D2Q37" | "D2Q17"), ``nx``, ``ny``, ``tau``, ``rho0``, ``sides``
 (four of "periodic" | "cbc" | "inflow" | "zg", order W, E, S, N),
 ``schemes`` (four of "lodi" | "lodi_relax" | "cbc" | "cbc_relax"),
-``viscous`` ("meso" | "fd" | "off"), ``dirichlet`` ("eq" | "neep"), ``alpha_T``, ``beta_P``,
+``viscous`` ("meso" | "fd" | "off"), ``dirichlet`` ("eq" | "neep" | "reg"), ``alpha_T``, ``beta_P``,
 ``t_inf``, ``p_inf`` (four values) and ``inflow`` (rho, ux, uy, T).
 """
 import ctypes as C
@@ -21,7 +21,7 @@ from . import build as _build
 LATTICES = {"D2Q9": 0, "D2Q37": 1, "D2Q17": 2}
 SIDES = {"periodic": 0, "cbc": 1, "inflow": 2, "zg": 3}
 SCHEMES = {"lodi": 0, "lodi_relax": 1, "cbc": 2, "cbc_relax": 3}
-DIRICHLET = {"eq": 0, "neep": 1}
+DIRICHLET = {"eq": 0, "neep": 1, "reg": 2}
 VISCOUS = {"meso": 0, "fd": 1, "off": 2}
 
 
@@ -48,6 +48,7 @@ def lib():
         ip = C.POINTER(C.c_int)
         L.orc_lattice_info.argtypes = [C.c_int, ip, ip, dp, ip, dp]
         L.orc_feq.argtypes = [C.c_int, C.c_double, dp, dp]
+        L.orc_regularize.argtypes = [C.c_int, dp]
         L.orc_moments.argtypes = [C.c_int, C.c_double, dp, dp]
         L.orc_char_matrices.argtypes = [C.c_int, C.c_double, dp, dp, dp, dp]
         L.orc_char_rhs.argtypes = [C.POINTER(Params), dp, dp, dp, dp, C.c_int, C.c_double, C.c_int, dp]
@@ -125,6 +126,14 @@ def feq(lattice, rho0, U):
     u = _f64(U)
     lib().orc_feq(LATTICES[lattice], rho0, _dp(u), _dp(g))
     return g
+
+
+def regularize(lattice, g):
+    """Hermite projection (orders 2, and 3 on the thermal lattices) of a
+    non-equilibrium vector g; returns a new array."""
+    out = _f64(g).copy()
+    lib().orc_regularize(LATTICES[lattice], _dp(out))
+    return out
 
 
 def moments(lattice, rho0, g):

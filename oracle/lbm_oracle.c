@@ -200,6 +200,46 @@ void orc_moments(int lattice, double rho0, const double* g, double U[4])
     moments_shifted(&L, rho0, g, U);
 }
 
+/* Regularised non-equilibrium part (the regularised Dirichlet schemes the
+ * paper names for future work, Sec. 5): the projection of g onto the
+ * Hermite polynomials of orders 2 and, on the thermal lattices, 3,
+ *   g_i <- w_i [ H2_i : a2 / (2 c_s^4) + H3_i : a3 / (6 c_s^6) ],
+ *   a_n = sum_i H_n(c_i) g_i,  H2_ab = c_a c_b - c_s^2 d_ab,
+ *   H3_abc = c_a c_b c_c - c_s^2 (c_a d_bc + c_b d_ac + c_c d_ab).
+ * The quadratures are exact for these products (D2Q9: degree 5 >= 4 for
+ * order 2; D2Q17, D2Q37: degree >= 6), so the projection keeps a2 and a3. */
+static void regularize(const lattice_t* L, double* g)
+{
+    const double cs2 = L->cs2;
+    double a2[3] = {0, 0, 0}, a3[4] = {0, 0, 0, 0};      /* xx xy yy; xxx xxy xyy yyy */
+    for (int i = 0; i < L->q; i++) {
+        double cx = L->c[i][0], cy = L->c[i][1];
+        a2[0] += (cx * cx - cs2) * g[i];
+        a2[1] += cx * cy * g[i];
+        a2[2] += (cy * cy - cs2) * g[i];
+        a3[0] += (cx * cx * cx - 3.0 * cs2 * cx) * g[i];
+        a3[1] += (cx * cx * cy - cs2 * cy) * g[i];
+        a3[2] += (cx * cy * cy - cs2 * cx) * g[i];
+        a3[3] += (cy * cy * cy - 3.0 * cs2 * cy) * g[i];
+    }
+    int third = L->order >= 3;
+    for (int i = 0; i < L->q; i++) {
+        double cx = L->c[i][0], cy = L->c[i][1];
+        double h2 = (cx * cx - cs2) * a2[0] + 2.0 * cx * cy * a2[1] + (cy * cy - cs2) * a2[2];
+        double h3 = (cx * cx * cx - 3.0 * cs2 * cx) * a3[0] + 3.0 * (cx * cx * cy - cs2 * cy) * a3[1]
+                  + 3.0 * (cx * cy * cy - cs2 * cx) * a3[2] + (cy * cy * cy - 3.0 * cs2 * cy) * a3[3];
+        g[i] = L->w[i] * (h2 / (2.0 * cs2 * cs2) + (third ? h3 / (6.0 * cs2 * cs2 * cs2) : 0.0));
+    }
+}
+
+int orc_regularize(int lattice, double* g)
+{
+    lattice_t L;
+    if (make_lattice(lattice, &L)) return -1;
+    regularize(&L, g);
+    return 0;
+}
+
 /* Viscous stress sigma' (Eq. LaplaceU) and heat flux q (Eqs. heatflux,
  * LaplaceT) from the non-equilibrium part f - f^eq of one node.  The
  * equilibrium part of the central third moment vanishes on D2Q37 and D2Q17
@@ -481,7 +521,7 @@ static int validate(const orc_params* p, const lattice_t* L)
     if (p->nx < 1 || p->ny < 1 || !(p->tau > 0.5)) return -1;
     if ((p->side[0] == ORC_PERIODIC) != (p->side[1] == ORC_PERIODIC)) return -1;
     if ((p->side[2] == ORC_PERIODIC) != (p->side[3] == ORC_PERIODIC)) return -1;
-    if (p->viscous < 0 || p->viscous > 2 || (p->dirichlet != 0 && p->dirichlet != 1)) return -1;
+    if (p->viscous < 0 || p->viscous > 2 || p->dirichlet < 0 || p->dirichlet > 2) return -1;
     for (int sd = 0; sd < 4; sd++) {
         if (p->side[sd] < 0 || p->side[sd] > 3) return -1;
         if (p->scheme[sd] < 0 || p->scheme[sd] > 3) return -1;
@@ -950,7 +990,8 @@ static void step_once(orc_sim* s)
         /* RK4 over all layers and corners at once. */
         rk4_step(4 * s->ncbc, s->Y, 1.0, band_rhs, s, s->work);
 
-        /* Mesoscopic Dirichlet condition: equilibrium (+ NEEP). */
+        /* Mesoscopic Dirichlet condition: equilibrium (+ NEEP, or its
+         * regularised form). */
         for (int u = 0; u < s->ncbc; u++) {
             int sd = s->u_side[u];
             const double* Unew = s->Y + 4 * u;
@@ -960,9 +1001,12 @@ static void step_once(orc_sim* s)
             int node = s->u_node[u], x = node % nx, y = node / nx;
             if (sd < 4) src = node_at(s, x - s->u_j[u] * SN[sd][0], y - s->u_j[u] * SN[sd][1]);
             else src = node_at(s, x - CD[sd - 4][0], y - CD[sd - 4][1]);
-            if (s->P.dirichlet == 1) {
+            if (s->P.dirichlet >= 1) {
+                double gn[QMAX];
                 feq_shifted(L, rho0, s->Ut1 + 4 * (size_t)src, gf);
-                for (int i = 0; i < q; i++) ge[i] += s->gnew[(size_t)src * q + i] - gf[i];
+                for (int i = 0; i < q; i++) gn[i] = s->gnew[(size_t)src * q + i] - gf[i];
+                if (s->P.dirichlet == 2) regularize(L, gn);
+                for (int i = 0; i < q; i++) ge[i] += gn[i];
             }
             if (sd < 4) {
                 memcpy(s->gnew + (size_t)node * q, ge, q * sizeof(double));

@@ -39,7 +39,8 @@ typedef struct {
     int side[4];       /* kind of each side (W,E,S,N)                          */
     int scheme[4];     /* incoming-wave scheme of each CBC side, Tab. CBCs     */
     int viscous;       /* 0: mesoscopic (Eqs. LaplaceU/T); 1: -FD; 2: none    */
-    int dirichlet;     /* 0: equilibrium BC; 1: NEEP (Eq. NEEP)                */
+    int dirichlet;     /* 0: equilibrium BC; 1: NEEP (Eq. NEEP); 2: NEEP with the
+                          non-equilibrium part regularised (orders 2, 3)       */
     double alpha_T;    /* alpha of Eqs. CBC-Relax / LODI-Relax (transversal)   */
     double beta_P;     /* beta of Eqs. CBC-Relax / LODI-Relax (pressure)       */
     double t_inf;      /* target transversal amplitude T^inf                   */
@@ -54,6 +55,9 @@ int    orc_lattice_info(int lattice, int* q, int* M, double* cs2, int* c, double
 
 /* Shifted equilibrium g_i = f^eq_i - w_i rho0 (Eqs. feq-3/feq-4). */
 void   orc_feq(int lattice, double rho0, const double U[4], double* g);
+/* Hermite projection of a non-equilibrium vector g[q] onto orders 2 (and 3
+ * on the thermal lattices), in place. */
+int    orc_regularize(int lattice, double* g);
 /* Moments (Eq. macro) of shifted populations: U = (drho, ux, uy, dT). */
 void   orc_moments(int lattice, double rho0, const double* g, double U[4]);
 

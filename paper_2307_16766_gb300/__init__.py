@@ -39,7 +39,7 @@ STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16}
 SIDES = {"periodic": 0, "cbc": 1, "inflow": 2, "zg": 3}
 SCHEMES = {"lodi": 0, "lodi_relax": 1, "cbc": 2, "cbc_relax": 3}
 VISCOUS = {"meso": 0, "fd": 1, "off": 2}
-DIRICHLET = {"eq": 0, "neep": 1}
+DIRICHLET = {"eq": 0, "neep": 1, "reg": 2}
 ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_ALLOC", -3: "LBM_ERR_CUDA",
           -4: "LBM_ERR_NUMERICAL", -5: "LBM_ERR_STATE", -6: "LBM_ERR_TIMEOUT"}
 

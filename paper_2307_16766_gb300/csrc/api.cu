@@ -139,7 +139,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     if (p->storage < LBM_F64 || p->storage > LBM_F16) { err = fmt("unknown storage %d", p->storage); return LBM_ERR_ARG; }
     if (!(p->rho0 > 0.0)) { err = "rho0 must be positive"; return LBM_ERR_ARG; }
     if (p->viscous < 0 || p->viscous > 2) { err = "unknown viscous mode"; return LBM_ERR_ARG; }
-    if (p->dirichlet < 0 || p->dirichlet > 1) { err = "unknown Dirichlet mode"; return LBM_ERR_ARG; }
+    if (p->dirichlet < 0 || p->dirichlet > 2) { err = "unknown Dirichlet mode"; return LBM_ERR_ARG; }
     for (int s = 0; s < 4; ++s) {
         if (p->side[s] < 0 || p->side[s] > 3) { err = fmt("unknown kind %d of side %d", p->side[s], s); return LBM_ERR_ARG; }
         if (p->scheme[s] < 0 || p->scheme[s] > 3) { err = fmt("unknown scheme of side %d", s); return LBM_ERR_ARG; }
@@ -414,7 +414,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
                     }
                     for (int k = 0; k < 5; ++k)
                         D.vs[k] = comp && D.kind < 4 && p->viscous == LBM_VISCOUS_MESO ? node_of(Dg.vs[k]) : 0;
-                    if (level[q] == 0 && p->dirichlet == LBM_DIRICHLET_NEEP) {
+                    if (level[q] == 0 && p->dirichlet != LBM_DIRICHLET_EQ) {
                         const int nl = node_of(Dg.wslot);
                         D.wslot = nl;
                         auto it = fxl.find(nl);
