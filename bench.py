@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch-leg", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -279,6 +281,66 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
     return res
 
 
+def run_batch(args, local_rank):
+    """The batched coefficient sweep (96 uneven D2Q9/D2Q37 FP32 runs, CBC on
+    all sides): every run stepped --batch-steps times through one Batch
+    (persistent launches replayed as CUDA graphs), timed with CUDA events on
+    the batch's stream; beside it the same runs stepped one after another
+    as separate Simulations.  The batch's populations (about 2 GB) exceed
+    L2, so no flush is needed between steps."""
+    import torch
+    import paper_2307_16766_gb300 as lbm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    runs = W.sweep_batch(96, storage="f32", steps=args.batch_steps)
+    cfgs = [c for c, _ in runs]
+    nodes = sum(c["nx"] * c["ny"] for c in cfgs)
+    B = lbm.Batch(cfgs, device=dev)
+    for r, (_, f) in enumerate(runs):
+        B[r].init_fields(*f)
+    B.step(max(3, args.warmup))                 # autotune, inflow-free graphs captured
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = args.batch_steps
+    with torch.cuda.stream(B.stream):
+        e0.record(B.stream)
+        B.step(K)
+        e1.record(B.stream)
+    torch.cuda.synchronize(dev)
+    batch_s = e0.elapsed_time(e1) / 1e3
+    finite = all(bool(np.all(np.isfinite(B[r].macros()[0]))) for r in range(0, len(B), 8))
+    ctas = {"D2Q9": B.ctas_per_sm("D2Q9", "f32"), "D2Q37": B.ctas_per_sm("D2Q37", "f32")}
+    B.close()
+
+    # the plain form: each run its own Simulation, stepped in turn
+    KS = min(K, 100)
+    sims = [lbm.Simulation(c, device=dev).init_fields(*f) for c, f in runs]
+    for s_ in sims:
+        s_.step(3)
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    e0.record(stream)
+    for s_ in sims:
+        s_.step(KS)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    seq_s = e0.elapsed_time(e1) / 1e3
+    for s_ in sims:
+        s_.close()
+    q = {"D2Q9": 9, "D2Q37": 37}
+    step_bytes = sum(2 * q[c["lattice"]] * 4 * c["nx"] * c["ny"] for c in cfgs)
+    return {"value": nodes * K / batch_s / 1e6, "unit": "MLUPS", "runs": len(cfgs),
+            "lattices": {k: sum(c["lattice"] == k for c in cfgs) for k in q},
+            "nodes_per_step": nodes, "steps": K, "ms_per_step": batch_s / K * 1e3,
+            "step_GBps": step_bytes * K / batch_s / 1e9, "ctas_per_sm": ctas,
+            "sequential_value": nodes * KS / seq_s / 1e6, "sequential_steps": KS,
+            "finite": finite,
+            "workload": "96-run CBC coefficient sweep: D2Q9/D2Q37 by seeded coin, nx, ny ~ U{128..512}, "
+                        "tau ~ U[0.55, 1], alpha_T, beta_P ~ U[0, 1], CBC-RELAX on four sides, viscous vector off, "
+                        "Gaussian pulses, FP32 storage"}
+
+
 def max_over_ranks(seconds, world):
     """The slowest rank's timed-region length (replicas run in lock step
     between the barriers; the job is as fast as its slowest GPU)."""
@@ -358,6 +420,10 @@ def main():
         a2.steps = min(args.steps, 50)
         fp64 = run_gpu(a2, rank, world, local_rank, "f64", want_e2e=False)
 
+    batch = None
+    if not args.no_batch_leg and args.storage == "f32":
+        batch = run_batch(args, local_rank)
+
     K = args.steps
     nodes = args.nx * args.ny
     step_s = max_over_ranks(res["step_ms_total"] / 1e3, world)
@@ -396,6 +462,8 @@ def main():
                             "phased_bulk_ms": fp64["bulk_ms_mean"],
                             "phased_boundary_ms": fp64["boundary_ms_mean"],
                             "interior_GBps": 2 * Q * 8 * fp64["interior_nodes"] / (fp64["interior_ms_mean"] / 1e3) / 1e9}
+        if batch is not None:
+            line["batch"] = batch
         if not args.no_cpu_baseline and world == 1:
             cfg, fields = workload(args.nx, args.ny, "f64", 1)
             line["cpu_baseline"] = cpu_baseline(cfg, fields)

@@ -181,6 +181,50 @@ const char* lbm_last_error(const lbm_handle* h);
 /* Free everything the handle owns.  NULL is ignored. */
 void lbm_destroy(lbm_handle* h);
 
+/* ---------------------------------------------------------------------- */
+/* Batches: many independent runs stepped together                        */
+/* ---------------------------------------------------------------------- */
+
+typedef struct lbm_batch lbm_batch;
+
+/* Create a batch of n independent runs -- lattices, grids, relaxation times
+ * and boundary parameters may all differ (the paper tunes its relaxation
+ * coefficients by such scans) -- each as lbm_create(lattice[r], nx[r],
+ * ny[r], tau[r], &params[r]) would.  Every step of the batch then issues,
+ * per lattice and storage, one band launch covering the boundary tiles of
+ * all its runs and one persistent bulk launch whose CTAs loop over the row
+ * segments of all its runs; after the first two steps each parity's step
+ * is captured once as a CUDA graph and replayed.  The persistent kernel's
+ * CTAs per SM are autotuned on the first step (fastest of 1..5) and cached
+ * per device, lattice, storage and size bucket in the text file named by
+ * the environment variable LBM_AUTOTUNE_CACHE (default
+ * ~/.cache/lbm_cbc_autotune.txt; an empty value turns the cache off).  At
+ * most 256 runs per lattice and storage.  Allocates with cudaMalloc. */
+int lbm_batch_create(int n, const int* lattice, const int* nx, const int* ny, const double* tau,
+                     const lbm_cbc_params* params, lbm_batch** out);
+
+/* The handle of run r (owned by the batch): use it with lbm_init_fields,
+ * lbm_get_macros, lbm_get_state and lbm_steps_done; stepping it alone
+ * (lbm_step) puts it out of step with the batch, which lbm_batch_step then
+ * rejects. */
+int lbm_batch_run(lbm_batch* b, int r, lbm_handle** h);
+
+/* Issue the batch's work, and that of every run, on stream (cudaStream_t). */
+int lbm_batch_set_stream(lbm_batch* b, void* stream);
+
+/* Advance every run n steps (asynchronous).  Every run must have been
+ * initialised. */
+int lbm_batch_step(lbm_batch* b, int n);
+
+/* The autotuned CTAs per SM of the persistent bulk kernel for the runs of
+ * one lattice and storage (0 before the first step or if there are none). */
+int lbm_batch_ctas_per_sm(const lbm_batch* b, int lattice, int storage);
+
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Free the batch and its runs.  NULL is ignored. */
+void lbm_batch_destroy(lbm_batch* b);
+
 /* Allocation-free boundary step for one side.  The paper has no counterpart:
  * this exists for callers that cannot allocate device memory -- code running
  * inside another framework's memory pool, under a no-allocation policy, or

@@ -93,6 +93,14 @@ def lib():
             "lbm_destroy": (None, [vp]),
             "lbm_cbc_side_step_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, pp,
                                                     vp, vp, vp, vp, vp]),
+            "lbm_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                           C.POINTER(C.c_int), dp, pp, C.POINTER(vp)]),
+            "lbm_batch_run": (C.c_int, [vp, C.c_int, C.POINTER(vp)]),
+            "lbm_batch_set_stream": (C.c_int, [vp, vp]),
+            "lbm_batch_step": (C.c_int, [vp, C.c_int]),
+            "lbm_batch_ctas_per_sm": (C.c_int, [vp, C.c_int, C.c_int]),
+            "lbm_batch_last_error": (C.c_char_p, [vp]),
+            "lbm_batch_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -254,6 +262,49 @@ def lbm_cbc_side_step_noalloc(lattice, side, length, tau, params, ub_ptr, strip_
                                            C.c_void_p(neq_t_ptr or None), C.c_void_p(stream_ptr or None)))
 
 
+def _check_batch(rc, b):
+    if rc != 0:
+        raise LbmError(rc, lib().lbm_batch_last_error(b).decode() if b else "")
+
+
+def lbm_batch_create(lattices, nxs, nys, taus, params):
+    n = len(lattices)
+    if not (len(nxs) == len(nys) == len(taus) == len(params) == n):
+        raise ValueError("lbm_batch_create: per-run lists differ in length")
+    ints = C.c_int * n
+    P = (LbmCbcParams * n)(*params)
+    b = C.c_void_p()
+    _check(lib().lbm_batch_create(n, ints(*lattices), ints(*nxs), ints(*nys),
+                                  (C.c_double * n)(*taus), P, C.byref(b)))
+    return b.value
+
+
+def lbm_batch_run(b, r):
+    h = C.c_void_p()
+    _check_batch(lib().lbm_batch_run(b, r, C.byref(h)), b)
+    return h.value
+
+
+def lbm_batch_set_stream(b, stream_ptr):
+    _check_batch(lib().lbm_batch_set_stream(b, stream_ptr), b)
+
+
+def lbm_batch_step(b, n):
+    _check_batch(lib().lbm_batch_step(b, n), b)
+
+
+def lbm_batch_ctas_per_sm(b, lattice, storage) -> int:
+    rc = lib().lbm_batch_ctas_per_sm(b, lattice, storage)
+    if rc < 0:
+        _check_batch(rc, b)
+    return rc
+
+
+def lbm_batch_destroy(b):
+    if b:
+        lib().lbm_batch_destroy(b)
+
+
 # ---------------------------------------------------------- convenience ---
 
 class Simulation:
@@ -324,3 +375,66 @@ class Simulation:
 
     def set_state(self, state: bytes):
         lbm_set_state(self.handle, state)
+
+
+class _BatchRun:
+    """View of one run of a Batch (its handle is owned by the batch)."""
+
+    def __init__(self, batch, r, cfg):
+        self.batch, self.index, self.cfg = batch, r, dict(cfg)
+        self.nx, self.ny = int(cfg["nx"]), int(cfg["ny"])
+        self.device = batch.device
+        self.handle = lbm_batch_run(batch.handle, r)
+
+    steps_done = Simulation.steps_done
+    init_fields = Simulation.init_fields
+    macros = Simulation.macros
+    get_state = Simulation.get_state
+
+
+class Batch:
+    """Many independent runs (lattices, sizes, relaxation times and boundary
+    parameters may all differ) stepped together: per lattice and storage one
+    batched band launch and one persistent bulk launch a step, replayed as a
+    CUDA graph once the first steps are done.  Work is issued on torch's
+    current CUDA stream."""
+
+    def __init__(self, cfgs, device=None):
+        import torch
+        cfgs = list(cfgs)
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self.handle = lbm_batch_create([LATTICES[c["lattice"]] for c in cfgs],
+                                           [int(c["nx"]) for c in cfgs],
+                                           [int(c["ny"]) for c in cfgs],
+                                           [float(c["tau"]) for c in cfgs],
+                                           [params_from_run(c) for c in cfgs])
+        self.stream = torch.cuda.current_stream(self.device)
+        lbm_batch_set_stream(self.handle, self.stream.cuda_stream)
+        self.runs = [_BatchRun(self, r, c) for r, c in enumerate(cfgs)]
+
+    def __len__(self):
+        return len(self.runs)
+
+    def __getitem__(self, r):
+        return self.runs[r]
+
+    def step(self, n=1):
+        lbm_batch_step(self.handle, n)
+        return self
+
+    def ctas_per_sm(self, lattice, storage):
+        return lbm_batch_ctas_per_sm(self.handle, LATTICES[lattice] if isinstance(lattice, str)
+                                     else lattice, STORAGES[storage] if isinstance(storage, str)
+                                     else storage)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -6,6 +6,7 @@
 // and RK4 stage buffers, a macro buffer and a status flag.  Every launch goes
 // to the handle's stream.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -15,6 +16,8 @@
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
+
+#include <sys/stat.h>
 
 #include <cudaTypedefs.h>
 
@@ -44,7 +47,10 @@ struct lbm_handle {
     size_t ws_bytes = 0;
     bool owns_ws = false;
     cudaStream_t stream = nullptr;
-    Region bulk{};           // nodes of the bulk kernel: all but the CBC strip nodes
+    Region bulk{};           // nodes of the bulk kernel
+    bool persistent = false; // single grids: the one-segment-per-CTA kernel measured faster
+    BulkRun* brun = nullptr; // its run descriptor (workspace)
+    int bulk_items = 0, bulk_grid = 0;
     size_t band_pad = 0;     // extra shared memory per band CTA (SM reservation)
     cudaStream_t aux = nullptr;              // internal stream: the bulk beside the band
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -80,7 +86,7 @@ struct Plan {
     std::vector<int> inflow;
     double Uin[4] = {0, 0, 0, 0};
     size_t off_f0 = 0, off_f1 = 0, off_sU = 0, off_sN = 0, off_Ub = 0, off_ud = 0, off_ld = 0,
-           off_sn = 0, off_zg = 0, off_in = 0, off_macro = 0, off_flag = 0,
+           off_sn = 0, off_brun = 0, off_zg = 0, off_in = 0, off_macro = 0, off_flag = 0,
            total = 0;
 };
 
@@ -496,6 +502,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     pl.off_ud = take(nu * sizeof(UDesc));
     pl.off_ld = take(pl.ldp.size() * sizeof(UDesc));
     pl.off_sn = take(pl.snp.size() * sizeof(StripNode));
+    pl.off_brun = take(sizeof(BulkRun));
     pl.off_zg = take(pl.zg.size() * sizeof(int2));
     pl.off_in = take(pl.inflow.size() * sizeof(int));
     pl.off_macro = take((size_t)4 * nx * ny * 8);
@@ -609,6 +616,35 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
             const int rc = encode_population_map(h, h->f[b], depths[k] <= h->Q ? depths[k] : 1, &h->tmap[b][k]);
             if (rc != LBM_OK) return rc;
         }
+    // Run descriptor of the persistent bulk kernel (this grid alone).
+    {
+        BulkRun r;
+        std::memset(&r, 0, sizeof r);
+        CUtensorMap* dst[5] = {&r.maps[0].m7, &r.maps[0].m5, &r.maps[0].m3, &r.maps[0].m2, &r.maps[0].m1};
+        CUtensorMap* dst1[5] = {&r.maps[1].m7, &r.maps[1].m5, &r.maps[1].m3, &r.maps[1].m2, &r.maps[1].m1};
+        for (int k = 0; k < 5; ++k) {
+            *dst[k] = h->tmap[0][k];
+            *dst1[k] = h->tmap[1][k];
+        }
+        r.f[0] = h->f[0];
+        r.f[1] = h->f[1];
+        r.status = h->flag + 1;
+        r.G = h->G;
+        r.R = h->bulk;
+        r.seg0 = h->bulk.x0 / 128;
+        r.nseg = (h->bulk.x1 + 127) / 128 - r.seg0;
+        r.first = 0;
+        h->bulk_items = h->bulk.x1 > h->bulk.x0 ? r.nseg * (h->bulk.y1 - h->bulk.y0) : 0;
+        h->brun = at<BulkRun>(ws, pl.off_brun);
+        int dev = 0, nsm = 0;
+        cudaError_t e0 = cudaGetDevice(&dev);
+        if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(h->brun, &r, sizeof r, cudaMemcpyHostToDevice, h->stream);
+        if (e0 != cudaSuccess) return cuda_fail(h, e0, "persistent bulk set-up");
+        h->bulk_grid = nsm * 5;
+        if (prepare_bulk_persistent(h->lattice, h->storage) != 0)
+            return cuda_fail(h, cudaGetLastError(), "persistent bulk shared memory");
+    }
     // The bulk kernel runs on an internal stream beside the band kernel,
     // which stays on the handle's stream so that it is queued first.
     // (Reserving whole SMs for the band through its shared-memory request
@@ -658,8 +694,12 @@ int bulk(lbm_handle* h, int par, cudaStream_t st)
 {
     int rc = mark(h, 0, st);
     if (rc != LBM_OK) return rc;
-    rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->bulk, h->tmap[par], h->f[par],
-                     h->f[par ^ 1], h->flag + 1, st);
+    if (h->persistent)
+        rc = launch_bulk_persistent(h->lattice, h->storage, h->brun, 1, h->bulk_items, par,
+                                    h->bulk_grid, st);
+    else
+        rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->bulk, h->tmap[par], h->f[par],
+                         h->f[par ^ 1], h->flag + 1, st);
     if (rc) return check_launch(h, rc, "bulk kernel");
     return mark(h, 1, st);
 }
@@ -1044,6 +1084,386 @@ void lbm_destroy(lbm_handle* h)
     release_streams(h);
     if (h->owns_ws && h->ws) cudaFree(h->ws);
     delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many independent runs stepped together
+// ---------------------------------------------------------------------------
+
+struct lbm_batch {
+    int n = 0;
+    std::vector<lbm_handle*> runs;
+    struct Group {
+        int lattice = 0, storage = 0;
+        std::vector<int> members;          // run indices
+        BulkRun* bulk = nullptr;           // device: one per member
+        int total_items = 0, grid = 0, ctas_per_sm = 0;
+        BandRun* band = nullptr;           // device: one per member
+        int2* tile_run = nullptr;          // device: (member, tile) per band tile
+        int n_tiles = 0;
+        size_t band_smem = 0;
+    };
+    std::vector<Group> groups;
+    void* dev = nullptr;                   // the groups' descriptor arrays
+    cudaStream_t stream = nullptr, aux = nullptr, cap = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool tuned = false;
+    int nsm = 0;
+    long long steps = 0;
+    std::string err;
+};
+
+namespace {
+
+int batch_fail(lbm_batch* b, cudaError_t e, const char* what)
+{
+    b->err = fmt("%s: %s", what, cudaGetErrorString(e));
+    return LBM_ERR_CUDA;
+}
+
+// Autotuned CTAs per SM of the persistent bulk kernel, cached in a text file
+// (LBM_AUTOTUNE_CACHE, default ~/.cache/lbm_cbc_autotune.txt; empty = off):
+// one line "device lattice storage bucket ctas_per_sm" per tuned case, the
+// bucket being log2 of the group's work items.
+std::string autotune_path()
+{
+    const char* p = getenv("LBM_AUTOTUNE_CACHE");
+    if (p) return p;
+    const char* home = getenv("HOME");
+    return home ? std::string(home) + "/.cache/lbm_cbc_autotune.txt" : std::string();
+}
+
+std::string autotune_key(int lattice, int storage, int items)
+{
+    int dev = 0;
+    cudaDeviceProp prop;
+    std::memset(&prop, 0, sizeof prop);
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaGetDeviceProperties(&prop, dev);
+    std::string name = prop.name;
+    for (char& c : name)
+        if (c == ' ') c = '_';
+    int bucket = 0;
+    while ((1 << bucket) < items) ++bucket;
+    return fmt("%s %d %d %d", name.c_str(), lattice, storage, bucket);
+}
+
+int autotune_lookup(const std::string& key)
+{
+    const std::string path = autotune_path();
+    if (path.empty()) return 0;
+    FILE* fp = fopen(path.c_str(), "r");
+    if (!fp) return 0;
+    char line[512];
+    int found = 0;
+    while (fgets(line, sizeof line, fp)) {
+        std::string l(line);
+        const size_t sp = l.find_last_of(' ');
+        if (sp == std::string::npos) continue;
+        if (l.compare(0, sp, key) == 0) found = atoi(l.c_str() + sp + 1);   // last entry wins
+    }
+    fclose(fp);
+    return found >= 1 && found <= 8 ? found : 0;
+}
+
+void autotune_store(const std::string& key, int value)
+{
+    const std::string path = autotune_path();
+    if (path.empty()) return;
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos) {
+        const std::string dir = path.substr(0, slash);
+        for (size_t i = 1; i <= dir.size(); ++i)        // mkdir -p
+            if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+    }
+    FILE* fp = fopen(path.c_str(), "a");
+    if (!fp) return;
+    fprintf(fp, "%s %d\n", key.c_str(), value);
+    fclose(fp);
+}
+
+// One step of every run: per group one batched band launch on the batch's
+// stream and one persistent bulk launch (plus zero-gradient copies) on the
+// internal stream, forked and joined like lbm_step.
+int batch_issue_step(lbm_batch* b, int par, cudaStream_t s0, bool with_inflow)
+{
+    // inflow equilibria (once per buffer) ahead of the fork, so that every
+    // kernel of the step comes after them
+    if (with_inflow)
+        for (lbm_handle* h : b->runs)
+            if (h->n_inflow > 0 && !h->inflow_done[par ^ 1]) {
+                if (launch_inflow(h->lattice, h->storage, h->G, h->inflow_nodes, h->n_inflow, h->Uin,
+                                  h->f[par ^ 1], s0))
+                    return batch_fail(b, cudaGetLastError(), "inflow kernel");
+                h->inflow_done[par ^ 1] = true;
+            }
+    cudaError_t e = cudaEventRecord(b->ev_fork, s0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
+    if (e != cudaSuccess) return batch_fail(b, e, "fork");
+    for (auto& g : b->groups) {
+        if (g.n_tiles > 0 &&
+            launch_band_batch(g.lattice, g.storage, g.band, g.tile_run, g.n_tiles, g.band_smem, par, s0))
+            return batch_fail(b, cudaGetLastError(), "batched band kernel");
+        if (launch_bulk_persistent(g.lattice, g.storage, g.bulk, int(g.members.size()), g.total_items, par,
+                                   g.grid, b->aux))
+            return batch_fail(b, cudaGetLastError(), "persistent bulk kernel");
+        for (int m : g.members) {
+            lbm_handle* h = b->runs[m];
+            if (h->B.n_zg > 0 && launch_zg(h->lattice, h->storage, h->G, h->B, h->f[par ^ 1], b->aux))
+                return batch_fail(b, cudaGetLastError(), "zero-gradient kernel");
+        }
+    }
+    e = cudaEventRecord(b->ev_join, b->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, b->ev_join, 0);
+    return e == cudaSuccess ? LBM_OK : batch_fail(b, e, "join");
+}
+
+// Pick the persistent bulk kernel's CTAs per SM for each group: the fastest
+// of 1..5 over three timed launches each (the launches rewrite the new
+// buffer from the current one, which the following step rewrites again).
+int batch_autotune(lbm_batch* b)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return batch_fail(b, e, "autotune events");
+    const int par = int(b->steps & 1);
+    for (auto& g : b->groups) {
+        const std::string key = autotune_key(g.lattice, g.storage, g.total_items);
+        int best = autotune_lookup(key);
+        if (!best) {
+            float best_ms = 1e30f;
+            for (int m = 1; m <= 5; ++m) {
+                const int grid = b->nsm * m;
+                launch_bulk_persistent(g.lattice, g.storage, g.bulk, int(g.members.size()), g.total_items, par,
+                                       grid, b->stream);                 // warm-up
+                cudaEventRecord(e0, b->stream);
+                for (int r = 0; r < 3; ++r)
+                    launch_bulk_persistent(g.lattice, g.storage, g.bulk, int(g.members.size()), g.total_items,
+                                           par, grid, b->stream);
+                cudaEventRecord(e1, b->stream);
+                e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return batch_fail(b, e, "autotune");
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) { best_ms = ms; best = m; }
+            }
+            autotune_store(key, best);
+        }
+        g.ctas_per_sm = best;
+        g.grid = b->nsm * best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tuned = true;
+    return LBM_OK;
+}
+
+void batch_release(lbm_batch* b)
+{
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    for (int k = 0; k < 2; ++k)
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->aux) cudaStreamDestroy(b->aux);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->dev) cudaFree(b->dev);
+    for (lbm_handle* h : b->runs) lbm_destroy(h);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(int n, const int* lattice, const int* nx, const int* ny, const double* tau,
+                     const lbm_cbc_params* params, lbm_batch** out)
+{
+    if (!out || n < 1 || !lattice || !nx || !ny || !tau || !params) return LBM_ERR_ARG;
+    *out = nullptr;
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ERR_ALLOC;
+    b->n = n;
+    for (int r = 0; r < n; ++r) {
+        lbm_handle* h = nullptr;
+        const int rc = lbm_create(lattice[r], nx[r], ny[r], tau[r], params + r, &h);
+        if (rc != LBM_OK) {
+            fprintf(stderr, "lbm_batch_create: run %d rejected\n", r);
+            batch_release(b);
+            return rc;
+        }
+        b->runs.push_back(h);
+    }
+    // groups by lattice and storage
+    for (int r = 0; r < n; ++r) {
+        lbm_handle* h = b->runs[r];
+        lbm_batch::Group* g = nullptr;
+        for (auto& x : b->groups)
+            if (x.lattice == h->lattice && x.storage == h->storage) g = &x;
+        if (!g) {
+            b->groups.emplace_back();
+            g = &b->groups.back();
+            g->lattice = h->lattice;
+            g->storage = h->storage;
+        }
+        g->members.push_back(r);
+    }
+    // descriptor arrays (host copies, then one device allocation)
+    std::vector<std::vector<BulkRun>> bulk(b->groups.size());
+    std::vector<std::vector<BandRun>> band(b->groups.size());
+    std::vector<std::vector<int2>> tiles(b->groups.size());
+    size_t bytes = 0;
+    std::vector<size_t> off_bulk, off_band, off_tiles;
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        auto& g = b->groups[gi];
+        if ((int)g.members.size() > kMaxBatchRuns) {
+            fprintf(stderr, "lbm_batch_create: more than %d runs of one lattice and storage\n", kMaxBatchRuns);
+            batch_release(b);
+            return LBM_ERR_ARG;
+        }
+        int first = 0;
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            lbm_handle* h = b->runs[g.members[k]];
+            BulkRun r;
+            const cudaError_t e = cudaMemcpy(&r, h->brun, sizeof r, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                fprintf(stderr, "lbm_batch_create: %s\n", cudaGetErrorString(e));
+                batch_release(b);
+                return LBM_ERR_CUDA;
+            }
+            r.first = first;
+            first += h->bulk_items;
+            bulk[gi].push_back(r);
+            BandRun br;
+            std::memset(&br, 0, sizeof br);
+            br.G = h->G;
+            br.O = h->O;
+            br.B = h->B;
+            br.E = h->E;
+            br.f[0] = h->f[0];
+            br.f[1] = h->f[1];
+            band[gi].push_back(br);
+            for (int t = 0; t < h->B.n_tiles; ++t) tiles[gi].push_back(make_int2(int(k), t));
+            g.band_smem = std::max(g.band_smem, band_dynamic_smem(h->lattice, h->storage, h->B));
+        }
+        g.total_items = first;
+        g.n_tiles = int(tiles[gi].size());
+        off_bulk.push_back(bytes);
+        bytes = align_up(bytes + bulk[gi].size() * sizeof(BulkRun));
+        off_band.push_back(bytes);
+        bytes = align_up(bytes + band[gi].size() * sizeof(BandRun));
+        off_tiles.push_back(bytes);
+        bytes = align_up(bytes + std::max<size_t>(1, tiles[gi].size()) * sizeof(int2));
+    }
+    cudaError_t e = cudaMalloc(&b->dev, bytes);
+    for (size_t gi = 0; e == cudaSuccess && gi < b->groups.size(); ++gi) {
+        auto& g = b->groups[gi];
+        g.bulk = at<BulkRun>(b->dev, off_bulk[gi]);
+        g.band = at<BandRun>(b->dev, off_band[gi]);
+        g.tile_run = at<int2>(b->dev, off_tiles[gi]);
+        e = cudaMemcpy(g.bulk, bulk[gi].data(), bulk[gi].size() * sizeof(BulkRun), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.band, band[gi].data(), band[gi].size() * sizeof(BandRun), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !tiles[gi].empty())
+            e = cudaMemcpy(g.tile_run, tiles[gi].data(), tiles[gi].size() * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && prepare_bulk_persistent(g.lattice, g.storage)) e = cudaGetLastError();
+        if (e == cudaSuccess && prepare_band_batch(g.lattice, g.storage, g.band_smem)) e = cudaGetLastError();
+    }
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+    for (auto& g : b->groups) g.grid = b->nsm * 4;               // until tuned
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "lbm_batch_create: %s\n", cudaGetErrorString(e));
+        batch_release(b);
+        return LBM_ERR_CUDA;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_run(lbm_batch* b, int run, lbm_handle** h)
+{
+    if (!b || !h || run < 0 || run >= b->n) return LBM_ERR_ARG;
+    *h = b->runs[run];
+    return LBM_OK;
+}
+
+int lbm_batch_set_stream(lbm_batch* b, void* stream)
+{
+    if (!b) return LBM_ERR_ARG;
+    b->stream = static_cast<cudaStream_t>(stream);
+    for (lbm_handle* h : b->runs) h->stream = b->stream;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int n)
+{
+    if (!b || n < 0) return LBM_ERR_ARG;
+    for (lbm_handle* h : b->runs) {
+        if (!h->initialized) { b->err = "lbm_batch_step before every run's lbm_init_fields"; return LBM_ERR_STATE; }
+        if (h->steps != b->runs[0]->steps) { b->err = "runs of a batch stepped apart"; return LBM_ERR_STATE; }
+    }
+    b->steps = b->runs[0]->steps;
+    if (n > 0 && !b->tuned) {
+        const int rc = batch_autotune(b);
+        if (rc != LBM_OK) return rc;
+    }
+    for (int i = 0; i < n; ++i) {
+        const int par = int(b->steps & 1);
+        bool eager = false;
+        for (lbm_handle* h : b->runs)
+            if (h->n_inflow > 0 && !(h->inflow_done[0] && h->inflow_done[1])) eager = true;
+        if (eager) {
+            const int rc = batch_issue_step(b, par, b->stream, true);
+            if (rc != LBM_OK) return rc;
+        } else {
+            if (!b->graph[par]) {
+                // capture this parity's step once on an internal stream
+                cudaGraph_t gr = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) return batch_fail(b, e, "capture");
+                const int rc = batch_issue_step(b, par, b->cap, false);
+                e = cudaStreamEndCapture(b->cap, &gr);
+                if (rc != LBM_OK) return rc;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[par], gr, 0);
+                if (gr) cudaGraphDestroy(gr);
+                if (e != cudaSuccess) return batch_fail(b, e, "graph");
+            }
+            const cudaError_t e = cudaGraphLaunch(b->graph[par], b->stream);
+            if (e != cudaSuccess) return batch_fail(b, e, "graph launch");
+        }
+        b->steps++;
+        for (lbm_handle* h : b->runs) h->steps++;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_ctas_per_sm(const lbm_batch* b, int lattice, int storage)
+{
+    if (!b) return LBM_ERR_ARG;
+    for (const auto& g : b->groups)
+        if (g.lattice == lattice && g.storage == storage) return g.ctas_per_sm;
+    return 0;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : "NULL batch"; }
+
+void lbm_batch_destroy(lbm_batch* b)
+{
+    if (b) batch_release(b);
 }
 
 }  // extern "C"

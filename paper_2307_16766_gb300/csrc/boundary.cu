@@ -635,16 +635,15 @@ __device__ __forceinline__ double lab_component(int m, int kind, double r, doubl
 // 3. The owners write U(t + 1) and the mesoscopic Dirichlet populations
 //    (equilibrium or Eq. NEEP), shared out over the four CTAs.
 template <int LAT, typename S>
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads)
-    k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
-           int par_t)
+__device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const Band& B,
+                                          const Export& E, const S* __restrict__ fin,
+                                          S* __restrict__ f, int par_t, int tile)
 {
     using L = Lat<LAT>;
     using C = typename Store<S>::C;
     constexpr bool TH = L::THERMAL;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = int(cl.block_rank());
-    const int tile = blockIdx.x / kCluster;
     const int l = threadIdx.x;
     __shared__ __align__(16) double Ys[kTileThreads * 4];   // stage values, lab frame
     __shared__ __align__(16) double Xp[kTileThreads * 8];   // shares of the characteristic system
@@ -896,6 +895,32 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads)
     cl.sync();                          // no CTA leaves while its Fx may be read
 }
 
+template <int LAT, typename S>
+__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads)
+    k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
+           int par_t)
+{
+    band_tile<LAT, S>(G, O, B, E, fin, f, par_t, blockIdx.x / kCluster);
+}
+
+// Band tiles of many grids in one launch: cluster t takes tile tile_run[t].y
+// of run tile_run[t].x, whose structures it copies to shared memory first.
+template <int LAT, typename S>
+__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads)
+    k_band_batch(const BandRun* __restrict__ runs, const int2* __restrict__ tile_run, int par_t)
+{
+    __shared__ __align__(16) BandRun R;
+    const int2 tr = tile_run[blockIdx.x / kCluster];
+    {
+        const int* src = reinterpret_cast<const int*>(runs + tr.x);
+        int* dst = reinterpret_cast<int*>(&R);
+        for (int k = threadIdx.x; k < int(sizeof(BandRun) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    band_tile<LAT, S>(R.G, R.O, R.B, R.E, static_cast<const S*>(R.f[par_t]),
+                      static_cast<S*>(R.f[par_t ^ 1]), par_t, tr.y);
+}
+
 // Zero gradient (Eq. zg-bc): the post-collision populations of x_f.
 template <int LAT, typename S>
 __global__ void k_zg(Geom G, Band B, S* __restrict__ f)
@@ -922,6 +947,22 @@ int boundary_t(const Geom& G, const Offsets& O, const Export& E, const Band& B, 
     k_band<LAT, S><<<B.n_tiles * kCluster, kTileThreads, smem, st>>>(
         G, O, B, E, static_cast<const S*>(fin), static_cast<S*>(fnew), par_t);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int LAT, typename S>
+int band_batch_t(const BandRun* runs, const int2* tile_run, int n_tiles, size_t smem, int par_t,
+                 cudaStream_t st)
+{
+    if (n_tiles == 0) return 0;
+    k_band_batch<LAT, S><<<n_tiles * kCluster, kTileThreads, smem, st>>>(runs, tile_run, par_t);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int LAT, typename S>
+int prepare_batch_t(size_t smem)
+{
+    return cudaFuncSetAttribute(k_band_batch<LAT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(smem)) == cudaSuccess ? 0 : -1;
 }
 
 template <int LAT, typename S>
@@ -981,6 +1022,23 @@ size_t band_dynamic_smem(int lat, int storage, const Band& B)
 int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad)
 {
 #define CALL(L, S) prepare_t<L, S>(B, smem_pad)
+    BAND_DISPATCH(lat, storage, CALL);
+#undef CALL
+    return -1;
+}
+
+int launch_band_batch(int lat, int storage, const BandRun* runs, const int2* tile_run, int n_tiles,
+                      size_t smem, int par_t, cudaStream_t st)
+{
+#define CALL(L, S) band_batch_t<L, S>(runs, tile_run, n_tiles, smem, par_t, st)
+    BAND_DISPATCH(lat, storage, CALL);
+#undef CALL
+    return -1;
+}
+
+int prepare_band_batch(int lat, int storage, size_t smem)
+{
+#define CALL(L, S) prepare_batch_t<L, S>(smem)
     BAND_DISPATCH(lat, storage, CALL);
 #undef CALL
     return -1;

@@ -65,10 +65,10 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Wait for the transaction barrier (phase 0) with a 1 s limit; on timeout
-// record it in *status and wait once more (again bounded) for copies still
-// in flight before giving up.
-__device__ bool wait_tx(unsigned long long* bar, int* status)
+// Wait for phase `parity` of a transaction barrier with a 1 s limit; on
+// timeout record it in *status and wait once more (again bounded) for copies
+// still in flight before giving up.
+__device__ bool wait_tx(unsigned long long* bar, int* status, unsigned parity = 0)
 {
     const unsigned a = smem_u32(bar);
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -80,7 +80,7 @@ __device__ bool wait_tx(unsigned long long* bar, int* status)
                 " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                 " selp.u32 %0, 1, 0, p;\n}"
                 : "=r"(ok)
-                : "r"(a), "r"(0u)
+                : "r"(a), "r"(parity)
                 : "memory");
             if (ok) return attempt == 0;
             if (global_ns() - t0 > 1000000000ull) break;
@@ -90,11 +90,6 @@ __device__ bool wait_tx(unsigned long long* bar, int* status)
     return false;
 }
 
-// Tensor maps of the input buffer: box depths 7, 5, 3, 2 and 1 planes
-// (the c_y group sizes of the three lattices).
-struct Maps {
-    CUtensorMap m7, m5, m3, m2, m1;
-};
 
 // One 3D tensor copy per c_y group; every offset, coordinate shift and map
 // choice is a template constant so nothing is looked up at run time.
@@ -195,6 +190,117 @@ __global__ void __launch_bounds__(kBulkThreads)
         pull_plain<LAT, S, C>(G, O, fin, x, y, g);
     }
     collide_store<LAT, S, C>(G, O, fout, x, y, g);
+}
+
+// Persistent form of k_bulk for one or many grids of one lattice and
+// storage: `grid` CTAs loop over all work items (run, row, 128-node segment)
+// of the runs in turn, and each CTA keeps the tensor copies of its next item
+// in flight while it computes the current one (two staging buffers, one
+// transaction barrier each).  The arithmetic per node is that of k_bulk.
+template <int LAT, typename S>
+__global__ void __launch_bounds__(kBulkThreads)
+    k_bulk_persistent(const BulkRun* __restrict__ runs, int n_runs, int total, int par)
+{
+    using L = Lat<LAT>;
+    using C = typename Store<S>::C;
+    using BX = Stage<LAT, S>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];   // 2 x BX::TOTAL
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ int s_first[kMaxBatchRuns + 1];
+    for (int k = threadIdx.x; k <= n_runs; k += blockDim.x) s_first[k] = k < n_runs ? runs[k].first : total;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    // work item w -> run, segment origin x0, row y; staged unless its
+    // sources wrap around a periodic axis
+    struct Item {
+        int run, x0, y;
+        bool staged;
+    };
+    auto locate = [&](int w) {
+        int lo = 0, hi = n_runs - 1;
+        while (lo < hi) {                   // last run whose first item is <= w
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_first[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const BulkRun& R = runs[lo];
+        const int local = w - s_first[lo];
+        Item it;
+        it.run = lo;
+        it.x0 = (R.seg0 + local % R.nseg) * kBulkThreads;
+        it.y = R.R.y0 + local / R.nseg;
+        it.staged = !((R.G.pery && (it.y < L::M || it.y >= R.G.ny - L::M)) ||
+                      (R.G.perx && (it.x0 - L::M < 0 || it.x0 + kBulkThreads + L::M > R.G.nx)));
+        return it;
+    };
+    auto issue = [&](const Item& it, int stage) {
+        if (threadIdx.x != 0 || !it.staged) return;
+        const unsigned b = smem_u32(&bar[stage]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(BX::TX)
+                     : "memory");
+        issue_copies<LAT, S>(runs[it.run].maps[par], smem_raw + stage * BX::TOTAL, it.x0, it.y, b,
+                             std::make_integer_sequence<int, L::NG>{});
+    };
+
+    unsigned phase0 = 0u, phase1 = 0u;      // next phase of each stage's barrier
+    int w = blockIdx.x, stage = 0;
+    Item cur{0, 0, 0, false};
+    if (w < total) {
+        cur = locate(w);
+        issue(cur, 0);
+    }
+    while (w < total) {
+        const int wn = w + gridDim.x;
+        Item nxt{0, 0, 0, false};
+        if (wn < total) {                   // the buffer of stage ^ 1 was released last iteration
+            nxt = locate(wn);
+            issue(nxt, stage ^ 1);
+        }
+        const BulkRun& R = runs[cur.run];
+        const int x = cur.x0 + threadIdx.x;
+        const bool valid = x >= R.R.x0 && x < R.R.x1;
+        bool ok = true;
+        C g[L::Q];
+        if (cur.staged) {
+            ok = wait_tx(&bar[stage], R.status, stage ? phase1 : phase0);
+            if (stage) phase1 ^= 1u;
+            else phase0 ^= 1u;
+            ok = __syncthreads_and(ok);     // one decision for the whole CTA
+            if (ok && valid)
+                gather_staged<LAT, S, C>(g, reinterpret_cast<const S*>(smem_raw + stage * BX::TOTAL),
+                                         threadIdx.x, std::make_integer_sequence<int, L::Q>{});
+        } else if (valid) {
+            pull_plain_planes<LAT, S, C>(R.G, static_cast<const S*>(R.f[par]), x, cur.y, g);
+        }
+        if (!ok) {
+            // a copy never completed: wait (bounded) for the one in flight
+            // for the next item, then leave
+            if (wn < total && nxt.staged) wait_tx(&bar[stage ^ 1], R.status, stage ? phase0 : phase1);
+            return;
+        }
+        if (valid) {
+            if (Store<S>::SCALED) {
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) g[i] *= C(L::w(i));
+            }
+            S* out = static_cast<S*>(R.f[par ^ 1]) + (cur.y * R.G.nxp + x);
+            const int plane = int(R.G.plane);
+            collide<LAT, C>(R.G, g, [&](int i, C v) {
+                if (Store<S>::SCALED) v *= C(1.0 / L::w(i));
+                Store<S>::put(out + L::plane_of(i) * plane, v);
+            });
+        }
+        __syncthreads();                    // stage buffer read by all before its reuse
+        w = wn;
+        cur = nxt;
+        stage ^= 1;
+    }
 }
 
 template <int LAT, typename S>
@@ -349,6 +455,22 @@ int bulk_t(const Geom& G, const Offsets& O, const Region& R, const CUtensorMap* 
 }
 
 template <int LAT, typename S>
+int bulk_persistent_t(const BulkRun* runs, int n_runs, int total, int par, int grid, cudaStream_t st)
+{
+    if (total <= 0) return 0;
+    if (n_runs > kMaxBatchRuns) return -1;
+    k_bulk_persistent<LAT, S><<<grid, kBulkThreads, 2 * Stage<LAT, S>::TOTAL, st>>>(runs, n_runs, total, par);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int LAT, typename S>
+int prepare_persistent_t()
+{
+    return cudaFuncSetAttribute(k_bulk_persistent<LAT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                2 * Stage<LAT, S>::TOTAL) == cudaSuccess ? 0 : -1;
+}
+
+template <int LAT, typename S>
 int macros_t(const Geom& G, const void* f, double* rho, double* ux, double* uy, double* T,
              int* flag, cudaStream_t st)
 {
@@ -403,6 +525,21 @@ int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Reg
 #undef CALL
 }
 
+
+int launch_bulk_persistent(int lat, int storage, const BulkRun* runs, int n_runs, int total, int par,
+                           int grid, cudaStream_t st)
+{
+#define CALL(L, S) bulk_persistent_t<L, S>(runs, n_runs, total, par, grid, st)
+    LBM_DISPATCH(lat, storage, CALL);
+#undef CALL
+}
+
+int prepare_bulk_persistent(int lat, int storage)
+{
+#define CALL(L, S) prepare_persistent_t<L, S>()
+    LBM_DISPATCH(lat, storage, CALL);
+#undef CALL
+}
 
 int launch_macros(int lat, int storage, const Geom& G, const void* f, double* rho, double* ux,
                   double* uy, double* T, int* flag, cudaStream_t st)

@@ -66,6 +66,23 @@ __device__ __forceinline__ void pull_plain(const Geom& G, const Offsets& O,
     }
 }
 
+// The same with the plane offsets computed from the plane size (for kernels
+// that serve several grids in one launch).
+template <int LAT, typename S, typename C>
+__device__ __forceinline__ void pull_plain_planes(const Geom& G, const S* __restrict__ fin, int x,
+                                                  int y, C* g)
+{
+    using L = Lat<LAT>;
+    const int plane = int(G.plane);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        int xs = x - L::cx(i), ys = y - L::cy(i);
+        if (L::cx(i) && G.perx) xs = xs < 0 ? xs + G.nx : (xs >= G.nx ? xs - G.nx : xs);
+        if (L::cy(i) && G.pery) ys = ys < 0 ? ys + G.ny : (ys >= G.ny ? ys - G.ny : ys);
+        g[i] = C(Store<S>::load(fin + (L::plane_of(i) * plane + ys * G.nxp + xs)));
+    }
+}
+
 // Moments (Eq. macro) and BGK collision (Eq. bgk) of one node whose pulled
 // populations are in g (already multiplied by w for scaled storage).  The
 // post-collision value of velocity i goes to put(i, value); the moments of

@@ -416,6 +416,27 @@ struct Region {
     int x0, x1, y0, y1;
 };
 
+// Tensor maps of one population buffer: box depths 7, 5, 3, 2 and 1 planes
+// (the c_y group sizes of the three lattices).
+struct Maps {
+    CUtensorMap m7, m5, m3, m2, m1;
+};
+
+// Most runs one persistent bulk launch takes.
+constexpr int kMaxBatchRuns = 256;
+
+// One run of the persistent bulk kernel, in device memory: tensor maps and
+// pointers of its two population buffers, geometry, the bulk region and
+// the first of its work items (one item = one 128-node row segment).
+struct BulkRun {
+    Maps maps[2];
+    void* f[2];
+    int* status;
+    Geom G;
+    Region R;
+    int seg0, nseg, first, pad;
+};
+
 
 // Offsets (in elements) of the pull sources and of the output planes, used
 // by the bulk kernel away from periodic wrap-around: source of velocity i is
@@ -531,8 +552,28 @@ int launch_macros(int lat, int storage, const Geom& G, const void* f, double* rh
 int launch_boundary(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
                     const Band& B, const void* fin, void* fnew, int par_t, size_t smem_pad,
                     cudaStream_t st);
+// One grid of the batched band kernel, in device memory.
+struct BandRun {
+    Geom G;
+    Offsets O;
+    Band B;
+    Export E;
+    void* f[2];
+};
+// Band tiles of many grids of one lattice and storage in one launch:
+// tile_run[t] = (run, tile of that run); smem = the largest band_dynamic_smem.
+int launch_band_batch(int lat, int storage, const BandRun* runs, const int2* tile_run, int n_tiles,
+                      size_t smem, int par_t, cudaStream_t st);
+int prepare_band_batch(int lat, int storage, size_t smem);
 // Dynamic shared memory the band kernel needs per CTA (without padding).
 size_t band_dynamic_smem(int lat, int storage, const Band& B);
+// Persistent bulk step of n_runs runs of one lattice and storage (buffer
+// par -> par ^ 1 of each) with `grid` CTAs looping over the total work
+// items, a two-stage tensor-copy pipeline per CTA.
+int launch_bulk_persistent(int lat, int storage, const BulkRun* runs, int n_runs, int total, int par,
+                           int grid, cudaStream_t st);
+// Opt the persistent bulk kernel in to its dynamic shared memory.
+int prepare_bulk_persistent(int lat, int storage);
 // Opt the band kernel in to its dynamic shared memory (once, at creation).
 int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad);
 // Zero-gradient copies (Eq. zg-bc) in fnew, after the bulk update of x_f.
