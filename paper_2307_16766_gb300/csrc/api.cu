@@ -496,8 +496,9 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes); return at; };
     pl.off_f0 = take(pl.f_bytes);
     pl.off_f1 = take(pl.f_bytes);
-    pl.off_sU = take(pl.stripU_n * 8);
-    pl.off_sN = take(pl.stripN_n * 8);
+    E.sesize = p->storage == LBM_F64 ? 8 : 4;
+    pl.off_sU = take(pl.stripU_n * E.sesize);
+    pl.off_sN = take(pl.stripN_n * E.sesize);
     pl.off_Ub = take(2 * nu * 32);
     pl.off_ud = take(nu * sizeof(UDesc));
     pl.off_ld = take(pl.ldp.size() * sizeof(UDesc));
@@ -596,8 +597,8 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     h->owns_ws = owns;
     h->f[0] = at<char>(ws, pl.off_f0);
     h->f[1] = at<char>(ws, pl.off_f1);
-    h->E.stripU = at<double>(ws, pl.off_sU);
-    h->E.stripN = at<double>(ws, pl.off_sN);
+    h->E.stripU = at<char>(ws, pl.off_sU);
+    h->E.stripN = at<char>(ws, pl.off_sN);
     h->B.Ub = at<double>(ws, pl.off_Ub);
     h->B.Ya = h->B.Yb = h->B.acc = h->B.V = nullptr;
     h->B.mask = nullptr;
@@ -658,9 +659,9 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     if (e != cudaSuccess) return cuda_fail(h, e, "stream set-up");
     // Zero the strips (positions no kernel writes stay finite) and the
     // status words, and upload the boundary tables.
-    e = cudaMemsetAsync(h->E.stripU, 0, pl.stripU_n * 8, h->stream);
+    e = cudaMemsetAsync(h->E.stripU, 0, pl.stripU_n * h->E.sesize, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, 2 * sizeof(int), h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->E.stripN, 0, pl.stripN_n * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->E.stripN, 0, pl.stripN_n * h->E.sesize, h->stream);
     if (e == cudaSuccess && !pl.ud.empty())
         e = cudaMemcpyAsync(const_cast<UDesc*>(h->B.ud), pl.ud.data(), pl.ud.size() * sizeof(UDesc),
                             cudaMemcpyHostToDevice, h->stream);
@@ -1009,7 +1010,7 @@ struct StateHeader {
 int lbm_state_bytes(const lbm_handle* h, size_t* bytes)
 {
     if (!h || !bytes) return LBM_ERR_ARG;
-    *bytes = sizeof(StateHeader) + h->f_bytes + (18ull * h->E.nslots + 4ull * h->B.n_unk) * 8;
+    *bytes = sizeof(StateHeader) + h->f_bytes + 18ull * h->E.nslots * h->E.sesize + 32ull * h->B.n_unk;
     return LBM_OK;
 }
 
@@ -1020,7 +1021,7 @@ int lbm_get_state(lbm_handle* h, void* buf, size_t bytes)
     if (bytes < need) { h->err = fmt("state buffer needs %zu bytes", need); return LBM_ERR_ARG; }
     if (!h->initialized || h->bulk_pending) { h->err = "no complete state to save"; return LBM_ERR_STATE; }
     StateHeader hd{};
-    std::memcpy(hd.magic, "LBMCBC01", 8);
+    std::memcpy(hd.magic, "LBMCBC02", 8);
     hd.lattice = h->lattice; hd.nx = h->nx; hd.ny = h->ny; hd.storage = h->storage; hd.n_unk = h->B.n_unk;
     hd.steps = h->steps; hd.f_bytes = h->f_bytes; hd.stripU_n = 8ull * h->E.nslots; hd.stripN_n = 10ull * h->E.nslots;
     char* p = static_cast<char*>(buf);
@@ -1028,10 +1029,11 @@ int lbm_get_state(lbm_handle* h, void* buf, size_t bytes)
     p += sizeof hd;
     cudaError_t e = cudaMemcpyAsync(p, h->f[h->steps & 1], h->f_bytes, cudaMemcpyDeviceToHost, h->stream);
     p += h->f_bytes;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->E.stripU, 8ull * h->E.nslots * 8, cudaMemcpyDeviceToHost, h->stream);
-    p += 8ull * h->E.nslots * 8;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->E.stripN, 10ull * h->E.nslots * 8, cudaMemcpyDeviceToHost, h->stream);
-    p += 10ull * h->E.nslots * 8;
+    const size_t su = 8ull * h->E.nslots * h->E.sesize, sn = 10ull * h->E.nslots * h->E.sesize;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->E.stripU, su, cudaMemcpyDeviceToHost, h->stream);
+    p += su;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->E.stripN, sn, cudaMemcpyDeviceToHost, h->stream);
+    p += sn;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p, h->B.Ub + (h->steps & 1) * 4ull * h->B.n_unk, 32ull * h->B.n_unk,
                             cudaMemcpyDeviceToHost, h->stream);
@@ -1047,7 +1049,7 @@ int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes)
     if (bytes < need) { h->err = "state buffer too small"; return LBM_ERR_ARG; }
     StateHeader hd;
     std::memcpy(&hd, buf, sizeof hd);
-    if (std::memcmp(hd.magic, "LBMCBC01", 8) != 0 || hd.lattice != h->lattice || hd.nx != h->nx ||
+    if (std::memcmp(hd.magic, "LBMCBC02", 8) != 0 || hd.lattice != h->lattice || hd.nx != h->nx ||
         hd.ny != h->ny || hd.storage != h->storage || hd.n_unk != h->B.n_unk || hd.f_bytes != h->f_bytes ||
         hd.stripU_n != 8ull * h->E.nslots || hd.stripN_n != 10ull * h->E.nslots) {
         h->err = "state was saved from a different configuration";
@@ -1056,10 +1058,11 @@ int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes)
     const char* p = static_cast<const char*>(buf) + sizeof hd;
     cudaError_t e = cudaMemcpyAsync(h->f[hd.steps & 1], p, h->f_bytes, cudaMemcpyHostToDevice, h->stream);
     p += h->f_bytes;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->E.stripU, p, 8ull * h->E.nslots * 8, cudaMemcpyHostToDevice, h->stream);
-    p += 8ull * h->E.nslots * 8;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->E.stripN, p, 10ull * h->E.nslots * 8, cudaMemcpyHostToDevice, h->stream);
-    p += 10ull * h->E.nslots * 8;
+    const size_t su = 8ull * h->E.nslots * h->E.sesize, sn = 10ull * h->E.nslots * h->E.sesize;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->E.stripU, p, su, cudaMemcpyHostToDevice, h->stream);
+    p += su;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->E.stripN, p, sn, cudaMemcpyHostToDevice, h->stream);
+    p += sn;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->B.Ub + (hd.steps & 1) * 4ull * h->B.n_unk, p, 32ull * h->B.n_unk,
                             cudaMemcpyHostToDevice, h->stream);

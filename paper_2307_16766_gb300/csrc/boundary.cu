@@ -8,10 +8,12 @@
 //            populations (equilibrium or Eq. NEEP) post-collision.
 //  k_zg      zero-gradient copies (Eq. zg-bc), after the bulk update.
 //
-// All characteristic arithmetic is FP64.  Every neighbour a right-hand side
-// needs is resolved on the host into a UDesc: another unknown (stage value)
-// or a strip node holding a bulk node's macros at t and t + 1 (interpolated
-// linearly at the stage time, Sec. 3.3).
+// The characteristic decomposition and the RK4 update are FP64; with FP32
+// or FP16 storage the fused kernel forms their inputs (stencils,
+// transversal and viscous terms, strip macros) in FP32.  Every neighbour a
+// right-hand side needs is resolved on the host into a UDesc: another
+// unknown (stage value) or a strip node holding a bulk node's macros at t
+// and t + 1 (interpolated linearly at the stage time, Sec. 3.3).
 #include "collide.cuh"
 
 #include <cooperative_groups.h>
@@ -31,7 +33,8 @@ constexpr int kCluster = 4;         // CTAs per band tile: one per characteristi
 
 // Lab <-> local frame.  Sides: n the outward normal, t = +y (W, E) or +x
 // (S, N).  Corners: n = (sx, sy)/sqrt(2), t = n rotated by +90 degrees.
-__device__ __forceinline__ void to_local(int kind, double r, const double* U, double* Lc)
+template <typename R>
+__device__ __forceinline__ void to_local(int kind, R r, const R* U, R* Lc)
 {
     Lc[0] = U[0];
     Lc[3] = U[3];
@@ -42,7 +45,7 @@ __device__ __forceinline__ void to_local(int kind, double r, const double* U, do
     case 3: Lc[1] = U[2]; Lc[2] = U[1]; break;
     default: {
         const int c = kind - 4;
-        const double n0 = (c & 1) ? r : -r, n1 = (c & 2) ? r : -r;
+        const R n0 = (c & 1) ? r : -r, n1 = (c & 2) ? r : -r;
         Lc[1] = U[1] * n0 + U[2] * n1;
         Lc[2] = -U[1] * n1 + U[2] * n0;
     }
@@ -67,30 +70,40 @@ __device__ __forceinline__ void to_lab(int kind, double r, const double* Lc, dou
     }
 }
 
-struct Ctx {
-    const double* Y;     // stage values of the unknowns
-    const double* St;    // strip macros at t
-    const double* St1;   // strip macros at t + 1
-    double frac;         // stage time fraction in [0, 1]
+// Where a right-hand side reads its neighbours, in arithmetic type R.
+template <typename R>
+struct CtxT {
+    const R* Y;     // stage values of the unknowns
+    const R* St;    // strip macros at t
+    const R* St1;   // strip macros at t + 1
+    R frac;         // stage time fraction in [0, 1]
 };
+using Ctx = CtxT<double>;
 
-__device__ __forceinline__ void fetch(const Ctx& X, int ref, double* U)
+template <typename R>
+__device__ __forceinline__ void fetch(const CtxT<R>& X, int ref, R* U)
 {
     if (ref >= 0) {
-        const double2* p = reinterpret_cast<const double2*>(X.Y + 4LL * ref);
-        const double2 a = p[0], b = p[1];
-        U[0] = a.x; U[1] = a.y; U[2] = b.x; U[3] = b.y;
+        if constexpr (sizeof(R) == 8) {
+            const double2* p = reinterpret_cast<const double2*>(X.Y + 4LL * ref);
+            const double2 a = p[0], b = p[1];
+            U[0] = a.x; U[1] = a.y; U[2] = b.x; U[3] = b.y;
+        } else {
+            const float4 a = *reinterpret_cast<const float4*>(X.Y + 4LL * ref);
+            U[0] = a.x; U[1] = a.y; U[2] = a.z; U[3] = a.w;
+        }
     } else {
         const long long s = 4LL * (-ref - 1);
-        const double w0 = 1.0 - X.frac, w1 = X.frac;
+        const R w0 = R(1) - X.frac, w1 = X.frac;
 #pragma unroll
         for (int c = 0; c < 4; ++c) U[c] = w0 * X.St[s + c] + w1 * X.St1[s + c];
     }
 }
 
-__device__ __forceinline__ void fetch_local(const Ctx& X, int ref, int kind, double r, double* Lc)
+template <typename R>
+__device__ __forceinline__ void fetch_local(const CtxT<R>& X, int ref, int kind, R r, R* Lc)
 {
-    double U[4];
+    R U[4];
     fetch(X, ref, U);
     to_local(kind, r, U, Lc);
 }
@@ -390,9 +403,9 @@ __device__ void unknown_rhs(const Geom& G, const Band& B, const Ctx& X, const UD
 // (dirichlet 2) that part projected onto the Hermite polynomials of orders 2
 // and 3 (a regularised scheme, named by the paper as future work).
 // Computed in the arithmetic type of the storage.
-template <int LAT, typename S>
-__device__ void dirichlet(const Geom& G, const Band& B, S* f, const double* Us, const S* fsrc,
-                          const UDesc& D, const double* Unew)
+template <int LAT, typename S, typename R>
+__device__ void dirichlet(const Geom& G, const Band& B, S* f, const R* Us, const S* fsrc,
+                          const UDesc& D, const R* Unew)
 {
     // Us: macros of x_f at t + 1; fsrc: its stored post-collision
     // populations, indexed by velocity (both read only for Eq. NEEP)
@@ -403,7 +416,7 @@ __device__ void dirichlet(const Geom& G, const Band& B, S* f, const double* Us, 
     m.rho = Cm(G.rho0) + m.s0;
     m.ux = Cm(Unew[1]);
     m.uy = Cm(Unew[2]);
-    m.dT = Cm(L::THERMAL ? Unew[3] : 0.0);
+    m.dT = L::THERMAL ? Cm(Unew[3]) : Cm(0);
     Cm ge[L::Q];
     equilibrium<LAT, Cm>(m, ge);
     if (B.dirichlet >= 1) {             // Eq. NEEP, or its regularised form
@@ -412,7 +425,7 @@ __device__ void dirichlet(const Geom& G, const Band& B, S* f, const double* Us, 
         ms.rho = Cm(G.rho0) + ms.s0;
         ms.ux = Cm(Us[1]);
         ms.uy = Cm(Us[2]);
-        ms.dT = Cm(L::THERMAL ? Us[3] : 0.0);
+        ms.dT = L::THERMAL ? Cm(Us[3]) : Cm(0);
         Cm gs[L::Q];
         equilibrium<LAT, Cm>(ms, gs);
         Cm gn[L::Q];
@@ -517,20 +530,19 @@ __device__ __forceinline__ double wave(int i, const Band& B, int scheme, int mas
     return st + sv + B.alpha_T * (B.t_inf - st) + relaxP;
 }
 
-// Share c of the mesoscopic viscous vector (see vis_meso): V1 for c = 1,
-// V2 for c = 2; V3 is split, its conductive part for c = 0 and its
-// viscous-heating part for c = 3 (V0 = 0).
-template <bool TH>
-__device__ double vis_meso_c(int c, const Geom& G, const double* SU, const double* SN,
-                             const UDesc& D, double cs2)
+// Share c of the mesoscopic viscous vector (see vis_meso), in arithmetic
+// type R: V1 for c = 1, V2 for c = 2; V3 is split, its conductive part for
+// c = 0 and its viscous-heating part for c = 3 (V0 = 0).
+template <bool TH, typename R>
+__device__ R vis_meso_c(int c, const Geom& G, const R* SU, const R* SN, const UDesc& D, R cs2)
 {
-    if (!TH && (c == 0 || c == 3)) return 0.0;
+    if (!TH && (c == 0 || c == 3)) return R(0);
     const int s = D.kind;
     const int an = s < 2 ? 0 : 1, at = 1 - an;
-    const double sn = (s == 0 || s == 2) ? -1.0 : 1.0;
-    auto h = [&](int k, int m) -> double {
-        const double* n = SN + 5LL * D.vs[k];
-        const double* u = SU + 4LL * D.vs[k];
+    const R sn = (s == 0 || s == 2) ? R(-1) : R(1);
+    auto h = [&](int k, int m) -> R {
+        const R* n = SN + 5LL * D.vs[k];
+        const R* u = SU + 4LL * D.vs[k];
         switch (m) {
         case 0: return an == 0 ? n[0] : n[2];
         case 1: return sn * n[1];
@@ -541,58 +553,58 @@ __device__ double vis_meso_c(int c, const Geom& G, const double* SU, const doubl
         default: return u[1 + at];
         }
     };
-    auto dn = [&](int m) { return 0.5 * (3.0 * h(0, m) - 4.0 * h(1, m) + h(2, m)); };
+    auto dn = [&](int m) { return R(0.5) * (R(3) * h(0, m) - R(4) * h(1, m) + h(2, m)); };
     auto dt = [&](int m) {
-        if (D.tmode == 0) return 0.5 * (h(3, m) - h(4, m));
-        return double(D.tmode) * 0.5 * (3.0 * h(0, m) - 4.0 * h(3, m) + h(4, m));
+        if (D.tmode == 0) return R(0.5) * (h(3, m) - h(4, m));
+        return R(D.tmode) * R(0.5) * (R(3) * h(0, m) - R(4) * h(3, m) + h(4, m));
     };
     if (c == 3) {
-        const double nu = (G.tau - 0.5) * cs2;
-        const double e1 = dn(5) - dt(6), e2 = dn(6) + dt(5);
-        return nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
+        const R nu = (R(G.tau) - R(0.5)) * cs2;
+        const R e1 = dn(5) - dt(6), e2 = dn(6) + dt(5);
+        return nu * (R(1) / cs2) * (e1 * e1 + e2 * e2);
     }
-    const double irho = 1.0 / (G.rho0 + SU[4LL * D.vs[0]]);
+    const R irho = R(1) / (rho0_of<R>(G) + SU[4LL * D.vs[0]]);
     if (c == 1) return (dn(0) + dt(1)) * irho;
     if (c == 2) return (dn(1) + dt(2)) * irho;
-    return -(dn(3) + dt(4)) * irho * (1.0 / cs2);
+    return -(dn(3) + dt(4)) * irho * (R(1) / cs2);
 }
 
 // Share c of the "-FD" viscous vector (see vis_fd), split as vis_meso_c:
 // V3 = (c = 0 part) + (c = 3 part).
-template <bool TH>
-__device__ double vis_fd_c(int c, const Geom& G, const Band& B, const Ctx& X0, const UDesc& D, int u,
-                           double cs2)
+template <bool TH, typename R>
+__device__ R vis_fd_c(int c, const Geom& G, const Band& B, const CtxT<R>& X0, const UDesc& D, int u,
+                      R cs2)
 {
-    if (!TH && (c == 0 || c == 3)) return 0.0;
+    if (!TH && (c == 0 || c == 3)) return R(0);
     const int kind = D.kind;
-    double U[4], A[4], Bv[4], Cv[4], Tp[4], Tm[4], dnn[4], d1n[4];
-    fetch_local(X0, u, kind, 0.0, U);
-    fetch_local(X0, D.nb[1], kind, 0.0, Bv);
-    fetch_local(X0, D.nb[4], kind, 0.0, Tp);
-    fetch_local(X0, D.nb[5], kind, 0.0, Tm);
+    R U[4], A[4], Bv[4], Cv[4], Tp[4], Tm[4], dnn[4], d1n[4];
+    fetch_local(X0, u, kind, R(0), U);
+    fetch_local(X0, D.nb[1], kind, R(0), Bv);
+    fetch_local(X0, D.nb[4], kind, R(0), Tp);
+    fetch_local(X0, D.nb[5], kind, R(0), Tm);
     if (D.j == B.M) {
-        fetch_local(X0, D.nb[2], kind, 0.0, A);
-        fetch_local(X0, D.nb[3], kind, 0.0, Cv);
+        fetch_local(X0, D.nb[2], kind, R(0), A);
+        fetch_local(X0, D.nb[3], kind, R(0), Cv);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            dnn[m] = 2.0 * U[m] - 5.0 * Bv[m] + 4.0 * A[m] - Cv[m];
-            d1n[m] = 0.5 * (3.0 * U[m] - 4.0 * Bv[m] + A[m]);
+            dnn[m] = R(2) * U[m] - R(5) * Bv[m] + R(4) * A[m] - Cv[m];
+            d1n[m] = R(0.5) * (R(3) * U[m] - R(4) * Bv[m] + A[m]);
         }
     } else {
-        fetch_local(X0, D.nb[0], kind, 0.0, A);
+        fetch_local(X0, D.nb[0], kind, R(0), A);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            dnn[m] = A[m] - 2.0 * U[m] + Bv[m];
-            d1n[m] = 0.5 * (A[m] - Bv[m]);
+            dnn[m] = A[m] - R(2) * U[m] + Bv[m];
+            d1n[m] = R(0.5) * (A[m] - Bv[m]);
         }
     }
-    const double nu = (G.tau - 0.5) * cs2;
-    if (c == 1) return nu * (dnn[1] + (Tp[1] - 2.0 * U[1] + Tm[1]));
-    if (c == 2) return nu * (dnn[2] + (Tp[2] - 2.0 * U[2] + Tm[2]));
-    if (c == 0) return 2.0 * nu * (dnn[3] + (Tp[3] - 2.0 * U[3] + Tm[3]));
-    const double d1t1 = 0.5 * (Tp[1] - Tm[1]), d1t2 = 0.5 * (Tp[2] - Tm[2]);
-    const double e1 = d1n[1] - d1t2, e2 = d1n[2] + d1t1;
-    return nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
+    const R nu = (R(G.tau) - R(0.5)) * cs2;
+    if (c == 1) return nu * (dnn[1] + (Tp[1] - R(2) * U[1] + Tm[1]));
+    if (c == 2) return nu * (dnn[2] + (Tp[2] - R(2) * U[2] + Tm[2]));
+    if (c == 0) return R(2) * nu * (dnn[3] + (Tp[3] - R(2) * U[3] + Tm[3]));
+    const R d1t1 = R(0.5) * (Tp[1] - Tm[1]), d1t2 = R(0.5) * (Tp[2] - Tm[2]);
+    const R e1 = d1n[1] - d1t2, e2 = d1n[2] + d1t1;
+    return nu * (R(1) / cs2) * (e1 * e1 + e2 * e2);
 }
 
 // Lab component m of a local-frame vector (m = 1, 2 need k1 and k2).
@@ -614,6 +626,18 @@ __device__ __forceinline__ double lab_component(int m, int kind, double r, doubl
     }
 }
 
+// The band kernel forms the inputs of the characteristic system (stencils,
+// transversal and viscous terms, strip-node macros) in StripReal<S>: FP64
+// with FP64 storage, FP32 otherwise.  The characteristic decomposition
+// (projection on the waves, wave amplitudes with their relaxation towards
+// the targets, and back to the lab frame) and the RK4 update of the
+// boundary state are FP64 for every storage.
+
+__device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+
 // One tile of the boundary band per cluster: a run of positions of one
 // characteristic side (all M layers, and the corner next to it on a W/E
 // side), plus the halo its four RK4 stages need (Sec. 3.3).
@@ -627,11 +651,12 @@ __device__ __forceinline__ double lab_component(int m, int kind, double r, doubl
 // 2. RK4 (Sec. 3.3, "Time integration"): the local table lists the tile's
 //    unknowns by level: level 0 are owned, level l computes the first 4 - l
 //    stages, level 4 only supplies U(t).  Per stage, CTA r computes its
-//    share of the characteristic system (1/rho, sqrt(theta),
-//    1/sqrt(theta), P - P_inf and the transversal terms), then wave r,
-//    then lab component r of the right-hand side and of the stage value.
-//    Stage 0 freezes the viscous vector and the incoming-wave mask of time
-//    t.
+//    share of the inputs of the characteristic system (1/rho,
+//    sqrt(theta), 1/sqrt(theta), P - P_inf and the transversal terms; in
+//    type R), then wave r (FP64), then lab component r of the right-hand
+//    side and of the stage value (FP64; stage values are shared in type R).
+//    Stage 0 freezes the viscous vector and the incoming-wave mask of
+//    time t.
 // 3. The owners write U(t + 1) and the mesoscopic Dirichlet populations
 //    (equilibrium or Eq. NEEP), shared out over the four CTAs.
 template <int LAT, typename S>
@@ -641,20 +666,21 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
 {
     using L = Lat<LAT>;
     using C = typename Store<S>::C;
+    using R = typename StripReal<S>::T;
     constexpr bool TH = L::THERMAL;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = int(cl.block_rank());
     const int l = threadIdx.x;
-    __shared__ __align__(16) double Ys[kTileThreads * 4];   // stage values, lab frame
-    __shared__ __align__(16) double Xp[kTileThreads * 8];   // shares of the characteristic system
+    __shared__ __align__(16) R Ys[kTileThreads * 4];        // stage values, lab frame
+    __shared__ __align__(16) R Xp[kTileThreads * 8];        // shares of the system's inputs
     __shared__ __align__(16) double Xw[kTileThreads * 4];   // wave amplitudes
-    __shared__ __align__(16) double Xv[kTileThreads * 4];   // viscous vector (local frame, frozen)
-    extern __shared__ __align__(16) double dyn[];
-    double* SUt = dyn;                              // [max_nodes][4] macros of t
-    double* SUt1 = SUt + 4 * B.max_nodes;           // [max_nodes][4] macros of t + 1
-    double* SNt = SUt1 + 4 * B.max_nodes;           // [max_nodes][5] moments of t
+    __shared__ __align__(16) R Xv[kTileThreads * 4];        // viscous vector (local frame, frozen)
+    extern __shared__ __align__(16) unsigned char dyn_raw[];
+    R* SUt = reinterpret_cast<R*>(dyn_raw);        // [max_nodes][4] macros of t
+    R* SUt1 = SUt + 4 * B.max_nodes;               // [max_nodes][4] macros of t + 1
+    R* SNt = SUt1 + 4 * B.max_nodes;               // [max_nodes][5] moments of t
     S* Fx = reinterpret_cast<S*>(SNt + 5 * B.max_nodes);   // [max_fx][Q], node k in CTA k % 4
-    auto bcast = [&](double* p, double v) {
+    auto bcast = [&](auto* p, auto v) {
 #pragma unroll
         for (int q = 0; q < kCluster; ++q) *cl.map_shared_rank(p, q) = v;
     };
@@ -662,7 +688,9 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     // dependent global round trip costs microseconds.
     const int ns = B.max_nodes;
     const StripNode* snt = B.sn + (long long)tile * ns;
-    const int kp = rank + kCluster * l;             // the strip node this thread pulls
+    // the strip node this thread pulls: node k goes to CTA k % 4, and the
+    // nodes of a CTA are dealt round the four warps
+    const int kp = rank + kCluster * (4 * (l % 32) + l / 32);
     StripNode Na{-1, -1, 0, -1, -1}, Nb{-1, -1, 0, -1, -1};
     if (l < ns) Na = snt[l];
     if (kp < ns) Nb = snt[kp];
@@ -672,8 +700,8 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     // 1. strip nodes: macros of t and moments of t for every CTA; macros of
     //    t + 1 (pull and Eq. macro) by CTA k % kCluster for node k, shared
     //    out; post-collision populations of Eq. NEEP sources kept locally
-    const double* gU = E.stripU + (long long)par_t * E.nslots * 4;
-    const double* gN = E.stripN + (long long)par_t * E.nslots * 5;
+    const R* gU = static_cast<const R*>(E.stripU) + (long long)par_t * E.nslots * 4;
+    const R* gN = static_cast<const R*>(E.stripN) + (long long)par_t * E.nslots * 5;
     auto load_t = [&](int k, int ts) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) SUt[4 * k + c] = gU[4LL * ts + c];
@@ -697,14 +725,14 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         } else {
             m = moments<LAT, C>(g, rho0_of<C>(G));
         }
-        const double U1[4] = {double(m.s0), double(m.ux), double(m.uy), double(m.dT)};
+        const R U1[4] = {R(m.s0), R(m.ux), R(m.uy), R(m.dT)};
 #pragma unroll
         for (int c = 0; c < 4; ++c) bcast(SUt1 + 4 * k + c, U1[c]);
         if (N.gslot >= 0) {             // the strips of t + 1, for the next step
-            double N1[5];
-            neq_moments<LAT, C>(g, m, 1.0 - 0.5 / G.tau, N1);
-            double* u = E.stripU + ((long long)(par_t ^ 1) * E.nslots + N.gslot) * 4;
-            double* q = E.stripN + ((long long)(par_t ^ 1) * E.nslots + N.gslot) * 5;
+            R N1[5];
+            neq_moments<LAT, C, R>(g, m, R(1) - R(0.5) * omega_of<R>(G), N1);
+            R* u = static_cast<R*>(E.stripU) + ((long long)(par_t ^ 1) * E.nslots + N.gslot) * 4;
+            R* q = static_cast<R*>(E.stripN) + ((long long)(par_t ^ 1) * E.nslots + N.gslot) * 5;
 #pragma unroll
             for (int c = 0; c < 4; ++c) u[c] = U1[c];
 #pragma unroll
@@ -731,155 +759,238 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     }
     if (lev <= 4) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) Ys[4 * l + m] = U0[m];
+        for (int m = 0; m < 4; ++m) Ys[4 * l + m] = R(U0[m]);
     }
     cl.sync();
 
     // 2. RK4, component rank of every unknown
-    Ctx X;
+    CtxT<R> X;
     X.Y = Ys;
     X.St = SUt;
     X.St1 = SUt1;
-    const double rho0 = G.rho0, cs2 = L::CS2, kr = B.kR;
+    const double rho0 = G.rho0;
+    const R rho0r = rho0_of<R>(G), cs2r = R(L::CS2), kr = R(B.kR);
     const bool corner = lev <= 4 && D.kind >= 4;
     const int scheme = corner ? SCH_LODI : (lev <= 4 ? B.scheme[D.kind] : 0);
     const bool cbc = scheme == SCH_CBC || scheme == SCH_CBC_RELAX;
     double acc = 0.0, kc = 0.0;         // lab component rank of sum k and of the last k
     const double u0r = rank == 0 ? U0[0] : rank == 1 ? U0[1] : rank == 2 ? U0[2] : U0[3];
-    int mask = 0;
+    bool incoming = false;              // wave rank incoming at time t
+    // In FP32 every CTA forms all inputs of the system itself; in FP64 each
+    // CTA forms a share and the shares are exchanged (FP64 issue is slow).
+    constexpr bool kLocal = sizeof(R) == 4;
+    R xs[8] = {0, 0, 0, 0, 0, 0, 0, 0}; // the inputs, kLocal
+    R Vs[4] = {0, 0, 0, 0};             // viscous vector (local frame, frozen), kLocal
     for (int stage = 0; stage < 4; ++stage) {
         const bool comp = lev <= 3 - stage;
-        X.frac = stage == 0 ? 0.0 : (stage == 3 ? 1.0 : 0.5);
-        double Ul[4] = {0.0, 0.0, 0.0, 0.0}, dUn[4] = {0.0, 0.0, 0.0, 0.0};
-        double Up[4] = {0.0, 0.0, 0.0, 0.0}, Um[4] = {0.0, 0.0, 0.0, 0.0};
-        // A: shares
+        X.frac = stage == 0 ? R(0) : (stage == 3 ? R(1) : R(0.5));
+        R Ul[4] = {0, 0, 0, 0}, dUn[4] = {0, 0, 0, 0};
+        R d_ut = 0;
+        // A: inputs of the system, type R: 1/rho, the transversal terms,
+        // sqrt(theta), 1/sqrt(theta), P - P_inf and d(rho T)/dt (thermal) or
+        // d rho/dt (isothermal)
         if (comp) {
             const int kind = D.kind;
-            double A[4], Bv[4];
+            R A[4], Bv[4], Up[4], Um[4];
             fetch_local(X, l, kind, kr, Ul);
             if (corner) {
                 // LODI along the outward diagonal, one-sided difference of
                 // spacing sqrt(2) through the two diagonal bulk nodes
                 fetch_local(X, D.nb[0], kind, kr, A);
                 fetch_local(X, D.nb[1], kind, kr, Bv);
+                const R kC = R(B.kC);
 #pragma unroll
-                for (int m = 0; m < 4; ++m) dUn[m] = (3.0 * Ul[m] - 4.0 * A[m] + Bv[m]) * B.kC;
+                for (int m = 0; m < 4; ++m) dUn[m] = (R(3) * Ul[m] - R(4) * A[m] + Bv[m]) * kC;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) Up[m] = Um[m] = R(0);
             } else {
                 if (D.j == B.M) {        // Eq. FD-dx-bw at the outermost layer
                     fetch_local(X, D.nb[1], kind, kr, A);
                     fetch_local(X, D.nb[2], kind, kr, Bv);
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) dUn[m] = 0.5 * (3.0 * Ul[m] - 4.0 * A[m] + Bv[m]);
+                    for (int m = 0; m < 4; ++m) dUn[m] = R(0.5) * (R(3) * Ul[m] - R(4) * A[m] + Bv[m]);
                 } else {                 // Eq. FD-dx-center at inner layers
                     fetch_local(X, D.nb[0], kind, kr, A);
                     fetch_local(X, D.nb[1], kind, kr, Bv);
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) dUn[m] = 0.5 * (A[m] - Bv[m]);
+                    for (int m = 0; m < 4; ++m) dUn[m] = R(0.5) * (A[m] - Bv[m]);
                 }
                 fetch_local(X, D.nb[4], kind, kr, Up);
                 fetch_local(X, D.nb[5], kind, kr, Um);
             }
-            double* xp = Xp + 8 * l;
-            if (rank == 0) {
-                bcast(xp + 0, 1.0 / (rho0 + Ul[0]));
-                bcast(xp + 1, corner ? 0.0 : -0.5 * ((rho0 + Up[0]) * Up[2] - (rho0 + Um[0]) * Um[2]));
-            } else if (rank == 1) {
-                if (TH) bcast(xp + 2, sqrt(1.0 + Ul[3]));
-                bcast(xp + 3, corner ? 0.0 : -Ul[2] * (0.5 * (Up[1] - Um[1])));
-            } else if (rank == 2) {
-                if (TH) bcast(xp + 4, rsqrt(1.0 + Ul[3]));
-                const double dP = TH ? cs2 * (Ul[0] + rho0 * Ul[3] + Ul[0] * Ul[3]) : cs2 * Ul[0];
-                bcast(xp + 5, corner ? 0.0 : dP - B.pdev[kind]);
-                if (!TH) bcast(xp + 6, 0.5 * (Up[0] - Um[0]));
-            } else if (TH) {
-                // rho T - rho0 = drho + rho0 dT + drho dT
-                bcast(xp + 6, 0.5 * ((Up[0] + rho0 * Up[3] + Up[0] * Up[3]) -
-                                     (Um[0] + rho0 * Um[3] + Um[0] * Um[3])));
-                bcast(xp + 7, corner ? 0.0 : -0.5 * ((1.0 + Up[3]) * Up[2] - (1.0 + Um[3]) * Um[2]));
-            }
-            if (stage == 0) {
-                double v = 0.0;
-                if (!corner && B.viscous == VIS_FD) v = vis_fd_c<TH>(rank, G, B, X, D, l, cs2);
-                else if (!corner && B.viscous == VIS_MESO) v = vis_meso_c<TH>(rank, G, SUt, SNt, D, cs2);
-                bcast(Xv + 4 * l + rank, v);
-            }
-        }
-        cl.sync();
-        // B: wave rank
-        double TT[4] = {0.0, 0.0, 0.0, 0.0}, V[4] = {0.0, 0.0, 0.0, 0.0};
-        double ir = 0.0, bb = 0.0, csr = 0.0;
-        if (comp) {
-            const double* xp = Xp + 8 * l;
-            const double irho = xp[0], rho = rho0 + Ul[0];
-            const double d_ut = 0.5 * (Up[2] - Um[2]);
-            double lam[4], rr = 0.0, a = 0.0, h = 0.0;
-            if (TH) {
-                const double sth = xp[2], isth = xp[4], th = 1.0 + Ul[3];
-                rr = th * irho;
-                ir = rho * isth * isth;
-                a = sth * B.kA;
-                bb = isth * B.kB;
-                const double c = sth * B.kB;
-                lam[0] = Ul[1];
-                lam[1] = Ul[1];
-                lam[2] = Ul[1] - c;
-                lam[3] = Ul[1] + c;
-                if (!corner) {
-                    TT[0] = xp[1];
-                    TT[1] = xp[3];
-                    TT[2] = -cs2 * irho * xp[6] - Ul[2] * d_ut;
-                    TT[3] = xp[7];
+            d_ut = R(0.5) * (Up[2] - Um[2]);
+            // share q of the inputs (q = 0..3: entries {0,1}, {2,3},
+            // {4,5,6 isothermal}, {6,7 thermal})
+            auto input = [&](int i) -> R {
+                switch (i) {
+                case 0: return R(1) / (rho0r + Ul[0]);
+                case 1: return corner ? R(0) : R(-0.5) * ((rho0r + Up[0]) * Up[2] - (rho0r + Um[0]) * Um[2]);
+                case 2: return TH ? sqrt_r(R(1) + Ul[3]) : R(0);
+                case 3: return corner ? R(0) : -Ul[2] * (R(0.5) * (Up[1] - Um[1]));
+                case 4: return TH ? rsqrt_r(R(1) + Ul[3]) : R(0);
+                case 5: {
+                    const R dP = TH ? cs2r * (Ul[0] + rho0r * Ul[3] + Ul[0] * Ul[3]) : cs2r * Ul[0];
+                    return corner ? R(0) : dP - R(B.pdev[kind]);
+                }
+                case 6:
+                    // rho T - rho0 = drho + rho0 dT + drho dT
+                    return TH ? R(0.5) * ((Up[0] + rho0r * Up[3] + Up[0] * Up[3]) -
+                                          (Um[0] + rho0r * Um[3] + Um[0] * Um[3]))
+                              : R(0.5) * (Up[0] - Um[0]);
+                default:
+                    return (TH && !corner) ? R(-0.5) * ((R(1) + Up[3]) * Up[2] - (R(1) + Um[3]) * Um[2]) : R(0);
+                }
+            };
+            if constexpr (kLocal) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) xs[i] = input(i);
+                if (stage == 0 && !corner) {
+                    if (B.viscous == VIS_FD) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) Vs[c] = vis_fd_c<TH, R>(c, G, B, X, D, l, cs2r);
+                    } else if (B.viscous == VIS_MESO) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) Vs[c] = vis_meso_c<TH, R>(c, G, SUt, SNt, D, cs2r);
+                    }
                 }
             } else {
-                h = rho * B.ihcs;
-                csr = B.cs * irho;
-                lam[0] = Ul[1] - B.cs;
-                lam[1] = Ul[1];
-                lam[2] = Ul[1] + B.cs;
-                lam[3] = 0.0;
-                if (!corner) {
-                    TT[0] = xp[1];
-                    TT[1] = xp[3];
-                    TT[2] = -cs2 * irho * xp[6] - Ul[2] * d_ut;
+                R* xp = Xp + 8 * l;
+                if (rank == 0) {
+                    bcast(xp + 0, input(0));
+                    bcast(xp + 1, input(1));
+                } else if (rank == 1) {
+                    if (TH) bcast(xp + 2, input(2));
+                    bcast(xp + 3, input(3));
+                } else if (rank == 2) {
+                    if (TH) bcast(xp + 4, input(4));
+                    bcast(xp + 5, input(5));
+                    if (!TH) bcast(xp + 6, input(6));
+                } else if (TH) {
+                    bcast(xp + 6, input(6));
+                    bcast(xp + 7, input(7));
+                }
+                if (stage == 0) {
+                    R v = R(0);
+                    if (!corner && B.viscous == VIS_FD) v = vis_fd_c<TH, R>(rank, G, B, X, D, l, cs2r);
+                    else if (!corner && B.viscous == VIS_MESO) v = vis_meso_c<TH, R>(rank, G, SUt, SNt, D, cs2r);
+                    bcast(Xv + 4 * l + rank, v);
                 }
             }
-            if (stage == 0)
-                for (int i = 0; i < (TH ? 4 : 3); ++i)
-                    if (lam[i] < 0.0) mask |= 1 << i;
-            V[1] = Xv[4 * l + 1];
-            V[2] = Xv[4 * l + 2];
-            V[3] = TH ? Xv[4 * l + 0] + Xv[4 * l + 3] : 0.0;   // V0 = 0; V3 from two shares
-            const double lr = rank == 0 ? lam[0] : rank == 1 ? lam[1] : rank == 2 ? lam[2] : lam[3];
-            const double w = wave<TH>(rank, B, scheme, mask, lr, s_row<TH>(rank, rr, a, h, dUn),
-                                      s_row<TH>(rank, rr, a, h, TT), s_row<TH>(rank, rr, a, h, V),
-                                      xp[5]);
+        }
+        if constexpr (!kLocal) cl.sync();
+        // B: wave rank, FP64.  Row rank of S (see apply_S) applied to dU/dn,
+        // T and V, with Lambda_rank.
+        auto XP = [&](int i) -> R {
+            if constexpr (kLocal) return xs[i];
+            else return Xp[8 * l + i];
+        };
+        R TTr[4] = {0, 0, 0, 0};        // transversal terms, local frame
+        R Vr[4] = {0, 0, 0, 0};
+        double ir = 0.0, bb = 0.0, csr = 0.0;
+        if (comp) {
+            if (!corner) {
+                TTr[0] = XP(1);
+                TTr[1] = XP(3);
+                TTr[2] = -cs2r * XP(0) * XP(6) - Ul[2] * d_ut;
+                TTr[3] = TH ? XP(7) : R(0);
+            }
+            if constexpr (kLocal) {
+                Vr[1] = Vs[1];
+                Vr[2] = Vs[2];
+                Vr[3] = TH ? Vs[0] + Vs[3] : R(0);      // V0 = 0; V3 from two shares
+            } else {
+                const R* xv = Xv + 4 * l;
+                Vr[1] = xv[1];
+                Vr[2] = xv[2];
+                Vr[3] = TH ? xv[0] + xv[3] : R(0);
+            }
+            const double irho = double(XP(0));
+            const double un = double(Ul[1]);
+            double k0 = 0.0, k1 = 0.0, k2 = 0.0, k3 = 0.0, lam = un;   // row rank of S
+            bool acoustic = false;
+            if (TH) {
+                const double sth = double(XP(2)), isth = double(XP(4));
+                const double rr = (1.0 + double(Ul[3])) * irho;
+                ir = (rho0 + double(Ul[0])) * isth * isth;
+                bb = isth * B.kB;
+                if (rank == 0) { k0 = -0.5 * rr; k3 = 0.5; }
+                else if (rank == 1) { k2 = 1.0; }
+                else {
+                    const double sg = rank == 2 ? -1.0 : 1.0;
+                    k0 = 0.25 * rr;
+                    k1 = sg * (sth * B.kA);
+                    k3 = 0.25;
+                    lam = un + sg * (sth * B.kB);
+                    acoustic = true;
+                }
+            } else {
+                csr = B.cs * irho;
+                if (rank == 1) { k2 = 1.0; }
+                else if (rank != 3) {
+                    const double sg = rank == 0 ? -1.0 : 1.0;
+                    k0 = 0.5;
+                    k1 = sg * ((rho0 + double(Ul[0])) * B.ihcs);
+                    lam = un + sg * B.cs;
+                    acoustic = true;
+                }
+            }
+            auto srow = [&](const R* v) {
+                return k0 * double(v[0]) + k1 * double(v[1]) + k2 * double(v[2]) + k3 * double(v[3]);
+            };
+            if (stage == 0) incoming = lam < 0.0;
+            double w = 0.0;
+            if (TH || rank != 3) {
+                if (!incoming) {
+                    w = lam * srow(dUn);
+                } else if (scheme != SCH_LODI) {
+                    const double st = srow(TTr);
+                    const double relaxP = acoustic ? B.beta_P * double(XP(5)) : 0.0;
+                    if (scheme == SCH_LODI_RELAX) w = B.alpha_T * (B.t_inf - st) + relaxP;
+                    else if (scheme == SCH_CBC) w = st + srow(Vr);
+                    else w = st + srow(Vr) + B.alpha_T * (B.t_inf - st) + relaxP;
+                }
+            }
             bcast(Xw + 4 * l + rank, w);
+            // the transversal and viscous terms this CTA adds in step C
+            if (cbc) {
+                if (rank == 3) {
+                    TTr[3] += Vr[3];
+                } else if (rank != 0) {         // V0 = 0
+                    TTr[1] += Vr[1];
+                    TTr[2] += Vr[2];
+                }
+            }
         }
         cl.sync();
-        // C: lab component rank of the right-hand side; RK4 update
+        // C: lab component rank of the right-hand side; RK4 update (FP64)
         if (comp) {
             const double* w = Xw + 4 * l;
-            double kl[4] = {0.0, 0.0, 0.0, 0.0};
-            if (rank == 0) kl[0] = -(TH ? (w[2] + w[3] - w[0]) * ir : w[0] + w[2]);
-            if (rank == 3) kl[3] = TH ? -(w[0] + w[2] + w[3]) : 0.0;
-            if (rank == 1 || rank == 2) {
-                kl[1] = -(TH ? bb * (w[3] - w[2]) : csr * (w[2] - w[0]));
-                kl[2] = -w[1];
+            double kl1 = 0.0, kl2 = 0.0, klr = 0.0;
+            if (rank == 0) {
+                klr = -(TH ? (w[2] + w[3] - w[0]) * ir : w[0] + w[2]);
+                if (cbc) klr += double(TTr[0]);
+            } else if (rank == 3) {
+                klr = TH ? -(w[0] + w[2] + w[3]) : 0.0;
+                if (cbc && TH) klr += double(TTr[3]);
+            } else {
+                kl1 = -(TH ? bb * (w[3] - w[2]) : csr * (w[2] - w[0]));
+                kl2 = -w[1];
+                if (cbc) {
+                    kl1 += double(TTr[1]);
+                    kl2 += double(TTr[2]);
+                }
             }
-            if (cbc)
-#pragma unroll
-                for (int m = 0; m < 4; ++m) kl[m] += TT[m] + V[m];
-            kc = lab_component(rank, D.kind, kr, kl[0], kl[1], kl[2], kl[3]);
+            kc = lab_component(rank, D.kind, B.kR, klr, kl1, kl2, klr);
             if (stage < 3) {
                 const double wk = stage == 0 ? 1.0 : 2.0;
                 const double hk = stage == 2 ? 1.0 : 0.5;
                 acc = (stage == 0 ? 0.0 : acc) + wk * kc;
-                bcast(Ys + 4 * l + rank, u0r + hk * kc);
+                bcast(Ys + 4 * l + rank, R(u0r + hk * kc));
             } else {
                 // RK4: U(t + 1) = U(t) + (k1 + 2 k2 + 2 k3 + k4) / 6
                 const double un = u0r + (acc + kc) * (1.0 / 6.0);
                 B.Ub[((long long)(par_t ^ 1) * B.n_unk + D.gid) * 4 + rank] = un;
-                bcast(Ys + 4 * l + rank, un);
+                bcast(Ys + 4 * l + rank, R(un));
             }
         }
         cl.sync();
@@ -887,10 +998,10 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
 
     // 3. Dirichlet populations of unknown l, on CTA l % kCluster
     if (lev == 0 && l % kCluster == rank) {
-        const double Unew[4] = {Ys[4 * l], Ys[4 * l + 1], Ys[4 * l + 2], Ys[4 * l + 3]};
+        const R Unew[4] = {Ys[4 * l], Ys[4 * l + 1], Ys[4 * l + 2], Ys[4 * l + 3]};
         const bool neep = B.dirichlet >= 1;     // needs x_f: NEEP or regularised NEEP
         const S* fs = neep ? cl.map_shared_rank(Fx + D.wsrc * L::Q, D.wslot % kCluster) : nullptr;
-        dirichlet<LAT, S>(G, B, f, neep ? SUt1 + 4 * D.wslot : nullptr, fs, D, Unew);
+        dirichlet<LAT, S, R>(G, B, f, neep ? SUt1 + 4 * D.wslot : nullptr, fs, D, Unew);
     }
     cl.sync();                          // no CTA leaves while its Fx may be read
 }
@@ -935,7 +1046,8 @@ __global__ void k_zg(Geom G, Band B, S* __restrict__ f)
 template <int LAT, typename S>
 size_t band_smem(const Band& B)
 {
-    return (size_t)B.max_nodes * 13 * sizeof(double) + (size_t)B.max_fx * Lat<LAT>::Q * sizeof(S);
+    return (size_t)B.max_nodes * 13 * sizeof(typename StripReal<S>::T) +
+           (size_t)B.max_fx * Lat<LAT>::Q * sizeof(S);
 }
 
 template <int LAT, typename S>
@@ -1126,7 +1238,8 @@ __global__ void __launch_bounds__(kBandThreads)
         mask = incoming_mask<Lt::THERMAL>(char_sys<Lt::THERMAL>(B, G.rho0, Ul));
         if (B.viscous == VIS_OFF) V[0] = V[1] = V[2] = V[3] = 0.0;
         else if (B.viscous == VIS_FD) vis_fd<Lt::THERMAL>(G, B, X, D, u, Lt::CS2, V);
-        else vis_meso<Lt::THERMAL>(G, E.stripU, E.stripN, D, Lt::CS2, V);
+        else vis_meso<Lt::THERMAL>(G, static_cast<const double*>(E.stripU),
+                                   static_cast<const double*>(E.stripN), D, Lt::CS2, V);
         for (int m = 0; m < 4; ++m) B.V[4LL * u + m] = V[m];
         B.mask[u] = mask;
     } else {
@@ -1238,6 +1351,7 @@ extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, doub
     B.mask = reinterpret_cast<int*>(scratch + 16ull * kNoAllocMaxUnknowns);
     Export E{};
     E.nslots = 3 * length;
+    E.sesize = 8;
     E.stripU = const_cast<double*>(strip_t);
     E.stripN = const_cast<double*>(neq_t);
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -333,15 +333,16 @@ __global__ void k_init(Geom G, Export E, const double* __restrict__ rho,
     const bool inbx = (G.perx || (x >= G.M && x < G.nx - G.M));
     const bool inby = (G.pery || (y >= G.M && y < G.ny - G.M));
     if (!(inbx && inby)) return;
-    const double U[4] = {m.s0, m.ux, m.uy, m.dT};
+    using R = typename StripReal<S>::T;
+    const R U[4] = {R(m.s0), R(m.ux), R(m.uy), R(m.dT)};
     for (int s = 0; s < 4; ++s) {
         if (!E.cbc[s] || dd[s] < 0 || dd[s] > 2) continue;
         const int p = s < 2 ? y : x;
         const long long slot = E.offS[s] + dd[s] * E.L[s] + p;
-        double* u = E.stripU + slot * 4;
-        double* nn = E.stripN + slot * 5;
+        R* u = static_cast<R*>(E.stripU) + slot * 4;
+        R* nn = static_cast<R*>(E.stripN) + slot * 5;
         for (int c = 0; c < 4; ++c) u[c] = U[c];
-        for (int c = 0; c < 5; ++c) nn[c] = 0.0;
+        for (int c = 0; c < 5; ++c) nn[c] = R(0);
     }
 }
 

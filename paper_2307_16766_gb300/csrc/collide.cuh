@@ -22,9 +22,8 @@ __device__ __forceinline__ double rho0_of<double>(const Geom& G) { return G.rho0
 // and heat flux q = (1 - 1/(2 tau)) 1/2 sum (f - f^eq) |c-u|^2 (c-u)
 // (Eqs. heatflux, LaplaceT; the equilibrium part of the central third
 // moment vanishes on D2Q37).
-template <int LAT, typename C>
-__device__ __forceinline__ void neq_moments(const C* g, const Moments<LAT, C>& m, double fac,
-                                         double* N)
+template <int LAT, typename C, typename T>
+__device__ __forceinline__ void neq_moments(const C* g, const Moments<LAT, C>& m, T fac, T* N)
 {
     using L = Lat<LAT>;
     C geq[L::Q];
@@ -44,11 +43,11 @@ __device__ __forceinline__ void neq_moments(const C* g, const Moments<LAT, C>& m
             qy += h * ey;
         }
     }
-    N[0] = -fac * double(pxx);
-    N[1] = -fac * double(pxy);
-    N[2] = -fac * double(pyy);
-    N[3] = fac * double(qx);
-    N[4] = fac * double(qy);
+    N[0] = -fac * T(pxx);
+    N[1] = -fac * T(pxy);
+    N[2] = -fac * T(pyy);
+    N[3] = fac * T(qx);
+    N[4] = fac * T(qy);
 }
 
 // Plain pull of node (x, y) with periodic wrap-around of the sources.

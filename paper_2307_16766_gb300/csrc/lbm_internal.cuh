@@ -457,8 +457,20 @@ struct Export {
     int offS[4];
     int L[4];
     int nslots;
-    double* stripU;
-    double* stripN;
+    int sesize;      // bytes per strip value: 8 with FP64 storage, else 4 (StripReal)
+    void* stripU;
+    void* stripN;
+};
+
+// Arithmetic type of the strips and of the band kernel's stencils,
+// transversal and viscous terms: FP64 with FP64 storage, FP32 otherwise.
+template <typename S>
+struct StripReal {
+    using T = float;
+};
+template <>
+struct StripReal<double> {
+    using T = double;
 };
 
 // One unknown of the boundary ODE: layer j of a characteristic side at one
