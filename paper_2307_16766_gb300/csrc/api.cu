@@ -611,6 +611,7 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     for (int c = 0; c < 4; ++c) h->Uin[c] = pl.Uin[c];
     h->macro = at<double>(ws, pl.off_macro);
     h->flag = at<int>(ws, pl.off_flag);
+    h->B.status = h->flag + 1;
     const int depths[5] = {7, 5, 3, 2, 1};
     for (int b = 0; b < 2; ++b)
         for (int k = 0; k < 5; ++k) {
@@ -988,7 +989,8 @@ int lbm_get_macros(lbm_handle* h, double* rho, double* ux, double* uy, double* T
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "macros");
     if (flag[1]) {
-        h->err = "a tensor copy of the bulk kernel did not complete in time";
+        h->err = (flag[1] & 2) ? "a tensor copy of the bulk kernel did not complete in time"
+                               : "a cluster exchange of the band kernel did not complete in time";
         return LBM_ERR_TIMEOUT;
     }
     if (flag[0]) {

@@ -633,6 +633,69 @@ __device__ __forceinline__ double lab_component(int m, int kind, double r, doubl
 // the targets, and back to the lab frame) and the RK4 update of the
 // boundary state are FP64 for every storage.
 
+// Exchanges inside a cluster without a cluster barrier: a CTA stores a
+// value into the shared memory of every CTA of its cluster with st.async,
+// which counts the bytes on the receiving CTA's transaction barrier; each
+// CTA expects the bytes of one exchange on its own barrier and waits for
+// them (bounded).
+__device__ __forceinline__ unsigned cluster_map(unsigned a, unsigned q)
+{
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(q));
+    return r;
+}
+
+__device__ __forceinline__ void put_async(unsigned a, double v, unsigned bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+                 ::"r"(a), "l"(__double_as_longlong(v)), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void put_async(unsigned a, float v, unsigned bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+                 ::"r"(a), "r"(__float_as_uint(v)), "r"(bar) : "memory");
+}
+
+// v into slot p of every CTA of the cluster, counted on barrier `bar` there
+template <typename T>
+__device__ __forceinline__ void put_cluster(T* p, T v, unsigned long long* bar)
+{
+    const unsigned a = smem_u32(p), b = smem_u32(bar);
+#pragma unroll
+    for (unsigned q = 0; q < kCluster; ++q) put_async(cluster_map(a, q), v, cluster_map(b, q));
+}
+
+__device__ __forceinline__ void expect_bytes(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Wait for phase `parity` of an exchange barrier, at most 1 s; a timeout is
+// recorded as bit 2 of *status (the values read after it are not valid) and
+// returns false.
+__device__ __forceinline__ bool wait_exchange(unsigned long long* bar, unsigned parity, int* status)
+{
+    const unsigned b = smem_u32(bar);
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n"
+            " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > 1000000000ull) {
+            atomicOr(status, 4);
+            return false;
+        }
+    }
+}
+
 __device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
@@ -675,6 +738,9 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     __shared__ __align__(16) R Xp[kTileThreads * 8];        // shares of the system's inputs
     __shared__ __align__(16) double Xw[kTileThreads * 4];   // wave amplitudes
     __shared__ __align__(16) R Xv[kTileThreads * 4];        // viscous vector (local frame, frozen)
+    // exchange barriers: waves of even / odd stages, stage values of even /
+    // odd stages
+    __shared__ __align__(8) unsigned long long xbar[4];
     extern __shared__ __align__(16) unsigned char dyn_raw[];
     R* SUt = reinterpret_cast<R*>(dyn_raw);        // [max_nodes][4] macros of t
     R* SUt1 = SUt + 4 * B.max_nodes;               // [max_nodes][4] macros of t + 1
@@ -695,6 +761,14 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     if (l < ns) Na = snt[l];
     if (kp < ns) Nb = snt[kp];
     const UDesc D = B.ld[(long long)tile * kTileUnknowns + l];
+    if (l == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&xbar[k])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // unknowns that compute stage s (the same in every CTA of the cluster)
+    const int nc0 = __syncthreads_count(D.level <= 3), nc1 = __syncthreads_count(D.level <= 2),
+              nc2 = __syncthreads_count(D.level <= 1), nc3 = __syncthreads_count(D.level <= 0);
     cl.sync();                          // every CTA of the cluster runs before any remote store
 
     // 1. strip nodes: macros of t and moments of t for every CTA; macros of
@@ -781,8 +855,14 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     constexpr bool kLocal = sizeof(R) == 4;
     R xs[8] = {0, 0, 0, 0, 0, 0, 0, 0}; // the inputs, kLocal
     R Vs[4] = {0, 0, 0, 0};             // viscous vector (local frame, frozen), kLocal
+    bool xok = true;                    // every exchange so far completed in time
     for (int stage = 0; stage < 4; ++stage) {
         const bool comp = lev <= 3 - stage;
+        if (l == 0) {                   // bytes of this stage's two exchanges
+            const unsigned ncomp = unsigned(stage == 0 ? nc0 : stage == 1 ? nc1 : stage == 2 ? nc2 : nc3);
+            expect_bytes(&xbar[stage & 1], unsigned(kCluster * sizeof(double)) * ncomp);
+            expect_bytes(&xbar[2 + (stage & 1)], unsigned(kCluster * sizeof(R)) * ncomp);
+        }
         X.frac = stage == 0 ? R(0) : (stage == 3 ? R(1) : R(0.5));
         R Ul[4] = {0, 0, 0, 0}, dUn[4] = {0, 0, 0, 0};
         R d_ut = 0;
@@ -950,7 +1030,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                     else w = st + srow(Vr) + B.alpha_T * (B.t_inf - st) + relaxP;
                 }
             }
-            bcast(Xw + 4 * l + rank, w);
+            put_cluster(Xw + 4 * l + rank, w, &xbar[stage & 1]);
             // the transversal and viscous terms this CTA adds in step C
             if (cbc) {
                 if (rank == 3) {
@@ -961,7 +1041,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                 }
             }
         }
-        cl.sync();
+        if (xok) xok = wait_exchange(&xbar[stage & 1], (stage >> 1) & 1, B.status);
         // C: lab component rank of the right-hand side; RK4 update (FP64)
         if (comp) {
             const double* w = Xw + 4 * l;
@@ -985,15 +1065,15 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                 const double wk = stage == 0 ? 1.0 : 2.0;
                 const double hk = stage == 2 ? 1.0 : 0.5;
                 acc = (stage == 0 ? 0.0 : acc) + wk * kc;
-                bcast(Ys + 4 * l + rank, R(u0r + hk * kc));
+                put_cluster(Ys + 4 * l + rank, R(u0r + hk * kc), &xbar[2 + (stage & 1)]);
             } else {
                 // RK4: U(t + 1) = U(t) + (k1 + 2 k2 + 2 k3 + k4) / 6
                 const double un = u0r + (acc + kc) * (1.0 / 6.0);
                 B.Ub[((long long)(par_t ^ 1) * B.n_unk + D.gid) * 4 + rank] = un;
-                bcast(Ys + 4 * l + rank, R(un));
+                put_cluster(Ys + 4 * l + rank, R(un), &xbar[2 + (stage & 1)]);
             }
         }
-        cl.sync();
+        if (xok) xok = wait_exchange(&xbar[2 + (stage & 1)], (stage >> 1) & 1, B.status);
     }
 
     // 3. Dirichlet populations of unknown l, on CTA l % kCluster

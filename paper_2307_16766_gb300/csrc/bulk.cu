@@ -53,18 +53,6 @@ struct Stage {
     }
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void* p)
-{
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Wait for phase `parity` of a transaction barrier with a 1 s limit; on
 // timeout record it in *status and wait once more (again bounded) for copies
 // still in flight before giving up.

@@ -462,6 +462,20 @@ struct Export {
     void* stripN;
 };
 
+// Shared-memory address of a generic pointer, and the global nanosecond
+// timer (for bounded waits).
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Arithmetic type of the strips and of the band kernel's stencils,
 // transversal and viscous terms: FP64 with FP64 storage, FP32 otherwise.
 template <typename S>
@@ -535,6 +549,7 @@ struct Band {
     const StripNode* sn;
     double* Ub;      // boundary state [parity][n_unk][4] (the fused kernel); [n_unk][4]
                      // in the allocation-free path
+    int* status;     // kernel status bits (bit 2: a cluster exchange timed out)
     double *Ya, *Yb, *acc, *V;   // stage scratch of the allocation-free path
     int* mask;
 };
