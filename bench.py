@@ -10,11 +10,14 @@ bracketed by CUDA events on the solver's stream with an L2 flush (a write,
 then a read, of a 512 MB buffer) between timed steps; barrier + synchronize
 around the timed region; the max over ranks is reported.  A step is one
 lbm_step(1): the band kernel (strip nodes + characteristic boundary solver)
-beside the bulk kernel, whose duration (the roofline's kernel time) is
-taken with events the library records around it.  N > 1 runs independent
-replicas, one per GPU (weak scaling; the method has no cross-GPU exchange in
-this configuration).  The reference arm times the FP64 CPU oracle on this
-host on the same workload and metric.
+and the bulk kernel beside it.  The bulk kernel's duration (the roofline's
+kernel time) comes from a second loop over the same steps in which the
+library records the caller's events around each launch.  A third loop runs
+the phases in sequence (breakdown), and a batched 96-run coefficient sweep
+is timed beside the same runs stepped one after another.  N > 1 runs
+independent replicas, one per GPU (weak scaling; the method has no
+cross-GPU exchange in this configuration).  The reference arm times the
+FP64 CPU oracle on this host on the same workload and metric.
 """
 import argparse
 import hashlib
@@ -195,13 +198,6 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
 
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
-    # per step: bulk before/after (the solver's internal stream), step start,
-    # band before/after (the solver's stream)
-    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
-    with torch.cuda.stream(stream):
-        for evs in kev:                # events exist once recorded
-            for e in evs:
-                e.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -216,19 +212,35 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
             # flush lands inside the next timed step).
             flush.fill_(float(k))
             torch.sum(flush, dim=0, out=flush_sum)
-            lbm.lbm_set_kernel_events(sim.handle, [e.cuda_event for e in kev[k]])
             ev[k][0].record(stream)
-            sim.step(1)                 # rim + boundary beside the interior
+            sim.step(1)                 # band kernel, bulk kernel beside it
             ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    lbm.lbm_set_kernel_events(sim.handle, [])
     step_ms = np.array([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)])
-    interior_ms = np.array([kev[k][0].elapsed_time(kev[k][1]) for k in range(K)])
-    chain_ms = np.array([kev[k][3].elapsed_time(kev[k][4]) for k in range(K)])
+
+    # Kernel durations while the two kernels run side by side: the same steps
+    # with the library's timing hook, which records events around each
+    # launch (the bulk kernel then runs on the solver's internal stream,
+    # forked from and joined to the solver's stream).
+    KE = min(K, 50)
+    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(KE)]
+    with torch.cuda.stream(stream):
+        for evs in kev:                # events exist once recorded
+            for e in evs:
+                e.record(stream)
+        for k in range(KE):
+            flush.fill_(float(k))
+            torch.sum(flush, dim=0, out=flush_sum)
+            lbm.lbm_set_kernel_events(sim.handle, [e.cuda_event for e in kev[k]])
+            sim.step(1)
+    torch.cuda.synchronize(dev)
+    lbm.lbm_set_kernel_events(sim.handle, [])
+    interior_ms = np.array([kev[k][0].elapsed_time(kev[k][1]) for k in range(KE)])
+    chain_ms = np.array([kev[k][3].elapsed_time(kev[k][4]) for k in range(KE)])
 
     # Breakdown, not part of the headline: the same steps with the phases in
     # sequence (bulk = rim + interior, then the boundary phase).

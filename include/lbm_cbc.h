@@ -130,10 +130,10 @@ int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
                     const double* uy, const double* T, int on_device);
 
 /* Advance n time steps (asynchronous on the handle's stream).  Per step, the
- * band kernel (the boundary solver) runs on the handle's stream while the
- * bulk kernel (every bulk node) and the zero-gradient copies run on the
- * internal stream.  The result is identical to phase 0 followed by
- * phase 1. */
+ * band kernel (the boundary solver) runs on the internal high-priority
+ * stream while the bulk kernel (every bulk node) and the zero-gradient
+ * copies run on the handle's stream.  The result is identical to phase 0
+ * followed by phase 1. */
 int lbm_step(lbm_handle* h, int n);
 
 /* Issue one phase of one step on the handle's stream, without overlap:
@@ -151,8 +151,8 @@ int lbm_step_phase(lbm_handle* h, int phase);
  *   events[2]             at the start of the step;
  *   events[3], events[4]  before / after the band launch (with the inflow
  *                         write of the first steps);
- * all on the handle's stream except events[0..1] in lbm_step(), which go
- * on the internal stream with the bulk launch.  The events stay owned by the
+ * all on the handle's stream except events[3..4] in lbm_step(), which go
+ * on the internal stream with the band launch.  The events stay owned by the
  * caller, who must keep them alive while the hook is set; with several steps
  * per call only the last step's records remain.  A NULL entry among the
  * first n is LBM_ERR_ARG. */

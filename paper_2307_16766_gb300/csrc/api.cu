@@ -52,7 +52,7 @@ struct lbm_handle {
     BulkRun* brun = nullptr; // its run descriptor (workspace)
     int bulk_items = 0, bulk_grid = 0;
     size_t band_pad = 0;     // extra shared memory per band CTA (SM reservation)
-    cudaStream_t aux = nullptr;              // internal stream: the bulk beside the band
+    cudaStream_t aux = nullptr;              // internal stream: the bulk beside the band, when timed
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t kev[5] = {};  // caller's timing events (see lbm_set_kernel_events)
     long long steps = 0;
@@ -647,10 +647,9 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
         if (prepare_bulk_persistent(h->lattice, h->storage) != 0)
             return cuda_fail(h, cudaGetLastError(), "persistent bulk shared memory");
     }
-    // The bulk kernel runs on an internal stream beside the band kernel,
-    // which stays on the handle's stream so that it is queued first.
-    // (Reserving whole SMs for the band through its shared-memory request
-    // measured slower: the bulk loses more than the band gains.)
+    // Band CTAs share their SMs with bulk CTAs.  (Reserving whole SMs for
+    // the band through its shared-memory request measured slower: the bulk
+    // loses more than the band gains.)
     h->band_pad = 0;
     if (h->B.n_tiles > 0 && prepare_boundary(h->lattice, h->storage, h->B, h->band_pad) != 0)
         return cuda_fail(h, cudaGetLastError(), "band kernel shared memory");
@@ -691,17 +690,18 @@ int mark(lbm_handle* h, int k, cudaStream_t st)
 }
 
 // Bulk update of step (parity par) on stream st, bracketed by the caller's
-// timing events 0 and 1 when set.
-int bulk(lbm_handle* h, int par, cudaStream_t st)
+// timing events 0 and 1 when set; early: start beside the band kernel just
+// launched on st (programmatic stream serialization).
+int bulk(lbm_handle* h, int par, cudaStream_t st, bool early = false)
 {
     int rc = mark(h, 0, st);
     if (rc != LBM_OK) return rc;
     if (h->persistent)
         rc = launch_bulk_persistent(h->lattice, h->storage, h->brun, 1, h->bulk_items, par,
-                                    h->bulk_grid, st);
+                                    h->bulk_grid, st, early);
     else
         rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->bulk, h->tmap[par], h->f[par],
-                         h->f[par ^ 1], h->flag + 1, st);
+                         h->f[par ^ 1], h->flag + 1, st, early);
     if (rc) return check_launch(h, rc, "bulk kernel");
     return mark(h, 1, st);
 }
@@ -926,11 +926,23 @@ int lbm_step(lbm_handle* h, int n)
             h->steps++;
             continue;
         }
-        // Fork: the band kernel on the handle's stream (queued first, so its
-        // few CTAs take their SMs before the bulk's), the bulk kernel and the
-        // zero-gradient copies on the internal stream; join before the next
-        // step.  The kernels write disjoint nodes of the new buffer and read
-        // only the old one.
+        // The band kernel and the bulk kernel write disjoint nodes of the
+        // new buffer and read only the old one, so they run side by side:
+        // the band first (its few CTAs take their SMs before the bulk's),
+        // then the bulk on the same stream with early start, which the band
+        // kernel allows at once; the zero-gradient copies and the next step
+        // wait for both.
+        if (!h->kev[0] && !h->kev[3]) {
+            rc = band(h, par, h->stream);
+            if (rc == LBM_OK) rc = bulk(h, par, h->stream, true);
+            if (rc == LBM_OK) rc = zero_gradient(h, par, h->stream);
+            if (rc != LBM_OK) return rc;
+            h->steps++;
+            continue;
+        }
+        // With the caller's timing events between the launches: fork the
+        // bulk kernel and the zero-gradient copies onto the internal stream
+        // and join before the next step.
         cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
         if (e != cudaSuccess) return cuda_fail(h, e, "fork");
@@ -1112,8 +1124,7 @@ struct lbm_batch {
     };
     std::vector<Group> groups;
     void* dev = nullptr;                   // the groups' descriptor arrays
-    cudaStream_t stream = nullptr, aux = nullptr, cap = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t stream = nullptr, cap = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool tuned = false;
     int nsm = 0;
@@ -1189,11 +1200,16 @@ void autotune_store(const std::string& key, int value)
     fclose(fp);
 }
 
-// One step of every run: per group one batched band launch on the batch's
-// stream and one persistent bulk launch (plus zero-gradient copies) on the
-// internal stream, forked and joined like lbm_step.
+// One step of every run: per group one batched band launch on the internal
+// high-priority stream and one persistent bulk launch (plus zero-gradient
+// copies) on the batch's stream, forked and joined like lbm_step.
 int batch_issue_step(lbm_batch* b, int par, cudaStream_t s0, bool with_inflow)
 {
+    // All on one stream: the band kernels of the groups, then their bulk
+    // kernels, each after the first with early start (every kernel here
+    // signals its dependents at once; none reads what another writes), so
+    // all run side by side; the zero-gradient copies and the next step
+    // wait for all of them.
     // inflow equilibria (once per buffer) ahead of the fork, so that every
     // kernel of the step comes after them
     if (with_inflow)
@@ -1204,25 +1220,24 @@ int batch_issue_step(lbm_batch* b, int par, cudaStream_t s0, bool with_inflow)
                     return batch_fail(b, cudaGetLastError(), "inflow kernel");
                 h->inflow_done[par ^ 1] = true;
             }
-    cudaError_t e = cudaEventRecord(b->ev_fork, s0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
-    if (e != cudaSuccess) return batch_fail(b, e, "fork");
+    bool first = true;
     for (auto& g : b->groups) {
-        if (g.n_tiles > 0 &&
-            launch_band_batch(g.lattice, g.storage, g.band, g.tile_run, g.n_tiles, g.band_smem, par, s0))
+        if (g.n_tiles == 0) continue;
+        if (launch_band_batch(g.lattice, g.storage, g.band, g.tile_run, g.n_tiles, g.band_smem, par, s0,
+                              !first))
             return batch_fail(b, cudaGetLastError(), "batched band kernel");
-        if (launch_bulk_persistent(g.lattice, g.storage, g.bulk, int(g.members.size()), g.total_items, par,
-                                   g.grid, b->aux))
-            return batch_fail(b, cudaGetLastError(), "persistent bulk kernel");
-        for (int m : g.members) {
-            lbm_handle* h = b->runs[m];
-            if (h->B.n_zg > 0 && launch_zg(h->lattice, h->storage, h->G, h->B, h->f[par ^ 1], b->aux))
-                return batch_fail(b, cudaGetLastError(), "zero-gradient kernel");
-        }
+        first = false;
     }
-    e = cudaEventRecord(b->ev_join, b->aux);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, b->ev_join, 0);
-    return e == cudaSuccess ? LBM_OK : batch_fail(b, e, "join");
+    for (auto& g : b->groups) {
+        if (launch_bulk_persistent(g.lattice, g.storage, g.bulk, int(g.members.size()), g.total_items, par,
+                                   g.grid, s0, !first))
+            return batch_fail(b, cudaGetLastError(), "persistent bulk kernel");
+        first = false;
+    }
+    for (lbm_handle* h : b->runs)
+        if (h->B.n_zg > 0 && launch_zg(h->lattice, h->storage, h->G, h->B, h->f[par ^ 1], s0))
+            return batch_fail(b, cudaGetLastError(), "zero-gradient kernel");
+    return LBM_OK;
 }
 
 // Pick the persistent bulk kernel's CTAs per SM for each group: the fastest
@@ -1276,9 +1291,6 @@ void batch_release(lbm_batch* b)
     else cudaDeviceSynchronize();
     for (int k = 0; k < 2; ++k)
         if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
-    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-    if (b->ev_join) cudaEventDestroy(b->ev_join);
-    if (b->aux) cudaStreamDestroy(b->aux);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->dev) cudaFree(b->dev);
     for (lbm_handle* h : b->runs) lbm_destroy(h);
@@ -1386,10 +1398,8 @@ int lbm_batch_create(int n, const int* lattice, const int* nx, const int* ny, co
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
     for (auto& g : b->groups) g.grid = b->nsm * 4;               // until tuned
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
+
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         fprintf(stderr, "lbm_batch_create: %s\n", cudaGetErrorString(e));
         batch_release(b);

@@ -731,6 +731,9 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     using C = typename Store<S>::C;
     using R = typename StripReal<S>::T;
     constexpr bool TH = L::THERMAL;
+    // a kernel launched after this one for early start (the bulk update,
+    // which reads only the old buffer) may begin now
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     cg::cluster_group cl = cg::this_cluster();
     const int rank = int(cl.block_rank());
     const int l = threadIdx.x;
@@ -1143,11 +1146,11 @@ int boundary_t(const Geom& G, const Offsets& O, const Export& E, const Band& B, 
 
 template <int LAT, typename S>
 int band_batch_t(const BandRun* runs, const int2* tile_run, int n_tiles, size_t smem, int par_t,
-                 cudaStream_t st)
+                 cudaStream_t st, bool early)
 {
     if (n_tiles == 0) return 0;
-    k_band_batch<LAT, S><<<n_tiles * kCluster, kTileThreads, smem, st>>>(runs, tile_run, par_t);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return launch_ex(k_band_batch<LAT, S>, dim3(n_tiles * kCluster), dim3(kTileThreads), smem, st, early,
+                     runs, tile_run, par_t);
 }
 
 template <int LAT, typename S>
@@ -1220,9 +1223,9 @@ int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad)
 }
 
 int launch_band_batch(int lat, int storage, const BandRun* runs, const int2* tile_run, int n_tiles,
-                      size_t smem, int par_t, cudaStream_t st)
+                      size_t smem, int par_t, cudaStream_t st, bool early)
 {
-#define CALL(L, S) band_batch_t<L, S>(runs, tile_run, n_tiles, smem, par_t, st)
+#define CALL(L, S) band_batch_t<L, S>(runs, tile_run, n_tiles, smem, par_t, st, early)
     BAND_DISPATCH(lat, storage, CALL);
 #undef CALL
     return -1;

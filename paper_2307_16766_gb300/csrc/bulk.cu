@@ -195,6 +195,8 @@ __global__ void __launch_bounds__(kBulkThreads)
     extern __shared__ __align__(128) unsigned char smem_raw[];   // 2 x BX::TOTAL
     __shared__ __align__(8) unsigned long long bar[2];
     __shared__ int s_first[kMaxBatchRuns + 1];
+    // the next group's kernel of a batched step (other grids) may begin now
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     for (int k = threadIdx.x; k <= n_runs; k += blockDim.x) s_first[k] = k < n_runs ? runs[k].first : total;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
@@ -425,7 +427,7 @@ int inflow_t(const Geom& G, const int* nodes, int n, const double U[4], void* f,
 
 template <int LAT, typename S>
 int bulk_t(const Geom& G, const Offsets& O, const Region& R, const CUtensorMap* tmaps,
-           const void* fin, void* fout, int* status, cudaStream_t st)
+           const void* fin, void* fout, int* status, cudaStream_t st, bool early)
 {
     const int h = R.y1 - R.y0;
     if (R.x1 <= R.x0 || h <= 0) return 0;
@@ -438,18 +440,18 @@ int bulk_t(const Geom& G, const Offsets& O, const Region& R, const CUtensorMap* 
     tm.m2 = tmaps[3];
     tm.m1 = tmaps[4];
     dim3 blk(kBulkThreads), grd(t1 - t0, h);
-    k_bulk<LAT, S><<<grd, blk, smem, st>>>(tm, G, O, R, static_cast<const S*>(fin),
-                                           static_cast<S*>(fout), status);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return launch_ex(k_bulk<LAT, S>, grd, blk, smem, st, early, tm, G, O, R, static_cast<const S*>(fin),
+                     static_cast<S*>(fout), status);
 }
 
 template <int LAT, typename S>
-int bulk_persistent_t(const BulkRun* runs, int n_runs, int total, int par, int grid, cudaStream_t st)
+int bulk_persistent_t(const BulkRun* runs, int n_runs, int total, int par, int grid, cudaStream_t st,
+                      bool early)
 {
     if (total <= 0) return 0;
     if (n_runs > kMaxBatchRuns) return -1;
-    k_bulk_persistent<LAT, S><<<grid, kBulkThreads, 2 * Stage<LAT, S>::TOTAL, st>>>(runs, n_runs, total, par);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return launch_ex(k_bulk_persistent<LAT, S>, dim3(grid), dim3(kBulkThreads), 2 * Stage<LAT, S>::TOTAL, st,
+                     early, runs, n_runs, total, par);
 }
 
 template <int LAT, typename S>
@@ -507,18 +509,18 @@ int launch_inflow(int lat, int storage, const Geom& G, const int* nodes, int n, 
 
 int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Region& R,
                 const CUtensorMap* tmaps, const void* fin, void* fout, int* status,
-                cudaStream_t st)
+                cudaStream_t st, bool early)
 {
-#define CALL(L, S) bulk_t<L, S>(G, O, R, tmaps, fin, fout, status, st)
+#define CALL(L, S) bulk_t<L, S>(G, O, R, tmaps, fin, fout, status, st, early)
     LBM_DISPATCH(lat, storage, CALL);
 #undef CALL
 }
 
 
 int launch_bulk_persistent(int lat, int storage, const BulkRun* runs, int n_runs, int total, int par,
-                           int grid, cudaStream_t st)
+                           int grid, cudaStream_t st, bool early)
 {
-#define CALL(L, S) bulk_persistent_t<L, S>(runs, n_runs, total, par, grid, st)
+#define CALL(L, S) bulk_persistent_t<L, S>(runs, n_runs, total, par, grid, st, early)
     LBM_DISPATCH(lat, storage, CALL);
 #undef CALL
 }

@@ -558,6 +558,28 @@ struct Band {
 // Host-side launchers (defined in bulk.cu / boundary.cu)
 // ---------------------------------------------------------------------------
 
+// Launch with or without programmatic stream serialization: with it the
+// kernel may start as soon as every CTA of the kernel before it in the
+// stream has signalled (griddepcontrol.launch_dependents); it never waits on
+// that kernel's results, so it must not read what that kernel writes.  Work
+// issued after it in the stream still waits for both.
+template <typename... K, typename... A>
+inline int launch_ex(void (*kern)(K...), dim3 grd, dim3 blk, size_t smem, cudaStream_t st, bool early, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grd;
+    cfg.blockDim = blk;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = early ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...) == cudaSuccess ? 0 : -1;
+}
+
+
 // Initial populations f^eq(U0) into f, strips of time 0, boundary state.
 int launch_init(int lat, int storage, const Geom& G, const Export& E, const Band& B,
                 const double* rho, const double* ux, const double* uy, const double* T, void* f,
@@ -567,10 +589,12 @@ int launch_inflow(int lat, int storage, const Geom& G, const int* nodes, int n, 
                   void* f, cudaStream_t st);
 // One bulk step fin -> fout over the nodes of region R; tmaps[0..4] describe
 // fin for the tensor copies (box depths 7, 5, 3, 2, 1 planes); *status gets bit 1
-// if a copy never completed.
+// if a copy never completed.  early: programmatic stream serialization (the
+// launch may start while the kernel before it in the stream runs, once that
+// kernel's CTAs have signalled; it must not read what that kernel writes).
 int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Region& R,
                 const CUtensorMap* tmaps, const void* fin, void* fout, int* status,
-                cudaStream_t st);
+                cudaStream_t st, bool early = false);
 int launch_macros(int lat, int storage, const Geom& G, const void* f, double* rho, double* ux,
                   double* uy, double* T, int* flag, cudaStream_t st);
 // The band of one step fin -> fnew: strip nodes, RK4 of the characteristic
@@ -590,7 +614,7 @@ struct BandRun {
 // Band tiles of many grids of one lattice and storage in one launch:
 // tile_run[t] = (run, tile of that run); smem = the largest band_dynamic_smem.
 int launch_band_batch(int lat, int storage, const BandRun* runs, const int2* tile_run, int n_tiles,
-                      size_t smem, int par_t, cudaStream_t st);
+                      size_t smem, int par_t, cudaStream_t st, bool early = false);
 int prepare_band_batch(int lat, int storage, size_t smem);
 // Dynamic shared memory the band kernel needs per CTA (without padding).
 size_t band_dynamic_smem(int lat, int storage, const Band& B);
@@ -598,7 +622,7 @@ size_t band_dynamic_smem(int lat, int storage, const Band& B);
 // par -> par ^ 1 of each) with `grid` CTAs looping over the total work
 // items, a two-stage tensor-copy pipeline per CTA.
 int launch_bulk_persistent(int lat, int storage, const BulkRun* runs, int n_runs, int total, int par,
-                           int grid, cudaStream_t st);
+                           int grid, cudaStream_t st, bool early = false);
 // Opt the persistent bulk kernel in to its dynamic shared memory.
 int prepare_bulk_persistent(int lat, int storage);
 // Opt the band kernel in to its dynamic shared memory (once, at creation).
