@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch-leg", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--batch-steps", type=int, default=1000)
     return ap.parse_args()
 
@@ -425,7 +426,7 @@ def main():
         return
 
     import torch
-    res = run_gpu(args, rank, world, local_rank, args.storage)
+    res = run_gpu(args, rank, world, local_rank, args.storage, want_e2e=not args.no_e2e)
     fp64 = None
     if not args.no_fp64_leg and args.storage != "f64":
         a2 = argparse.Namespace(**vars(args))
