@@ -228,3 +228,57 @@ class Sim:
         U = np.zeros((self.ny, self.nx, 4))
         lib().orc_boundary_state(self._h, _dp(U))
         return U
+
+
+# ------------------------------------------------------ pressure loss -------
+# The loss used to tune the relaxation parameters: the squared deviation of
+# the pressure P = rho c_s^2 T (isothermal: rho c_s^2) from a reference over
+# the nodes off the M boundary layers, summed over the steps -- the
+# reflection measure of Sec. "Numerical Results" (pressure against a
+# reference run on a larger domain) taken as an energy.  Here P - c_s^2 rho0
+# is formed as c_s^2 ((rho - rho0) + rho0 (T - 1) + (rho - rho0)(T - 1)).
+
+def pressure_loss(cfg, fields, steps, dP_ref=None):
+    """J = sum_{n=1..steps} sum_x (P_n(x) - c_s^2 rho0 - dP_ref[n-1](x))^2
+    over x off the boundary layers of non-periodic axes.  dP_ref: None or
+    an array [steps, ny, nx]."""
+    info = lattice_info(cfg["lattice"])
+    cs2, M = info["cs2"], info["M"]
+    rho0 = cfg.get("rho0", 1.0)
+    nx, ny = cfg["nx"], cfg["ny"]
+    perx = cfg["sides"][0] == "periodic"
+    pery = cfg["sides"][2] == "periodic"
+    xs = slice(0, nx) if perx else slice(M, nx - M)
+    ys = slice(0, ny) if pery else slice(M, ny - M)
+    s = Sim(cfg).init(*fields)
+    J = 0.0
+    for n in range(steps):
+        s.step(1)
+        rho, ux, uy, T = s.macros()
+        dr = rho - rho0
+        dP = cs2 * (dr + rho0 * (T - 1.0) + dr * (T - 1.0)) if cfg["lattice"] != "D2Q9" else cs2 * dr
+        e = dP[ys, xs] - (0.0 if dP_ref is None else dP_ref[n][ys, xs])
+        J += float(np.sum(e * e))
+    return J
+
+
+def with_relaxation(cfg, alpha_T, beta_P, p_inf):
+    c = dict(cfg)
+    c["alpha_T"], c["beta_P"], c["p_inf"] = float(alpha_T), float(beta_P), [float(p_inf)] * 4
+    return c
+
+
+def pressure_loss_fd_gradient(cfg, fields, steps, h=(1e-4, 1e-4, 1e-4), dP_ref=None):
+    """Central differences of pressure_loss in (alpha_T, beta_P, P_inf),
+    P_inf moved on every side together (cfg's p_inf must be equal on all
+    sides)."""
+    th = [cfg["alpha_T"], cfg["beta_P"], cfg["p_inf"][0]]
+    g = []
+    for k in range(3):
+        up, dn = list(th), list(th)
+        up[k] += h[k]
+        dn[k] -= h[k]
+        Jp = pressure_loss(with_relaxation(cfg, *up), fields, steps, dP_ref)
+        Jm = pressure_loss(with_relaxation(cfg, *dn), fields, steps, dP_ref)
+        g.append((Jp - Jm) / (2.0 * h[k]))
+    return g

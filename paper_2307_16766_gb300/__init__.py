@@ -93,6 +93,10 @@ def lib():
             "lbm_destroy": (None, [vp]),
             "lbm_cbc_side_step_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, pp,
                                                     vp, vp, vp, vp, vp]),
+            "lbm_grad_begin": (C.c_int, [vp]),
+            "lbm_grad_step": (C.c_int, [vp, C.c_int, vp, C.c_longlong]),
+            "lbm_grad_result": (C.c_int, [vp, dp, dp]),
+            "lbm_grad_end": (C.c_int, [vp]),
             "lbm_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                            C.POINTER(C.c_int), dp, pp, C.POINTER(vp)]),
             "lbm_batch_run": (C.c_int, [vp, C.c_int, C.POINTER(vp)]),
@@ -260,6 +264,26 @@ def lbm_cbc_side_step_noalloc(lattice, side, length, tau, params, ub_ptr, strip_
                                            C.byref(params), C.c_void_p(ub_ptr),
                                            C.c_void_p(strip_t_ptr), C.c_void_p(strip_t1_ptr),
                                            C.c_void_p(neq_t_ptr or None), C.c_void_p(stream_ptr or None)))
+
+
+def lbm_grad_begin(h):
+    _check(lib().lbm_grad_begin(h), h)
+
+
+def lbm_grad_step(h, n, dP_ref_ptr=None, ref_stride=0):
+    _check(lib().lbm_grad_step(h, n, dP_ref_ptr, ref_stride), h)
+
+
+def lbm_grad_result(h):
+    """(J, [dJ/dalpha_T, dJ/dbeta_P, dJ/dP_inf])"""
+    J = C.c_double()
+    dJ = (C.c_double * 3)()
+    _check(lib().lbm_grad_result(h, C.byref(J), dJ), h)
+    return J.value, list(dJ)
+
+
+def lbm_grad_end(h):
+    _check(lib().lbm_grad_end(h), h)
 
 
 def _check_batch(rc, b):
@@ -438,3 +462,70 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------- gradients ---
+
+def pressure_loss_and_gradient(cfg, fields, steps, dP_ref=None, device=None):
+    """J = sum over `steps` steps and the nodes off the boundary layers of
+    (P - c_s^2 rho0 - dP_ref)^2, and dJ/d(alpha_T, beta_P, P_inf), by
+    tangent-linear steps of a fresh solver (lbm_grad_*).  dP_ref: None or
+    a CUDA float64 tensor [steps, ny, nx].  Returns (J, [3 derivatives])."""
+    import torch
+    sim = Simulation(cfg, device=device).init_fields(*fields)
+    try:
+        lbm_grad_begin(sim.handle)
+        if dP_ref is None:
+            lbm_grad_step(sim.handle, steps)
+        else:
+            ref = dP_ref.contiguous()
+            if ref.dtype != torch.float64 or tuple(ref.shape) != (steps, sim.ny, sim.nx):
+                raise ValueError("dP_ref must be float64 [steps, ny, nx]")
+            lbm_grad_step(sim.handle, steps, ref.data_ptr(), sim.ny * sim.nx)
+        J, dJ = lbm_grad_result(sim.handle)
+        lbm_grad_end(sim.handle)
+    finally:
+        sim.close()
+    return J, dJ
+
+
+def _with_theta(cfg, theta):
+    c = dict(cfg)
+    c["alpha_T"], c["beta_P"] = float(theta[0]), float(theta[1])
+    c["p_inf"] = [float(theta[2])] * 4
+    return c
+
+
+def _make_cbc_loss():
+    import torch
+
+    class CBCLoss(torch.autograd.Function):
+        """J(theta) for theta = (alpha_T, beta_P, P_inf) as a differentiable
+        function: forward runs the tangent-linear steps (which give J and
+        dJ/dtheta together), backward scales the stored derivatives."""
+
+        @staticmethod
+        def forward(ctx, theta, cfg, fields, steps, dP_ref=None):
+            th = theta.detach().cpu().double().tolist()
+            J, dJ = pressure_loss_and_gradient(_with_theta(cfg, th), fields, steps, dP_ref)
+            ctx.save_for_backward(torch.tensor(dJ, dtype=theta.dtype, device=theta.device))
+            return torch.tensor(J, dtype=theta.dtype, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (dJ,) = ctx.saved_tensors
+            return grad_out * dJ, None, None, None, None
+
+    return CBCLoss
+
+
+_CBCLoss = None
+
+
+def cbc_loss(theta, cfg, fields, steps, dP_ref=None):
+    """Differentiable pressure loss J(alpha_T, beta_P, P_inf) (torch
+    autograd; theta a 3-element tensor)."""
+    global _CBCLoss
+    if _CBCLoss is None:
+        _CBCLoss = _make_cbc_loss()
+    return _CBCLoss.apply(theta, cfg, fields, steps, dP_ref)

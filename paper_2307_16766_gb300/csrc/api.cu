@@ -58,8 +58,20 @@ struct lbm_handle {
     long long steps = 0;
     bool initialized = false;
     bool bulk_pending = false;   // phase 0 issued, phase 1 not yet
+    // tangent-linear steps (lbm_grad_*): their state, and whether they
+    // advanced the populations past the strips and boundary state of the
+    // ordinary step (which then needs lbm_init_fields or lbm_set_state)
+    TLState tl{};
+    void* tl_mem = nullptr;
+    bool grad_stale = false;
     std::string err;
 };
+
+namespace {
+const char* const kGradStale =
+    "gradient steps advanced this handle past its boundary strips: call lbm_init_fields or "
+    "lbm_set_state before stepping it again";
+}  // namespace
 
 namespace {
 
@@ -873,6 +885,7 @@ int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux, const do
     h->steps = 0;
     h->initialized = true;
     h->bulk_pending = false;
+    h->grad_stale = false;
     return LBM_OK;
 }
 
@@ -883,6 +896,7 @@ int lbm_step_phase(lbm_handle* h, int phase)
         h->err = "lbm_step before lbm_init_fields";
         return LBM_ERR_STATE;
     }
+    if (h->grad_stale) { h->err = kGradStale; return LBM_ERR_STATE; }
     const int par = int(h->steps & 1);
     if (phase == 0) {
         if (h->bulk_pending) { h->err = "bulk phase issued twice"; return LBM_ERR_STATE; }
@@ -913,6 +927,7 @@ int lbm_step(lbm_handle* h, int n)
         return LBM_ERR_STATE;
     }
     if (h->bulk_pending) { h->err = "lbm_step in the middle of a phased step"; return LBM_ERR_STATE; }
+    if (h->grad_stale) { h->err = kGradStale; return LBM_ERR_STATE; }
     for (int i = 0; i < n; ++i) {
         const int par = int(h->steps & 1);
         int rc = mark(h, 2, h->stream);
@@ -1034,6 +1049,7 @@ int lbm_get_state(lbm_handle* h, void* buf, size_t bytes)
     if (lbm_state_bytes(h, &need) != LBM_OK || !buf) return LBM_ERR_ARG;
     if (bytes < need) { h->err = fmt("state buffer needs %zu bytes", need); return LBM_ERR_ARG; }
     if (!h->initialized || h->bulk_pending) { h->err = "no complete state to save"; return LBM_ERR_STATE; }
+    if (h->grad_stale) { h->err = kGradStale; return LBM_ERR_STATE; }
     StateHeader hd{};
     std::memcpy(hd.magic, "LBMCBC02", 8);
     hd.lattice = h->lattice; hd.nx = h->nx; hd.ny = h->ny; hd.storage = h->storage; hd.n_unk = h->B.n_unk;
@@ -1085,11 +1101,110 @@ int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes)
     h->steps = hd.steps;
     h->initialized = true;
     h->bulk_pending = false;
+    h->grad_stale = false;
     h->inflow_done[0] = h->inflow_done[1] = false;
     return LBM_OK;
 }
 
 long long lbm_steps_done(const lbm_handle* h) { return h ? h->steps : -1; }
+
+// ---------------------------------------------------------------------------
+// Gradients with respect to the relaxation parameters (tangent-linear steps)
+// ---------------------------------------------------------------------------
+
+int lbm_grad_begin(lbm_handle* h)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (!h->initialized || h->bulk_pending) { h->err = "lbm_grad_begin before a complete step state"; return LBM_ERR_STATE; }
+    if (h->tl_mem) { h->err = "gradient steps already begun"; return LBM_ERR_STATE; }
+    if (h->storage != LBM_F64 && h->storage != LBM_F32) {
+        h->err = "gradient steps need FP64 or FP32 storage";
+        return LBM_ERR_ARG;
+    }
+    if (h->B.n_unk > 0 && (h->B.viscous != VIS_OFF || h->B.dirichlet != 0)) {
+        h->err = "gradient steps need viscous = off and the equilibrium Dirichlet condition";
+        return LBM_ERR_ARG;
+    }
+    if (h->n_inflow > 0 || h->B.n_zg > 0) {
+        h->err = "gradient steps support characteristic and periodic sides only";
+        return LBM_ERR_ARG;
+    }
+    const size_t dual = tl_dual_bytes();
+    const size_t tbytes = 3 * h->f_bytes;
+    const size_t sbytes = (size_t)std::max(1, h->E.nslots) * 4 * dual;
+    const size_t ubytes = (size_t)std::max(1, h->B.n_unk) * 4 * dual;
+    size_t o = 0;
+    auto take = [&](size_t b) { const size_t at = o; o = align_up(o + b); return at; };
+    const size_t o_t0 = take(tbytes), o_t1 = take(tbytes), o_st = take(sbytes), o_st1 = take(sbytes),
+                 o_ud = take(ubytes), o_ya = take(ubytes), o_yb = take(ubytes), o_acc = take(ubytes),
+                 o_mask = take((size_t)std::max(1, h->B.n_unk) * sizeof(int)), o_sums = take(4 * sizeof(double));
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, o);
+    if (e != cudaSuccess) return cuda_fail(h, e, "gradient state allocation");
+    TLState& T = h->tl;
+    T.t[0] = at<char>(mem, o_t0);
+    T.t[1] = at<char>(mem, o_t1);
+    T.St = at<char>(mem, o_st);
+    T.St1 = at<char>(mem, o_st1);
+    T.Ud = at<char>(mem, o_ud);
+    T.Ya = at<char>(mem, o_ya);
+    T.Yb = at<char>(mem, o_yb);
+    T.acc = at<char>(mem, o_acc);
+    T.mask = at<int>(mem, o_mask);
+    T.sums = at<double>(mem, o_sums);
+    h->tl_mem = mem;
+    // the initial fields do not depend on the parameters: zero derivatives
+    e = cudaMemsetAsync(mem, 0, o, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "gradient state");
+    if (launch_tl_seed(T, h->B, int(h->steps & 1), false, h->stream))
+        return check_launch(h, -1, "gradient seed kernel");
+    h->grad_stale = true;
+    return LBM_OK;
+}
+
+int lbm_grad_step(lbm_handle* h, int n, const double* dP_ref, long long ref_stride)
+{
+    if (!h || n < 0) return LBM_ERR_ARG;
+    if (!h->tl_mem) { h->err = "lbm_grad_step before lbm_grad_begin"; return LBM_ERR_STATE; }
+    Region loss;
+    loss.x0 = h->G.perx ? 0 : h->M;
+    loss.x1 = h->G.perx ? h->nx : h->nx - h->M;
+    loss.y0 = h->G.pery ? 0 : h->M;
+    loss.y1 = h->G.pery ? h->ny : h->ny - h->M;
+    for (int i = 0; i < n; ++i) {
+        const int par = int(h->steps & 1);
+        const double* ref = dP_ref ? dP_ref + (long long)i * ref_stride : nullptr;
+        if (launch_tl_step(h->lattice, h->storage, h->tl, h->G, h->E, h->B, h->bulk, loss, h->f, par, ref,
+                           h->stream))
+            return check_launch(h, -1, "tangent-linear step");
+        h->steps++;
+    }
+    return LBM_OK;
+}
+
+int lbm_grad_result(lbm_handle* h, double* J, double* dJ)
+{
+    if (!h || !J || !dJ) return LBM_ERR_ARG;
+    if (!h->tl_mem) { h->err = "lbm_grad_result before lbm_grad_begin"; return LBM_ERR_STATE; }
+    double v[4];
+    cudaError_t e = cudaMemcpyAsync(v, h->tl.sums, sizeof v, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "gradient result");
+    *J = v[0];
+    for (int k = 0; k < 3; ++k) dJ[k] = v[k + 1];
+    return LBM_OK;
+}
+
+int lbm_grad_end(lbm_handle* h)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (!h->tl_mem) return LBM_OK;
+    cudaError_t e = h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize();
+    cudaFree(h->tl_mem);
+    h->tl_mem = nullptr;
+    h->tl = TLState{};
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "gradient state release");
+}
 
 const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
 
@@ -1099,6 +1214,7 @@ void lbm_destroy(lbm_handle* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     release_streams(h);
+    if (h->tl_mem) cudaFree(h->tl_mem);
     if (h->owns_ws && h->ws) cudaFree(h->ws);
     delete h;
 }
@@ -1430,6 +1546,7 @@ int lbm_batch_step(lbm_batch* b, int n)
     for (lbm_handle* h : b->runs) {
         if (!h->initialized) { b->err = "lbm_batch_step before every run's lbm_init_fields"; return LBM_ERR_STATE; }
         if (h->steps != b->runs[0]->steps) { b->err = "runs of a batch stepped apart"; return LBM_ERR_STATE; }
+        if (h->grad_stale) { b->err = kGradStale; return LBM_ERR_STATE; }
     }
     b->steps = b->runs[0]->steps;
     if (n > 0 && !b->tuned) {

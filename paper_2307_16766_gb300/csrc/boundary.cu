@@ -14,7 +14,7 @@
 // right-hand side needs is resolved on the host into a UDesc: another
 // unknown (stage value) or a strip node holding a bulk node's macros at t
 // and t + 1 (interpolated linearly at the stage time, Sec. 3.3).
-#include "collide.cuh"
+#include "charsys.cuh"
 
 #include <cooperative_groups.h>
 
@@ -30,368 +30,6 @@ constexpr int kBandThreads = 32;   // allocation-free path: one thread per unkno
 // the characteristic arithmetic; the host sizes tiles to fit.
 constexpr int kTileThreads = kTileUnknowns;
 constexpr int kCluster = 4;         // CTAs per band tile: one per characteristic component
-
-// Lab <-> local frame.  Sides: n the outward normal, t = +y (W, E) or +x
-// (S, N).  Corners: n = (sx, sy)/sqrt(2), t = n rotated by +90 degrees.
-template <typename R>
-__device__ __forceinline__ void to_local(int kind, R r, const R* U, R* Lc)
-{
-    Lc[0] = U[0];
-    Lc[3] = U[3];
-    switch (kind) {
-    case 0: Lc[1] = -U[1]; Lc[2] = U[2]; break;
-    case 1: Lc[1] = U[1]; Lc[2] = U[2]; break;
-    case 2: Lc[1] = -U[2]; Lc[2] = U[1]; break;
-    case 3: Lc[1] = U[2]; Lc[2] = U[1]; break;
-    default: {
-        const int c = kind - 4;
-        const R n0 = (c & 1) ? r : -r, n1 = (c & 2) ? r : -r;
-        Lc[1] = U[1] * n0 + U[2] * n1;
-        Lc[2] = -U[1] * n1 + U[2] * n0;
-    }
-    }
-}
-
-__device__ __forceinline__ void to_lab(int kind, double r, const double* Lc, double* U)
-{
-    U[0] = Lc[0];
-    U[3] = Lc[3];
-    switch (kind) {
-    case 0: U[1] = -Lc[1]; U[2] = Lc[2]; break;
-    case 1: U[1] = Lc[1]; U[2] = Lc[2]; break;
-    case 2: U[2] = -Lc[1]; U[1] = Lc[2]; break;
-    case 3: U[2] = Lc[1]; U[1] = Lc[2]; break;
-    default: {
-        const int c = kind - 4;
-        const double n0 = (c & 1) ? r : -r, n1 = (c & 2) ? r : -r;
-        U[1] = Lc[1] * n0 - Lc[2] * n1;
-        U[2] = Lc[1] * n1 + Lc[2] * n0;
-    }
-    }
-}
-
-// Where a right-hand side reads its neighbours, in arithmetic type R.
-template <typename R>
-struct CtxT {
-    const R* Y;     // stage values of the unknowns
-    const R* St;    // strip macros at t
-    const R* St1;   // strip macros at t + 1
-    R frac;         // stage time fraction in [0, 1]
-};
-using Ctx = CtxT<double>;
-
-template <typename R>
-__device__ __forceinline__ void fetch(const CtxT<R>& X, int ref, R* U)
-{
-    if (ref >= 0) {
-        if constexpr (sizeof(R) == 8) {
-            const double2* p = reinterpret_cast<const double2*>(X.Y + 4LL * ref);
-            const double2 a = p[0], b = p[1];
-            U[0] = a.x; U[1] = a.y; U[2] = b.x; U[3] = b.y;
-        } else {
-            const float4 a = *reinterpret_cast<const float4*>(X.Y + 4LL * ref);
-            U[0] = a.x; U[1] = a.y; U[2] = a.z; U[3] = a.w;
-        }
-    } else {
-        const long long s = 4LL * (-ref - 1);
-        const R w0 = R(1) - X.frac, w1 = X.frac;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) U[c] = w0 * X.St[s + c] + w1 * X.St1[s + c];
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ void fetch_local(const CtxT<R>& X, int ref, int kind, R r, R* Lc)
-{
-    R U[4];
-    fetch(X, ref, U);
-    to_local(kind, r, U, Lc);
-}
-
-// ---------------------------------------------------------------------------
-// Characteristic system in the local frame (Sec. 3.1)
-// ---------------------------------------------------------------------------
-// Thermal, U = (drho, u_n, u_t, dT), theta = 1 + dT, T~ = c_s^2 theta:
-//   S rows: (-r/2, 0, 0, 1/2), (0, 0, 1, 0), (r/4, -a, 0, 1/4), (r/4, a, 0, 1/4)
-//   S^-1 rows: (-1/r, 0, 1/r, 1/r), (0, 0, -b, b), (0, 1, 0, 0), (1, 0, 1, 1)
-//   with r = T~/(rho c_s^2) = theta/rho, a = sqrt(T~/(8 c_s^4)),
-//   b = sqrt(2 c_s^4 / T~) and Lambda = (u_n, u_n, u_n - c, u_n + c),
-//   c = sqrt(2 T~).
-// Isothermal D2Q9, U = (drho, u_n, u_t):
-//   S rows: (1/2, -h, 0), (0, 0, 1), (1/2, h, 0) with h = rho/(2 c_s),
-//   S^-1 rows: (1, 0, 1), (-c_s/rho, 0, c_s/rho), (0, 1, 0),
-//   Lambda = (u_n - c_s, u_n, u_n + c_s).
-struct CharSys {
-    double rho, irho, r, ir, a, b, h, csr;
-    double lam[4];
-};
-
-template <bool TH>
-__device__ __forceinline__ CharSys char_sys(const Band& B, double rho0, const double* U)
-{
-    CharSys C;
-    C.rho = rho0 + U[0];
-    C.irho = 1.0 / C.rho;
-    if (TH) {
-        const double th = 1.0 + U[3];
-        const double sth = sqrt(th);
-        const double isth = 1.0 / sth;
-        C.r = th * C.irho;
-        C.ir = C.rho * isth * isth;
-        C.a = sth * B.kA;
-        C.b = isth * B.kB;
-        const double c = sth * B.kB;
-        C.lam[0] = U[1];
-        C.lam[1] = U[1];
-        C.lam[2] = U[1] - c;
-        C.lam[3] = U[1] + c;
-        C.h = C.csr = 0.0;
-    } else {
-        C.h = C.rho * B.ihcs;
-        C.csr = B.cs * C.irho;
-        C.lam[0] = U[1] - B.cs;
-        C.lam[1] = U[1];
-        C.lam[2] = U[1] + B.cs;
-        C.lam[3] = 0.0;
-        C.r = C.ir = C.a = C.b = 0.0;
-    }
-    return C;
-}
-
-template <bool TH>
-__device__ __forceinline__ void apply_S(const CharSys& C, const double* v, double* o)
-{
-    if (TH) {
-        const double rv = 0.25 * C.r * v[0], q = 0.25 * v[3], av = C.a * v[1];
-        o[0] = -2.0 * rv + 2.0 * q;
-        o[1] = v[2];
-        o[2] = rv - av + q;
-        o[3] = rv + av + q;
-    } else {
-        const double hv = C.h * v[1];
-        o[0] = 0.5 * v[0] - hv;
-        o[1] = v[2];
-        o[2] = 0.5 * v[0] + hv;
-        o[3] = 0.0;
-    }
-}
-
-template <bool TH>
-__device__ __forceinline__ int incoming_mask(const CharSys& C)
-{
-    int m = 0;
-#pragma unroll
-    for (int i = 0; i < (TH ? 4 : 3); ++i)
-        if (C.lam[i] < 0.0) m |= 1 << i;
-    return m;
-}
-
-// dU/dt = -S^-1 Lbar (+ T + V for the CBC schemes): Lbar_i = L_i =
-// Lambda_i (S dU/dn)_i for outgoing waves (Eq. thermal_WAV); for incoming
-// waves Eq. PNR (LODI), Eq. LODI-Relax, Eq. CBC-PNR (CBC) or Eq. CBC-Relax,
-// with beta (Z - Z_inf) on the incoming acoustic waves.
-template <bool TH>
-__device__ __forceinline__ void char_rhs(const CharSys& C, const Band& B, const double* dUn,
-                                         const double* TT, const double* VV, int mask, double dP,
-                                         int scheme, double* k)
-{
-    double sd[4], st[4], sv[4], w[4];
-    apply_S<TH>(C, dUn, sd);
-    apply_S<TH>(C, TT, st);
-    apply_S<TH>(C, VV, sv);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (!TH && i == 3) { w[i] = 0.0; continue; }
-        if (!((mask >> i) & 1)) {
-            w[i] = C.lam[i] * sd[i];
-            continue;
-        }
-        const bool acoustic = TH ? (i >= 2) : (i != 1);
-        const double relaxP = acoustic ? B.beta_P * dP : 0.0;
-        if (scheme == SCH_LODI) w[i] = 0.0;
-        else if (scheme == SCH_LODI_RELAX) w[i] = B.alpha_T * (B.t_inf - st[i]) + relaxP;
-        else if (scheme == SCH_CBC) w[i] = st[i] + sv[i];
-        else w[i] = st[i] + sv[i] + B.alpha_T * (B.t_inf - st[i]) + relaxP;
-    }
-    double o[4];
-    if (TH) {
-        o[0] = (w[2] + w[3] - w[0]) * C.ir;
-        o[1] = C.b * (w[3] - w[2]);
-        o[2] = w[1];
-        o[3] = w[0] + w[2] + w[3];
-    } else {
-        o[0] = w[0] + w[2];
-        o[1] = C.csr * (w[2] - w[0]);
-        o[2] = w[1];
-        o[3] = 0.0;
-    }
-    const bool cbc = scheme == SCH_CBC || scheme == SCH_CBC_RELAX;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) k[m] = -o[m] + (cbc ? TT[m] + VV[m] : 0.0);
-}
-
-// ---------------------------------------------------------------------------
-// Viscous vectors, frozen at time t
-// ---------------------------------------------------------------------------
-
-// Mesoscopic form at x_f (Eqs. LaplaceU, LaplaceT): normal derivatives
-// one-sided into the bulk (Eq. FD-dx-bw), tangential ones central
-// (Eq. FD-dx-center) or one-sided inward next to a boundary node:
-//   V = (0, (1/rho) d_j s'_jn, (1/rho) d_j s'_jt,
-//        -div q / (rho c_s^2) + (nu / c_s^2) ((d_n u_n - d_t u_t)^2 + (d_n u_t + d_t u_n)^2)).
-template <bool TH>
-__device__ void vis_meso(const Geom& G, const double* SU, const double* SN, const UDesc& D,
-                         double cs2, double* V)
-{
-    // SU, SN: macros [.][4] and non-equilibrium moments [.][5] of time t,
-    // indexed by D.vs[]
-    const int s = D.kind;
-    const int an = s < 2 ? 0 : 1, at = 1 - an;     // axes of n and t
-    const double sn = (s == 0 || s == 2) ? -1.0 : 1.0;
-    double h[5][7];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const double* n = SN + 5LL * D.vs[k];
-        const double* u = SU + 4LL * D.vs[k];
-        const double sxx = n[0], sxy = n[1], syy = n[2];
-        h[k][0] = an == 0 ? sxx : syy;              // sigma'_nn
-        h[k][1] = sn * sxy;                         // sigma'_nt
-        h[k][2] = an == 0 ? syy : sxx;              // sigma'_tt
-        h[k][3] = sn * n[3 + an];                   // q_n
-        h[k][4] = n[3 + at];                        // q_t
-        h[k][5] = sn * u[1 + an];                   // u_n
-        h[k][6] = u[1 + at];                        // u_t
-    }
-    double dn[7], dt[7];
-#pragma unroll
-    for (int m = 0; m < 7; ++m) {
-        dn[m] = 0.5 * (3.0 * h[0][m] - 4.0 * h[1][m] + h[2][m]);
-        if (D.tmode == 0) dt[m] = 0.5 * (h[3][m] - h[4][m]);
-        else dt[m] = double(D.tmode) * 0.5 * (3.0 * h[0][m] - 4.0 * h[3][m] + h[4][m]);
-    }
-    const double irho = 1.0 / (G.rho0 + SU[4LL * D.vs[0]]);
-    V[0] = 0.0;
-    V[1] = (dn[0] + dt[1]) * irho;
-    V[2] = (dn[1] + dt[2]) * irho;
-    V[3] = 0.0;
-    if (TH) {
-        const double nu = (G.tau - 0.5) * cs2;
-        const double e1 = dn[5] - dt[6], e2 = dn[6] + dt[5];
-        V[3] = -(dn[3] + dt[4]) * irho * (1.0 / cs2) + nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
-    }
-}
-
-// "-FD" form (Sec. 4.2) at layer j from the macros of time t: 4-point
-// one-sided second derivative at j = M, 3-point central elsewhere.
-template <bool TH>
-__device__ void vis_fd(const Geom& G, const Band& B, const Ctx& X0, const UDesc& D, int u,
-                       double cs2, double* V)
-{
-    const int kind = D.kind;
-    double U[4], A[4], Bv[4], Cv[4], Tp[4], Tm[4], dnn[4], d1n[4];
-    fetch_local(X0, u, kind, 0.0, U);
-    fetch_local(X0, D.nb[1], kind, 0.0, Bv);
-    fetch_local(X0, D.nb[4], kind, 0.0, Tp);
-    fetch_local(X0, D.nb[5], kind, 0.0, Tm);
-    if (D.j == B.M) {
-        fetch_local(X0, D.nb[2], kind, 0.0, A);
-        fetch_local(X0, D.nb[3], kind, 0.0, Cv);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            dnn[m] = 2.0 * U[m] - 5.0 * Bv[m] + 4.0 * A[m] - Cv[m];
-            d1n[m] = 0.5 * (3.0 * U[m] - 4.0 * Bv[m] + A[m]);
-        }
-    } else {
-        fetch_local(X0, D.nb[0], kind, 0.0, A);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            dnn[m] = A[m] - 2.0 * U[m] + Bv[m];
-            d1n[m] = 0.5 * (A[m] - Bv[m]);
-        }
-    }
-    const double nu = (G.tau - 0.5) * cs2;
-    V[0] = 0.0;
-    V[1] = nu * (dnn[1] + (Tp[1] - 2.0 * U[1] + Tm[1]));
-    V[2] = nu * (dnn[2] + (Tp[2] - 2.0 * U[2] + Tm[2]));
-    V[3] = 0.0;
-    if (TH) {
-        const double d1t1 = 0.5 * (Tp[1] - Tm[1]), d1t2 = 0.5 * (Tp[2] - Tm[2]);
-        const double e1 = d1n[1] - d1t2, e2 = d1n[2] + d1t1;
-        V[3] = 2.0 * nu * (dnn[3] + (Tp[3] - 2.0 * U[3] + Tm[3])) + nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Right-hand side of one unknown
-// ---------------------------------------------------------------------------
-
-template <int LAT>
-__device__ void unknown_rhs(const Geom& G, const Band& B, const Ctx& X, const UDesc& D, int u,
-                            const double* V, int mask, double* k)
-{
-    using L = Lat<LAT>;
-    constexpr bool TH = L::THERMAL;
-    const int kind = D.kind;
-    const double r = B.kR;
-    double U[4], A[4], Bv[4], dUn[4];
-    fetch_local(X, u, kind, r, U);
-    if (kind >= 4) {
-        // Corner: LODI (Eq. PNR) along the outward diagonal, one-sided
-        // difference of spacing sqrt(2) through the two diagonal bulk nodes.
-        fetch_local(X, D.nb[0], kind, r, A);
-        fetch_local(X, D.nb[1], kind, r, Bv);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) dUn[m] = (3.0 * U[m] - 4.0 * A[m] + Bv[m]) * B.kC;
-        const double zero[4] = {0.0, 0.0, 0.0, 0.0};
-        const CharSys C = char_sys<TH>(B, G.rho0, U);
-        double kl[4];
-        char_rhs<TH>(C, B, dUn, zero, zero, mask, 0.0, SCH_LODI, kl);
-        to_lab(kind, r, kl, k);
-        return;
-    }
-    if (D.j == B.M) {            // Eq. FD-dx-bw at the outermost layer
-        fetch_local(X, D.nb[1], kind, r, A);
-        fetch_local(X, D.nb[2], kind, r, Bv);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) dUn[m] = 0.5 * (3.0 * U[m] - 4.0 * A[m] + Bv[m]);
-    } else {                     // Eq. FD-dx-center at inner layers
-        fetch_local(X, D.nb[0], kind, r, A);
-        fetch_local(X, D.nb[1], kind, r, Bv);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) dUn[m] = 0.5 * (A[m] - Bv[m]);
-    }
-    // transversal vector T (Sec. 3.1) from central differences along the side
-    double Up[4], Um[4];
-    fetch_local(X, D.nb[4], kind, r, Up);
-    fetch_local(X, D.nb[5], kind, r, Um);
-    const double rho0 = G.rho0, cs2 = L::CS2;
-    const CharSys C = char_sys<TH>(B, rho0, U);
-    const double ut = U[2];
-    const double d_rhout = 0.5 * ((rho0 + Up[0]) * Up[2] - (rho0 + Um[0]) * Um[2]);
-    const double d_un = 0.5 * (Up[1] - Um[1]);
-    const double d_ut = 0.5 * (Up[2] - Um[2]);
-    double TT[4], dP;
-    if (TH) {
-        // rho T - rho0 = drho + rho0 dT + drho dT
-        const double d_rhoT = 0.5 * ((Up[0] + rho0 * Up[3] + Up[0] * Up[3]) -
-                                     (Um[0] + rho0 * Um[3] + Um[0] * Um[3]));
-        const double d_Tut = 0.5 * ((1.0 + Up[3]) * Up[2] - (1.0 + Um[3]) * Um[2]);
-        TT[0] = -d_rhout;
-        TT[1] = -ut * d_un;
-        TT[2] = -cs2 * C.irho * d_rhoT - ut * d_ut;
-        TT[3] = -d_Tut;
-        dP = cs2 * (U[0] + rho0 * U[3] + U[0] * U[3]) - B.pdev[kind];
-    } else {
-        TT[0] = -d_rhout;
-        TT[1] = -ut * d_un;
-        TT[2] = -cs2 * C.irho * 0.5 * (Up[0] - Um[0]) - ut * d_ut;
-        TT[3] = 0.0;
-        dP = cs2 * U[0] - B.pdev[kind];
-    }
-    double kl[4];
-    char_rhs<TH>(C, B, dUn, TT, V, mask, dP, B.scheme[kind], kl);
-    to_lab(kind, r, kl, k);
-}
 
 // ---------------------------------------------------------------------------
 // Population writes (stage 3)
@@ -493,42 +131,6 @@ __device__ void dirichlet(const Geom& G, const Band& B, S* f, const R* Us, const
 // over the four CTAs of a cluster (four SMs): CTA r owns component / wave r
 // of every unknown of the tile, and the CTAs exchange their shares through
 // distributed shared memory between cluster barriers.
-
-// Row i of S (Sec. 3.1) applied to v: thermal rows (-r/2, 0, 0, 1/2),
-// (0, 0, 1, 0), (r/4, -a, 0, 1/4), (r/4, a, 0, 1/4); isothermal rows
-// (1/2, -h, 0), (0, 0, 1), (1/2, h, 0).
-template <bool TH>
-__device__ __forceinline__ double s_row(int i, double rr, double a, double h, const double* v)
-{
-    if (TH) {
-        const double rv = 0.25 * rr * v[0], q = 0.25 * v[3], av = a * v[1];
-        if (i == 0) return -2.0 * rv + 2.0 * q;
-        if (i == 1) return v[2];
-        if (i == 2) return rv - av + q;
-        return rv + av + q;
-    }
-    const double hv = h * v[1];
-    if (i == 0) return 0.5 * v[0] - hv;
-    if (i == 1) return v[2];
-    if (i == 2) return 0.5 * v[0] + hv;
-    return 0.0;
-}
-
-// Amplitude of wave i (Eq. thermal_WAV for outgoing waves; Eqs. PNR,
-// LODI-Relax, CBC-PNR, CBC-Relax for incoming ones).
-template <bool TH>
-__device__ __forceinline__ double wave(int i, const Band& B, int scheme, int mask, double lam,
-                                       double sd, double st, double sv, double dP)
-{
-    if (!TH && i == 3) return 0.0;
-    if (!((mask >> i) & 1)) return lam * sd;
-    const bool acoustic = TH ? (i >= 2) : (i != 1);
-    const double relaxP = acoustic ? B.beta_P * dP : 0.0;
-    if (scheme == SCH_LODI) return 0.0;
-    if (scheme == SCH_LODI_RELAX) return B.alpha_T * (B.t_inf - st) + relaxP;
-    if (scheme == SCH_CBC) return st + sv;
-    return st + sv + B.alpha_T * (B.t_inf - st) + relaxP;
-}
 
 // Share c of the mesoscopic viscous vector (see vis_meso), in arithmetic
 // type R: V1 for c = 1, V2 for c = 2; V3 is split, its conductive part for
@@ -1330,7 +932,7 @@ __global__ void __launch_bounds__(kBandThreads)
         mask = B.mask[u];
     }
     double k[4];
-    unknown_rhs<LAT>(G, B, X, D, u, V, mask, k);
+    unknown_rhs<LAT, double>(G, B, relax_of<double>(B), X, D, u, V, mask, k);
     const double* U0 = B.Ub + 4LL * u;
     double* acc = B.acc + 4LL * u;
     if (stage < 3) {

@@ -1,0 +1,406 @@
+// charsys.cuh -- the characteristic system of the boundary solver (Sec. 3):
+// frames, neighbour fetches, the decomposition and incoming-wave choice,
+// the viscous vectors and the right-hand side of one boundary unknown.
+// Used by the allocation-free boundary step and the tangent-linear step;
+// the fused band kernel (boundary.cu) has its own cluster-split form of the
+// same arithmetic.
+#pragma once
+#include "collide.cuh"
+
+#include <type_traits>
+
+namespace lbmgb {
+
+// Lab <-> local frame.  Sides: n the outward normal, t = +y (W, E) or +x
+// (S, N).  Corners: n = (sx, sy)/sqrt(2), t = n rotated by +90 degrees.
+template <typename R>
+__device__ __forceinline__ void to_local(int kind, R r, const R* U, R* Lc)
+{
+    Lc[0] = U[0];
+    Lc[3] = U[3];
+    switch (kind) {
+    case 0: Lc[1] = -U[1]; Lc[2] = U[2]; break;
+    case 1: Lc[1] = U[1]; Lc[2] = U[2]; break;
+    case 2: Lc[1] = -U[2]; Lc[2] = U[1]; break;
+    case 3: Lc[1] = U[2]; Lc[2] = U[1]; break;
+    default: {
+        const int c = kind - 4;
+        const R n0 = (c & 1) ? r : -r, n1 = (c & 2) ? r : -r;
+        Lc[1] = U[1] * n0 + U[2] * n1;
+        Lc[2] = -U[1] * n1 + U[2] * n0;
+    }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void to_lab(int kind, R r, const R* Lc, R* U)
+{
+    U[0] = Lc[0];
+    U[3] = Lc[3];
+    switch (kind) {
+    case 0: U[1] = -Lc[1]; U[2] = Lc[2]; break;
+    case 1: U[1] = Lc[1]; U[2] = Lc[2]; break;
+    case 2: U[2] = -Lc[1]; U[1] = Lc[2]; break;
+    case 3: U[2] = Lc[1]; U[1] = Lc[2]; break;
+    default: {
+        const int c = kind - 4;
+        const R n0 = (c & 1) ? r : -r, n1 = (c & 2) ? r : -r;
+        U[1] = Lc[1] * n0 - Lc[2] * n1;
+        U[2] = Lc[1] * n1 + Lc[2] * n0;
+    }
+    }
+}
+
+// Where a right-hand side reads its neighbours, in arithmetic type R.
+template <typename R>
+struct CtxT {
+    const R* Y;     // stage values of the unknowns
+    const R* St;    // strip macros at t
+    const R* St1;   // strip macros at t + 1
+    R frac;         // stage time fraction in [0, 1]
+};
+using Ctx = CtxT<double>;
+
+template <typename R>
+__device__ __forceinline__ void fetch(const CtxT<R>& X, int ref, R* U)
+{
+    if (ref >= 0) {
+        if constexpr (std::is_same<R, double>::value) {
+            const double2* p = reinterpret_cast<const double2*>(X.Y + 4LL * ref);
+            const double2 a = p[0], b = p[1];
+            U[0] = a.x; U[1] = a.y; U[2] = b.x; U[3] = b.y;
+        } else if constexpr (std::is_same<R, float>::value) {
+            const float4 a = *reinterpret_cast<const float4*>(X.Y + 4LL * ref);
+            U[0] = a.x; U[1] = a.y; U[2] = a.z; U[3] = a.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) U[c] = X.Y[4LL * ref + c];
+        }
+    } else {
+        const long long s = 4LL * (-ref - 1);
+        const R w0 = R(1) - X.frac, w1 = X.frac;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) U[c] = w0 * X.St[s + c] + w1 * X.St1[s + c];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void fetch_local(const CtxT<R>& X, int ref, int kind, R r, R* Lc)
+{
+    R U[4];
+    fetch(X, ref, U);
+    to_local(kind, r, U, Lc);
+}
+
+// ---------------------------------------------------------------------------
+// Characteristic system in the local frame (Sec. 3.1)
+// ---------------------------------------------------------------------------
+// Thermal, U = (drho, u_n, u_t, dT), theta = 1 + dT, T~ = c_s^2 theta:
+//   S rows: (-r/2, 0, 0, 1/2), (0, 0, 1, 0), (r/4, -a, 0, 1/4), (r/4, a, 0, 1/4)
+//   S^-1 rows: (-1/r, 0, 1/r, 1/r), (0, 0, -b, b), (0, 1, 0, 0), (1, 0, 1, 1)
+//   with r = T~/(rho c_s^2) = theta/rho, a = sqrt(T~/(8 c_s^4)),
+//   b = sqrt(2 c_s^4 / T~) and Lambda = (u_n, u_n, u_n - c, u_n + c),
+//   c = sqrt(2 T~).
+// Isothermal D2Q9, U = (drho, u_n, u_t):
+//   S rows: (1/2, -h, 0), (0, 0, 1), (1/2, h, 0) with h = rho/(2 c_s),
+//   S^-1 rows: (1, 0, 1), (-c_s/rho, 0, c_s/rho), (0, 1, 0),
+//   Lambda = (u_n - c_s, u_n, u_n + c_s).
+// Everything below is templated on the arithmetic type T (double, or a
+// Dual number for the tangent-linear step).
+template <typename T>
+struct CharSys {
+    T rho, irho, r, ir, a, b, h, csr;
+    T lam[4];
+};
+
+// The relaxation parameters of the incoming waves (Eqs. LODI-Relax,
+// CBC-Relax): alpha_T on the transversal terms, beta_P on P - P_inf,
+// the target transversal term t_inf, and P_inf - c_s^2 rho0 per side.
+template <typename T>
+struct Relax {
+    T alpha_T, beta_P, t_inf;
+    T pdev[4];
+};
+
+template <typename T>
+__device__ __forceinline__ Relax<T> relax_of(const Band& B)
+{
+    Relax<T> P;
+    P.alpha_T = T(B.alpha_T);
+    P.beta_P = T(B.beta_P);
+    P.t_inf = T(B.t_inf);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) P.pdev[s] = T(B.pdev[s]);
+    return P;
+}
+
+template <bool TH, typename T>
+__device__ __forceinline__ CharSys<T> char_sys(const Band& B, double rho0, const T* U)
+{
+    CharSys<T> C;
+    C.rho = T(rho0) + U[0];
+    C.irho = T(1) / C.rho;
+    if (TH) {
+        const T th = T(1) + U[3];
+        const T sth = sqrt(th);
+        const T isth = T(1) / sth;
+        C.r = th * C.irho;
+        C.ir = C.rho * isth * isth;
+        C.a = sth * T(B.kA);
+        C.b = isth * T(B.kB);
+        const T c = sth * T(B.kB);
+        C.lam[0] = U[1];
+        C.lam[1] = U[1];
+        C.lam[2] = U[1] - c;
+        C.lam[3] = U[1] + c;
+        C.h = C.csr = T(0);
+    } else {
+        C.h = C.rho * T(B.ihcs);
+        C.csr = T(B.cs) * C.irho;
+        C.lam[0] = U[1] - T(B.cs);
+        C.lam[1] = U[1];
+        C.lam[2] = U[1] + T(B.cs);
+        C.lam[3] = T(0);
+        C.r = C.ir = C.a = C.b = T(0);
+    }
+    return C;
+}
+
+template <bool TH, typename T>
+__device__ __forceinline__ void apply_S(const CharSys<T>& C, const T* v, T* o)
+{
+    if (TH) {
+        const T rv = T(0.25) * C.r * v[0], q = T(0.25) * v[3], av = C.a * v[1];
+        o[0] = T(-2) * rv + T(2) * q;
+        o[1] = v[2];
+        o[2] = rv - av + q;
+        o[3] = rv + av + q;
+    } else {
+        const T hv = C.h * v[1];
+        o[0] = T(0.5) * v[0] - hv;
+        o[1] = v[2];
+        o[2] = T(0.5) * v[0] + hv;
+        o[3] = T(0);
+    }
+}
+
+template <bool TH, typename T>
+__device__ __forceinline__ int incoming_mask(const CharSys<T>& C)
+{
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < (TH ? 4 : 3); ++i)
+        if (C.lam[i] < 0.0) m |= 1 << i;
+    return m;
+}
+
+// dU/dt = -S^-1 Lbar (+ T + V for the CBC schemes): Lbar_i = L_i =
+// Lambda_i (S dU/dn)_i for outgoing waves (Eq. thermal_WAV); for incoming
+// waves Eq. PNR (LODI), Eq. LODI-Relax, Eq. CBC-PNR (CBC) or Eq. CBC-Relax,
+// with beta (Z - Z_inf) on the incoming acoustic waves.
+template <bool TH, typename T>
+__device__ __forceinline__ void char_rhs(const CharSys<T>& C, const Relax<T>& P, const T* dUn,
+                                         const T* TT, const T* VV, int mask, const T& dP, int scheme,
+                                         T* k)
+{
+    T sd[4], st[4], sv[4], w[4];
+    apply_S<TH>(C, dUn, sd);
+    apply_S<TH>(C, TT, st);
+    apply_S<TH>(C, VV, sv);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (!TH && i == 3) { w[i] = T(0); continue; }
+        if (!((mask >> i) & 1)) {
+            w[i] = C.lam[i] * sd[i];
+            continue;
+        }
+        const bool acoustic = TH ? (i >= 2) : (i != 1);
+        const T relaxP = acoustic ? P.beta_P * dP : T(0);
+        if (scheme == SCH_LODI) w[i] = T(0);
+        else if (scheme == SCH_LODI_RELAX) w[i] = P.alpha_T * (P.t_inf - st[i]) + relaxP;
+        else if (scheme == SCH_CBC) w[i] = st[i] + sv[i];
+        else w[i] = st[i] + sv[i] + P.alpha_T * (P.t_inf - st[i]) + relaxP;
+    }
+    T o[4];
+    if (TH) {
+        o[0] = (w[2] + w[3] - w[0]) * C.ir;
+        o[1] = C.b * (w[3] - w[2]);
+        o[2] = w[1];
+        o[3] = w[0] + w[2] + w[3];
+    } else {
+        o[0] = w[0] + w[2];
+        o[1] = C.csr * (w[2] - w[0]);
+        o[2] = w[1];
+        o[3] = T(0);
+    }
+    const bool cbc = scheme == SCH_CBC || scheme == SCH_CBC_RELAX;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) k[m] = cbc ? -o[m] + (TT[m] + VV[m]) : -o[m];
+}
+
+// ---------------------------------------------------------------------------
+// Viscous vectors, frozen at time t
+// ---------------------------------------------------------------------------
+
+// Mesoscopic form at x_f (Eqs. LaplaceU, LaplaceT): normal derivatives
+// one-sided into the bulk (Eq. FD-dx-bw), tangential ones central
+// (Eq. FD-dx-center) or one-sided inward next to a boundary node:
+//   V = (0, (1/rho) d_j s'_jn, (1/rho) d_j s'_jt,
+//        -div q / (rho c_s^2) + (nu / c_s^2) ((d_n u_n - d_t u_t)^2 + (d_n u_t + d_t u_n)^2)).
+template <bool TH>
+__device__ void vis_meso(const Geom& G, const double* SU, const double* SN, const UDesc& D,
+                         double cs2, double* V)
+{
+    // SU, SN: macros [.][4] and non-equilibrium moments [.][5] of time t,
+    // indexed by D.vs[]
+    const int s = D.kind;
+    const int an = s < 2 ? 0 : 1, at = 1 - an;     // axes of n and t
+    const double sn = (s == 0 || s == 2) ? -1.0 : 1.0;
+    double h[5][7];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double* n = SN + 5LL * D.vs[k];
+        const double* u = SU + 4LL * D.vs[k];
+        const double sxx = n[0], sxy = n[1], syy = n[2];
+        h[k][0] = an == 0 ? sxx : syy;              // sigma'_nn
+        h[k][1] = sn * sxy;                         // sigma'_nt
+        h[k][2] = an == 0 ? syy : sxx;              // sigma'_tt
+        h[k][3] = sn * n[3 + an];                   // q_n
+        h[k][4] = n[3 + at];                        // q_t
+        h[k][5] = sn * u[1 + an];                   // u_n
+        h[k][6] = u[1 + at];                        // u_t
+    }
+    double dn[7], dt[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+        dn[m] = 0.5 * (3.0 * h[0][m] - 4.0 * h[1][m] + h[2][m]);
+        if (D.tmode == 0) dt[m] = 0.5 * (h[3][m] - h[4][m]);
+        else dt[m] = double(D.tmode) * 0.5 * (3.0 * h[0][m] - 4.0 * h[3][m] + h[4][m]);
+    }
+    const double irho = 1.0 / (G.rho0 + SU[4LL * D.vs[0]]);
+    V[0] = 0.0;
+    V[1] = (dn[0] + dt[1]) * irho;
+    V[2] = (dn[1] + dt[2]) * irho;
+    V[3] = 0.0;
+    if (TH) {
+        const double nu = (G.tau - 0.5) * cs2;
+        const double e1 = dn[5] - dt[6], e2 = dn[6] + dt[5];
+        V[3] = -(dn[3] + dt[4]) * irho * (1.0 / cs2) + nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
+    }
+}
+
+// "-FD" form (Sec. 4.2) at layer j from the macros of time t: 4-point
+// one-sided second derivative at j = M, 3-point central elsewhere.
+template <bool TH>
+__device__ void vis_fd(const Geom& G, const Band& B, const Ctx& X0, const UDesc& D, int u,
+                       double cs2, double* V)
+{
+    const int kind = D.kind;
+    double U[4], A[4], Bv[4], Cv[4], Tp[4], Tm[4], dnn[4], d1n[4];
+    fetch_local(X0, u, kind, 0.0, U);
+    fetch_local(X0, D.nb[1], kind, 0.0, Bv);
+    fetch_local(X0, D.nb[4], kind, 0.0, Tp);
+    fetch_local(X0, D.nb[5], kind, 0.0, Tm);
+    if (D.j == B.M) {
+        fetch_local(X0, D.nb[2], kind, 0.0, A);
+        fetch_local(X0, D.nb[3], kind, 0.0, Cv);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            dnn[m] = 2.0 * U[m] - 5.0 * Bv[m] + 4.0 * A[m] - Cv[m];
+            d1n[m] = 0.5 * (3.0 * U[m] - 4.0 * Bv[m] + A[m]);
+        }
+    } else {
+        fetch_local(X0, D.nb[0], kind, 0.0, A);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            dnn[m] = A[m] - 2.0 * U[m] + Bv[m];
+            d1n[m] = 0.5 * (A[m] - Bv[m]);
+        }
+    }
+    const double nu = (G.tau - 0.5) * cs2;
+    V[0] = 0.0;
+    V[1] = nu * (dnn[1] + (Tp[1] - 2.0 * U[1] + Tm[1]));
+    V[2] = nu * (dnn[2] + (Tp[2] - 2.0 * U[2] + Tm[2]));
+    V[3] = 0.0;
+    if (TH) {
+        const double d1t1 = 0.5 * (Tp[1] - Tm[1]), d1t2 = 0.5 * (Tp[2] - Tm[2]);
+        const double e1 = d1n[1] - d1t2, e2 = d1n[2] + d1t1;
+        V[3] = 2.0 * nu * (dnn[3] + (Tp[3] - 2.0 * U[3] + Tm[3])) + nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand side of one unknown
+// ---------------------------------------------------------------------------
+
+template <int LAT, typename T>
+__device__ void unknown_rhs(const Geom& G, const Band& B, const Relax<T>& P, const CtxT<T>& X,
+                            const UDesc& D, int u, const T* V, int mask, T* k)
+{
+    using L = Lat<LAT>;
+    constexpr bool TH = L::THERMAL;
+    const int kind = D.kind;
+    const T r = T(B.kR);
+    T U[4], A[4], Bv[4], dUn[4];
+    fetch_local(X, u, kind, r, U);
+    if (kind >= 4) {
+        // Corner: LODI (Eq. PNR) along the outward diagonal, one-sided
+        // difference of spacing sqrt(2) through the two diagonal bulk nodes.
+        fetch_local(X, D.nb[0], kind, r, A);
+        fetch_local(X, D.nb[1], kind, r, Bv);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) dUn[m] = (T(3) * U[m] - T(4) * A[m] + Bv[m]) * T(B.kC);
+        const T zero[4] = {T(0), T(0), T(0), T(0)};
+        const CharSys<T> C = char_sys<TH>(B, G.rho0, U);
+        T kl[4];
+        char_rhs<TH>(C, P, dUn, zero, zero, mask, T(0), SCH_LODI, kl);
+        to_lab(kind, r, kl, k);
+        return;
+    }
+    if (D.j == B.M) {            // Eq. FD-dx-bw at the outermost layer
+        fetch_local(X, D.nb[1], kind, r, A);
+        fetch_local(X, D.nb[2], kind, r, Bv);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) dUn[m] = T(0.5) * (T(3) * U[m] - T(4) * A[m] + Bv[m]);
+    } else {                     // Eq. FD-dx-center at inner layers
+        fetch_local(X, D.nb[0], kind, r, A);
+        fetch_local(X, D.nb[1], kind, r, Bv);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) dUn[m] = T(0.5) * (A[m] - Bv[m]);
+    }
+    // transversal vector T (Sec. 3.1) from central differences along the side
+    T Up[4], Um[4];
+    fetch_local(X, D.nb[4], kind, r, Up);
+    fetch_local(X, D.nb[5], kind, r, Um);
+    const T rho0 = T(G.rho0), cs2 = T(L::CS2);
+    const CharSys<T> C = char_sys<TH>(B, G.rho0, U);
+    const T ut = U[2];
+    const T d_rhout = T(0.5) * ((rho0 + Up[0]) * Up[2] - (rho0 + Um[0]) * Um[2]);
+    const T d_un = T(0.5) * (Up[1] - Um[1]);
+    const T d_ut = T(0.5) * (Up[2] - Um[2]);
+    // P_inf - c_s^2 rho0 of this side (selected, not indexed: no stack)
+    const T pdev = kind == 0 ? P.pdev[0] : kind == 1 ? P.pdev[1] : kind == 2 ? P.pdev[2] : P.pdev[3];
+    T TT[4], dP;
+    if (TH) {
+        // rho T - rho0 = drho + rho0 dT + drho dT
+        const T d_rhoT = T(0.5) * ((Up[0] + rho0 * Up[3] + Up[0] * Up[3]) -
+                                   (Um[0] + rho0 * Um[3] + Um[0] * Um[3]));
+        const T d_Tut = T(0.5) * ((T(1) + Up[3]) * Up[2] - (T(1) + Um[3]) * Um[2]);
+        TT[0] = -d_rhout;
+        TT[1] = -ut * d_un;
+        TT[2] = -cs2 * C.irho * d_rhoT - ut * d_ut;
+        TT[3] = -d_Tut;
+        dP = cs2 * (U[0] + rho0 * U[3] + U[0] * U[3]) - pdev;
+    } else {
+        TT[0] = -d_rhout;
+        TT[1] = -ut * d_un;
+        TT[2] = -cs2 * C.irho * T(0.5) * (Up[0] - Um[0]) - ut * d_ut;
+        TT[3] = T(0);
+        dP = cs2 * U[0] - pdev;
+    }
+    T kl[4];
+    char_rhs<TH>(C, P, dUn, TT, V, mask, dP, B.scheme[kind], kl);
+    to_lab(kind, r, kl, k);
+}
+
+}  // namespace lbmgb

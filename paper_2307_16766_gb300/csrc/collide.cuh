@@ -1,22 +1,25 @@
 // collide.cuh -- the per-node update shared by the bulk kernels (bulk.cu)
 // and the band kernel (boundary.cu): plain pull, moments, BGK collision.
 #pragma once
+#include "dual.cuh"
 #include "lbm_internal.cuh"
 
 namespace lbmgb {
 
+// 1/tau and rho0 in the precision of arithmetic type C (float-based types
+// take the float-rounded values).
 template <typename C>
-__device__ __forceinline__ C omega_of(const Geom& G);
-template <>
-__device__ __forceinline__ float omega_of<float>(const Geom& G) { return G.omega_f; }
-template <>
-__device__ __forceinline__ double omega_of<double>(const Geom& G) { return G.omega; }
+__device__ __forceinline__ C omega_of(const Geom& G)
+{
+    if constexpr (sizeof(typename DualTraits<C>::Value) == 4) return C(G.omega_f);
+    else return C(G.omega);
+}
 template <typename C>
-__device__ __forceinline__ C rho0_of(const Geom& G);
-template <>
-__device__ __forceinline__ float rho0_of<float>(const Geom& G) { return G.rho0_f; }
-template <>
-__device__ __forceinline__ double rho0_of<double>(const Geom& G) { return G.rho0; }
+__device__ __forceinline__ C rho0_of(const Geom& G)
+{
+    if constexpr (sizeof(typename DualTraits<C>::Value) == 4) return C(G.rho0_f);
+    else return C(G.rho0);
+}
 
 // Viscous stress sigma' = -(1 - 1/(2 tau)) sum c c (f - f^eq) (Eq. LaplaceU)
 // and heat flux q = (1 - 1/(2 tau)) 1/2 sum (f - f^eq) |c-u|^2 (c-u)
@@ -101,7 +104,7 @@ __device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Pu
     const C uxs = m.ux * ics2, uys = m.uy * ics2;
     const EqPoly<C> e = eq_poly<LAT, C>(m.ux * uxs + m.uy * uys, m.dT);
     const C om = omega_of<C>(G);
-    if (sizeof(C) == 8) {
+    if (sizeof(typename DualTraits<C>::Value) == 8) {
         {
             const C geq = C(L::w(0)) * (m.s0 + m.rho * e.A0);
             put(0, g[0] + om * (geq - g[0]));

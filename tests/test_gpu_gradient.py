@@ -1,0 +1,135 @@
+"""Gradients of the pressure loss with respect to the relaxation parameters
+(alpha_T, beta_P, P_inf) by tangent-linear steps on the GPU, against the
+FP64 oracle: its loss, and its central differences (h = 1e-4)."""
+import numpy as np
+import pytest
+
+import lbm_workloads as W
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def lbm():
+    import paper_2307_16766_gb300 as m
+    return m
+
+
+def _case(lat="D2Q37", n=32, m=24, u=(0.04, 0.03), sides=("cbc",) * 4):
+    """A pulse carried by a mean flow oblique to every side, so that no wave
+    changes between incoming and outgoing (the loss is smooth there)."""
+    cs2 = W.CS2[lat]
+    cfg = W.run(lat, n, m, 0.8, sides=sides, schemes=("cbc_relax",) * 4, viscous="off",
+                alpha_T=0.5, beta_P=0.3, p_inf=[cs2 * 1.0002] * 4)
+    f = list(W.gaussian_pulse(n, m, 1e-3, 1e-3 if lat != "D2Q9" else 0.0, 3.0,
+                              center=(n / 2 - 0.7, m / 2 - 0.4)))
+    f[1] = f[1] + u[0]
+    f[2] = f[2] + u[1]
+    return cfg, tuple(f)
+
+
+def _loss_by_steps(cfg, f, steps):
+    """The same loss from ordinary steps and the macros after each."""
+    m = lbm()
+    cs2, M = W.CS2[cfg["lattice"]], W.M_OF[cfg["lattice"]]
+    sim = m.Simulation(cfg).init_fields(*f)
+    J = 0.0
+    for _ in range(steps):
+        sim.step(1)
+        rho, ux, uy, T = sim.macros()
+        dr = rho - 1.0
+        dP = cs2 * (dr + (T - 1.0) + dr * (T - 1.0)) if cfg["lattice"] != "D2Q9" else cs2 * dr
+        ys = slice(0, cfg["ny"]) if cfg["sides"][2] == "periodic" else slice(M, cfg["ny"] - M)
+        xs = slice(0, cfg["nx"]) if cfg["sides"][0] == "periodic" else slice(M, cfg["nx"] - M)
+        J += float(np.sum(dP[ys, xs] ** 2))
+    sim.close()
+    return J
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-4)])
+def test_tangent_steps_carry_the_ordinary_step(storage, tol):
+    cfg, f = _case()
+    c = dict(cfg, storage=storage)
+    J, _ = lbm().pressure_loss_and_gradient(c, f, 60)
+    Js = _loss_by_steps(c, f, 60)
+    assert abs(J - Js) <= tol * Js, (J, Js)
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q17", "D2Q37"])
+def test_gradient_matches_oracle_central_differences(lat):
+    cfg, f = _case(lat)
+    steps = 60
+    cs2 = W.CS2[lat]
+    J, dJ = lbm().pressure_loss_and_gradient(dict(cfg, storage="f64"), f, steps)
+    Jo = oracle.pressure_loss(cfg, f, steps)
+    assert abs(J - Jo) <= 1e-10 * Jo, (J, Jo)
+    fd = oracle.pressure_loss_fd_gradient(cfg, f, steps, (1e-4, 1e-4, 1e-4 * cs2))
+    for k in range(3):
+        assert abs(dJ[k] - fd[k]) <= 1e-4 * abs(fd[k]), (k, dJ, fd)
+
+
+def test_gradient_on_periodic_sides_with_a_reference_field():
+    """Characteristic W/E sides, periodic S/N, a seeded reference pressure
+    field per step: loss and gradient against the oracle's."""
+    import torch
+    cfg, f = _case("D2Q37", 40, 20, u=(0.05, 0.0), sides=("cbc", "cbc", "periodic", "periodic"))
+    steps = 50
+    rng = np.random.default_rng(3)
+    ref = 1e-5 * rng.standard_normal((steps, 20, 40))
+    J, dJ = lbm().pressure_loss_and_gradient(dict(cfg, storage="f64"), f, steps,
+                                             torch.tensor(ref, device="cuda"))
+    Jo = oracle.pressure_loss(cfg, f, steps, ref)
+    assert abs(J - Jo) <= 1e-10 * Jo
+    fd = oracle.pressure_loss_fd_gradient(cfg, f, steps, (1e-4, 1e-4, 1e-4 * W.CS2["D2Q37"]), ref)
+    for k in range(3):
+        assert abs(dJ[k] - fd[k]) <= 1e-4 * abs(fd[k]), (k, dJ, fd)
+
+
+def test_fp32_gradient_against_fp64(capsys):
+    cfg, f = _case()
+    _, g64 = lbm().pressure_loss_and_gradient(dict(cfg, storage="f64"), f, 60)
+    _, g32 = lbm().pressure_loss_and_gradient(dict(cfg, storage="f32"), f, 60)
+    rel = [abs(a - b) / abs(b) for a, b in zip(g32, g64)]
+    with capsys.disabled():
+        print("\nFP32 storage gradient vs FP64, rel. errors (alpha_T, beta_P, P_inf):",
+              ["%.1e" % r for r in rel])
+    assert max(rel) < 1e-2
+
+
+def test_autograd_function_returns_the_tangent_gradient():
+    import torch
+    m = lbm()
+    cfg, f = _case()
+    cs2 = W.CS2["D2Q37"]
+    theta = torch.tensor([0.5, 0.3, cs2 * 1.0002], dtype=torch.float64, requires_grad=True)
+    J = m.cbc_loss(theta, dict(cfg, storage="f64"), f, 40)
+    J.backward()
+    Jr, dJ = m.pressure_loss_and_gradient(dict(cfg, storage="f64"), f, 40)
+    assert abs(J.item() - Jr) <= 1e-14 * Jr
+    assert np.allclose(theta.grad.numpy(), dJ, rtol=1e-14, atol=0.0)
+
+
+def test_gradient_steps_are_checked_and_fence_ordinary_steps():
+    m = lbm()
+    cfg, f = _case()
+    sim = m.Simulation(dict(cfg, storage="f64", viscous="meso")).init_fields(*f)
+    with pytest.raises(m.LbmError, match="viscous"):
+        m.lbm_grad_begin(sim.handle)
+    sim.close()
+    sim = m.Simulation(dict(cfg, storage="f16")).init_fields(*f)
+    with pytest.raises(m.LbmError, match="storage"):
+        m.lbm_grad_begin(sim.handle)
+    sim.close()
+    sim = m.Simulation(dict(cfg, storage="f64")).init_fields(*f)
+    with pytest.raises(m.LbmError):
+        m.lbm_grad_step(sim.handle, 1)          # before lbm_grad_begin
+    m.lbm_grad_begin(sim.handle)
+    m.lbm_grad_step(sim.handle, 3)
+    m.lbm_grad_end(sim.handle)
+    with pytest.raises(m.LbmError, match="lbm_init_fields"):
+        sim.step(1)
+    rho, _, _, _ = sim.macros()                  # the populations the gradient steps made
+    assert np.all(np.isfinite(rho)) and sim.steps_done == 3
+    sim.init_fields(*f)
+    sim.step(1)
+    sim.close()
