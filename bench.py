@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch-leg", action="store_true")
+    ap.add_argument("--no-gradient-leg", action="store_true")
+    ap.add_argument("--gradient-steps", type=int, default=1500)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--batch-steps", type=int, default=1000)
     return ap.parse_args()
@@ -354,6 +356,63 @@ def run_batch(args, local_rank):
                         "Gaussian pulses, FP32 storage"}
 
 
+def run_gradient(args, local_rank):
+    """Gradient of the pressure loss against a larger periodic reference
+    with respect to (alpha_T, beta_P, P_inf) on the D2Q37 512x256 FP32
+    pulse: --gradient-steps tangent-linear steps timed with CUDA events,
+    beside the same number of ordinary steps of the same grid (both
+    L2-resident at this size, so neither is flushed)."""
+    import torch
+    import paper_2307_16766_gb300 as lbm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    K = args.gradient_steps
+    cfg, f, rcfg, rf, (x0, y0) = W.gradient_pulse(steps=K)
+    nx, ny = cfg["nx"], cfg["ny"]
+    cs2 = W.CS2["D2Q37"]
+    # reference pressure of the interior crop, every step
+    ref = lbm.Simulation(rcfg, device=dev).init_fields(*rf)
+    dP = torch.empty((K, ny, nx), dtype=torch.float64, device=dev)
+    for k in range(K):
+        ref.step(1)
+        rho, _, _, T = ref.macros(device=True)
+        dr = rho[y0:y0 + ny, x0:x0 + nx] - 1.0
+        dT = T[y0:y0 + ny, x0:x0 + nx] - 1.0
+        dP[k] = cs2 * (dr + dT + dr * dT)
+    ref.close()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # ordinary steps
+    sim = lbm.Simulation(cfg, device=dev).init_fields(*f)
+    sim.step(5)
+    torch.cuda.synchronize(dev)
+    e0.record(sim.stream)
+    sim.step(K)
+    e1.record(sim.stream)
+    torch.cuda.synchronize(dev)
+    fwd_s = e0.elapsed_time(e1) / 1e3
+    # tangent-linear steps from the initial state
+    sim.init_fields(*f)
+    lbm.lbm_grad_begin(sim.handle)
+    torch.cuda.synchronize(dev)
+    e0.record(sim.stream)
+    lbm.lbm_grad_step(sim.handle, K, dP.data_ptr(), ny * nx)
+    e1.record(sim.stream)
+    torch.cuda.synchronize(dev)
+    grad_s = e0.elapsed_time(e1) / 1e3
+    J, dJ = lbm.lbm_grad_result(sim.handle)
+    lbm.lbm_grad_end(sim.handle)
+    sim.close()
+    return {"value": grad_s / fwd_s, "unit": "gradient step time / forward step time",
+            "steps": K, "gradient_ms_per_step": grad_s / K * 1e3, "forward_ms_per_step": fwd_s / K * 1e3,
+            "J": J, "dJ": {"alpha_T": dJ[0], "beta_P": dJ[1], "P_inf": dJ[2]},
+            "mode": "forward (tangent-linear, 3 directions), no checkpoints",
+            "gpu_launches_per_step": 8,
+            "workload": "D2Q37 %dx%d FP32 rho+T Gaussian pulse, CBC-RELAX on four sides, viscous off, "
+                        "alpha_T = beta_P = 0.5, P_inf = c_s^2 rho0; loss against the centre crop of a "
+                        "%dx%d periodic run, every step" % (nx, ny, rcfg["nx"], rcfg["ny"])}
+
+
 def max_over_ranks(seconds, world):
     """The slowest rank's timed-region length (replicas run in lock step
     between the barriers; the job is as fast as its slowest GPU)."""
@@ -436,6 +495,9 @@ def main():
     batch = None
     if not args.no_batch_leg and args.storage == "f32":
         batch = run_batch(args, local_rank)
+    gradient = None
+    if not args.no_gradient_leg and args.storage == "f32":
+        gradient = run_gradient(args, local_rank)
 
     K = args.steps
     nodes = args.nx * args.ny
@@ -477,6 +539,8 @@ def main():
                             "interior_GBps": 2 * Q * 8 * fp64["interior_nodes"] / (fp64["interior_ms_mean"] / 1e3) / 1e9}
         if batch is not None:
             line["batch"] = batch
+        if gradient is not None:
+            line["gradient"] = gradient
         if not args.no_cpu_baseline and world == 1:
             cfg, fields = workload(args.nx, args.ny, "f64", 1)
             line["cpu_baseline"] = cpu_baseline(cfg, fields)

@@ -220,3 +220,23 @@ def sweep_batch(n_runs=96, seed=4, steps=1000, storage="f32", lo=128, hi=512, vi
                            center=((nx - 1) / 2.0 + ox, (ny - 1) / 2.0 + oy))
         out.append((cfg, f))
     return out
+
+
+def gradient_pulse(nx=512, ny=256, steps=1500, storage="f32", ref_scale=4, alpha_T=0.5, beta_P=0.5,
+                   tau=0.8, width=8.0):
+    """Relaxation-parameter gradient workload: D2Q37 nx x ny, a combined
+    rho/T Gaussian pulse (a = 1e-3, width 8) at the centre, CBC-RELAX on
+    four sides without the viscous vector, P_inf = c_s^2 rho0; and its
+    reference, the same pulse at the centre of a periodic grid ref_scale
+    times larger per axis.  Returns (cfg, fields, ref_cfg, ref_fields,
+    (x0, y0)) with (x0, y0) the crop origin in the reference grid."""
+    cfg = run("D2Q37", nx, ny, tau, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4, viscous="off",
+              alpha_T=alpha_T, beta_P=beta_P, storage=storage, steps=steps,
+              name="D2Q37 %dx%d rho+T pulse, CBC-RELAX, gradient workload" % (nx, ny))
+    f = gaussian_pulse(nx, ny, 1e-3, 1e-3, width)
+    rx, ry = nx * ref_scale, ny * ref_scale
+    x0, y0 = (rx - nx) // 2, (ry - ny) // 2
+    ref_cfg = run("D2Q37", rx, ry, tau, storage=storage, steps=steps,
+                  name="D2Q37 %dx%d periodic reference" % (rx, ry))
+    ref_f = gaussian_pulse(rx, ry, 1e-3, 1e-3, width, center=(x0 + (nx - 1) / 2.0, y0 + (ny - 1) / 2.0))
+    return cfg, f, ref_cfg, ref_f, (x0, y0)

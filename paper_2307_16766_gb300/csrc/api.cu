@@ -1136,7 +1136,8 @@ int lbm_grad_begin(lbm_handle* h)
     size_t o = 0;
     auto take = [&](size_t b) { const size_t at = o; o = align_up(o + b); return at; };
     const size_t o_t0 = take(tbytes), o_t1 = take(tbytes), o_st = take(sbytes), o_st1 = take(sbytes),
-                 o_ud = take(ubytes), o_ya = take(ubytes), o_yb = take(ubytes), o_acc = take(ubytes),
+                 o_ud = take(ubytes), o_uf = take(ubytes), o_ya = take(ubytes), o_yb = take(ubytes),
+                 o_acc = take(ubytes),
                  o_mask = take((size_t)std::max(1, h->B.n_unk) * sizeof(int)), o_sums = take(4 * sizeof(double));
     void* mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, o);
@@ -1147,6 +1148,7 @@ int lbm_grad_begin(lbm_handle* h)
     T.St = at<char>(mem, o_st);
     T.St1 = at<char>(mem, o_st1);
     T.Ud = at<char>(mem, o_ud);
+    T.Uf = at<char>(mem, o_uf);
     T.Ya = at<char>(mem, o_ya);
     T.Yb = at<char>(mem, o_yb);
     T.acc = at<char>(mem, o_acc);
@@ -1156,7 +1158,7 @@ int lbm_grad_begin(lbm_handle* h)
     // the initial fields do not depend on the parameters: zero derivatives
     e = cudaMemsetAsync(mem, 0, o, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "gradient state");
-    if (launch_tl_seed(T, h->B, int(h->steps & 1), false, h->stream))
+    if (launch_tl_seed(T, h->B, h->storage, int(h->steps & 1), h->stream))
         return check_launch(h, -1, "gradient seed kernel");
     h->grad_stale = true;
     return LBM_OK;
@@ -1166,15 +1168,10 @@ int lbm_grad_step(lbm_handle* h, int n, const double* dP_ref, long long ref_stri
 {
     if (!h || n < 0) return LBM_ERR_ARG;
     if (!h->tl_mem) { h->err = "lbm_grad_step before lbm_grad_begin"; return LBM_ERR_STATE; }
-    Region loss;
-    loss.x0 = h->G.perx ? 0 : h->M;
-    loss.x1 = h->G.perx ? h->nx : h->nx - h->M;
-    loss.y0 = h->G.pery ? 0 : h->M;
-    loss.y1 = h->G.pery ? h->ny : h->ny - h->M;
     for (int i = 0; i < n; ++i) {
         const int par = int(h->steps & 1);
         const double* ref = dP_ref ? dP_ref + (long long)i * ref_stride : nullptr;
-        if (launch_tl_step(h->lattice, h->storage, h->tl, h->G, h->E, h->B, h->bulk, loss, h->f, par, ref,
+        if (launch_tl_step(h->lattice, h->storage, h->tl, h->G, h->E, h->B, h->bulk, h->f, par, ref,
                            h->stream))
             return check_launch(h, -1, "tangent-linear step");
         h->steps++;

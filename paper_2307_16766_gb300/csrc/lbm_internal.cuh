@@ -631,27 +631,29 @@ int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad);
 int launch_zg(int lat, int storage, const Geom& G, const Band& B, void* fnew, cudaStream_t st);
 
 // State of the tangent-linear step (tangent.cu): derivatives along three
-// directions (alpha_T, beta_P, P_inf).  Dual values are Dual<double, 3>
-// (tl_dual_bytes() each).
+// directions (alpha_T, beta_P, P_inf).  Dual values take tl_dual_bytes()
+// each (the FP64 state type; the stage type is no larger).
 struct TLState {
     void* t[2];      // derivative populations per parity: [3][Q][plane], storage type
-    void* St;        // strip macros at t: [nslots][4] Dual
-    void* St1;       // strip macros at t + 1: [nslots][4] Dual
-    void* Ud;        // boundary state: [n_unk][4] Dual
-    void *Ya, *Yb, *acc;   // RK4 stage values and sum: [n_unk][4] Dual
+    void* St;        // strip macros at t: [nslots][4], stage type
+    void* St1;       // strip macros at t + 1: [nslots][4], stage type
+    void* Ud;        // boundary state: [n_unk][4], FP64 Dual
+    void* Uf;        // the same in the stage type
+    void *Ya, *Yb;   // RK4 stage values: [n_unk][4], stage type
+    void* acc;       // RK4 sum: [n_unk][4], FP64 Dual
     int* mask;       // incoming waves at t: [n_unk]
     double* sums;    // J, dJ/dalpha_T, dJ/dbeta_P, dJ/dP_inf
 };
 size_t tl_dual_bytes();
 // One tangent-linear step f[par] -> f[par ^ 1] (FP64 or FP32 storage; the
 // handle's checks exclude the viscous vector, NEEP and inflow / zero-gradient
-// sides), adding the loss over region `loss` against dPref ([ny][nx] of
-// P_ref - c_s^2 rho0, or null for 0) to T.sums.
+// sides), adding the loss over the bulk nodes (the nodes off the boundary
+// layers) against dPref ([ny][nx] of P_ref - c_s^2 rho0, or null for 0) to
+// T.sums.
 int launch_tl_step(int lat, int storage, const TLState& T, const Geom& G, const Export& E,
-                   const Band& B, const Region& bulk, const Region& loss, void* const f[2], int par,
-                   const double* dPref, cudaStream_t st);
-// Boundary state parity par <-> T.Ud (back = false: seed with zero
-// derivatives; true: write the values back).
-int launch_tl_seed(const TLState& T, const Band& B, int par, bool back, cudaStream_t st);
+                   const Band& B, const Region& bulk, void* const f[2], int par, const double* dPref,
+                   cudaStream_t st);
+// Seed T.Ud / T.Uf with the boundary state of parity par, zero derivatives.
+int launch_tl_seed(const TLState& T, const Band& B, int storage, int par, cudaStream_t st);
 
 }  // namespace lbmgb

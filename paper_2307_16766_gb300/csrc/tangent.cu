@@ -8,12 +8,13 @@
 //   k_tl_strip     macros of the strip nodes at t (their populations) and
 //                  at t + 1 (pulled, Eq. lbe), value and derivatives
 //   k_tl_stage     one RK4 stage of every boundary unknown (Sec. 3.3),
-//                  right-hand side from charsys.cuh on Dual<double, 3>
+//                  right-hand side from charsys.cuh on Dual numbers of the
+//                  storage's arithmetic, state and RK4 sum in FP64
 //   k_tl_dirichlet f^eq of the new boundary state on the band nodes
-//   k_tl_bulk      pull-stream + BGK collide of every bulk node on
-//                  Dual<C, 3> (C the storage's arithmetic type)
-//   k_tl_loss      J += sum over the loss region of (P - P_ref)^2 and its
-//                  derivatives, P - c_s^2 rho0 = c_s^2 (drho + rho0 dT + drho dT)
+//   k_tl_bulk      pull-stream + BGK collide of every bulk node, one
+//                  derivative direction at a time, and the loss of the node:
+//                  J += (P - P_ref)^2 and its derivatives,
+//                  P - c_s^2 rho0 = c_s^2 (drho + rho0 dT + drho dT)
 //
 // Supported: FP64 and FP32 storage, equilibrium Dirichlet condition, no
 // viscous vector, characteristic and periodic sides (checked on the host).
@@ -24,15 +25,19 @@ namespace lbmgb {
 namespace {
 
 constexpr int kTD = 3;                      // derivative directions
-using TD = Dual<double, kTD>;               // boundary solver type
+using TS = Dual<double, kTD>;               // boundary state and RK4 sum
+// arithmetic of the strips, stage values and right-hand sides: the
+// storage's (FP32 inputs around an FP64 state with FP32 storage)
+template <typename S>
+using TB = Dual<typename Store<S>::C, kTD>;
 
-template <typename C>
-__device__ __forceinline__ TD to_td(const C& a)
+template <typename To, typename From>
+__device__ __forceinline__ To dcast(const From& a)
 {
-    TD r;
-    r.v = double(a.v);
+    To r;
+    r.v = decltype(r.v)(a.v);
 #pragma unroll
-    for (int k = 0; k < kTD; ++k) r.d[k] = double(a.d[k]);
+    for (int k = 0; k < kTD; ++k) r.d[k] = decltype(r.v)(a.d[k]);
     return r;
 }
 
@@ -51,7 +56,18 @@ __device__ __forceinline__ void load_node(const Geom& G, const S* f, const S* t,
     }
 }
 
-// Pull (Eq. lbe) of node (x, y) as Dual numbers, periodic wrap-around.
+// Source offset of velocity i's pull (Eq. lbe) at node (x, y), periodic
+// wrap-around.
+template <int LAT>
+__device__ __forceinline__ long long pull_src(const Geom& G, int i, int x, int y)
+{
+    using L = Lat<LAT>;
+    int xs = x - L::cx(i), ys = y - L::cy(i);
+    if (L::cx(i) && G.perx) xs = xs < 0 ? xs + G.nx : (xs >= G.nx ? xs - G.nx : xs);
+    if (L::cy(i) && G.pery) ys = ys < 0 ? ys + G.ny : (ys >= G.ny ? ys - G.ny : ys);
+    return (long long)L::plane_of(i) * G.plane + (long long)ys * G.nxp + xs;
+}
+
 template <int LAT, typename S, typename C>
 __device__ __forceinline__ void pull_node(const Geom& G, const S* f, const S* t, int x, int y, C* g)
 {
@@ -59,10 +75,7 @@ __device__ __forceinline__ void pull_node(const Geom& G, const S* f, const S* t,
     const long long dstride = (long long)L::Q * G.plane;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        int xs = x - L::cx(i), ys = y - L::cy(i);
-        if (L::cx(i) && G.perx) xs = xs < 0 ? xs + G.nx : (xs >= G.nx ? xs - G.nx : xs);
-        if (L::cy(i) && G.pery) ys = ys < 0 ? ys + G.ny : (ys >= G.ny ? ys - G.ny : ys);
-        const long long o = (long long)L::plane_of(i) * G.plane + (long long)ys * G.nxp + xs;
+        const long long o = pull_src<LAT>(G, i, x, y);
         g[i].v = f[o];
 #pragma unroll
         for (int k = 0; k < kTD; ++k) g[i].d[k] = t[k * dstride + o];
@@ -91,95 +104,103 @@ __device__ __forceinline__ bool slot_node(const Geom& G, const Export& E, int q,
 
 template <int LAT, typename S>
 __global__ void k_tl_strip(Geom G, Export E, const S* __restrict__ f, const S* __restrict__ t,
-                           TD* __restrict__ St, TD* __restrict__ St1)
+                           TB<S>* __restrict__ St, TB<S>* __restrict__ St1)
 {
     using L = Lat<LAT>;
-    using C = Dual<typename Store<S>::C, kTD>;
+    using C = TB<S>;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= E.nslots) return;
     int x = 0, y = 0;
-    TD* a = St + 4LL * q;
-    TD* b = St1 + 4LL * q;
+    C* a = St + 4LL * q;
+    C* b = St1 + 4LL * q;
     if (!slot_node(G, E, q, x, y)) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) a[c] = b[c] = TD(0);
+        for (int c = 0; c < 4; ++c) a[c] = b[c] = C(0);
         return;
     }
     C g[L::Q];
     // time t: the stored (post-collision) populations carry the macros of t
     load_node<LAT, S, C>(G, f, t, (long long)y * G.nxp + x, g);
     Moments<LAT, C> m = moments<LAT, C>(g, rho0_of<C>(G));
-    a[0] = to_td(m.s0); a[1] = to_td(m.ux); a[2] = to_td(m.uy); a[3] = to_td(m.dT);
+    a[0] = m.s0; a[1] = m.ux; a[2] = m.uy; a[3] = m.dT;
     // time t + 1: pulled
     pull_node<LAT, S, C>(G, f, t, x, y, g);
     m = moments<LAT, C>(g, rho0_of<C>(G));
-    b[0] = to_td(m.s0); b[1] = to_td(m.ux); b[2] = to_td(m.uy); b[3] = to_td(m.dT);
+    b[0] = m.s0; b[1] = m.ux; b[2] = m.uy; b[3] = m.dT;
 }
 
-// One RK4 stage of every boundary unknown: Y (stage values), acc (sum of
-// k), U (state, updated in place at stage 3), mask (incoming waves at t).
-template <int LAT>
-__global__ void k_tl_stage(Geom G, Band B, Relax<TD> P, const TD* __restrict__ St,
-                           const TD* __restrict__ St1, TD* Ud, TD* Ya, TD* Yb, TD* acc, int* mask,
-                           int stage)
+// One RK4 stage of every boundary unknown.  Ud, acc: state and sum of k
+// (FP64); Uf: the state in the stage type, for the neighbours' stencils;
+// Ya, Yb: stage values; mask: incoming waves at t.
+template <int LAT, typename S>
+__global__ void k_tl_stage(Geom G, Band B, Relax<TB<S>> P, const TB<S>* __restrict__ St,
+                           const TB<S>* __restrict__ St1, TS* Ud, TB<S>* Uf, TB<S>* Ya, TB<S>* Yb,
+                           TS* acc, int* mask, int stage)
 {
     using Lt = Lat<LAT>;
+    using T = TB<S>;
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= B.n_unk) return;
     const UDesc D = B.ud[u];
-    CtxT<TD> X;
-    X.Y = stage == 0 ? Ud : (stage == 2 ? Yb : Ya);
+    CtxT<T> X;
+    X.Y = stage == 0 ? Uf : (stage == 2 ? Yb : Ya);
     X.St = St;
     X.St1 = St1;
-    X.frac = stage == 0 ? TD(0) : (stage == 3 ? TD(1) : TD(0.5));
-    TD* Yout = stage == 1 ? Yb : Ya;
-    const TD V[4] = {TD(0), TD(0), TD(0), TD(0)};
+    X.frac = stage == 0 ? T(0) : (stage == 3 ? T(1) : T(0.5));
+    T* Yout = stage == 1 ? Yb : Ya;
+    const T V[4] = {T(0), T(0), T(0), T(0)};
     int mk;
     if (stage == 0) {
-        TD Ul[4];
-        to_local(D.kind, TD(B.kR), Ud + 4LL * u, Ul);
+        T Ul[4];
+        to_local(D.kind, T(B.kR), Uf + 4LL * u, Ul);
         mk = incoming_mask<Lt::THERMAL>(char_sys<Lt::THERMAL>(B, G.rho0, Ul));
         mask[u] = mk;
     } else {
         mk = mask[u];
     }
-    TD k[4];
-    unknown_rhs<LAT, TD>(G, B, P, X, D, u, V, mk, k);
-    TD* U0 = Ud + 4LL * u;
-    TD* ac = acc + 4LL * u;
+    T k[4];
+    unknown_rhs<LAT, T>(G, B, P, X, D, u, V, mk, k);
+    TS* U0 = Ud + 4LL * u;
+    TS* ac = acc + 4LL * u;
     if (stage < 3) {
         const double wk = stage == 0 ? 1.0 : 2.0;
         const double hk = stage == 2 ? 1.0 : 0.5;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            ac[m] = (stage == 0 ? TD(0) : ac[m]) + TD(wk) * k[m];
-            Yout[4LL * u + m] = U0[m] + TD(hk) * k[m];
+            const TS km = dcast<TS>(k[m]);
+            ac[m] = (stage == 0 ? TS(0) : ac[m]) + TS(wk) * km;
+            Yout[4LL * u + m] = dcast<T>(U0[m] + TS(hk) * km);
         }
         return;
     }
 #pragma unroll
-    for (int m = 0; m < 4; ++m) U0[m] = U0[m] + (ac[m] + k[m]) * TD(1.0 / 6.0);
+    for (int m = 0; m < 4; ++m) {
+        U0[m] = U0[m] + (ac[m] + dcast<TS>(k[m])) * TS(1.0 / 6.0);
+        Uf[4LL * u + m] = dcast<T>(U0[m]);
+    }
 }
 
 // Equilibrium Dirichlet condition: f^eq(U_b(t + 1)) on the unknown's band
-// node (corner: its M x M block), value and derivatives.
+// node (corner: its M x M block), value and derivatives, in the storage's
+// arithmetic.
 template <int LAT, typename S>
-__global__ void k_tl_dirichlet(Geom G, Band B, const TD* __restrict__ Ud, S* __restrict__ f,
+__global__ void k_tl_dirichlet(Geom G, Band B, const TS* __restrict__ Ud, S* __restrict__ f,
                                S* __restrict__ t)
 {
     using L = Lat<LAT>;
+    using C = TB<S>;
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= B.n_unk) return;
     const UDesc D = B.ud[u];
-    const TD* U = Ud + 4LL * u;
-    Moments<LAT, TD> m;
-    m.s0 = U[0];
-    m.rho = TD(G.rho0) + U[0];
-    m.ux = U[1];
-    m.uy = U[2];
-    m.dT = L::THERMAL ? U[3] : TD(0);
-    TD ge[L::Q];
-    equilibrium<LAT, TD>(m, ge);
+    const TS* U = Ud + 4LL * u;
+    Moments<LAT, C> m;
+    m.s0 = dcast<C>(U[0]);
+    m.rho = rho0_of<C>(G) + m.s0;
+    m.ux = dcast<C>(U[1]);
+    m.uy = dcast<C>(U[2]);
+    m.dT = L::THERMAL ? dcast<C>(U[3]) : C(0);
+    C ge[L::Q];
+    equilibrium<LAT, C>(m, ge);
     const long long dstride = (long long)L::Q * G.plane;
     const int nb = D.kind >= 4 ? G.M : 1;
     for (int a = 0; a < nb; ++a)
@@ -195,55 +216,59 @@ __global__ void k_tl_dirichlet(Geom G, Band B, const TD* __restrict__ Ud, S* __r
         }
 }
 
+// Pull-stream + BGK collide of every bulk node, one derivative direction
+// at a time (Dual<C, 1>: the three passes share the pulled values), and the
+// loss of the node: the bulk nodes are the nodes off the boundary layers,
+// and the collision keeps the macros, so the pulled populations' moments
+// give P at t + 1.
 template <int LAT, typename S>
 __global__ void __launch_bounds__(128) k_tl_bulk(Geom G, Region R, const S* __restrict__ f,
                                                  const S* __restrict__ t, S* __restrict__ fo,
-                                                 S* __restrict__ to)
+                                                 S* __restrict__ to, const double* __restrict__ dPref,
+                                                 double* sums)
 {
     using L = Lat<LAT>;
-    using C = Dual<typename Store<S>::C, kTD>;
+    using CV = typename Store<S>::C;
+    using C1 = Dual<CV, 1>;
     const int x = R.x0 + blockIdx.x * blockDim.x + threadIdx.x;
     const int y = R.y0 + blockIdx.y;
-    if (x >= R.x1) return;
-    C g[L::Q];
-    pull_node<LAT, S, C>(G, f, t, x, y, g);
-    const long long node = (long long)y * G.nxp + x;
-    const long long dstride = (long long)L::Q * G.plane;
-    collide<LAT, C>(G, g, [&](int i, const C& v) {
-        const long long o = (long long)L::plane_of(i) * G.plane + node;
-        fo[o] = v.v;
-#pragma unroll
-        for (int k = 0; k < kTD; ++k) to[k * dstride + o] = v.d[k];
-    });
-}
-
-// J += sum (dP - dP_ref)^2 and dJ_k += sum 2 (dP - dP_ref) dP'_k over the
-// loss region; sums[0] = J, sums[1..3] = dJ.  dP_ref: [ny][nx] or null.
-template <int LAT, typename S>
-__global__ void __launch_bounds__(128) k_tl_loss(Geom G, Region R, const S* __restrict__ f,
-                                                 const S* __restrict__ t,
-                                                 const double* __restrict__ dPref, double* sums)
-{
-    using L = Lat<LAT>;
-    using C = Dual<typename Store<S>::C, kTD>;
-    const int x = R.x0 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = R.y0 + blockIdx.y;
-    double v[kTD + 1] = {0.0, 0.0, 0.0, 0.0};
+    double acc[kTD + 1] = {0.0, 0.0, 0.0, 0.0};
     if (x < R.x1) {
-        C g[L::Q];
-        load_node<LAT, S, C>(G, f, t, (long long)y * G.nxp + x, g);
-        const Moments<LAT, C> m = moments<LAT, C>(g, rho0_of<C>(G));
-        const TD s0 = to_td(m.s0), dT = to_td(m.dT);
-        const TD dP = L::THERMAL ? TD(L::CS2) * (s0 + TD(G.rho0) * dT + s0 * dT) : TD(L::CS2) * s0;
-        const double e = dP.v - (dPref ? dPref[(long long)y * G.nx + x] : 0.0);
-        v[0] = e * e;
+        const long long node = (long long)y * G.nxp + x;
+        const long long dstride = (long long)L::Q * G.plane;
+        CV gv[L::Q];
 #pragma unroll
-        for (int k = 0; k < kTD; ++k) v[k + 1] = 2.0 * e * dP.d[k];
+        for (int i = 0; i < L::Q; ++i) gv[i] = f[pull_src<LAT>(G, i, x, y)];
+        double e = 0.0;
+#pragma unroll 1
+        for (int k = 0; k < kTD; ++k) {
+            C1 g[L::Q];
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                g[i].v = gv[i];
+                g[i].d[0] = t[k * dstride + pull_src<LAT>(G, i, x, y)];
+            }
+            const Moments<LAT, C1> m = collide<LAT, C1>(G, g, [&](int i, const C1& v) {
+                const long long o = (long long)L::plane_of(i) * G.plane + node;
+                if (k == 0) fo[o] = v.v;
+                to[k * dstride + o] = v.d[0];
+            });
+            // P - c_s^2 rho0 = c_s^2 (drho + rho0 dT + drho dT)
+            const double s0 = double(m.s0.v), dT = double(m.dT.v);
+            const double s0d = double(m.s0.d[0]), dTd = double(m.dT.d[0]);
+            if (k == 0) {
+                const double dP = L::THERMAL ? L::CS2 * (s0 + G.rho0 * dT + s0 * dT) : L::CS2 * s0;
+                e = dP - (dPref ? dPref[(long long)y * G.nx + x] : 0.0);
+                acc[0] = e * e;
+            }
+            const double dPd = L::THERMAL ? L::CS2 * (s0d + G.rho0 * dTd + s0d * dT + s0 * dTd) : L::CS2 * s0d;
+            acc[k + 1] = 2.0 * e * dPd;
+        }
     }
     __shared__ double red[kTD + 1][4];
 #pragma unroll
     for (int c = 0; c < kTD + 1; ++c) {
-        double a = v[c];
+        double a = acc[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = a;
@@ -257,62 +282,53 @@ __global__ void __launch_bounds__(128) k_tl_loss(Geom G, Region R, const S* __re
 
 template <int LAT, typename S>
 int tl_step_t(const TLState& T, const Geom& G, const Export& E, const Band& B, const Region& bulk,
-              const Region& loss, void* const f[2], int par, const double* dPref, cudaStream_t st)
+              void* const f[2], int par, const double* dPref, cudaStream_t st)
 {
+    using R = TB<S>;
     const S* fi = static_cast<const S*>(f[par]);
     S* fo = static_cast<S*>(f[par ^ 1]);
     const S* ti = static_cast<const S*>(T.t[par]);
     S* to = static_cast<S*>(T.t[par ^ 1]);
-    TD* St = static_cast<TD*>(T.St);
-    TD* St1 = static_cast<TD*>(T.St1);
-    TD* Ud = static_cast<TD*>(T.Ud);
-    Relax<TD> P;
-    P.alpha_T = TD(B.alpha_T);
-    P.alpha_T.d[0] = 1.0;                       // direction 0: alpha_T
-    P.beta_P = TD(B.beta_P);
-    P.beta_P.d[1] = 1.0;                        // direction 1: beta_P
-    P.t_inf = TD(B.t_inf);
+    R* St = static_cast<R*>(T.St);
+    R* St1 = static_cast<R*>(T.St1);
+    Relax<R> P;
+    P.alpha_T = R(B.alpha_T);
+    P.alpha_T.d[0] = 1;                         // direction 0: alpha_T
+    P.beta_P = R(B.beta_P);
+    P.beta_P.d[1] = 1;                          // direction 1: beta_P
+    P.t_inf = R(B.t_inf);
     for (int s = 0; s < 4; ++s) {
-        P.pdev[s] = TD(B.pdev[s]);
-        P.pdev[s].d[2] = 1.0;                   // direction 2: P_inf (all sides)
+        P.pdev[s] = R(B.pdev[s]);
+        P.pdev[s].d[2] = 1;                     // direction 2: P_inf (all sides)
     }
     if (B.n_unk > 0) {
         if (E.nslots > 0)
             k_tl_strip<LAT, S><<<(E.nslots + 127) / 128, 128, 0, st>>>(G, E, fi, ti, St, St1);
         for (int stage = 0; stage < 4; ++stage)
-            k_tl_stage<LAT><<<(B.n_unk + 127) / 128, 128, 0, st>>>(
-                G, B, P, St, St1, Ud, static_cast<TD*>(T.Ya), static_cast<TD*>(T.Yb),
-                static_cast<TD*>(T.acc), T.mask, stage);
-        k_tl_dirichlet<LAT, S><<<(B.n_unk + 127) / 128, 128, 0, st>>>(G, B, Ud, fo, to);
+            k_tl_stage<LAT, S><<<(B.n_unk + 127) / 128, 128, 0, st>>>(
+                G, B, P, St, St1, static_cast<TS*>(T.Ud), static_cast<R*>(T.Uf), static_cast<R*>(T.Ya),
+                static_cast<R*>(T.Yb), static_cast<TS*>(T.acc), T.mask, stage);
+        k_tl_dirichlet<LAT, S><<<(B.n_unk + 127) / 128, 128, 0, st>>>(G, B, static_cast<const TS*>(T.Ud),
+                                                                      fo, to);
     }
     if (bulk.x1 > bulk.x0 && bulk.y1 > bulk.y0) {
         dim3 grd((bulk.x1 - bulk.x0 + 127) / 128, bulk.y1 - bulk.y0);
-        k_tl_bulk<LAT, S><<<grd, 128, 0, st>>>(G, bulk, fi, ti, fo, to);
-    }
-    if (loss.x1 > loss.x0 && loss.y1 > loss.y0) {
-        dim3 grd((loss.x1 - loss.x0 + 127) / 128, loss.y1 - loss.y0);
-        k_tl_loss<LAT, S><<<grd, 128, 0, st>>>(G, loss, fo, to, dPref, T.sums);
+        k_tl_bulk<LAT, S><<<grd, 128, 0, st>>>(G, bulk, fi, ti, fo, to, dPref, T.sums);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <int LAT>
-__global__ void k_tl_seed(Band B, TD* Ud, int par)
-{
-    // boundary state of the current parity with zero derivatives
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= B.n_unk) return;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) Ud[4LL * u + m] = TD(B.Ub[((long long)par * B.n_unk + u) * 4 + m]);
-}
-
-template <int LAT>
-__global__ void k_tl_unseed(Band B, const TD* Ud, int par)
+// boundary state of parity par -> Ud (and its copy Uf in the stage type)
+template <typename S>
+__global__ void k_tl_seed(Band B, TS* Ud, TB<S>* Uf, int par)
 {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= B.n_unk) return;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) B.Ub[((long long)par * B.n_unk + u) * 4 + m] = Ud[4LL * u + m].v;
+    for (int m = 0; m < 4; ++m) {
+        Ud[4LL * u + m] = TS(B.Ub[((long long)par * B.n_unk + u) * 4 + m]);
+        Uf[4LL * u + m] = dcast<TB<S>>(Ud[4LL * u + m]);
+    }
 }
 
 #define TL_DISPATCH(lat, storage, CALL)                                    \
@@ -332,23 +348,25 @@ __global__ void k_tl_unseed(Band B, const TD* Ud, int par)
 
 }  // namespace
 
-size_t tl_dual_bytes() { return sizeof(TD); }
+size_t tl_dual_bytes() { return sizeof(TS); }
 
 int launch_tl_step(int lat, int storage, const TLState& T, const Geom& G, const Export& E,
-                   const Band& B, const Region& bulk, const Region& loss, void* const f[2], int par,
-                   const double* dPref, cudaStream_t st)
+                   const Band& B, const Region& bulk, void* const f[2], int par, const double* dPref,
+                   cudaStream_t st)
 {
-#define CALL(L, S) tl_step_t<L, S>(T, G, E, B, bulk, loss, f, par, dPref, st)
+#define CALL(L, S) tl_step_t<L, S>(T, G, E, B, bulk, f, par, dPref, st)
     TL_DISPATCH(lat, storage, CALL);
 #undef CALL
 }
 
-int launch_tl_seed(const TLState& T, const Band& B, int par, bool back, cudaStream_t st)
+int launch_tl_seed(const TLState& T, const Band& B, int storage, int par, cudaStream_t st)
 {
     if (B.n_unk == 0) return 0;
-    TD* Ud = static_cast<TD*>(T.Ud);
-    if (back) k_tl_unseed<D2Q37><<<(B.n_unk + 127) / 128, 128, 0, st>>>(B, Ud, par);
-    else k_tl_seed<D2Q37><<<(B.n_unk + 127) / 128, 128, 0, st>>>(B, Ud, par);
+    const int nb = (B.n_unk + 127) / 128;
+    if (storage == 0)
+        k_tl_seed<double><<<nb, 128, 0, st>>>(B, static_cast<TS*>(T.Ud), static_cast<TB<double>*>(T.Uf), par);
+    else
+        k_tl_seed<float><<<nb, 128, 0, st>>>(B, static_cast<TS*>(T.Ud), static_cast<TB<float>*>(T.Uf), par);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

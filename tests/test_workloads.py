@@ -33,3 +33,11 @@ def test_sweep_batch_is_seeded_and_in_range():
     sizes = {(c["nx"], c["ny"]) for c, _ in a}
     assert len(sizes) > 90                          # uneven
     assert W.sweep_batch(4, seed=5)[0][0] != a[0][0]
+
+
+def test_gradient_pulse_reference_is_centred_on_the_crop():
+    cfg, f, rcfg, rf, (x0, y0) = W.gradient_pulse(nx=64, ny=32, ref_scale=4)
+    assert (rcfg["nx"], rcfg["ny"]) == (256, 128) and rcfg["sides"] == ["periodic"] * 4
+    assert cfg["viscous"] == "off" and cfg["sides"] == ["cbc"] * 4
+    for a, b in zip(f, rf):
+        assert np.allclose(b[y0:y0 + 32, x0:x0 + 64], a, rtol=0.0, atol=1e-15)
