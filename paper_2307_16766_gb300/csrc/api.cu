@@ -1145,8 +1145,8 @@ int lbm_grad_begin(lbm_handle* h)
     TLState& T = h->tl;
     T.t[0] = at<char>(mem, o_t0);
     T.t[1] = at<char>(mem, o_t1);
-    T.St = at<char>(mem, o_st);
-    T.St1 = at<char>(mem, o_st1);
+    T.strip[0] = at<char>(mem, o_st);
+    T.strip[1] = at<char>(mem, o_st1);
     T.Ud = at<char>(mem, o_ud);
     T.Uf = at<char>(mem, o_uf);
     T.Ya = at<char>(mem, o_ya);
@@ -1158,7 +1158,7 @@ int lbm_grad_begin(lbm_handle* h)
     // the initial fields do not depend on the parameters: zero derivatives
     e = cudaMemsetAsync(mem, 0, o, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "gradient state");
-    if (launch_tl_seed(T, h->B, h->storage, int(h->steps & 1), h->stream))
+    if (launch_tl_seed(h->lattice, h->storage, T, h->G, h->E, h->B, h->f, int(h->steps & 1), h->stream))
         return check_launch(h, -1, "gradient seed kernel");
     h->grad_stale = true;
     return LBM_OK;

@@ -631,16 +631,15 @@ int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad);
 int launch_zg(int lat, int storage, const Geom& G, const Band& B, void* fnew, cudaStream_t st);
 
 // State of the tangent-linear step (tangent.cu): derivatives along three
-// directions (alpha_T, beta_P, P_inf).  Dual values take tl_dual_bytes()
-// each (the FP64 state type; the stage type is no larger).
+// directions (alpha_T, beta_P, P_inf).  Arrays are sized with
+// tl_dual_bytes() per value (the largest element type used).
 struct TLState {
     void* t[2];      // derivative populations per parity: [3][Q][plane], storage type
-    void* St;        // strip macros at t: [nslots][4], stage type
-    void* St1;       // strip macros at t + 1: [nslots][4], stage type
-    void* Ud;        // boundary state: [n_unk][4], FP64 Dual
+    void* strip[2];  // strip macros per parity (t, then t + 1): [nslots][4], stage type
+    void* Ud;        // boundary state: [n_unk][4], FP64 value + FP32 derivatives
     void* Uf;        // the same in the stage type
     void *Ya, *Yb;   // RK4 stage values: [n_unk][4], stage type
-    void* acc;       // RK4 sum: [n_unk][4], FP64 Dual
+    void* acc;       // RK4 sum: [n_unk][4], as Ud
     int* mask;       // incoming waves at t: [n_unk]
     double* sums;    // J, dJ/dalpha_T, dJ/dbeta_P, dJ/dP_inf
 };
@@ -653,7 +652,10 @@ size_t tl_dual_bytes();
 int launch_tl_step(int lat, int storage, const TLState& T, const Geom& G, const Export& E,
                    const Band& B, const Region& bulk, void* const f[2], int par, const double* dPref,
                    cudaStream_t st);
-// Seed T.Ud / T.Uf with the boundary state of parity par, zero derivatives.
-int launch_tl_seed(const TLState& T, const Band& B, int storage, int par, cudaStream_t st);
+// Seed the strip macros of parity par from f[par] and T.Ud / T.Uf with the
+// boundary state of parity par (the derivatives as T holds them: zero after
+// lbm_grad_begin's clear).
+int launch_tl_seed(int lat, int storage, const TLState& T, const Geom& G, const Export& E, const Band& B,
+                   void* const f[2], int par, cudaStream_t st);
 
 }  // namespace lbmgb

@@ -5,27 +5,48 @@
 // derivatives with respect to the three parameters of the incoming-wave
 // relaxation (Eqs. LODI-Relax, CBC-Relax): alpha_T, beta_P and P_inf.
 //
-//   k_tl_strip     macros of the strip nodes at t (their populations) and
-//                  at t + 1 (pulled, Eq. lbe), value and derivatives
+//   k_tl_strip     macros of the strip nodes at t (the first step's seed)
+//   k_tl_bulk      (first) pull-stream + BGK collide of every bulk node, one
+//                  derivative direction at a time, the macros of t + 1 of
+//                  the strip nodes (Eq. lbe, Eq. macro), and the loss of the
+//                  node: J += (P - P_ref)^2 and its derivatives,
+//                  P - c_s^2 rho0 = c_s^2 (drho + rho0 dT + drho dT)
 //   k_tl_stage     one RK4 stage of every boundary unknown (Sec. 3.3),
 //                  right-hand side from charsys.cuh on Dual numbers of the
-//                  storage's arithmetic, state and RK4 sum in FP64
+//                  storage's arithmetic, state and RK4 sum with FP64 values
 //   k_tl_dirichlet f^eq of the new boundary state on the band nodes
-//   k_tl_bulk      pull-stream + BGK collide of every bulk node, one
-//                  derivative direction at a time, and the loss of the node:
-//                  J += (P - P_ref)^2 and its derivatives,
-//                  P - c_s^2 rho0 = c_s^2 (drho + rho0 dT + drho dT)
+//                  (equilibrium Dirichlet condition)
 //
 // Supported: FP64 and FP32 storage, equilibrium Dirichlet condition, no
 // viscous vector, characteristic and periodic sides (checked on the host).
 #include "charsys.cuh"
+
+#include <type_traits>
 
 namespace lbmgb {
 
 namespace {
 
 constexpr int kTD = 3;                      // derivative directions
-using TS = Dual<double, kTD>;               // boundary state and RK4 sum
+
+// Boundary state and RK4 sum: FP64 value (the state accumulates over the
+// steps, as in the ordinary step) with FP32 derivatives.  Only the linear
+// RK4 bookkeeping is done on it.
+struct TS {
+    double v;
+    float d[kTD];
+};
+
+template <typename C>
+__device__ __forceinline__ TS ts_axpy(const TS& a, double w, const C& k)
+{
+    // a + w k
+    TS r;
+    r.v = a.v + w * double(k.v);
+#pragma unroll
+    for (int q = 0; q < kTD; ++q) r.d[q] = a.d[q] + float(w) * float(k.d[q]);
+    return r;
+}
 // arithmetic of the strips, stage values and right-hand sides: the
 // storage's (FP32 inputs around an FP64 state with FP32 storage)
 template <typename S>
@@ -34,10 +55,14 @@ using TB = Dual<typename Store<S>::C, kTD>;
 template <typename To, typename From>
 __device__ __forceinline__ To dcast(const From& a)
 {
+    // element types by value (an element expression's decltype is a
+    // reference, and casting to it would reinterpret the source's bytes)
+    using V = std::remove_cv_t<std::remove_reference_t<decltype(To{}.v)>>;
+    using E = std::remove_cv_t<std::remove_reference_t<decltype(To{}.d[0])>>;
     To r;
-    r.v = decltype(r.v)(a.v);
+    r.v = static_cast<V>(a.v);
 #pragma unroll
-    for (int k = 0; k < kTD; ++k) r.d[k] = decltype(r.v)(a.d[k]);
+    for (int k = 0; k < kTD; ++k) r.d[k] = static_cast<E>(a.d[k]);
     return r;
 }
 
@@ -102,9 +127,13 @@ __device__ __forceinline__ bool slot_node(const Geom& G, const Export& E, int q,
     return inbx && inby;
 }
 
+// Strip macros of time t from the stored (post-collision) populations,
+// which carry the macros of t (the collision keeps them): the seed of the
+// first tangent-linear step; later steps take them from the bulk pass of the
+// step before.
 template <int LAT, typename S>
 __global__ void k_tl_strip(Geom G, Export E, const S* __restrict__ f, const S* __restrict__ t,
-                           TB<S>* __restrict__ St, TB<S>* __restrict__ St1)
+                           TB<S>* __restrict__ St)
 {
     using L = Lat<LAT>;
     using C = TB<S>;
@@ -112,21 +141,15 @@ __global__ void k_tl_strip(Geom G, Export E, const S* __restrict__ f, const S* _
     if (q >= E.nslots) return;
     int x = 0, y = 0;
     C* a = St + 4LL * q;
-    C* b = St1 + 4LL * q;
     if (!slot_node(G, E, q, x, y)) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) a[c] = b[c] = C(0);
+        for (int c = 0; c < 4; ++c) a[c] = C(0);
         return;
     }
     C g[L::Q];
-    // time t: the stored (post-collision) populations carry the macros of t
     load_node<LAT, S, C>(G, f, t, (long long)y * G.nxp + x, g);
-    Moments<LAT, C> m = moments<LAT, C>(g, rho0_of<C>(G));
+    const Moments<LAT, C> m = moments<LAT, C>(g, rho0_of<C>(G));
     a[0] = m.s0; a[1] = m.ux; a[2] = m.uy; a[3] = m.dT;
-    // time t + 1: pulled
-    pull_node<LAT, S, C>(G, f, t, x, y, g);
-    m = moments<LAT, C>(g, rho0_of<C>(G));
-    b[0] = m.s0; b[1] = m.ux; b[2] = m.uy; b[3] = m.dT;
 }
 
 // One RK4 stage of every boundary unknown.  Ud, acc: state and sum of k
@@ -139,6 +162,9 @@ __global__ void k_tl_stage(Geom G, Band B, Relax<TB<S>> P, const TB<S>* __restri
 {
     using Lt = Lat<LAT>;
     using T = TB<S>;
+    // stage 0 reads only time t: the bulk pass launched after it for early
+    // start (it writes only t + 1) may begin now
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= B.n_unk) return;
     const UDesc D = B.ud[u];
@@ -167,24 +193,25 @@ __global__ void k_tl_stage(Geom G, Band B, Relax<TB<S>> P, const TB<S>* __restri
         const double hk = stage == 2 ? 1.0 : 0.5;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const TS km = dcast<TS>(k[m]);
-            ac[m] = (stage == 0 ? TS(0) : ac[m]) + TS(wk) * km;
-            Yout[4LL * u + m] = dcast<T>(U0[m] + TS(hk) * km);
+            ac[m] = ts_axpy(stage == 0 ? TS{0.0, {0.f, 0.f, 0.f}} : ac[m], wk, k[m]);
+            Yout[4LL * u + m] = dcast<T>(ts_axpy(U0[m], hk, k[m]));
         }
-        return;
-    }
+    } else {
+        // RK4: U(t + 1) = U(t) + (k1 + 2 k2 + 2 k3 + k4) / 6
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        U0[m] = U0[m] + (ac[m] + dcast<TS>(k[m])) * TS(1.0 / 6.0);
-        Uf[4LL * u + m] = dcast<T>(U0[m]);
+        for (int m = 0; m < 4; ++m) {
+            TS s = ts_axpy(ac[m], 1.0, k[m]);
+            U0[m] = ts_axpy(U0[m], 1.0 / 6.0, s);
+            Uf[4LL * u + m] = dcast<T>(U0[m]);
+        }
     }
 }
 
-// Equilibrium Dirichlet condition: f^eq(U_b(t + 1)) on the unknown's band
-// node (corner: its M x M block), value and derivatives, in the storage's
-// arithmetic.
+// Equilibrium Dirichlet condition of the new boundary state: f^eq on the
+// unknown's band node (corner: its M x M block), value and derivatives, in
+// the storage's arithmetic.
 template <int LAT, typename S>
-__global__ void k_tl_dirichlet(Geom G, Band B, const TS* __restrict__ Ud, S* __restrict__ f,
+__global__ void k_tl_dirichlet(Geom G, Band B, const TB<S>* __restrict__ Uf, S* __restrict__ f,
                                S* __restrict__ t)
 {
     using L = Lat<LAT>;
@@ -192,13 +219,13 @@ __global__ void k_tl_dirichlet(Geom G, Band B, const TS* __restrict__ Ud, S* __r
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= B.n_unk) return;
     const UDesc D = B.ud[u];
-    const TS* U = Ud + 4LL * u;
+    const C* U = Uf + 4LL * u;
     Moments<LAT, C> m;
-    m.s0 = dcast<C>(U[0]);
+    m.s0 = U[0];
     m.rho = rho0_of<C>(G) + m.s0;
-    m.ux = dcast<C>(U[1]);
-    m.uy = dcast<C>(U[2]);
-    m.dT = L::THERMAL ? dcast<C>(U[3]) : C(0);
+    m.ux = U[1];
+    m.uy = U[2];
+    m.dT = L::THERMAL ? U[3] : C(0);
     C ge[L::Q];
     equilibrium<LAT, C>(m, ge);
     const long long dstride = (long long)L::Q * G.plane;
@@ -222,37 +249,53 @@ __global__ void k_tl_dirichlet(Geom G, Band B, const TS* __restrict__ Ud, S* __r
 // and the collision keeps the macros, so the pulled populations' moments
 // give P at t + 1.
 template <int LAT, typename S>
-__global__ void __launch_bounds__(128) k_tl_bulk(Geom G, Region R, const S* __restrict__ f,
+__global__ void __launch_bounds__(128) k_tl_bulk(Geom G, Region R, Export E, const S* __restrict__ f,
                                                  const S* __restrict__ t, S* __restrict__ fo,
-                                                 S* __restrict__ to, const double* __restrict__ dPref,
-                                                 double* sums)
+                                                 S* __restrict__ to, TB<S>* __restrict__ St1,
+                                                 const double* __restrict__ dPref, double* sums)
 {
     using L = Lat<LAT>;
-    using CV = typename Store<S>::C;
-    using C1 = Dual<CV, 1>;
+    using C1 = Dual<typename Store<S>::C, 1>;
     const int x = R.x0 + blockIdx.x * blockDim.x + threadIdx.x;
     const int y = R.y0 + blockIdx.y;
     double acc[kTD + 1] = {0.0, 0.0, 0.0, 0.0};
     if (x < R.x1) {
         const long long node = (long long)y * G.nxp + x;
         const long long dstride = (long long)L::Q * G.plane;
-        CV gv[L::Q];
+        // strip slots of this node (depth 0..2 inside a characteristic
+        // side; up to two sides near a corner): its macros at t + 1
+        int slot[2] = {-1, -1}, ns = 0;
+        {
+            const int dd[4] = {x - G.M, G.nx - 1 - G.M - x, y - G.M, G.ny - 1 - G.M - y};
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) gv[i] = f[pull_src<LAT>(G, i, x, y)];
+            for (int s = 0; s < 4; ++s)
+                if (E.cbc[s] && dd[s] >= 0 && dd[s] <= 2 && ns < 2)
+                    slot[ns++] = E.offS[s] + dd[s] * E.L[s] + (s < 2 ? y : x);
+        }
         double e = 0.0;
 #pragma unroll 1
         for (int k = 0; k < kTD; ++k) {
             C1 g[L::Q];
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
-                g[i].v = gv[i];
-                g[i].d[0] = t[k * dstride + pull_src<LAT>(G, i, x, y)];
+                const long long o = pull_src<LAT>(G, i, x, y);
+                g[i].v = f[o];
+                g[i].d[0] = t[k * dstride + o];
             }
             const Moments<LAT, C1> m = collide<LAT, C1>(G, g, [&](int i, const C1& v) {
                 const long long o = (long long)L::plane_of(i) * G.plane + node;
                 if (k == 0) fo[o] = v.v;
                 to[k * dstride + o] = v.d[0];
             });
+            for (int q = 0; q < ns; ++q) {
+                TB<S>* a = St1 + 4LL * slot[q];
+                const C1 mc[4] = {m.s0, m.ux, m.uy, m.dT};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (k == 0) a[c].v = mc[c].v;
+                    a[c].d[k] = mc[c].d[0];
+                }
+            }
             // P - c_s^2 rho0 = c_s^2 (drho + rho0 dT + drho dT)
             const double s0 = double(m.s0.v), dT = double(m.dT.v);
             const double s0d = double(m.s0.d[0]), dTd = double(m.dT.d[0]);
@@ -289,8 +332,8 @@ int tl_step_t(const TLState& T, const Geom& G, const Export& E, const Band& B, c
     S* fo = static_cast<S*>(f[par ^ 1]);
     const S* ti = static_cast<const S*>(T.t[par]);
     S* to = static_cast<S*>(T.t[par ^ 1]);
-    R* St = static_cast<R*>(T.St);
-    R* St1 = static_cast<R*>(T.St1);
+    R* St = static_cast<R*>(T.strip[par]);
+    R* St1 = static_cast<R*>(T.strip[par ^ 1]);
     Relax<R> P;
     P.alpha_T = R(B.alpha_T);
     P.alpha_T.d[0] = 1;                         // direction 0: alpha_T
@@ -301,20 +344,42 @@ int tl_step_t(const TLState& T, const Geom& G, const Export& E, const Band& B, c
         P.pdev[s] = R(B.pdev[s]);
         P.pdev[s].d[2] = 1;                     // direction 2: P_inf (all sides)
     }
+    // RK4 stage 0 (time t only) and, beside it by programmatic launch, the
+    // bulk pass, which also gives the strip macros of t + 1 that stages 1-3
+    // read; stages 1-3 and the Dirichlet write follow in stream order
+    const int nb = (B.n_unk + 127) / 128;
+    auto stage = [&](int k, bool early) {
+        return launch_ex(k_tl_stage<LAT, S>, dim3(nb), dim3(128), 0, st, early, G, B, P,
+                         static_cast<const R*>(St), static_cast<const R*>(St1), static_cast<TS*>(T.Ud),
+                         static_cast<R*>(T.Uf), static_cast<R*>(T.Ya), static_cast<R*>(T.Yb),
+                         static_cast<TS*>(T.acc), T.mask, k);
+    };
+    bool first = true;
     if (B.n_unk > 0) {
-        if (E.nslots > 0)
-            k_tl_strip<LAT, S><<<(E.nslots + 127) / 128, 128, 0, st>>>(G, E, fi, ti, St, St1);
-        for (int stage = 0; stage < 4; ++stage)
-            k_tl_stage<LAT, S><<<(B.n_unk + 127) / 128, 128, 0, st>>>(
-                G, B, P, St, St1, static_cast<TS*>(T.Ud), static_cast<R*>(T.Uf), static_cast<R*>(T.Ya),
-                static_cast<R*>(T.Yb), static_cast<TS*>(T.acc), T.mask, stage);
-        k_tl_dirichlet<LAT, S><<<(B.n_unk + 127) / 128, 128, 0, st>>>(G, B, static_cast<const TS*>(T.Ud),
-                                                                      fo, to);
+        if (stage(0, false)) return -1;
+        first = false;
     }
     if (bulk.x1 > bulk.x0 && bulk.y1 > bulk.y0) {
         dim3 grd((bulk.x1 - bulk.x0 + 127) / 128, bulk.y1 - bulk.y0);
-        k_tl_bulk<LAT, S><<<grd, 128, 0, st>>>(G, bulk, fi, ti, fo, to, dPref, T.sums);
+        if (launch_ex(k_tl_bulk<LAT, S>, grd, dim3(128), 0, st, !first, G, bulk, E, fi, ti, fo, to, St1, dPref,
+                      T.sums))
+            return -1;
     }
+    if (B.n_unk > 0) {
+        for (int k = 1; k < 4; ++k)
+            if (stage(k, false)) return -1;
+        k_tl_dirichlet<LAT, S><<<nb, 128, 0, st>>>(G, B, static_cast<const R*>(T.Uf), fo, to);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int LAT, typename S>
+int tl_seed_strips_t(const TLState& T, const Geom& G, const Export& E, void* const f[2], int par,
+                     cudaStream_t st)
+{
+    if (E.nslots == 0) return 0;
+    k_tl_strip<LAT, S><<<(E.nslots + 127) / 128, 128, 0, st>>>(
+        G, E, static_cast<const S*>(f[par]), static_cast<const S*>(T.t[par]), static_cast<TB<S>*>(T.strip[par]));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -326,7 +391,7 @@ __global__ void k_tl_seed(Band B, TS* Ud, TB<S>* Uf, int par)
     if (u >= B.n_unk) return;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        Ud[4LL * u + m] = TS(B.Ub[((long long)par * B.n_unk + u) * 4 + m]);
+        Ud[4LL * u + m] = TS{B.Ub[((long long)par * B.n_unk + u) * 4 + m], {0.f, 0.f, 0.f}};
         Uf[4LL * u + m] = dcast<TB<S>>(Ud[4LL * u + m]);
     }
 }
@@ -348,7 +413,7 @@ __global__ void k_tl_seed(Band B, TS* Ud, TB<S>* Uf, int par)
 
 }  // namespace
 
-size_t tl_dual_bytes() { return sizeof(TS); }
+size_t tl_dual_bytes() { return sizeof(TS) > sizeof(TB<double>) ? sizeof(TS) : sizeof(TB<double>); }
 
 int launch_tl_step(int lat, int storage, const TLState& T, const Geom& G, const Export& E,
                    const Band& B, const Region& bulk, void* const f[2], int par, const double* dPref,
@@ -359,8 +424,17 @@ int launch_tl_step(int lat, int storage, const TLState& T, const Geom& G, const 
 #undef CALL
 }
 
-int launch_tl_seed(const TLState& T, const Band& B, int storage, int par, cudaStream_t st)
+int launch_tl_seed(int lat, int storage, const TLState& T, const Geom& G, const Export& E, const Band& B,
+                   void* const f[2], int par, cudaStream_t st)
 {
+    {
+        const int rc = [&]() -> int {
+#define CALL(L, S) tl_seed_strips_t<L, S>(T, G, E, f, par, st)
+            TL_DISPATCH(lat, storage, CALL);
+#undef CALL
+        }();
+        if (rc) return rc;
+    }
     if (B.n_unk == 0) return 0;
     const int nb = (B.n_unk + 127) / 128;
     if (storage == 0)
