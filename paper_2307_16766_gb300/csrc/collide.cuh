@@ -89,12 +89,13 @@ __device__ __forceinline__ void pull_plain_planes(const Geom& G, const S* __rest
 // populations are in g (already multiplied by w for scaled storage).  The
 // post-collision value of velocity i goes to put(i, value); the moments of
 // the pulled populations are returned.
-template <int LAT, typename C, typename Put>
-__device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Put&& put)
+// BGK collision of a node whose moments m are known; gi(i) gives the
+// pre-collision population i (read as the pair loop needs it).
+template <int LAT, typename C, typename Get, typename Put>
+__device__ __forceinline__ void collide_given(const Geom& G, const Moments<LAT, C>& m, Get&& gi, Put&& put)
 {
     using L = Lat<LAT>;
     constexpr int Q = L::Q;
-    const Moments<LAT, C> m = moments<LAT, C>(g, rho0_of<C>(G));
 
     // BGK collide (Eq. bgk), one opposite pair at a time:
     // g^eq_{+-} = w (rho - rho0) + w rho (even +- odd) in p = c.u / c_s^2.
@@ -107,7 +108,7 @@ __device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Pu
     if (sizeof(typename DualTraits<C>::Value) == 8) {
         {
             const C geq = C(L::w(0)) * (m.s0 + m.rho * e.A0);
-            put(0, g[0] + om * (geq - g[0]));
+            { const C g_ = gi(0); put(0, g_ + om * (geq - g_)); }
         }
 #pragma unroll
         for (int i = 1; i < Q; i += 2) {
@@ -126,8 +127,8 @@ __device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Pu
             const C ws0 = C(L::w(i)) * m.s0, wr = C(L::w(i)) * m.rho;
             const C gp = ws0 + wr * (ev + od);
             const C gm = ws0 + wr * (ev - od);
-            put(i, g[i] + om * (gp - g[i]));
-            put(i + 1, g[i + 1] + om * (gm - g[i + 1]));
+            { const C g_ = gi(i); put(i, g_ + om * (gp - g_)); }
+            { const C g_ = gi(i + 1); put(i + 1, g_ + om * (gm - g_)); }
         }
     } else {
         // FP32 arithmetic.  Float-rounded weights and c_s^2 miss the discrete
@@ -159,8 +160,8 @@ __device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Pu
             if (L::cx(i)) Mx += C(L::cx(i)) * dif;
             if (L::cy(i)) My += C(L::cy(i)) * dif;
             if (L::THERMAL) Me += C(L::c2cls(k)) * sum;
-            put(i, g[i] + om * (gp - g[i]));
-            put(i + 1, g[i + 1] + om * (gm - g[i + 1]));
+            { const C g_ = gi(i); put(i, g_ + om * (gp - g_)); }
+            { const C g_ = gi(i + 1); put(i + 1, g_ + om * (gm - g_)); }
         }
         // |c| = 1 class: (1,0) and (-1,0) are velocities 1, 2; (0,1), (0,-1) are 3, 4
         const C a0 = e.A0 + ics2 * (e.B0 + e.C0 * ics2);
@@ -175,14 +176,21 @@ __device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Pu
             ey += d;
         }
         const C ox = C(0.5) * (m.sx - Mx), oy = C(0.5) * (m.sy - My);
-        put(1, g[1] + om * (ex + ox - g[1]));
-        put(2, g[2] + om * (ex - ox - g[2]));
-        put(3, g[3] + om * (ey + oy - g[3]));
-        put(4, g[4] + om * (ey - oy - g[4]));
+        { const C g_ = gi(1); put(1, g_ + om * (ex + ox - g_)); }
+        { const C g_ = gi(2); put(2, g_ + om * (ex - ox - g_)); }
+        { const C g_ = gi(3); put(3, g_ + om * (ey + oy - g_)); }
+        { const C g_ = gi(4); put(4, g_ + om * (ey - oy - g_)); }
         const C geq0 = m.s0 - M0 - C(2) * (ex + ey);
-        put(0, g[0] + om * (geq0 - g[0]));
+        { const C g_ = gi(0); put(0, g_ + om * (geq0 - g_)); }
     }
 
+}
+
+template <int LAT, typename C, typename Put>
+__device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Put&& put)
+{
+    const Moments<LAT, C> m = moments<LAT, C>(g, rho0_of<C>(G));
+    collide_given<LAT, C>(G, m, [&](int i) -> const C& { return g[i]; }, put);
     return m;
 }
 

@@ -341,18 +341,11 @@ struct Moments {
 // Eq. macro on shifted populations (sum_i w_i c_i = 0, sum_i w_i |c_i|^2 =
 // 2 c_s^2): rho = rho0 + sum g, rho u = sum g c, and
 // theta - 1 = (sum g |c|^2 - rho |u|^2 - 2 c_s^2 (rho - rho0)) / (2 rho c_s^2).
+// The same from the sums s0 = sum g, (sx, sy) = sum g c, se = sum g |c|^2.
 template <int LAT, typename C>
-__device__ __forceinline__ Moments<LAT, C> moments(const C* g, C rho0)
+__device__ __forceinline__ Moments<LAT, C> moments_of_sums(C s0, C sx, C sy, C se, C rho0)
 {
     using L = Lat<LAT>;
-    C s0 = 0, sx = 0, sy = 0, se = 0;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        s0 += g[i];
-        if (L::cx(i)) sx += C(L::cx(i)) * g[i];
-        if (L::cy(i)) sy += C(L::cy(i)) * g[i];
-        if (L::THERMAL && i) se += C(L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i)) * g[i];
-    }
     Moments<LAT, C> m;
     m.s0 = s0;
     m.sx = sx;
@@ -367,6 +360,21 @@ __device__ __forceinline__ Moments<LAT, C> moments(const C* g, C rho0)
         m.dT = (se - m.rho * (m.ux * m.ux + m.uy * m.uy) - C(2.0 * L::CS2) * s0) * irho *
                C(0.5 / L::CS2);
     return m;
+}
+
+template <int LAT, typename C>
+__device__ __forceinline__ Moments<LAT, C> moments(const C* g, C rho0)
+{
+    using L = Lat<LAT>;
+    C s0 = 0, sx = 0, sy = 0, se = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        s0 += g[i];
+        if (L::cx(i)) sx += C(L::cx(i)) * g[i];
+        if (L::cy(i)) sy += C(L::cy(i)) * g[i];
+        if (L::THERMAL && i) se += C(L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i)) * g[i];
+    }
+    return moments_of_sums<LAT, C>(s0, sx, sy, se, rho0);
 }
 
 // Shifted equilibrium of all velocities (g^eq = f^eq - w rho0).
