@@ -50,6 +50,7 @@ struct lbm_handle {
     Region bulk{};           // nodes of the bulk kernel
     bool persistent = false; // single grids: the one-segment-per-CTA kernel measured faster
     BulkRun* brun = nullptr; // its run descriptor (workspace)
+    unsigned* queue = nullptr;  // its work queue (workspace, 2 words)
     int bulk_items = 0, bulk_grid = 0;
     size_t band_pad = 0;     // extra shared memory per band CTA (SM reservation)
     cudaStream_t aux = nullptr;              // internal stream: the bulk beside the band, when timed
@@ -98,7 +99,7 @@ struct Plan {
     std::vector<int> inflow;
     double Uin[4] = {0, 0, 0, 0};
     size_t off_f0 = 0, off_f1 = 0, off_sU = 0, off_sN = 0, off_Ub = 0, off_ud = 0, off_ld = 0,
-           off_sn = 0, off_brun = 0, off_zg = 0, off_in = 0, off_macro = 0, off_flag = 0,
+           off_sn = 0, off_brun = 0, off_queue = 0, off_zg = 0, off_in = 0, off_macro = 0, off_flag = 0,
            total = 0;
 };
 
@@ -516,6 +517,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     pl.off_ld = take(pl.ldp.size() * sizeof(UDesc));
     pl.off_sn = take(pl.snp.size() * sizeof(StripNode));
     pl.off_brun = take(sizeof(BulkRun));
+    pl.off_queue = take(2 * sizeof(unsigned));
     pl.off_zg = take(pl.zg.size() * sizeof(int2));
     pl.off_in = take(pl.inflow.size() * sizeof(int));
     pl.off_macro = take((size_t)4 * nx * ny * 8);
@@ -650,10 +652,12 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
         r.first = 0;
         h->bulk_items = h->bulk.x1 > h->bulk.x0 ? r.nseg * (h->bulk.y1 - h->bulk.y0) : 0;
         h->brun = at<BulkRun>(ws, pl.off_brun);
+        h->queue = at<unsigned>(ws, pl.off_queue);
         int dev = 0, nsm = 0;
         cudaError_t e0 = cudaGetDevice(&dev);
         if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(h->brun, &r, sizeof r, cudaMemcpyHostToDevice, h->stream);
+        if (e0 == cudaSuccess) e0 = cudaMemsetAsync(h->queue, 0, 2 * sizeof(unsigned), h->stream);
         if (e0 != cudaSuccess) return cuda_fail(h, e0, "persistent bulk set-up");
         h->bulk_grid = nsm * 5;
         if (prepare_bulk_persistent(h->lattice, h->storage) != 0)
@@ -710,7 +714,7 @@ int bulk(lbm_handle* h, int par, cudaStream_t st, bool early = false)
     if (rc != LBM_OK) return rc;
     if (h->persistent)
         rc = launch_bulk_persistent(h->lattice, h->storage, h->brun, 1, h->bulk_items, par,
-                                    h->bulk_grid, st, early);
+                                    h->bulk_grid, h->queue, st, early);
     else
         rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->bulk, h->tmap[par], h->f[par],
                          h->f[par ^ 1], h->flag + 1, st, early);
@@ -1232,6 +1236,7 @@ struct lbm_batch {
         int total_items = 0, grid = 0, ctas_per_sm = 0;
         BandRun* band = nullptr;           // device: one per member
         int2* tile_run = nullptr;          // device: (member, tile) per band tile
+        unsigned* queue = nullptr;         // device: work queue of the persistent bulk kernel
         int n_tiles = 0;
         size_t band_smem = 0;
     };
@@ -1343,7 +1348,7 @@ int batch_issue_step(lbm_batch* b, int par, cudaStream_t s0, bool with_inflow)
     }
     for (auto& g : b->groups) {
         if (launch_bulk_persistent(g.lattice, g.storage, g.bulk, int(g.members.size()), g.total_items, par,
-                                   g.grid, s0, !first))
+                                   g.grid, g.queue, s0, !first))
             return batch_fail(b, cudaGetLastError(), "persistent bulk kernel");
         first = false;
     }
@@ -1371,11 +1376,11 @@ int batch_autotune(lbm_batch* b)
             for (int m = 1; m <= 5; ++m) {
                 const int grid = b->nsm * m;
                 launch_bulk_persistent(g.lattice, g.storage, g.bulk, int(g.members.size()), g.total_items, par,
-                                       grid, b->stream);                 // warm-up
+                                       grid, g.queue, b->stream);        // warm-up
                 cudaEventRecord(e0, b->stream);
                 for (int r = 0; r < 3; ++r)
                     launch_bulk_persistent(g.lattice, g.storage, g.bulk, int(g.members.size()), g.total_items,
-                                           par, grid, b->stream);
+                                           par, grid, g.queue, b->stream);
                 cudaEventRecord(e1, b->stream);
                 e = cudaEventSynchronize(e1);
                 if (e != cudaSuccess) {
@@ -1451,7 +1456,7 @@ int lbm_batch_create(int n, const int* lattice, const int* nx, const int* ny, co
     std::vector<std::vector<BandRun>> band(b->groups.size());
     std::vector<std::vector<int2>> tiles(b->groups.size());
     size_t bytes = 0;
-    std::vector<size_t> off_bulk, off_band, off_tiles;
+    std::vector<size_t> off_bulk, off_band, off_tiles, off_queue;
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         auto& g = b->groups[gi];
         if ((int)g.members.size() > kMaxBatchRuns) {
@@ -1492,6 +1497,8 @@ int lbm_batch_create(int n, const int* lattice, const int* nx, const int* ny, co
         bytes = align_up(bytes + band[gi].size() * sizeof(BandRun));
         off_tiles.push_back(bytes);
         bytes = align_up(bytes + std::max<size_t>(1, tiles[gi].size()) * sizeof(int2));
+        off_queue.push_back(bytes);
+        bytes = align_up(bytes + 2 * sizeof(unsigned));
     }
     cudaError_t e = cudaMalloc(&b->dev, bytes);
     for (size_t gi = 0; e == cudaSuccess && gi < b->groups.size(); ++gi) {
@@ -1499,9 +1506,11 @@ int lbm_batch_create(int n, const int* lattice, const int* nx, const int* ny, co
         g.bulk = at<BulkRun>(b->dev, off_bulk[gi]);
         g.band = at<BandRun>(b->dev, off_band[gi]);
         g.tile_run = at<int2>(b->dev, off_tiles[gi]);
+        g.queue = at<unsigned>(b->dev, off_queue[gi]);
         e = cudaMemcpy(g.bulk, bulk[gi].data(), bulk[gi].size() * sizeof(BulkRun), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(g.band, band[gi].data(), band[gi].size() * sizeof(BandRun), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(g.queue, 0, 2 * sizeof(unsigned));
         if (e == cudaSuccess && !tiles[gi].empty())
             e = cudaMemcpy(g.tile_run, tiles[gi].data(), tiles[gi].size() * sizeof(int2), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && prepare_bulk_persistent(g.lattice, g.storage)) e = cudaGetLastError();

@@ -181,13 +181,13 @@ __global__ void __launch_bounds__(kBulkThreads)
 }
 
 // Persistent form of k_bulk for one or many grids of one lattice and
-// storage: `grid` CTAs loop over all work items (run, row, 128-node segment)
-// of the runs in turn, and each CTA keeps the tensor copies of its next item
-// in flight while it computes the current one (two staging buffers, one
-// transaction barrier each).  The arithmetic per node is that of k_bulk.
+// storage: `grid` CTAs take the work items (run, row, 128-node segment) of
+// the runs from a queue, and each CTA keeps the tensor copies of its next
+// item in flight while it computes the current one (two staging buffers,
+// one transaction barrier each).  The arithmetic per node is that of k_bulk.
 template <int LAT, typename S>
 __global__ void __launch_bounds__(kBulkThreads)
-    k_bulk_persistent(const BulkRun* __restrict__ runs, int n_runs, int total, int par)
+    k_bulk_persistent(const BulkRun* __restrict__ runs, int n_runs, int total, int par, unsigned* queue)
 {
     using L = Lat<LAT>;
     using C = typename Store<S>::C;
@@ -238,15 +238,26 @@ __global__ void __launch_bounds__(kBulkThreads)
                              std::make_integer_sequence<int, L::NG>{});
     };
 
+    // Work items are taken from a queue (queue[0]: next item) as CTAs free
+    // up, so that CTAs on SMs that hold other kernels' CTAs (the band
+    // kernel beside this one) take fewer items.  The last CTA to finish
+    // (queue[1] counts them) resets the queue for the next launch.
+    __shared__ int s_w[2];
+    auto grab = [&]() { return int(atomicAdd(&queue[0], 1u)); };
     unsigned phase0 = 0u, phase1 = 0u;      // next phase of each stage's barrier
-    int w = blockIdx.x, stage = 0;
+    int stage = 0;
+    if (threadIdx.x == 0) s_w[0] = grab();
+    __syncthreads();
+    int w = s_w[0];
     Item cur{0, 0, 0, false};
     if (w < total) {
         cur = locate(w);
         issue(cur, 0);
     }
     while (w < total) {
-        const int wn = w + gridDim.x;
+        if (threadIdx.x == 0) s_w[stage ^ 1] = grab();
+        __syncthreads();
+        const int wn = s_w[stage ^ 1];
         Item nxt{0, 0, 0, false};
         if (wn < total) {                   // the buffer of stage ^ 1 was released last iteration
             nxt = locate(wn);
@@ -272,7 +283,7 @@ __global__ void __launch_bounds__(kBulkThreads)
             // a copy never completed: wait (bounded) for the one in flight
             // for the next item, then leave
             if (wn < total && nxt.staged) wait_tx(&bar[stage ^ 1], R.status, stage ? phase0 : phase1);
-            return;
+            break;
         }
         if (valid) {
             if (Store<S>::SCALED) {
@@ -290,6 +301,15 @@ __global__ void __launch_bounds__(kBulkThreads)
         w = wn;
         cur = nxt;
         stage ^= 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&queue[1], 1u) == gridDim.x - 1) {   // every CTA has taken its last item
+            queue[0] = 0u;
+            queue[1] = 0u;
+            __threadfence();
+        }
     }
 }
 
@@ -445,13 +465,13 @@ int bulk_t(const Geom& G, const Offsets& O, const Region& R, const CUtensorMap* 
 }
 
 template <int LAT, typename S>
-int bulk_persistent_t(const BulkRun* runs, int n_runs, int total, int par, int grid, cudaStream_t st,
-                      bool early)
+int bulk_persistent_t(const BulkRun* runs, int n_runs, int total, int par, int grid, unsigned* queue,
+                      cudaStream_t st, bool early)
 {
     if (total <= 0) return 0;
     if (n_runs > kMaxBatchRuns) return -1;
     return launch_ex(k_bulk_persistent<LAT, S>, dim3(grid), dim3(kBulkThreads), 2 * Stage<LAT, S>::TOTAL, st,
-                     early, runs, n_runs, total, par);
+                     early, runs, n_runs, total, par, queue);
 }
 
 template <int LAT, typename S>
@@ -518,9 +538,9 @@ int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Reg
 
 
 int launch_bulk_persistent(int lat, int storage, const BulkRun* runs, int n_runs, int total, int par,
-                           int grid, cudaStream_t st, bool early)
+                           int grid, unsigned* queue, cudaStream_t st, bool early)
 {
-#define CALL(L, S) bulk_persistent_t<L, S>(runs, n_runs, total, par, grid, st, early)
+#define CALL(L, S) bulk_persistent_t<L, S>(runs, n_runs, total, par, grid, queue, st, early)
     LBM_DISPATCH(lat, storage, CALL);
 #undef CALL
 }

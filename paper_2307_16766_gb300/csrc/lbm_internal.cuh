@@ -627,10 +627,12 @@ int prepare_band_batch(int lat, int storage, size_t smem);
 // Dynamic shared memory the band kernel needs per CTA (without padding).
 size_t band_dynamic_smem(int lat, int storage, const Band& B);
 // Persistent bulk step of n_runs runs of one lattice and storage (buffer
-// par -> par ^ 1 of each) with `grid` CTAs looping over the total work
-// items, a two-stage tensor-copy pipeline per CTA.
+// par -> par ^ 1 of each) with `grid` CTAs taking the total work items from
+// a queue (two unsigned words in device memory, zero before the first
+// launch; each launch leaves them zero), a two-stage tensor-copy pipeline
+// per CTA.  Launches sharing a queue must not overlap.
 int launch_bulk_persistent(int lat, int storage, const BulkRun* runs, int n_runs, int total, int par,
-                           int grid, cudaStream_t st, bool early = false);
+                           int grid, unsigned* queue, cudaStream_t st, bool early = false);
 // Opt the persistent bulk kernel in to its dynamic shared memory.
 int prepare_bulk_persistent(int lat, int storage);
 // Opt the band kernel in to its dynamic shared memory (once, at creation).
