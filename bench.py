@@ -14,7 +14,9 @@ and the bulk kernel beside it.  The bulk kernel's duration (the roofline's
 kernel time) comes from a second loop over the same steps in which the
 library records the caller's events around each launch.  A third loop runs
 the phases in sequence (breakdown), and a batched 96-run coefficient sweep
-is timed beside the same runs stepped one after another.  N > 1 runs
+is timed beside the same runs stepped one after another; a 4096^2 pulse
+(5 GB of populations) gives the step's throughput where the bulk dominates.
+N > 1 runs
 independent replicas, one per GPU (weak scaling; the method has no
 cross-GPU exchange in this configuration).  The reference arm times the
 FP64 CPU oracle on this host on the same workload and metric.
@@ -54,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch-leg", action="store_true")
     ap.add_argument("--no-gradient-leg", action="store_true")
+    ap.add_argument("--no-large-leg", action="store_true", help="skip the 4096^2 pulse throughput leg")
     ap.add_argument("--gradient-steps", type=int, default=1500)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--batch-steps", type=int, default=1000)
@@ -296,6 +299,74 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
     return res
 
 
+def run_large(args, local_rank, n=4096):
+    """The n x n D2Q37 FP32 pulse (CBC-RELAX on four sides, the 256^2 parity
+    workload's recipe at the size of the largest throughput grid): whole
+    steps timed with CUDA events (its 5 GB of populations exceed L2, so no
+    flush), then the bulk kernel's duration beside the band kernel through
+    the timing hook, then both phases in sequence."""
+    import torch
+    import paper_2307_16766_gb300 as lbm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cfg, fields = W.pulse_d2q37(n=n, storage="f32")
+    sim = lbm.Simulation(cfg, device=dev).init_fields(*fields)
+    del fields
+    stream = sim.stream
+    sim.step(max(3, args.warmup))
+    torch.cuda.synchronize(dev)
+    K = max(1, min(args.steps, 40))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(K):
+            sim.step(1)
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    step_ms = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(K)])
+    KE = min(K, 20)
+    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(KE)]
+    with torch.cuda.stream(stream):
+        for evs in kev:
+            for e in evs:
+                e.record(stream)
+        for k in range(KE):
+            lbm.lbm_set_kernel_events(sim.handle, [e.cuda_event for e in kev[k]])
+            sim.step(1)
+    torch.cuda.synchronize(dev)
+    lbm.lbm_set_kernel_events(sim.handle, [])
+    bulk_ms = np.array([kev[k][0].elapsed_time(kev[k][1]) for k in range(KE)])
+    band_ms = np.array([kev[k][3].elapsed_time(kev[k][4]) for k in range(KE)])
+    KB = min(K, 10)
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(KB)]
+    with torch.cuda.stream(stream):
+        for k in range(KB):
+            pev[k][0].record(stream)
+            sim.step_phase(0)
+            pev[k][1].record(stream)
+            sim.step_phase(1)
+            pev[k][2].record(stream)
+    torch.cuda.synchronize(dev)
+    p_bulk = np.array([pev[k][0].elapsed_time(pev[k][1]) for k in range(KB)])
+    p_band = np.array([pev[k][1].elapsed_time(pev[k][2]) for k in range(KB)])
+    rho = sim.macros()[0]
+    finite = bool(np.all(np.isfinite(rho)))
+    sim.close()
+    peak, peak_kind = measured_peaks()
+    nodes, bn = n * n, bulk_nodes(cfg)
+    step_s = float(step_ms.sum()) / 1e3
+    return {"value": nodes * K / step_s / 1e6, "unit": "MLUPS", "steps": K,
+            "ms_per_step": step_s / K * 1e3,
+            "step_frac": 296.0 * nodes * K / step_s / 1e9 / peak,
+            "bulk_ms": float(bulk_ms.mean()), "band_overlapped_ms": float(band_ms.mean()),
+            "bulk_frac": 296.0 * bn / (float(bulk_ms.mean()) / 1e3) / 1e9 / peak,
+            "phased_bulk_ms": float(p_bulk.mean()), "phased_band_ms": float(p_band.mean()),
+            "peak_GBps": peak, "peak_kind": peak_kind, "finite": finite,
+            "workload": cfg["name"] + ", tau 0.8, FP32 storage",
+            "l2": "not flushed (populations exceed L2)"}
+
+
 def run_batch(args, local_rank):
     """The batched coefficient sweep (96 uneven D2Q9/D2Q37 FP32 runs, CBC on
     all sides): every run stepped --batch-steps times through one Batch
@@ -495,6 +566,9 @@ def main():
     batch = None
     if not args.no_batch_leg and args.storage == "f32":
         batch = run_batch(args, local_rank)
+    large = None
+    if not args.no_large_leg and args.storage == "f32":
+        large = run_large(args, local_rank)
     gradient = None
     if not args.no_gradient_leg and args.storage == "f32":
         gradient = run_gradient(args, local_rank)
@@ -539,6 +613,8 @@ def main():
                             "interior_GBps": 2 * Q * 8 * fp64["interior_nodes"] / (fp64["interior_ms_mean"] / 1e3) / 1e9}
         if batch is not None:
             line["batch"] = batch
+        if large is not None:
+            line["large"] = large
         if gradient is not None:
             line["gradient"] = gradient
         if not args.no_cpu_baseline and world == 1:

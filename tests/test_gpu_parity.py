@@ -275,6 +275,36 @@ def test_d2q37_vortex_1024x512_full_grid_short():
     assert_parity(cfg, f, 20, "f32", "vortex1024")
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_d2q37_pulse_4096_window_matches_periodic_oracle(storage):
+    """The 4096^2 throughput grid (the 256^2 pulse recipe, CBC-RELAX on four
+    sides) in the launch configuration the benchmark times.  After 30 steps
+    the disturbance has travelled ~35 cells and the stencils reach at most
+    90: the 256^2 window around the pulse must equal the oracle's 256^2
+    periodic run of the same pulse (the fields outside the window differ
+    from the periodic images by the Gaussian tail at 128 cells, e^-128), and
+    the boundary layers, which the disturbance has not reached, must still
+    hold the uniform state."""
+    n, w, x0, steps = 4096, 256, 1920, 30
+    cfg, f = W.pulse_d2q37(n, storage=storage, steps=steps)
+    rng = W.SplitMix64(0)                       # the recipe's centre offset
+    ox, oy = rng.uniform(-10.0, 10.0), rng.uniform(-10.0, 10.0)
+    centre = ((n - 1) / 2.0 + ox - x0, (n - 1) / 2.0 + oy - x0)
+    got = gpu_run(cfg, f, steps)
+    del f
+    win = [a[x0:x0 + w, x0:x0 + w] for a in got]
+    rcfg = W.run("D2Q37", w, w, cfg["tau"], storage="f64", steps=steps)
+    ref = oracle_run(rcfg, W.gaussian_pulse(w, w, 1e-3, 1e-3, 8.0, center=centre), steps,
+                     key="pulse4096window")
+    e = rel_errors(win, ref)
+    assert max(e.values()) < TOL[storage], (storage, e)
+    rho, ux, uy, T = got
+    band = np.ones_like(rho, dtype=bool)
+    band[3:-3, 3:-3] = False
+    assert np.abs(rho[band] - 1.0).max() < 1e-6 and np.abs(T[band] - 1.0).max() < 1e-6
+    assert max(np.abs(ux[band]).max(), np.abs(uy[band]).max()) < 1e-6
+
+
 def test_f16_storage_error_per_field(capsys):
     """FP16 storage (g / w in half precision, FP32 arithmetic): errors against
     the oracle are reported per field; they stay at the half-precision level."""

@@ -195,3 +195,30 @@ def test_pressure_relaxation_pulls_boundary_towards_target():
         rho, ux, uy, T = s.macros()
         dev.append(abs(cs2 * rho[0, -1] * T[0, -1] - P_inf))
     assert dev[-1] < dev[0] < cs2 * 0.01
+
+
+def test_window_of_a_large_cbc_run_equals_a_periodic_run():
+    """Locality (streaming moves a population by c_i per step, Sec. 2, and
+    no velocity component exceeds M, Sec. 3.3): until a
+    disturbance or its stencil reach leaves a window, a window of a larger
+    run with characteristic sides equals a periodic run of the window's
+    size, and the boundary layers keep the uniform state.  This is the
+    property the 4096^2 parity test relies on, here on a 512^2 grid."""
+    n, w, steps = 512, 256, 30
+    x0 = n // 2 - w // 2
+    cfg, f = W.pulse_d2q37(n, storage="f64", steps=steps)
+    rng = W.SplitMix64(0)
+    ox, oy = rng.uniform(-10.0, 10.0), rng.uniform(-10.0, 10.0)
+    centre = ((n - 1) / 2.0 + ox - x0, (n - 1) / 2.0 + oy - x0)
+    big = oracle.Sim(cfg).init(*f).step(steps).macros()
+    rcfg = W.run("D2Q37", w, w, cfg["tau"], storage="f64", steps=steps)
+    ref = oracle.Sim(rcfg).init(*W.gaussian_pulse(w, w, 1e-3, 1e-3, 8.0, center=centre)).step(steps).macros()
+    for a, b in zip(big, ref):
+        assert np.abs(a[x0:x0 + w, x0:x0 + w] - b).max() <= 1e-15
+    band = np.ones((n, n), dtype=bool)
+    band[3:-3, 3:-3] = False
+    rho, ux, uy, T = big
+    assert np.abs(rho[band] - 1.0).max() == 0.0 and np.abs(T[band] - 1.0).max() == 0.0
+    assert np.abs(ux[band]).max() == 0.0 and np.abs(uy[band]).max() == 0.0
+    # the window is not trivially uniform: the pulse has moved the fluid
+    assert np.abs(ref[1]).max() > 1e-4
