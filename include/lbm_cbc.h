@@ -129,11 +129,12 @@ int lbm_set_stream(lbm_handle* h, void* stream);
 int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
                     const double* uy, const double* T, int on_device);
 
-/* Advance n time steps (asynchronous on the handle's stream).  Per step, the
- * band kernel (the boundary solver) runs on the internal high-priority
- * stream while the bulk kernel (every bulk node) and the zero-gradient
- * copies run on the handle's stream.  The result is identical to phase 0
- * followed by phase 1. */
+/* Advance n time steps (asynchronous on the handle's stream).  Per step the
+ * band kernel (strip nodes and the boundary solver) is launched first and the
+ * bulk kernel (every bulk node) behind it on the same stream with
+ * programmatic stream serialization, so the two run side by side; the
+ * zero-gradient copies and the next step follow in stream order.  The result
+ * is identical to phase 0 followed by phase 1. */
 int lbm_step(lbm_handle* h, int n);
 
 /* Issue one phase of one step on the handle's stream, without overlap:

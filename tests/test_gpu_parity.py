@@ -305,6 +305,19 @@ def test_d2q37_pulse_4096_window_matches_periodic_oracle(storage):
     assert max(np.abs(ux[band]).max(), np.abs(uy[band]).max()) < 1e-6
 
 
+def test_d2q37_many_tiles_pulse_through_a_corner():
+    """400 x 300 with four CBC-RELAX sides: 42 band tiles, more four-CTA
+    clusters than fit on a GB300 at one per four SMs, so the band launch
+    runs in more than one wave; the pulse crosses the W and S sides and the
+    corner between them."""
+    cs2 = W.CS2["D2Q37"]
+    cfg = W.run("D2Q37", 400, 300, 0.8, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4,
+                alpha_T=0.5, beta_P=0.3, p_inf=[cs2 * 1.0001] * 4, steps=80)
+    f = W.gaussian_pulse(400, 300, 1e-3, 1e-3, 5.0, center=(24.3, 31.7))
+    assert_parity(cfg, f, 80, "f64", "many_tiles")
+    assert_parity(cfg, f, 80, "f32", "many_tiles")
+
+
 def test_f16_storage_error_per_field(capsys):
     """FP16 storage (g / w in half precision, FP32 arithmetic): errors against
     the oracle are reported per field; they stay at the half-precision level."""
