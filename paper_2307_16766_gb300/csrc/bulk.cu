@@ -137,47 +137,80 @@ __device__ __forceinline__ void collide_store(const Geom& G, const Offsets& O, S
     });
 }
 
+// Row segments per CTA of k_bulk: the tensor copies of every row are issued
+// at once (one transaction barrier each), so the copies of later rows land
+// while earlier rows are computed.  With two rows a CTA keeps 40 KB (FP32)
+// in flight with the registers of one row: five CTAs per SM, by shared
+// memory, carry more bytes in flight than seven one-row CTAs and leave the
+// registers of a band CTA free beside them, so the band kernel costs the
+// bulk kernel no CTAs when both share an SM.  FP64 storage (ALU-bound on
+// GB300, twice the staging) keeps one row.
+template <typename S>
+constexpr int bulk_rows() { return sizeof(S) == 8 ? 1 : 2; }
+
 template <int LAT, typename S>
 __global__ void __launch_bounds__(kBulkThreads)
     k_bulk(const __grid_constant__ Maps tm, Geom G, Offsets O, Region R,
            const S* __restrict__ fin, S* __restrict__ fout, int* status)
 {
+    constexpr int ROWS = bulk_rows<S>();
     using L = Lat<LAT>;
     using C = typename Store<S>::C;
     using BX = Stage<LAT, S>;
     constexpr int Q = L::Q;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long bar;
+    extern __shared__ __align__(128) unsigned char smem_raw[];   // ROWS x BX::TOTAL
+    __shared__ __align__(8) unsigned long long bar[ROWS];
     const int x0 = (R.x0 / kBulkThreads + blockIdx.x) * kBulkThreads;   // tiles aligned to 128
     const int x = x0 + threadIdx.x;
-    const int y = R.y0 + blockIdx.y;
+    const int yb = R.y0 + blockIdx.y * ROWS;
     const bool valid = x >= R.x0 && x < R.x1;
 
-    // Pull stream (Eq. lbe): g_i(x) = g*_i(x - c_i).  Segments whose sources
+    // Pull stream (Eq. lbe): g_i(x) = g*_i(x - c_i).  Rows whose sources
     // wrap around a periodic axis use plain loads; all others stage the 37
     // shifted source rows through shared memory with tensor copies.
-    const bool wrap = (G.pery && (y < L::M || y >= G.ny - L::M)) ||
-                      (G.perx && (x0 - L::M < 0 || x0 + kBulkThreads + L::M > G.nx));
-    C g[Q];
-    if (!wrap) {
-        S* sb = reinterpret_cast<S*>(smem_raw);
-        if (threadIdx.x == 0) {
-            const unsigned b = smem_u32(&bar);
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const bool xwrap = G.perx && (x0 - L::M < 0 || x0 + kBulkThreads + L::M > G.nx);
+    auto staged = [&](int y) {
+        return y < R.y1 && !xwrap && !(G.pery && (y < L::M || y >= G.ny - L::M));
+    };
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[r])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            if (!staged(yb + r)) continue;
+            const unsigned b = smem_u32(&bar[r]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                          ::"r"(b), "r"(BX::TX) : "memory");
-            issue_copies<LAT, S>(tm, smem_raw, x0, y, b, std::make_integer_sequence<int, L::NG>{});
+            issue_copies<LAT, S>(tm, smem_raw + r * BX::TOTAL, x0, yb + r, b,
+                                 std::make_integer_sequence<int, L::NG>{});
         }
-        __syncthreads();
-        if (!wait_tx(&bar, status) || !valid) return;
-        gather_staged<LAT, S, C>(g, sb, threadIdx.x, std::make_integer_sequence<int, Q>{});
-    } else {
-        if (!valid) return;
-        pull_plain<LAT, S, C>(G, O, fin, x, y, g);
     }
-    collide_store<LAT, S, C>(G, O, fout, x, y, g);
+    __syncthreads();
+#pragma unroll 1
+    for (int r = 0; r < ROWS; ++r) {
+        const int y = yb + r;
+        if (y >= R.y1) break;
+        C g[Q];
+        if (staged(y)) {
+            if (!wait_tx(&bar[r], status)) {
+                // timed out (status set): let the later rows' copies land
+                // (bounded) before the CTA's shared memory goes away
+                for (int q = r + 1; q < ROWS; ++q)
+                    if (staged(yb + q)) wait_tx(&bar[q], status);
+                return;
+            }
+            if (!valid) continue;
+            gather_staged<LAT, S, C>(g, reinterpret_cast<const S*>(smem_raw + r * BX::TOTAL), threadIdx.x,
+                                     std::make_integer_sequence<int, Q>{});
+        } else {
+            if (!valid) continue;
+            pull_plain<LAT, S, C>(G, O, fin, x, y, g);
+        }
+        collide_store<LAT, S, C>(G, O, fout, x, y, g);
+    }
 }
 
 // Persistent form of k_bulk for one or many grids of one lattice and
@@ -452,14 +485,16 @@ int bulk_t(const Geom& G, const Offsets& O, const Region& R, const CUtensorMap* 
     const int h = R.y1 - R.y0;
     if (R.x1 <= R.x0 || h <= 0) return 0;
     const int t0 = R.x0 / kBulkThreads, t1 = (R.x1 + kBulkThreads - 1) / kBulkThreads;
-    const size_t smem = Stage<LAT, S>::TOTAL;
+    constexpr int ROWS = bulk_rows<S>();
+    constexpr size_t smem = ROWS * Stage<LAT, S>::TOTAL;
+    static_assert(smem <= 48 * 1024, "bulk staging above the default dynamic shared memory");
     Maps tm;
     tm.m7 = tmaps[0];
     tm.m5 = tmaps[1];
     tm.m3 = tmaps[2];
     tm.m2 = tmaps[3];
     tm.m1 = tmaps[4];
-    dim3 blk(kBulkThreads), grd(t1 - t0, h);
+    dim3 blk(kBulkThreads), grd(t1 - t0, (h + ROWS - 1) / ROWS);
     return launch_ex(k_bulk<LAT, S>, grd, blk, smem, st, early, tm, G, O, R, static_cast<const S*>(fin),
                      static_cast<S*>(fout), status);
 }
