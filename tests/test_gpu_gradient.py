@@ -93,7 +93,34 @@ def test_fp32_gradient_against_fp64(capsys):
     with capsys.disabled():
         print("\nFP32 storage gradient vs FP64, rel. errors (alpha_T, beta_P, P_inf):",
               ["%.1e" % r for r in rel])
-    assert max(rel) < 1e-2
+    assert max(rel) < 1e-4
+
+
+def test_gradient_matches_gpu_central_differences_and_a_random_direction():
+    """Central differences of the loss from ordinary GPU steps (FP64
+    storage, h = 1e-4) per parameter, and along one seeded random direction
+    v of the parameters the directional difference equals dJ . v (the
+    forward-mode counterpart of an adjoint's dot-product test)."""
+    cfg, f = _case()
+    c = dict(cfg, storage="f64")
+    steps = 60
+    cs2 = W.CS2["D2Q37"]
+    J, dJ = lbm().pressure_loss_and_gradient(c, f, steps)
+
+    def loss(d):
+        q = dict(c, alpha_T=c["alpha_T"] + d[0], beta_P=c["beta_P"] + d[1],
+                 p_inf=[p + d[2] for p in c["p_inf"]])
+        return _loss_by_steps(q, f, steps)
+
+    hs = (1e-4, 1e-4, 1e-4 * cs2)
+    for k in range(3):
+        e = [0.0, 0.0, 0.0]
+        e[k] = hs[k]
+        fd = (loss(e) - loss([-x for x in e])) / (2 * hs[k])
+        assert abs(dJ[k] - fd) <= 1e-4 * abs(fd), (k, dJ[k], fd)
+    v = np.random.default_rng(5).standard_normal(3) * np.array(hs)
+    fd_v = (loss(v) - loss(-v)) / 2.0
+    assert abs(float(np.dot(dJ, v)) - fd_v) <= 1e-4 * abs(fd_v), (np.dot(dJ, v), fd_v)
 
 
 def test_autograd_function_returns_the_tangent_gradient():
