@@ -93,12 +93,16 @@ typedef struct lbm_cbc_params {
     double inflow[4];   /* rho, ux, uy, T imposed on LBM_SIDE_INFLOW sides              */
     int    storage;     /* enum lbm_storage                                             */
     double rho0;        /* reference density of the population shift                   */
+    double alpha_V;     /* relaxation of the viscous term towards 0 in Eq. CBC-Relax:
+                           L_i = T_i + V_i + alpha_T (T_inf - T_i) + alpha_V (0 - V_i)
+                           + beta_P (P - P_inf) on incoming waves (an extension; 0 is
+                           the paper's equation; other schemes ignore it)            */
 } lbm_cbc_params;
 
 typedef struct lbm_handle lbm_handle;
 
 /* Fill p with defaults: all sides periodic, CBC-RELAX, mesoscopic viscous
- * terms, equilibrium Dirichlet, alpha_T = beta_P = t_inf = 0,
+ * terms, equilibrium Dirichlet, alpha_T = beta_P = t_inf = alpha_V = 0,
  * p_inf = rho0 c_s^2 (set per lattice by lbm_create when left at 0),
  * inflow = (1, 0, 0, 1), F32 storage, rho0 = 1. */
 int lbm_params_default(lbm_cbc_params* p);

@@ -43,7 +43,7 @@ class SplitMix64:
 
 def run(lattice, nx, ny, tau, sides=("periodic",) * 4, schemes=("cbc",) * 4,
         viscous="meso", dirichlet="eq", alpha_T=0.0, beta_P=0.0, t_inf=0.0,
-        p_inf=None, inflow=None, rho0=1.0, storage="f64", steps=1, name=""):
+        p_inf=None, inflow=None, rho0=1.0, storage="f64", steps=1, name="", alpha_V=0.0):
     """A run description understood by both the CUDA binding and the oracle."""
     cs2 = CS2[lattice]
     return {
@@ -51,7 +51,7 @@ def run(lattice, nx, ny, tau, sides=("periodic",) * 4, schemes=("cbc",) * 4,
         "tau": float(tau), "rho0": float(rho0), "sides": list(sides),
         "schemes": list(schemes), "viscous": viscous,
         "dirichlet": dirichlet, "alpha_T": float(alpha_T), "beta_P": float(beta_P),
-        "t_inf": float(t_inf),
+        "t_inf": float(t_inf), "alpha_V": float(alpha_V),
         "p_inf": list(p_inf) if p_inf is not None else [cs2 * rho0] * 4,
         "inflow": list(inflow) if inflow is not None else [rho0, 0.0, 0.0, 1.0],
         "storage": storage, "steps": int(steps),

@@ -9,7 +9,8 @@ A run is described by a plain dict (see ``lbm_workloads``) with the keys
 (four of "periodic" | "cbc" | "inflow" | "zg", order W, E, S, N),
 ``schemes`` (four of "lodi" | "lodi_relax" | "cbc" | "cbc_relax"),
 ``viscous`` ("meso" | "fd" | "off"), ``dirichlet`` ("eq" | "neep" | "reg"), ``alpha_T``, ``beta_P``,
-``t_inf``, ``p_inf`` (four values) and ``inflow`` (rho, ux, uy, T).
+``t_inf``, ``p_inf`` (four values), ``inflow`` (rho, ux, uy, T) and ``alpha_V`` (the relaxation of
+the viscous term in Eq. CBC-Relax, 0 by default: the paper's equation).
 """
 import ctypes as C
 import os
@@ -33,6 +34,7 @@ class Params(C.Structure):
         ("viscous", C.c_int), ("dirichlet", C.c_int),
         ("alpha_T", C.c_double), ("beta_P", C.c_double), ("t_inf", C.c_double),
         ("p_inf", C.c_double * 4), ("inflow", C.c_double * 4),
+        ("alpha_V", C.c_double),
     ]
 
 
@@ -94,6 +96,7 @@ def make_params(cfg) -> Params:
     p.alpha_T = float(cfg.get("alpha_T", 0.0))
     p.beta_P = float(cfg.get("beta_P", 0.0))
     p.t_inf = float(cfg.get("t_inf", 0.0))
+    p.alpha_V = float(cfg.get("alpha_V", 0.0))
     cs2 = lattice_info(cfg["lattice"])["cs2"]
     pinf = cfg.get("p_inf", [cs2 * p.rho0] * 4)
     for i in range(4):

@@ -364,7 +364,10 @@ static void char_rhs(const lattice_t* L, const orc_params* P, const double Ul[4]
         case ORC_LODI:       Lb[i] = 0.0; break;
         case ORC_LODI_RELAX: Lb[i] = P->alpha_T * (P->t_inf - st) + relaxP; break;
         case ORC_CBC:        Lb[i] = st + sv; break;
-        default:             Lb[i] = st + sv + P->alpha_T * (P->t_inf - st) + relaxP; break;
+        default:             /* Eq. CBC-Relax, with the viscous term relaxed
+                                towards 0 at rate alpha_V (0: the paper's) */
+                             Lb[i] = st + sv + P->alpha_T * (P->t_inf - st) +
+                                     P->alpha_V * (0.0 - sv) + relaxP; break;
         }
     }
     int cbc = (scheme == ORC_CBC || scheme == ORC_CBC_RELAX);

@@ -46,6 +46,8 @@ typedef struct {
     double t_inf;      /* target transversal amplitude T^inf                   */
     double p_inf[4];   /* target pressure Z_inf = P_inf per side (lattice P)   */
     double inflow[4];  /* rho, ux, uy, T imposed on inflow sides               */
+    double alpha_V;    /* relaxation of the viscous term towards 0 in Eq.
+                          CBC-Relax (an extension; 0 is the paper's equation) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;

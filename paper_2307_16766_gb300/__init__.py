@@ -56,7 +56,7 @@ class LbmCbcParams(C.Structure):
         ("side", C.c_int * 4), ("scheme", C.c_int * 4), ("viscous", C.c_int),
         ("dirichlet", C.c_int), ("alpha_T", C.c_double), ("beta_P", C.c_double),
         ("t_inf", C.c_double), ("p_inf", C.c_double * 4), ("inflow", C.c_double * 4),
-        ("storage", C.c_int), ("rho0", C.c_double),
+        ("storage", C.c_int), ("rho0", C.c_double), ("alpha_V", C.c_double),
     ]
 
 
@@ -134,6 +134,7 @@ def params_from_run(cfg) -> LbmCbcParams:
     p.alpha_T = float(cfg.get("alpha_T", 0.0))
     p.beta_P = float(cfg.get("beta_P", 0.0))
     p.t_inf = float(cfg.get("t_inf", 0.0))
+    p.alpha_V = float(cfg.get("alpha_V", 0.0))
     for i, v in enumerate(cfg.get("p_inf", [0.0] * 4)):
         p.p_inf[i] = float(v)
     for i, v in enumerate(cfg.get("inflow", [1.0, 0.0, 0.0, 1.0])):

@@ -159,6 +159,11 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     if (!(p->rho0 > 0.0)) { err = "rho0 must be positive"; return LBM_ERR_ARG; }
     if (p->viscous < 0 || p->viscous > 2) { err = "unknown viscous mode"; return LBM_ERR_ARG; }
     if (p->dirichlet < 0 || p->dirichlet > 2) { err = "unknown Dirichlet mode"; return LBM_ERR_ARG; }
+    if (!std::isfinite(p->alpha_T) || !std::isfinite(p->beta_P) || !std::isfinite(p->t_inf) ||
+        !std::isfinite(p->alpha_V)) {
+        err = "relaxation parameters must be finite";
+        return LBM_ERR_ARG;
+    }
     for (int s = 0; s < 4; ++s) {
         if (p->side[s] < 0 || p->side[s] > 3) { err = fmt("unknown kind %d of side %d", p->side[s], s); return LBM_ERR_ARG; }
         if (p->scheme[s] < 0 || p->scheme[s] > 3) { err = fmt("unknown scheme of side %d", s); return LBM_ERR_ARG; }
@@ -488,6 +493,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     B.alpha_T = p->alpha_T;
     B.beta_P = p->beta_P;
     B.t_inf = p->t_inf;
+    B.alpha_V = p->alpha_V;
     B.kA = 1.0 / std::sqrt(8.0 * cs2);
     B.kB = std::sqrt(2.0 * cs2);
     B.kC = 1.0 / (2.0 * std::sqrt(2.0));

@@ -632,7 +632,12 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                     const double relaxP = acoustic ? B.beta_P * double(XP(5)) : 0.0;
                     if (scheme == SCH_LODI_RELAX) w = B.alpha_T * (B.t_inf - st) + relaxP;
                     else if (scheme == SCH_CBC) w = st + srow(Vr);
-                    else w = st + srow(Vr) + B.alpha_T * (B.t_inf - st) + relaxP;
+                    else {
+                        // Eq. CBC-Relax; the viscous term relaxed towards 0
+                        // at rate alpha_V (0: the paper's equation)
+                        const double sv = srow(Vr);
+                        w = st + sv + B.alpha_T * (B.t_inf - st) + B.alpha_V * (0.0 - sv) + relaxP;
+                    }
                 }
             }
             put_cluster(Xw + 4 * l + rank, w, &xbar[stage & 1]);
@@ -1020,6 +1025,7 @@ extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, doub
     B.alpha_T = p->alpha_T;
     B.beta_P = p->beta_P;
     B.t_inf = p->t_inf;
+    B.alpha_V = p->alpha_V;
     const double pinf = p->p_inf[side] != 0.0 ? p->p_inf[side] : cs2 * p->rho0;
     B.pdev[side] = pinf - cs2 * p->rho0;
     B.kA = 1.0 / std::sqrt(8.0 * cs2);

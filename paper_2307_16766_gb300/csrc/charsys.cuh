@@ -115,10 +115,11 @@ struct CharSys {
 
 // The relaxation parameters of the incoming waves (Eqs. LODI-Relax,
 // CBC-Relax): alpha_T on the transversal terms, beta_P on P - P_inf,
-// the target transversal term t_inf, and P_inf - c_s^2 rho0 per side.
+// the target transversal term t_inf, alpha_V on the viscous term (towards
+// 0; 0 is the paper's equation), and P_inf - c_s^2 rho0 per side.
 template <typename T>
 struct Relax {
-    T alpha_T, beta_P, t_inf;
+    T alpha_T, beta_P, t_inf, alpha_V;
     T pdev[4];
 };
 
@@ -129,6 +130,7 @@ __device__ __forceinline__ Relax<T> relax_of(const Band& B)
     P.alpha_T = T(B.alpha_T);
     P.beta_P = T(B.beta_P);
     P.t_inf = T(B.t_inf);
+    P.alpha_V = T(B.alpha_V);
 #pragma unroll
     for (int s = 0; s < 4; ++s) P.pdev[s] = T(B.pdev[s]);
     return P;
@@ -219,7 +221,7 @@ __device__ __forceinline__ void char_rhs(const CharSys<T>& C, const Relax<T>& P,
         if (scheme == SCH_LODI) w[i] = T(0);
         else if (scheme == SCH_LODI_RELAX) w[i] = P.alpha_T * (P.t_inf - st[i]) + relaxP;
         else if (scheme == SCH_CBC) w[i] = st[i] + sv[i];
-        else w[i] = st[i] + sv[i] + P.alpha_T * (P.t_inf - st[i]) + relaxP;
+        else w[i] = st[i] + sv[i] + P.alpha_T * (P.t_inf - st[i]) + P.alpha_V * (T(0) - sv[i]) + relaxP;
     }
     T o[4];
     if (TH) {

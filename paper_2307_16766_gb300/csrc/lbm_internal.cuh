@@ -536,6 +536,7 @@ struct Band {
     int viscous, dirichlet;
     int scheme[4];
     double alpha_T, beta_P, t_inf;
+    double alpha_V;  // relaxation of the viscous term towards 0 (Eq. CBC-Relax extended)
     double pdev[4];  // P_inf - c_s^2 rho0 per side
     double kA;       // 1 / sqrt(8 c_s^2)
     double kB;       // sqrt(2 c_s^2)

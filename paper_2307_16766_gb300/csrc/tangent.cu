@@ -340,6 +340,7 @@ int tl_step_t(const TLState& T, const Geom& G, const Export& E, const Band& B, c
     P.beta_P = R(B.beta_P);
     P.beta_P.d[1] = 1;                          // direction 1: beta_P
     P.t_inf = R(B.t_inf);
+    P.alpha_V = R(B.alpha_V);
     for (int s = 0; s < 4; ++s) {
         P.pdev[s] = R(B.pdev[s]);
         P.pdev[s].d[2] = 1;                     // direction 2: P_inf (all sides)

@@ -123,6 +123,21 @@ def test_d2q37_schemes(scheme, vis, dirichlet):
     assert_parity(cfg, f, 60)
 
 
+@pytest.mark.parametrize("lat,vis", [("D2Q37", "meso"), ("D2Q37", "fd"), ("D2Q17", "meso"), ("D2Q9", "fd")])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_viscous_relaxation_alpha_V(lat, vis, storage):
+    """CBC-RELAX with the viscous term relaxed towards 0 at rate alpha_V = 0.6
+    in the incoming amplitudes (an extension of Eq. CBC-Relax); a pulse that
+    crosses two sides and a corner."""
+    n, m = 41, 33
+    cs2 = W.CS2[lat]
+    cfg = W.run(lat, n, m, 0.75, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4, viscous=vis,
+                alpha_T=0.3, beta_P=0.2, p_inf=[cs2 * 1.0002] * 4, alpha_V=0.6)
+    f = W.gaussian_pulse(n, m, 1e-3, 1e-3 if lat != "D2Q9" else 0.0, 3.5, center=(9.4, 8.1),
+                         u=(0.01, 0.005))
+    assert_parity(cfg, f, 60, storage, "alpha_V_%s_%s" % (lat, vis))
+
+
 @pytest.mark.parametrize("sides", [("zg",) * 4, ("inflow", "zg", "zg", "zg"),
                                    ("periodic",) * 4, ("periodic", "periodic", "cbc", "cbc")])
 def test_d2q37_side_kinds(sides):

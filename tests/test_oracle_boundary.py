@@ -222,3 +222,33 @@ def test_window_of_a_large_cbc_run_equals_a_periodic_run():
     assert np.abs(ux[band]).max() == 0.0 and np.abs(uy[band]).max() == 0.0
     # the window is not trivially uniform: the pulse has moved the fluid
     assert np.abs(ref[1]).max() > 1e-4
+
+
+def test_viscous_relaxation_enters_cbc_relax_only():
+    """alpha_V (the viscous term relaxed towards 0 in Eq. CBC-Relax, an
+    extension) at 0 is the paper's equation bit for bit; it leaves LODI,
+    LODI-RELAX, CBC and runs without viscous terms bit for bit unchanged; in
+    CBC-RELAX with viscous terms it changes the result."""
+    cs2 = CS2["D2Q37"]
+    f = W.gaussian_pulse(40, 30, 1e-3, 1e-3, 3.0, center=(8.3, 11.6))
+
+    def run(**kw):
+        cfg = W.run("D2Q37", 40, 30, 0.8, sides=("cbc",) * 4, alpha_T=0.4, beta_P=0.2,
+                    p_inf=[cs2 * 1.0001] * 4, **kw)
+        return oracle.Sim(cfg).init(*f).step(40).macros()
+
+    def same(a, b):
+        return all(np.array_equal(x, y) for x, y in zip(a, b))
+
+    base = run(schemes=("cbc_relax",) * 4, viscous="meso")
+    cfg0 = W.run("D2Q37", 40, 30, 0.8, sides=("cbc",) * 4, alpha_T=0.4, beta_P=0.2,
+                 p_inf=[cs2 * 1.0001] * 4, schemes=("cbc_relax",) * 4, viscous="meso")
+    del cfg0["alpha_V"]
+    assert same(base, oracle.Sim(cfg0).init(*f).step(40).macros())
+    for sch in ("lodi", "lodi_relax", "cbc"):
+        assert same(run(schemes=(sch,) * 4, viscous="meso"),
+                    run(schemes=(sch,) * 4, viscous="meso", alpha_V=0.7)), sch
+    assert same(run(schemes=("cbc_relax",) * 4, viscous="off"),
+                run(schemes=("cbc_relax",) * 4, viscous="off", alpha_V=0.7))
+    moved = run(schemes=("cbc_relax",) * 4, viscous="meso", alpha_V=0.7)
+    assert max(np.abs(a - b).max() for a, b in zip(moved, base)) > 1e-9

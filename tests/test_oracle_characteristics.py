@@ -69,16 +69,21 @@ def cfg_for(lat, **kw):
 
 @pytest.mark.parametrize("lat", ["D2Q9", "D2Q37", "D2Q17"])
 @pytest.mark.parametrize("scheme", ["lodi", "lodi_relax", "cbc", "cbc_relax"])
-def test_char_rhs_projections(lat, scheme):
+@pytest.mark.parametrize("alpha_V", [0.0, 0.6])
+def test_char_rhs_projections(lat, scheme, alpha_V):
     """Eqs. PNR / LODI-Relax / CBC-PNR / CBC-Relax seen through independent
     left eigenvectors l_i of A:
       outgoing i:  l_i.k = -lambda_i l_i.dU_n + [CBC] l_i.(T + V)
       incoming i:  l_i.k = [LODI] 0, [CBC] 0,
-                           [RELAX, alpha=1, T_inf=0] l_i.T  (+ beta dP term)."""
+                           [RELAX, alpha=1, T_inf=0] l_i.T  (+ beta dP term)
+                           + [CBC-RELAX] alpha_V l_i.V: the viscous term
+                           relaxed towards 0 at rate alpha_V in the incoming
+                           amplitude (0: the paper's equation) leaves that
+                           share of V in the incoming characteristic."""
     rng = np.random.default_rng(5)
     n = 3 if lat == "D2Q9" else 4
     alpha = 1.0 if scheme.endswith("relax") else 0.0
-    cfg = cfg_for(lat, alpha_T=alpha, beta_P=0.0)
+    cfg = cfg_for(lat, alpha_T=alpha, beta_P=0.0, alpha_V=alpha_V)
     cbc = scheme.startswith("cbc")
     for trial in range(30):
         Ul = rand_local(rng, lat)
@@ -103,6 +108,8 @@ def test_char_rhs_projections(lat, scheme):
                 want = 0.0
                 if alpha == 1.0:
                     want = li @ TT[:n]
+                if scheme == "cbc_relax":
+                    want += alpha_V * (li @ VV[:n])
             else:
                 assert any(abs(wi - v) < 1e-12 for v in outgoing_vals)
                 want = -wi * (li @ dUn[:n]) + ((li @ (TT[:n] + VV[:n])) if cbc else 0.0)
