@@ -190,40 +190,49 @@ void lbm_destroy(lbm_handle* h);
 /* Gradients with respect to the relaxation parameters                    */
 /* ---------------------------------------------------------------------- */
 
-/* The incoming-wave relaxation of Eqs. LODI-Relax and CBC-Relax has three
- * free parameters the paper leaves to be chosen by hand: alpha_T (the
- * transversal terms), beta_P (P - P_inf on the acoustic waves) and the
- * target pressure P_inf.  These calls advance a handle by tangent-linear
- * steps: the step of the method (strip macros, RK4 of the characteristic
- * boundary state, equilibrium Dirichlet write, pull-stream + BGK collide)
- * evaluated together with its derivatives along the three parameters, and
- * accumulate the pressure loss
+/* The incoming-wave relaxation of Eqs. LODI-Relax and CBC-Relax has free
+ * parameters the paper leaves to be chosen by hand: alpha_T (the transversal
+ * terms), beta_P (P - P_inf on the acoustic waves), the target pressure P_inf
+ * and the target transversal amplitude t_inf, and this library adds alpha_V
+ * (the viscous term's relaxation towards 0).  These calls advance a handle by
+ * tangent-linear steps: the step of the method (strip macros, RK4 of the
+ * characteristic boundary state, equilibrium Dirichlet write, pull-stream +
+ * BGK collide) evaluated together with its derivatives along three
+ * directions in theta = (alpha_T, beta_P, P_inf, alpha_V, t_inf) (P_inf
+ * moved on every characteristic side together), and accumulate the pressure
+ * loss
  *     J = sum over the steps and over the nodes off the M boundary layers of
  *         (P - c_s^2 rho0 - dP_ref)^2,   P = rho c_s^2 T (D2Q9: rho c_s^2)
- * with dJ/d(alpha_T, beta_P, P_inf) (P_inf moved on every characteristic
- * side together).  Derivatives are exact up to rounding (forward mode), in
- * FP64 for the boundary state; populations and their derivatives are held
- * in the handle's storage precision.
+ * with its three directional derivatives.  Derivatives are exact up to
+ * rounding (forward mode), in FP64 for the boundary state; populations and
+ * their derivatives are held in the handle's storage precision.
  *
- * Supported: FP64 or FP32 storage, viscous = LBM_VISCOUS_OFF, the
- * equilibrium Dirichlet condition, characteristic and periodic sides
- * (otherwise LBM_ERR_ARG).  Gradient steps use the handle's stream and
+ * Supported: FP64 or FP32 storage, viscous = LBM_VISCOUS_OFF or
+ * LBM_VISCOUS_FD (the "-FD" vector, frozen at time t as in the ordinary
+ * step), the equilibrium Dirichlet condition, characteristic and periodic
+ * sides (otherwise LBM_ERR_ARG).  Gradient steps use the handle's stream and
  * steps counter; afterwards the handle's ordinary step state (strips,
  * boundary state) is behind: lbm_step, lbm_step_phase, lbm_get_state and
  * batch steps return LBM_ERR_STATE until lbm_init_fields or lbm_set_state.
  * lbm_get_macros reads the populations the gradient steps produced. */
 
 /* Allocate the derivative state (cudaMalloc: about 3 x the populations),
- * zero the derivatives and the sums, starting from the current state. */
+ * zero the derivatives and the sums, starting from the current state; the
+ * three directions are d/dalpha_T, d/dbeta_P and d/dP_inf. */
 int lbm_grad_begin(lbm_handle* h);
+
+/* As lbm_grad_begin, with direction k = dirs[5 k .. 5 k + 4], a vector in
+ * theta = (alpha_T, beta_P, P_inf, alpha_V, t_inf) (host array of 15
+ * finite doubles, row-major [3][5]; NULL = the first three unit vectors). */
+int lbm_grad_begin_along(lbm_handle* h, const double* dirs);
 
 /* n tangent-linear steps (asynchronous).  dP_ref: NULL (reference 0) or a
  * device array holding, for step i of this call, the [ny][nx] doubles of
  * P_ref - c_s^2 rho0 at dP_ref + i * ref_stride. */
 int lbm_grad_step(lbm_handle* h, int n, const double* dP_ref, long long ref_stride);
 
-/* J and dJ[0..2] = dJ/d(alpha_T, beta_P, P_inf) accumulated since
- * lbm_grad_begin (synchronises the handle's stream). */
+/* J and dJ[k] = the derivative of J along direction k (k = 0, 1, 2)
+ * accumulated since lbm_grad_begin (synchronises the handle's stream). */
 int lbm_grad_result(lbm_handle* h, double* J, double* dJ);
 
 /* Free the derivative state.  NULL-safe on a handle without one. */

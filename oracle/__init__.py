@@ -265,23 +265,26 @@ def pressure_loss(cfg, fields, steps, dP_ref=None):
     return J
 
 
-def with_relaxation(cfg, alpha_T, beta_P, p_inf):
+def _value_of(cfg, name):
+    return cfg["p_inf"][0] if name == "p_inf" else cfg.get(name, 0.0)
+
+
+def _with_value(cfg, name, v):
     c = dict(cfg)
-    c["alpha_T"], c["beta_P"], c["p_inf"] = float(alpha_T), float(beta_P), [float(p_inf)] * 4
+    c[name] = [float(v)] * 4 if name == "p_inf" else float(v)
     return c
 
 
-def pressure_loss_fd_gradient(cfg, fields, steps, h=(1e-4, 1e-4, 1e-4), dP_ref=None):
-    """Central differences of pressure_loss in (alpha_T, beta_P, P_inf),
-    P_inf moved on every side together (cfg's p_inf must be equal on all
-    sides)."""
-    th = [cfg["alpha_T"], cfg["beta_P"], cfg["p_inf"][0]]
+def pressure_loss_fd_gradient(cfg, fields, steps, h=(1e-4, 1e-4, 1e-4), dP_ref=None,
+                              params=("alpha_T", "beta_P", "p_inf")):
+    """Central differences of pressure_loss in the named relaxation
+    parameters (any of alpha_T, beta_P, p_inf, alpha_V, t_inf), step h[k]
+    for params[k]; p_inf is moved on every side together (cfg's p_inf must
+    be equal on all sides)."""
     g = []
-    for k in range(3):
-        up, dn = list(th), list(th)
-        up[k] += h[k]
-        dn[k] -= h[k]
-        Jp = pressure_loss(with_relaxation(cfg, *up), fields, steps, dP_ref)
-        Jm = pressure_loss(with_relaxation(cfg, *dn), fields, steps, dP_ref)
-        g.append((Jp - Jm) / (2.0 * h[k]))
+    for name, hk in zip(params, h):
+        v = _value_of(cfg, name)
+        Jp = pressure_loss(_with_value(cfg, name, v + hk), fields, steps, dP_ref)
+        Jm = pressure_loss(_with_value(cfg, name, v - hk), fields, steps, dP_ref)
+        g.append((Jp - Jm) / (2.0 * hk))
     return g

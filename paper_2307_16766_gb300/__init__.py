@@ -94,6 +94,7 @@ def lib():
             "lbm_cbc_side_step_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, pp,
                                                     vp, vp, vp, vp, vp]),
             "lbm_grad_begin": (C.c_int, [vp]),
+            "lbm_grad_begin_along": (C.c_int, [vp, C.POINTER(C.c_double)]),
             "lbm_grad_step": (C.c_int, [vp, C.c_int, vp, C.c_longlong]),
             "lbm_grad_result": (C.c_int, [vp, dp, dp]),
             "lbm_grad_end": (C.c_int, [vp]),
@@ -271,12 +272,20 @@ def lbm_grad_begin(h):
     _check(lib().lbm_grad_begin(h), h)
 
 
+def lbm_grad_begin_along(h, dirs):
+    """dirs: 3 x 5 numbers, direction k over THETA."""
+    flat = [float(v) for row in dirs for v in row]
+    if len(flat) != 15:
+        raise ValueError("directions must be 3 x 5")
+    _check(lib().lbm_grad_begin_along(h, (C.c_double * 15)(*flat)), h)
+
+
 def lbm_grad_step(h, n, dP_ref_ptr=None, ref_stride=0):
     _check(lib().lbm_grad_step(h, n, dP_ref_ptr, ref_stride), h)
 
 
 def lbm_grad_result(h):
-    """(J, [dJ/dalpha_T, dJ/dbeta_P, dJ/dP_inf])"""
+    """(J, [the derivatives along the three directions])"""
     J = C.c_double()
     dJ = (C.c_double * 3)()
     _check(lib().lbm_grad_result(h, C.byref(J), dJ), h)
@@ -467,15 +476,25 @@ class Batch:
 
 # ------------------------------------------------------------- gradients ---
 
-def pressure_loss_and_gradient(cfg, fields, steps, dP_ref=None, device=None):
+THETA = ("alpha_T", "beta_P", "p_inf", "alpha_V", "t_inf")
+"""The relaxation parameters gradient steps differentiate, in the order of
+lbm_grad_begin_along's directions (p_inf: every characteristic side)."""
+
+
+def pressure_loss_and_gradient(cfg, fields, steps, dP_ref=None, device=None, directions=None):
     """J = sum over `steps` steps and the nodes off the boundary layers of
-    (P - c_s^2 rho0 - dP_ref)^2, and dJ/d(alpha_T, beta_P, P_inf), by
-    tangent-linear steps of a fresh solver (lbm_grad_*).  dP_ref: None or
-    a CUDA float64 tensor [steps, ny, nx].  Returns (J, [3 derivatives])."""
+    (P - c_s^2 rho0 - dP_ref)^2, and its derivatives along three directions
+    in THETA (default: d/dalpha_T, d/dbeta_P, d/dP_inf), by tangent-linear
+    steps of a fresh solver (lbm_grad_*).  dP_ref: None or a CUDA float64
+    tensor [steps, ny, nx]; directions: None or 3 x 5 numbers.  Returns
+    (J, [3 derivatives])."""
     import torch
     sim = Simulation(cfg, device=device).init_fields(*fields)
     try:
-        lbm_grad_begin(sim.handle)
+        if directions is None:
+            lbm_grad_begin(sim.handle)
+        else:
+            lbm_grad_begin_along(sim.handle, directions)
         if dP_ref is None:
             lbm_grad_step(sim.handle, steps)
         else:
@@ -490,32 +509,53 @@ def pressure_loss_and_gradient(cfg, fields, steps, dP_ref=None, device=None):
     return J, dJ
 
 
-def _with_theta(cfg, theta):
+def with_parameters(cfg, params, values):
+    """A copy of cfg with the named THETA parameters set (p_inf on every
+    side)."""
     c = dict(cfg)
-    c["alpha_T"], c["beta_P"] = float(theta[0]), float(theta[1])
-    c["p_inf"] = [float(theta[2])] * 4
+    for name, v in zip(params, values):
+        if name not in THETA:
+            raise ValueError("unknown relaxation parameter %r" % (name,))
+        c[name] = [float(v)] * 4 if name == "p_inf" else float(v)
     return c
+
+
+def pressure_loss_gradient_in(cfg, fields, steps, params, dP_ref=None, device=None):
+    """(J, dJ/dparams) for any of the THETA parameters: one run of gradient
+    steps per three of them."""
+    params = list(params)
+    grads = []
+    J = None
+    for g0 in range(0, len(params), 3):
+        dirs = [[0.0] * 5 for _ in range(3)]
+        chunk = params[g0:g0 + 3]
+        for k, name in enumerate(chunk):
+            dirs[k][THETA.index(name)] = 1.0
+        J, dJ = pressure_loss_and_gradient(cfg, fields, steps, dP_ref, device, dirs)
+        grads += dJ[:len(chunk)]
+    return J, grads
 
 
 def _make_cbc_loss():
     import torch
 
     class CBCLoss(torch.autograd.Function):
-        """J(theta) for theta = (alpha_T, beta_P, P_inf) as a differentiable
-        function: forward runs the tangent-linear steps (which give J and
-        dJ/dtheta together), backward scales the stored derivatives."""
+        """J(theta) for theta over named THETA parameters as a
+        differentiable function: forward runs the tangent-linear steps
+        (which give J and its derivatives together), backward scales the
+        stored derivatives."""
 
         @staticmethod
-        def forward(ctx, theta, cfg, fields, steps, dP_ref=None):
+        def forward(ctx, theta, cfg, fields, steps, dP_ref, params):
             th = theta.detach().cpu().double().tolist()
-            J, dJ = pressure_loss_and_gradient(_with_theta(cfg, th), fields, steps, dP_ref)
+            J, dJ = pressure_loss_gradient_in(with_parameters(cfg, params, th), fields, steps, params, dP_ref)
             ctx.save_for_backward(torch.tensor(dJ, dtype=theta.dtype, device=theta.device))
             return torch.tensor(J, dtype=theta.dtype, device=theta.device)
 
         @staticmethod
         def backward(ctx, grad_out):
             (dJ,) = ctx.saved_tensors
-            return grad_out * dJ, None, None, None, None
+            return grad_out * dJ, None, None, None, None, None
 
     return CBCLoss
 
@@ -523,10 +563,10 @@ def _make_cbc_loss():
 _CBCLoss = None
 
 
-def cbc_loss(theta, cfg, fields, steps, dP_ref=None):
-    """Differentiable pressure loss J(alpha_T, beta_P, P_inf) (torch
-    autograd; theta a 3-element tensor)."""
+def cbc_loss(theta, cfg, fields, steps, dP_ref=None, params=("alpha_T", "beta_P", "p_inf")):
+    """Differentiable pressure loss J(theta) (torch autograd), theta a tensor
+    of the named THETA parameters (default alpha_T, beta_P, P_inf)."""
     global _CBCLoss
     if _CBCLoss is None:
         _CBCLoss = _make_cbc_loss()
-    return _CBCLoss.apply(theta, cfg, fields, steps, dP_ref)
+    return _CBCLoss.apply(theta, cfg, fields, steps, dP_ref, tuple(params))

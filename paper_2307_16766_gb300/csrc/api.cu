@@ -1122,17 +1122,22 @@ long long lbm_steps_done(const lbm_handle* h) { return h ? h->steps : -1; }
 // Gradients with respect to the relaxation parameters (tangent-linear steps)
 // ---------------------------------------------------------------------------
 
-int lbm_grad_begin(lbm_handle* h)
+int lbm_grad_begin(lbm_handle* h) { return lbm_grad_begin_along(h, nullptr); }
+
+int lbm_grad_begin_along(lbm_handle* h, const double* dirs)
 {
     if (!h) return LBM_ERR_ARG;
+    if (dirs)
+        for (int i = 0; i < 3 * kTLParams; ++i)
+            if (!std::isfinite(dirs[i])) { h->err = "gradient directions must be finite"; return LBM_ERR_ARG; }
     if (!h->initialized || h->bulk_pending) { h->err = "lbm_grad_begin before a complete step state"; return LBM_ERR_STATE; }
     if (h->tl_mem) { h->err = "gradient steps already begun"; return LBM_ERR_STATE; }
     if (h->storage != LBM_F64 && h->storage != LBM_F32) {
         h->err = "gradient steps need FP64 or FP32 storage";
         return LBM_ERR_ARG;
     }
-    if (h->B.n_unk > 0 && (h->B.viscous != VIS_OFF || h->B.dirichlet != 0)) {
-        h->err = "gradient steps need viscous = off and the equilibrium Dirichlet condition";
+    if (h->B.n_unk > 0 && (h->B.viscous == VIS_MESO || h->B.dirichlet != 0)) {
+        h->err = "gradient steps need viscous = off or fd and the equilibrium Dirichlet condition";
         return LBM_ERR_ARG;
     }
     if (h->n_inflow > 0 || h->B.n_zg > 0) {
@@ -1147,7 +1152,7 @@ int lbm_grad_begin(lbm_handle* h)
     auto take = [&](size_t b) { const size_t at = o; o = align_up(o + b); return at; };
     const size_t o_t0 = take(tbytes), o_t1 = take(tbytes), o_st = take(sbytes), o_st1 = take(sbytes),
                  o_ud = take(ubytes), o_uf = take(ubytes), o_ya = take(ubytes), o_yb = take(ubytes),
-                 o_acc = take(ubytes),
+                 o_acc = take(ubytes), o_vv = take(ubytes),
                  o_mask = take((size_t)std::max(1, h->B.n_unk) * sizeof(int)), o_sums = take(4 * sizeof(double));
     void* mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, o);
@@ -1163,7 +1168,10 @@ int lbm_grad_begin(lbm_handle* h)
     T.Yb = at<char>(mem, o_yb);
     T.acc = at<char>(mem, o_acc);
     T.mask = at<int>(mem, o_mask);
+    T.Vv = at<char>(mem, o_vv);
     T.sums = at<double>(mem, o_sums);
+    for (int k = 0; k < 3; ++k)
+        for (int q = 0; q < kTLParams; ++q) T.dirs[k][q] = dirs ? dirs[k * kTLParams + q] : (q == k ? 1.0 : 0.0);
     h->tl_mem = mem;
     // the initial fields do not depend on the parameters: zero derivatives
     e = cudaMemsetAsync(mem, 0, o, h->stream);

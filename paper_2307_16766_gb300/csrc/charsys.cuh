@@ -292,42 +292,43 @@ __device__ void vis_meso(const Geom& G, const double* SU, const double* SN, cons
 }
 
 // "-FD" form (Sec. 4.2) at layer j from the macros of time t: 4-point
-// one-sided second derivative at j = M, 3-point central elsewhere.
-template <bool TH>
-__device__ void vis_fd(const Geom& G, const Band& B, const Ctx& X0, const UDesc& D, int u,
-                       double cs2, double* V)
+// one-sided second derivative at j = M, 3-point central elsewhere.  In the
+// context's arithmetic R (FP64, or Dual numbers in the tangent-linear step).
+template <bool TH, typename R>
+__device__ void vis_fd(const Geom& G, const Band& B, const CtxT<R>& X0, const UDesc& D, int u,
+                       double cs2, R* V)
 {
     const int kind = D.kind;
-    double U[4], A[4], Bv[4], Cv[4], Tp[4], Tm[4], dnn[4], d1n[4];
-    fetch_local(X0, u, kind, 0.0, U);
-    fetch_local(X0, D.nb[1], kind, 0.0, Bv);
-    fetch_local(X0, D.nb[4], kind, 0.0, Tp);
-    fetch_local(X0, D.nb[5], kind, 0.0, Tm);
+    R U[4], A[4], Bv[4], Cv[4], Tp[4], Tm[4], dnn[4], d1n[4];
+    fetch_local(X0, u, kind, R(0), U);
+    fetch_local(X0, D.nb[1], kind, R(0), Bv);
+    fetch_local(X0, D.nb[4], kind, R(0), Tp);
+    fetch_local(X0, D.nb[5], kind, R(0), Tm);
     if (D.j == B.M) {
-        fetch_local(X0, D.nb[2], kind, 0.0, A);
-        fetch_local(X0, D.nb[3], kind, 0.0, Cv);
+        fetch_local(X0, D.nb[2], kind, R(0), A);
+        fetch_local(X0, D.nb[3], kind, R(0), Cv);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            dnn[m] = 2.0 * U[m] - 5.0 * Bv[m] + 4.0 * A[m] - Cv[m];
-            d1n[m] = 0.5 * (3.0 * U[m] - 4.0 * Bv[m] + A[m]);
+            dnn[m] = R(2) * U[m] - R(5) * Bv[m] + R(4) * A[m] - Cv[m];
+            d1n[m] = R(0.5) * (R(3) * U[m] - R(4) * Bv[m] + A[m]);
         }
     } else {
-        fetch_local(X0, D.nb[0], kind, 0.0, A);
+        fetch_local(X0, D.nb[0], kind, R(0), A);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            dnn[m] = A[m] - 2.0 * U[m] + Bv[m];
-            d1n[m] = 0.5 * (A[m] - Bv[m]);
+            dnn[m] = A[m] - R(2) * U[m] + Bv[m];
+            d1n[m] = R(0.5) * (A[m] - Bv[m]);
         }
     }
-    const double nu = (G.tau - 0.5) * cs2;
-    V[0] = 0.0;
-    V[1] = nu * (dnn[1] + (Tp[1] - 2.0 * U[1] + Tm[1]));
-    V[2] = nu * (dnn[2] + (Tp[2] - 2.0 * U[2] + Tm[2]));
-    V[3] = 0.0;
+    const R nu = R((G.tau - 0.5) * cs2);
+    V[0] = R(0);
+    V[1] = nu * (dnn[1] + (Tp[1] - R(2) * U[1] + Tm[1]));
+    V[2] = nu * (dnn[2] + (Tp[2] - R(2) * U[2] + Tm[2]));
+    V[3] = R(0);
     if (TH) {
-        const double d1t1 = 0.5 * (Tp[1] - Tm[1]), d1t2 = 0.5 * (Tp[2] - Tm[2]);
-        const double e1 = d1n[1] - d1t2, e2 = d1n[2] + d1t1;
-        V[3] = 2.0 * nu * (dnn[3] + (Tp[3] - 2.0 * U[3] + Tm[3])) + nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
+        const R d1t1 = R(0.5) * (Tp[1] - Tm[1]), d1t2 = R(0.5) * (Tp[2] - Tm[2]);
+        const R e1 = d1n[1] - d1t2, e2 = d1n[2] + d1t1;
+        V[3] = R(2) * nu * (dnn[3] + (Tp[3] - R(2) * U[3] + Tm[3])) + nu * R(1.0 / cs2) * (e1 * e1 + e2 * e2);
     }
 }
 

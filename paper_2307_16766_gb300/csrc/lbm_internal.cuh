@@ -642,8 +642,11 @@ int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad);
 int launch_zg(int lat, int storage, const Geom& G, const Band& B, void* fnew, cudaStream_t st);
 
 // State of the tangent-linear step (tangent.cu): derivatives along three
-// directions (alpha_T, beta_P, P_inf).  Arrays are sized with
+// directions in the space of the relaxation parameters theta = (alpha_T,
+// beta_P, P_inf (all sides), alpha_V, t_inf): direction k is dirs[k][.]
+// (by default the first three unit vectors).  Arrays are sized with
 // tl_dual_bytes() per value (the largest element type used).
+constexpr int kTLParams = 5;
 struct TLState {
     void* t[2];      // derivative populations per parity: [3][Q][plane], storage type
     void* strip[2];  // strip macros per parity (t, then t + 1): [nslots][4], stage type
@@ -652,7 +655,9 @@ struct TLState {
     void *Ya, *Yb;   // RK4 stage values: [n_unk][4], stage type
     void* acc;       // RK4 sum: [n_unk][4], as Ud
     int* mask;       // incoming waves at t: [n_unk]
-    double* sums;    // J, dJ/dalpha_T, dJ/dbeta_P, dJ/dP_inf
+    void* Vv;        // "-FD" viscous vector of time t: [n_unk][4], stage type
+    double* sums;    // J and its derivatives along the three directions
+    double dirs[3][kTLParams];
 };
 size_t tl_dual_bytes();
 // One tangent-linear step f[par] -> f[par ^ 1] (FP64 or FP32 storage; the

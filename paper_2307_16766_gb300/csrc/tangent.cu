@@ -2,8 +2,9 @@
 // same strip macros, characteristic boundary solver, Dirichlet write and
 // fused pull-stream + BGK collide) evaluated on Dual numbers, so that the
 // populations, the boundary state and a pressure loss carry their
-// derivatives with respect to the three parameters of the incoming-wave
-// relaxation (Eqs. LODI-Relax, CBC-Relax): alpha_T, beta_P and P_inf.
+// derivatives along three directions in the space of the incoming-wave
+// relaxation parameters (Eqs. LODI-Relax, CBC-Relax): alpha_T, beta_P, P_inf,
+// alpha_V (the viscous term's relaxation) and t_inf.
 //
 //   k_tl_strip     macros of the strip nodes at t (the first step's seed)
 //   k_tl_bulk      (first) pull-stream + BGK collide of every bulk node, one
@@ -18,7 +19,8 @@
 //                  (equilibrium Dirichlet condition)
 //
 // Supported: FP64 and FP32 storage, equilibrium Dirichlet condition, no
-// viscous vector, characteristic and periodic sides (checked on the host).
+// viscous vector or its "-FD" form (frozen at time t, as in the ordinary
+// step), characteristic and periodic sides (checked on the host).
 #include "charsys.cuh"
 
 #include <type_traits>
@@ -158,7 +160,7 @@ __global__ void k_tl_strip(Geom G, Export E, const S* __restrict__ f, const S* _
 template <int LAT, typename S>
 __global__ void k_tl_stage(Geom G, Band B, Relax<TB<S>> P, const TB<S>* __restrict__ St,
                            const TB<S>* __restrict__ St1, TS* Ud, TB<S>* Uf, TB<S>* Ya, TB<S>* Yb,
-                           TS* acc, int* mask, int stage)
+                           TS* acc, int* mask, TB<S>* Vv, int stage)
 {
     using Lt = Lat<LAT>;
     using T = TB<S>;
@@ -174,7 +176,20 @@ __global__ void k_tl_stage(Geom G, Band B, Relax<TB<S>> P, const TB<S>* __restri
     X.St1 = St1;
     X.frac = stage == 0 ? T(0) : (stage == 3 ? T(1) : T(0.5));
     T* Yout = stage == 1 ? Yb : Ya;
-    const T V[4] = {T(0), T(0), T(0), T(0)};
+    // "-FD" viscous vector: from the macros of time t at stage 0, then
+    // frozen for the later stages (corners take none)
+    T V[4] = {T(0), T(0), T(0), T(0)};
+    if (B.viscous == VIS_FD && D.kind < 4) {
+        T* Vu = Vv + 4LL * u;
+        if (stage == 0) {
+            vis_fd<Lt::THERMAL>(G, B, X, D, u, Lt::CS2, V);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) Vu[m] = V[m];
+        } else {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) V[m] = Vu[m];
+        }
+    }
     int mk;
     if (stage == 0) {
         T Ul[4];
@@ -334,16 +349,20 @@ int tl_step_t(const TLState& T, const Geom& G, const Export& E, const Band& B, c
     S* to = static_cast<S*>(T.t[par ^ 1]);
     R* St = static_cast<R*>(T.strip[par]);
     R* St1 = static_cast<R*>(T.strip[par ^ 1]);
+    // the parameters as Dual numbers seeded with the three directions
     Relax<R> P;
     P.alpha_T = R(B.alpha_T);
-    P.alpha_T.d[0] = 1;                         // direction 0: alpha_T
     P.beta_P = R(B.beta_P);
-    P.beta_P.d[1] = 1;                          // direction 1: beta_P
-    P.t_inf = R(B.t_inf);
     P.alpha_V = R(B.alpha_V);
-    for (int s = 0; s < 4; ++s) {
-        P.pdev[s] = R(B.pdev[s]);
-        P.pdev[s].d[2] = 1;                     // direction 2: P_inf (all sides)
+    P.t_inf = R(B.t_inf);
+    for (int s = 0; s < 4; ++s) P.pdev[s] = R(B.pdev[s]);
+    using Ed = typename Store<S>::C;
+    for (int k = 0; k < kTD; ++k) {
+        P.alpha_T.d[k] = Ed(T.dirs[k][0]);
+        P.beta_P.d[k] = Ed(T.dirs[k][1]);
+        for (int s = 0; s < 4; ++s) P.pdev[s].d[k] = Ed(T.dirs[k][2]);
+        P.alpha_V.d[k] = Ed(T.dirs[k][3]);
+        P.t_inf.d[k] = Ed(T.dirs[k][4]);
     }
     // RK4 stage 0 (time t only) and, beside it by programmatic launch, the
     // bulk pass, which also gives the strip macros of t + 1 that stages 1-3
@@ -353,7 +372,7 @@ int tl_step_t(const TLState& T, const Geom& G, const Export& E, const Band& B, c
         return launch_ex(k_tl_stage<LAT, S>, dim3(nb), dim3(128), 0, st, early, G, B, P,
                          static_cast<const R*>(St), static_cast<const R*>(St1), static_cast<TS*>(T.Ud),
                          static_cast<R*>(T.Uf), static_cast<R*>(T.Ya), static_cast<R*>(T.Yb),
-                         static_cast<TS*>(T.acc), T.mask, k);
+                         static_cast<TS*>(T.acc), T.mask, static_cast<R*>(T.Vv), k);
     };
     bool first = true;
     if (B.n_unk > 0) {

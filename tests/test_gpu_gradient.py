@@ -1,6 +1,6 @@
 """Gradients of the pressure loss with respect to the relaxation parameters
-(alpha_T, beta_P, P_inf) by tangent-linear steps on the GPU, against the
-FP64 oracle: its loss, and its central differences (h = 1e-4)."""
+(alpha_T, beta_P, P_inf, alpha_V, t_inf) by tangent-linear steps on the
+GPU, against the FP64 oracle: its loss, and its central differences."""
 import numpy as np
 import pytest
 
@@ -123,6 +123,37 @@ def test_gradient_matches_gpu_central_differences_and_a_random_direction():
     assert abs(float(np.dot(dJ, v)) - fd_v) <= 1e-4 * abs(fd_v), (np.dot(dJ, v), fd_v)
 
 
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q37"])
+def test_gradient_in_alpha_V_and_t_inf_with_fd_viscous_terms(lat):
+    """With the "-FD" viscous vector (frozen at t) in CBC-RELAX: dJ/d(alpha_T,
+    alpha_V, t_inf) against the oracle's central differences."""
+    cfg, f = _case(lat)
+    cfg = dict(cfg, viscous="fd", alpha_V=0.4, t_inf=0.0)
+    params = ("alpha_T", "alpha_V", "t_inf")
+    steps = 60
+    J, dJ = lbm().pressure_loss_gradient_in(dict(cfg, storage="f64"), f, steps, params)
+    Jo = oracle.pressure_loss(cfg, f, steps)
+    assert abs(J - Jo) <= 1e-10 * Jo, (J, Jo)
+    fd = oracle.pressure_loss_fd_gradient(cfg, f, steps, (1e-4, 1e-4, 1e-7), params=params)
+    for k in range(3):
+        assert fd[k] != 0.0
+        assert abs(dJ[k] - fd[k]) <= 1e-4 * abs(fd[k]), (k, dJ, fd)
+
+
+def test_gradient_directions_combine_linearly():
+    """A direction that mixes parameters gives the same combination of the
+    unit-direction derivatives (forward mode is linear in the seed)."""
+    cfg, f = _case()
+    cfg = dict(cfg, viscous="fd", alpha_V=0.2, storage="f64")
+    m = lbm()
+    _, unit = m.pressure_loss_gradient_in(cfg, f, 40, m.THETA)
+    rng = np.random.default_rng(8)
+    dirs = rng.standard_normal((3, 5))
+    _, mixed = m.pressure_loss_and_gradient(cfg, f, 40, directions=dirs.tolist())
+    want = dirs @ np.array(unit)
+    assert np.allclose(mixed, want, rtol=1e-10, atol=1e-12 * np.abs(want).max()), (mixed, want)
+
+
 def test_autograd_function_returns_the_tangent_gradient():
     import torch
     m = lbm()
@@ -134,6 +165,13 @@ def test_autograd_function_returns_the_tangent_gradient():
     Jr, dJ = m.pressure_loss_and_gradient(dict(cfg, storage="f64"), f, 40)
     assert abs(J.item() - Jr) <= 1e-14 * Jr
     assert np.allclose(theta.grad.numpy(), dJ, rtol=1e-14, atol=0.0)
+    # all five parameters (two runs of gradient steps)
+    c5 = dict(cfg, storage="f64", viscous="fd", alpha_V=0.3)
+    th5 = torch.tensor([0.5, 0.3, cs2 * 1.0002, 0.3, 0.0], dtype=torch.float64, requires_grad=True)
+    J5 = m.cbc_loss(th5, c5, f, 30, params=m.THETA)
+    J5.backward()
+    _, g5 = m.pressure_loss_gradient_in(c5, f, 30, m.THETA)
+    assert np.allclose(th5.grad.numpy(), g5, rtol=1e-14, atol=0.0)
 
 
 def test_gradient_steps_are_checked_and_fence_ordinary_steps():
@@ -142,6 +180,12 @@ def test_gradient_steps_are_checked_and_fence_ordinary_steps():
     sim = m.Simulation(dict(cfg, storage="f64", viscous="meso")).init_fields(*f)
     with pytest.raises(m.LbmError, match="viscous"):
         m.lbm_grad_begin(sim.handle)
+    sim.close()
+    sim = m.Simulation(dict(cfg, storage="f64")).init_fields(*f)
+    with pytest.raises(m.LbmError, match="finite"):
+        m.lbm_grad_begin_along(sim.handle, [[float("nan")] * 5] * 3)
+    with pytest.raises(ValueError):
+        m.lbm_grad_begin_along(sim.handle, [[1.0] * 4] * 3)
     sim.close()
     sim = m.Simulation(dict(cfg, storage="f16")).init_fields(*f)
     with pytest.raises(m.LbmError, match="storage"):
