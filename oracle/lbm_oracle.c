@@ -16,7 +16,7 @@
  * Only tests/, __graft_entry__.smoke() and bench.py's CPU baseline may use
  * this file.  It shares nothing with the CUDA implementation.
  *
- * Readings of the paper taken here (each also listed in the design doc):
+ * Readings of the paper taken here:
  *  - Eq. feq-4: the (u.c)^2 (T-1) term uses (xi^2 - 6), not (c^2 - 4): only
  *    then are the Maxwellian moments reproduced (tests/test_oracle_tables.py).
  *  - Eqs. feq-3/feq-4 are the Hermite expansion in xi = c/c_s, u~ = u/c_s.
