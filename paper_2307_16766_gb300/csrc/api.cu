@@ -1136,8 +1136,8 @@ int lbm_grad_begin_along(lbm_handle* h, const double* dirs)
         h->err = "gradient steps need FP64 or FP32 storage";
         return LBM_ERR_ARG;
     }
-    if (h->B.n_unk > 0 && (h->B.viscous == VIS_MESO || h->B.dirichlet != 0)) {
-        h->err = "gradient steps need viscous = off or fd and the equilibrium Dirichlet condition";
+    if (h->B.n_unk > 0 && h->B.dirichlet != 0) {
+        h->err = "gradient steps need the equilibrium Dirichlet condition";
         return LBM_ERR_ARG;
     }
     if (h->n_inflow > 0 || h->B.n_zg > 0) {
@@ -1147,10 +1147,12 @@ int lbm_grad_begin_along(lbm_handle* h, const double* dirs)
     const size_t dual = tl_dual_bytes();
     const size_t tbytes = 3 * h->f_bytes;
     const size_t sbytes = (size_t)std::max(1, h->E.nslots) * 4 * dual;
+    const size_t nbytes = (size_t)std::max(1, h->E.nslots) * 5 * dual;
     const size_t ubytes = (size_t)std::max(1, h->B.n_unk) * 4 * dual;
     size_t o = 0;
     auto take = [&](size_t b) { const size_t at = o; o = align_up(o + b); return at; };
     const size_t o_t0 = take(tbytes), o_t1 = take(tbytes), o_st = take(sbytes), o_st1 = take(sbytes),
+                 o_sn = take(nbytes), o_sn1 = take(nbytes),
                  o_ud = take(ubytes), o_uf = take(ubytes), o_ya = take(ubytes), o_yb = take(ubytes),
                  o_acc = take(ubytes), o_vv = take(ubytes),
                  o_mask = take((size_t)std::max(1, h->B.n_unk) * sizeof(int)), o_sums = take(4 * sizeof(double));
@@ -1162,6 +1164,8 @@ int lbm_grad_begin_along(lbm_handle* h, const double* dirs)
     T.t[1] = at<char>(mem, o_t1);
     T.strip[0] = at<char>(mem, o_st);
     T.strip[1] = at<char>(mem, o_st1);
+    T.stripN[0] = at<char>(mem, o_sn);
+    T.stripN[1] = at<char>(mem, o_sn1);
     T.Ud = at<char>(mem, o_ud);
     T.Uf = at<char>(mem, o_uf);
     T.Ya = at<char>(mem, o_ya);

@@ -249,21 +249,21 @@ __device__ __forceinline__ void char_rhs(const CharSys<T>& C, const Relax<T>& P,
 // (Eq. FD-dx-center) or one-sided inward next to a boundary node:
 //   V = (0, (1/rho) d_j s'_jn, (1/rho) d_j s'_jt,
 //        -div q / (rho c_s^2) + (nu / c_s^2) ((d_n u_n - d_t u_t)^2 + (d_n u_t + d_t u_n)^2)).
-template <bool TH>
-__device__ void vis_meso(const Geom& G, const double* SU, const double* SN, const UDesc& D,
-                         double cs2, double* V)
+template <bool TH, typename T>
+__device__ void vis_meso(const Geom& G, const T* SU, const T* SN, const UDesc& D, double cs2, T* V)
 {
     // SU, SN: macros [.][4] and non-equilibrium moments [.][5] of time t,
-    // indexed by D.vs[]
+    // indexed by D.vs[]; arithmetic T (FP64, or Dual numbers in the
+    // tangent-linear step)
     const int s = D.kind;
     const int an = s < 2 ? 0 : 1, at = 1 - an;     // axes of n and t
-    const double sn = (s == 0 || s == 2) ? -1.0 : 1.0;
-    double h[5][7];
+    const T sn = T((s == 0 || s == 2) ? -1.0 : 1.0);
+    T h[5][7];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        const double* n = SN + 5LL * D.vs[k];
-        const double* u = SU + 4LL * D.vs[k];
-        const double sxx = n[0], sxy = n[1], syy = n[2];
+        const T* n = SN + 5LL * D.vs[k];
+        const T* u = SU + 4LL * D.vs[k];
+        const T sxx = n[0], sxy = n[1], syy = n[2];
         h[k][0] = an == 0 ? sxx : syy;              // sigma'_nn
         h[k][1] = sn * sxy;                         // sigma'_nt
         h[k][2] = an == 0 ? syy : sxx;              // sigma'_tt
@@ -272,22 +272,22 @@ __device__ void vis_meso(const Geom& G, const double* SU, const double* SN, cons
         h[k][5] = sn * u[1 + an];                   // u_n
         h[k][6] = u[1 + at];                        // u_t
     }
-    double dn[7], dt[7];
+    T dn[7], dt[7];
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
-        dn[m] = 0.5 * (3.0 * h[0][m] - 4.0 * h[1][m] + h[2][m]);
-        if (D.tmode == 0) dt[m] = 0.5 * (h[3][m] - h[4][m]);
-        else dt[m] = double(D.tmode) * 0.5 * (3.0 * h[0][m] - 4.0 * h[3][m] + h[4][m]);
+        dn[m] = T(0.5) * (T(3) * h[0][m] - T(4) * h[1][m] + h[2][m]);
+        if (D.tmode == 0) dt[m] = T(0.5) * (h[3][m] - h[4][m]);
+        else dt[m] = T(double(D.tmode)) * T(0.5) * (T(3) * h[0][m] - T(4) * h[3][m] + h[4][m]);
     }
-    const double irho = 1.0 / (G.rho0 + SU[4LL * D.vs[0]]);
-    V[0] = 0.0;
+    const T irho = T(1) / (T(G.rho0) + SU[4LL * D.vs[0]]);
+    V[0] = T(0);
     V[1] = (dn[0] + dt[1]) * irho;
     V[2] = (dn[1] + dt[2]) * irho;
-    V[3] = 0.0;
+    V[3] = T(0);
     if (TH) {
-        const double nu = (G.tau - 0.5) * cs2;
-        const double e1 = dn[5] - dt[6], e2 = dn[6] + dt[5];
-        V[3] = -(dn[3] + dt[4]) * irho * (1.0 / cs2) + nu * (1.0 / cs2) * (e1 * e1 + e2 * e2);
+        const T nu = T((G.tau - 0.5) * cs2);
+        const T e1 = dn[5] - dt[6], e2 = dn[6] + dt[5];
+        V[3] = -(dn[3] + dt[4]) * irho * T(1.0 / cs2) + nu * T(1.0 / cs2) * (e1 * e1 + e2 * e2);
     }
 }
 

@@ -650,6 +650,8 @@ constexpr int kTLParams = 5;
 struct TLState {
     void* t[2];      // derivative populations per parity: [3][Q][plane], storage type
     void* strip[2];  // strip macros per parity (t, then t + 1): [nslots][4], stage type
+    void* stripN[2]; // strip non-equilibrium moments per parity: [nslots][5], stage type
+                     // (mesoscopic viscous vector only)
     void* Ud;        // boundary state: [n_unk][4], FP64 value + FP32 derivatives
     void* Uf;        // the same in the stage type
     void *Ya, *Yb;   // RK4 stage values: [n_unk][4], stage type

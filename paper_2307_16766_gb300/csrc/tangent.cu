@@ -18,9 +18,12 @@
 //   k_tl_dirichlet f^eq of the new boundary state on the band nodes
 //                  (equilibrium Dirichlet condition)
 //
-// Supported: FP64 and FP32 storage, equilibrium Dirichlet condition, no
-// viscous vector or its "-FD" form (frozen at time t, as in the ordinary
-// step), characteristic and periodic sides (checked on the host).
+//   k_tl_neq       (mesoscopic viscous vector) non-equilibrium moments of
+//                  the strip nodes at t + 1 (Eqs. LaplaceU, LaplaceT)
+//
+// Supported: FP64 and FP32 storage, equilibrium Dirichlet condition, any
+// viscous vector (frozen at time t, as in the ordinary step),
+// characteristic and periodic sides (checked on the host).
 #include "charsys.cuh"
 
 #include <type_traits>
@@ -154,13 +157,67 @@ __global__ void k_tl_strip(Geom G, Export E, const S* __restrict__ f, const S* _
     a[0] = m.s0; a[1] = m.ux; a[2] = m.uy; a[3] = m.dT;
 }
 
+// Non-equilibrium moments (sigma', q) of the strip nodes at t + 1, from
+// their pulled (pre-collision) populations, for the mesoscopic viscous
+// vector of the next step; the same arithmetic as the ordinary step's strip
+// phase, on Dual numbers.
+template <int LAT, typename S>
+__global__ void k_tl_neq(Geom G, Export E, const S* __restrict__ f, const S* __restrict__ t,
+                         TB<S>* __restrict__ StN1)
+{
+    using L = Lat<LAT>;
+    using C = TB<S>;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= E.nslots) return;
+    int x = 0, y = 0;
+    C* a = StN1 + 5LL * q;
+    if (!slot_node(G, E, q, x, y)) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) a[c] = C(0);
+        return;
+    }
+    // one derivative direction at a time (Dual<., 1>), as in the bulk pass
+    using C1 = Dual<typename Store<S>::C, 1>;
+    const long long dstride = (long long)L::Q * G.plane;
+#pragma unroll 1
+    for (int k = 0; k < kTD; ++k) {
+        C1 g[L::Q];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const long long o = pull_src<LAT>(G, i, x, y);
+            g[i].v = f[o];
+            g[i].d[0] = t[k * dstride + o];
+        }
+        const Moments<LAT, C1> m = moments<LAT, C1>(g, rho0_of<C1>(G));
+        C1 N[5];
+        neq_moments<LAT, C1, C1>(g, m, C1(1) - C1(0.5) * omega_of<C1>(G), N);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            if (k == 0) a[c].v = N[c].v;
+            a[c].d[k] = N[c].d[0];
+        }
+    }
+}
+
+// The strips' non-equilibrium moments of time t from the handle's own
+// strips (values), with zero derivatives: the first tangent-linear step's
+// seed.
+template <typename S>
+__global__ void k_tl_seed_neq(Export E, const typename StripReal<S>::T* __restrict__ SN, TB<S>* StN)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= E.nslots) return;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) StN[5LL * q + c] = TB<S>(typename Store<S>::C(SN[5LL * q + c]));
+}
+
 // One RK4 stage of every boundary unknown.  Ud, acc: state and sum of k
 // (FP64); Uf: the state in the stage type, for the neighbours' stencils;
 // Ya, Yb: stage values; mask: incoming waves at t.
 template <int LAT, typename S>
 __global__ void k_tl_stage(Geom G, Band B, Relax<TB<S>> P, const TB<S>* __restrict__ St,
-                           const TB<S>* __restrict__ St1, TS* Ud, TB<S>* Uf, TB<S>* Ya, TB<S>* Yb,
-                           TS* acc, int* mask, TB<S>* Vv, int stage)
+                           const TB<S>* __restrict__ St1, const TB<S>* __restrict__ StN, TS* Ud,
+                           TB<S>* Uf, TB<S>* Ya, TB<S>* Yb, TS* acc, int* mask, TB<S>* Vv, int stage)
 {
     using Lt = Lat<LAT>;
     using T = TB<S>;
@@ -176,13 +233,14 @@ __global__ void k_tl_stage(Geom G, Band B, Relax<TB<S>> P, const TB<S>* __restri
     X.St1 = St1;
     X.frac = stage == 0 ? T(0) : (stage == 3 ? T(1) : T(0.5));
     T* Yout = stage == 1 ? Yb : Ya;
-    // "-FD" viscous vector: from the macros of time t at stage 0, then
-    // frozen for the later stages (corners take none)
+    // viscous vector: of time t at stage 0, then frozen for the later
+    // stages (corners take none)
     T V[4] = {T(0), T(0), T(0), T(0)};
-    if (B.viscous == VIS_FD && D.kind < 4) {
+    if (B.viscous != VIS_OFF && D.kind < 4) {
         T* Vu = Vv + 4LL * u;
         if (stage == 0) {
-            vis_fd<Lt::THERMAL>(G, B, X, D, u, Lt::CS2, V);
+            if (B.viscous == VIS_FD) vis_fd<Lt::THERMAL>(G, B, X, D, u, Lt::CS2, V);
+            else vis_meso<Lt::THERMAL>(G, St, StN, D, Lt::CS2, V);
 #pragma unroll
             for (int m = 0; m < 4; ++m) Vu[m] = V[m];
         } else {
@@ -370,7 +428,8 @@ int tl_step_t(const TLState& T, const Geom& G, const Export& E, const Band& B, c
     const int nb = (B.n_unk + 127) / 128;
     auto stage = [&](int k, bool early) {
         return launch_ex(k_tl_stage<LAT, S>, dim3(nb), dim3(128), 0, st, early, G, B, P,
-                         static_cast<const R*>(St), static_cast<const R*>(St1), static_cast<TS*>(T.Ud),
+                         static_cast<const R*>(St), static_cast<const R*>(St1),
+                         static_cast<const R*>(T.stripN[par]), static_cast<TS*>(T.Ud),
                          static_cast<R*>(T.Uf), static_cast<R*>(T.Ya), static_cast<R*>(T.Yb),
                          static_cast<TS*>(T.acc), T.mask, static_cast<R*>(T.Vv), k);
     };
@@ -390,6 +449,8 @@ int tl_step_t(const TLState& T, const Geom& G, const Export& E, const Band& B, c
             if (stage(k, false)) return -1;
         k_tl_dirichlet<LAT, S><<<nb, 128, 0, st>>>(G, B, static_cast<const R*>(T.Uf), fo, to);
     }
+    if (B.viscous == VIS_MESO && E.nslots > 0)
+        k_tl_neq<LAT, S><<<(E.nslots + 127) / 128, 128, 0, st>>>(G, E, fi, ti, static_cast<R*>(T.stripN[par ^ 1]));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -398,8 +459,12 @@ int tl_seed_strips_t(const TLState& T, const Geom& G, const Export& E, void* con
                      cudaStream_t st)
 {
     if (E.nslots == 0) return 0;
-    k_tl_strip<LAT, S><<<(E.nslots + 127) / 128, 128, 0, st>>>(
+    const int nb = (E.nslots + 127) / 128;
+    k_tl_strip<LAT, S><<<nb, 128, 0, st>>>(
         G, E, static_cast<const S*>(f[par]), static_cast<const S*>(T.t[par]), static_cast<TB<S>*>(T.strip[par]));
+    using SR = typename StripReal<S>::T;
+    k_tl_seed_neq<S><<<nb, 128, 0, st>>>(E, static_cast<const SR*>(E.stripN) + (long long)par * E.nslots * 5,
+                                         static_cast<TB<S>*>(T.stripN[par]));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -47,9 +47,10 @@ def _loss_by_steps(cfg, f, steps):
 
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-4)])
-def test_tangent_steps_carry_the_ordinary_step(storage, tol):
+@pytest.mark.parametrize("viscous", ["off", "fd", "meso"])
+def test_tangent_steps_carry_the_ordinary_step(storage, tol, viscous):
     cfg, f = _case()
-    c = dict(cfg, storage=storage)
+    c = dict(cfg, storage=storage, viscous=viscous, alpha_V=0.3)
     J, _ = lbm().pressure_loss_and_gradient(c, f, 60)
     Js = _loss_by_steps(c, f, 60)
     assert abs(J - Js) <= tol * Js, (J, Js)
@@ -140,6 +141,25 @@ def test_gradient_in_alpha_V_and_t_inf_with_fd_viscous_terms(lat):
         assert abs(dJ[k] - fd[k]) <= 1e-4 * abs(fd[k]), (k, dJ, fd)
 
 
+@pytest.mark.parametrize("lat", ["D2Q17", "D2Q37"])
+def test_gradient_with_mesoscopic_viscous_terms(lat):
+    """With the mesoscopic viscous vector (Eqs. LaplaceU, LaplaceT; strips'
+    non-equilibrium moments carried with their derivatives):
+    dJ/d(alpha_T, beta_P, alpha_V) against the oracle's central
+    differences."""
+    cfg, f = _case(lat)
+    cfg = dict(cfg, viscous="meso", alpha_V=0.4)
+    params = ("alpha_T", "beta_P", "alpha_V")
+    steps = 60
+    J, dJ = lbm().pressure_loss_gradient_in(dict(cfg, storage="f64"), f, steps, params)
+    Jo = oracle.pressure_loss(cfg, f, steps)
+    assert abs(J - Jo) <= 1e-10 * Jo, (J, Jo)
+    fd = oracle.pressure_loss_fd_gradient(cfg, f, steps, (1e-4, 1e-4, 1e-4), params=params)
+    for k in range(3):
+        assert fd[k] != 0.0
+        assert abs(dJ[k] - fd[k]) <= 1e-4 * abs(fd[k]), (k, dJ, fd)
+
+
 def test_gradient_directions_combine_linearly():
     """A direction that mixes parameters gives the same combination of the
     unit-direction derivatives (forward mode is linear in the seed, up to
@@ -178,8 +198,8 @@ def test_autograd_function_returns_the_tangent_gradient():
 def test_gradient_steps_are_checked_and_fence_ordinary_steps():
     m = lbm()
     cfg, f = _case()
-    sim = m.Simulation(dict(cfg, storage="f64", viscous="meso")).init_fields(*f)
-    with pytest.raises(m.LbmError, match="viscous"):
+    sim = m.Simulation(dict(cfg, storage="f64", dirichlet="neep")).init_fields(*f)
+    with pytest.raises(m.LbmError, match="Dirichlet"):
         m.lbm_grad_begin(sim.handle)
     sim.close()
     sim = m.Simulation(dict(cfg, storage="f64")).init_fields(*f)
