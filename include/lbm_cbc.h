@@ -207,10 +207,9 @@ void lbm_destroy(lbm_handle* h);
  * rounding (forward mode), in FP64 for the boundary state; populations and
  * their derivatives are held in the handle's storage precision.
  *
- * Supported: FP64 or FP32 storage, viscous = LBM_VISCOUS_OFF or
- * LBM_VISCOUS_FD (the "-FD" vector, frozen at time t as in the ordinary
- * step), the equilibrium Dirichlet condition, characteristic and periodic
- * sides (otherwise LBM_ERR_ARG).  Gradient steps use the handle's stream and
+ * Supported: FP64 or FP32 storage, every viscous form (the vector frozen at
+ * time t as in the ordinary step), the equilibrium Dirichlet condition,
+ * characteristic and periodic sides (otherwise LBM_ERR_ARG).  Gradient steps use the handle's stream and
  * steps counter; afterwards the handle's ordinary step state (strips,
  * boundary state) is behind: lbm_step, lbm_step_phase, lbm_get_state and
  * batch steps return LBM_ERR_STATE until lbm_init_fields or lbm_set_state.

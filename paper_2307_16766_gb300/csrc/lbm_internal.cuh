@@ -663,8 +663,7 @@ struct TLState {
 };
 size_t tl_dual_bytes();
 // One tangent-linear step f[par] -> f[par ^ 1] (FP64 or FP32 storage; the
-// handle's checks exclude the viscous vector, NEEP and inflow / zero-gradient
-// sides), adding the loss over the bulk nodes (the nodes off the boundary
+// handle's checks exclude NEEP and inflow / zero-gradient sides), adding the loss over the bulk nodes (the nodes off the boundary
 // layers) against dPref ([ny][nx] of P_ref - c_s^2 rho0, or null for 0) to
 // T.sums.
 int launch_tl_step(int lat, int storage, const TLState& T, const Geom& G, const Export& E,
