@@ -282,25 +282,34 @@ __global__ void k_tl_stage(Geom G, Band B, Relax<TB<S>> P, const TB<S>* __restri
 
 // Equilibrium Dirichlet condition of the new boundary state: f^eq on the
 // unknown's band node (corner: its M x M block), value and derivatives, in
-// the storage's arithmetic.
+// the storage's arithmetic.  Thread (u, k) takes derivative direction k of
+// unknown u on Dual<., 1> numbers (direction 0 also writes the values):
+// three short chains per unknown instead of one long one.
 template <int LAT, typename S>
 __global__ void k_tl_dirichlet(Geom G, Band B, const TB<S>* __restrict__ Uf, S* __restrict__ f,
                                S* __restrict__ t)
 {
     using L = Lat<LAT>;
-    using C = TB<S>;
+    using C1 = Dual<typename Store<S>::C, 1>;
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
     if (u >= B.n_unk) return;
     const UDesc D = B.ud[u];
-    const C* U = Uf + 4LL * u;
-    Moments<LAT, C> m;
-    m.s0 = U[0];
-    m.rho = rho0_of<C>(G) + m.s0;
-    m.ux = U[1];
-    m.uy = U[2];
-    m.dT = L::THERMAL ? U[3] : C(0);
-    C ge[L::Q];
-    equilibrium<LAT, C>(m, ge);
+    const TB<S>* U = Uf + 4LL * u;
+    C1 Uk[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        Uk[c].v = U[c].v;
+        Uk[c].d[0] = U[c].d[k];
+    }
+    Moments<LAT, C1> m;
+    m.s0 = Uk[0];
+    m.rho = rho0_of<C1>(G) + m.s0;
+    m.ux = Uk[1];
+    m.uy = Uk[2];
+    m.dT = L::THERMAL ? Uk[3] : C1(0);
+    C1 ge[L::Q];
+    equilibrium<LAT, C1>(m, ge);
     const long long dstride = (long long)L::Q * G.plane;
     const int nb = D.kind >= 4 ? G.M : 1;
     for (int a = 0; a < nb; ++a)
@@ -309,9 +318,8 @@ __global__ void k_tl_dirichlet(Geom G, Band B, const TB<S>* __restrict__ Uf, S* 
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
                 const long long o = (long long)L::plane_of(i) * G.plane + node;
-                f[o] = S(ge[i].v);
-#pragma unroll
-                for (int k = 0; k < kTD; ++k) t[k * dstride + o] = S(ge[i].d[k]);
+                if (k == 0) f[o] = S(ge[i].v);
+                t[k * dstride + o] = S(ge[i].d[0]);
             }
         }
 }
@@ -321,15 +329,29 @@ __global__ void k_tl_dirichlet(Geom G, Band B, const TB<S>* __restrict__ Uf, S* 
 // loss of the node: the bulk nodes are the nodes off the boundary layers,
 // and the collision keeps the macros, so the pulled populations' moments
 // give P at t + 1.
+// Threads of a bulk-pass CTA: the pulled populations of one direction are
+// staged in shared memory, a column per thread (37 x 128 FP32 Dual numbers
+// or 37 x 64 FP64 ones: 37 KB), rather than held in registers, and the
+// registers are capped so that four FP32 CTAs share an SM (the collision's
+// working set then spills a few words; at two CTAs per SM, uncapped, the
+// pass ran 1.2x slower).
+template <typename S>
+constexpr int tl_bulk_threads() { return sizeof(typename Store<S>::C) == 8 ? 64 : 128; }
+template <typename S>
+constexpr int tl_bulk_min_blocks() { return sizeof(typename Store<S>::C) == 8 ? 1 : 4; }
+
 template <int LAT, typename S>
-__global__ void __launch_bounds__(128) k_tl_bulk(Geom G, Region R, Export E, const S* __restrict__ f,
-                                                 const S* __restrict__ t, S* __restrict__ fo,
-                                                 S* __restrict__ to, TB<S>* __restrict__ St1,
-                                                 const double* __restrict__ dPref, double* sums)
+__global__ void __launch_bounds__(tl_bulk_threads<S>(), tl_bulk_min_blocks<S>())
+    k_tl_bulk(Geom G, Region R, Export E, const S* __restrict__ f, const S* __restrict__ t,
+              S* __restrict__ fo, S* __restrict__ to, TB<S>* __restrict__ St1,
+              const double* __restrict__ dPref, double* sums)
 {
     using L = Lat<LAT>;
     using C1 = Dual<typename Store<S>::C, 1>;
-    const int x = R.x0 + blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int NT = tl_bulk_threads<S>();
+    __shared__ C1 sg[L::Q][NT];
+    const int l = threadIdx.x;
+    const int x = R.x0 + blockIdx.x * NT + l;
     const int y = R.y0 + blockIdx.y;
     double acc[kTD + 1] = {0.0, 0.0, 0.0, 0.0};
     if (x < R.x1) {
@@ -348,18 +370,35 @@ __global__ void __launch_bounds__(128) k_tl_bulk(Geom G, Region R, Export E, con
         double e = 0.0;
 #pragma unroll 1
         for (int k = 0; k < kTD; ++k) {
-            C1 g[L::Q];
+            // offsets inside one buffer fit in 32 bits (the grid check keeps
+            // Q x plane below 2^31); direction k's planes start at tk / tok
+            const S* tk = t + k * dstride;
+            S* tok = to + k * dstride;
+            // pull (Eq. lbe) into the thread's column, summing the moments
+            // as moments() does
+            C1 s0 = 0, sx = 0, sy = 0, se = 0;
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
-                const long long o = pull_src<LAT>(G, i, x, y);
-                g[i].v = f[o];
-                g[i].d[0] = t[k * dstride + o];
+                const int o = int(pull_src<LAT>(G, i, x, y));
+                C1 g;
+                g.v = f[o];
+                g.d[0] = tk[o];
+                sg[i][l] = g;
+                s0 += g;
+                if (L::cx(i)) sx += C1(L::cx(i)) * g;
+                if (L::cy(i)) sy += C1(L::cy(i)) * g;
+                if (L::THERMAL && i) se += C1(L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i)) * g;
             }
-            const Moments<LAT, C1> m = collide<LAT, C1>(G, g, [&](int i, const C1& v) {
-                const long long o = (long long)L::plane_of(i) * G.plane + node;
+            // read the column back below rather than keeping it in registers
+            asm volatile("" ::: "memory");
+            const Moments<LAT, C1> m = moments_of_sums<LAT, C1>(s0, sx, sy, se, rho0_of<C1>(G));
+            const int nd = int(node);
+            collide_given<LAT, C1>(G, m, [&](int i) -> C1 { return sg[i][l]; }, [&](int i, const C1& v) {
+                const int o = L::plane_of(i) * int(G.plane) + nd;
                 if (k == 0) fo[o] = v.v;
-                to[k * dstride + o] = v.d[0];
+                tok[o] = v.d[0];
             });
+            asm volatile("" ::: "memory");
             for (int q = 0; q < ns; ++q) {
                 TB<S>* a = St1 + 4LL * slot[q];
                 const C1 mc[4] = {m.s0, m.ux, m.uy, m.dT};
@@ -370,29 +409,32 @@ __global__ void __launch_bounds__(128) k_tl_bulk(Geom G, Region R, Export E, con
                 }
             }
             // P - c_s^2 rho0 = c_s^2 (drho + rho0 dT + drho dT)
-            const double s0 = double(m.s0.v), dT = double(m.dT.v);
+            const double s0v = double(m.s0.v), dT = double(m.dT.v);
             const double s0d = double(m.s0.d[0]), dTd = double(m.dT.d[0]);
             if (k == 0) {
-                const double dP = L::THERMAL ? L::CS2 * (s0 + G.rho0 * dT + s0 * dT) : L::CS2 * s0;
+                const double dP = L::THERMAL ? L::CS2 * (s0v + G.rho0 * dT + s0v * dT) : L::CS2 * s0v;
                 e = dP - (dPref ? dPref[(long long)y * G.nx + x] : 0.0);
                 acc[0] = e * e;
             }
-            const double dPd = L::THERMAL ? L::CS2 * (s0d + G.rho0 * dTd + s0d * dT + s0 * dTd) : L::CS2 * s0d;
+            const double dPd = L::THERMAL ? L::CS2 * (s0d + G.rho0 * dTd + s0d * dT + s0v * dTd) : L::CS2 * s0d;
             acc[k + 1] = 2.0 * e * dPd;
         }
     }
-    __shared__ double red[kTD + 1][4];
+    constexpr int NW = NT / 32;
+    __shared__ double red[kTD + 1][NW];
 #pragma unroll
     for (int c = 0; c < kTD + 1; ++c) {
         double a = acc[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = a;
+        if ((l & 31) == 0) red[c][l >> 5] = a;
     }
     __syncthreads();
-    if (threadIdx.x < kTD + 1) {
-        const double a = red[threadIdx.x][0] + red[threadIdx.x][1] + red[threadIdx.x][2] + red[threadIdx.x][3];
-        atomicAdd(sums + threadIdx.x, a);
+    if (l < kTD + 1) {
+        double a = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) a += red[l][w];
+        atomicAdd(sums + l, a);
     }
 }
 
@@ -439,15 +481,16 @@ int tl_step_t(const TLState& T, const Geom& G, const Export& E, const Band& B, c
         first = false;
     }
     if (bulk.x1 > bulk.x0 && bulk.y1 > bulk.y0) {
-        dim3 grd((bulk.x1 - bulk.x0 + 127) / 128, bulk.y1 - bulk.y0);
-        if (launch_ex(k_tl_bulk<LAT, S>, grd, dim3(128), 0, st, !first, G, bulk, E, fi, ti, fo, to, St1, dPref,
+        constexpr int NT = tl_bulk_threads<S>();
+        dim3 grd((bulk.x1 - bulk.x0 + NT - 1) / NT, bulk.y1 - bulk.y0);
+        if (launch_ex(k_tl_bulk<LAT, S>, grd, dim3(NT), 0, st, !first, G, bulk, E, fi, ti, fo, to, St1, dPref,
                       T.sums))
             return -1;
     }
     if (B.n_unk > 0) {
         for (int k = 1; k < 4; ++k)
             if (stage(k, false)) return -1;
-        k_tl_dirichlet<LAT, S><<<nb, 128, 0, st>>>(G, B, static_cast<const R*>(T.Uf), fo, to);
+        k_tl_dirichlet<LAT, S><<<dim3(nb, kTD), 128, 0, st>>>(G, B, static_cast<const R*>(T.Uf), fo, to);
     }
     if (B.viscous == VIS_MESO && E.nslots > 0)
         k_tl_neq<LAT, S><<<(E.nslots + 127) / 128, 128, 0, st>>>(G, E, fi, ti, static_cast<R*>(T.stripN[par ^ 1]));
