@@ -1336,9 +1336,9 @@ void autotune_store(const std::string& key, int value)
     fclose(fp);
 }
 
-// One step of every run: per group one batched band launch on the internal
-// high-priority stream and one persistent bulk launch (plus zero-gradient
-// copies) on the batch's stream, forked and joined like lbm_step.
+// One step of every run: per group one batched band launch and one
+// persistent bulk launch, then the zero-gradient copies, on the batch's
+// stream.
 int batch_issue_step(lbm_batch* b, int par, cudaStream_t s0, bool with_inflow)
 {
     // All on one stream: the band kernels of the groups, then their bulk
