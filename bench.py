@@ -501,7 +501,27 @@ def whole_job_mlups(nodes, steps, world, seconds):
     return nodes * steps * world / seconds / 1e6
 
 
-def cpu_baseline(cfg, fields, seconds=15.0):
+def cpu_model():
+    """The host CPU's name from /proc/cpuinfo (x86: model name; Arm: the
+    implementer / part codes), else the machine type."""
+    import platform
+    info = {}
+    try:
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                info.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if "model name" in info:
+        return info["model name"]
+    if "CPU part" in info:
+        return "%s, CPU implementer %s part %s" % (platform.machine(), info.get("CPU implementer", "?"),
+                                                   info["CPU part"])
+    return platform.machine()
+
+
+def _oracle_rate(cfg, fields, seconds):
     import oracle
     s = oracle.Sim(cfg).init(*fields)
     t = time.perf_counter()
@@ -511,10 +531,24 @@ def cpu_baseline(cfg, fields, seconds=15.0):
     t = time.perf_counter()
     s.step(n)
     dt = time.perf_counter() - t
-    mlups = cfg["nx"] * cfg["ny"] * n / dt / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
-            "sample": "%d FP64 oracle steps of the %dx%d workload after one warm-up step (%.1f s)"
-                      % (n, cfg["nx"], cfg["ny"], dt)}
+    return cfg["nx"] * cfg["ny"] * n / dt / 1e6, n, dt
+
+
+def cpu_baseline(cfg, fields, seconds=15.0, seconds_1t=6.0):
+    """The FP64 oracle on this host: all threads (the baseline) and one
+    thread, each on a bounded number of steps of the workload."""
+    import oracle
+    nproc = oracle.threads()
+    mlups, n, dt = _oracle_rate(cfg, fields, seconds)
+    oracle.set_threads(1)
+    try:
+        m1, n1, dt1 = _oracle_rate(cfg, fields, seconds_1t)
+    finally:
+        oracle.set_threads(nproc)
+    return {"value": mlups, "unit": "MLUPS", "cores": nproc, "kind": "oracle",
+            "cpu": cpu_model(), "single_thread_value": m1,
+            "sample": "%d FP64 oracle steps of the %dx%d workload after one warm-up step (%.1f s) on %d "
+                      "threads; %d steps (%.1f s) on 1 thread" % (n, cfg["nx"], cfg["ny"], dt, nproc, n1, dt1)}
 
 
 def main():
@@ -545,7 +579,7 @@ def main():
                     "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                     "config": workload_config(cfg, {"l2": "n/a (CPU)"}),
                     "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.threads(),
-                                     "kind": "oracle",
+                                     "kind": "oracle", "cpu": cpu_model(),
                                      "sample": "%d of %d requested steps of the full grid" % (n, args.steps)},
                     "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                     "gpu_launches": 0}

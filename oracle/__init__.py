@@ -69,6 +69,8 @@ def lib():
         L.orc_steps_done.argtypes = [C.c_void_p]
         L.orc_steps_done.restype = C.c_long
         L.orc_threads.restype = C.c_int
+        L.orc_set_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -172,6 +174,11 @@ def rk4_scalar(lam, y0, h, nsteps):
 
 def threads():
     return lib().orc_threads()
+
+
+def set_threads(n):
+    """Threads of the following steps; returns the count now in use."""
+    return lib().orc_set_threads(int(n))
 
 
 class Sim:

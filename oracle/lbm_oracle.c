@@ -1071,3 +1071,15 @@ int orc_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the following steps (n >= 1); returns the count now in use.
+ * The result of a step does not depend on it (rows are independent). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return orc_threads();
+}

@@ -103,6 +103,7 @@ void     orc_vis_meso_at(const orc_sim* s, int side, int x, int y, double V[4]);
 void     orc_boundary_state(const orc_sim* s, double* Ub);
 long     orc_steps_done(const orc_sim* s);
 int      orc_threads(void);
+int      orc_set_threads(int n);
 
 #ifdef __cplusplus
 }
