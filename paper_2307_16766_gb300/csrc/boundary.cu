@@ -631,11 +631,13 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                     const double st = srow(TTr);
                     const double relaxP = acoustic ? B.beta_P * double(XP(5)) : 0.0;
                     if (scheme == SCH_LODI_RELAX) w = B.alpha_T * (B.t_inf - st) + relaxP;
-                    else if (scheme == SCH_CBC) w = st + srow(Vr);
+                    // the viscous projection (four FP64 products; none
+                    // when the viscous vector is off)
+                    else if (scheme == SCH_CBC) w = st + (B.viscous != VIS_OFF ? srow(Vr) : 0.0);
                     else {
                         // Eq. CBC-Relax; the viscous term relaxed towards 0
                         // at rate alpha_V (0: the paper's equation)
-                        const double sv = srow(Vr);
+                        const double sv = B.viscous != VIS_OFF ? srow(Vr) : 0.0;
                         w = st + sv + B.alpha_T * (B.t_inf - st) + B.alpha_V * (0.0 - sv) + relaxP;
                     }
                 }
