@@ -708,8 +708,16 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads)
 
 // Band tiles of many grids in one launch: cluster t takes tile tile_run[t].y
 // of run tile_run[t].x, whose structures it copies to shared memory first.
+// With FP32 / FP16 storage its registers are capped so that five CTAs share
+// an SM: a batch's many tiles run in waves whose FP64 issue and exchange
+// latencies more CTAs hide better (a few hundred bytes spill; four CTAs per
+// SM, uncapped, measured 4% slower on the 96-run sweep, six 1% slower).  The
+// FP64 form would spill kilobytes and keeps its registers.
+template <typename S>
+constexpr int band_batch_min_blocks() { return sizeof(S) == 8 ? 1 : 5; }
+
 template <int LAT, typename S>
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads)
+__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads, band_batch_min_blocks<S>())
     k_band_batch(const BandRun* __restrict__ runs, const int2* __restrict__ tile_run, int par_t)
 {
     __shared__ __align__(16) BandRun R;
