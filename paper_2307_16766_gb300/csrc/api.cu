@@ -48,11 +48,8 @@ struct lbm_handle {
     bool owns_ws = false;
     cudaStream_t stream = nullptr;
     Region bulk{};           // nodes of the bulk kernel
-    bool persistent = false; // single grids: the one-segment-per-CTA kernel measured faster
     BulkRun* brun = nullptr; // its run descriptor (workspace)
-    unsigned* queue = nullptr;  // its work queue (workspace, 2 words)
-    int bulk_items = 0, bulk_grid = 0;
-    size_t band_pad = 0;     // extra shared memory per band CTA (SM reservation)
+    int bulk_items = 0;      // its work items (row segments)
     cudaStream_t aux = nullptr;              // internal stream: the bulk beside the band, when timed
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t kev[5] = {};  // caller's timing events (see lbm_set_kernel_events)
@@ -99,7 +96,7 @@ struct Plan {
     std::vector<int> inflow;
     double Uin[4] = {0, 0, 0, 0};
     size_t off_f0 = 0, off_f1 = 0, off_sU = 0, off_sN = 0, off_Ub = 0, off_ud = 0, off_ld = 0,
-           off_sn = 0, off_brun = 0, off_queue = 0, off_zg = 0, off_in = 0, off_macro = 0, off_flag = 0,
+           off_sn = 0, off_brun = 0, off_zg = 0, off_in = 0, off_macro = 0, off_flag = 0,
            total = 0;
 };
 
@@ -523,7 +520,6 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     pl.off_ld = take(pl.ldp.size() * sizeof(UDesc));
     pl.off_sn = take(pl.snp.size() * sizeof(StripNode));
     pl.off_brun = take(sizeof(BulkRun));
-    pl.off_queue = take(2 * sizeof(unsigned));
     pl.off_zg = take(pl.zg.size() * sizeof(int2));
     pl.off_in = take(pl.inflow.size() * sizeof(int));
     pl.off_macro = take((size_t)4 * nx * ny * 8);
@@ -638,7 +634,8 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
             const int rc = encode_population_map(h, h->f[b], depths[k] <= h->Q ? depths[k] : 1, &h->tmap[b][k]);
             if (rc != LBM_OK) return rc;
         }
-    // Run descriptor of the persistent bulk kernel (this grid alone).
+    // Run descriptor of the persistent bulk kernel (this grid alone), which
+    // a batch copies into its group's table.
     {
         BulkRun r;
         std::memset(&r, 0, sizeof r);
@@ -658,22 +655,13 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
         r.first = 0;
         h->bulk_items = h->bulk.x1 > h->bulk.x0 ? r.nseg * (h->bulk.y1 - h->bulk.y0) : 0;
         h->brun = at<BulkRun>(ws, pl.off_brun);
-        h->queue = at<unsigned>(ws, pl.off_queue);
-        int dev = 0, nsm = 0;
-        cudaError_t e0 = cudaGetDevice(&dev);
-        if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(h->brun, &r, sizeof r, cudaMemcpyHostToDevice, h->stream);
-        if (e0 == cudaSuccess) e0 = cudaMemsetAsync(h->queue, 0, 2 * sizeof(unsigned), h->stream);
-        if (e0 != cudaSuccess) return cuda_fail(h, e0, "persistent bulk set-up");
-        h->bulk_grid = nsm * 5;
-        if (prepare_bulk_persistent(h->lattice, h->storage) != 0)
-            return cuda_fail(h, cudaGetLastError(), "persistent bulk shared memory");
+        const cudaError_t e0 = cudaMemcpyAsync(h->brun, &r, sizeof r, cudaMemcpyHostToDevice, h->stream);
+        if (e0 != cudaSuccess) return cuda_fail(h, e0, "bulk run descriptor");
     }
-    // Band CTAs share their SMs with bulk CTAs.  (Reserving whole SMs for
-    // the band through its shared-memory request measured slower: the bulk
-    // loses more than the band gains.)
-    h->band_pad = 0;
-    if (h->B.n_tiles > 0 && prepare_boundary(h->lattice, h->storage, h->B, h->band_pad) != 0)
+    // Band CTAs share their SMs with bulk CTAs (reserving whole SMs for the
+    // band through its shared-memory request measured slower: the bulk loses
+    // more than the band gains).
+    if (h->B.n_tiles > 0 && prepare_boundary(h->lattice, h->storage, h->B) != 0)
         return cuda_fail(h, cudaGetLastError(), "band kernel shared memory");
     cudaError_t e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
@@ -718,12 +706,8 @@ int bulk(lbm_handle* h, int par, cudaStream_t st, bool early = false)
 {
     int rc = mark(h, 0, st);
     if (rc != LBM_OK) return rc;
-    if (h->persistent)
-        rc = launch_bulk_persistent(h->lattice, h->storage, h->brun, 1, h->bulk_items, par,
-                                    h->bulk_grid, h->queue, st, early);
-    else
-        rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->bulk, h->tmap[par], h->f[par],
-                         h->f[par ^ 1], h->flag + 1, st, early);
+    rc = launch_bulk(h->lattice, h->storage, h->G, h->O, h->bulk, h->tmap[par], h->f[par],
+                     h->f[par ^ 1], h->flag + 1, st, early);
     if (rc) return check_launch(h, rc, "bulk kernel");
     return mark(h, 1, st);
 }
@@ -744,7 +728,7 @@ int band(lbm_handle* h, int par, cudaStream_t st)
         h->inflow_done[par ^ 1] = true;
     }
     rc = launch_boundary(h->lattice, h->storage, h->G, h->O, h->E, h->B, h->f[par], h->f[par ^ 1],
-                         par, h->band_pad, st);
+                         par, st);
     if (rc) return check_launch(h, rc, "band kernel");
     return mark(h, 4, st);
 }

@@ -752,10 +752,10 @@ size_t band_smem(const Band& B)
 
 template <int LAT, typename S>
 int boundary_t(const Geom& G, const Offsets& O, const Export& E, const Band& B, const void* fin,
-               void* fnew, int par_t, size_t smem_pad, cudaStream_t st)
+               void* fnew, int par_t, cudaStream_t st)
 {
     if (B.n_tiles == 0) return 0;
-    const size_t smem = band_smem<LAT, S>(B) + smem_pad;
+    const size_t smem = band_smem<LAT, S>(B);
     k_band<LAT, S><<<B.n_tiles * kCluster, kTileThreads, smem, st>>>(
         G, O, B, E, static_cast<const S*>(fin), static_cast<S*>(fnew), par_t);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -778,10 +778,10 @@ int prepare_batch_t(size_t smem)
 }
 
 template <int LAT, typename S>
-int prepare_t(const Band& B, size_t smem_pad)
+int prepare_t(const Band& B)
 {
     // the 48 KB default covers static + dynamic shared memory: always opt in
-    const size_t smem = band_smem<LAT, S>(B) + smem_pad;
+    const size_t smem = band_smem<LAT, S>(B);
     return cudaFuncSetAttribute(k_band<LAT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(smem)) == cudaSuccess ? 0 : -1;
 }
@@ -814,10 +814,9 @@ int zg_t(const Geom& G, const Band& B, void* fnew, cudaStream_t st)
     } while (0)
 
 int launch_boundary(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
-                    const Band& B, const void* fin, void* fnew, int par_t, size_t smem_pad,
-                    cudaStream_t st)
+                    const Band& B, const void* fin, void* fnew, int par_t, cudaStream_t st)
 {
-#define CALL(L, S) boundary_t<L, S>(G, O, E, B, fin, fnew, par_t, smem_pad, st)
+#define CALL(L, S) boundary_t<L, S>(G, O, E, B, fin, fnew, par_t, st)
     BAND_DISPATCH(lat, storage, CALL);
 #undef CALL
     return -1;
@@ -831,9 +830,9 @@ size_t band_dynamic_smem(int lat, int storage, const Band& B)
     return 0;
 }
 
-int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad)
+int prepare_boundary(int lat, int storage, const Band& B)
 {
-#define CALL(L, S) prepare_t<L, S>(B, smem_pad)
+#define CALL(L, S) prepare_t<L, S>(B)
     BAND_DISPATCH(lat, storage, CALL);
 #undef CALL
     return -1;

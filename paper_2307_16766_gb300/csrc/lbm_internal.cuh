@@ -607,10 +607,9 @@ int launch_bulk(int lat, int storage, const Geom& G, const Offsets& O, const Reg
 int launch_macros(int lat, int storage, const Geom& G, const void* f, double* rho, double* ux,
                   double* uy, double* T, int* flag, cudaStream_t st);
 // The band of one step fin -> fnew: strip nodes, RK4 of the characteristic
-// boundary state, Dirichlet populations.  smem_pad: extra dynamic shared
-// memory per CTA (0 = none), which keeps other kernels' CTAs off its SMs.
+// boundary state, Dirichlet populations.
 int launch_boundary(int lat, int storage, const Geom& G, const Offsets& O, const Export& E,
-                    const Band& B, const void* fin, void* fnew, int par_t, size_t smem_pad,
+                    const Band& B, const void* fin, void* fnew, int par_t,
                     cudaStream_t st);
 // One grid of the batched band kernel, in device memory.
 struct BandRun {
@@ -637,7 +636,7 @@ int launch_bulk_persistent(int lat, int storage, const BulkRun* runs, int n_runs
 // Opt the persistent bulk kernel in to its dynamic shared memory.
 int prepare_bulk_persistent(int lat, int storage);
 // Opt the band kernel in to its dynamic shared memory (once, at creation).
-int prepare_boundary(int lat, int storage, const Band& B, size_t smem_pad);
+int prepare_boundary(int lat, int storage, const Band& B);
 // Zero-gradient copies (Eq. zg-bc) in fnew, after the bulk update of x_f.
 int launch_zg(int lat, int storage, const Geom& G, const Band& B, void* fnew, cudaStream_t st);
 
