@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--no-fp64-leg", action="store_true")
+    ap.add_argument("--no-fp16-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch-leg", action="store_true")
     ap.add_argument("--no-gradient-leg", action="store_true")
@@ -596,6 +597,11 @@ def main():
         a2 = argparse.Namespace(**vars(args))
         a2.steps = min(args.steps, 50)
         fp64 = run_gpu(a2, rank, world, local_rank, "f64", want_e2e=False)
+    fp16 = None
+    if not args.no_fp16_leg and args.storage == "f32":
+        a2 = argparse.Namespace(**vars(args))
+        a2.steps = min(args.steps, 50)
+        fp16 = run_gpu(a2, rank, world, local_rank, "f16", want_e2e=False)
 
     batch = None
     if not args.no_batch_leg and args.storage == "f32":
@@ -645,6 +651,14 @@ def main():
                             "phased_bulk_ms": fp64["bulk_ms_mean"],
                             "phased_boundary_ms": fp64["boundary_ms_mean"],
                             "interior_GBps": 2 * Q * 8 * fp64["interior_nodes"] / (fp64["interior_ms_mean"] / 1e3) / 1e9}
+        if fp16 is not None:
+            line["fp16"] = {"value": nodes / (fp16["step_ms_total"] / 1e3 / min(K, 50)) / 1e6,
+                            "unit": "MLUPS", "interior_ms": fp16["interior_ms_mean"],
+                            "phased_bulk_ms": fp16["bulk_ms_mean"],
+                            "phased_boundary_ms": fp16["boundary_ms_mean"],
+                            "interior_GBps": 2 * Q * 2 * fp16["interior_nodes"] / (fp16["interior_ms_mean"] / 1e3) / 1e9,
+                            "phased_bulk_GBps": 2 * Q * 2 * fp16["interior_nodes"] / (fp16["bulk_ms_mean"] / 1e3) / 1e9,
+                            "storage": "shifted FP16 (g / w), FP32 arithmetic"}
         if batch is not None:
             line["batch"] = batch
         if large is not None:
