@@ -86,6 +86,12 @@ def test_defaults_and_workspace_size():
     (lbm.LBM_D2Q37, 16, 16, dict(rho0=0.0), False),
     (lbm.LBM_D2Q17, 9, 9, dict(side=[1, 1, 1, 1]), True),          # D2Q17: M = 3 as well
     (lbm.LBM_D2Q17, 9, 8, dict(side=[1, 1, 1, 1]), False),
+    (lbm.LBM_D2Q37, 7616, 7616, dict(side=[1, 1, 1, 1]), True),    # 37 x 7616^2 < 2^31 values
+    (lbm.LBM_D2Q37, 7680, 7616, dict(side=[1, 1, 1, 1]), False),   # 37 x 7616 x 7680 > 2^31
+    (lbm.LBM_D2Q9, 15360, 15360, dict(), True),                    # 9 x 15360^2 < 2^31
+    (lbm.LBM_D2Q9, 16384, 15360, dict(), False),
+    (lbm.LBM_D2Q37, 16, 16, dict(alpha_V=float("nan")), False),    # relaxation parameters finite
+    (lbm.LBM_D2Q37, 16, 16, dict(alpha_T=float("inf")), False),
     (3, 16, 16, dict(), False),                                    # unknown lattice
     (-1, 16, 16, dict(), False),
 ])

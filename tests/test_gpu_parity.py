@@ -290,17 +290,20 @@ def test_d2q37_vortex_1024x512_full_grid_short():
     assert_parity(cfg, f, 20, "f32", "vortex1024")
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_d2q37_pulse_4096_window_matches_periodic_oracle(storage):
-    """The 4096^2 throughput grid (the 256^2 pulse recipe, CBC-RELAX on four
-    sides) in the launch configuration the benchmark times.  After 30 steps
-    the disturbance has travelled ~35 cells and the stencils reach at most
-    90: the 256^2 window around the pulse must equal the oracle's 256^2
-    periodic run of the same pulse (the fields outside the window differ
-    from the periodic images by the Gaussian tail at 128 cells, e^-128), and
-    the boundary layers, which the disturbance has not reached, must still
-    hold the uniform state."""
-    n, w, x0, steps = 4096, 256, 1920, 30
+@pytest.mark.parametrize("n,storage", [(4096, "f64"), (4096, "f32"), (7616, "f32")])
+def test_d2q37_pulse_large_grid_window_matches_periodic_oracle(n, storage):
+    """The 4096^2 throughput grid, and the largest D2Q37 grid the library
+    accepts (7616^2: 37 x 7616^2 population values, just under 2^31, so the
+    32-bit element offsets reach their limit), with the 256^2 pulse recipe
+    (CBC-RELAX on four sides) in the launch configuration the benchmark
+    times.  After 30 steps the disturbance has travelled ~35 cells and the
+    stencils reach at most 90: the 256^2 window around the pulse must equal
+    the oracle's 256^2 periodic run of the same pulse (the fields outside
+    the window differ from the periodic images by the Gaussian tail at 128
+    cells, e^-128), and the boundary layers, which the disturbance has not
+    reached, must still hold the uniform state."""
+    w, steps = 256, 30
+    x0 = n // 2 - w // 2
     cfg, f = W.pulse_d2q37(n, storage=storage, steps=steps)
     rng = W.SplitMix64(0)                       # the recipe's centre offset
     ox, oy = rng.uniform(-10.0, 10.0), rng.uniform(-10.0, 10.0)
@@ -310,9 +313,9 @@ def test_d2q37_pulse_4096_window_matches_periodic_oracle(storage):
     win = [a[x0:x0 + w, x0:x0 + w] for a in got]
     rcfg = W.run("D2Q37", w, w, cfg["tau"], storage="f64", steps=steps)
     ref = oracle_run(rcfg, W.gaussian_pulse(w, w, 1e-3, 1e-3, 8.0, center=centre), steps,
-                     key="pulse4096window")
+                     key="pulse_window_%d" % n)
     e = rel_errors(win, ref)
-    assert max(e.values()) < TOL[storage], (storage, e)
+    assert max(e.values()) < TOL[storage], (n, storage, e)
     rho, ux, uy, T = got
     band = np.ones_like(rho, dtype=bool)
     band[3:-3, 3:-3] = False
