@@ -10,7 +10,8 @@
 // Populations are stored post-collision and shifted, g = f* - w rho0, in SoA
 // planes [Q][ny][nxp].  A bulk node pulls g*_i(x - c_i) for every i.  Away
 // from periodic wrap-around the 37 shifted source rows of a 128-node row
-// segment are staged through shared memory by tensor copies (TMA); stores
+// segment are staged through shared memory by tensor copies (TMA), two row
+// segments per CTA with FP32 / FP16 storage; stores
 // go straight to global memory at fixed plane offsets (Offsets, in the
 // kernel parameter bank).  The FP32/FP16 paths do all of their arithmetic in
 // FP32; the FP64 path in FP64.
@@ -22,7 +23,7 @@ namespace lbmgb {
 
 namespace {
 
-constexpr int kBulkThreads = 128;   // one CTA = one row segment of 128 nodes
+constexpr int kBulkThreads = 128;   // a thread per node of a 128-node row segment
 
 // TMA staging.  For population i a CTA needs the source row segment
 // [x0 - c_ix, x0 + 127 - c_ix] of row y - c_iy.  Planes are stored grouped by
