@@ -300,18 +300,22 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True):
     return res
 
 
-def run_large(args, local_rank, n=4096):
-    """The n x n D2Q37 FP32 pulse (CBC-RELAX on four sides, the 256^2 parity
-    workload's recipe at the size of the largest throughput grid): whole
-    steps timed with CUDA events (its 5 GB of populations exceed L2, so no
-    flush), then the bulk kernel's duration beside the band kernel through
-    the timing hook, then both phases in sequence."""
+def run_large(args, local_rank, n=4096, kind="pulse"):
+    """An n x n D2Q37 FP32 throughput grid: the pulse (CBC-RELAX on four
+    sides, the 256^2 parity workload's recipe) or the benchmark's vortex
+    workload (inflow | CBC-RELAX, periodic y) at that size.  Whole steps
+    timed with CUDA events (5 GB of populations exceed L2, so no flush),
+    then the bulk kernel's duration beside the band kernel through the
+    timing hook, then both phases in sequence."""
     import torch
     import paper_2307_16766_gb300 as lbm
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    cfg, fields = W.pulse_d2q37(n=n, storage="f32")
+    if kind == "pulse":
+        cfg, fields = W.pulse_d2q37(n=n, storage="f32")
+    else:
+        cfg, fields = workload(n, n, "f32", 1)
     sim = lbm.Simulation(cfg, device=dev).init_fields(*fields)
     del fields
     stream = sim.stream
@@ -606,9 +610,10 @@ def main():
     batch = None
     if not args.no_batch_leg and args.storage == "f32":
         batch = run_batch(args, local_rank)
-    large = None
+    large = large_vortex = None
     if not args.no_large_leg and args.storage == "f32":
         large = run_large(args, local_rank)
+        large_vortex = run_large(args, local_rank, kind="vortex")
     gradient = None
     if not args.no_gradient_leg and args.storage == "f32":
         gradient = run_gradient(args, local_rank)
@@ -663,6 +668,8 @@ def main():
             line["batch"] = batch
         if large is not None:
             line["large"] = large
+        if large_vortex is not None:
+            line["large_vortex"] = large_vortex
         if gradient is not None:
             line["gradient"] = gradient
         if not args.no_cpu_baseline and world == 1:
