@@ -364,6 +364,13 @@ def test_vortex_1024x512_20000_steps_fp32_fp16_against_fp64(Ma, capsys):
     assert res["f16"]["rho"] < 5e-3 and res["f16"]["T"] < 5e-3 and res["f16"]["u"] < 2e-2, res
 
 
+def test_d2q37_vortex_1024x512_first_500_steps_f64():
+    """The benchmark configuration as timed (mesoscopic viscous vector) over
+    its first 500 steps, FP64 storage, every node against the oracle."""
+    cfg, f = W.vortex_d2q37(1024, 512, Ma=0.1, steps=500, storage="f64")
+    assert_parity(cfg, f, 500, "f64", "vortex1024_500")
+
+
 def test_f16_storage_error_per_field(capsys):
     """FP16 storage (g / w in half precision, FP32 arithmetic): errors against
     the oracle are reported per field; they stay at the half-precision level."""
