@@ -667,9 +667,13 @@ int setup(lbm_handle* h, int lattice, int nx, int ny, double tau, const lbm_cbc_
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(h, e, "stream set-up");
-    // Zero the strips (positions no kernel writes stay finite) and the
-    // status words, and upload the boundary tables.
-    e = cudaMemsetAsync(h->E.stripU, 0, pl.stripU_n * h->E.sesize, h->stream);
+    // Zero the population buffers (the row padding x >= nx is never written,
+    // and a saved state then holds no leftover bytes of the workspace), the
+    // strips (positions no kernel writes stay finite) and the status words,
+    // and upload the boundary tables.
+    e = cudaMemsetAsync(h->f[0], 0, h->f_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, h->f_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->E.stripU, 0, pl.stripU_n * h->E.sesize, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, 2 * sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->E.stripN, 0, pl.stripN_n * h->E.sesize, h->stream);
     if (e == cudaSuccess && !pl.ud.empty())

@@ -389,6 +389,27 @@ def test_f16_storage_error_per_field(capsys):
 
 # ---------------------------------------------------------- API behaviour ---
 
+def test_saved_state_holds_no_leftover_workspace_bytes():
+    """A handle's population buffers are zeroed at creation, so a saved
+    state does not depend on what the workspace held before (the row
+    padding x >= nx is never written by a kernel): two handles made on
+    workspaces left dirty with different bytes save equal states."""
+    import torch
+    cfg = W.run("D2Q17", 200, 100, 0.8, sides=("cbc",) * 4, schemes=("cbc",) * 4,
+                dirichlet="neep", storage="f32")
+    f = W.gaussian_pulse(200, 100, 1e-3, 1e-3, 4.0)
+    states = []
+    for fill in (float("nan"), 7.0):
+        junk = torch.full((64 << 20,), fill, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        del junk                         # back to the caching allocator, dirty
+        sim = lbm().Simulation(cfg).init_fields(*f)
+        sim.step(5)
+        states.append(sim.get_state())
+        sim.close()
+    assert states[0] == states[1]
+
+
 def test_checkpoint_resume_is_bit_exact():
     cfg, f = W.pulse_d2q37(64, alpha_T=0.5, steps=100, storage="f32", width=5.0, offset=3.0)
     sim = lbm().Simulation(cfg).init_fields(*f)
