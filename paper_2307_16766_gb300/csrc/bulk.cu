@@ -363,14 +363,23 @@ __global__ void k_init(Geom G, Export E, const double* __restrict__ rho,
     m.ux = ux[n];
     m.uy = uy[n];
     m.dT = L::THERMAL ? T[n] - 1.0 : 0.0;
-    double geq[L::Q];
-    equilibrium<LAT, double>(m, geq);
+    // the equilibrium in the storage's arithmetic (as the bulk update
+    // evaluates it), from the deviations formed in FP64
+    using C = typename Store<S>::C;
+    Moments<LAT, C> mc;
+    mc.s0 = C(m.s0);
+    mc.rho = C(m.rho);
+    mc.ux = C(m.ux);
+    mc.uy = C(m.uy);
+    mc.dT = C(m.dT);
+    C geq[L::Q];
+    equilibrium<LAT, C>(mc, geq);
     S* out = f + (long long)y * G.nxp + x;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        double v = geq[i];
-        if (Store<S>::SCALED) v *= 1.0 / L::w(i);
-        Store<S>::put(out + (long long)L::plane_of(i) * G.plane, typename Store<S>::C(v));
+        C v = geq[i];
+        if (Store<S>::SCALED) v *= C(1.0 / L::w(i));
+        Store<S>::put(out + (long long)L::plane_of(i) * G.plane, v);
     }
     // strips of time 0 (parity 0): U0 and zero non-equilibrium moments
     const int dd[4] = {x - G.M, G.nx - 1 - G.M - x, y - G.M, G.ny - 1 - G.M - y};
