@@ -224,6 +224,9 @@ __global__ void k_tl_stage(Geom G, Band B, Relax<TB<S>> P, const TB<S>* __restri
     // stage 0 reads only time t: the bulk pass launched after it for early
     // start (it writes only t + 1) may begin now
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // stages 2 and 3 start early behind the stage before them: wait for it
+    // (and its memory) before reading what it wrote
+    if (stage >= 2) asm volatile("griddepcontrol.wait;" ::: "memory");
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= B.n_unk) return;
     const UDesc D = B.ud[u];
@@ -291,6 +294,8 @@ __global__ void k_tl_dirichlet(Geom G, Band B, const TB<S>* __restrict__ Uf, S* 
 {
     using L = Lat<LAT>;
     using C1 = Dual<typename Store<S>::C, 1>;
+    // launched early behind the last stage: wait for it
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
     if (u >= B.n_unk) return;
@@ -489,8 +494,10 @@ int tl_step_t(const TLState& T, const Geom& G, const Export& E, const Band& B, c
     }
     if (B.n_unk > 0) {
         for (int k = 1; k < 4; ++k)
-            if (stage(k, false)) return -1;
-        k_tl_dirichlet<LAT, S><<<dim3(nb, kTD), 128, 0, st>>>(G, B, static_cast<const R*>(T.Uf), fo, to);
+            if (stage(k, k >= 2)) return -1;
+        if (launch_ex(k_tl_dirichlet<LAT, S>, dim3(nb, kTD), dim3(128), 0, st, true, G, B,
+                      static_cast<const R*>(T.Uf), fo, to))
+            return -1;
     }
     if (B.viscous == VIS_MESO && E.nslots > 0)
         k_tl_neq<LAT, S><<<(E.nslots + 127) / 128, 128, 0, st>>>(G, E, fi, ti, static_cast<R*>(T.stripN[par ^ 1]));
