@@ -1,0 +1,45 @@
+"""Host-side helpers of bench.py: the DRAM-traffic figure from the committed
+ncu capture (used only while the bulk kernel's source is unchanged), the
+bulk-node counts of the benchmark workloads, and the CPU baseline's one-thread
+leg (which restores the oracle's thread count)."""
+import hashlib
+import os
+import re
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import lbm_workloads as W  # noqa: E402
+import oracle  # noqa: E402
+
+
+def test_traffic_capture_matches_the_current_bulk_source():
+    line = [l for l in open(os.path.join(ROOT, "profiles", "k_bulk_d2q37_traffic.txt"))
+            if l.startswith("traffic")][0]
+    m = re.match(r"traffic\s+storage=(\w+)\s+nodes=(\d+)\s+bytes=(\d+)\s+src=(\w+)", line)
+    src = open(os.path.join(ROOT, "paper_2307_16766_gb300", "csrc", "bulk.cu"), "rb").read()
+    assert m.group(4) == hashlib.sha256(src).hexdigest()[:12]
+    nodes, b = int(m.group(2)), int(m.group(3))
+    assert bench.bulk_traffic("f32", nodes) == b
+    assert abs(bench.bulk_traffic("f32", 2 * nodes) - 2 * b) <= 1
+    assert bench.bulk_traffic("f64", nodes) is None          # no capture for that storage
+
+
+def test_bulk_nodes_of_the_workloads():
+    cfg, _ = bench.workload(1024, 512, "f32", 1)                    # inflow | CBC, periodic y
+    assert bench.bulk_nodes(cfg) == (1024 - 6) * 512
+    cfg, _ = W.pulse_d2q37(64, storage="f32")                       # four characteristic sides
+    assert bench.bulk_nodes(cfg) == (64 - 6) ** 2
+    cfg = W.run("D2Q9", 40, 30, 0.6, sides=("cbc",) * 4)
+    assert bench.bulk_nodes(cfg) == 38 * 28
+
+
+def test_cpu_baseline_reports_one_thread_and_restores_threads():
+    cfg, f = W.vortex_d2q37(64, 32, steps=1, storage="f64")
+    n = oracle.threads()
+    r = bench.cpu_baseline(cfg, f, seconds=0.2, seconds_1t=0.2)
+    assert oracle.threads() == n
+    assert r["cores"] == n and r["kind"] == "oracle" and r["value"] > 0 and r["single_thread_value"] > 0
+    assert isinstance(r["cpu"], str) and r["cpu"]
