@@ -106,6 +106,27 @@ def isentropic_vortex(nx, ny, lattice, Ma, strength=0.05, radius=20.0, center=No
     return rho, ux, uy, T
 
 
+def thermal_vortex(n, L, lattice, Ma=0.1, r=0.7, b=0.15, K=0.0, offset=0, isothermal=False):
+    """The thermal vortex of the paper's Sec. 4.2 on an n x n grid whose
+    window [offset, offset + L)^2 is the L x L benchmark domain: normalised
+    coordinates x^ = 2 (x - 1) / (L - 1) - 1 (x counted from 1 in the
+    window), a vortex at (K / (L - 1), 0) of radius r and strength b in a
+    stream u0 = (Ma c_s, 0):  u = u0 + (5 c_s Ma / 2) 2^(-(x^2 + y^2) / b^2)
+    (y, -x) and T = T0 + y^ (5 c_s Ma / 2) 2^(-(x^2 + y^2) / b^2) inside r
+    (T = T0 for the iso-thermal vortex of Sec. 4.4), rho = rho0 = 1."""
+    cs = math.sqrt(CS2[lattice])
+    i = np.arange(n, dtype=np.float64) - offset
+    xh = 2.0 * i / (L - 1) - 1.0
+    X, Y = np.meshgrid(xh, xh)
+    dx, dy = X - K / (L - 1), Y
+    inside = dx * dx + dy * dy < r * r
+    amp = 2.5 * cs * Ma * np.power(2.0, -(dx * dx + dy * dy) / (b * b))
+    ux = Ma * cs + np.where(inside, amp * dy, 0.0)
+    uy = np.where(inside, -amp * dx, 0.0)
+    T = np.ones_like(X) if isothermal else 1.0 + np.where(inside, Y * amp, 0.0)
+    return np.ones_like(X), ux, uy, T
+
+
 def shear_wave(nx, ny, amp, k_axis="x", rho0=1.0):
     """u_y = A sin(2 pi x / nx) (k_axis "x") or u_x = A sin(2 pi y / ny)."""
     x, y = grid(nx, ny)

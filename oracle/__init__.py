@@ -9,8 +9,9 @@ A run is described by a plain dict (see ``lbm_workloads``) with the keys
 (four of "periodic" | "cbc" | "inflow" | "zg", order W, E, S, N),
 ``schemes`` (four of "lodi" | "lodi_relax" | "cbc" | "cbc_relax"),
 ``viscous`` ("meso" | "fd" | "off"), ``dirichlet`` ("eq" | "neep" | "reg"), ``alpha_T``, ``beta_P``,
-``t_inf``, ``p_inf`` (four values), ``inflow`` (rho, ux, uy, T) and ``alpha_V`` (the relaxation of
-the viscous term in Eq. CBC-Relax, 0 by default: the paper's equation).
+``t_inf``, ``p_inf`` (four values), ``inflow`` (rho, ux, uy, T), ``alpha_V`` (the relaxation of
+the viscous term in Eq. CBC-Relax, 0 by default: the paper's equation) and, for tests only,
+``meso_depth`` (where the mesoscopic viscous stencil starts below x_f; default M).
 """
 import ctypes as C
 import os
@@ -34,7 +35,7 @@ class Params(C.Structure):
         ("viscous", C.c_int), ("dirichlet", C.c_int),
         ("alpha_T", C.c_double), ("beta_P", C.c_double), ("t_inf", C.c_double),
         ("p_inf", C.c_double * 4), ("inflow", C.c_double * 4),
-        ("alpha_V", C.c_double),
+        ("alpha_V", C.c_double), ("meso_depth", C.c_int),
     ]
 
 
@@ -99,6 +100,7 @@ def make_params(cfg) -> Params:
     p.beta_P = float(cfg.get("beta_P", 0.0))
     p.t_inf = float(cfg.get("t_inf", 0.0))
     p.alpha_V = float(cfg.get("alpha_V", 0.0))
+    p.meso_depth = int(cfg.get("meso_depth", -1))
     cs2 = lattice_info(cfg["lattice"])["cs2"]
     pinf = cfg.get("p_inf", [cs2 * p.rho0] * 4)
     for i in range(4):

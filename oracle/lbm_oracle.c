@@ -25,6 +25,12 @@
  *  - Sec. 3.1: the (4,1) entry of S is T~/(4 rho c_s^2).
  *  - Eq. LaplaceU: f^neq = f - f^eq; sigma' = -(1 - 1/(2 tau)) sum c c f^neq.
  *  - Eq. LaplaceT: physical heat flux q = (1 - 1/(2 tau)) 1/2 sum f^neq |c-u|^2 (c-u).
+ *  - Sec. 3.3, "Evaluation of viscous terms": the one-sided stencil of the
+ *    mesoscopic viscous terms starts M nodes below x_f, at the first node
+ *    none of whose populations was streamed from a boundary layer.  At x_f
+ *    itself (the literal reading) the moments mix in the Dirichlet-written
+ *    layers and the scheme grows on the paper's Sec. 4.2 vortex, where the
+ *    paper reports it stable (tests/test_oracle_viscous.py).
  *  - D2Q9 runs isothermal (Sec. 4.4) with the 3x3 system for (rho, u_n, u_t).
  *  - Corners: plain LODI (Eq. PNR) along the outward diagonal at the
  *    innermost corner node, copied to the M x M corner block (Sec. 3.3, 4.4).
@@ -531,6 +537,14 @@ static int validate(const orc_params* p, const lattice_t* L)
     }
     if (p->side[0] != ORC_PERIODIC && p->nx < 2 * L->M + 3) return -1;
     if (p->side[2] != ORC_PERIODIC && p->ny < 2 * L->M + 3) return -1;
+    if (p->viscous == ORC_VIS_MESO) {
+        /* the mesoscopic stencil's deepest node, x_f - (d0 + 2) n, must be a
+         * bulk node */
+        int d0 = p->meso_depth < 0 ? L->M : p->meso_depth;
+        int need = 2 * L->M + 3 + d0;
+        if ((p->side[0] == ORC_SIDE_CBC || p->side[1] == ORC_SIDE_CBC) && p->nx < need) return -1;
+        if ((p->side[2] == ORC_SIDE_CBC || p->side[3] == ORC_SIDE_CBC) && p->ny < need) return -1;
+    }
     if (p->side[0] != ORC_PERIODIC && p->side[2] != ORC_PERIODIC) {
         int ncbc = 0;
         for (int sd = 0; sd < 4; sd++) ncbc += p->side[sd] == ORC_SIDE_CBC;
@@ -679,11 +693,12 @@ void orc_init(orc_sim* s, const double* rho, const double* ux, const double* uy,
 
 static int is_bulk(const orc_sim* s, int n) { return n >= 0 && s->kind[n] == K_BULK; }
 
-/* Mesoscopic viscous vector at node (x, y) acting as x_f of side sd, from the
- * pre-collision populations of time t (Sec. 3.3, "Evaluation of viscous
- * terms"): normal derivatives one-sided into the bulk (Eq. FD-dx-bw at x_f),
- * tangential derivatives central (Eq. FD-dx-center), one-sided inward where
- * the tangential neighbour is itself a boundary node. */
+/* Mesoscopic viscous vector of side sd with its stencil starting at node
+ * (x, y), from the pre-collision populations of time t (Sec. 3.3,
+ * "Evaluation of viscous terms"): normal derivatives one-sided into the bulk
+ * (Eq. FD-dx-bw through (x, y), (x, y) - n, (x, y) - 2n), tangential
+ * derivatives central (Eq. FD-dx-center), one-sided inward where the
+ * tangential neighbour is itself a boundary node. */
 static void vis_meso(const orc_sim* s, int sd, int x, int y, double V[4])
 {
     double n[2], t[2];
@@ -982,9 +997,10 @@ static void step_once(orc_sim* s)
                 } else if (s->P.viscous == ORC_VIS_FD) {
                     vis_fd(s, sd, s->u_j[u], s->u_p[u], s->W, s->V + 4 * u);
                 } else {
-                    int x, y;
+                    /* stencil start: M nodes below x_f (see the readings) */
+                    int x, y, d0 = s->P.meso_depth < 0 ? s->M : s->P.meso_depth;
                     xf_of(s, sd, s->u_p[u], &x, &y);
-                    vis_meso(s, sd, x, y, s->V + 4 * u);
+                    vis_meso(s, sd, x - d0 * SN[sd][0], y - d0 * SN[sd][1], s->V + 4 * u);
                 }
             }
             to_local(s->Y + 4 * u, n, t, Ul);

@@ -48,6 +48,12 @@ typedef struct {
     double inflow[4];  /* rho, ux, uy, T imposed on inflow sides               */
     double alpha_V;    /* relaxation of the viscous term towards 0 in Eq.
                           CBC-Relax (an extension; 0 is the paper's equation) */
+    int meso_depth;    /* depth below x_f of the first node of the mesoscopic
+                          viscous stencil (Sec. 3.3, "Evaluation of viscous
+                          terms"); negative: M, the first node none of whose
+                          populations was streamed from a boundary layer.  0
+                          is x_f itself, the literal reading, kept so a test
+                          can show its growth on the Sec. 4.2 vortex.        */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -95,8 +101,10 @@ void     orc_populations(const orc_sim* s, double* g);
 /* Non-equilibrium moments at node (x,y): sigma'_xx, sigma'_xy, sigma'_yy
  * (Eq. LaplaceU) and q_x, q_y (Eq. LaplaceT, with the (1-1/(2 tau)) factor). */
 void     orc_neq_moments(const orc_sim* s, int x, int y, double out[5]);
-/* Viscous vector V (local frame of side `side`) that the boundary solver
- * uses at node (x,y) playing the role of x_f (mesoscopic form). */
+/* Mesoscopic viscous vector V (local frame of side `side`) with its stencil
+ * starting at node (x,y): one-sided normal differences through (x,y),
+ * (x,y) - n, (x,y) - 2n and central tangential ones.  The boundary solver
+ * evaluates it at x_f - meso_depth n. */
 void     orc_vis_meso_at(const orc_sim* s, int side, int x, int y, double V[4]);
 /* Boundary state of the last step: U of each node in deviation form,
  * [ny][nx][4]; meaningful on boundary nodes. */
