@@ -25,11 +25,13 @@
  *    duration of that call.
  *  - Work is issued on the handle's CUDA stream (default: the legacy default
  *    stream; see lbm_set_stream()).  lbm_step() is asynchronous; the calls
- *    that return data to the caller synchronise the stream.  Each handle
- *    also owns one internal stream of the highest priority: lbm_step() forks
- *    onto it from the handle's stream and joins back before returning
- *    control of the step, so work issued afterwards on the handle's stream
- *    sees the whole step (and the fork/join is legal under stream capture).
+ *    that return data to the caller synchronise the stream.  A step's
+ *    kernels all go on the handle's stream (the bulk kernel behind the band
+ *    kernel with programmatic stream serialization, so the two run side by
+ *    side), so work issued afterwards on that stream sees the whole step.
+ *    Only with the timing hook of lbm_set_kernel_events() does a step fork
+ *    onto the handle's internal stream and join back (legal under stream
+ *    capture).
  *  - A handle must not be used from two threads at once.
  */
 #ifndef LBM_CBC_H
@@ -71,8 +73,10 @@ enum lbm_side_kind {
 enum lbm_scheme { LBM_LODI = 0, LBM_LODI_RELAX = 1, LBM_CBC = 2, LBM_CBC_RELAX = 3 };
 
 /* Viscous vector V of the CBC schemes: mesoscopic (Eqs. LaplaceU, LaplaceT,
- * evaluated at the bulk node next to the boundary), finite differences of the
- * macros ("-FD" of Sec. 4.2), or none. */
+ * with the one-sided stencil starting M nodes below x_f, at the first node
+ * none of whose populations was streamed from a boundary layer; a
+ * characteristic side then needs 3 M + 3 nodes across), finite differences
+ * of the macros ("-FD" of Sec. 4.2), or none. */
 enum lbm_viscous { LBM_VISCOUS_MESO = 0, LBM_VISCOUS_FD = 1, LBM_VISCOUS_OFF = 2 };
 
 /* Mesoscopic Dirichlet condition (Sec. 3.3): equilibrium, Eq. NEEP, or NEEP
@@ -111,8 +115,9 @@ int lbm_params_default(lbm_cbc_params* p);
 int lbm_workspace_bytes(int lattice, int nx, int ny, const lbm_cbc_params* p, size_t* bytes);
 
 /* Create a solver for an nx x ny grid with BGK relaxation time tau > 1/2
- * (Eq. bgk).  Non-periodic axes need at least 2M + 3 nodes; when both axes
- * are non-periodic, either all four sides are CBC or none is.  Allocates its
+ * (Eq. bgk).  Non-periodic axes need at least 2M + 3 nodes (3M + 3 across
+ * a CBC side with the mesoscopic viscous vector); when both axes are
+ * non-periodic, either all four sides are CBC or none is.  Allocates its
  * device memory with cudaMalloc on the current device. */
 int lbm_create(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p,
                lbm_handle** out);
@@ -296,24 +301,32 @@ void lbm_batch_destroy(lbm_batch* b);
  *   strip_t   device, [3][length][4]: the same quantities on the bulk nodes
  *             at depths 0, 1, 2 inside the layers (x_f, x_f - n, x_f - 2n)
  *             at time t;  strip_t1: the same at time t + 1.
- *   neq_t     device, [3][length][5]: sigma'_xx, sigma'_xy, sigma'_yy, q_x,
- *             q_y on those nodes at time t; needed only when p->viscous is
+ *   neq_t     device, [3][length][9]: the nodes of the mesoscopic stencil,
+ *             depths M, M + 1, M + 2 inside the layers (x_f - M n, ...), at
+ *             time t: sigma'_xx, sigma'_xy, sigma'_yy, q_x, q_y, then
+ *             rho - rho0, u_x, u_y, T - 1.  sigma' = -(1 - 1/(2 tau))
+ *             sum_i c_i c_i (f_i - f_i^eq) and q = +(1 - 1/(2 tau)) 1/2
+ *             sum_i (f_i - f_i^eq) |c_i - u|^2 (c_i - u), from the node's
+ *             pulled (pre-collision) populations -- not the raw
+ *             non-equilibrium moments.  Needed only when p->viscous is
  *             LBM_VISCOUS_MESO, otherwise may be NULL.
  *   stream    cudaStream_t (NULL = legacy default); the call is asynchronous.
- * Only p->scheme[side], p->viscous, alpha_T, beta_P, t_inf, p_inf[side] and
- * rho0 are read.  length * M may not exceed 12288 (4096 positions on D2Q37
- * and D2Q17, 12288 on D2Q9); larger sides are rejected with LBM_ERR_ARG and a message
- * on stderr.
+ * tau is the BGK relaxation time.  Of p, only scheme[side], viscous,
+ * alpha_T, beta_P, t_inf, alpha_V, p_inf[side] and rho0 are read.
+ * length * M may not exceed 12288 (4096 positions on D2Q37 and D2Q17, 12288
+ * on D2Q9); larger sides are rejected with LBM_ERR_ARG and a message on
+ * stderr.
  *
  * Nothing is allocated: the RK4 stage scratch lives in one fixed ~1.6 MB
  * device array inside the library, held by every GPU that loads it until the
- * process exits.  The first call on a device looks that array's address up
- * (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents
- * (every value a stage reads is written earlier in the same call, so nothing
- * needs clearing); calls that overlap on the GPU -- on different streams, or
- * from different threads -- race on it and must be serialised by the
- * caller. */
+ * process exits.  The first call in a CUDA context looks that array's
+ * address up (cudaGetSymbolAddress) and keeps it for that context, so make
+ * that first call before any stream capture; a device reset that recreates
+ * the primary context at the same address is not supported.  All calls share
+ * the array and it keeps the last call's contents (every value a stage reads
+ * is written earlier in the same call, so nothing needs clearing); calls
+ * that overlap on the GPU -- on different streams, or from different
+ * threads -- race on it and must be serialised by the caller. */
 int lbm_cbc_side_step_noalloc(int lattice, int side, int length, double tau,
                               const lbm_cbc_params* p, double* Ub, const double* strip_t,
                               const double* strip_t1, const double* neq_t, void* stream);

@@ -184,6 +184,17 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
         for (int s = 0; s < 4; ++s) ncbc += p->side[s] == LBM_SIDE_CBC;
         if (ncbc != 0 && ncbc != 4) { err = "with four open sides, either all or none must be CBC"; return LBM_ERR_ARG; }
     }
+    if (p->viscous == LBM_VISCOUS_MESO) {
+        // the mesoscopic stencil's deepest node, x_f - (M + 2) n, must be a
+        // bulk node: 3 M + 3 nodes on an axis with a characteristic side
+        const int nmin_v = 3 * M + 3;
+        if (((p->side[0] == LBM_SIDE_CBC || p->side[1] == LBM_SIDE_CBC) && nx < nmin_v) ||
+            ((p->side[2] == LBM_SIDE_CBC || p->side[3] == LBM_SIDE_CBC) && ny < nmin_v)) {
+            err = fmt("the mesoscopic viscous terms need at least %d nodes across a characteristic side",
+                      nmin_v);
+            return LBM_ERR_ARG;
+        }
+    }
     const int nxp = (nx + 63) / 64 * 64;
     if ((double)Q * ny * nxp >= 2147483647.0) { err = "grid too large (more than 2^31 population values)"; return LBM_ERR_ARG; }
 
@@ -217,6 +228,9 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
 
     // strips: slots (side, depth, position) of the characteristic sides
     Export& E = pl.E;
+    const bool meso = p->viscous == LBM_VISCOUS_MESO;
+    // depths 0..2 for the stencils; M..M+2 for the mesoscopic viscous terms
+    E.ND = 3 + (meso ? M : 0);
     int L[4], lo[4], hi[4], tper[4];
     for (int s = 0; s < 4; ++s) {
         L[s] = s < 2 ? ny : nx;
@@ -226,7 +240,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
         E.cbc[s] = p->side[s] == LBM_SIDE_CBC;
         E.L[s] = L[s];
         E.offS[s] = E.nslots;
-        if (E.cbc[s]) E.nslots += 3 * L[s];
+        if (E.cbc[s]) E.nslots += E.ND * L[s];
     }
     auto slot = [&](int s, int d, int pp) {
         if (tper[s]) pp = ((pp % L[s]) + L[s]) % L[s];
@@ -278,12 +292,17 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
                 D.nb[4] = ref(s, j, pp + 1);
                 D.nb[5] = ref(s, j, pp - 1);
                 D.tmode = tper[s] ? 0 : (pp == hi[s] ? 1 : (pp == lo[s] ? -1 : 0));
-                D.vs[0] = slot(s, 0, pp);
-                D.vs[1] = slot(s, 1, pp);
-                D.vs[2] = slot(s, 2, pp);
-                if (D.tmode == 0) { D.vs[3] = slot(s, 0, pp + 1); D.vs[4] = slot(s, 0, pp - 1); }
-                else if (D.tmode == 1) { D.vs[3] = slot(s, 0, pp - 1); D.vs[4] = slot(s, 0, pp - 2); }
-                else { D.vs[3] = slot(s, 0, pp + 1); D.vs[4] = slot(s, 0, pp + 2); }
+                if (meso) {
+                    // Sec. 3.3, "Evaluation of viscous terms": the one-sided
+                    // stencil starts M nodes below x_f, at the first node none
+                    // of whose populations came from a boundary layer
+                    D.vs[0] = slot(s, M, pp);
+                    D.vs[1] = slot(s, M + 1, pp);
+                    D.vs[2] = slot(s, M + 2, pp);
+                    if (D.tmode == 0) { D.vs[3] = slot(s, M, pp + 1); D.vs[4] = slot(s, M, pp - 1); }
+                    else if (D.tmode == 1) { D.vs[3] = slot(s, M, pp - 1); D.vs[4] = slot(s, M, pp - 2); }
+                    else { D.vs[3] = slot(s, M, pp + 1); D.vs[4] = slot(s, M, pp + 2); }
+                }
                 int x, y;
                 side_xf(s, pp, nx, ny, M, x, y);
                 D.wsrc = goff(x, y);
@@ -359,7 +378,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
         // grid node of strip slot sl: side s, depth d, position pp
         auto slot_side = [&](int sl) {
             int s = 0;
-            while (!(E.cbc[s] && sl >= E.offS[s] && sl < E.offS[s] + 3 * L[s])) ++s;
+            while (!(E.cbc[s] && sl >= E.offS[s] && sl < E.offS[s] + E.ND * L[s])) ++s;
             return s;
         };
         auto slot_x = [&](int sl) {
@@ -407,22 +426,28 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
                     err = fmt("internal: boundary tile of %zu unknowns", list.size());
                     return LBM_ERR_ARG;
                 }
-                // strip nodes the tile reads or owns; node key = grid offset
+                // strip nodes the tile reads or owns; node key = grid offset;
+                // `use` adds kSN* bits to the node's flags
                 std::vector<StripNode> nodes;
                 std::unordered_map<int, int> n2l, fxl;
-                auto node_of = [&](int sl) {
+                auto node_of = [&](int sl, int use) {
                     const int x = slot_x(sl), y = slot_y(sl), key = goff(x, y);
                     auto it = n2l.find(key);
-                    if (it != n2l.end()) return it->second;
+                    if (it != n2l.end()) {
+                        nodes[it->second].flags |= use;
+                        return it->second;
+                    }
                     n2l[key] = int(nodes.size());
-                    nodes.push_back(StripNode{x, y, sl, -1, -1});
+                    nodes.push_back(StripNode{x, y, sl, -1, -1, use});
                     return int(nodes.size()) - 1;
                 };
-                // the strips of the tile's own positions: written by the tile
-                for (int d = 0; d < 3; ++d)
+                // the strips of the tile's own positions: pulled and written
+                // by the tile (with the non-equilibrium moments at the depths
+                // of the mesoscopic stencil)
+                for (int d = 0; d < E.ND; ++d)
                     for (int pp = a; pp <= b; ++pp) {
                         const int sl = slot(s, d, pp);
-                        nodes[node_of(sl)].gslot = sl;
+                        nodes[node_of(sl, kSNPull | (meso && d >= M ? kSNNeq : 0))].gslot = sl;
                     }
                 pl.tbeg.push_back(int(pl.ld.size()));
                 for (size_t q = 0; q < list.size(); ++q) {
@@ -431,12 +456,12 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
                     const bool comp = level[q] <= 3;
                     for (int k = 0; k < 6; ++k) {
                         if (D.nb[k] >= 0) D.nb[k] = g2l[D.nb[k]] >= 0 ? g2l[D.nb[k]] : 0;
-                        else D.nb[k] = comp ? -(node_of(-Dg.nb[k] - 1) + 1) : -1;
+                        else D.nb[k] = comp ? -(node_of(-Dg.nb[k] - 1, kSNLoadT | kSNPull) + 1) : -1;
                     }
                     for (int k = 0; k < 5; ++k)
-                        D.vs[k] = comp && D.kind < 4 && p->viscous == LBM_VISCOUS_MESO ? node_of(Dg.vs[k]) : 0;
+                        D.vs[k] = comp && D.kind < 4 && meso ? node_of(Dg.vs[k], kSNLoadT) : 0;
                     if (level[q] == 0 && p->dirichlet != LBM_DIRICHLET_EQ) {
-                        const int nl = node_of(Dg.wslot);
+                        const int nl = node_of(Dg.wslot, kSNPull);
                         D.wslot = nl;
                         auto it = fxl.find(nl);
                         if (it == fxl.end()) {
@@ -472,7 +497,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
         std::memset(&pad_u, 0, sizeof pad_u);
         pad_u.level = 99;
         pl.ldp.assign((size_t)B.n_tiles * kTileUnknowns, pad_u);
-        pl.snp.assign((size_t)B.n_tiles * B.max_nodes, StripNode{-1, -1, 0, -1, -1});
+        pl.snp.assign((size_t)B.n_tiles * B.max_nodes, StripNode{-1, -1, 0, -1, -1, 0});
         for (int t = 0; t < B.n_tiles; ++t) {
             std::copy(pl.ld.begin() + pl.tbeg[t], pl.ld.begin() + pl.tbeg[t + 1],
                       pl.ldp.begin() + (size_t)t * kTileUnknowns);

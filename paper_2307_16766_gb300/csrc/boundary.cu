@@ -362,9 +362,21 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     // the strip node this thread pulls: node k goes to CTA k % 4, and the
     // nodes of a CTA are dealt round the four warps
     const int kp = rank + kCluster * (4 * (l % 32) + l / 32);
-    StripNode Na{-1, -1, 0, -1, -1}, Nb{-1, -1, 0, -1, -1};
-    if (l < ns) Na = snt[l];
+    StripNode Nb{-1, -1, 0, -1, -1, 0};
     if (kp < ns) Nb = snt[kp];
+    // the time-t slots this thread loads: nodes l, l + 128, ... (descriptors
+    // of the first kLT issued here, the rest in a loop)
+    constexpr int kLT = 3;
+    int tsl[kLT];
+#pragma unroll
+    for (int j = 0; j < kLT; ++j) {
+        const int k = l + j * kTileThreads;
+        tsl[j] = -1;
+        if (k < ns) {
+            const StripNode& N = snt[k];
+            if (N.x >= 0 && (N.flags & kSNLoadT)) tsl[j] = N.tslot;
+        }
+    }
     const UDesc D = B.ld[(long long)tile * kTileUnknowns + l];
     if (l == 0) {
 #pragma unroll
@@ -381,11 +393,14 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     //    out; post-collision populations of Eq. NEEP sources kept locally
     const R* gU = static_cast<const R*>(E.stripU) + (long long)par_t * E.nslots * 4;
     const R* gN = static_cast<const R*>(E.stripN) + (long long)par_t * E.nslots * 5;
+    const bool meso = B.viscous == VIS_MESO;
     auto load_t = [&](int k, int ts) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) SUt[4 * k + c] = gU[4LL * ts + c];
+        if (meso) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) SNt[5 * k + c] = gN[5LL * ts + c];
+            for (int c = 0; c < 5; ++c) SNt[5 * k + c] = gN[5LL * ts + c];
+        }
     };
     auto pull_t1 = [&](int k, const StripNode& N) {
         C g[L::Q];
@@ -408,14 +423,16 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
 #pragma unroll
         for (int c = 0; c < 4; ++c) bcast(SUt1 + 4 * k + c, U1[c]);
         if (N.gslot >= 0) {             // the strips of t + 1, for the next step
-            R N1[5];
-            neq_moments<LAT, C, R>(g, m, R(1) - R(0.5) * omega_of<R>(G), N1);
             R* u = static_cast<R*>(E.stripU) + ((long long)(par_t ^ 1) * E.nslots + N.gslot) * 4;
-            R* q = static_cast<R*>(E.stripN) + ((long long)(par_t ^ 1) * E.nslots + N.gslot) * 5;
 #pragma unroll
             for (int c = 0; c < 4; ++c) u[c] = U1[c];
+            if (N.flags & kSNNeq) {     // a node of the mesoscopic stencil
+                R N1[5];
+                neq_moments<LAT, C, R>(g, m, R(1) - R(0.5) * omega_of<R>(G), N1);
+                R* q = static_cast<R*>(E.stripN) + ((long long)(par_t ^ 1) * E.nslots + N.gslot) * 5;
 #pragma unroll
-            for (int c = 0; c < 5; ++c) q[c] = N1[c];
+                for (int c = 0; c < 5; ++c) q[c] = N1[c];
+            }
         }
     };
     // U(t) of the tile's unknowns: every CTA loads its own copy
@@ -426,15 +443,17 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         const double2 a = p[0], b = p[1];
         U0[0] = a.x; U0[1] = a.y; U0[2] = b.x; U0[3] = b.y;
     }
-    if (Na.x >= 0) load_t(l, Na.tslot);
-    if (Nb.x >= 0) pull_t1(kp, Nb);
-    for (int k = l + kTileThreads; k < ns; k += kTileThreads) {
+#pragma unroll
+    for (int j = 0; j < kLT; ++j)
+        if (tsl[j] >= 0) load_t(l + j * kTileThreads, tsl[j]);
+    if (Nb.x >= 0 && (Nb.flags & kSNPull)) pull_t1(kp, Nb);
+    for (int k = l + kLT * kTileThreads; k < ns; k += kTileThreads) {
         const StripNode N = snt[k];
-        if (N.x >= 0) load_t(k, N.tslot);
+        if (N.x >= 0 && (N.flags & kSNLoadT)) load_t(k, N.tslot);
     }
     for (int k = kp + kCluster * kTileThreads; k < ns; k += kCluster * kTileThreads) {
         const StripNode N = snt[k];
-        if (N.x >= 0) pull_t1(k, N);
+        if (N.x >= 0 && (N.flags & kSNPull)) pull_t1(k, N);
     }
     if (lev <= 4) {
 #pragma unroll
@@ -891,8 +910,37 @@ constexpr size_t kNoAllocDoubles = 16ull * kNoAllocMaxUnknowns + kNoAllocMaxUnkn
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
+// Address of the scratch array per CUDA context: a module is loaded once per
+// context, so another context on the same device (a driver-API context, or
+// the primary context recreated after a reset) holds its own copy.
+struct NoallocAddr {
+    void* ctx;
+    double* addr;
+};
 std::mutex g_noalloc_mutex;
-double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+NoallocAddr g_noalloc_addr[kNoAllocMaxDevices] = {};
+int g_noalloc_n = 0;
+
+// The current context (cuCtxGetCurrent, looked up through the runtime), or
+// null if the driver does not provide it.
+void* current_context()
+{
+    using Fn = int (*)(void**);
+    static Fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(p);
+    }
+    void* ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
 
 template <int LAT>
 __global__ void __launch_bounds__(kBandThreads)
@@ -937,8 +985,9 @@ __global__ void __launch_bounds__(kBandThreads)
         mask = incoming_mask<Lt::THERMAL>(char_sys<Lt::THERMAL>(B, G.rho0, Ul));
         if (B.viscous == VIS_OFF) V[0] = V[1] = V[2] = V[3] = 0.0;
         else if (B.viscous == VIS_FD) vis_fd<Lt::THERMAL>(G, B, X, D, u, Lt::CS2, V);
-        else vis_meso<Lt::THERMAL>(G, static_cast<const double*>(E.stripU),
-                                   static_cast<const double*>(E.stripN), D, Lt::CS2, V);
+        // the caller's deep strip: 5 moments then the 4 macros per node
+        else vis_meso<Lt::THERMAL>(G, static_cast<const double*>(E.stripN) + 5, 9,
+                                   static_cast<const double*>(E.stripN), 9, D, Lt::CS2, V);
         for (int m = 0; m < 4; ++m) B.V[4LL * u + m] = V[m];
         B.mask[u] = mask;
     } else {
@@ -963,33 +1012,32 @@ __global__ void __launch_bounds__(kBandThreads)
     for (int m = 0; m < 4; ++m) B.Ub[4LL * u + m] = Unew[m];
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the array's name as a device address).
+// Device address of the scratch array in the current context, looked up
+// once per context (host code cannot use the array's name as a device
+// address).
 int noalloc_scratch(double** out)
 {
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = cudaGetDevice(&dev);     // makes the device's primary context current if none is
     if (e != cudaSuccess) {
         fprintf(stderr, "lbm_cbc_side_step_noalloc: cudaGetDevice: %s\n", cudaGetErrorString(e));
         return LBM_ERR_CUDA;
     }
-    if (dev < 0 || dev >= kNoAllocMaxDevices) {
-        fprintf(stderr, "lbm_cbc_side_step_noalloc: device %d beyond the supported %d\n", dev,
-                kNoAllocMaxDevices);
-        return LBM_ERR_ARG;
-    }
+    void* ctx = current_context();
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) {
-            fprintf(stderr, "lbm_cbc_side_step_noalloc: cudaGetSymbolAddress: %s\n",
-                    cudaGetErrorString(e));
-            return LBM_ERR_CUDA;
+    for (int k = 0; k < g_noalloc_n; ++k)
+        if (ctx && g_noalloc_addr[k].ctx == ctx) {
+            *out = g_noalloc_addr[k].addr;
+            return LBM_OK;
         }
-        g_noalloc_addr[dev] = static_cast<double*>(p);
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "lbm_cbc_side_step_noalloc: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
     }
-    *out = g_noalloc_addr[dev];
+    if (ctx && g_noalloc_n < kNoAllocMaxDevices) g_noalloc_addr[g_noalloc_n++] = NoallocAddr{ctx, static_cast<double*>(p)};
+    *out = static_cast<double*>(p);
     return LBM_OK;
 }
 

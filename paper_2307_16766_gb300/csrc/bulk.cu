@@ -389,7 +389,7 @@ __global__ void k_init(Geom G, Export E, const double* __restrict__ rho,
     using R = typename StripReal<S>::T;
     const R U[4] = {R(m.s0), R(m.ux), R(m.uy), R(m.dT)};
     for (int s = 0; s < 4; ++s) {
-        if (!E.cbc[s] || dd[s] < 0 || dd[s] > 2) continue;
+        if (!E.cbc[s] || dd[s] < 0 || dd[s] >= E.ND) continue;
         const int p = s < 2 ? y : x;
         const long long slot = E.offS[s] + dd[s] * E.L[s] + p;
         R* u = static_cast<R*>(E.stripU) + slot * 4;

@@ -244,25 +244,29 @@ __device__ __forceinline__ void char_rhs(const CharSys<T>& C, const Relax<T>& P,
 // Viscous vectors, frozen at time t
 // ---------------------------------------------------------------------------
 
-// Mesoscopic form at x_f (Eqs. LaplaceU, LaplaceT): normal derivatives
-// one-sided into the bulk (Eq. FD-dx-bw), tangential ones central
-// (Eq. FD-dx-center) or one-sided inward next to a boundary node:
+// Mesoscopic form (Eqs. LaplaceU, LaplaceT) with the stencil starting M
+// nodes below x_f (the first node none of whose populations came from a
+// boundary layer): normal derivatives one-sided into the bulk
+// (Eq. FD-dx-bw), tangential ones central (Eq. FD-dx-center) or one-sided
+// inward next to a boundary node:
 //   V = (0, (1/rho) d_j s'_jn, (1/rho) d_j s'_jt,
 //        -div q / (rho c_s^2) + (nu / c_s^2) ((d_n u_n - d_t u_t)^2 + (d_n u_t + d_t u_n)^2)).
 template <bool TH, typename T>
-__device__ void vis_meso(const Geom& G, const T* SU, const T* SN, const UDesc& D, double cs2, T* V)
+__device__ void vis_meso(const Geom& G, const T* SU, int su, const T* SN, int sn_, const UDesc& D,
+                         double cs2, T* V)
 {
-    // SU, SN: macros [.][4] and non-equilibrium moments [.][5] of time t,
-    // indexed by D.vs[]; arithmetic T (FP64, or Dual numbers in the
-    // tangent-linear step)
+    // SU, SN: macros (drho, ux, uy, ...) and non-equilibrium moments
+    // (sigma'_xx, sigma'_xy, sigma'_yy, q_x, q_y) of time t, node k at
+    // SU + su * k and SN + sn_ * k, indexed by D.vs[]; arithmetic T (FP64,
+    // or Dual numbers in the tangent-linear step)
     const int s = D.kind;
     const int an = s < 2 ? 0 : 1, at = 1 - an;     // axes of n and t
     const T sn = T((s == 0 || s == 2) ? -1.0 : 1.0);
     T h[5][7];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        const T* n = SN + 5LL * D.vs[k];
-        const T* u = SU + 4LL * D.vs[k];
+        const T* n = SN + (long long)sn_ * D.vs[k];
+        const T* u = SU + (long long)su * D.vs[k];
         const T sxx = n[0], sxy = n[1], syy = n[2];
         h[k][0] = an == 0 ? sxx : syy;              // sigma'_nn
         h[k][1] = sn * sxy;                         // sigma'_nt
@@ -279,7 +283,7 @@ __device__ void vis_meso(const Geom& G, const T* SU, const T* SN, const UDesc& D
         if (D.tmode == 0) dt[m] = T(0.5) * (h[3][m] - h[4][m]);
         else dt[m] = T(double(D.tmode)) * T(0.5) * (T(3) * h[0][m] - T(4) * h[3][m] + h[4][m]);
     }
-    const T irho = T(1) / (T(G.rho0) + SU[4LL * D.vs[0]]);
+    const T irho = T(1) / (T(G.rho0) + SU[(long long)su * D.vs[0]]);
     V[0] = T(0);
     V[1] = (dn[0] + dt[1]) * irho;
     V[2] = (dn[1] + dt[2]) * irho;

@@ -454,16 +454,21 @@ struct Offsets {
     int st[37];
 };
 
-// Near-boundary strips exported by the bulk kernel for each characteristic
-// side: macros U = (drho, ux, uy, dT) and non-equilibrium moments
-// N = (sigma'_xx, sigma'_xy, sigma'_yy, q_x, q_y) of the bulk nodes at depths
-// d = 0, 1, 2 inside the boundary layers (x_f, x_f - n, x_f - 2n), for two
-// time levels.  Slot of (side s, depth d, position p) = offS[s] + d L[s] + p;
-// arrays are [parity][slot][4] and [parity][slot][5].
+// Near-boundary strips of each characteristic side, written by the band
+// kernel for the next step: macros U = (drho, ux, uy, dT) and
+// non-equilibrium moments N = (sigma'_xx, sigma'_xy, sigma'_yy, q_x, q_y)
+// of the bulk nodes at depths d = 0 .. ND - 1 inside the boundary layers
+// (x_f - d n), for two time levels.  Depths 0, 1, 2 serve the stencils of
+// the boundary solver; with the mesoscopic viscous vector ND = M + 3 and
+// depths M, M + 1, M + 2 serve its one-sided stencil, which starts at the
+// first node none of whose populations was streamed from a boundary layer
+// (N is kept there only).  Slot of (side s, depth d, position p) =
+// offS[s] + d L[s] + p; arrays are [parity][slot][4] and [parity][slot][5].
 struct Export {
     int cbc[4];
     int offS[4];
     int L[4];
+    int ND;          // strip depths per side: 3, or M + 3 with the mesoscopic viscous vector
     int nslots;
     int sesize;      // bytes per strip value: 8 with FP64 storage, else 4 (StripReal)
     void* stripU;
@@ -506,7 +511,8 @@ struct UDesc {
     int tmode;       // tangential stencil of the viscous terms: 0 central, 1 backward, -1 forward
     int wslot;       // strip slot of the NEEP source node (its macros at t + 1)
     int nb[6];       // +n, -n, -2n, -3n, +t, -t (corners: nb[0] = c - s, nb[1] = c - 2s)
-    int vs[5];       // strip slots for the viscous terms: d = 0, 1, 2 at p, then two tangential
+    int vs[5];       // strip slots of the mesoscopic viscous terms: depths M, M + 1, M + 2 at p,
+                     // then two tangential neighbours at depth M
     int wsrc;        // grid offset of the NEEP source node
     int wnode;       // grid offset of the node written (corner: block origin)
     int wdx, wdy;    // corner block: grid-offset steps along x and y
@@ -518,15 +524,21 @@ struct UDesc {
 // Unknowns per tile of the fused band kernel (its block size).
 constexpr int kTileUnknowns = 128;
 
-// A bulk node at depth 0..2 next to a characteristic side (a strip node)
-// that a band tile reads.  The bulk kernel updates it; the tile pulls it
-// again for its macros and non-equilibrium moments at t + 1 (and, for
-// Eq. NEEP sources, its post-collision populations).
+// A bulk node next to a characteristic side (a strip node) that a band tile
+// reads or writes.  The bulk kernel updates it; the tile pulls it again for
+// its macros (and non-equilibrium moments) at t + 1 and, for Eq. NEEP
+// sources, its post-collision populations.
+enum {
+    kSNLoadT = 1,    // the tile reads its strip values of time t (stencils at stage 0, viscous terms)
+    kSNPull = 2,     // the tile pulls it: macros of t + 1, Eq. NEEP copy, strips of t + 1
+    kSNNeq = 4,      // the strips of t + 1 the tile writes include its non-equilibrium moments
+};
 struct StripNode {
     int x, y;
     int tslot;   // a strip slot of the node: its macros and moments of time t
     int fx;      // index of its population copy in shared memory (Eq. NEEP source), or -1
     int gslot;   // strip slot this tile writes for t + 1 (own side, owned position), or -1
+    int flags;   // kSN* bits
 };
 
 struct Band {

@@ -119,7 +119,7 @@ __device__ __forceinline__ bool slot_node(const Geom& G, const Export& E, int q,
     int s = -1;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        if (E.cbc[k] && q >= E.offS[k] && q < E.offS[k] + 3 * E.L[k]) s = k;
+        if (E.cbc[k] && q >= E.offS[k] && q < E.offS[k] + E.ND * E.L[k]) s = k;
     if (s < 0) return false;
     const int r = q - E.offS[s], d = r / E.L[s], p = r % E.L[s];
     const int M = G.M;
@@ -243,7 +243,7 @@ __global__ void k_tl_stage(Geom G, Band B, Relax<TB<S>> P, const TB<S>* __restri
         T* Vu = Vv + 4LL * u;
         if (stage == 0) {
             if (B.viscous == VIS_FD) vis_fd<Lt::THERMAL>(G, B, X, D, u, Lt::CS2, V);
-            else vis_meso<Lt::THERMAL>(G, St, StN, D, Lt::CS2, V);
+            else vis_meso<Lt::THERMAL>(G, St, 4, StN, 5, D, Lt::CS2, V);
 #pragma unroll
             for (int m = 0; m < 4; ++m) Vu[m] = V[m];
         } else {
@@ -362,14 +362,15 @@ __global__ void __launch_bounds__(tl_bulk_threads<S>(), tl_bulk_min_blocks<S>())
     if (x < R.x1) {
         const long long node = (long long)y * G.nxp + x;
         const long long dstride = (long long)L::Q * G.plane;
-        // strip slots of this node (depth 0..2 inside a characteristic
-        // side; up to two sides near a corner): its macros at t + 1
-        int slot[2] = {-1, -1}, ns = 0;
+        // strip slots of this node (depth 0 .. ND - 1 inside a
+        // characteristic side; on a small grid a node can lie in the strips
+        // of all four sides): its macros at t + 1
+        int slot[4] = {-1, -1, -1, -1}, ns = 0;
         {
             const int dd[4] = {x - G.M, G.nx - 1 - G.M - x, y - G.M, G.ny - 1 - G.M - y};
 #pragma unroll
             for (int s = 0; s < 4; ++s)
-                if (E.cbc[s] && dd[s] >= 0 && dd[s] <= 2 && ns < 2)
+                if (E.cbc[s] && dd[s] >= 0 && dd[s] < E.ND)
                     slot[ns++] = E.offS[s] + dd[s] * E.L[s] + (s < 2 ? y : x);
         }
         double e = 0.0;

@@ -71,9 +71,16 @@ def test_defaults_and_workspace_size():
 
 
 @pytest.mark.parametrize("lattice,nx,ny,kw,ok", [
-    (lbm.LBM_D2Q37, 9, 9, dict(side=[1, 1, 1, 1]), True),          # minimal 2M+3
-    (lbm.LBM_D2Q37, 8, 9, dict(side=[1, 1, 1, 1]), False),         # too small
-    (lbm.LBM_D2Q9, 5, 5, dict(side=[1, 1, 1, 1]), True),
+    (lbm.LBM_D2Q37, 9, 9, dict(side=[1, 1, 1, 1], viscous=1), True),    # minimal 2M+3
+    (lbm.LBM_D2Q37, 8, 9, dict(side=[1, 1, 1, 1], viscous=1), False),   # too small
+    (lbm.LBM_D2Q37, 12, 12, dict(side=[1, 1, 1, 1]), True),        # mesoscopic stencil: 3M+3
+    (lbm.LBM_D2Q37, 11, 12, dict(side=[1, 1, 1, 1]), False),
+    (lbm.LBM_D2Q37, 12, 11, dict(side=[1, 1, 1, 1]), False),
+    (lbm.LBM_D2Q37, 11, 16, dict(side=[1, 1, 0, 0]), False),       # ... across a CBC side
+    (lbm.LBM_D2Q37, 11, 16, dict(side=[3, 3, 0, 0]), True),        # zero gradient: 2M+3
+    (lbm.LBM_D2Q9, 5, 5, dict(side=[1, 1, 1, 1], viscous=2), True),
+    (lbm.LBM_D2Q9, 6, 6, dict(side=[1, 1, 1, 1]), True),
+    (lbm.LBM_D2Q9, 5, 6, dict(side=[1, 1, 1, 1]), False),
     (lbm.LBM_D2Q9, 4, 5, dict(side=[3, 3, 3, 3]), False),
     (lbm.LBM_D2Q37, 16, 3, dict(side=[1, 1, 0, 0]), True),         # periodic axis of length M
     (lbm.LBM_D2Q37, 16, 2, dict(side=[1, 1, 0, 0]), False),
@@ -84,8 +91,9 @@ def test_defaults_and_workspace_size():
     (lbm.LBM_D2Q37, 16, 16, dict(storage=7), False),
     (lbm.LBM_D2Q37, 16, 16, dict(viscous=3), False),
     (lbm.LBM_D2Q37, 16, 16, dict(rho0=0.0), False),
-    (lbm.LBM_D2Q17, 9, 9, dict(side=[1, 1, 1, 1]), True),          # D2Q17: M = 3 as well
-    (lbm.LBM_D2Q17, 9, 8, dict(side=[1, 1, 1, 1]), False),
+    (lbm.LBM_D2Q17, 9, 9, dict(side=[1, 1, 1, 1], viscous=2), True),    # D2Q17: M = 3 as well
+    (lbm.LBM_D2Q17, 9, 8, dict(side=[1, 1, 1, 1], viscous=2), False),
+    (lbm.LBM_D2Q17, 12, 12, dict(side=[1, 1, 1, 1]), True),
     (lbm.LBM_D2Q37, 7616, 7616, dict(side=[1, 1, 1, 1]), True),    # 37 x 7616^2 < 2^31 values
     (lbm.LBM_D2Q37, 7680, 7616, dict(side=[1, 1, 1, 1]), False),   # 37 x 7616 x 7680 > 2^31
     (lbm.LBM_D2Q9, 15360, 15360, dict(), True),                    # 9 x 15360^2 < 2^31

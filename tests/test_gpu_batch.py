@@ -38,7 +38,8 @@ def _mixed_runs():
     cfg = W.run("D2Q17", 41, 31, 0.75, sides=("cbc",) * 4, schemes=("cbc",) * 4, dirichlet="neep",
                 alpha_T=0.3, beta_P=0.2, p_inf=[cs2_17 * 1.0002] * 4)
     runs.append((dict(cfg, storage="f32"), W.gaussian_pulse(41, 31, 1e-3, 1e-3, 3.5, center=(19.4, 14.1))))
-    cfg = W.run("D2Q37", 9, 9, 0.9, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4, alpha_T=0.5)
+    cfg = W.run("D2Q37", 9, 9, 0.9, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4, alpha_T=0.5,
+                viscous="fd")
     runs.append((dict(cfg, storage="f32"), W.gaussian_pulse(9, 9, 1e-3, 1e-3, 2.0)))
     cfg = W.run("D2Q37", 80, 60, 0.65, sides=("zg", "cbc", "periodic", "periodic"), schemes=("cbc_relax",) * 4,
                 dirichlet="reg", viscous="off", alpha_T=1.0)
@@ -98,7 +99,9 @@ def test_batch_of_many_uneven_runs():
     cfgs, fields = [], []
     for r in range(40):
         nx, ny = int(rng.integers(9, 120)), int(rng.integers(9, 120))
+        # the mesoscopic viscous stencil needs 3 M + 3 = 12 nodes across
         cfg = W.run("D2Q37", nx, ny, float(rng.uniform(0.55, 1.0)), sides=("cbc",) * 4,
+                    viscous="meso" if min(nx, ny) >= 12 else "fd",
                     schemes=("cbc_relax",) * 4, alpha_T=float(rng.uniform(0, 1)),
                     beta_P=float(rng.uniform(0, 1)))
         cfgs.append(dict(cfg, storage="f32"))

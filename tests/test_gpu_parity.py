@@ -155,10 +155,14 @@ def test_d2q37_vortex_through_outlet_small():
     assert_parity(cfg, f, 400)
 
 
-def test_d2q37_minimal_grid():
-    """Smallest admissible grid (2M + 3 = 9 nodes per open axis)."""
-    cfg = W.run("D2Q37", 9, 9, 0.9, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4, alpha_T=0.5)
-    f = W.gaussian_pulse(9, 9, 1e-3, 1e-3, 2.0)
+@pytest.mark.parametrize("n,vis", [(9, "fd"), (12, "meso")])
+def test_d2q37_minimal_grid(n, vis):
+    """Smallest admissible grids: 2M + 3 = 9 nodes per open axis, 3M + 3 =
+    12 with the mesoscopic viscous stencil (it reaches M + 2 nodes below
+    x_f)."""
+    cfg = W.run("D2Q37", n, n, 0.9, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4, alpha_T=0.5,
+                viscous=vis)
+    f = W.gaussian_pulse(n, n, 1e-3, 1e-3, 2.0)
     assert_parity(cfg, f, 50)
 
 
@@ -526,7 +530,7 @@ def test_overlapped_step_is_bit_identical_to_phased_step(case):
         f = W.gaussian_pulse(50, 30, 1e-3, 1e-3, 4.0)
     elif case == "d2q37_interior_empty":
         cfg = W.run("D2Q37", 11, 12, 0.9, sides=("cbc",) * 4, schemes=("cbc_relax",) * 4,
-                    alpha_T=0.5, storage="f64")
+                    alpha_T=0.5, storage="f64", viscous="fd")
         f = W.gaussian_pulse(11, 12, 1e-3, 1e-3, 2.0)
     elif case == "d2q17_four_cbc_neep_f32":
         cfg = W.run("D2Q17", 48, 40, 0.8, sides=("cbc",) * 4, schemes=("cbc",) * 4,
