@@ -55,6 +55,7 @@ def lib():
         L.orc_moments.argtypes = [C.c_int, C.c_double, dp, dp]
         L.orc_char_matrices.argtypes = [C.c_int, C.c_double, dp, dp, dp, dp]
         L.orc_char_rhs.argtypes = [C.POINTER(Params), dp, dp, dp, dp, C.c_int, C.c_double, C.c_int, dp]
+        L.orc_corner_rhs.argtypes = [C.POINTER(Params), C.c_int, dp, dp, dp, dp]
         L.orc_rk4_scalar.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
         L.orc_rk4_scalar.restype = C.c_double
         L.orc_create.argtypes = [C.POINTER(Params)]
@@ -167,6 +168,17 @@ def char_rhs(cfg, Ul, dUn, TT, VV, mask, dP, scheme):
     args = [_f64(a) for a in (Ul, dUn, TT, VV)]
     lib().orc_char_rhs(C.byref(p), *[_dp(a) for a in args], int(mask), float(dP),
                        SCHEMES[scheme], _dp(k))
+    return k
+
+
+def corner_rhs(cfg, cid, Uc, U1, U2):
+    """Lab-frame right-hand side of corner cid from the corner node's state
+    and those one and two diagonal steps inward (deviation form)."""
+    p = make_params(cfg)
+    k = np.zeros(4)
+    args = [_f64(a) for a in (Uc, U1, U2)]
+    if lib().orc_corner_rhs(C.byref(p), int(cid), *[_dp(a) for a in args], _dp(k)):
+        raise ValueError("bad corner")
     return k
 
 

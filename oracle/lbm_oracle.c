@@ -837,25 +837,47 @@ static void fill_stage_field(orc_sim* s, double frac, const double* Y)
     }
 }
 
+/* Corner cid (Sec. 3.3, Fig. Layer-Multispeed-BC): LODI (Eq. PNR) along the
+ * outward diagonal n at the innermost corner node, the normal derivative by
+ * the one-sided difference of Eq. FD-dx-bw through the node (lab state Uc)
+ * and the two diagonal nodes inward (U1 = one diagonal step in, U2 = two),
+ * whose spacing is sqrt(2).  k: lab-frame right-hand side. */
+static void corner_rhs(const lattice_t* L, const orc_params* P, int cid, const double* Uc,
+                       const double* U1lab, const double* U2lab, int mask, double k[4])
+{
+    double n[2], t[2];
+    corner_frame(cid, n, t);
+    double U[4], U1[4], U2[4], dUn[4], kl[4], zero[4] = {0, 0, 0, 0};
+    to_local(Uc, n, t, U);
+    to_local(U1lab, n, t, U1);
+    to_local(U2lab, n, t, U2);
+    for (int m = 0; m < 4; m++) dUn[m] = (3.0 * U[m] - 4.0 * U1[m] + U2[m]) / (2.0 * sqrt(2.0));
+    char_rhs(L, P, U, dUn, zero, zero, mask, 0.0, ORC_LODI, kl);
+    to_lab(kl, n, t, k);
+}
+
+int orc_corner_rhs(const orc_params* p, int cid, const double Uc[4], const double U1[4],
+                   const double U2[4], double k[4])
+{
+    lattice_t L;
+    if (make_lattice(p->lattice, &L) || cid < 0 || cid > 3) return -1;
+    double n[2], t[2], Ul[4];
+    corner_frame(cid, n, t);
+    to_local(Uc, n, t, Ul);
+    corner_rhs(&L, p, cid, Uc, U1, U2, incoming_mask(&L, p->rho0, Ul), k);
+    return 0;
+}
+
 /* Right-hand side at one characteristic unknown from the stage field W. */
 static void unknown_rhs(const orc_sim* s, int u, double k[4])
 {
     const double* W = s->W;
     int sd = s->u_side[u];
     if (sd >= 4) {
-        /* Corner: LODI along the outward diagonal, one-sided difference with
-         * spacing sqrt(2) through the innermost corner node. */
-        int cid = sd - 4;
-        double n[2], t[2];
-        corner_frame(cid, n, t);
-        int node = s->u_node[u], x = node % s->nx, y = node / s->nx;
-        double U[4], U1[4], U2[4], dUn[4], kl[4], zero[4] = {0, 0, 0, 0};
-        to_local(W + 4 * node, n, t, U);
-        to_local(W + 4 * node_at(s, x - CD[cid][0], y - CD[cid][1]), n, t, U1);
-        to_local(W + 4 * node_at(s, x - 2 * CD[cid][0], y - 2 * CD[cid][1]), n, t, U2);
-        for (int m = 0; m < 4; m++) dUn[m] = (3.0 * U[m] - 4.0 * U1[m] + U2[m]) / (2.0 * sqrt(2.0));
-        char_rhs(&s->L, &s->P, U, dUn, zero, zero, s->mask[u], 0.0, ORC_LODI, kl);
-        to_lab(kl, n, t, k);
+        int cid = sd - 4, node = s->u_node[u], x = node % s->nx, y = node / s->nx;
+        corner_rhs(&s->L, &s->P, cid, W + 4 * node,
+                   W + 4 * node_at(s, x - CD[cid][0], y - CD[cid][1]),
+                   W + 4 * node_at(s, x - 2 * CD[cid][0], y - 2 * CD[cid][1]), s->mask[u], k);
         return;
     }
     double n[2], t[2];

@@ -84,6 +84,13 @@ void   orc_char_rhs(const orc_params* p, const double Ul[4], const double dUn[4]
                     const double TT[4], const double VV[4], int incoming_mask,
                     double dP, int scheme, double k[4]);
 
+/* Right-hand side of the corner unknown cid (0 SW, 1 SE, 2 NW, 3 NE) from
+ * the lab-frame states (drho, ux, uy, dT) of the innermost corner node and
+ * of the nodes one and two diagonal steps inward (Sec. 3.3: LODI along the
+ * outward diagonal, one-sided difference of spacing sqrt(2)); lab frame. */
+int    orc_corner_rhs(const orc_params* p, int cid, const double Uc[4], const double U1[4],
+                      const double U2[4], double k[4]);
+
 /* Generic classical RK4 step of size 1 over n unknowns; used by the boundary
  * solver and exported so a test can drive it with a scalar ODE y' = lam y. */
 double orc_rk4_scalar(double lam, double y0, double h, int nsteps);

@@ -157,3 +157,54 @@ def test_rk4_is_classical_fourth_order():
     e1 = abs(oracle.rk4_scalar(-2.0, 1.0, 0.1, 10) - math.exp(-2.0))
     e2 = abs(oracle.rk4_scalar(-2.0, 1.0, 0.05, 20) - math.exp(-2.0))
     assert 14.0 < e1 / e2 < 18.0
+
+
+def _corner_frame(cid):
+    """Outward diagonal n of corner cid (0 SW, 1 SE, 2 NW, 3 NE) and t = n
+    turned by +90 degrees."""
+    sx = 1.0 if cid & 1 else -1.0
+    sy = 1.0 if cid & 2 else -1.0
+    n = np.array([sx, sy]) / math.sqrt(2.0)
+    return n, np.array([-n[1], n[0]]), np.array([sx, sy])
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q37", "D2Q17"])
+@pytest.mark.parametrize("cid", [0, 1, 2, 3])
+def test_corner_lodi_along_the_diagonal(lat, cid):
+    """Sec. 3.3 / Fig. Layer-Multispeed-BC: the corner node takes LODI
+    (Eq. PNR) along the outward diagonal, with the normal derivative by the
+    one-sided Eq. FD-dx-bw through the node and the two diagonal nodes inward
+    (spacing sqrt(2)).  On a field linear in space (exact for that
+    difference) the right-hand side must be dU/dt = -A_out dU/dn, A_out the
+    outgoing part of the Euler flux matrix along n (numpy eigenvectors): a
+    spacing of 1, a sign flip or the inward diagonal all fail."""
+    rng = np.random.default_rng(40 + cid)
+    cs2 = CS2[lat]
+    n, t, s = _corner_frame(cid)
+    cfg = cfg_for(lat)
+    for _ in range(6):
+        # lab state at the corner node and a small lab-frame gradient G (4 x 2)
+        U = np.array([rng.uniform(-0.05, 0.05), rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2),
+                      rng.uniform(-0.05, 0.05) if lat != "D2Q9" else 0.0])
+        G = 1e-3 * rng.standard_normal((4, 2))
+        if lat == "D2Q9":
+            G[3] = 0.0
+        U1, U2 = U - G @ s, U - 2.0 * G @ s
+        k = oracle.corner_rhs(cfg, cid, U, U1, U2)
+        # expected, from the local frame (rho, u_n, u_t, T)
+        Ul = np.array([U[0], U[1:3] @ n, U[1:3] @ t, U[3]])
+        dlab = G @ n                                   # d/dn of the lab components
+        dUn = np.array([dlab[0], dlab[1:3] @ n, dlab[1:3] @ t, dlab[3]])
+        A = euler_A(lat, Ul)
+        m = A.shape[0]
+        w, R = np.linalg.eig(A)
+        w, R = w.real, R.real
+        Lm = np.linalg.inv(R)
+        Aout = R @ np.diag(np.where(w >= 0.0, w, 0.0)) @ Lm
+        kl = np.zeros(4)
+        kl[:m] = -Aout @ dUn[:m]
+        want = np.array([kl[0], kl[1] * n[0] + kl[2] * t[0], kl[1] * n[1] + kl[2] * t[1], kl[3]])
+        scale = np.abs(want).max()
+        assert np.abs(k - want).max() <= 1e-12 * scale + 1e-18, (k, want)
+        # the same corner with unit spacing would be sqrt(2) off
+        assert np.abs(k * math.sqrt(2.0) - want).max() > 1e-3 * scale

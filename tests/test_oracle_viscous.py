@@ -117,3 +117,33 @@ def test_fd_fails_at_nu_03_where_mesoscopic_holds():
     assert not np.all(np.isfinite(edge_f)) or edge_f[-1] > 1.0, edge_f
     edge_m, _ = _run(_vortex_cfg(0.3, "meso"), 1000)
     assert np.all(np.isfinite(edge_m)) and edge_m.max() < 2e-3, edge_m
+
+
+def test_viscous_heating_of_a_shear_wave():
+    """The viscous-heating part of the fourth component of the viscous
+    vector (Sec. 3.1: (nu / c_s^2) ((d_x u_x - d_y u_y)^2 + (d_y u_x +
+    d_x u_y)^2), with the velocity derivatives by the stencil's differences)
+    on a plane shear wave u_y = A sin(k x): averaged over a wavelength, where
+    the heat-flux divergence of the other part of V_4 sums to zero,
+    V_4 = (nu / c_s^2) (A k)^2 / 2; its cos(2 k x) component carries the same
+    amplitude less what conduction has smoothed; both quadratic in A."""
+    lat, n, tau = "D2Q37", 48, 0.8
+    cs2 = W.CS2[lat]
+    nu = (tau - 0.5) * cs2
+    k = 2.0 * math.pi / n
+    x = np.arange(n)
+
+    def V4_modes(A):
+        cfg = W.run(lat, n, n, tau)
+        s = oracle.Sim(cfg).init(*W.shear_wave(n, n, A, k_axis="x"))
+        s.step(10)
+        amp = np.abs(s.macros()[2][5]).max()
+        V4 = np.array([s.vis_meso_at(1, xx, 5)[3] for xx in x])
+        return V4.mean(), 2.0 * np.mean(V4 * np.cos(2.0 * k * x)), amp
+
+    mean, c2, amp = V4_modes(0.02)
+    heat = nu / cs2 * (amp * k) ** 2 / 2.0
+    assert abs(mean - heat) < 0.03 * heat, (mean, heat)
+    assert 0.8 * heat < c2 < 1.0 * heat, (c2, heat)
+    mean2, _, amp2 = V4_modes(0.04)
+    assert abs(mean2 / mean - (amp2 / amp) ** 2) < 0.03 * (amp2 / amp) ** 2
