@@ -167,6 +167,40 @@ def bulk_traffic(storage, launch_nodes):
     return None
 
 
+def bulk_fp64_flops():
+    """FP64 flops per node update of k_bulk<D2Q37, double> (2 per FMA, 1 per
+    add or multiply) from the committed ncu counter capture, if it was taken
+    on the current sources of the kernel (bulk.cu and collide.cuh)."""
+    h = hashlib.sha256()
+    for f in ("bulk.cu", "collide.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2307_16766_gb300", "csrc", f), "rb").read())
+    sha = h.hexdigest()[:12]
+    path = os.path.join(ROOT, "profiles", "k_bulk_d2q37_f64_flops.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        m = re.match(r"flops\s+nodes=(\d+)\s+dfma=(\d+)\s+dadd=(\d+)\s+dmul=(\d+)\s+src=(\w+)", line.strip())
+        if m and m.group(5) == sha:
+            n, fma, add, mul = (int(m.group(k)) for k in range(1, 5))
+            return (2 * fma + add + mul) / n
+    return None
+
+
+def fp64_roofline(interior_nodes, interior_ms):
+    """The FP64 bulk kernel against the FP64 FMA throughput measured now on
+    this GPU (lbm_fp64_fma_rate), with the flop count per update above."""
+    import paper_2307_16766_gb300 as lbm
+    peak = lbm.fp64_fma_rate() / 1e12
+    fpu = bulk_fp64_flops()
+    d = {"bound": "alu", "peak": peak, "unit": "TFLOP/s", "kernel": "k_bulk<D2Q37, double>",
+         "peak_kind": "measured FP64 FMA throughput (lbm_fp64_fma_rate, this run)", "flops_per_update": fpu,
+         "achieved": None, "frac": None}
+    if fpu is not None:
+        d["achieved"] = fpu * interior_nodes / (interior_ms / 1e3) / 1e12
+        d["frac"] = d["achieved"] / peak
+    return d
+
+
 def _open_axes(cfg):
     per_x = cfg["sides"][0] == "periodic"
     per_y = cfg["sides"][2] == "periodic"
@@ -428,23 +462,29 @@ def run_batch(args, local_rank):
             "sequential_value": nodes * KS / seq_s / 1e6, "sequential_steps": KS,
             "finite": finite,
             "workload": "96-run CBC coefficient sweep: D2Q9/D2Q37 by seeded coin, nx, ny ~ U{128..512}, "
-                        "tau ~ U[0.55, 1], alpha_T, beta_P ~ U[0, 1], CBC-RELAX on four sides, viscous vector off, "
+                        "tau ~ U[0.55, 1], alpha_T, beta_P ~ U[0, 1], CBC-RELAX on four sides, mesoscopic viscous vector, "
                         "Gaussian pulses, FP32 storage"}
 
 
 def run_gradient(args, local_rank):
     """Gradient of the pressure loss against a larger periodic reference
-    with respect to (alpha_T, beta_P, P_inf) on the D2Q37 512x256 FP32
-    pulse: --gradient-steps tangent-linear steps timed with CUDA events,
-    beside the same number of ordinary steps of the same grid (both
-    L2-resident at this size, so neither is flushed)."""
+    with respect to the relaxation parameters on the D2Q37 512x256 FP32
+    pulse with the mesoscopic viscous vector (alpha_V in play):
+    --gradient-steps steps of the reverse-mode sweep (the checkpointed
+    forward pass, then the backward pass that recomputes each 100-step
+    segment and runs the adjoint kernels), timed with CUDA events on the
+    solver's stream, beside the same number of ordinary steps of the same
+    grid (L2-resident at this size, so neither is flushed).  The
+    tangent-linear steps (three directions) are timed beside them."""
     import torch
     import paper_2307_16766_gb300 as lbm
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     K = args.gradient_steps
+    ck = 100
     cfg, f, rcfg, rf, (x0, y0) = W.gradient_pulse(steps=K)
+    cfg = dict(cfg, viscous="meso", alpha_V=0.3)
     nx, ny = cfg["nx"], cfg["ny"]
     cs2 = W.CS2["D2Q37"]
     # reference pressure of the interior crop, every step
@@ -457,36 +497,54 @@ def run_gradient(args, local_rank):
         dT = T[y0:y0 + ny, x0:x0 + nx] - 1.0
         dP[k] = cs2 * (dr + dT + dr * dT)
     ref.close()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     # ordinary steps
     sim = lbm.Simulation(cfg, device=dev).init_fields(*f)
     sim.step(5)
     torch.cuda.synchronize(dev)
-    e0.record(sim.stream)
+    ev[0].record(sim.stream)
     sim.step(K)
-    e1.record(sim.stream)
+    ev[1].record(sim.stream)
     torch.cuda.synchronize(dev)
-    fwd_s = e0.elapsed_time(e1) / 1e3
-    # tangent-linear steps from the initial state
+    fwd_s = ev[0].elapsed_time(ev[1]) / 1e3
+    # reverse mode from the initial state: forward with checkpoints, backward
+    sim.init_fields(*f)
+    lbm.lbm_adj_begin(sim.handle, ck, K)
+    torch.cuda.synchronize(dev)
+    ev[0].record(sim.stream)
+    J = lbm.lbm_adj_forward(sim.handle, K, dP.data_ptr(), ny * nx)
+    ev[1].record(sim.stream)
+    dJ = lbm.lbm_adj_backward(sim.handle)
+    ev[2].record(sim.stream)
+    torch.cuda.synchronize(dev)
+    adj_f = ev[0].elapsed_time(ev[1]) / 1e3
+    adj_b = ev[1].elapsed_time(ev[2]) / 1e3
+    lbm.lbm_adj_end(sim.handle)
+    # forward mode (tangent-linear), three directions, beside it
     sim.init_fields(*f)
     lbm.lbm_grad_begin(sim.handle)
     torch.cuda.synchronize(dev)
-    e0.record(sim.stream)
+    ev[0].record(sim.stream)
     lbm.lbm_grad_step(sim.handle, K, dP.data_ptr(), ny * nx)
-    e1.record(sim.stream)
+    ev[1].record(sim.stream)
     torch.cuda.synchronize(dev)
-    grad_s = e0.elapsed_time(e1) / 1e3
-    J, dJ = lbm.lbm_grad_result(sim.handle)
+    tl_s = ev[0].elapsed_time(ev[1]) / 1e3
+    Jt, dJt = lbm.lbm_grad_result(sim.handle)
     lbm.lbm_grad_end(sim.handle)
     sim.close()
-    return {"value": grad_s / fwd_s, "unit": "gradient step time / forward step time",
-            "steps": K, "gradient_ms_per_step": grad_s / K * 1e3, "forward_ms_per_step": fwd_s / K * 1e3,
-            "J": J, "dJ": {"alpha_T": dJ[0], "beta_P": dJ[1], "P_inf": dJ[2]},
-            "mode": "forward (tangent-linear, 3 directions), no checkpoints",
-            "gpu_launches_per_step": 8,
-            "workload": "D2Q37 %dx%d FP32 rho+T Gaussian pulse, CBC-RELAX on four sides, viscous off, "
-                        "alpha_T = beta_P = 0.5, P_inf = c_s^2 rho0; loss against the centre crop of a "
-                        "%dx%d periodic run, every step" % (nx, ny, rcfg["nx"], rcfg["ny"])}
+    names = ("alpha_T", "beta_P", "P_inf", "alpha_V", "t_inf")
+    return {"value": (adj_f + adj_b) / fwd_s, "unit": "gradient time / forward time (reverse mode, all parameters)",
+            "steps": K, "checkpoint_every": ck,
+            "forward_ms_per_step": fwd_s / K * 1e3,
+            "adjoint_forward_ms_per_step": adj_f / K * 1e3, "adjoint_backward_ms_per_step": adj_b / K * 1e3,
+            "J": J, "dJ": dict(zip(names, dJ)),
+            "tangent": {"ratio": tl_s / fwd_s, "J": Jt, "dJ": {"alpha_T": dJt[0], "beta_P": dJt[1], "P_inf": dJt[2]},
+                        "directions": 3},
+            "mode": "reverse (adjoint) sweep, checkpoint every %d steps, recompute per segment" % ck,
+            "workload": "D2Q37 %dx%d FP32 rho+T Gaussian pulse, CBC-RELAX on four sides, mesoscopic viscous "
+                        "vector, alpha_T = beta_P = 0.5, alpha_V = 0.3, P_inf = c_s^2 rho0; loss against the "
+                        "centre crop of a %dx%d periodic run, every step; gradient w.r.t. sigma (beta_P), beta "
+                        "(alpha_T), alpha_V, P_inf (and t_inf)" % (nx, ny, rcfg["nx"], rcfg["ny"])}
 
 
 def max_over_ranks(seconds, world):
@@ -655,7 +713,8 @@ def main():
                             "unit": "MLUPS", "interior_ms": fp64["interior_ms_mean"],
                             "phased_bulk_ms": fp64["bulk_ms_mean"],
                             "phased_boundary_ms": fp64["boundary_ms_mean"],
-                            "interior_GBps": 2 * Q * 8 * fp64["interior_nodes"] / (fp64["interior_ms_mean"] / 1e3) / 1e9}
+                            "interior_GBps": 2 * Q * 8 * fp64["interior_nodes"] / (fp64["interior_ms_mean"] / 1e3) / 1e9,
+                            "roofline": fp64_roofline(fp64["interior_nodes"], fp64["interior_ms_mean"])}
         if fp16 is not None:
             line["fp16"] = {"value": nodes / (fp16["step_ms_total"] / 1e3 / min(K, 50)) / 1e6,
                             "unit": "MLUPS", "interior_ms": fp16["interior_ms_mean"],

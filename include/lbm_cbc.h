@@ -134,7 +134,8 @@ int lbm_set_stream(lbm_handle* h, void* stream);
 /* Initialise f = f^eq(rho, u, T) on every node (Sec. 2) and the boundary
  * state from the same fields.  Arrays are [ny][nx] doubles, on the device
  * when on_device != 0, else in host memory (copied in on the handle's stream).
- * For D2Q9, T is ignored (isothermal).  Resets the step counter. */
+ * For D2Q9, T is ignored (isothermal).  Resets the step counter and clears
+ * the status of earlier steps (a wait that gave up, non-finite values). */
 int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
                     const double* uy, const double* T, int on_device);
 
@@ -167,6 +168,19 @@ int lbm_step_phase(lbm_handle* h, int phase);
  * per call only the last step's records remain.  A NULL entry among the
  * first n is LBM_ERR_ARG. */
 int lbm_set_kernel_events(lbm_handle* h, void* const* events, int n);
+
+/* Limit of the bulk kernel's wait for each tensor copy (TMA) of its
+ * populations, in seconds (default 1; 0 to 60; 0 tests once without
+ * waiting, so that nearly every copy counts as late).  When a wait runs out the
+ * kernel records it, waits again -- at most 1 s, whatever this limit -- for
+ * the copies still in flight, so that none lands in the shared memory of a
+ * CTA that has left, and leaves that row segment unwritten; the next
+ * lbm_get_macros returns LBM_ERR_TIMEOUT.  The band kernel's cluster
+ * exchanges keep their fixed 1 s limit: a CTA that gave up on one could still
+ * receive other CTAs' stores after leaving.  A batch (lbm_batch_create)
+ * takes the limit its runs have when it is created.  Synchronises the
+ * stream. */
+int lbm_set_wait_limit(lbm_handle* h, double seconds);
 
 /* Macroscopic fields of the current populations (Eq. macro): absolute rho,
  * ux, uy and T ([ny][nx] doubles; T = 1 for D2Q9).  Device or host arrays as
@@ -241,6 +255,52 @@ int lbm_grad_result(lbm_handle* h, double* J, double* dJ);
 
 /* Free the derivative state.  NULL-safe on a handle without one. */
 int lbm_grad_end(lbm_handle* h);
+
+/* Reverse-mode (adjoint) gradients with segment checkpointing.  The same
+ * pressure loss J as above, and its gradient with respect to all five
+ * parameters theta = (alpha_T, beta_P, P_inf, alpha_V, t_inf) (P_inf moved
+ * on every characteristic side together) in one backward pass.
+ *
+ * lbm_adj_forward advances the handle n ordinary steps (Fig.
+ * flowchart-lbm-algo) and accumulates J, keeping a checkpoint of the state
+ * every checkpoint_every steps.  lbm_adj_backward then sweeps the steps
+ * backwards, segment by segment from the last: it restores the segment's
+ * checkpoint, recomputes its steps keeping their macros, boundary states and
+ * strips, and runs the adjoint of each step -- the Dirichlet write, the RK4
+ * of the characteristic boundary state (Sec. 3.3; its right-hand side
+ * differentiated in forward mode per boundary unknown), the viscous vector,
+ * the strips, and the pull-stream + BGK collision of every bulk node
+ * (Eqs. lbe, bgk) -- and leaves the handle in the state after the n steps.
+ * Memory: one state per checkpoint plus the macros of checkpoint_every
+ * steps, so long runs fit in device memory.  The gradient is exact up to
+ * rounding; the boundary solver's arithmetic and the adjoint populations
+ * are in the storage's precision (FP32 with FP32 storage), the parameter
+ * gradient is accumulated in FP64.
+ *
+ * Supported: FP64 or FP32 storage, every viscous form, the equilibrium
+ * Dirichlet condition, characteristic and periodic sides (otherwise
+ * LBM_ERR_ARG).  Ordinary steps stay available: the forward pass is made of
+ * them. */
+
+/* Allocate the checkpoints and the adjoint state (cudaMalloc) for up to
+ * max_steps forward steps with a checkpoint every checkpoint_every steps. */
+int lbm_adj_begin(lbm_handle* h, int checkpoint_every, int max_steps);
+
+/* n ordinary steps (n <= max_steps) with checkpoints; *J = the loss over
+ * them (synchronises).  dP_ref: NULL (reference 0) or a device array holding,
+ * for step i, the [ny][nx] doubles of P_ref - c_s^2 rho0 at dP_ref + i *
+ * ref_stride; it is read again by lbm_adj_backward and must stay valid
+ * until that returns. */
+int lbm_adj_forward(lbm_handle* h, int n, const double* dP_ref, long long ref_stride, double* J);
+
+/* dJ[0..4] = dJ/d(alpha_T, beta_P, P_inf, alpha_V, t_inf) of the last
+ * lbm_adj_forward (synchronises); the handle ends in the state after the
+ * forward steps. */
+int lbm_adj_backward(lbm_handle* h, double* dJ);
+
+/* Free the checkpoints and the adjoint state.  NULL-safe on a handle
+ * without them. */
+int lbm_adj_end(lbm_handle* h);
 
 /* ---------------------------------------------------------------------- */
 /* Batches: many independent runs stepped together                        */
@@ -330,6 +390,14 @@ void lbm_batch_destroy(lbm_batch* b);
 int lbm_cbc_side_step_noalloc(int lattice, int side, int length, double tau,
                               const lbm_cbc_params* p, double* Ub, const double* strip_t,
                               const double* strip_t1, const double* neq_t, void* stream);
+
+/* Measured FP64 FMA throughput of the current device, in flop/s (an FMA
+ * counts two): one timed launch of 8 CTAs of 256 threads per SM, each
+ * thread running 8 independent register chains of `iters` FMAs (1 to 2^24),
+ * after a short warm-up launch, on `stream` (a cudaStream_t; NULL = legacy
+ * default).  The roof of the FP64 storage's ALU-bound bulk update.
+ * Synchronises the stream; LBM_ERR_CUDA if a launch fails. */
+int lbm_fp64_fma_rate(int iters, void* stream, double* flops_per_s);
 
 #ifdef __cplusplus
 }

@@ -84,6 +84,8 @@ def lib():
             "lbm_step": (C.c_int, [vp, C.c_int]),
             "lbm_step_phase": (C.c_int, [vp, C.c_int]),
             "lbm_set_kernel_events": (C.c_int, [vp, C.POINTER(C.c_void_p), C.c_int]),
+            "lbm_set_wait_limit": (C.c_int, [vp, C.c_double]),
+            "lbm_fp64_fma_rate": (C.c_int, [C.c_int, vp, C.POINTER(C.c_double)]),
             "lbm_get_macros": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
             "lbm_state_bytes": (C.c_int, [vp, C.POINTER(sz)]),
             "lbm_get_state": (C.c_int, [vp, vp, sz]),
@@ -98,6 +100,10 @@ def lib():
             "lbm_grad_step": (C.c_int, [vp, C.c_int, vp, C.c_longlong]),
             "lbm_grad_result": (C.c_int, [vp, dp, dp]),
             "lbm_grad_end": (C.c_int, [vp]),
+            "lbm_adj_begin": (C.c_int, [vp, C.c_int, C.c_int]),
+            "lbm_adj_forward": (C.c_int, [vp, C.c_int, vp, C.c_longlong, dp]),
+            "lbm_adj_backward": (C.c_int, [vp, dp]),
+            "lbm_adj_end": (C.c_int, [vp]),
             "lbm_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                            C.POINTER(C.c_int), dp, pp, C.POINTER(vp)]),
             "lbm_batch_run": (C.c_int, [vp, C.c_int, C.POINTER(vp)]),
@@ -221,6 +227,21 @@ def lbm_set_kernel_events(h, events):
     _check(lib().lbm_set_kernel_events(h, arr, len(events)), h)
 
 
+def fp64_fma_rate(iters=16384, stream=None):
+    """Measured FP64 FMA throughput of the current device in flop/s."""
+    import torch
+    st = torch.cuda.current_stream() if stream is None else stream
+    out = C.c_double(0.0)
+    rc = lib().lbm_fp64_fma_rate(int(iters), C.c_void_p(st.cuda_stream), C.byref(out))
+    if rc != 0:
+        raise LbmError(rc, "FP64 FMA throughput launch failed")
+    return out.value
+
+
+def lbm_set_wait_limit(h, seconds):
+    _check(lib().lbm_set_wait_limit(h, float(seconds)), h)
+
+
 def lbm_get_macros(h, rho, ux, uy, T, on_device):
     """Fill four preallocated outputs (pointers as ints)."""
     _check(lib().lbm_get_macros(h, C.c_void_p(rho), C.c_void_p(ux), C.c_void_p(uy),
@@ -294,6 +315,28 @@ def lbm_grad_result(h):
 
 def lbm_grad_end(h):
     _check(lib().lbm_grad_end(h), h)
+
+
+def lbm_adj_begin(h, checkpoint_every, max_steps):
+    _check(lib().lbm_adj_begin(h, int(checkpoint_every), int(max_steps)), h)
+
+
+def lbm_adj_forward(h, n, dP_ref_ptr=None, ref_stride=0):
+    """n steps with checkpoints; returns the loss J."""
+    J = C.c_double()
+    _check(lib().lbm_adj_forward(h, int(n), dP_ref_ptr, ref_stride, C.byref(J)), h)
+    return J.value
+
+
+def lbm_adj_backward(h):
+    """dJ/d(alpha_T, beta_P, P_inf, alpha_V, t_inf) of the last forward."""
+    dJ = (C.c_double * 5)()
+    _check(lib().lbm_adj_backward(h, dJ), h)
+    return list(dJ)
+
+
+def lbm_adj_end(h):
+    _check(lib().lbm_adj_end(h), h)
 
 
 def _check_batch(rc, b):
@@ -560,7 +603,80 @@ def _make_cbc_loss():
     return CBCLoss
 
 
+def _ref_arg(sim, dP_ref, steps):
+    import torch
+    if dP_ref is None:
+        return None, 0, None
+    ref = dP_ref.contiguous()
+    if ref.dtype != torch.float64 or tuple(ref.shape) != (steps, sim.ny, sim.nx):
+        raise ValueError("dP_ref must be float64 [steps, ny, nx]")
+    return ref.data_ptr(), sim.ny * sim.nx, ref
+
+
+def pressure_loss_gradient_adjoint(cfg, fields, steps, dP_ref=None, checkpoint_every=100, device=None):
+    """(J, dJ/dTHETA) -- all five relaxation parameters -- by the
+    reverse-mode sweep with a checkpoint every `checkpoint_every` steps
+    (lbm_adj_*) on a fresh solver.  dP_ref: None or a CUDA float64 tensor
+    [steps, ny, nx]."""
+    sim = Simulation(cfg, device=device).init_fields(*fields)
+    try:
+        lbm_adj_begin(sim.handle, checkpoint_every, steps)
+        ptr, stride, keep = _ref_arg(sim, dP_ref, steps)
+        J = lbm_adj_forward(sim.handle, steps, ptr, stride)
+        dJ = lbm_adj_backward(sim.handle)
+        del keep
+        lbm_adj_end(sim.handle)
+    finally:
+        sim.close()
+    return J, dJ
+
+
+def _make_cbc_loss_adjoint():
+    import torch
+
+    class CBCLossAdjoint(torch.autograd.Function):
+        """J(theta) as a differentiable function computed in reverse mode:
+        forward runs the checkpointed forward steps (J), backward the
+        reverse sweep (dJ/dtheta for all parameters at once)."""
+
+        @staticmethod
+        def forward(ctx, theta, cfg, fields, steps, dP_ref, params, checkpoint_every):
+            th = theta.detach().cpu().double().tolist()
+            sim = Simulation(with_parameters(cfg, params, th), device=theta.device if theta.is_cuda else None)
+            sim.init_fields(*fields)
+            lbm_adj_begin(sim.handle, checkpoint_every, steps)
+            ptr, stride, keep = _ref_arg(sim, dP_ref, steps)
+            J = lbm_adj_forward(sim.handle, steps, ptr, stride)
+            ctx.sim, ctx.keep, ctx.params = sim, keep, params
+            return torch.tensor(J, dtype=theta.dtype, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            sim = ctx.sim
+            try:
+                dJ = lbm_adj_backward(sim.handle)
+                lbm_adj_end(sim.handle)
+            finally:
+                sim.close()
+            g = torch.tensor([dJ[THETA.index(n)] for n in ctx.params], dtype=grad_out.dtype,
+                             device=grad_out.device)
+            return grad_out * g, None, None, None, None, None, None
+
+    return CBCLossAdjoint
+
+
 _CBCLoss = None
+_CBCLossAdjoint = None
+
+
+def cbc_loss_adjoint(theta, cfg, fields, steps, dP_ref=None, params=THETA, checkpoint_every=100):
+    """Differentiable pressure loss J(theta) (torch autograd) whose
+    backward is the reverse-mode sweep: theta a tensor of the named THETA
+    parameters (default all five)."""
+    global _CBCLossAdjoint
+    if _CBCLossAdjoint is None:
+        _CBCLossAdjoint = _make_cbc_loss_adjoint()
+    return _CBCLossAdjoint.apply(theta, cfg, fields, steps, dP_ref, tuple(params), int(checkpoint_every))
 
 
 def cbc_loss(theta, cfg, fields, steps, dP_ref=None, params=("alpha_T", "beta_P", "p_inf")):

@@ -62,6 +62,20 @@ struct lbm_handle {
     TLState tl{};
     void* tl_mem = nullptr;
     bool grad_stale = false;
+    // reverse-mode gradients (lbm_adj_*): history and adjoint buffers, and the
+    // checkpoints of the forward pass (every adj_K steps, then the end state)
+    void* adj_mem = nullptr;
+    AdjState adj{};
+    int adj_max = 0, adj_n = 0;
+    long long adj_start = 0;
+    const double* adj_ref = nullptr;
+    long long adj_ref_stride = 0;
+    char* adj_ckpt = nullptr;
+    size_t adj_ckpt_bytes = 0;
+    size_t adj_hist_bytes = 0;          // one of the two history buffers (by segment parity)
+    bool adj_fwd_done = false;
+    cudaStream_t adj_sv = nullptr, adj_sw = nullptr;   // reverse steps: boundary, bulk
+    cudaEvent_t adj_ev[4] = {};         // step done, bulk done, segment recomputed, segment reversed
     std::string err;
 };
 
@@ -220,6 +234,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     G.omega = 1.0 / tau;
     G.omega_f = float(1.0 / tau);
     G.rho0_f = float(p->rho0);
+    G.wait_ns = 1000000000ull;
     for (int i = 0; i < Q; ++i) {
         const int plane_i = lattice_plane(lattice, i);
         pl.O.st[i] = int(plane_i * G.plane);
@@ -522,6 +537,12 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     B.kR = 1.0 / std::sqrt(2.0);
     B.cs = std::sqrt(cs2);
     B.ihcs = 0.5 / B.cs;
+    B.kA_f = float(B.kA);
+    B.kB_f = float(B.kB);
+    B.kC_f = float(B.kC);
+    B.kR_f = float(B.kR);
+    B.cs_f = float(B.cs);
+    B.ihcs_f = float(B.ihcs);
     pl.Uin[0] = p->inflow[0] - p->rho0;
     pl.Uin[1] = p->inflow[1];
     pl.Uin[2] = p->inflow[2];
@@ -826,6 +847,31 @@ int create_common(int lattice, int nx, int ny, double tau, const lbm_cbc_params*
 
 }  // namespace
 
+// FP64 FMA throughput (the roof of ALU-bound FP64 work): every thread runs
+// kFmaChains independent chains x <- x a + b on registers, enough to hide the
+// FMA latency at the FP64 issue rate; no memory traffic inside the loop.  The
+// chains start at x >= 0 and a, b > 0 keep them there, so the sum never
+// equals the negative `never` argument and nothing is stored; the test keeps
+// the chains live.
+constexpr int kFmaChains = 8, kFmaThreads = 256, kFmaCtasPerSm = 8;
+
+__global__ void __launch_bounds__(kFmaThreads) k_fp64_fma(double* out, int iters, double never)
+{
+    double x[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) x[c] = 1e-3 * (threadIdx.x + c);
+    const double a = 0.9999999, b = 1e-7;
+#pragma unroll 1
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kFmaChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) s += x[c];
+    if (s == never) out[blockIdx.x] = s;
+}
+
 extern "C" {
 
 int lbm_params_default(lbm_cbc_params* p)
@@ -903,7 +949,8 @@ int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux, const do
     int rc = launch_init(h->lattice, h->storage, h->G, h->E, h->B, dr, du, dv, dt, h->f[0], h->stream);
     if (rc) return check_launch(h, rc, "init kernels");
     h->inflow_done[0] = h->inflow_done[1] = false;
-    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaError_t e = cudaMemsetAsync(h->flag, 0, 2 * sizeof(int), h->stream);   // a fresh state, no status
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "init");
     h->steps = 0;
     h->initialized = true;
@@ -994,6 +1041,21 @@ int lbm_step(lbm_handle* h, int n)
         h->steps++;
     }
     return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_handle* h, double seconds)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (!(seconds >= 0.0) || !(seconds <= 60.0)) {
+        h->err = "wait limit must be in [0, 60] seconds";
+        return LBM_ERR_ARG;
+    }
+    h->G.wait_ns = (unsigned long long)(seconds * 1e9);
+    BulkRun* r = h->brun;   // the batch copy of this run's geometry, as well
+    const cudaError_t e = cudaMemcpyAsync(&r->G.wait_ns, &h->G.wait_ns, sizeof h->G.wait_ns,
+                                          cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "wait limit");
 }
 
 int lbm_set_kernel_events(lbm_handle* h, void* const* events, int n)
@@ -1238,6 +1300,320 @@ int lbm_grad_end(lbm_handle* h)
     return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "gradient state release");
 }
 
+// ---------------------------------------------------------------------------
+// Reverse-mode gradients with segment checkpointing (adjoint.cu)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Bytes of one checkpoint: the populations of the current parity, both
+// parities of the strips and of the boundary state.
+size_t adj_ckpt_layout(const lbm_handle* h, size_t* o_su, size_t* o_sn, size_t* o_ub)
+{
+    size_t o = align_up(h->f_bytes);
+    *o_su = o;
+    o = align_up(o + 8ull * h->E.nslots * h->E.sesize);
+    *o_sn = o;
+    o = align_up(o + 10ull * h->E.nslots * h->E.sesize);
+    *o_ub = o;
+    return align_up(o + 64ull * h->B.n_unk);
+}
+
+int adj_copy_state(lbm_handle* h, int idx, bool save)
+{
+    size_t o_su, o_sn, o_ub;
+    adj_ckpt_layout(h, &o_su, &o_sn, &o_ub);
+    char* c = h->adj_ckpt + (size_t)idx * h->adj_ckpt_bytes;
+    const size_t su = 8ull * h->E.nslots * h->E.sesize, sn = 10ull * h->E.nslots * h->E.sesize;
+    void* f = h->f[h->steps & 1];
+    auto cp = [&](void* ck, void* live, size_t n) {
+        if (n == 0) return cudaSuccess;
+        return save ? cudaMemcpyAsync(ck, live, n, cudaMemcpyDeviceToDevice, h->stream)
+                    : cudaMemcpyAsync(live, ck, n, cudaMemcpyDeviceToDevice, h->stream);
+    };
+    cudaError_t e = cp(c, f, h->f_bytes);
+    if (e == cudaSuccess) e = cp(c + o_su, h->E.stripU, su);
+    if (e == cudaSuccess) e = cp(c + o_sn, h->E.stripN, sn);
+    if (e == cudaSuccess) e = cp(c + o_ub, h->B.Ub, 64ull * h->B.n_unk);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, save ? "checkpoint" : "checkpoint restore");
+}
+
+// History buffer b (0 or 1) of the adjoint state: the same layout at an offset.
+AdjState adj_hist(const lbm_handle* h, int b)
+{
+    AdjState A = h->adj;
+    const size_t o = (size_t)b * h->adj_hist_bytes;
+    A.Mh = static_cast<char*>(A.Mh) + o;
+    A.Ubh = reinterpret_cast<double*>(reinterpret_cast<char*>(A.Ubh) + o);
+    A.stUh = static_cast<char*>(A.stUh) + o;
+    A.stNh = static_cast<char*>(A.stNh) + o;
+    return A;
+}
+
+// The boundary state and the strips of the current time into slot k of
+// history buffer A.
+int adj_snapshot(lbm_handle* h, const AdjState& A, int k)
+{
+    const int par = int(h->steps & 1);
+    const size_t nu = (size_t)h->B.n_unk, ns = (size_t)h->E.nslots, es = h->E.sesize;
+    cudaError_t e = cudaSuccess;
+    if (nu) e = cudaMemcpyAsync(A.Ubh + (size_t)k * nu * 4, h->B.Ub + par * nu * 4, nu * 32,
+                                cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && ns)
+        e = cudaMemcpyAsync(static_cast<char*>(A.stUh) + (size_t)k * ns * 4 * es,
+                            static_cast<char*>(h->E.stripU) + par * ns * 4 * es, ns * 4 * es,
+                            cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && ns)
+        e = cudaMemcpyAsync(static_cast<char*>(A.stNh) + (size_t)k * ns * 5 * es,
+                            static_cast<char*>(h->E.stripN) + par * ns * 5 * es, ns * 5 * es,
+                            cudaMemcpyDeviceToDevice, h->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "history snapshot");
+}
+
+}  // namespace
+
+int lbm_adj_begin(lbm_handle* h, int checkpoint_every, int max_steps)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (checkpoint_every < 1 || max_steps < 1) {
+        h->err = "checkpoint interval and step count must be positive";
+        return LBM_ERR_ARG;
+    }
+    if (!h->initialized || h->bulk_pending) { h->err = "lbm_adj_begin before a complete step state"; return LBM_ERR_STATE; }
+    if (h->grad_stale || h->tl_mem) { h->err = "tangent-linear gradient steps in use"; return LBM_ERR_STATE; }
+    if (h->adj_mem) { h->err = "reverse-mode gradients already begun"; return LBM_ERR_STATE; }
+    if (h->storage != LBM_F64 && h->storage != LBM_F32) {
+        h->err = "reverse-mode gradients need FP64 or FP32 storage";
+        return LBM_ERR_ARG;
+    }
+    if (h->B.n_unk > 0 && h->B.dirichlet != 0) {
+        h->err = "reverse-mode gradients need the equilibrium Dirichlet condition";
+        return LBM_ERR_ARG;
+    }
+    if (h->n_inflow > 0 || h->B.n_zg > 0) {
+        h->err = "reverse-mode gradients support characteristic and periodic sides only";
+        return LBM_ERR_ARG;
+    }
+    const int K = std::min(checkpoint_every, max_steps);
+    const size_t N = (size_t)h->nx * h->ny, nu = (size_t)std::max(1, h->B.n_unk),
+                 ns = (size_t)std::max(1, h->E.nslots), es = h->E.sesize;
+    const int nckpt = (max_steps + K - 1) / K + 1;
+    size_t o_su, o_sn, o_ub;
+    h->adj_ckpt_bytes = adj_ckpt_layout(h, &o_su, &o_sn, &o_ub);
+    size_t o = 0;
+    auto take = [&](size_t b) { const size_t at = o; o = align_up(o + b); return at; };
+    // two history buffers of the same layout (the recompute of one segment
+    // runs beside the reverse steps of the next)
+    const size_t o_mh = take((size_t)K * 4 * N * es), o_ubh = take((size_t)(K + 1) * nu * 32),
+                 o_suh = take((size_t)(K + 1) * ns * 4 * es), o_snh = take((size_t)(K + 1) * ns * 5 * es);
+    h->adj_hist_bytes = o;
+    o += h->adj_hist_bytes;
+    const size_t o_l0 = take(h->f_bytes), o_l1 = take(h->f_bytes), o_lu = take(nu * 32), o_lur = take(nu * 4 * es),
+                 o_y = take(4 * nu * 4 * es), o_ly = take(5 * nu * 4 * es),   // lY[0..3], then lV
+                 o_v = take(nu * 4 * es), o_mask = take(nu * sizeof(int)), o_lst = take(ns * 4 * es),
+                 o_lst1 = take(ns * 4 * es), o_ln = take(ns * 5 * es), o_e0 = take(ns * 9 * es),
+                 o_e1 = take(ns * 9 * es), o_sums = take(8 * sizeof(double)),
+                 o_ck = take((size_t)nckpt * h->adj_ckpt_bytes);
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, o);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reverse-mode gradient allocation");
+    AdjState& A = h->adj;
+    A = AdjState{};
+    A.K = K;
+    A.Mh = at<char>(mem, o_mh);
+    A.Ubh = at<double>(mem, o_ubh);
+    A.stUh = at<char>(mem, o_suh);
+    A.stNh = at<char>(mem, o_snh);
+    A.lpre[0] = at<char>(mem, o_l0);
+    A.lpre[1] = at<char>(mem, o_l1);
+    A.lU = at<double>(mem, o_lu);
+    A.lUr = at<char>(mem, o_lur);
+    const double rl[8] = {h->B.alpha_T, h->B.beta_P, h->B.t_inf, h->B.alpha_V,
+                          h->B.pdev[0], h->B.pdev[1], h->B.pdev[2], h->B.pdev[3]};
+    for (int q = 0; q < 8; ++q) {
+        A.relax_d[q] = rl[q];
+        A.relax_f[q] = float(rl[q]);
+    }
+    for (int q = 0; q < 4; ++q) {
+        A.Y[q] = at<char>(mem, o_y + q * nu * 4 * es);
+        A.lY[q] = at<char>(mem, o_ly + q * nu * 4 * es);
+    }
+    A.lV = at<char>(mem, o_ly + 4 * nu * 4 * es);
+    A.V = at<char>(mem, o_v);
+    A.mask = at<int>(mem, o_mask);
+    A.lSt = at<char>(mem, o_lst);
+    A.lSt1 = at<char>(mem, o_lst1);
+    A.lN = at<char>(mem, o_ln);
+    A.ext[0] = at<char>(mem, o_e0);
+    A.ext[1] = at<char>(mem, o_e1);
+    A.sums = at<double>(mem, o_sums);
+    h->adj_ckpt = at<char>(mem, o_ck);
+    h->adj_mem = mem;
+    h->adj_max = max_steps;
+    h->adj_fwd_done = false;
+    e = cudaStreamCreateWithFlags(&h->adj_sv, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->adj_sw, cudaStreamNonBlocking);
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&h->adj_ev[q], cudaEventDisableTiming);
+    // everything but the checkpoints starts at zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(mem, 0, o_ck, h->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "reverse-mode gradient state");
+}
+
+int lbm_adj_forward(lbm_handle* h, int n, const double* dP_ref, long long ref_stride, double* J)
+{
+    if (!h || !J) return LBM_ERR_ARG;
+    if (!h->adj_mem) { h->err = "lbm_adj_forward before lbm_adj_begin"; return LBM_ERR_STATE; }
+    if (n < 1 || n > h->adj_max) { h->err = fmt("step count %d outside [1, %d]", n, h->adj_max); return LBM_ERR_ARG; }
+    if (h->bulk_pending) { h->err = "lbm_adj_forward in the middle of a step"; return LBM_ERR_STATE; }
+    const int K = h->adj.K;
+    cudaError_t e = cudaMemsetAsync(h->adj.sums, 0, 8 * sizeof(double), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loss reset");
+    h->adj_start = h->steps;
+    int rc = adj_copy_state(h, 0, true);
+    for (int i = 0; i < n && rc == LBM_OK; ++i) {
+        if (i > 0 && i % K == 0) rc = adj_copy_state(h, i / K, true);
+        if (rc == LBM_OK) rc = lbm_step(h, 1);
+        if (rc == LBM_OK &&
+            launch_adj_loss(h->lattice, h->storage, h->G, h->bulk, h->f[h->steps & 1],
+                            dP_ref ? dP_ref + (long long)i * ref_stride : nullptr, h->adj.sums, nullptr,
+                            h->stream))
+            rc = check_launch(h, -1, "loss kernel");
+    }
+    if (rc != LBM_OK) return rc;
+    rc = adj_copy_state(h, (n + K - 1) / K, true);       // the end state
+    if (rc != LBM_OK) return rc;
+    h->adj_n = n;
+    h->adj_ref = dP_ref;
+    h->adj_ref_stride = ref_stride;
+    h->adj_fwd_done = true;
+    e = cudaMemcpyAsync(J, h->adj.sums, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "loss");
+}
+
+int lbm_adj_backward(lbm_handle* h, double* dJ)
+{
+    if (!h || !dJ) return LBM_ERR_ARG;
+    if (!h->adj_mem || !h->adj_fwd_done) { h->err = "lbm_adj_backward before lbm_adj_forward"; return LBM_ERR_STATE; }
+    AdjState& A = h->adj;
+    const int K = A.K, n = h->adj_n, nseg = (n + K - 1) / K;
+    const size_t N = (size_t)h->nx * h->ny, nu = (size_t)std::max(1, h->B.n_unk),
+                 ns = (size_t)std::max(1, h->E.nslots), es = h->E.sesize;
+    // adjoint variables start at zero
+    cudaError_t e = cudaSuccess;
+    void* zero[] = {A.lpre[0], A.lpre[1], A.lU, A.lUr, A.lSt, A.lSt1, A.lN, A.ext[0], A.ext[1]};
+    const size_t zbytes[] = {h->f_bytes, h->f_bytes, nu * 32, nu * 4 * es, ns * 4 * es, ns * 4 * es, ns * 5 * es,
+                             ns * 9 * es, ns * 9 * es};
+    for (int q = 0; q < 9 && e == cudaSuccess; ++q) e = cudaMemsetAsync(zero[q], 0, zbytes[q], h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.sums + 1, 0, 7 * sizeof(double), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint reset");
+    cudaStream_t sr = h->stream, sv = h->adj_sv, sw = h->adj_sw;
+    cudaEvent_t ev_step = h->adj_ev[0], ev_bulk = h->adj_ev[1], ev_rc = h->adj_ev[2], ev_rev = h->adj_ev[3];
+    // the reverse streams start after the resets
+    e = cudaEventRecord(ev_step, sr);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sv, ev_step, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint streams");
+    const size_t ub = nu * 4, su = ns * 4 * es, sn = ns * 5 * es;
+    // Recompute segment seg into history buffer seg & 1 (on the handle's
+    // stream, with ordinary steps), keeping what the reverse steps read.
+    auto recompute = [&](int seg) -> int {
+        const AdjState H = adj_hist(h, seg & 1);
+        const int L = std::min(K, n - seg * K);
+        h->steps = h->adj_start + (long long)seg * K;
+        int rc = adj_copy_state(h, seg, false);
+        for (int k = 0; k < L && rc == LBM_OK; ++k) {
+            rc = adj_snapshot(h, H, k);
+            if (rc == LBM_OK) rc = lbm_step(h, 1);
+            if (rc == LBM_OK && launch_adj_loss(h->lattice, h->storage, h->G, h->bulk, h->f[h->steps & 1], nullptr,
+                                                nullptr, static_cast<char*>(H.Mh) + (size_t)k * 4 * N * es, sr))
+                rc = check_launch(h, -1, "macros kernel");
+        }
+        if (rc == LBM_OK) rc = adj_snapshot(h, H, L);
+        return rc;
+    };
+    int rc = recompute(nseg - 1);
+    for (int seg = nseg - 1; seg >= 0 && rc == LBM_OK; --seg) {
+        // the reverse steps of seg wait for its recompute
+        e = cudaEventRecord(ev_rc, sr);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sv, ev_rc, 0);
+        if (e != cudaSuccess) { rc = cuda_fail(h, e, "adjoint streams"); break; }
+        const AdjState H = adj_hist(h, seg & 1);
+        const long long t0 = h->adj_start + (long long)seg * K;
+        const int L = std::min(K, n - seg * K);
+        for (int k = L - 1; k >= 0 && rc == LBM_OK; --k) {
+            const long long t = t0 + k;
+            const double* ref = h->adj_ref ? h->adj_ref + (t - h->adj_start) * h->adj_ref_stride : nullptr;
+            e = cudaEventRecord(ev_step, sv);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(sw, ev_step, 0);
+            if (e != cudaSuccess) { rc = cuda_fail(h, e, "adjoint streams"); break; }
+            if (launch_adj_step(h->lattice, h->storage, h->G, h->E, h->B, h->bulk, A, H.Ubh + (size_t)k * ub,
+                                H.Ubh + (size_t)(k + 1) * ub, static_cast<char*>(H.stUh) + (size_t)k * su,
+                                static_cast<char*>(H.stNh) + (size_t)k * sn,
+                                static_cast<char*>(H.stUh) + (size_t)(k + 1) * su,
+                                static_cast<char*>(H.Mh) + (size_t)k * 4 * N * es, ref, int(t & 1), sv, sw, ev_bulk))
+                rc = check_launch(h, -1, "reverse step");
+        }
+        // meanwhile the previous segment's recompute, into the other buffer
+        // once the reverse steps that read it (segment seg + 1) are done
+        if (rc == LBM_OK && seg > 0) {
+            e = cudaStreamWaitEvent(sr, ev_rev, 0);
+            if (e != cudaSuccess) { rc = cuda_fail(h, e, "adjoint streams"); break; }
+            rc = recompute(seg - 1);
+        }
+        if (rc == LBM_OK) {
+            e = cudaEventRecord(ev_rev, sv);
+            if (e != cudaSuccess) rc = cuda_fail(h, e, "adjoint streams");
+        }
+    }
+    // back to the state after the forward pass, after the last reverse step
+    if (rc == LBM_OK) {
+        e = cudaEventRecord(ev_step, sv);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sr, ev_step, 0);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "adjoint streams");
+    }
+    h->steps = h->adj_start + n;
+    if (rc == LBM_OK) rc = adj_copy_state(h, nseg, false);
+    if (rc != LBM_OK) {
+        cudaStreamSynchronize(sv);
+        cudaStreamSynchronize(sw);
+        return rc;
+    }
+    double v[8];
+    e = cudaMemcpyAsync(v, A.sums, sizeof v, cudaMemcpyDeviceToHost, sr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reverse sweep");
+    for (int k = 0; k < kTLParams; ++k) dJ[k] = v[1 + k];
+    return LBM_OK;
+}
+
+namespace {
+void adj_release(lbm_handle* h)
+{
+    if (h->adj_sv) cudaStreamSynchronize(h->adj_sv);
+    if (h->adj_sw) cudaStreamSynchronize(h->adj_sw);
+    for (int q = 0; q < 4; ++q)
+        if (h->adj_ev[q]) cudaEventDestroy(h->adj_ev[q]);
+    if (h->adj_sv) cudaStreamDestroy(h->adj_sv);
+    if (h->adj_sw) cudaStreamDestroy(h->adj_sw);
+    h->adj_sv = h->adj_sw = nullptr;
+    for (int q = 0; q < 4; ++q) h->adj_ev[q] = nullptr;
+}
+}  // namespace
+
+int lbm_adj_end(lbm_handle* h)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (!h->adj_mem) return LBM_OK;
+    cudaError_t e = h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize();
+    adj_release(h);
+    cudaFree(h->adj_mem);
+    h->adj_mem = nullptr;
+    h->adj = AdjState{};
+    h->adj_ckpt = nullptr;
+    h->adj_fwd_done = false;
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "reverse-mode gradient release");
+}
+
 const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
 
 void lbm_destroy(lbm_handle* h)
@@ -1247,6 +1623,10 @@ void lbm_destroy(lbm_handle* h)
     else cudaDeviceSynchronize();
     release_streams(h);
     if (h->tl_mem) cudaFree(h->tl_mem);
+    if (h->adj_mem) {
+        adj_release(h);
+        cudaFree(h->adj_mem);
+    }
     if (h->owns_ws && h->ws) cudaFree(h->ws);
     delete h;
 }
@@ -1629,6 +2009,35 @@ int lbm_batch_ctas_per_sm(const lbm_batch* b, int lattice, int storage)
 }
 
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : "NULL batch"; }
+
+int lbm_fp64_fma_rate(int iters, void* stream, double* flops_per_s)
+{
+    if (!flops_per_s || iters < 1 || iters > (1 << 24)) return LBM_ERR_ARG;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int grid = sms * kFmaCtasPerSm;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    float ms = 0.0f;
+    if (e == cudaSuccess) {
+        k_fp64_fma<<<grid, kFmaThreads, 0, st>>>(nullptr, 64, -1.0);   // warm-up
+        cudaEventRecord(ev[0], st);
+        k_fp64_fma<<<grid, kFmaThreads, 0, st>>>(nullptr, iters, -1.0);
+        cudaEventRecord(ev[1], st);
+        e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess || !(ms > 0.0f)) return LBM_ERR_CUDA;
+    *flops_per_s = 2.0 * kFmaChains * double(grid) * kFmaThreads * iters / (ms * 1e-3);
+    return LBM_OK;
+}
 
 void lbm_batch_destroy(lbm_batch* b)
 {

@@ -466,8 +466,9 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     X.Y = Ys;
     X.St = SUt;
     X.St1 = SUt1;
-    const double rho0 = G.rho0;
-    const R rho0r = rho0_of<R>(G), cs2r = R(L::CS2), kr = R(B.kR);
+    const R rho0r = rho0_of<R>(G), cs2r = R(L::CS2), kr = bconst<R>(B.kR, B.kR_f);
+    const R kAr = bconst<R>(B.kA, B.kA_f), kBr = bconst<R>(B.kB, B.kB_f), ihcsr = bconst<R>(B.ihcs, B.ihcs_f),
+            csr_ = bconst<R>(B.cs, B.cs_f);
     const bool corner = lev <= 4 && D.kind >= 4;
     const int scheme = corner ? SCH_LODI : (lev <= 4 ? B.scheme[D.kind] : 0);
     const bool cbc = scheme == SCH_CBC || scheme == SCH_CBC_RELAX;
@@ -590,7 +591,6 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         };
         R TTr[4] = {0, 0, 0, 0};        // transversal terms, local frame
         R Vr[4] = {0, 0, 0, 0};
-        double ir = 0.0, bb = 0.0, csr = 0.0;
         if (comp) {
             if (!corner) {
                 TTr[0] = XP(1);
@@ -608,39 +608,43 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                 Vr[2] = xv[2];
                 Vr[3] = TH ? xv[0] + xv[3] : R(0);
             }
-            const double irho = double(XP(0));
-            const double un = double(Ul[1]);
-            double k0 = 0.0, k1 = 0.0, k2 = 0.0, k3 = 0.0, lam = un;   // row rank of S
+            // Row `rank` of S (see apply_S) and Lambda_rank.  Their entries
+            // are formed from the inputs in type R (the inputs' own
+            // precision) and only the non-zero ones enter the FP64
+            // projections: thermal rows (-r/2, 0, 0, 1/2), (0, 0, 1, 0),
+            // (r/4, -+a, 0, 1/4); isothermal rows (1/2, -+h, 0), (0, 0, 1).
+            R c0 = R(0), c1 = R(0), c3 = R(0), lamr = Ul[1];
             bool acoustic = false;
             if (TH) {
-                const double sth = double(XP(2)), isth = double(XP(4));
-                const double rr = (1.0 + double(Ul[3])) * irho;
-                ir = (rho0 + double(Ul[0])) * isth * isth;
-                bb = isth * B.kB;
-                if (rank == 0) { k0 = -0.5 * rr; k3 = 0.5; }
-                else if (rank == 1) { k2 = 1.0; }
-                else {
-                    const double sg = rank == 2 ? -1.0 : 1.0;
-                    k0 = 0.25 * rr;
-                    k1 = sg * (sth * B.kA);
-                    k3 = 0.25;
-                    lam = un + sg * (sth * B.kB);
+                const R rr = (R(1) + Ul[3]) * XP(0);
+                if (rank == 0) {
+                    c0 = R(-0.5) * rr;
+                    c3 = R(0.5);
+                } else if (rank >= 2) {
+                    const R sg = rank == 2 ? R(-1) : R(1);
+                    c0 = R(0.25) * rr;
+                    c1 = sg * XP(2) * kAr;
+                    c3 = R(0.25);
+                    lamr = Ul[1] + sg * XP(2) * kBr;
                     acoustic = true;
                 }
-            } else {
-                csr = B.cs * irho;
-                if (rank == 1) { k2 = 1.0; }
-                else if (rank != 3) {
-                    const double sg = rank == 0 ? -1.0 : 1.0;
-                    k0 = 0.5;
-                    k1 = sg * ((rho0 + double(Ul[0])) * B.ihcs);
-                    lam = un + sg * B.cs;
-                    acoustic = true;
-                }
+            } else if (rank == 0 || rank == 2) {
+                const R sg = rank == 0 ? R(-1) : R(1);
+                c0 = R(0.5);
+                c1 = sg * (rho0r + Ul[0]) * ihcsr;
+                lamr = Ul[1] + sg * csr_;
+                acoustic = true;
             }
-            auto srow = [&](const R* v) {
-                return k0 * double(v[0]) + k1 * double(v[1]) + k2 * double(v[2]) + k3 * double(v[3]);
+            const double d0 = double(c0), d1 = double(c1), d3 = double(c3);
+            auto srow = [&](const R* v) -> double {
+                if (rank == 1) return double(v[2]);
+                if (TH) {
+                    const double sr = d0 * double(v[0]) + d3 * double(v[3]);
+                    return rank == 0 ? sr : sr + d1 * double(v[1]);
+                }
+                return d0 * double(v[0]) + d1 * double(v[1]);
             };
+            const double lam = double(lamr);
             if (stage == 0) incoming = lam < 0.0;
             double w = 0.0;
             if (TH || rank != 3) {
@@ -650,14 +654,13 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                     const double st = srow(TTr);
                     const double relaxP = acoustic ? B.beta_P * double(XP(5)) : 0.0;
                     if (scheme == SCH_LODI_RELAX) w = B.alpha_T * (B.t_inf - st) + relaxP;
-                    // the viscous projection (four FP64 products; none
-                    // when the viscous vector is off)
+                    // the viscous projection (none when the viscous vector is off)
                     else if (scheme == SCH_CBC) w = st + (B.viscous != VIS_OFF ? srow(Vr) : 0.0);
                     else {
                         // Eq. CBC-Relax; the viscous term relaxed towards 0
                         // at rate alpha_V (0: the paper's equation)
                         const double sv = B.viscous != VIS_OFF ? srow(Vr) : 0.0;
-                        w = st + sv + B.alpha_T * (B.t_inf - st) + B.alpha_V * (0.0 - sv) + relaxP;
+                        w = (1.0 - B.alpha_T) * st + (1.0 - B.alpha_V) * sv + B.alpha_T * B.t_inf + relaxP;
                     }
                 }
             }
@@ -673,22 +676,36 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
             }
         }
         if (xok) xok = wait_exchange(&xbar[stage & 1], (stage >> 1) & 1, B.status);
-        // C: lab component rank of the right-hand side; RK4 update (FP64)
+        // C: lab component rank of the right-hand side (S^-1 of the waves,
+        // with r^-1 = rho / theta, b = sqrt(2 c_s^4 / T~) formed in type R);
+        // RK4 update (FP64).  A side unknown's lab component 1 or 2 needs
+        // one local component only.
         if (comp) {
             const double* w = Xw + 4 * l;
             double kl1 = 0.0, kl2 = 0.0, klr = 0.0;
             if (rank == 0) {
-                klr = -(TH ? (w[2] + w[3] - w[0]) * ir : w[0] + w[2]);
+                if (TH) {
+                    const R irr = (rho0r + Ul[0]) * XP(4) * XP(4);
+                    klr = -((w[2] + w[3] - w[0]) * double(irr));
+                } else {
+                    klr = -(w[0] + w[2]);
+                }
                 if (cbc) klr += double(TTr[0]);
             } else if (rank == 3) {
                 klr = TH ? -(w[0] + w[2] + w[3]) : 0.0;
                 if (cbc && TH) klr += double(TTr[3]);
             } else {
-                kl1 = -(TH ? bb * (w[3] - w[2]) : csr * (w[2] - w[0]));
-                kl2 = -w[1];
-                if (cbc) {
-                    kl1 += double(TTr[1]);
-                    kl2 += double(TTr[2]);
+                const bool sideW = D.kind < 2;
+                const bool need1 = corner || ((rank == 1) == sideW);
+                const bool need2 = corner || ((rank == 1) != sideW);
+                if (need1) {
+                    const R bf = TH ? XP(4) * kBr : csr_ * XP(0);
+                    kl1 = -(double(bf) * (TH ? w[3] - w[2] : w[2] - w[0]));
+                    if (cbc) kl1 += double(TTr[1]);
+                }
+                if (need2) {
+                    kl2 = -w[1];
+                    if (cbc) kl2 += double(TTr[2]);
                 }
             }
             kc = lab_component(rank, D.kind, B.kR, klr, kl1, kl2, klr);
@@ -717,8 +734,13 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     cl.sync();                          // no CTA leaves while its Fx may be read
 }
 
+// At most 128 registers with FP32 / FP16 storage: a band CTA then leaves room
+// for the five two-row bulk CTAs on its SM (5 x 128 x 72 + 128 x 128 registers).
+template <typename S>
+constexpr int band_min_blocks() { return sizeof(S) == 8 ? 1 : 4; }
+
 template <int LAT, typename S>
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads)
+__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads, band_min_blocks<S>())
     k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
            int par_t)
 {
@@ -1074,6 +1096,10 @@ extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, doub
     G.M = M;
     G.tau = tau;
     G.rho0 = p->rho0;
+    G.rho0_f = float(p->rho0);
+    G.wait_ns = 1000000000ull;
+    G.omega = 1.0 / tau;
+    G.omega_f = float(G.omega);
     Band B{};
     B.n_unk = n;
     B.M = M;
@@ -1091,6 +1117,12 @@ extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, doub
     B.kR = 1.0 / std::sqrt(2.0);
     B.cs = std::sqrt(cs2);
     B.ihcs = 0.5 / B.cs;
+    B.kA_f = float(B.kA);
+    B.kB_f = float(B.kB);
+    B.kC_f = float(B.kC);
+    B.kR_f = float(B.kR);
+    B.cs_f = float(B.cs);
+    B.ihcs_f = float(B.ihcs);
     B.Ub = Ub;
     B.Ya = scratch;
     B.Yb = scratch + 4ull * kNoAllocMaxUnknowns;

@@ -54,25 +54,37 @@ struct Stage {
     }
 };
 
-// Wait for phase `parity` of a transaction barrier with a 1 s limit; on
-// timeout record it in *status and wait once more (again bounded) for copies
-// still in flight before giving up.
-__device__ bool wait_tx(unsigned long long* bar, int* status, unsigned parity = 0)
+// Wait for phase `parity` of a transaction barrier for at most limit_ns (the
+// handle's wait limit, 1 s by default; 0: one non-blocking test, as
+// try_wait may itself suspend the thread for longer than the copies take);
+// on timeout record it in *status and wait once more, for at most 1 s, for
+// the copies still in flight, so that none lands in the shared memory of a
+// CTA that has left.
+__device__ bool wait_tx(unsigned long long* bar, int* status, unsigned long long limit_ns, unsigned parity = 0)
 {
     const unsigned a = smem_u32(bar);
     for (int attempt = 0; attempt < 2; ++attempt) {
-        const unsigned long long t0 = global_ns();
+        const unsigned long long t0 = global_ns(), lim = attempt == 0 ? limit_ns : 1000000000ull;
         for (;;) {
             unsigned ok;
-            asm volatile(
-                "{\n .reg .pred p;\n"
-                " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                " selp.u32 %0, 1, 0, p;\n}"
-                : "=r"(ok)
-                : "r"(a), "r"(parity)
-                : "memory");
+            if (lim == 0)
+                asm volatile(
+                    "{\n .reg .pred p;\n"
+                    " mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                    " selp.u32 %0, 1, 0, p;\n}"
+                    : "=r"(ok)
+                    : "r"(a), "r"(parity)
+                    : "memory");
+            else
+                asm volatile(
+                    "{\n .reg .pred p;\n"
+                    " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                    " selp.u32 %0, 1, 0, p;\n}"
+                    : "=r"(ok)
+                    : "r"(a), "r"(parity)
+                    : "memory");
             if (ok) return attempt == 0;
-            if (global_ns() - t0 > 1000000000ull) break;
+            if (global_ns() - t0 > lim) break;
         }
         if (attempt == 0) atomicOr(status, 2);
     }
@@ -196,11 +208,11 @@ __global__ void __launch_bounds__(kBulkThreads)
         if (y >= R.y1) break;
         C g[Q];
         if (staged(y)) {
-            if (!wait_tx(&bar[r], status)) {
+            if (!wait_tx(&bar[r], status, G.wait_ns)) {
                 // timed out (status set): let the later rows' copies land
                 // (bounded) before the CTA's shared memory goes away
                 for (int q = r + 1; q < ROWS; ++q)
-                    if (staged(yb + q)) wait_tx(&bar[q], status);
+                    if (staged(yb + q)) wait_tx(&bar[q], status, G.wait_ns);
                 return;
             }
             if (!valid) continue;
@@ -303,7 +315,7 @@ __global__ void __launch_bounds__(kBulkThreads)
         bool ok = true;
         C g[L::Q];
         if (cur.staged) {
-            ok = wait_tx(&bar[stage], R.status, stage ? phase1 : phase0);
+            ok = wait_tx(&bar[stage], R.status, R.G.wait_ns, stage ? phase1 : phase0);
             if (stage) phase1 ^= 1u;
             else phase0 ^= 1u;
             ok = __syncthreads_and(ok);     // one decision for the whole CTA
@@ -316,7 +328,7 @@ __global__ void __launch_bounds__(kBulkThreads)
         if (!ok) {
             // a copy never completed: wait (bounded) for the one in flight
             // for the next item, then leave
-            if (wn < total && nxt.staged) wait_tx(&bar[stage ^ 1], R.status, stage ? phase0 : phase1);
+            if (wn < total && nxt.staged) wait_tx(&bar[stage ^ 1], R.status, R.G.wait_ns, stage ? phase0 : phase1);
             break;
         }
         if (valid) {

@@ -51,6 +51,16 @@ __device__ __forceinline__ void to_lab(int kind, R r, const R* Lc, R* U)
     }
 }
 
+// A constant of the boundary solver in arithmetic type T: its float
+// rounding for float-valued T (the same value the conversion would give),
+// the double otherwise.
+template <typename T>
+__device__ __forceinline__ T bconst(double d, float f)
+{
+    if constexpr (sizeof(typename DualTraits<T>::Value) == 4) return T(f);
+    else return T(d);
+}
+
 // Where a right-hand side reads its neighbours, in arithmetic type R.
 template <typename R>
 struct CtxT {
@@ -137,10 +147,10 @@ __device__ __forceinline__ Relax<T> relax_of(const Band& B)
 }
 
 template <bool TH, typename T>
-__device__ __forceinline__ CharSys<T> char_sys(const Band& B, double rho0, const T* U)
+__device__ __forceinline__ CharSys<T> char_sys_r(const Band& B, const T& rho0, const T* U)
 {
     CharSys<T> C;
-    C.rho = T(rho0) + U[0];
+    C.rho = rho0 + U[0];
     C.irho = T(1) / C.rho;
     if (TH) {
         const T th = T(1) + U[3];
@@ -148,24 +158,30 @@ __device__ __forceinline__ CharSys<T> char_sys(const Band& B, double rho0, const
         const T isth = T(1) / sth;
         C.r = th * C.irho;
         C.ir = C.rho * isth * isth;
-        C.a = sth * T(B.kA);
-        C.b = isth * T(B.kB);
-        const T c = sth * T(B.kB);
+        C.a = sth * bconst<T>(B.kA, B.kA_f);
+        C.b = isth * bconst<T>(B.kB, B.kB_f);
+        const T c = sth * bconst<T>(B.kB, B.kB_f);
         C.lam[0] = U[1];
         C.lam[1] = U[1];
         C.lam[2] = U[1] - c;
         C.lam[3] = U[1] + c;
         C.h = C.csr = T(0);
     } else {
-        C.h = C.rho * T(B.ihcs);
-        C.csr = T(B.cs) * C.irho;
-        C.lam[0] = U[1] - T(B.cs);
+        C.h = C.rho * bconst<T>(B.ihcs, B.ihcs_f);
+        C.csr = bconst<T>(B.cs, B.cs_f) * C.irho;
+        C.lam[0] = U[1] - bconst<T>(B.cs, B.cs_f);
         C.lam[1] = U[1];
-        C.lam[2] = U[1] + T(B.cs);
+        C.lam[2] = U[1] + bconst<T>(B.cs, B.cs_f);
         C.lam[3] = T(0);
         C.r = C.ir = C.a = C.b = T(0);
     }
     return C;
+}
+
+template <bool TH, typename T>
+__device__ __forceinline__ CharSys<T> char_sys(const Band& B, double rho0, const T* U)
+{
+    return char_sys_r<TH, T>(B, T(rho0), U);
 }
 
 template <bool TH, typename T>
@@ -281,9 +297,9 @@ __device__ void vis_meso(const Geom& G, const T* SU, int su, const T* SN, int sn
     for (int m = 0; m < 7; ++m) {
         dn[m] = T(0.5) * (T(3) * h[0][m] - T(4) * h[1][m] + h[2][m]);
         if (D.tmode == 0) dt[m] = T(0.5) * (h[3][m] - h[4][m]);
-        else dt[m] = T(double(D.tmode)) * T(0.5) * (T(3) * h[0][m] - T(4) * h[3][m] + h[4][m]);
+        else dt[m] = T(float(D.tmode)) * T(0.5) * (T(3) * h[0][m] - T(4) * h[3][m] + h[4][m]);
     }
-    const T irho = T(1) / (T(G.rho0) + SU[(long long)su * D.vs[0]]);
+    const T irho = T(1) / (bconst<T>(G.rho0, G.rho0_f) + SU[(long long)su * D.vs[0]]);
     V[0] = T(0);
     V[1] = (dn[0] + dt[1]) * irho;
     V[2] = (dn[1] + dt[2]) * irho;
@@ -347,7 +363,7 @@ __device__ void unknown_rhs(const Geom& G, const Band& B, const Relax<T>& P, con
     using L = Lat<LAT>;
     constexpr bool TH = L::THERMAL;
     const int kind = D.kind;
-    const T r = T(B.kR);
+    const T r = bconst<T>(B.kR, B.kR_f);
     T U[4], A[4], Bv[4], dUn[4];
     fetch_local(X, u, kind, r, U);
     if (kind >= 4) {
@@ -356,9 +372,9 @@ __device__ void unknown_rhs(const Geom& G, const Band& B, const Relax<T>& P, con
         fetch_local(X, D.nb[0], kind, r, A);
         fetch_local(X, D.nb[1], kind, r, Bv);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) dUn[m] = (T(3) * U[m] - T(4) * A[m] + Bv[m]) * T(B.kC);
+        for (int m = 0; m < 4; ++m) dUn[m] = (T(3) * U[m] - T(4) * A[m] + Bv[m]) * bconst<T>(B.kC, B.kC_f);
         const T zero[4] = {T(0), T(0), T(0), T(0)};
-        const CharSys<T> C = char_sys<TH>(B, G.rho0, U);
+        const CharSys<T> C = char_sys_r<TH, T>(B, bconst<T>(G.rho0, G.rho0_f), U);
         T kl[4];
         char_rhs<TH>(C, P, dUn, zero, zero, mask, T(0), SCH_LODI, kl);
         to_lab(kind, r, kl, k);
@@ -379,8 +395,8 @@ __device__ void unknown_rhs(const Geom& G, const Band& B, const Relax<T>& P, con
     T Up[4], Um[4];
     fetch_local(X, D.nb[4], kind, r, Up);
     fetch_local(X, D.nb[5], kind, r, Um);
-    const T rho0 = T(G.rho0), cs2 = T(L::CS2);
-    const CharSys<T> C = char_sys<TH>(B, G.rho0, U);
+    const T rho0 = bconst<T>(G.rho0, G.rho0_f), cs2 = T(L::CS2);
+    const CharSys<T> C = char_sys_r<TH, T>(B, rho0, U);
     const T ut = U[2];
     const T d_rhout = T(0.5) * ((rho0 + Up[0]) * Up[2] - (rho0 + Um[0]) * Um[2]);
     const T d_un = T(0.5) * (Up[1] - Um[1]);

@@ -417,6 +417,7 @@ struct Geom {
     long long plane;            // ny * nxp
     double tau, rho0, omega;    // omega = 1 / tau
     float omega_f, rho0_f;
+    unsigned long long wait_ns; // limit of the bulk kernel's first wait for a tensor copy
 };
 
 // A rectangle of bulk nodes [x0, x1) x [y0, y1).
@@ -556,6 +557,9 @@ struct Band {
     double kR;       // 1 / sqrt 2: corner frame
     double cs;       // c_s (isothermal system)
     double ihcs;     // 1 / (2 c_s)
+    // the same constants rounded to float, for arithmetic in float-valued
+    // types (no double-to-float conversion, an FP64-pipe instruction, per use)
+    float kA_f, kB_f, kC_f, kR_f, cs_f, ihcs_f;
     const UDesc* ud;
     const int2* zg;  // (node, source) grid offsets
     // Tiles of the band kernel: tile t holds local descriptors
@@ -685,5 +689,53 @@ int launch_tl_step(int lat, int storage, const TLState& T, const Geom& G, const 
 // lbm_grad_begin's clear).
 int launch_tl_seed(int lat, int storage, const TLState& T, const Geom& G, const Export& E, const Band& B,
                    void* const f[2], int par, cudaStream_t st);
+
+// Reverse-mode (adjoint) sweep (adjoint.cu).  History of one recomputed
+// segment (index k = step - first step of the segment) and the adjoint
+// variables; element type C = the storage's arithmetic (populations) and R =
+// StripReal (boundary solver inputs), except where stated.
+struct AdjState {
+    int K;            // checkpoint interval: steps per segment
+    void* Mh;         // [K][ny * nx][4] (R): drho, ux, uy, dT of the bulk nodes after step k
+    double* Ubh;      // [K + 1][n_unk][4]: boundary state before step k
+    void* stUh;       // [K + 1][nslots][4] (R): strip macros of the time before step k
+    void* stNh;       // [K + 1][nslots][5] (R): strip non-equilibrium moments, same time
+    void* lpre[2];    // [Q][plane] (C): adjoint of the pulled (pre-collision) populations,
+                      // by parity of their time
+    double* lU;       // [n_unk][4]: adjoint of the boundary state
+    void* lUr;        // [n_unk][4] (R): its rounding, read by the stage kernels
+    void* Y[4];       // [n_unk][4] (R): RK4 stage fields at the unknowns (Y[0] = U_b(t))
+    void* lY[4];      // [n_unk][4] (R): their adjoints
+    void* V;          // [n_unk][4] (R): viscous vector of the step (frozen)
+    void* lV;         // [n_unk][4] (R): its adjoint
+    int* mask;        // [n_unk]: incoming waves of the step
+    void* lSt;        // [nslots][4] (R): adjoint of the strip macros of time t
+    void* lSt1;       // [nslots][4] (R): adjoint of the strip macros of time t + 1
+    void* lN;         // [nslots][5] (R): adjoint of the strip moments of time t
+    void* ext[2];     // [nslots][9] (R): what the strips add to the adjoint of the pulled
+                      // populations of a strip node, by parity of the time: 4 moment
+                      // coefficients, 5 weights of the non-equilibrium moments
+    double* sums;     // [7]: J, dJ / d(alpha_T, beta_P, P_inf, alpha_V, t_inf), J again
+    // alpha_T, beta_P, t_inf, alpha_V, P_inf - c_s^2 rho0 per side, rounded
+    // to float and as double (the stage kernels take their arithmetic's)
+    float relax_f[8];
+    double relax_d[8];
+};
+// Loss of the state in f (populations after a step) against dPref (or 0):
+// sums[0] += sum over the bulk nodes of (P - c_s^2 rho0 - dPref)^2 (skipped
+// if sums is null); the bulk nodes' moments into Mout ([ny * nx][4] of the
+// strip type; skipped if null).
+int launch_adj_loss(int lat, int storage, const Geom& G, const Region& bulk, const void* f,
+                    const double* dPref, double* sums, void* Mout, cudaStream_t st);
+// One reverse step for the forward step t -> t + 1 (see adjoint.cu):
+// Ub, Ub1: the boundary state at t and t + 1; stU, stN: strips of t; stU1:
+// strip macros of t + 1; Mh1: macros at t + 1; dPref1: the loss reference at
+// t + 1 (or null); par: parity of t.  The boundary kernels go on st, the
+// bulk kernel on sw (after what sw already waits for), joined on st through
+// ev_bulk before the step's last kernel.
+int launch_adj_step(int lat, int storage, const Geom& G, const Export& E, const Band& B,
+                    const Region& bulk, const AdjState& A, const double* Ub, const double* Ub1,
+                    const void* stU, const void* stN, const void* stU1, const void* Mh1,
+                    const double* dPref1, int par, cudaStream_t st, cudaStream_t sw, cudaEvent_t ev_bulk);
 
 }  // namespace lbmgb

@@ -258,24 +258,38 @@ def test_d2q37_pulse_256_full_2000_steps_f32_continuous_scheme():
 def test_d2q37_pulse_256_f32_switching_scheme(capsys):
     """alpha_T = 0.5: the incoming-wave treatment of the waves with
     Lambda = u_n jumps by (1 - alpha_T) T_i when u_n changes sign (Sec. 3.2
-    classifies by the sign of Lambda).  At a boundary at rest FP32 rounding
-    can put a node on the other side of that switch once the boundary is
-    nearly at rest, so FP32 is held to 1e-5 while the pulse crosses the
-    boundary (150 steps) and its 2000-step error is reported against an
-    absolute bound."""
+    classifies by the sign of Lambda), and once the pulse has left, the
+    boundary is nearly at rest and that switch amplifies any perturbation.
+    FP32 storage meets 1e-5 while the pulse crosses the boundary (150 steps).
+    After 2000 steps it does not (rel_u ~0.17 against the tiny residual
+    flow); the FP64 run itself, with its initial fields perturbed by 1e-10
+    (seeded), moves as far from the unperturbed FP64 oracle.  The test
+    reports both and holds FP32 to within a factor of 3 of that conditioning
+    figure, and reports the error against max |u| over the whole run."""
     cfg, f = W.pulse_d2q37(256, alpha_T=0.5, steps=2000, storage="f64")
     cfg["viscous"] = "off"
     assert_parity(cfg, f, 150, "f32", ("pulse256", 0.5, 150))
-    c = dict(cfg)
-    c["storage"] = "f32"
-    got = gpu_run(c, f, 2000)
-    ref = oracle_run(cfg, f, 2000, ("pulse256", 0.5, 2000))
-    e = rel_errors(got, ref)
-    absd = max(np.abs(g - r).max() for g, r in zip(got, ref))
+    # oracle history: max |u| over the run
+    o = oracle.Sim(cfg).init(*f)
+    umax_run = 0.0
+    for _ in range(40):
+        o.step(50)
+        m = o.macros()
+        umax_run = max(umax_run, np.abs(m[1]).max(), np.abs(m[2]).max())
+    ref = o.macros()
+    got32 = gpu_run(dict(cfg, storage="f32"), f, 2000)
+    rng = np.random.default_rng(5)
+    fp = tuple(a * (1.0 + 1e-10 * rng.standard_normal(a.shape)) if i in (0, 3) else a
+               for i, a in enumerate(f))
+    got64p = gpu_run(cfg, fp, 2000)
+    e32, econd = rel_errors(got32, ref), rel_errors(got64p, ref)
+    du32 = max(np.abs(got32[1] - ref[1]).max(), np.abs(got32[2] - ref[2]).max())
     with capsys.disabled():
-        print("\nFP32, alpha_T = 0.5, 2000 steps: rel errors", {k: "%.2e" % v for k, v in e.items()},
-              "max abs %.2e" % absd)
-    assert absd < 1e-6
+        print("\nalpha_T = 0.5, 2000 steps: FP32 rel errors", {k: "%.2e" % v for k, v in e32.items()},
+              "| FP64 with 1e-10 perturbed fields", {k: "%.2e" % v for k, v in econd.items()},
+              "| FP32 |du| / max|u| over the run %.2e" % (du32 / umax_run))
+    assert e32["rho"] < 1e-5 and e32["T"] < 1e-5, e32
+    assert e32["u"] < 3.0 * econd["u"], (e32, econd)
 
 
 def test_d2q37_pulse_256_meso_viscous_prefix():
@@ -342,30 +356,35 @@ def test_d2q37_many_tiles_pulse_through_a_corner():
 
 @pytest.mark.parametrize("Ma", [0.1, 0.3])
 def test_vortex_1024x512_20000_steps_fp32_fp16_against_fp64(Ma, capsys):
-    """The benchmark grid's vortex (inflow | CBC-RELAX, periodic y) at Ma =
-    0.1 and 0.3 over 20000 steps, FP32 and FP16 storage against the FP64
-    path (which matches the oracle to 1e-12 on the shorter runs above), per
-    field.  The viscous vector is off: with either viscous form this set-up
-    becomes non-finite within a few thousand steps in FP64 as well (the
-    finding recorded for the vortex benchmark), while the benchmark's timed
-    window, a few hundred steps, stays finite.  FP32: rho and T within 1e-5;
-    u (relative to max |u|) accumulates the FP32 rounding of the stored
-    populations in the moving flow, 2-6e-5 measured, bar 1e-4.  FP16:
-    reported, with loose bars."""
+    """The benchmark grid's vortex (inflow | CBC-RELAX with the mesoscopic
+    viscous vector, periodic y) at Ma = 0.1 and 0.3 over 20000 steps, FP32
+    and FP16 storage against the FP64 path (which matches the oracle to
+    1e-12 over the first 2000 steps, below), per field.  FP32: rho and T
+    within the 1e-5 target; u (relative to max |u|) misses it -- 2.9e-5 and
+    4.2e-5 measured -- and is held here to 1e-4 so that a change for the
+    worse shows.  FP16: reported, with loose bars."""
     steps = 20000
 
     def run(storage):
         cfg, f = W.vortex_d2q37(1024, 512, Ma=Ma, steps=steps, storage=storage)
-        return gpu_run(dict(cfg, viscous="off"), f, steps)
+        return gpu_run(cfg, f, steps)
 
     ref = run("f64")
     res = {st: rel_errors(run(st), ref) for st in ("f32", "f16")}
     with capsys.disabled():
-        print("\nvortex 1024x512 Ma=%.1f, %d steps, viscous off, rel. errors vs FP64:" % (Ma, steps),
+        print("\nvortex 1024x512 Ma=%.1f, %d steps, mesoscopic V, rel. errors vs FP64 (target 1e-5):" % (Ma, steps),
               {st: {k: "%.2e" % v for k, v in e.items()} for st, e in res.items()})
     assert res["f32"]["rho"] < 1e-5 and res["f32"]["T"] < 1e-5, res
     assert res["f32"]["u"] < 1e-4, res
     assert res["f16"]["rho"] < 5e-3 and res["f16"]["T"] < 5e-3 and res["f16"]["u"] < 2e-2, res
+
+
+def test_d2q37_vortex_1024x512_2000_steps_f64_oracle():
+    """The benchmark configuration (mesoscopic viscous vector) over 2000
+    steps, FP64 storage, every node against the oracle (about a minute of
+    oracle time on the host)."""
+    cfg, f = W.vortex_d2q37(1024, 512, Ma=0.1, steps=2000, storage="f64")
+    assert_parity(cfg, f, 2000, "f64", "vortex1024_2000")
 
 
 def test_d2q37_vortex_1024x512_first_500_steps_f64():
@@ -392,6 +411,29 @@ def test_f16_storage_error_per_field(capsys):
 
 
 # ---------------------------------------------------------- API behaviour ---
+
+def test_bounded_tma_wait_gives_up_with_a_timeout_status():
+    """With a wait limit of 0 the bulk kernel's first wait for its tensor
+    copies runs out: the kernel records it, waits (bounded, 1 s) for the
+    copies in flight and leaves; the macros call reports LBM_ERR_TIMEOUT and
+    the context stays usable -- with the default limit restored, the same
+    run matches the oracle again."""
+    L = lbm()
+    cfg, f = W.pulse_d2q37(64, alpha_T=0.5, steps=5, storage="f32", width=5.0, offset=3.0)
+    sim = L.Simulation(cfg).init_fields(*f)
+    L.lbm_set_wait_limit(sim.handle, 0.0)
+    sim.step(2)
+    with pytest.raises(L.LbmError) as e:
+        sim.macros()
+    assert e.value.code == -6
+    L.lbm_set_wait_limit(sim.handle, 1.0)
+    sim.init_fields(*f)
+    sim.step(5)
+    got = sim.macros()
+    sim.close()
+    e2 = rel_errors(got, oracle_run(dict(cfg, storage="f64"), f, 5))
+    assert max(e2.values()) < 1e-5, e2
+
 
 def test_saved_state_holds_no_leftover_workspace_bytes():
     """A handle's population buffers are zeroed at creation, so a saved
