@@ -182,7 +182,7 @@ def bulk_fp64_flops():
         m = re.match(r"flops\s+nodes=(\d+)\s+dfma=(\d+)\s+dadd=(\d+)\s+dmul=(\d+)\s+src=(\w+)", line.strip())
         if m and m.group(5) == sha:
             n, fma, add, mul = (int(m.group(k)) for k in range(1, 5))
-            return (2 * fma + add + mul) / n
+            return {"flops": (2 * fma + add + mul) / n, "instructions": (fma + add + mul) / n}
     return None
 
 
@@ -191,13 +191,18 @@ def fp64_roofline(interior_nodes, interior_ms):
     this GPU (lbm_fp64_fma_rate), with the flop count per update above."""
     import paper_2307_16766_gb300 as lbm
     peak = lbm.fp64_fma_rate() / 1e12
-    fpu = bulk_fp64_flops()
+    cnt = bulk_fp64_flops()
     d = {"bound": "alu", "peak": peak, "unit": "TFLOP/s", "kernel": "k_bulk<D2Q37, double>",
-         "peak_kind": "measured FP64 FMA throughput (lbm_fp64_fma_rate, this run)", "flops_per_update": fpu,
-         "achieved": None, "frac": None}
-    if fpu is not None:
-        d["achieved"] = fpu * interior_nodes / (interior_ms / 1e3) / 1e12
+         "peak_kind": "measured FP64 FMA throughput (lbm_fp64_fma_rate, this run)",
+         "flops_per_update": None, "achieved": None, "frac": None, "issue_frac": None}
+    if cnt is not None:
+        rate = interior_nodes / (interior_ms / 1e3)
+        d["flops_per_update"] = cnt["flops"]
+        d["fp64_instructions_per_update"] = cnt["instructions"]
+        d["achieved"] = cnt["flops"] * rate / 1e12
         d["frac"] = d["achieved"] / peak
+        # FP64 instructions issued against the pipe's rate (an FMA is 2 flops, one issue)
+        d["issue_frac"] = cnt["instructions"] * rate / (peak * 1e12 / 2)
     return d
 
 

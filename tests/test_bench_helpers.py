@@ -27,6 +27,19 @@ def test_traffic_capture_matches_the_current_bulk_source():
     assert bench.bulk_traffic("f64", nodes) is None          # no capture for that storage
 
 
+def test_fp64_flop_count_matches_the_current_bulk_source():
+    line = [l for l in open(os.path.join(ROOT, "profiles", "k_bulk_d2q37_f64_flops.txt"))
+            if l.startswith("flops")][0]
+    m = re.match(r"flops\s+nodes=(\d+)\s+dfma=(\d+)\s+dadd=(\d+)\s+dmul=(\d+)\s+src=(\w+)", line)
+    h = hashlib.sha256()
+    for f in ("bulk.cu", "collide.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2307_16766_gb300", "csrc", f), "rb").read())
+    assert m.group(5) == h.hexdigest()[:12]
+    n, fma, add, mul = (int(m.group(k)) for k in range(1, 5))
+    c = bench.bulk_fp64_flops()
+    assert c["flops"] == (2 * fma + add + mul) / n and c["instructions"] == (fma + add + mul) / n
+
+
 def test_bulk_nodes_of_the_workloads():
     cfg, _ = bench.workload(1024, 512, "f32", 1)                    # inflow | CBC, periodic y
     assert bench.bulk_nodes(cfg) == (1024 - 6) * 512
