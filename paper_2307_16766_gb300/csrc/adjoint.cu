@@ -60,10 +60,15 @@ template <typename S>
 using RT = typename StripReal<S>::T;      // boundary solver inputs
 
 constexpr int kAdjThreads = 128;
-// Forward derivative directions per evaluation: two, so that one boundary
-// unknown's right-hand side is differentiated by 15 threads with few
-// registers each (eight directions per thread spilled and ran 4x slower).
-constexpr int kChunk = 2;
+// The cooperative boundary kernel: two CTAs of six warps per SM (at most 170
+// registers a thread), so that one stage's derivative items (eight per
+// unknown) and the next step's stage items run in one pass of the grid.
+constexpr int kBandThreads = 192;
+// Forward derivative directions per evaluation: four, so that one boundary
+// unknown's right-hand side is differentiated by eight threads within the
+// register cap of kBandThreads (eight directions per thread spilled and ran
+// 4x slower; two needed two passes of the grid per stage).
+constexpr int kChunk = 4;
 constexpr int kRhsInputs = 29;            // 5 stage-field neighbours x 4, V (4), theta (5)
 constexpr int kRhsChunks = (kRhsInputs + kChunk - 1) / kChunk;
 constexpr int kMesoInputs = 36;           // 5 stencil nodes x (5 moments, u_x, u_y), drho of node 0
@@ -177,10 +182,10 @@ __device__ __forceinline__ R relax_value(const AdjState& A, int q)
 
 // Block sum of v[0..NV) added to sums[0..NV) (one double atomic per block
 // and value); every thread of the block must call it.
-template <int NV>
+template <int NV, int NT = kAdjThreads>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sums)
 {
-    __shared__ double part[NV][kAdjThreads / 32];
+    __shared__ double part[NV][NT / 32];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
 #pragma unroll
@@ -191,7 +196,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sums)
     if (threadIdx.x < NV) {
         double a = 0.0;
 #pragma unroll
-        for (int w = 0; w < kAdjThreads / 32; ++w) a += part[threadIdx.x][w];
+        for (int w = 0; w < NT / 32; ++w) a += part[threadIdx.x][w];
         if (a != 0.0) atomicAdd(sums + threadIdx.x, a);
     }
 }
@@ -207,14 +212,30 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sums)
 template <int LAT, typename S>
 __global__ void __launch_bounds__(kAdjThreads)
     k_adj_loss(Geom G, Region R, const S* __restrict__ f, const double* __restrict__ dPref, double* sums,
-               RT<S>* __restrict__ Mout)
+               RT<S>* __restrict__ Mout, AdjRecord rec)
 {
     using L = Lat<LAT>;
     using C = CT<S>;
     using Rt = RT<S>;
+    {
+        // the history record, one value per thread of the grid
+        const long long nrec = rec.n_ub + rec.n_su + rec.n_sn;
+        const long long nthr = (long long)gridDim.x * gridDim.y * kAdjThreads;
+        for (long long i = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * kAdjThreads + threadIdx.x; i < nrec;
+             i += nthr) {
+            if (i < rec.n_ub) rec.ubh[i] = rec.ub[i];
+            else if (i < rec.n_ub + rec.n_su) {
+                const long long j = i - rec.n_ub;
+                static_cast<Rt*>(rec.suh)[j] = static_cast<const Rt*>(rec.su)[j];
+            } else {
+                const long long j = i - rec.n_ub - rec.n_su;
+                static_cast<Rt*>(rec.snh)[j] = static_cast<const Rt*>(rec.sn)[j];
+            }
+        }
+    }
     const int x = R.x0 + blockIdx.x * kAdjThreads + threadIdx.x, y = R.y0 + blockIdx.y;
     double v[1] = {0.0};
-    if (x < R.x1) {
+    if (x < R.x1 && y < R.y1) {
         C g[L::Q];
         const long long node = (long long)y * G.nxp + x;
 #pragma unroll
@@ -243,40 +264,26 @@ __global__ void __launch_bounds__(kAdjThreads)
 // ---------------------------------------------------------------------------
 
 // lambda_U(t+1)[u] += sum over the nodes b the unknown writes and the
-// velocities i of lambda*_{t+1}(b, i) d f^eq_i / dU at U_b(t+1).  Thread
-// (u, k) takes moment k (the equilibrium on forward derivatives along it);
-// thread (u, 0) also sets the stage-0 field Y0[u] = U_b(t).
+// velocities i of lambda*_{t+1}(b, i) d f^eq_i / dU at U_b(t+1): per node,
+// sum_i lambda*_i dg^eq_i/dU_k of one node the Dirichlet write of unknown u
+// set (node q of a corner's M x M block, row-major; the node itself for a
+// side unknown), lambda*_i = lambda^pre_{t+2}(node + c_i, i), U = U_b(t+1).
 template <int LAT, typename S>
-__device__ __forceinline__ void adj_dirichlet_item(const Geom& G, const Band& B, const double* __restrict__ Ub,
-                                                   const double* __restrict__ Ub1, const CT<S>* __restrict__ lnext,
-                                                   double* lU, RT<S>* lUr, RT<S>* Y0, int tid)
+__device__ __forceinline__ CT<S> dirichlet_part(const Geom& G, const UDesc& D, const double* __restrict__ U,
+                                                const CT<S>* __restrict__ lnext, int k, int q)
 {
     using L = Lat<LAT>;
     using C = CT<S>;
     using D1 = Dual<C, 1>;
-    const int u = tid >> 2, k = tid & 3;
-    if (u >= B.n_unk) return;
-    if (k == 0) {
-#pragma unroll
-        for (int m = 0; m < 4; ++m) Y0[4LL * u + m] = RT<S>(Ub[4LL * u + m]);
-    }
-    if (!L::THERMAL && k == 3) return;
-    const UDesc D = B.ud[u];
+    const int a = q / G.M, b = q % G.M;
+    const long long node = D.wnode + (D.kind >= 4 ? a * D.wdx + b * D.wdy : 0);
+    const int x = int(node % G.nxp), y = int(node / G.nxp);
     C lam[L::Q];
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) lam[i] = C(0);
-    const int nb = D.kind >= 4 ? G.M : 1;
-    for (int a = 0; a < nb; ++a)
-        for (int b = 0; b < nb; ++b) {
-            const long long node = D.wnode + a * D.wdx + b * D.wdy;
-            const int x = int(node % G.nxp), y = int(node / G.nxp);
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) {
-                int xs = x + L::cx(i), ys = y + L::cy(i);
-                if (wrap_bulk(G, xs, ys)) lam[i] += lnext[L::plane_of(i) * G.plane + (long long)ys * G.nxp + xs];
-            }
-        }
-    const double* U = Ub1 + 4LL * u;
+    for (int i = 0; i < L::Q; ++i) {
+        int xs = x + L::cx(i), ys = y + L::cy(i);
+        lam[i] = wrap_bulk(G, xs, ys) ? lnext[L::plane_of(i) * G.plane + (long long)ys * G.nxp + xs] : C(0);
+    }
     Moments<LAT, D1> m;
     m.s0 = D1(U[0]);
     m.ux = D1(U[1]);
@@ -286,18 +293,65 @@ __device__ __forceinline__ void adj_dirichlet_item(const Geom& G, const Band& B,
     m.rho = D1(G.rho0) + m.s0;
     D1 ge[L::Q];
     equilibrium<LAT, D1>(m, ge);
-    C a = C(0);
+    C s = C(0);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) a += lam[i] * ge[i].d[0];
-    const double v = lU[4LL * u + k] + double(a);
+    for (int i = 0; i < L::Q; ++i) s += lam[i] * ge[i].d[0];
+    return s;
+}
+
+// The Dirichlet write's adjoint, thread (u, k): lambda_U(t+1)_k of unknown
+// u gains the share of the node it writes (of the first node of a corner's
+// block; the other M^2 - 1 nodes of the four corner blocks are items of
+// adj_corner_item, folded in by the next phase in a fixed order), by
+// forward derivatives of the equilibrium along moment k; thread (u, 0)
+// also sets the stage-0 field Y0[u] = U_b(t).
+template <int LAT, typename S>
+__device__ __forceinline__ void adj_dirichlet_item(const Geom& G, const Band& B, const double* __restrict__ Ub,
+                                                   const double* __restrict__ Ub1, const CT<S>* __restrict__ lnext,
+                                                   double* lU, RT<S>* lUr, RT<S>* Y0, int tid)
+{
+    using L = Lat<LAT>;
+    const int u = tid >> 2, k = tid & 3;
+    if (u >= B.n_unk) return;
+    if (k == 0) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) Y0[4LL * u + m] = RT<S>(Ub[4LL * u + m]);
+    }
+    if (!L::THERMAL && k == 3) return;
+    const double v = lU[4LL * u + k] + double(dirichlet_part<LAT, S>(G, B.ud[u], Ub1 + 4LL * u, lnext, k, 0));
     lU[4LL * u + k] = v;
     lUr[4LL * u + k] = RT<S>(v);
+}
+
+// Item (c, k, q) of the corner blocks: node q + 1 of corner c's block.
+template <int LAT, typename S>
+__device__ __forceinline__ void adj_corner_item(const Geom& G, const Band& B, const AdjState& A,
+                                                const double* __restrict__ Ub1, const CT<S>* __restrict__ lnext,
+                                                int tid)
+{
+    using L = Lat<LAT>;
+    const int per = G.M * G.M - 1;
+    const int c = tid / (4 * per), k = (tid / per) % 4, q = tid % per;
+    const int u = B.n_unk - 4 + c;
+    A.cpart[tid] = (!L::THERMAL && k == 3)
+                       ? 0.0
+                       : double(dirichlet_part<LAT, S>(G, B.ud[u], Ub1 + 4LL * u, lnext, k, q + 1));
+}
+
+// The other nodes' shares of corner unknown u's block (component k), in
+// order: the reverse step's first stage phase and its last phase add them.
+__device__ __forceinline__ double corner_share(const Geom& G, const Band& B, const AdjState& A, int u, int k)
+{
+    const int per = G.M * G.M - 1, c = u - (B.n_unk - 4);
+    double v = 0.0;
+    for (int q = 0; q < per; ++q) v += A.cpart[(c * 4 + k) * per + q];
+    return v;
 }
 
 // Stage `stage` (0, 1, 2) of step t recomputed: Y[stage + 1] = U_b(t) + h k;
 // stage 0 also freezes the viscous vector and the incoming waves.
 template <int LAT, typename S>
-__device__ __forceinline__ void adj_fwd_item(const Geom& G, const Band& B, const AdjState& A,
+__device__ __forceinline__ void adj_fwd_item(const Geom& G, const Band& B, const AdjState& A, const StageSet& Z,
                                              const RT<S>* __restrict__ stU, const RT<S>* __restrict__ stN,
                                              const RT<S>* __restrict__ stU1, int stage, int u)
 {
@@ -306,12 +360,12 @@ __device__ __forceinline__ void adj_fwd_item(const Geom& G, const Band& B, const
     if (u >= B.n_unk) return;
     const UDesc D = B.ud[u];
     CtxT<R> X;
-    X.Y = static_cast<const R*>(A.Y[stage]);
+    X.Y = static_cast<const R*>(Z.Y[stage]);
     X.St = stU;
     X.St1 = stU1;
     X.frac = stage == 0 ? R(0) : R(0.5);
     R V[4] = {R(0), R(0), R(0), R(0)};
-    R* Vu = static_cast<R*>(A.V) + 4LL * u;
+    R* Vu = static_cast<R*>(Z.V) + 4LL * u;
     int mk;
     if (stage == 0) {
         if (B.viscous != VIS_OFF && D.kind < 4) {
@@ -323,11 +377,11 @@ __device__ __forceinline__ void adj_fwd_item(const Geom& G, const Band& B, const
         R Ul[4];
         to_local(D.kind, R(B.kR), X.Y + 4LL * u, Ul);
         mk = incoming_mask<Lt::THERMAL>(char_sys<Lt::THERMAL>(B, G.rho0, Ul));
-        A.mask[u] = mk;
+        Z.mask[u] = mk;
     } else {
 #pragma unroll
         for (int m = 0; m < 4; ++m) V[m] = Vu[m];
-        mk = A.mask[u];
+        mk = Z.mask[u];
     }
     Relax<R> P;
     P.alpha_T = relax_value<R>(A, 0);
@@ -339,9 +393,9 @@ __device__ __forceinline__ void adj_fwd_item(const Geom& G, const Band& B, const
     R k[4];
     unknown_rhs<LAT, R>(G, B, P, X, D, u, V, mk, k);
     const R h = stage == 2 ? R(1) : R(0.5);
-    R* Yo = static_cast<R*>(A.Y[stage + 1]) + 4LL * u;
+    R* Yo = static_cast<R*>(Z.Y[stage + 1]) + 4LL * u;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) Yo[m] = static_cast<const R*>(A.Y[0])[4LL * u + m] + h * k[m];
+    for (int m = 0; m < 4; ++m) Yo[m] = static_cast<const R*>(Z.Y[0])[4LL * u + m] + h * k[m];
 }
 
 // lambda of one strip macro or stage value: the stage field at a reference
@@ -448,10 +502,17 @@ __device__ __forceinline__ void adj_vjp_item(const Geom& G, const Band& B, const
         const R cs = (stage == 0 || stage == 3) ? R(1.0 / 6.0) : R(1.0 / 3.0);
         const R ch = stage == 2 ? R(1) : R(0.5);
         R lk[4];
-        const R* lUr = static_cast<const R*>(A.lUr) + 4LL * u;
+        R* lUr = static_cast<R*>(A.lUr) + 4LL * u;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            lk[m] = cs * lUr[m];
+            R lu = lUr[m];
+            if (stage == 3 && corner && G.M > 1) {
+                // the corner block's other nodes (adj_corner_item) join here;
+                // the stages after this one read the rounded sum
+                lu = R(A.lU[4LL * u + m] + corner_share(G, B, A, u, m));
+                if (c == 0) lUr[m] = lu;
+            }
+            lk[m] = cs * lu;
             if (stage < 3) lk[m] += ch * static_cast<const R*>(A.lY[stage + 1])[4LL * u + m];
         }
         R* lY = static_cast<R*>(A.lY[stage]);
@@ -620,6 +681,7 @@ __device__ __forceinline__ void adj_extras_item(const Geom& G, const Export& E, 
             double sum = 0.0;
 #pragma unroll
             for (int r = 0; r < 4; ++r) sum += double(static_cast<const R*>(A.lY[r])[4LL * q + m]);
+            if (q >= B.n_unk - 4 && B.ud[q].kind >= 4 && G.M > 1) sum += corner_share(G, B, A, q, m);
             const double v = A.lU[4LL * q + m] + sum;
             A.lU[4LL * q + m] = v;
             static_cast<R*>(A.lUr)[4LL * q + m] = R(v);
@@ -675,33 +737,62 @@ __device__ __forceinline__ void adj_extras_item(const Geom& G, const Export& E, 
 // The boundary part of one reverse step in one cooperative launch (its CTAs
 // all resident): the phases above in order, each over all its items
 // (thread-strided), separated by grid-wide barriers -- the Dirichlet write's
-// adjoint (and the stage adjoints zeroed), the three stage fields, the four
-// stages backwards, the viscous vector, then lambda_U(t) and the strips'
-// shares.  The parameter sums of the stages are reduced per block at the end.
+// adjoint (and the stage adjoints zeroed), the three stage fields unless the
+// previous reverse step computed them (`pre`), the four stages backwards,
+// the viscous vector, then lambda_U(t) and the strips' shares.  Beside the
+// first three stage phases (items after the stage adjoint's) run the three
+// stage fields of step t - 1 into the other stage set Zn (`nxt`), from
+// U_b(t - 1) = Ubm and the strips of t - 1 and t; they depend on nothing the
+// adjoint computes.  The parameter sums of the stages are reduced per block
+// at the end.
 template <int LAT, typename S>
-__global__ void __launch_bounds__(kAdjThreads)
-    k_adj_band(Geom G, Export E, Band B, AdjState A, const double* __restrict__ Ub, const double* __restrict__ Ub1,
-               const CT<S>* __restrict__ lnext, const RT<S>* __restrict__ stU, const RT<S>* __restrict__ stN,
-               const RT<S>* __restrict__ stU1, int par)
+__global__ void __launch_bounds__(kBandThreads, 2)
+    k_adj_band(Geom G, Export E, Band B, AdjState A, StageSet Zn, const double* __restrict__ Ub,
+               const double* __restrict__ Ub1, const double* __restrict__ Ubm, const CT<S>* __restrict__ lnext,
+               const RT<S>* __restrict__ stU, const RT<S>* __restrict__ stN, const RT<S>* __restrict__ stU1,
+               const RT<S>* __restrict__ stUm, const RT<S>* __restrict__ stNm, int par, int pre, int nxt)
 {
     using R = RT<S>;
     cg::grid_group grid = cg::this_grid();
     const int nth = int(gridDim.x * blockDim.x), t0 = int(blockIdx.x * blockDim.x + threadIdx.x);
     const int nu = B.n_unk;
-    for (int i = t0; i < 4 * nu; i += nth)
-        adj_dirichlet_item<LAT, S>(G, B, Ub, Ub1, lnext, A.lU, static_cast<R*>(A.lUr), static_cast<R*>(A.Y[0]), i);
+    StageSet Z;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Z.Y[q] = A.Y[q];
+    Z.V = A.V;
+    Z.mask = A.mask;
+    // the corner unknowns, if any, are the last four
+    const int ncp = (nu >= 4 && B.ud[nu - 4].kind == 4) ? 16 * (G.M * G.M - 1) : 0;
+    for (int i = t0; i < 4 * nu + ncp; i += nth) {
+        if (i < 4 * nu) {
+            if (nxt && (i & 3) == 1) {
+                R* y = static_cast<R*>(Zn.Y[0]) + 4LL * (i >> 2);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) y[m] = R(Ubm[4LL * (i >> 2) + m]);
+            }
+            adj_dirichlet_item<LAT, S>(G, B, Ub, Ub1, lnext, A.lU, static_cast<R*>(A.lUr), static_cast<R*>(A.Y[0]), i);
+        } else {
+            adj_corner_item<LAT, S>(G, B, A, Ub1, lnext, i - 4 * nu);
+        }
+    }
     {
         R* z = static_cast<R*>(A.lY[0]);     // lY[0..3] and lV, contiguous
         for (long long i = t0; i < 20LL * nu; i += nth) z[i] = R(0);
     }
     grid.sync();
-    for (int s = 0; s < 3; ++s) {
-        for (int u = t0; u < nu; u += nth) adj_fwd_item<LAT, S>(G, B, A, stU, stN, stU1, s, u);
-        grid.sync();
+    if (!pre) {
+        for (int s = 0; s < 3; ++s) {
+            for (int u = t0; u < nu; u += nth) adj_fwd_item<LAT, S>(G, B, A, Z, stU, stN, stU1, s, u);
+            grid.sync();
+        }
     }
     double th[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int s = 3; s >= 0; --s) {
-        for (int i = t0; i < nu * kRhsChunks; i += nth) adj_vjp_item<LAT, S>(G, B, A, stU, stU1, s, i, th);
+        const int nv = nu * kRhsChunks, nf = (nxt && s > 0) ? nu : 0;
+        for (int i = t0; i < nv + nf; i += nth) {
+            if (i < nv) adj_vjp_item<LAT, S>(G, B, A, stU, stU1, s, i, th);
+            else adj_fwd_item<LAT, S>(G, B, A, Zn, stUm, stNm, stU, 3 - s, i - nv);
+        }
         grid.sync();
     }
     if (B.viscous == VIS_MESO) {
@@ -712,7 +803,7 @@ __global__ void __launch_bounds__(kAdjThreads)
     grid.sync();
     const int nq = nu > E.nslots ? nu : E.nslots;
     for (int q = t0; q < nq; q += nth) adj_extras_item<LAT, S>(G, E, B, A, stU, stN, par, q);
-    block_sum<5>(th, A.sums + 1);
+    block_sum<5, kBandThreads>(th, A.sums + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -846,26 +937,57 @@ __global__ void __launch_bounds__(kAdjThreads)
 
 template <int LAT, typename S>
 int adj_loss_t(const Geom& G, const Region& bulk, const void* f, const double* dPref, double* sums, void* Mout,
-               cudaStream_t st)
+               const AdjRecord& rec, cudaStream_t st)
 {
-    if (bulk.x1 <= bulk.x0 || bulk.y1 <= bulk.y0) return 0;
-    dim3 grd((bulk.x1 - bulk.x0 + kAdjThreads - 1) / kAdjThreads, bulk.y1 - bulk.y0);
+    // one block at least: the record is copied even without bulk nodes
+    dim3 grd(std::max(1, (bulk.x1 - bulk.x0 + kAdjThreads - 1) / kAdjThreads), std::max(1, bulk.y1 - bulk.y0));
     k_adj_loss<LAT, S><<<grd, kAdjThreads, 0, st>>>(G, bulk, static_cast<const S*>(f), dPref, sums,
-                                                    static_cast<RT<S>*>(Mout));
+                                                    static_cast<RT<S>*>(Mout), rec);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// The populations the Dirichlet write of a step set, from the recorded
+// boundary state U_b(t + 1): thread u writes unknown u's nodes exactly as the
+// band kernel does (dirichlet(), equilibrium form, the state rounded to the
+// strip type first).
+template <int LAT, typename S>
+__global__ void k_adj_dwrite(Geom G, Band B, const double* __restrict__ Ub1, S* __restrict__ f)
+{
+    using R = RT<S>;
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= B.n_unk) return;
+    const R Unew[4] = {R(Ub1[4LL * u]), R(Ub1[4LL * u + 1]), R(Ub1[4LL * u + 2]), R(Ub1[4LL * u + 3])};
+    dirichlet<LAT, S, R>(G, B, f, nullptr, nullptr, B.ud[u], Unew);
+}
+
+template <int LAT, typename S>
+int adj_dwrite_t(const Geom& G, const Band& B, const double* Ub1, void* f, cudaStream_t st)
+{
+    if (B.n_unk <= 0) return 0;
+    k_adj_dwrite<LAT, S><<<(B.n_unk + kAdjThreads - 1) / kAdjThreads, kAdjThreads, 0, st>>>(G, B, Ub1,
+                                                                                             static_cast<S*>(f));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <int LAT, typename S>
-int adj_step_t(const Geom& G, const Export& E, const Band& B, const Region& bulk, const AdjState& A,
+int adj_step_t(const Geom& G, const Export& E, const Band& B, const Region& bulk, const AdjState& A0,
                const double* Ub, const double* Ub1, const void* stU_, const void* stN_, const void* stU1_,
-               const void* Mh1_, const double* dPref1, int par, cudaStream_t st, cudaStream_t sw,
-               cudaEvent_t ev_bulk)
+               const void* Mh1_, const double* dPref1, int par, int set, int pre, int nxt, const double* Ubm,
+               const void* stUm_, const void* stNm_, cudaStream_t st, cudaStream_t sw, cudaEvent_t ev_bulk)
 {
     using R = RT<S>;
     using C = CT<S>;
+    AdjState A = A0;        // the current stage set
+#pragma unroll
+    for (int q = 0; q < 4; ++q) A.Y[q] = A0.sets[set].Y[q];
+    A.V = A0.sets[set].V;
+    A.mask = A0.sets[set].mask;
+    StageSet Zn = A0.sets[set ^ 1];
     const R* stU = static_cast<const R*>(stU_);
     const R* stN = static_cast<const R*>(stN_);
     const R* stU1 = static_cast<const R*>(stU1_);
+    const R* stUm = static_cast<const R*>(stUm_);
+    const R* stNm = static_cast<const R*>(stNm_);
     const R* Mh1 = static_cast<const R*>(Mh1_);
     const C* lnext = static_cast<const C*>(A.lpre[par]);      // lambda^pre_{t+2}
     C* lcur = static_cast<C*>(A.lpre[par ^ 1]);               // lambda^pre_{t+1}
@@ -883,16 +1005,19 @@ int adj_step_t(const Geom& G, const Export& E, const Band& B, const Region& bulk
             int per_sm = 0, sms = 0, dev = 0;
             if (cudaGetDevice(&dev) != cudaSuccess ||
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_band<LAT, S>, kAdjThreads, 0) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_band<LAT, S>, kBandThreads, 0) != cudaSuccess ||
                 per_sm < 1)
                 return -1;
+            // two CTAs per SM at most: more measured slower (longer grid
+            // barriers, less room for the kernels on the other streams)
             grid_ctas = std::min(per_sm, 2) * sms;
         }
         const double* a_Ub = Ub;
         const double* a_Ub1 = Ub1;
-        void* args[] = {const_cast<Geom*>(&G), const_cast<Export*>(&E), const_cast<Band*>(&B),
-                        const_cast<AdjState*>(&A), &a_Ub, &a_Ub1, &lnext, &stU, &stN, &stU1, &par};
-        if (cudaLaunchCooperativeKernel((const void*)k_adj_band<LAT, S>, dim3(grid_ctas), dim3(kAdjThreads), args, 0,
+        const double* a_Ubm = Ubm;
+        void* args[] = {const_cast<Geom*>(&G), const_cast<Export*>(&E), const_cast<Band*>(&B), &A, &Zn,
+                        &a_Ub, &a_Ub1, &a_Ubm, &lnext, &stU, &stN, &stU1, &stUm, &stNm, &par, &pre, &nxt};
+        if (cudaLaunchCooperativeKernel((const void*)k_adj_band<LAT, S>, dim3(grid_ctas), dim3(kBandThreads), args, 0,
                                         st) != cudaSuccess)
             return -1;
     }
@@ -919,9 +1044,17 @@ int adj_step_t(const Geom& G, const Export& E, const Band& B, const Region& bulk
 }  // namespace
 
 int launch_adj_loss(int lat, int storage, const Geom& G, const Region& bulk, const void* f,
-                    const double* dPref, double* sums, void* Mout, cudaStream_t st)
+                    const double* dPref, double* sums, void* Mout, const AdjRecord& rec, cudaStream_t st)
 {
-#define CALL(L, S) adj_loss_t<L, S>(G, bulk, f, dPref, sums, Mout, st)
+#define CALL(L, S) adj_loss_t<L, S>(G, bulk, f, dPref, sums, Mout, rec, st)
+    ADJ_DISPATCH(lat, storage, CALL);
+#undef CALL
+}
+
+int launch_adj_dwrite(int lat, int storage, const Geom& G, const Band& B, const double* Ub1, void* f,
+                      cudaStream_t st)
+{
+#define CALL(L, S) adj_dwrite_t<L, S>(G, B, Ub1, f, st)
     ADJ_DISPATCH(lat, storage, CALL);
 #undef CALL
 }
@@ -929,9 +1062,12 @@ int launch_adj_loss(int lat, int storage, const Geom& G, const Region& bulk, con
 int launch_adj_step(int lat, int storage, const Geom& G, const Export& E, const Band& B,
                     const Region& bulk, const AdjState& A, const double* Ub, const double* Ub1,
                     const void* stU, const void* stN, const void* stU1, const void* Mh1,
-                    const double* dPref1, int par, cudaStream_t st, cudaStream_t sw, cudaEvent_t ev_bulk)
+                    const double* dPref1, int par, int set, int pre, int nxt, const double* Ubm,
+                    const void* stUm, const void* stNm, cudaStream_t st, cudaStream_t sw, cudaEvent_t ev_bulk)
 {
-#define CALL(L, S) adj_step_t<L, S>(G, E, B, bulk, A, Ub, Ub1, stU, stN, stU1, Mh1, dPref1, par, st, sw, ev_bulk)
+#define CALL(L, S)                                                                                              \
+    adj_step_t<L, S>(G, E, B, bulk, A, Ub, Ub1, stU, stN, stU1, Mh1, dPref1, par, set, pre, nxt, Ubm, stUm, stNm, \
+                     st, sw, ev_bulk)
     ADJ_DISPATCH(lat, storage, CALL);
 #undef CALL
 }

@@ -1338,20 +1338,16 @@ int adj_copy_state(lbm_handle* h, int idx, bool save)
     return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, save ? "checkpoint" : "checkpoint restore");
 }
 
-// History buffer b (0 or 1) of the adjoint state: the same layout at an offset.
+// Bulk-macro history buffer b (0 or 1) of the adjoint state.
 AdjState adj_hist(const lbm_handle* h, int b)
 {
     AdjState A = h->adj;
-    const size_t o = (size_t)b * h->adj_hist_bytes;
-    A.Mh = static_cast<char*>(A.Mh) + o;
-    A.Ubh = reinterpret_cast<double*>(reinterpret_cast<char*>(A.Ubh) + o);
-    A.stUh = static_cast<char*>(A.stUh) + o;
-    A.stNh = static_cast<char*>(A.stNh) + o;
+    A.Mh = static_cast<char*>(A.Mh) + (size_t)b * h->adj_hist_bytes;
     return A;
 }
 
-// The boundary state and the strips of the current time into slot k of
-// history buffer A.
+// The boundary state and the strips of the current time into slot k (the
+// step index within the run) of the history.
 int adj_snapshot(lbm_handle* h, const AdjState& A, int k)
 {
     const int par = int(h->steps & 1);
@@ -1402,17 +1398,20 @@ int lbm_adj_begin(lbm_handle* h, int checkpoint_every, int max_steps)
     h->adj_ckpt_bytes = adj_ckpt_layout(h, &o_su, &o_sn, &o_ub);
     size_t o = 0;
     auto take = [&](size_t b) { const size_t at = o; o = align_up(o + b); return at; };
-    // two history buffers of the same layout (the recompute of one segment
-    // runs beside the reverse steps of the next)
-    const size_t o_mh = take((size_t)K * 4 * N * es), o_ubh = take((size_t)(K + 1) * nu * 32),
-                 o_suh = take((size_t)(K + 1) * ns * 4 * es), o_snh = take((size_t)(K + 1) * ns * 5 * es);
+    // the bulk macros of a segment in two buffers (the recompute of one
+    // segment runs beside the reverse steps of the next); the boundary state
+    // and the strips of every step of the run, recorded by the forward pass
+    const size_t o_mh = take((size_t)K * 4 * N * es);
     h->adj_hist_bytes = o;
     o += h->adj_hist_bytes;
+    const size_t o_ubh = take((size_t)(max_steps + 1) * nu * 32),
+                 o_suh = take((size_t)(max_steps + 1) * ns * 4 * es),
+                 o_snh = take((size_t)(max_steps + 1) * ns * 5 * es);
     const size_t o_l0 = take(h->f_bytes), o_l1 = take(h->f_bytes), o_lu = take(nu * 32), o_lur = take(nu * 4 * es),
-                 o_y = take(4 * nu * 4 * es), o_ly = take(5 * nu * 4 * es),   // lY[0..3], then lV
-                 o_v = take(nu * 4 * es), o_mask = take(nu * sizeof(int)), o_lst = take(ns * 4 * es),
+                 o_y = take(2 * 4 * nu * 4 * es), o_ly = take(5 * nu * 4 * es),   // lY[0..3], then lV
+                 o_v = take(2 * nu * 4 * es), o_mask = take(2 * nu * sizeof(int)), o_lst = take(ns * 4 * es),
                  o_lst1 = take(ns * 4 * es), o_ln = take(ns * 5 * es), o_e0 = take(ns * 9 * es),
-                 o_e1 = take(ns * 9 * es), o_sums = take(8 * sizeof(double)),
+                 o_e1 = take(ns * 9 * es), o_sums = take(8 * sizeof(double)), o_cp = take(16 * 9 * sizeof(double)),
                  o_ck = take((size_t)nckpt * h->adj_ckpt_bytes);
     void* mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, o);
@@ -1434,19 +1433,25 @@ int lbm_adj_begin(lbm_handle* h, int checkpoint_every, int max_steps)
         A.relax_d[q] = rl[q];
         A.relax_f[q] = float(rl[q]);
     }
+    for (int b = 0; b < 2; ++b) {
+        for (int q = 0; q < 4; ++q) A.sets[b].Y[q] = at<char>(mem, o_y + (b * 4 + q) * nu * 4 * es);
+        A.sets[b].V = at<char>(mem, o_v + b * nu * 4 * es);
+        A.sets[b].mask = at<int>(mem, o_mask + b * nu * sizeof(int));
+    }
     for (int q = 0; q < 4; ++q) {
-        A.Y[q] = at<char>(mem, o_y + q * nu * 4 * es);
+        A.Y[q] = A.sets[0].Y[q];
         A.lY[q] = at<char>(mem, o_ly + q * nu * 4 * es);
     }
     A.lV = at<char>(mem, o_ly + 4 * nu * 4 * es);
-    A.V = at<char>(mem, o_v);
-    A.mask = at<int>(mem, o_mask);
+    A.V = A.sets[0].V;
+    A.mask = A.sets[0].mask;
     A.lSt = at<char>(mem, o_lst);
     A.lSt1 = at<char>(mem, o_lst1);
     A.lN = at<char>(mem, o_ln);
     A.ext[0] = at<char>(mem, o_e0);
     A.ext[1] = at<char>(mem, o_e1);
     A.sums = at<double>(mem, o_sums);
+    A.cpart = at<double>(mem, o_cp);
     h->adj_ckpt = at<char>(mem, o_ck);
     h->adj_mem = mem;
     h->adj_max = max_steps;
@@ -1469,13 +1474,22 @@ int lbm_adj_forward(lbm_handle* h, int n, const double* dP_ref, long long ref_st
     cudaError_t e = cudaMemsetAsync(h->adj.sums, 0, 8 * sizeof(double), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "loss reset");
     h->adj_start = h->steps;
+    const size_t nu = (size_t)h->B.n_unk, ns = (size_t)h->E.nslots, es = h->E.sesize;
     int rc = adj_copy_state(h, 0, true);
+    if (rc == LBM_OK) rc = adj_snapshot(h, h->adj, 0);
     for (int i = 0; i < n && rc == LBM_OK; ++i) {
         if (i > 0 && i % K == 0) rc = adj_copy_state(h, i / K, true);
         if (rc == LBM_OK) rc = lbm_step(h, 1);
+        // the loss after step i, and the boundary history of that time
+        const int par = int(h->steps & 1);
+        AdjRecord rec{h->B.Ub + par * nu * 4, h->adj.Ubh + (size_t)(i + 1) * nu * 4, (long long)(nu * 4),
+                      static_cast<char*>(h->E.stripU) + par * ns * 4 * es,
+                      static_cast<char*>(h->adj.stUh) + (size_t)(i + 1) * ns * 4 * es, (long long)(ns * 4),
+                      static_cast<char*>(h->E.stripN) + par * ns * 5 * es,
+                      static_cast<char*>(h->adj.stNh) + (size_t)(i + 1) * ns * 5 * es, (long long)(ns * 5)};
         if (rc == LBM_OK &&
-            launch_adj_loss(h->lattice, h->storage, h->G, h->bulk, h->f[h->steps & 1],
-                            dP_ref ? dP_ref + (long long)i * ref_stride : nullptr, h->adj.sums, nullptr,
+            launch_adj_loss(h->lattice, h->storage, h->G, h->bulk, h->f[par],
+                            dP_ref ? dP_ref + (long long)i * ref_stride : nullptr, h->adj.sums, nullptr, rec,
                             h->stream))
             rc = check_launch(h, -1, "loss kernel");
     }
@@ -1514,21 +1528,30 @@ int lbm_adj_backward(lbm_handle* h, double* dJ)
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sv, ev_step, 0);
     if (e != cudaSuccess) return cuda_fail(h, e, "adjoint streams");
     const size_t ub = nu * 4, su = ns * 4 * es, sn = ns * 5 * es;
-    // Recompute segment seg into history buffer seg & 1 (on the handle's
-    // stream, with ordinary steps), keeping what the reverse steps read.
+    // Recompute the populations of segment seg from its checkpoint (on the
+    // handle's stream) and keep the bulk macros of every step in history
+    // buffer seg & 1: the bulk kernel of the ordinary step, then the
+    // Dirichlet write from the recorded boundary state (the boundary ODE is
+    // not solved again: its states and strips were recorded by the forward
+    // pass).
     auto recompute = [&](int seg) -> int {
         const AdjState H = adj_hist(h, seg & 1);
         const int L = std::min(K, n - seg * K);
         h->steps = h->adj_start + (long long)seg * K;
         int rc = adj_copy_state(h, seg, false);
         for (int k = 0; k < L && rc == LBM_OK; ++k) {
-            rc = adj_snapshot(h, H, k);
-            if (rc == LBM_OK) rc = lbm_step(h, 1);
-            if (rc == LBM_OK && launch_adj_loss(h->lattice, h->storage, h->G, h->bulk, h->f[h->steps & 1], nullptr,
-                                                nullptr, static_cast<char*>(H.Mh) + (size_t)k * 4 * N * es, sr))
+            const int par = int(h->steps & 1);
+            rc = bulk(h, par, sr);
+            if (rc == LBM_OK &&
+                launch_adj_dwrite(h->lattice, h->storage, h->G, h->B, A.Ubh + (size_t)(seg * K + k + 1) * nu * 4,
+                                  h->f[par ^ 1], sr))
+                rc = check_launch(h, -1, "Dirichlet write");
+            if (rc == LBM_OK && launch_adj_loss(h->lattice, h->storage, h->G, h->bulk, h->f[par ^ 1], nullptr,
+                                                nullptr, static_cast<char*>(H.Mh) + (size_t)k * 4 * N * es,
+                                                AdjRecord{}, sr))
                 rc = check_launch(h, -1, "macros kernel");
+            h->steps++;
         }
-        if (rc == LBM_OK) rc = adj_snapshot(h, H, L);
         return rc;
     };
     int rc = recompute(nseg - 1);
@@ -1542,15 +1565,21 @@ int lbm_adj_backward(lbm_handle* h, double* dJ)
         const int L = std::min(K, n - seg * K);
         for (int k = L - 1; k >= 0 && rc == LBM_OK; --k) {
             const long long t = t0 + k;
+            const size_t r = (size_t)seg * K + k;      // the step within the run
             const double* ref = h->adj_ref ? h->adj_ref + (t - h->adj_start) * h->adj_ref_stride : nullptr;
             e = cudaEventRecord(ev_step, sv);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(sw, ev_step, 0);
             if (e != cudaSuccess) { rc = cuda_fail(h, e, "adjoint streams"); break; }
-            if (launch_adj_step(h->lattice, h->storage, h->G, h->E, h->B, h->bulk, A, H.Ubh + (size_t)k * ub,
-                                H.Ubh + (size_t)(k + 1) * ub, static_cast<char*>(H.stUh) + (size_t)k * su,
-                                static_cast<char*>(H.stNh) + (size_t)k * sn,
-                                static_cast<char*>(H.stUh) + (size_t)(k + 1) * su,
-                                static_cast<char*>(H.Mh) + (size_t)k * 4 * N * es, ref, int(t & 1), sv, sw, ev_bulk))
+            // the stage fields of step r were computed by the reverse step of
+            // r + 1 unless r is the last step; those of r - 1 are computed now
+            const int pre = r + 1 < (size_t)n, nxt = r > 0;
+            const size_t rm = nxt ? r - 1 : r;
+            if (launch_adj_step(h->lattice, h->storage, h->G, h->E, h->B, h->bulk, A, A.Ubh + r * ub,
+                                A.Ubh + (r + 1) * ub, static_cast<char*>(A.stUh) + r * su,
+                                static_cast<char*>(A.stNh) + r * sn, static_cast<char*>(A.stUh) + (r + 1) * su,
+                                static_cast<char*>(H.Mh) + (size_t)k * 4 * N * es, ref, int(t & 1), int(r & 1),
+                                pre, nxt, A.Ubh + rm * ub, static_cast<char*>(A.stUh) + rm * su,
+                                static_cast<char*>(A.stNh) + rm * sn, sv, sw, ev_bulk))
                 rc = check_launch(h, -1, "reverse step");
         }
         // meanwhile the previous segment's recompute, into the other buffer

@@ -426,4 +426,92 @@ __device__ void unknown_rhs(const Geom& G, const Band& B, const Relax<T>& P, con
     to_lab(kind, r, kl, k);
 }
 
+// Mesoscopic Dirichlet condition for the new boundary state, stored
+// post-collision: f^eq(Unew) and, for Eq. NEEP, the non-equilibrium part of
+// the bulk neighbour after its collision, f*(x_f) - f^eq(U(x_f, t+1)), or
+// (dirichlet 2) that part projected onto the Hermite polynomials of orders 2
+// and 3 (a regularised scheme, named by the paper as future work).
+// Computed in the arithmetic type of the storage.
+template <int LAT, typename S, typename R>
+__device__ void dirichlet(const Geom& G, const Band& B, S* f, const R* Us, const S* fsrc,
+                          const UDesc& D, const R* Unew)
+{
+    // Us: macros of x_f at t + 1; fsrc: its stored post-collision
+    // populations, indexed by velocity (both read only for Eq. NEEP)
+    using L = Lat<LAT>;
+    using Cm = typename Store<S>::C;
+    Moments<LAT, Cm> m;
+    m.s0 = Cm(Unew[0]);
+    m.rho = Cm(G.rho0) + m.s0;
+    m.ux = Cm(Unew[1]);
+    m.uy = Cm(Unew[2]);
+    m.dT = L::THERMAL ? Cm(Unew[3]) : Cm(0);
+    Cm ge[L::Q];
+    equilibrium<LAT, Cm>(m, ge);
+    if (B.dirichlet >= 1) {             // Eq. NEEP, or its regularised form
+        Moments<LAT, Cm> ms;
+        ms.s0 = Cm(Us[0]);
+        ms.rho = Cm(G.rho0) + ms.s0;
+        ms.ux = Cm(Us[1]);
+        ms.uy = Cm(Us[2]);
+        ms.dT = L::THERMAL ? Cm(Us[3]) : Cm(0);
+        Cm gs[L::Q];
+        equilibrium<LAT, Cm>(ms, gs);
+        Cm gn[L::Q];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            Cm v = Cm(Store<S>::value(fsrc[i]));     // fsrc is in shared memory
+            if (Store<S>::SCALED) v *= Cm(L::w(i));
+            gn[i] = v - gs[i];
+        }
+        if (B.dirichlet == 2) {
+            // Regularised form: the Hermite projection of f^neq onto orders 2
+            // (and 3 on the thermal lattices),
+            // w_i [H2_i : a2 / (2 c_s^4) + H3_i : a3 / (6 c_s^6)], a_n = sum H_n f^neq
+            constexpr Cm cs2 = Cm(L::CS2);
+            Cm a2xx = 0, a2xy = 0, a2yy = 0, a3xxx = 0, a3xxy = 0, a3xyy = 0, a3yyy = 0;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const Cm cx = Cm(L::cx(i)), cy = Cm(L::cy(i));
+                a2xx += (cx * cx - cs2) * gn[i];
+                a2xy += cx * cy * gn[i];
+                a2yy += (cy * cy - cs2) * gn[i];
+                if (L::ORDER >= 3) {
+                    a3xxx += (cx * cx * cx - Cm(3) * cs2 * cx) * gn[i];
+                    a3xxy += (cx * cx * cy - cs2 * cy) * gn[i];
+                    a3xyy += (cx * cy * cy - cs2 * cx) * gn[i];
+                    a3yyy += (cy * cy * cy - Cm(3) * cs2 * cy) * gn[i];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const Cm cx = Cm(L::cx(i)), cy = Cm(L::cy(i));
+                const Cm h2 = (cx * cx - cs2) * a2xx + Cm(2) * cx * cy * a2xy + (cy * cy - cs2) * a2yy;
+                Cm h = h2 / (Cm(2) * cs2 * cs2);
+                if (L::ORDER >= 3) {
+                    const Cm h3 = (cx * cx * cx - Cm(3) * cs2 * cx) * a3xxx +
+                                  Cm(3) * (cx * cx * cy - cs2 * cy) * a3xxy +
+                                  Cm(3) * (cx * cy * cy - cs2 * cx) * a3xyy +
+                                  (cy * cy * cy - Cm(3) * cs2 * cy) * a3yyy;
+                    h += h3 / (Cm(6) * cs2 * cs2 * cs2);
+                }
+                gn[i] = Cm(L::w(i)) * h;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) ge[i] += gn[i];
+    }
+    const int nb = D.kind >= 4 ? G.M : 1;
+    for (int a = 0; a < nb; ++a)
+        for (int b = 0; b < nb; ++b) {
+            const long long node = D.wnode + a * D.wdx + b * D.wdy;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                Cm v = ge[i];
+                if (Store<S>::SCALED) v *= Cm(1.0 / L::w(i));
+                Store<S>::put(f + L::plane_of(i) * G.plane + node, v);
+            }
+        }
+}
+
 }  // namespace lbmgb

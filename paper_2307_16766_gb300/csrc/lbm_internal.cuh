@@ -694,21 +694,33 @@ int launch_tl_seed(int lat, int storage, const TLState& T, const Geom& G, const 
 // segment (index k = step - first step of the segment) and the adjoint
 // variables; element type C = the storage's arithmetic (populations) and R =
 // StripReal (boundary solver inputs), except where stated.
+// RK4 stage fields of one step at the unknowns, with the viscous vector and
+// the incoming waves frozen at its stage 0.
+struct StageSet {
+    void* Y[4];       // [n_unk][4] (R): Y[0] = U_b(t), Y[s + 1] = U_b(t) + h_s k_s
+    void* V;          // [n_unk][4] (R)
+    int* mask;        // [n_unk]
+};
+
 struct AdjState {
     int K;            // checkpoint interval: steps per segment
     void* Mh;         // [K][ny * nx][4] (R): drho, ux, uy, dT of the bulk nodes after step k
-    double* Ubh;      // [K + 1][n_unk][4]: boundary state before step k
-    void* stUh;       // [K + 1][nslots][4] (R): strip macros of the time before step k
-    void* stNh;       // [K + 1][nslots][5] (R): strip non-equilibrium moments, same time
+                      // of a segment (two buffers: recompute beside the reverse steps)
+    double* Ubh;      // [steps + 1][n_unk][4]: boundary state before step k of the run
+    void* stUh;       // [steps + 1][nslots][4] (R): strip macros of the time before step k
+    void* stNh;       // [steps + 1][nslots][5] (R): strip non-equilibrium moments, same time
     void* lpre[2];    // [Q][plane] (C): adjoint of the pulled (pre-collision) populations,
                       // by parity of their time
     double* lU;       // [n_unk][4]: adjoint of the boundary state
     void* lUr;        // [n_unk][4] (R): its rounding, read by the stage kernels
-    void* Y[4];       // [n_unk][4] (R): RK4 stage fields at the unknowns (Y[0] = U_b(t))
+    StageSet sets[2]; // stage fields by parity of the step index within the run; the
+                      // reverse step of t computes those of t - 1 beside its own adjoint
+    void* Y[4];       // [n_unk][4] (R): RK4 stage fields at the unknowns (Y[0] = U_b(t)),
+                      // the current set's
     void* lY[4];      // [n_unk][4] (R): their adjoints
-    void* V;          // [n_unk][4] (R): viscous vector of the step (frozen)
+    void* V;          // [n_unk][4] (R): viscous vector of the step (frozen), current set
     void* lV;         // [n_unk][4] (R): its adjoint
-    int* mask;        // [n_unk]: incoming waves of the step
+    int* mask;        // [n_unk]: incoming waves of the step, current set
     void* lSt;        // [nslots][4] (R): adjoint of the strip macros of time t
     void* lSt1;       // [nslots][4] (R): adjoint of the strip macros of time t + 1
     void* lN;         // [nslots][5] (R): adjoint of the strip moments of time t
@@ -716,6 +728,7 @@ struct AdjState {
                       // populations of a strip node, by parity of the time: 4 moment
                       // coefficients, 5 weights of the non-equilibrium moments
     double* sums;     // [7]: J, dJ / d(alpha_T, beta_P, P_inf, alpha_V, t_inf), J again
+    double* cpart;    // [4][4][M * M - 1]: corner blocks' Dirichlet shares (one step)
     // alpha_T, beta_P, t_inf, alpha_V, P_inf - c_s^2 rho0 per side, rounded
     // to float and as double (the stage kernels take their arithmetic's)
     float relax_f[8];
@@ -724,18 +737,40 @@ struct AdjState {
 // Loss of the state in f (populations after a step) against dPref (or 0):
 // sums[0] += sum over the bulk nodes of (P - c_s^2 rho0 - dPref)^2 (skipped
 // if sums is null); the bulk nodes' moments into Mout ([ny * nx][4] of the
-// strip type; skipped if null).
+// strip type; skipped if null); it also copies the record rec.
+// A history record copied by the loss kernel beside its work: the boundary
+// state (n_ub doubles) and the strips' macros and moments (n_su, n_sn values
+// of the strip type) of the time the loss is taken at (counts 0: none).
+struct AdjRecord {
+    const double* ub;
+    double* ubh;
+    long long n_ub;
+    const void* su;
+    void* suh;
+    long long n_su;
+    const void* sn;
+    void* snh;
+    long long n_sn;
+};
 int launch_adj_loss(int lat, int storage, const Geom& G, const Region& bulk, const void* f,
-                    const double* dPref, double* sums, void* Mout, cudaStream_t st);
+                    const double* dPref, double* sums, void* Mout, const AdjRecord& rec, cudaStream_t st);
+// The Dirichlet write of a step (equilibrium form) from the boundary state
+// Ub1 ([n_unk][4]) into the populations f.
+int launch_adj_dwrite(int lat, int storage, const Geom& G, const Band& B, const double* Ub1, void* f,
+                      cudaStream_t st);
 // One reverse step for the forward step t -> t + 1 (see adjoint.cu):
 // Ub, Ub1: the boundary state at t and t + 1; stU, stN: strips of t; stU1:
 // strip macros of t + 1; Mh1: macros at t + 1; dPref1: the loss reference at
 // t + 1 (or null); par: parity of t.  The boundary kernels go on st, the
 // bulk kernel on sw (after what sw already waits for), joined on st through
-// ev_bulk before the step's last kernel.
+// ev_bulk before the step's last kernel.  Stage set `set` (the parity of t's
+// index within the run) holds t's stage fields if `pre` (computed by the
+// reverse step of t + 1); with `nxt` this step computes those of t - 1 into
+// the other set from Ubm = U_b(t - 1) and the strips stUm, stNm of t - 1.
 int launch_adj_step(int lat, int storage, const Geom& G, const Export& E, const Band& B,
                     const Region& bulk, const AdjState& A, const double* Ub, const double* Ub1,
                     const void* stU, const void* stN, const void* stU1, const void* Mh1,
-                    const double* dPref1, int par, cudaStream_t st, cudaStream_t sw, cudaEvent_t ev_bulk);
+                    const double* dPref1, int par, int set, int pre, int nxt, const double* Ubm,
+                    const void* stUm, const void* stNm, cudaStream_t st, cudaStream_t sw, cudaEvent_t ev_bulk);
 
 }  // namespace lbmgb
