@@ -138,16 +138,12 @@ template <int LAT, typename S, typename C>
 __device__ __forceinline__ void collide_store(const Geom& G, const Offsets& O, S* __restrict__ fout,
                                               int x, int y, C* g)
 {
-    using L = Lat<LAT>;
-    if (Store<S>::SCALED) {
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) g[i] *= C(L::w(i));
-    }
     S* out = fout + (y * G.nxp + x);
-    collide<LAT, C>(G, g, [&](int i, C v) {
-        if (Store<S>::SCALED) v *= C(1.0 / L::w(i));
-        Store<S>::put(out + O.st[i], v);
-    });
+    if constexpr (Store<S>::SCALED) {
+        collide_scaled<LAT>(G, g, [&](int i, C v) { Store<S>::put(out + O.st[i], v); });
+    } else {
+        collide<LAT, C>(G, g, [&](int i, C v) { Store<S>::put(out + O.st[i], v); });
+    }
 }
 
 // Row segments per CTA of k_bulk: the tensor copies of every row are issued

@@ -186,6 +186,82 @@ __device__ __forceinline__ void collide_given(const Geom& G, const Moments<LAT, 
 
 }
 
+// The same collision for storage that holds h_i = g_i / w_i (FP16), done in
+// those scaled variables so that no population is multiplied by w_i on the
+// way in or divided by it on the way out: the moments are sums of w_i h_i
+// (w_i c_i folded into one constant), and h^eq_i = g^eq_i / w_i =
+// (rho - rho0) + rho (even +- odd) carries no weight.  FP32 arithmetic, with
+// the conserved-moment closure of the FP32 path above (the closure sums take
+// w_i back in).  put(i, value) receives h*_i.
+template <int LAT, typename Put>
+__device__ __forceinline__ void collide_scaled(const Geom& G, const float* h, Put&& put)
+{
+    using L = Lat<LAT>;
+    using C = float;
+    constexpr int Q = L::Q;
+    C s0 = 0, sx = 0, sy = 0, se = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        s0 += C(L::w(i)) * h[i];
+        if (L::cx(i)) sx += C(L::w(i) * L::cx(i)) * h[i];
+        if (L::cy(i)) sy += C(L::w(i) * L::cy(i)) * h[i];
+        if (L::THERMAL && i) se += C(L::w(i) * (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i))) * h[i];
+    }
+    const Moments<LAT, C> m = moments_of_sums<LAT, C>(s0, sx, sy, se, rho0_of<C>(G));
+    constexpr C ics2 = C(1.0 / L::CS2);
+    constexpr C a3 = L::ORDER >= 3 ? C(1.0 / 6.0) : C(0);
+    constexpr C a4 = L::ORDER >= 4 ? C(1.0 / 24.0) : C(0);
+    const C uxs = m.ux * ics2, uys = m.uy * ics2;
+    const EqPoly<C> e = eq_poly<LAT, C>(m.ux * uxs + m.uy * uys, m.dT);
+    const C om = omega_of<C>(G);
+    C M0 = 0, Mx = 0, My = 0, Me = 0;
+#pragma unroll
+    for (int i = 5; i < Q; i += 2) {
+        const int k = L::cls(i);
+        const C xi2 = C(L::c2cls(k)) * ics2;
+        const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
+        const C a1 = e.A1 + e.B1 * xi2;
+        const C a2 = e.A2 + e.B2 * xi2;
+        C p;
+        if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
+        else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
+        else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
+        const C p2 = p * p;
+        const C ev = a0 + p2 * (a2 + p2 * a4);
+        const C od = p * (a1 + p2 * a3);
+        const C hp = m.s0 + m.rho * (ev + od);
+        const C hm = m.s0 + m.rho * (ev - od);
+        const C sum = hp + hm, dif = hp - hm;
+        M0 += C(L::w(i)) * sum;
+        if (L::cx(i)) Mx += C(L::w(i) * L::cx(i)) * dif;
+        if (L::cy(i)) My += C(L::w(i) * L::cy(i)) * dif;
+        if (L::THERMAL) Me += C(L::w(i) * L::c2cls(k)) * sum;
+        put(i, h[i] + om * (hp - h[i]));
+        put(i + 1, h[i + 1] + om * (hm - h[i + 1]));
+    }
+    // |c| = 1 class and the rest velocity close the conserved moments, in
+    // unscaled units, then scaled
+    const C a0 = e.A0 + ics2 * (e.B0 + e.C0 * ics2);
+    const C a2 = e.A2 + e.B2 * ics2;
+    const C px2 = uxs * uxs, py2 = uys * uys;
+    const C ws0 = C(L::w(1)) * m.s0, wr = C(L::w(1)) * m.rho;
+    C ex = ws0 + wr * (a0 + px2 * (a2 + px2 * a4));
+    C ey = ws0 + wr * (a0 + py2 * (a2 + py2 * a4));
+    if (L::THERMAL) {
+        const C d = C(0.25) * (m.se - Me - C(2) * (ex + ey));
+        ex += d;
+        ey += d;
+    }
+    const C ox = C(0.5) * (m.sx - Mx), oy = C(0.5) * (m.sy - My);
+    constexpr C iw1 = C(1.0 / L::w(1));
+    put(1, h[1] + om * ((ex + ox) * iw1 - h[1]));
+    put(2, h[2] + om * ((ex - ox) * iw1 - h[2]));
+    put(3, h[3] + om * ((ey + oy) * iw1 - h[3]));
+    put(4, h[4] + om * ((ey - oy) * iw1 - h[4]));
+    const C geq0 = m.s0 - M0 - C(2) * (ex + ey);
+    put(0, h[0] + om * (geq0 * C(1.0 / L::w(0)) - h[0]));
+}
+
 template <int LAT, typename C, typename Put>
 __device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Put&& put)
 {
