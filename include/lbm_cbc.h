@@ -101,6 +101,14 @@ typedef struct lbm_cbc_params {
                            L_i = T_i + V_i + alpha_T (T_inf - T_i) + alpha_V (0 - V_i)
                            + beta_P (P - P_inf) on incoming waves (an extension; 0 is
                            the paper's equation; other schemes ignore it)            */
+    double u_ref[2];    /* reference velocity of the stored populations: they are held
+                           as f - f^eq(rho0, u_ref, T = 1) instead of f - w rho0, and
+                           every equilibrium is formed as its difference from that one.
+                           Exact for any value (|u_ref| < c_s); a value near the flow's
+                           mean velocity keeps the stored values, and with them the
+                           FP32/FP16 rounding, small.  (0, 0): the plain shift.  Not
+                           supported by the gradient calls or in batches; a saved state
+                           restores only into a solver with the same u_ref.         */
 } lbm_cbc_params;
 
 typedef struct lbm_handle lbm_handle;
@@ -108,7 +116,7 @@ typedef struct lbm_handle lbm_handle;
 /* Fill p with defaults: all sides periodic, CBC-RELAX, mesoscopic viscous
  * terms, equilibrium Dirichlet, alpha_T = beta_P = t_inf = alpha_V = 0,
  * p_inf = rho0 c_s^2 (set per lattice by lbm_create when left at 0),
- * inflow = (1, 0, 0, 1), F32 storage, rho0 = 1. */
+ * inflow = (1, 0, 0, 1), F32 storage, rho0 = 1, u_ref = (0, 0). */
 int lbm_params_default(lbm_cbc_params* p);
 
 /* Bytes of device workspace a configuration needs (for lbm_create_in). */

@@ -43,8 +43,11 @@ class SplitMix64:
 
 def run(lattice, nx, ny, tau, sides=("periodic",) * 4, schemes=("cbc",) * 4,
         viscous="meso", dirichlet="eq", alpha_T=0.0, beta_P=0.0, t_inf=0.0,
-        p_inf=None, inflow=None, rho0=1.0, storage="f64", steps=1, name="", alpha_V=0.0):
-    """A run description understood by both the CUDA binding and the oracle."""
+        p_inf=None, inflow=None, rho0=1.0, storage="f64", steps=1, name="", alpha_V=0.0,
+        u_ref=(0.0, 0.0)):
+    """A run description understood by both the CUDA binding and the oracle
+    (u_ref, the reference velocity of the CUDA path's stored populations, is
+    a storage detail the oracle does not need)."""
     cs2 = CS2[lattice]
     return {
         "name": name, "lattice": lattice, "nx": int(nx), "ny": int(ny),
@@ -54,7 +57,7 @@ def run(lattice, nx, ny, tau, sides=("periodic",) * 4, schemes=("cbc",) * 4,
         "t_inf": float(t_inf), "alpha_V": float(alpha_V),
         "p_inf": list(p_inf) if p_inf is not None else [cs2 * rho0] * 4,
         "inflow": list(inflow) if inflow is not None else [rho0, 0.0, 0.0, 1.0],
-        "storage": storage, "steps": int(steps),
+        "storage": storage, "steps": int(steps), "u_ref": [float(u_ref[0]), float(u_ref[1])],
     }
 
 
@@ -197,17 +200,22 @@ def pulse_d2q37(n=256, alpha_T=0.5, seed=0, steps=2000, storage="f32", tau=0.8,
 
 
 def vortex_d2q37(nx=1024, ny=512, Ma=0.1, steps=20000, storage="f32", tau=0.8,
-                 radius=20.0):
+                 radius=20.0, reference=None):
     """D2Q37 isentropic vortex (strength 0.05 U0, R = 20) convected by a stream
     U0 = Ma c_s: inflow equilibrium on the left, periodic top/bottom,
     CBC-RELAX on the right with alpha_T = Ma, beta_P = 0 (the paper's outlet
-    setting for its vortex benchmark)."""
+    setting for its vortex benchmark).  With `reference` (default: for FP32
+    and FP16 storage) the CUDA path holds its populations relative to the
+    stream's equilibrium (u_ref = (U0, 0))."""
     cs2 = CS2["D2Q37"]
     U0 = Ma * math.sqrt(cs2)
+    if reference is None:
+        reference = storage != "f64"
     cfg = run("D2Q37", nx, ny, tau,
               sides=("inflow", "cbc", "periodic", "periodic"),
               schemes=("cbc_relax",) * 4, alpha_T=Ma, beta_P=0.0,
               inflow=(1.0, U0, 0.0, 1.0), storage=storage, steps=steps,
+              u_ref=(U0, 0.0) if reference else (0.0, 0.0),
               name="D2Q37 %dx%d isentropic vortex Ma=%g, inflow|CBC, periodic y" % (nx, ny, Ma))
     return cfg, isentropic_vortex(nx, ny, "D2Q37", Ma, radius=radius)
 

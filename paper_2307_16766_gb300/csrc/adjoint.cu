@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kAdjThreads)
         const long long node = (long long)y * G.nxp + x;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) g[i] = C(f[L::plane_of(i) * G.plane + node]);
-        const Moments<LAT, C> m = moments<LAT, C>(g, C(G.rho0));
+        const Moments<LAT, C> m = moments_G<LAT, C>(G, g);
         const long long idx = (long long)y * G.nx + x;
         if (Mout) {
             Rt* o = Mout + 4 * idx;

@@ -175,6 +175,13 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
         err = "relaxation parameters must be finite";
         return LBM_ERR_ARG;
     }
+    {
+        const double ur2 = p->u_ref[0] * p->u_ref[0] + p->u_ref[1] * p->u_ref[1];
+        if (!std::isfinite(ur2) || !(ur2 < lattice_cs2(lattice))) {
+            err = "u_ref must be finite and slower than c_s";
+            return LBM_ERR_ARG;
+        }
+    }
     for (int s = 0; s < 4; ++s) {
         if (p->side[s] < 0 || p->side[s] > 3) { err = fmt("unknown kind %d of side %d", p->side[s], s); return LBM_ERR_ARG; }
         if (p->scheme[s] < 0 || p->scheme[s] > 3) { err = fmt("unknown scheme of side %d", s); return LBM_ERR_ARG; }
@@ -235,6 +242,11 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     G.omega_f = float(1.0 / tau);
     G.rho0_f = float(p->rho0);
     G.wait_ns = 1000000000ull;
+    G.ref = p->u_ref[0] != 0.0 || p->u_ref[1] != 0.0;
+    for (int k = 0; k < 2; ++k) {
+        G.uref[k] = p->u_ref[k];
+        G.uref_f[k] = float(p->u_ref[k]);
+    }
     for (int i = 0; i < Q; ++i) {
         const int plane_i = lattice_plane(lattice, i);
         pl.O.st[i] = int(plane_i * G.plane);
@@ -1118,6 +1130,7 @@ struct StateHeader {
     int lattice, nx, ny, storage, n_unk;
     long long steps;
     unsigned long long f_bytes, stripU_n, stripN_n;
+    double u_ref[2];    // the reference the populations are held against
 };
 }  // namespace
 
@@ -1136,9 +1149,11 @@ int lbm_get_state(lbm_handle* h, void* buf, size_t bytes)
     if (!h->initialized || h->bulk_pending) { h->err = "no complete state to save"; return LBM_ERR_STATE; }
     if (h->grad_stale) { h->err = kGradStale; return LBM_ERR_STATE; }
     StateHeader hd{};
-    std::memcpy(hd.magic, "LBMCBC02", 8);
+    std::memcpy(hd.magic, "LBMCBC03", 8);
     hd.lattice = h->lattice; hd.nx = h->nx; hd.ny = h->ny; hd.storage = h->storage; hd.n_unk = h->B.n_unk;
     hd.steps = h->steps; hd.f_bytes = h->f_bytes; hd.stripU_n = 8ull * h->E.nslots; hd.stripN_n = 10ull * h->E.nslots;
+    hd.u_ref[0] = h->G.ref ? h->G.uref[0] : 0.0;
+    hd.u_ref[1] = h->G.ref ? h->G.uref[1] : 0.0;
     char* p = static_cast<char*>(buf);
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
@@ -1164,9 +1179,10 @@ int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes)
     if (bytes < need) { h->err = "state buffer too small"; return LBM_ERR_ARG; }
     StateHeader hd;
     std::memcpy(&hd, buf, sizeof hd);
-    if (std::memcmp(hd.magic, "LBMCBC02", 8) != 0 || hd.lattice != h->lattice || hd.nx != h->nx ||
+    if (std::memcmp(hd.magic, "LBMCBC03", 8) != 0 || hd.lattice != h->lattice || hd.nx != h->nx ||
         hd.ny != h->ny || hd.storage != h->storage || hd.n_unk != h->B.n_unk || hd.f_bytes != h->f_bytes ||
-        hd.stripU_n != 8ull * h->E.nslots || hd.stripN_n != 10ull * h->E.nslots) {
+        hd.stripU_n != 8ull * h->E.nslots || hd.stripN_n != 10ull * h->E.nslots ||
+        hd.u_ref[0] != (h->G.ref ? h->G.uref[0] : 0.0) || hd.u_ref[1] != (h->G.ref ? h->G.uref[1] : 0.0)) {
         h->err = "state was saved from a different configuration";
         return LBM_ERR_ARG;
     }
@@ -1207,6 +1223,7 @@ int lbm_grad_begin_along(lbm_handle* h, const double* dirs)
             if (!std::isfinite(dirs[i])) { h->err = "gradient directions must be finite"; return LBM_ERR_ARG; }
     if (!h->initialized || h->bulk_pending) { h->err = "lbm_grad_begin before a complete step state"; return LBM_ERR_STATE; }
     if (h->tl_mem) { h->err = "gradient steps already begun"; return LBM_ERR_STATE; }
+    if (h->G.ref) { h->err = "gradient steps need u_ref = (0, 0)"; return LBM_ERR_ARG; }
     if (h->storage != LBM_F64 && h->storage != LBM_F32) {
         h->err = "gradient steps need FP64 or FP32 storage";
         return LBM_ERR_ARG;
@@ -1378,6 +1395,7 @@ int lbm_adj_begin(lbm_handle* h, int checkpoint_every, int max_steps)
     if (!h->initialized || h->bulk_pending) { h->err = "lbm_adj_begin before a complete step state"; return LBM_ERR_STATE; }
     if (h->grad_stale || h->tl_mem) { h->err = "tangent-linear gradient steps in use"; return LBM_ERR_STATE; }
     if (h->adj_mem) { h->err = "reverse-mode gradients already begun"; return LBM_ERR_STATE; }
+    if (h->G.ref) { h->err = "reverse-mode gradients need u_ref = (0, 0)"; return LBM_ERR_ARG; }
     if (h->storage != LBM_F64 && h->storage != LBM_F32) {
         h->err = "reverse-mode gradients need FP64 or FP32 storage";
         return LBM_ERR_ARG;
@@ -1869,6 +1887,11 @@ int lbm_batch_create(int n, const int* lattice, const int* nx, const int* ny, co
     b->n = n;
     for (int r = 0; r < n; ++r) {
         lbm_handle* h = nullptr;
+        if (params[r].u_ref[0] != 0.0 || params[r].u_ref[1] != 0.0) {
+            fprintf(stderr, "lbm_batch_create: run %d has u_ref != 0 (batches hold the plain shift)\n", r);
+            batch_release(b);
+            return LBM_ERR_ARG;
+        }
         const int rc = lbm_create(lattice[r], nx[r], ny[r], tau[r], params + r, &h);
         if (rc != LBM_OK) {
             fprintf(stderr, "lbm_batch_create: run %d rejected\n", r);

@@ -232,7 +232,7 @@ __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 //    time t.
 // 3. The owners write U(t + 1) and the mesoscopic Dirichlet populations
 //    (equilibrium or Eq. NEEP), shared out over the four CTAs.
-template <int LAT, typename S>
+template <int LAT, typename S, bool REF>
 __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const Band& B,
                                           const Export& E, const S* __restrict__ fin,
                                           S* __restrict__ f, int par_t, int tile)
@@ -320,12 +320,12 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         Moments<LAT, C> m;
         if (N.fx >= 0) {
             S* fx = Fx + N.fx * L::Q;
-            m = collide<LAT, C>(G, g, [&](int i, C v) {
+            m = collide<LAT, C, REF>(G, g, [&](int i, C v) {
                 if (Store<S>::SCALED) v *= C(1.0 / L::w(i));
                 Store<S>::put(fx + i, v);
             });
         } else {
-            m = moments<LAT, C>(g, rho0_of<C>(G));
+            m = moments_G<LAT, C, REF>(G, g);
         }
         const R U1[4] = {R(m.s0), R(m.ux), R(m.uy), R(m.dT)};
 #pragma unroll
@@ -637,7 +637,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         const R Unew[4] = {Ys[4 * l], Ys[4 * l + 1], Ys[4 * l + 2], Ys[4 * l + 3]};
         const bool neep = B.dirichlet >= 1;     // needs x_f: NEEP or regularised NEEP
         const S* fs = neep ? cl.map_shared_rank(Fx + D.wsrc * L::Q, D.wslot % kCluster) : nullptr;
-        dirichlet<LAT, S, R>(G, B, f, neep ? SUt1 + 4 * D.wslot : nullptr, fs, D, Unew);
+        dirichlet<LAT, S, R, REF>(G, B, f, neep ? SUt1 + 4 * D.wslot : nullptr, fs, D, Unew);
     }
     cl.sync();                          // no CTA leaves while its Fx may be read
 }
@@ -647,12 +647,12 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
 template <typename S>
 constexpr int band_min_blocks() { return sizeof(S) == 8 ? 1 : 4; }
 
-template <int LAT, typename S>
+template <int LAT, typename S, bool REF>
 __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads, band_min_blocks<S>())
     k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
            int par_t)
 {
-    band_tile<LAT, S>(G, O, B, E, fin, f, par_t, blockIdx.x / kCluster);
+    band_tile<LAT, S, REF>(G, O, B, E, fin, f, par_t, blockIdx.x / kCluster);
 }
 
 // Band tiles of many grids in one launch: cluster t takes tile tile_run[t].y
@@ -677,7 +677,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads,
         for (int k = threadIdx.x; k < int(sizeof(BandRun) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
     }
     __syncthreads();
-    band_tile<LAT, S>(R.G, R.O, R.B, R.E, static_cast<const S*>(R.f[par_t]),
+    band_tile<LAT, S, false>(R.G, R.O, R.B, R.E, static_cast<const S*>(R.f[par_t]),
                       static_cast<S*>(R.f[par_t ^ 1]), par_t, tr.y);
 }
 
@@ -705,8 +705,12 @@ int boundary_t(const Geom& G, const Offsets& O, const Export& E, const Band& B, 
 {
     if (B.n_tiles == 0) return 0;
     const size_t smem = band_smem<LAT, S>(B);
-    k_band<LAT, S><<<B.n_tiles * kCluster, kTileThreads, smem, st>>>(
-        G, O, B, E, static_cast<const S*>(fin), static_cast<S*>(fnew), par_t);
+    if (G.ref)
+        k_band<LAT, S, true><<<B.n_tiles * kCluster, kTileThreads, smem, st>>>(
+            G, O, B, E, static_cast<const S*>(fin), static_cast<S*>(fnew), par_t);
+    else
+        k_band<LAT, S, false><<<B.n_tiles * kCluster, kTileThreads, smem, st>>>(
+            G, O, B, E, static_cast<const S*>(fin), static_cast<S*>(fnew), par_t);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -731,8 +735,12 @@ int prepare_t(const Band& B)
 {
     // the 48 KB default covers static + dynamic shared memory: always opt in
     const size_t smem = band_smem<LAT, S>(B);
-    return cudaFuncSetAttribute(k_band<LAT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(smem)) == cudaSuccess ? 0 : -1;
+    return cudaFuncSetAttribute(k_band<LAT, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(smem)) == cudaSuccess &&
+                   cudaFuncSetAttribute(k_band<LAT, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(smem)) == cudaSuccess
+               ? 0
+               : -1;
 }
 
 template <int LAT, typename S>

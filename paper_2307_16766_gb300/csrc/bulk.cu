@@ -134,15 +134,15 @@ __device__ __forceinline__ void gather_staged(C* g, const S* sb, int t,
 
 // Pull-stream result g of node (x, y) -> moments, BGK collision (Eq. bgk)
 // and post-collision store.
-template <int LAT, typename S, typename C>
+template <int LAT, typename S, typename C, bool REF>
 __device__ __forceinline__ void collide_store(const Geom& G, const Offsets& O, S* __restrict__ fout,
                                               int x, int y, C* g)
 {
     S* out = fout + (y * G.nxp + x);
     if constexpr (Store<S>::SCALED) {
-        collide_scaled<LAT>(G, g, [&](int i, C v) { Store<S>::put(out + O.st[i], v); });
+        collide_scaled<LAT, REF>(G, g, [&](int i, C v) { Store<S>::put(out + O.st[i], v); });
     } else {
-        collide<LAT, C>(G, g, [&](int i, C v) { Store<S>::put(out + O.st[i], v); });
+        collide<LAT, C, REF>(G, g, [&](int i, C v) { Store<S>::put(out + O.st[i], v); });
     }
 }
 
@@ -157,10 +157,9 @@ __device__ __forceinline__ void collide_store(const Geom& G, const Offsets& O, S
 template <typename S>
 constexpr int bulk_rows() { return sizeof(S) == 8 ? 1 : 2; }
 
-template <int LAT, typename S>
-__global__ void __launch_bounds__(kBulkThreads)
-    k_bulk(const __grid_constant__ Maps tm, Geom G, Offsets O, Region R,
-           const S* __restrict__ fin, S* __restrict__ fout, int* status)
+template <int LAT, typename S, bool REF>
+__device__ __forceinline__ void bulk_body(const Maps& tm, const Geom& G, const Offsets& O, const Region& R,
+                                          const S* __restrict__ fin, S* __restrict__ fout, int* status)
 {
     constexpr int ROWS = bulk_rows<S>();
     using L = Lat<LAT>;
@@ -218,8 +217,27 @@ __global__ void __launch_bounds__(kBulkThreads)
             if (!valid) continue;
             pull_plain<LAT, S, C>(G, O, fin, x, y, g);
         }
-        collide_store<LAT, S, C>(G, O, fout, x, y, g);
+        collide_store<LAT, S, C, REF>(G, O, fout, x, y, g);
     }
+}
+
+template <int LAT, typename S>
+__global__ void __launch_bounds__(kBulkThreads)
+    k_bulk(const __grid_constant__ Maps tm, Geom G, Offsets O, Region R, const S* __restrict__ fin,
+           S* __restrict__ fout, int* status)
+{
+    bulk_body<LAT, S, false>(tm, G, O, R, fin, fout, status);
+}
+
+// With a reference equilibrium: about twice the equilibrium arithmetic per
+// node (89 registers with FP32 storage; capping them at the plain form's 72
+// spilled and measured slower).
+template <int LAT, typename S>
+__global__ void __launch_bounds__(kBulkThreads)
+    k_bulk_ref(const __grid_constant__ Maps tm, Geom G, Offsets O, Region R, const S* __restrict__ fin,
+               S* __restrict__ fout, int* status)
+{
+    bulk_body<LAT, S, true>(tm, G, O, R, fin, fout, status);
 }
 
 // Persistent form of k_bulk for one or many grids of one lattice and
@@ -328,16 +346,12 @@ __global__ void __launch_bounds__(kBulkThreads)
             break;
         }
         if (valid) {
-            if (Store<S>::SCALED) {
-#pragma unroll
-                for (int i = 0; i < L::Q; ++i) g[i] *= C(L::w(i));
-            }
             S* out = static_cast<S*>(R.f[par ^ 1]) + (cur.y * R.G.nxp + x);
             const int plane = int(R.G.plane);
-            collide<LAT, C>(R.G, g, [&](int i, C v) {
-                if (Store<S>::SCALED) v *= C(1.0 / L::w(i));
-                Store<S>::put(out + L::plane_of(i) * plane, v);
-            });
+            auto put = [&](int i, C v) { Store<S>::put(out + L::plane_of(i) * plane, v); };
+            // runs of a batch hold the plain shift (lbm_batch_create)
+            if constexpr (Store<S>::SCALED) collide_scaled<LAT, false>(R.G, g, put);
+            else collide<LAT, C, false>(R.G, g, put);
         }
         __syncthreads();                    // stage buffer read by all before its reuse
         w = wn;
@@ -380,6 +394,13 @@ __global__ void k_init(Geom G, Export E, const double* __restrict__ rho,
     mc.ux = C(m.ux);
     mc.uy = C(m.uy);
     mc.dT = C(m.dT);
+    if (G.ref) {                        // the deviation from the reference, in FP64
+        mc.ref = 1;
+        mc.Ux = uref_of<C>(G, 0);
+        mc.Uy = uref_of<C>(G, 1);
+        mc.vx = C(m.ux - stored_ref<S>(G, 0));
+        mc.vy = C(m.uy - stored_ref<S>(G, 1));
+    }
     C geq[L::Q];
     equilibrium<LAT, C>(mc, geq);
     S* out = f + (long long)y * G.nxp + x;
@@ -414,12 +435,8 @@ __global__ void k_inflow(Geom G, const int* __restrict__ nodes, int n, double d0
     using L = Lat<LAT>;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    Moments<LAT, double> m;
-    m.s0 = d0;
-    m.rho = G.rho0 + d0;
-    m.ux = d1;
-    m.uy = d2;
-    m.dT = L::THERMAL ? d3 : 0.0;
+    const Moments<LAT, double> m =
+        moments_of_macros<LAT, double>(d0, d1, d2, d3, G.rho0, G.ref, stored_ref<S>(G, 0), stored_ref<S>(G, 1));
     double geq[L::Q];
     equilibrium<LAT, double>(m, geq);
     const long long node = nodes[k];
@@ -467,7 +484,7 @@ __global__ void k_macros(Geom G, const S* __restrict__ f, double* __restrict__ r
         if (Store<S>::SCALED) v *= L::w(i);
         g[i] = v;
     }
-    const Moments<LAT, double> m = moments<LAT, double>(g, G.rho0);
+    const Moments<LAT, double> m = moments<LAT, double>(g, G.rho0, G.ref, stored_ref<S>(G, 0), stored_ref<S>(G, 1));
     const long long n = (long long)y * G.nx + x;
     rho[n] = G.rho0 + m.s0;
     ux[n] = m.ux;
@@ -513,6 +530,9 @@ int bulk_t(const Geom& G, const Offsets& O, const Region& R, const CUtensorMap* 
     tm.m2 = tmaps[3];
     tm.m1 = tmaps[4];
     dim3 blk(kBulkThreads), grd(t1 - t0, (h + ROWS - 1) / ROWS);
+    if (G.ref)
+        return launch_ex(k_bulk_ref<LAT, S>, grd, blk, smem, st, early, tm, G, O, R, static_cast<const S*>(fin),
+                         static_cast<S*>(fout), status);
     return launch_ex(k_bulk<LAT, S>, grd, blk, smem, st, early, tm, G, O, R, static_cast<const S*>(fin),
                      static_cast<S*>(fout), status);
 }

@@ -432,7 +432,7 @@ __device__ void unknown_rhs(const Geom& G, const Band& B, const Relax<T>& P, con
 // (dirichlet 2) that part projected onto the Hermite polynomials of orders 2
 // and 3 (a regularised scheme, named by the paper as future work).
 // Computed in the arithmetic type of the storage.
-template <int LAT, typename S, typename R>
+template <int LAT, typename S, typename R, bool REF = true>
 __device__ void dirichlet(const Geom& G, const Band& B, S* f, const R* Us, const S* fsrc,
                           const UDesc& D, const R* Unew)
 {
@@ -446,6 +446,13 @@ __device__ void dirichlet(const Geom& G, const Band& B, S* f, const R* Us, const
     m.ux = Cm(Unew[1]);
     m.uy = Cm(Unew[2]);
     m.dT = L::THERMAL ? Cm(Unew[3]) : Cm(0);
+    if (REF && G.ref) {
+        m.ref = 1;
+        m.Ux = Cm(stored_ref<S>(G, 0));
+        m.Uy = Cm(stored_ref<S>(G, 1));
+        m.vx = Cm(double(Unew[1]) - stored_ref<S>(G, 0));
+        m.vy = Cm(double(Unew[2]) - stored_ref<S>(G, 1));
+    }
     Cm ge[L::Q];
     equilibrium<LAT, Cm>(m, ge);
     if (B.dirichlet >= 1) {             // Eq. NEEP, or its regularised form
@@ -455,6 +462,13 @@ __device__ void dirichlet(const Geom& G, const Band& B, S* f, const R* Us, const
         ms.ux = Cm(Us[1]);
         ms.uy = Cm(Us[2]);
         ms.dT = L::THERMAL ? Cm(Us[3]) : Cm(0);
+        if (REF && G.ref) {
+            ms.ref = 1;
+            ms.Ux = Cm(stored_ref<S>(G, 0));
+            ms.Uy = Cm(stored_ref<S>(G, 1));
+            ms.vx = Cm(double(Us[1]) - stored_ref<S>(G, 0));
+            ms.vy = Cm(double(Us[2]) - stored_ref<S>(G, 1));
+        }
         Cm gs[L::Q];
         equilibrium<LAT, Cm>(ms, gs);
         Cm gn[L::Q];

@@ -21,6 +21,32 @@ __device__ __forceinline__ C rho0_of(const Geom& G)
     else return C(G.rho0);
 }
 
+// The reference velocity of the stored populations in the precision of C.
+template <typename C>
+__device__ __forceinline__ C uref_of(const Geom& G, int k)
+{
+    if constexpr (sizeof(typename DualTraits<C>::Value) == 4) return C(G.uref_f[k]);
+    else return C(G.uref[k]);
+}
+
+// The reference velocity the populations of storage S are held against, as
+// a double: the value in the storage's arithmetic (float-rounded for FP32
+// and FP16), so that every kernel shifts by the same equilibrium.
+template <typename S>
+__host__ __device__ __forceinline__ double stored_ref(const Geom& G, int k)
+{
+    if constexpr (sizeof(typename Store<S>::C) == 4) return double(G.uref_f[k]);
+    else return G.uref[k];
+}
+
+// Moments of the stored populations g of a node (the grid's reference; REF =
+// false compiles the plain shift only, for kernels instantiated per form).
+template <int LAT, typename C, bool REF = true>
+__device__ __forceinline__ Moments<LAT, C> moments_G(const Geom& G, const C* g)
+{
+    return moments<LAT, C>(g, rho0_of<C>(G), REF ? G.ref : 0, uref_of<C>(G, 0), uref_of<C>(G, 1));
+}
+
 // Viscous stress sigma' = -(1 - 1/(2 tau)) sum c c (f - f^eq) (Eq. LaplaceU)
 // and heat flux q = (1 - 1/(2 tau)) 1/2 sum (f - f^eq) |c-u|^2 (c-u)
 // (Eqs. heatflux, LaplaceT; the equilibrium part of the central third
@@ -98,35 +124,63 @@ __device__ __forceinline__ void collide_given(const Geom& G, const Moments<LAT, 
     constexpr int Q = L::Q;
 
     // BGK collide (Eq. bgk), one opposite pair at a time:
-    // g^eq_{+-} = w (rho - rho0) + w rho (even +- odd) in p = c.u / c_s^2.
+    // g^eq_{+-} = w (rho - rho0) + w rho (even +- odd) in p = c.u / c_s^2,
+    // or, relative to a reference equilibrium (m.ref), w (Ev +- Od) of
+    // eq_pair_ref.
     constexpr C ics2 = C(1.0 / L::CS2);
     constexpr C a3 = L::ORDER >= 3 ? C(1.0 / 6.0) : C(0);
     constexpr C a4 = L::ORDER >= 4 ? C(1.0 / 24.0) : C(0);
     const C uxs = m.ux * ics2, uys = m.uy * ics2;
     const EqPoly<C> e = eq_poly<LAT, C>(m.ux * uxs + m.uy * uys, m.dT);
     const C om = omega_of<C>(G);
+    const bool ref = m.ref != 0;
+    EqDelta<C> de;
+    C rho0r = C(0), Uxs = C(0), Uys = C(0), vxs = C(0), vys = C(0);
+    if (ref) {
+        Uxs = m.Ux * ics2;
+        Uys = m.Uy * ics2;
+        vxs = m.vx * ics2;
+        vys = m.vy * ics2;
+        de = eq_delta<LAT, C>(m.Ux * Uxs + m.Uy * Uys, C(2) * (m.Ux * vxs + m.Uy * vys) + m.vx * vxs + m.vy * vys,
+                              m.dT);
+        rho0r = m.rho - m.s0;
+    }
+    // g^eq of the pair (i, i + 1) of class k
+    auto pair = [&](int i, C& gp, C& gm) {
+        const int k = L::cls(i);
+        const C xi2 = C(L::c2cls(k)) * ics2;
+        if (ref) {
+            const C P = C(L::cx(i)) * Uxs + C(L::cy(i)) * Uys, q = C(L::cx(i)) * vxs + C(L::cy(i)) * vys;
+            C Ev, Od;
+            eq_pair_ref<LAT, C>(e, de, xi2, P, q, m.s0, rho0r, Ev, Od);
+            gp = C(L::w(i)) * (Ev + Od);
+            gm = C(L::w(i)) * (Ev - Od);
+            return;
+        }
+        const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
+        const C a1 = e.A1 + e.B1 * xi2;
+        const C a2 = e.A2 + e.B2 * xi2;
+        C p;
+        if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
+        else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
+        else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
+        const C p2 = p * p;
+        const C ev = a0 + p2 * (a2 + p2 * a4);
+        const C od = p * (a1 + p2 * a3);
+        const C ws0 = C(L::w(i)) * m.s0, wr = C(L::w(i)) * m.rho;
+        gp = ws0 + wr * (ev + od);
+        gm = ws0 + wr * (ev - od);
+    };
     if (sizeof(typename DualTraits<C>::Value) == 8) {
         {
-            const C geq = C(L::w(0)) * (m.s0 + m.rho * e.A0);
+            const C geq = ref ? C(L::w(0)) * (m.s0 * (C(1) + e.A0) + rho0r * de.A0)
+                              : C(L::w(0)) * (m.s0 + m.rho * e.A0);
             { const C g_ = gi(0); put(0, g_ + om * (geq - g_)); }
         }
 #pragma unroll
         for (int i = 1; i < Q; i += 2) {
-            const int k = L::cls(i);
-            const C xi2 = C(L::c2cls(k)) * ics2;
-            const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
-            const C a1 = e.A1 + e.B1 * xi2;
-            const C a2 = e.A2 + e.B2 * xi2;
-            C p;
-            if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
-            else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
-            else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
-            const C p2 = p * p;
-            const C ev = a0 + p2 * (a2 + p2 * a4);
-            const C od = p * (a1 + p2 * a3);
-            const C ws0 = C(L::w(i)) * m.s0, wr = C(L::w(i)) * m.rho;
-            const C gp = ws0 + wr * (ev + od);
-            const C gm = ws0 + wr * (ev - od);
+            C gp, gm;
+            pair(i, gp, gm);
             { const C g_ = gi(i); put(i, g_ + om * (gp - g_)); }
             { const C g_ = gi(i + 1); put(i + 1, g_ + om * (gm - g_)); }
         }
@@ -141,20 +195,8 @@ __device__ __forceinline__ void collide_given(const Geom& G, const Moments<LAT, 
 #pragma unroll
         for (int i = 5; i < Q; i += 2) {
             const int k = L::cls(i);
-            const C xi2 = C(L::c2cls(k)) * ics2;
-            const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
-            const C a1 = e.A1 + e.B1 * xi2;
-            const C a2 = e.A2 + e.B2 * xi2;
-            C p;
-            if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
-            else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
-            else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
-            const C p2 = p * p;
-            const C ev = a0 + p2 * (a2 + p2 * a4);
-            const C od = p * (a1 + p2 * a3);
-            const C ws0 = C(L::w(i)) * m.s0, wr = C(L::w(i)) * m.rho;
-            const C gp = ws0 + wr * (ev + od);
-            const C gm = ws0 + wr * (ev - od);
+            C gp, gm;
+            pair(i, gp, gm);
             const C sum = gp + gm, dif = gp - gm;
             M0 += sum;
             if (L::cx(i)) Mx += C(L::cx(i)) * dif;
@@ -164,12 +206,21 @@ __device__ __forceinline__ void collide_given(const Geom& G, const Moments<LAT, 
             { const C g_ = gi(i + 1); put(i + 1, g_ + om * (gm - g_)); }
         }
         // |c| = 1 class: (1,0) and (-1,0) are velocities 1, 2; (0,1), (0,-1) are 3, 4
-        const C a0 = e.A0 + ics2 * (e.B0 + e.C0 * ics2);
-        const C a2 = e.A2 + e.B2 * ics2;
-        const C px2 = uxs * uxs, py2 = uys * uys;
-        const C ws0 = C(L::w(1)) * m.s0, wr = C(L::w(1)) * m.rho;
-        C ex = ws0 + wr * (a0 + px2 * (a2 + px2 * a4));
-        C ey = ws0 + wr * (a0 + py2 * (a2 + py2 * a4));
+        C ex, ey;
+        if (ref) {
+            C Ev, Od;
+            eq_pair_ref<LAT, C>(e, de, ics2, Uxs, vxs, m.s0, rho0r, Ev, Od);
+            ex = C(L::w(1)) * Ev;
+            eq_pair_ref<LAT, C>(e, de, ics2, Uys, vys, m.s0, rho0r, Ev, Od);
+            ey = C(L::w(1)) * Ev;
+        } else {
+            const C a0 = e.A0 + ics2 * (e.B0 + e.C0 * ics2);
+            const C a2 = e.A2 + e.B2 * ics2;
+            const C px2 = uxs * uxs, py2 = uys * uys;
+            const C ws0 = C(L::w(1)) * m.s0, wr = C(L::w(1)) * m.rho;
+            ex = ws0 + wr * (a0 + px2 * (a2 + px2 * a4));
+            ey = ws0 + wr * (a0 + py2 * (a2 + py2 * a4));
+        }
         if (L::THERMAL) {
             const C d = C(0.25) * (m.se - Me - C(2) * (ex + ey));
             ex += d;
@@ -193,7 +244,7 @@ __device__ __forceinline__ void collide_given(const Geom& G, const Moments<LAT, 
 // (rho - rho0) + rho (even +- odd) carries no weight.  FP32 arithmetic, with
 // the conserved-moment closure of the FP32 path above (the closure sums take
 // w_i back in).  put(i, value) receives h*_i.
-template <int LAT, typename Put>
+template <int LAT, bool REF, typename Put>
 __device__ __forceinline__ void collide_scaled(const Geom& G, const float* h, Put&& put)
 {
     using L = Lat<LAT>;
@@ -207,30 +258,52 @@ __device__ __forceinline__ void collide_scaled(const Geom& G, const float* h, Pu
         if (L::cy(i)) sy += C(L::w(i) * L::cy(i)) * h[i];
         if (L::THERMAL && i) se += C(L::w(i) * (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i))) * h[i];
     }
-    const Moments<LAT, C> m = moments_of_sums<LAT, C>(s0, sx, sy, se, rho0_of<C>(G));
+    const Moments<LAT, C> m = moments_of_sums<LAT, C>(s0, sx, sy, se, rho0_of<C>(G), REF ? G.ref : 0,
+                                                      uref_of<C>(G, 0), uref_of<C>(G, 1));
     constexpr C ics2 = C(1.0 / L::CS2);
     constexpr C a3 = L::ORDER >= 3 ? C(1.0 / 6.0) : C(0);
     constexpr C a4 = L::ORDER >= 4 ? C(1.0 / 24.0) : C(0);
     const C uxs = m.ux * ics2, uys = m.uy * ics2;
     const EqPoly<C> e = eq_poly<LAT, C>(m.ux * uxs + m.uy * uys, m.dT);
     const C om = omega_of<C>(G);
+    const bool ref = m.ref != 0;
+    EqDelta<C> de;
+    C rho0r = C(0), Uxs = C(0), Uys = C(0), vxs = C(0), vys = C(0);
+    if (ref) {
+        Uxs = m.Ux * ics2;
+        Uys = m.Uy * ics2;
+        vxs = m.vx * ics2;
+        vys = m.vy * ics2;
+        de = eq_delta<LAT, C>(m.Ux * Uxs + m.Uy * Uys, C(2) * (m.Ux * vxs + m.Uy * vys) + m.vx * vxs + m.vy * vys,
+                              m.dT);
+        rho0r = m.rho - m.s0;
+    }
     C M0 = 0, Mx = 0, My = 0, Me = 0;
 #pragma unroll
     for (int i = 5; i < Q; i += 2) {
         const int k = L::cls(i);
         const C xi2 = C(L::c2cls(k)) * ics2;
-        const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
-        const C a1 = e.A1 + e.B1 * xi2;
-        const C a2 = e.A2 + e.B2 * xi2;
-        C p;
-        if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
-        else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
-        else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
-        const C p2 = p * p;
-        const C ev = a0 + p2 * (a2 + p2 * a4);
-        const C od = p * (a1 + p2 * a3);
-        const C hp = m.s0 + m.rho * (ev + od);
-        const C hm = m.s0 + m.rho * (ev - od);
+        C hp, hm;
+        if (ref) {
+            const C P = C(L::cx(i)) * Uxs + C(L::cy(i)) * Uys, q = C(L::cx(i)) * vxs + C(L::cy(i)) * vys;
+            C Ev, Od;
+            eq_pair_ref<LAT, C>(e, de, xi2, P, q, m.s0, rho0r, Ev, Od);
+            hp = Ev + Od;
+            hm = Ev - Od;
+        } else {
+            const C a0 = e.A0 + xi2 * (e.B0 + e.C0 * xi2);
+            const C a1 = e.A1 + e.B1 * xi2;
+            const C a2 = e.A2 + e.B2 * xi2;
+            C p;
+            if (L::cx(i) == 0) p = C(L::cy(i)) * uys;
+            else if (L::cy(i) == 0) p = C(L::cx(i)) * uxs;
+            else p = C(L::cx(i)) * uxs + C(L::cy(i)) * uys;
+            const C p2 = p * p;
+            const C ev = a0 + p2 * (a2 + p2 * a4);
+            const C od = p * (a1 + p2 * a3);
+            hp = m.s0 + m.rho * (ev + od);
+            hm = m.s0 + m.rho * (ev - od);
+        }
         const C sum = hp + hm, dif = hp - hm;
         M0 += C(L::w(i)) * sum;
         if (L::cx(i)) Mx += C(L::w(i) * L::cx(i)) * dif;
@@ -241,12 +314,21 @@ __device__ __forceinline__ void collide_scaled(const Geom& G, const float* h, Pu
     }
     // |c| = 1 class and the rest velocity close the conserved moments, in
     // unscaled units, then scaled
-    const C a0 = e.A0 + ics2 * (e.B0 + e.C0 * ics2);
-    const C a2 = e.A2 + e.B2 * ics2;
-    const C px2 = uxs * uxs, py2 = uys * uys;
-    const C ws0 = C(L::w(1)) * m.s0, wr = C(L::w(1)) * m.rho;
-    C ex = ws0 + wr * (a0 + px2 * (a2 + px2 * a4));
-    C ey = ws0 + wr * (a0 + py2 * (a2 + py2 * a4));
+    C ex, ey;
+    if (ref) {
+        C Ev, Od;
+        eq_pair_ref<LAT, C>(e, de, ics2, Uxs, vxs, m.s0, rho0r, Ev, Od);
+        ex = C(L::w(1)) * Ev;
+        eq_pair_ref<LAT, C>(e, de, ics2, Uys, vys, m.s0, rho0r, Ev, Od);
+        ey = C(L::w(1)) * Ev;
+    } else {
+        const C a0 = e.A0 + ics2 * (e.B0 + e.C0 * ics2);
+        const C a2 = e.A2 + e.B2 * ics2;
+        const C px2 = uxs * uxs, py2 = uys * uys;
+        const C ws0 = C(L::w(1)) * m.s0, wr = C(L::w(1)) * m.rho;
+        ex = ws0 + wr * (a0 + px2 * (a2 + px2 * a4));
+        ey = ws0 + wr * (a0 + py2 * (a2 + py2 * a4));
+    }
     if (L::THERMAL) {
         const C d = C(0.25) * (m.se - Me - C(2) * (ex + ey));
         ex += d;
@@ -262,10 +344,10 @@ __device__ __forceinline__ void collide_scaled(const Geom& G, const float* h, Pu
     put(0, h[0] + om * (geq0 * C(1.0 / L::w(0)) - h[0]));
 }
 
-template <int LAT, typename C, typename Put>
+template <int LAT, typename C, bool REF = false, typename Put>
 __device__ __forceinline__ Moments<LAT, C> collide(const Geom& G, const C* g, Put&& put)
 {
-    const Moments<LAT, C> m = moments<LAT, C>(g, rho0_of<C>(G));
+    const Moments<LAT, C> m = moments_G<LAT, C, REF>(G, g);
     collide_given<LAT, C>(G, m, [&](int i) -> const C& { return g[i]; }, put);
     return m;
 }

@@ -317,6 +317,70 @@ __device__ __forceinline__ EqPoly<C> eq_poly(C u2, C t)
     return e;
 }
 
+// Populations stored relative to a reference equilibrium f^eq(rho0, U, T0)
+// (the mean flow; "ref"): the equilibrium of a node is then needed as the
+// difference f^eq(rho, u, theta) - f^eq(rho0, U, 0), formed without
+// cancellation from the deviations s = rho - rho0, v = u - U, theta.  Its
+// coefficient differences dA_k = A_k(u2, t) - A_k(U2, 0) in d = u2 - U2 =
+// (2 U.v + |v|^2) / c_s^2 (the B and C coefficients vanish at t = 0, so
+// theirs are the values themselves), and the reference values A1r, A2r.
+template <typename C>
+struct EqDelta {
+    C A0, A1, A2, A1r, A2r;
+};
+
+template <int LAT, typename C>
+__device__ __forceinline__ EqDelta<C> eq_delta(C U2, C d, C t)
+{
+    EqDelta<C> e;
+    if (Lat<LAT>::ORDER == 3) {
+        e.A0 = C(-0.5) * d - t;
+        e.A1 = C(-0.5) * d - C(2) * t;
+        e.A2 = C(0);
+        e.A1r = C(1) - C(0.5) * U2;
+        e.A2r = C(0.5);
+    } else if (Lat<LAT>::THERMAL) {
+        e.A0 = C(-0.5) * d - t + C(0.125) * (C(2) * U2 + d) * d + t * (U2 + d) + t * t;
+        e.A1 = C(-0.5) * d - C(2) * t;
+        e.A2 = C(-0.25) * d - C(1.5) * t;
+        e.A1r = C(1) - C(0.5) * U2;
+        e.A2r = C(0.5) - C(0.25) * U2;
+    } else {
+        e.A0 = C(-0.5) * d;
+        e.A1 = C(0);
+        e.A2 = C(0);
+        e.A1r = C(1);
+        e.A2r = C(0.5);
+    }
+    return e;
+}
+
+// One opposite pair (+c, -c) of velocity class xi2 relative to the
+// reference: g^eq_(+-) / w = Ev +- Od with
+//   Ev = s (1 + ev) + rho0 dE,  Od = s od + rho0 dO,
+// ev, od the even and odd parts at (u, theta) (as eq_poly's pair loop), and
+// dE, dO their differences from the reference's, in q = c.v / c_s^2 and
+// P = c.U / c_s^2 (p = P + q):
+//   dE = da0 + da2 p^2 + a2r (p^2 - P^2) + a4 (p^2 - P^2)(p^2 + P^2)
+//   dO = da1 p + a1r q + a3 q (p^2 + p P + P^2),  p^2 - P^2 = q (p + P).
+template <int LAT, typename C>
+__device__ __forceinline__ void eq_pair_ref(const EqPoly<C>& e, const EqDelta<C>& de, C xi2, C P, C q, C s,
+                                            C rho0, C& Ev, C& Od)
+{
+    constexpr C a3 = Lat<LAT>::ORDER >= 3 ? C(1.0 / 6.0) : C(0);
+    constexpr C a4 = Lat<LAT>::ORDER >= 4 ? C(1.0 / 24.0) : C(0);
+    const C bc = e.B0 + e.C0 * xi2;
+    const C a0 = e.A0 + xi2 * bc, a1 = e.A1 + e.B1 * xi2, a2 = e.A2 + e.B2 * xi2;
+    const C da0 = de.A0 + xi2 * bc, da1 = de.A1 + e.B1 * xi2, da2 = de.A2 + e.B2 * xi2;
+    const C p = P + q, p2 = p * p, P2 = P * P, dp2 = q * (p + P);
+    const C ev = a0 + p2 * (a2 + p2 * a4);
+    const C od = p * (a1 + p2 * a3);
+    const C dE = da0 + da2 * p2 + de.A2r * dp2 + a4 * dp2 * (p2 + P2);
+    const C dO = da1 * p + de.A1r * q + a3 * q * (p2 + p * P + P2);
+    Ev = s * (C(1) + ev) + rho0 * dE;
+    Od = s * od + rho0 * dO;
+}
+
 template <int LAT, typename C>
 __device__ __forceinline__ void eq_coef(C u2, C dT, C* a0, C* a1, C* a2)
 {
@@ -336,14 +400,22 @@ template <int LAT, typename C>
 struct Moments {
     C s0, ux, uy, dT, rho;
     C sx, sy, se;   // sum g c_x, sum g c_y, sum g |c|^2
+    // ref: populations held relative to f^eq(rho0, U, T0); U and v = u - U
+    int ref = 0;
+    C Ux = C(0), Uy = C(0), vx = C(0), vy = C(0);
 };
 
 // Eq. macro on shifted populations (sum_i w_i c_i = 0, sum_i w_i |c_i|^2 =
 // 2 c_s^2): rho = rho0 + sum g, rho u = sum g c, and
 // theta - 1 = (sum g |c|^2 - rho |u|^2 - 2 c_s^2 (rho - rho0)) / (2 rho c_s^2).
 // The same from the sums s0 = sum g, (sx, sy) = sum g c, se = sum g |c|^2.
+// With a reference (ref, U = (Ux, Uy)) the sums are of g = f - f^eq(rho0,
+// U, 0): rho u = sum g c + rho0 U and sum f |c|^2 = sum g |c|^2 + rho0 (|U|^2
+// + 2 c_s^2), formed as v = (sum g c - s U) / rho and
+// theta = (sum g |c|^2 - 2 c_s^2 s - s |U|^2 - 2 rho U.v - rho |v|^2) / (2 rho c_s^2).
 template <int LAT, typename C>
-__device__ __forceinline__ Moments<LAT, C> moments_of_sums(C s0, C sx, C sy, C se, C rho0)
+__device__ __forceinline__ Moments<LAT, C> moments_of_sums(C s0, C sx, C sy, C se, C rho0, int ref = 0,
+                                                           C Ux = C(0), C Uy = C(0))
 {
     using L = Lat<LAT>;
     Moments<LAT, C> m;
@@ -353,17 +425,33 @@ __device__ __forceinline__ Moments<LAT, C> moments_of_sums(C s0, C sx, C sy, C s
     m.se = se;
     m.rho = rho0 + s0;
     const C irho = C(1) / m.rho;
-    m.ux = sx * irho;
-    m.uy = sy * irho;
     m.dT = C(0);
+    if (!ref) {
+        m.ux = sx * irho;
+        m.uy = sy * irho;
+        m.vx = m.ux;
+        m.vy = m.uy;
+        if (L::THERMAL)
+            m.dT = (se - m.rho * (m.ux * m.ux + m.uy * m.uy) - C(2.0 * L::CS2) * s0) * irho *
+                   C(0.5 / L::CS2);
+        return m;
+    }
+    m.ref = 1;
+    m.Ux = Ux;
+    m.Uy = Uy;
+    m.vx = (sx - s0 * Ux) * irho;
+    m.vy = (sy - s0 * Uy) * irho;
+    m.ux = Ux + m.vx;
+    m.uy = Uy + m.vy;
     if (L::THERMAL)
-        m.dT = (se - m.rho * (m.ux * m.ux + m.uy * m.uy) - C(2.0 * L::CS2) * s0) * irho *
-               C(0.5 / L::CS2);
+        m.dT = (se - C(2.0 * L::CS2) * s0 - s0 * (Ux * Ux + Uy * Uy) -
+                m.rho * (C(2) * (Ux * m.vx + Uy * m.vy) + m.vx * m.vx + m.vy * m.vy)) *
+               irho * C(0.5 / L::CS2);
     return m;
 }
 
 template <int LAT, typename C>
-__device__ __forceinline__ Moments<LAT, C> moments(const C* g, C rho0)
+__device__ __forceinline__ Moments<LAT, C> moments(const C* g, C rho0, int ref = 0, C Ux = C(0), C Uy = C(0))
 {
     using L = Lat<LAT>;
     C s0 = 0, sx = 0, sy = 0, se = 0;
@@ -374,7 +462,28 @@ __device__ __forceinline__ Moments<LAT, C> moments(const C* g, C rho0)
         if (L::cy(i)) sy += C(L::cy(i)) * g[i];
         if (L::THERMAL && i) se += C(L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i)) * g[i];
     }
-    return moments_of_sums<LAT, C>(s0, sx, sy, se, rho0);
+    return moments_of_sums<LAT, C>(s0, sx, sy, se, rho0, ref, Ux, Uy);
+}
+
+// Moments of given macros (drho, u, theta - 1), with the reference's
+// deviation v = u - U formed from vx = ux - Ux (the caller's values).
+template <int LAT, typename C>
+__device__ __forceinline__ Moments<LAT, C> moments_of_macros(C s0, C ux, C uy, C dT, C rho0, int ref = 0,
+                                                             C Ux = C(0), C Uy = C(0))
+{
+    Moments<LAT, C> m;
+    m.s0 = s0;
+    m.rho = rho0 + s0;
+    m.ux = ux;
+    m.uy = uy;
+    m.dT = Lat<LAT>::THERMAL ? dT : C(0);
+    m.sx = m.sy = m.se = C(0);
+    m.ref = ref;
+    m.Ux = ref ? Ux : C(0);
+    m.Uy = ref ? Uy : C(0);
+    m.vx = ux - m.Ux;
+    m.vy = uy - m.Uy;
+    return m;
 }
 
 // Shifted equilibrium of all velocities (g^eq = f^eq - w rho0).
@@ -385,6 +494,25 @@ __device__ __forceinline__ void equilibrium(const Moments<LAT, C>& m, C* geq)
     constexpr C ics2 = C(1.0 / L::CS2);
     constexpr C a3 = L::ORDER >= 3 ? C(1.0 / 6.0) : C(0);
     constexpr C a4 = L::ORDER >= 4 ? C(1.0 / 24.0) : C(0);
+    if (m.ref) {
+        // relative to the reference equilibrium (eq_pair_ref)
+        const C U2 = (m.Ux * m.Ux + m.Uy * m.Uy) * ics2;
+        const C d = (C(2) * (m.Ux * m.vx + m.Uy * m.vy) + m.vx * m.vx + m.vy * m.vy) * ics2;
+        const EqPoly<C> e = eq_poly<LAT, C>((m.ux * m.ux + m.uy * m.uy) * ics2, m.dT);
+        const EqDelta<C> de = eq_delta<LAT, C>(U2, d, m.dT);
+        const C rho0 = m.rho - m.s0;
+        geq[0] = C(L::w(0)) * (m.s0 * (C(1) + e.A0) + rho0 * de.A0);
+#pragma unroll
+        for (int i = 1; i < L::Q; i += 2) {
+            const C cx = C(L::cx(i)), cy = C(L::cy(i));
+            const C P = (cx * m.Ux + cy * m.Uy) * ics2, q = (cx * m.vx + cy * m.vy) * ics2;
+            C Ev, Od;
+            eq_pair_ref<LAT, C>(e, de, C(L::c2cls(L::cls(i))) * ics2, P, q, m.s0, rho0, Ev, Od);
+            geq[i] = C(L::w(i)) * (Ev + Od);
+            geq[i + 1] = C(L::w(i)) * (Ev - Od);
+        }
+        return;
+    }
     C a0[L::NCLS], a1[L::NCLS], a2[L::NCLS];
     eq_coef<LAT, C>((m.ux * m.ux + m.uy * m.uy) * ics2, m.dT, a0, a1, a2);
     geq[0] = C(L::w(0)) * (m.s0 + m.rho * a0[0]);
@@ -418,7 +546,13 @@ struct Geom {
     double tau, rho0, omega;    // omega = 1 / tau
     float omega_f, rho0_f;
     unsigned long long wait_ns; // limit of the bulk kernel's first wait for a tensor copy
+    // populations held relative to f^eq(rho0, uref, T0) (ref != 0) instead
+    // of w rho0; uref rounded to float for float-valued arithmetic
+    int ref;
+    double uref[2];
+    float uref_f[2];
 };
+
 
 // A rectangle of bulk nodes [x0, x1) x [y0, y1).
 struct Region {

@@ -52,7 +52,7 @@ def test_params_struct_layout_matches_header(tmp_path):
 def cfg_params(**kw):
     p = lbm.lbm_params_default()
     for k, v in kw.items():
-        if k in ("side", "scheme", "p_inf", "inflow"):
+        if k in ("side", "scheme", "p_inf", "inflow", "u_ref"):
             for i, x in enumerate(v):
                 getattr(p, k)[i] = x
         else:
@@ -100,6 +100,10 @@ def test_defaults_and_workspace_size():
     (lbm.LBM_D2Q9, 16384, 15360, dict(), False),
     (lbm.LBM_D2Q37, 16, 16, dict(alpha_V=float("nan")), False),    # relaxation parameters finite
     (lbm.LBM_D2Q37, 16, 16, dict(alpha_T=float("inf")), False),
+    (lbm.LBM_D2Q37, 16, 16, dict(u_ref=[0.3, 0.2]), True),          # reference velocity below c_s
+    (lbm.LBM_D2Q37, 16, 16, dict(u_ref=[0.8, 0.3]), False),         # |u_ref| >= c_s
+    (lbm.LBM_D2Q37, 16, 16, dict(u_ref=[float("nan"), 0.0]), False),
+    (lbm.LBM_D2Q9, 16, 16, dict(u_ref=[0.5, 0.3]), False),          # c_s^2 = 1/3 on D2Q9
     (3, 16, 16, dict(), False),                                    # unknown lattice
     (-1, 16, 16, dict(), False),
 ])

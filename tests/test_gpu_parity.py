@@ -358,11 +358,12 @@ def test_d2q37_many_tiles_pulse_through_a_corner():
 def test_vortex_1024x512_20000_steps_fp32_fp16_against_fp64(Ma, capsys):
     """The benchmark grid's vortex (inflow | CBC-RELAX with the mesoscopic
     viscous vector, periodic y) at Ma = 0.1 and 0.3 over 20000 steps, FP32
-    and FP16 storage against the FP64 path (which matches the oracle to
-    1e-12 over the first 2000 steps, below), per field.  FP32: rho and T
-    within the 1e-5 target; u (relative to max |u|) misses it -- 2.9e-5 and
-    4.2e-5 measured -- and is held here to 1e-4 so that a change for the
-    worse shows.  FP16: reported, with loose bars."""
+    and FP16 storage (populations held relative to the stream's
+    equilibrium, u_ref = (U0, 0)) against the FP64 path (which matches the
+    oracle to 1e-12 over the first 2000 steps, below), per field.  FP32:
+    every field within the 1e-5 target (with the plain shift u missed it:
+    2.9e-5 and 4.2e-5, the rounding of populations of the stream's size).
+    FP16: reported, with loose bars."""
     steps = 20000
 
     def run(storage):
@@ -374,8 +375,7 @@ def test_vortex_1024x512_20000_steps_fp32_fp16_against_fp64(Ma, capsys):
     with capsys.disabled():
         print("\nvortex 1024x512 Ma=%.1f, %d steps, mesoscopic V, rel. errors vs FP64 (target 1e-5):" % (Ma, steps),
               {st: {k: "%.2e" % v for k, v in e.items()} for st, e in res.items()})
-    assert res["f32"]["rho"] < 1e-5 and res["f32"]["T"] < 1e-5, res
-    assert res["f32"]["u"] < 1e-4, res
+    assert max(res["f32"].values()) < 1e-5, res
     assert res["f16"]["rho"] < 5e-3 and res["f16"]["T"] < 5e-3 and res["f16"]["u"] < 2e-2, res
 
 
