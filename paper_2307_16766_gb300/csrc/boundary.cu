@@ -29,7 +29,17 @@ constexpr int kBandThreads = 32;   // allocation-free path: one thread per unkno
 // issue (one warp instruction per 64 cycles on each sub-partition) bounds
 // the characteristic arithmetic; the host sizes tiles to fit.
 constexpr int kTileThreads = kTileUnknowns;
-constexpr int kCluster = 4;         // CTAs per band tile: one per characteristic component
+constexpr int kCluster = 4;         // groups per band tile: one per characteristic component
+
+// FP32 / FP16 storage: a band tile is one CTA of kCluster groups; FP64: a
+// cluster of kCluster CTAs.
+template <typename S>
+constexpr bool band_mono() { return sizeof(S) < 8; }
+template <typename S>
+constexpr int band_threads() { return band_mono<S>() ? kCluster * kTileThreads : kTileThreads; }
+// CTAs of a launch of n tiles
+template <typename S>
+constexpr int band_ctas(int n) { return band_mono<S>() ? n : n * kCluster; }
 
 // ---------------------------------------------------------------------------
 // The band kernel: one cluster of four CTAs per tile
@@ -244,9 +254,14 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     // a kernel launched after this one for early start (the bulk update,
     // which reads only the old buffer) may begin now
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = int(cl.block_rank());
-    const int l = threadIdx.x;
+    // FP32 / FP16 storage: one CTA of four 128-thread groups per tile, group
+    // r in the role of cluster rank r, exchanging through its own shared
+    // memory (the tile then holds one SM and leaves the others to the bulk
+    // kernel); FP64: a cluster of four 128-thread CTAs (FP64 issue is slow,
+    // so each component's arithmetic gets an SM of its own)
+    constexpr bool MONO = band_mono<S>();
+    const int rank = MONO ? int(threadIdx.x / kTileThreads) : int(cg::this_cluster().block_rank());
+    const int l = int(threadIdx.x % kTileThreads);
     __shared__ __align__(16) R Ys[kTileThreads * 4];        // stage values, lab frame
     __shared__ __align__(16) R Xp[kTileThreads * 8];        // shares of the system's inputs
     __shared__ __align__(16) double Xw[kTileThreads * 4];   // wave amplitudes
@@ -260,8 +275,31 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     R* SNt = SUt1 + 4 * B.max_nodes;               // [max_nodes][5] moments of t
     S* Fx = reinterpret_cast<S*>(SNt + 5 * B.max_nodes);   // [max_fx][Q], node k in CTA k % 4
     auto bcast = [&](auto* p, auto v) {
+        if constexpr (MONO) {
+            *p = v;
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
 #pragma unroll
-        for (int q = 0; q < kCluster; ++q) *cl.map_shared_rank(p, q) = v;
+            for (int q = 0; q < kCluster; ++q) *cl.map_shared_rank(p, q) = v;
+        }
+    };
+    auto sync_all = [&]() {
+        if constexpr (MONO) __syncthreads();
+        else cg::this_cluster().sync();
+    };
+    // the stage exchanges: a value into slot p of every group, then the wait
+    // for all of them
+    auto xput = [&](auto* p, auto v, unsigned long long* bar) {
+        if constexpr (MONO) *p = v;
+        else put_cluster(p, v, bar);
+    };
+    auto xwait = [&](unsigned long long* bar, unsigned parity) -> bool {
+        if constexpr (MONO) {
+            __syncthreads();
+            return true;
+        } else {
+            return wait_exchange(bar, parity, B.status);
+        }
     };
     // Descriptors first, all at once: under a saturated memory system each
     // dependent global round trip costs microseconds.
@@ -272,13 +310,16 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     const int kp = rank + kCluster * (4 * (l % 32) + l / 32);
     StripNode Nb{-1, -1, 0, -1, -1, 0};
     if (kp < ns) Nb = snt[kp];
-    // the time-t slots this thread loads: nodes l, l + 128, ... (descriptors
-    // of the first kLT issued here, the rest in a loop)
+    // the time-t slots this thread loads: nodes tl, tl + tstride, ...
+    // (descriptors of the first kLT issued here, the rest in a loop); every
+    // CTA of a cluster loads all of them into its own shared memory
     constexpr int kLT = 3;
+    constexpr int tstride = MONO ? kTileThreads * kCluster : kTileThreads;
+    const int tl = MONO ? int(threadIdx.x) : l;
     int tsl[kLT];
 #pragma unroll
     for (int j = 0; j < kLT; ++j) {
-        const int k = l + j * kTileThreads;
+        const int k = tl + j * tstride;
         tsl[j] = -1;
         if (k < ns) {
             const StripNode& N = snt[k];
@@ -286,15 +327,21 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         }
     }
     const UDesc D = B.ld[(long long)tile * kTileUnknowns + l];
-    if (l == 0) {
+    int nc0 = 0, nc1 = 0, nc2 = 0, nc3 = 0;
+    if constexpr (!MONO) {
+        if (l == 0) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&xbar[k])));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            for (int k = 0; k < 4; ++k)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&xbar[k])));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        // unknowns that compute stage s (the same in every CTA of the cluster)
+        nc0 = __syncthreads_count(D.level <= 3);
+        nc1 = __syncthreads_count(D.level <= 2);
+        nc2 = __syncthreads_count(D.level <= 1);
+        nc3 = __syncthreads_count(D.level <= 0);
     }
-    // unknowns that compute stage s (the same in every CTA of the cluster)
-    const int nc0 = __syncthreads_count(D.level <= 3), nc1 = __syncthreads_count(D.level <= 2),
-              nc2 = __syncthreads_count(D.level <= 1), nc3 = __syncthreads_count(D.level <= 0);
-    cl.sync();                          // every CTA of the cluster runs before any remote store
+    sync_all();                         // every CTA of the cluster runs before any remote store
 
     // 1. strip nodes: macros of t and moments of t for every CTA; macros of
     //    t + 1 (pull and Eq. macro) by CTA k % kCluster for node k, shared
@@ -353,9 +400,9 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     }
 #pragma unroll
     for (int j = 0; j < kLT; ++j)
-        if (tsl[j] >= 0) load_t(l + j * kTileThreads, tsl[j]);
+        if (tsl[j] >= 0) load_t(tl + j * tstride, tsl[j]);
     if (Nb.x >= 0 && (Nb.flags & kSNPull)) pull_t1(kp, Nb);
-    for (int k = l + kLT * kTileThreads; k < ns; k += kTileThreads) {
+    for (int k = tl + kLT * tstride; k < ns; k += tstride) {
         const StripNode N = snt[k];
         if (N.x >= 0 && (N.flags & kSNLoadT)) load_t(k, N.tslot);
     }
@@ -363,11 +410,11 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         const StripNode N = snt[k];
         if (N.x >= 0 && (N.flags & kSNPull)) pull_t1(k, N);
     }
-    if (lev <= 4) {
+    if (lev <= 4 && (!MONO || rank == 0)) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) Ys[4 * l + m] = R(U0[m]);
     }
-    cl.sync();
+    sync_all();
 
     // 2. RK4, component rank of every unknown
     CtxT<R> X;
@@ -391,7 +438,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     bool xok = true;                    // every exchange so far completed in time
     for (int stage = 0; stage < 4; ++stage) {
         const bool comp = lev <= 3 - stage;
-        if (l == 0) {                   // bytes of this stage's two exchanges
+        if (!MONO && l == 0) {          // bytes of this stage's two exchanges
             const unsigned ncomp = unsigned(stage == 0 ? nc0 : stage == 1 ? nc1 : stage == 2 ? nc2 : nc3);
             expect_bytes(&xbar[stage & 1], unsigned(kCluster * sizeof(double)) * ncomp);
             expect_bytes(&xbar[2 + (stage & 1)], unsigned(kCluster * sizeof(R)) * ncomp);
@@ -490,7 +537,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                 }
             }
         }
-        if constexpr (!kLocal) cl.sync();
+        if constexpr (!kLocal) sync_all();
         // B: wave rank, FP64.  Row rank of S (see apply_S) applied to dU/dn,
         // T and V, with Lambda_rank.
         auto XP = [&](int i) -> R {
@@ -572,7 +619,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                     }
                 }
             }
-            put_cluster(Xw + 4 * l + rank, w, &xbar[stage & 1]);
+            xput(Xw + 4 * l + rank, w, &xbar[stage & 1]);
             // the transversal and viscous terms this CTA adds in step C
             if (cbc) {
                 if (rank == 3) {
@@ -583,7 +630,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                 }
             }
         }
-        if (xok) xok = wait_exchange(&xbar[stage & 1], (stage >> 1) & 1, B.status);
+        if (xok) xok = xwait(&xbar[stage & 1], (stage >> 1) & 1);
         // C: lab component rank of the right-hand side (S^-1 of the waves,
         // with r^-1 = rho / theta, b = sqrt(2 c_s^4 / T~) formed in type R);
         // RK4 update (FP64).  A side unknown's lab component 1 or 2 needs
@@ -621,38 +668,41 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                 const double wk = stage == 0 ? 1.0 : 2.0;
                 const double hk = stage == 2 ? 1.0 : 0.5;
                 acc = (stage == 0 ? 0.0 : acc) + wk * kc;
-                put_cluster(Ys + 4 * l + rank, R(u0r + hk * kc), &xbar[2 + (stage & 1)]);
+                xput(Ys + 4 * l + rank, R(u0r + hk * kc), &xbar[2 + (stage & 1)]);
             } else {
                 // RK4: U(t + 1) = U(t) + (k1 + 2 k2 + 2 k3 + k4) / 6
                 const double un = u0r + (acc + kc) * (1.0 / 6.0);
                 B.Ub[((long long)(par_t ^ 1) * B.n_unk + D.gid) * 4 + rank] = un;
-                put_cluster(Ys + 4 * l + rank, R(un), &xbar[2 + (stage & 1)]);
+                xput(Ys + 4 * l + rank, R(un), &xbar[2 + (stage & 1)]);
             }
         }
-        if (xok) xok = wait_exchange(&xbar[2 + (stage & 1)], (stage >> 1) & 1, B.status);
+        if (xok) xok = xwait(&xbar[2 + (stage & 1)], (stage >> 1) & 1);
     }
 
     // 3. Dirichlet populations of unknown l, on CTA l % kCluster
     if (lev == 0 && l % kCluster == rank) {
         const R Unew[4] = {Ys[4 * l], Ys[4 * l + 1], Ys[4 * l + 2], Ys[4 * l + 3]};
         const bool neep = B.dirichlet >= 1;     // needs x_f: NEEP or regularised NEEP
-        const S* fs = neep ? cl.map_shared_rank(Fx + D.wsrc * L::Q, D.wslot % kCluster) : nullptr;
+        const S* fs = nullptr;
+        if (neep) {
+            if constexpr (MONO) fs = Fx + D.wsrc * L::Q;
+            else fs = cg::this_cluster().map_shared_rank(Fx + D.wsrc * L::Q, D.wslot % kCluster);
+        }
         dirichlet<LAT, S, R, REF>(G, B, f, neep ? SUt1 + 4 * D.wslot : nullptr, fs, D, Unew);
     }
-    cl.sync();                          // no CTA leaves while its Fx may be read
+    if constexpr (!MONO) cg::this_cluster().sync();   // no CTA leaves while its Fx may be read
 }
 
-// At most 128 registers with FP32 / FP16 storage: a band CTA then leaves room
-// for the five two-row bulk CTAs on its SM (5 x 128 x 72 + 128 x 128 registers).
-template <typename S>
-constexpr int band_min_blocks() { return sizeof(S) == 8 ? 1 : 4; }
-
+// FP32 / FP16 storage: one 512-thread CTA per tile, at most 128 registers a
+// thread (the whole register file of its SM, which then holds no bulk CTA:
+// the bulk kernel runs undisturbed on the other SMs).  FP64: a cluster of
+// four 128-thread CTAs (launched with the cluster attribute).
 template <int LAT, typename S, bool REF>
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads, band_min_blocks<S>())
+__global__ void __launch_bounds__(band_threads<S>(), 1)
     k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
            int par_t)
 {
-    band_tile<LAT, S, REF>(G, O, B, E, fin, f, par_t, blockIdx.x / kCluster);
+    band_tile<LAT, S, REF>(G, O, B, E, fin, f, par_t, band_mono<S>() ? blockIdx.x : blockIdx.x / kCluster);
 }
 
 // Band tiles of many grids in one launch: cluster t takes tile tile_run[t].y
@@ -662,15 +712,12 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads,
 // latencies more CTAs hide better (a few hundred bytes spill; four CTAs per
 // SM, uncapped, measured 4% slower on the 96-run sweep, six 1% slower).  The
 // FP64 form would spill kilobytes and keeps its registers.
-template <typename S>
-constexpr int band_batch_min_blocks() { return sizeof(S) == 8 ? 1 : 5; }
-
 template <int LAT, typename S>
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTileThreads, band_batch_min_blocks<S>())
+__global__ void __launch_bounds__(band_threads<S>(), 1)
     k_band_batch(const BandRun* __restrict__ runs, const int2* __restrict__ tile_run, int par_t)
 {
     __shared__ __align__(16) BandRun R;
-    const int2 tr = tile_run[blockIdx.x / kCluster];
+    const int2 tr = tile_run[band_mono<S>() ? blockIdx.x : blockIdx.x / kCluster];
     {
         const int* src = reinterpret_cast<const int*>(runs + tr.x);
         int* dst = reinterpret_cast<int*>(&R);
@@ -705,13 +752,13 @@ int boundary_t(const Geom& G, const Offsets& O, const Export& E, const Band& B, 
 {
     if (B.n_tiles == 0) return 0;
     const size_t smem = band_smem<LAT, S>(B);
+    const dim3 grd(band_ctas<S>(B.n_tiles)), blk(band_threads<S>());
+    const int cl = band_mono<S>() ? 1 : kCluster;
     if (G.ref)
-        k_band<LAT, S, true><<<B.n_tiles * kCluster, kTileThreads, smem, st>>>(
-            G, O, B, E, static_cast<const S*>(fin), static_cast<S*>(fnew), par_t);
-    else
-        k_band<LAT, S, false><<<B.n_tiles * kCluster, kTileThreads, smem, st>>>(
-            G, O, B, E, static_cast<const S*>(fin), static_cast<S*>(fnew), par_t);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+        return launch_ex_cl(k_band<LAT, S, true>, grd, blk, smem, st, false, cl, G, O, B, E, static_cast<const S*>(fin),
+                         static_cast<S*>(fnew), par_t);
+    return launch_ex_cl(k_band<LAT, S, false>, grd, blk, smem, st, false, cl, G, O, B, E, static_cast<const S*>(fin),
+                     static_cast<S*>(fnew), par_t);
 }
 
 template <int LAT, typename S>
@@ -719,8 +766,8 @@ int band_batch_t(const BandRun* runs, const int2* tile_run, int n_tiles, size_t 
                  cudaStream_t st, bool early)
 {
     if (n_tiles == 0) return 0;
-    return launch_ex(k_band_batch<LAT, S>, dim3(n_tiles * kCluster), dim3(kTileThreads), smem, st, early,
-                     runs, tile_run, par_t);
+    return launch_ex_cl(k_band_batch<LAT, S>, dim3(band_ctas<S>(n_tiles)), dim3(band_threads<S>()), smem, st, early,
+                     band_mono<S>() ? 1 : kCluster, runs, tile_run, par_t);
 }
 
 template <int LAT, typename S>

@@ -738,6 +738,35 @@ inline int launch_ex(void (*kern)(K...), dim3 grd, dim3 blk, size_t smem, cudaSt
     return cudaLaunchKernelEx(&cfg, kern, args...) == cudaSuccess ? 0 : -1;
 }
 
+// The same with thread-block clusters of `cluster` CTAs along x (1: none).
+template <typename... K, typename... A>
+inline int launch_ex_cl(void (*kern)(K...), dim3 grd, dim3 blk, size_t smem, cudaStream_t st, bool early,
+                        int cluster, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grd;
+    cfg.blockDim = blk;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    int n = 0;
+    if (early) {
+        at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[n].val.programmaticStreamSerializationAllowed = 1;
+        ++n;
+    }
+    if (cluster > 1) {
+        at[n].id = cudaLaunchAttributeClusterDimension;
+        at[n].val.clusterDim.x = unsigned(cluster);
+        at[n].val.clusterDim.y = 1;
+        at[n].val.clusterDim.z = 1;
+        ++n;
+    }
+    cfg.attrs = at;
+    cfg.numAttrs = n;
+    return cudaLaunchKernelEx(&cfg, kern, args...) == cudaSuccess ? 0 : -1;
+}
+
 
 // Initial populations f^eq(U0) into f, strips of time 0, boundary state.
 int launch_init(int lat, int storage, const Geom& G, const Export& E, const Band& B,
