@@ -532,6 +532,20 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
                       pl.snp.begin() + (size_t)t * B.max_nodes);
         }
     }
+    // With FP32 / FP16 storage, tiles whose clusters would not fit the GPU
+    // at once (four CTAs each) run as one CTA per tile: each then holds a
+    // whole SM and the bulk kernel keeps the others, and the waves of many
+    // tiles are not bound by FP64 issue.  A few tiles keep the cluster form,
+    // whose band is shorter on an otherwise busy GPU.
+    {
+        int sms = 0, dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+            cudaGetLastError();
+            sms = 152;
+        }
+        B.mono = p->storage != LBM_F64 && B.n_tiles * 4 > sms;
+    }
     B.viscous = p->viscous;
     B.dirichlet = p->dirichlet;
     for (int s = 0; s < 4; ++s) {
@@ -555,6 +569,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     B.kR_f = float(B.kR);
     B.cs_f = float(B.cs);
     B.ihcs_f = float(B.ihcs);
+    set_ffk(B);
     pl.Uin[0] = p->inflow[0] - p->rho0;
     pl.Uin[1] = p->inflow[1];
     pl.Uin[2] = p->inflow[2];

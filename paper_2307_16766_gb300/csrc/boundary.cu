@@ -31,15 +31,11 @@ constexpr int kBandThreads = 32;   // allocation-free path: one thread per unkno
 constexpr int kTileThreads = kTileUnknowns;
 constexpr int kCluster = 4;         // groups per band tile: one per characteristic component
 
-// FP32 / FP16 storage: a band tile is one CTA of kCluster groups; FP64: a
-// cluster of kCluster CTAs.
-template <typename S>
-constexpr bool band_mono() { return sizeof(S) < 8; }
-template <typename S>
-constexpr int band_threads() { return band_mono<S>() ? kCluster * kTileThreads : kTileThreads; }
-// CTAs of a launch of n tiles
-template <typename S>
-constexpr int band_ctas(int n) { return band_mono<S>() ? n : n * kCluster; }
+// A band tile is a cluster of kCluster CTAs of kTileThreads (one SM per
+// characteristic component) or, with FP32 / FP16 storage and MONO, one CTA
+// of kCluster such groups (the whole tile on one SM).
+template <bool MONO>
+constexpr int band_threads() { return MONO ? kCluster * kTileThreads : kTileThreads; }
 
 // ---------------------------------------------------------------------------
 // The band kernel: one cluster of four CTAs per tile
@@ -177,6 +173,60 @@ __device__ __forceinline__ void put_async(unsigned a, float v, unsigned bar)
                  ::"r"(a), "r"(__float_as_uint(v)), "r"(bar) : "memory");
 }
 
+// Unevaluated sums hi + lo of two floats ("float-float"), built from the
+// error-free transformations TwoSum (Knuth) and TwoProduct (by FMA): about
+// 48 significant bits at FP32 issue cost.  The band kernel forms the wave
+// amplitudes and the right-hand side with FP32 and FP16 storage in them
+// instead of FP64 (one FP64 warp instruction per 64 cycles on each SM
+// sub-partition; with the four components of a tile on one SM the FP64
+// work would queue there): their projections S dU/dn cancel (an acoustic
+// wave has a small entropy part), and plain FP32 lost accuracy there.
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ FF ff_fast(float a, float b)      // |a| >= |b|
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_two_sum(float a, float b)
+{
+    const float s = a + b, z = s - a;
+    return {s, (a - (s - z)) + (b - z)};
+}
+__device__ __forceinline__ FF ff_prod(float a, float b)
+{
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y)
+{
+    const FF s = ff_two_sum(x.h, y.h), t = ff_two_sum(x.l, y.l);
+    const FF u = ff_fast(s.h, s.l + t.h);
+    return ff_fast(u.h, u.l + t.l);
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ FF ff_mul(FF x, float b)
+{
+    const FF p = ff_prod(x.h, b);
+    return ff_fast(p.h, fmaf(x.l, b, p.l));
+}
+__device__ __forceinline__ FF ff_mul(FF x, FF y)
+{
+    const FF p = ff_prod(x.h, y.h);
+    return ff_fast(p.h, fmaf(x.h, y.l, fmaf(x.l, y.h, p.l)));
+}
+__device__ __forceinline__ double ff_to_double(FF x) { return double(x.h) + double(x.l); }
+__device__ __forceinline__ double ff_pack(FF x)
+{
+    return __hiloint2double(__float_as_int(x.h), __float_as_int(x.l));
+}
+__device__ __forceinline__ FF ff_unpack(double v)
+{
+    return {__int_as_float(__double2hiint(v)), __int_as_float(__double2loint(v))};
+}
+__device__ __forceinline__ FF ff_const(const float (&c)[2]) { return {c[0], c[1]}; }
+
 // v into slot p of every CTA of the cluster, counted on barrier `bar` there
 template <typename T>
 __device__ __forceinline__ void put_cluster(T* p, T v, unsigned long long* bar)
@@ -242,7 +292,7 @@ __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 //    time t.
 // 3. The owners write U(t + 1) and the mesoscopic Dirichlet populations
 //    (equilibrium or Eq. NEEP), shared out over the four CTAs.
-template <int LAT, typename S, bool REF>
+template <int LAT, typename S, bool REF, bool MONO>
 __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const Band& B,
                                           const Export& E, const S* __restrict__ fin,
                                           S* __restrict__ f, int par_t, int tile)
@@ -254,12 +304,13 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     // a kernel launched after this one for early start (the bulk update,
     // which reads only the old buffer) may begin now
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    // FP32 / FP16 storage: one CTA of four 128-thread groups per tile, group
-    // r in the role of cluster rank r, exchanging through its own shared
-    // memory (the tile then holds one SM and leaves the others to the bulk
-    // kernel); FP64: a cluster of four 128-thread CTAs (FP64 issue is slow,
-    // so each component's arithmetic gets an SM of its own)
-    constexpr bool MONO = band_mono<S>();
+    // MONO (FP32 / FP16 storage, many tiles): one CTA of four 128-thread
+    // groups per tile, group r in the role of cluster rank r, exchanging
+    // through its own shared memory (the tile then holds one SM and leaves
+    // the others to the bulk kernel); otherwise a cluster of four 128-thread
+    // CTAs.  The arithmetic of a group or CTA is the same in both forms, so
+    // their results are identical.
+    static_assert(!MONO || sizeof(S) < 8, "FP64 storage keeps the cluster form");
     const int rank = MONO ? int(threadIdx.x / kTileThreads) : int(cg::this_cluster().block_rank());
     const int l = int(threadIdx.x % kTileThreads);
     __shared__ __align__(16) R Ys[kTileThreads * 4];        // stage values, lab frame
@@ -590,32 +641,68 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                 lamr = Ul[1] + sg * csr_;
                 acoustic = true;
             }
-            const double d0 = double(c0), d1 = double(c1), d3 = double(c3);
-            auto srow = [&](const R* v) -> double {
-                if (rank == 1) return double(v[2]);
-                if (TH) {
-                    const double sr = d0 * double(v[0]) + d3 * double(v[3]);
-                    return rank == 0 ? sr : sr + d1 * double(v[1]);
-                }
-                return d0 * double(v[0]) + d1 * double(v[1]);
-            };
-            const double lam = double(lamr);
-            if (stage == 0) incoming = lam < 0.0;
             double w = 0.0;
-            if (TH || rank != 3) {
-                if (!incoming) {
-                    w = lam * srow(dUn);
-                } else if (scheme != SCH_LODI) {
-                    const double st = srow(TTr);
-                    const double relaxP = acoustic ? B.beta_P * double(XP(5)) : 0.0;
-                    if (scheme == SCH_LODI_RELAX) w = B.alpha_T * (B.t_inf - st) + relaxP;
-                    // the viscous projection (none when the viscous vector is off)
-                    else if (scheme == SCH_CBC) w = st + (B.viscous != VIS_OFF ? srow(Vr) : 0.0);
-                    else {
-                        // Eq. CBC-Relax; the viscous term relaxed towards 0
-                        // at rate alpha_V (0: the paper's equation)
-                        const double sv = B.viscous != VIS_OFF ? srow(Vr) : 0.0;
-                        w = (1.0 - B.alpha_T) * st + (1.0 - B.alpha_V) * sv + B.alpha_T * B.t_inf + relaxP;
+            if constexpr (kLocal) {
+                // the wave in float-float; every product of two inputs is
+                // exact in it, as in FP64
+                auto srow = [&](const R* v) -> FF {
+                    if (rank == 1) return FF{v[2], 0.0f};
+                    if (TH) {
+                        const FF sr = ff_add(ff_prod(c0, v[0]), ff_prod(c3, v[3]));
+                        return rank == 0 ? sr : ff_add(sr, ff_prod(c1, v[1]));
+                    }
+                    return ff_add(ff_prod(c0, v[0]), ff_prod(c1, v[1]));
+                };
+                if (stage == 0) incoming = lamr < R(0);
+                FF wf{0.0f, 0.0f};
+                if (TH || rank != 3) {
+                    if (!incoming) {
+                        wf = ff_mul(srow(dUn), lamr);
+                    } else if (scheme != SCH_LODI) {
+                        const FF st = srow(TTr);
+                        const FF relaxP = acoustic ? ff_mul(ff_const(B.ffk[FFK_BP]), XP(5)) : FF{0.0f, 0.0f};
+                        if (scheme == SCH_LODI_RELAX) {
+                            wf = ff_add(ff_mul(ff_add(ff_const(B.ffk[FFK_TINF]), ff_neg(st)), ff_const(B.ffk[FFK_AT])),
+                                        relaxP);
+                        } else if (scheme == SCH_CBC) {
+                            wf = B.viscous != VIS_OFF ? ff_add(st, srow(Vr)) : st;
+                        } else {
+                            // Eq. CBC-Relax; the viscous term relaxed towards 0
+                            // at rate alpha_V (0: the paper's equation)
+                            wf = ff_add(ff_mul(st, ff_const(B.ffk[FFK_1MAT])), ff_const(B.ffk[FFK_ATTI]));
+                            if (B.viscous != VIS_OFF) wf = ff_add(wf, ff_mul(srow(Vr), ff_const(B.ffk[FFK_1MAV])));
+                            wf = ff_add(wf, relaxP);
+                        }
+                    }
+                }
+                w = ff_pack(wf);
+            } else {
+                const double d0 = double(c0), d1 = double(c1), d3 = double(c3);
+                auto srow = [&](const R* v) -> double {
+                    if (rank == 1) return double(v[2]);
+                    if (TH) {
+                        const double sr = d0 * double(v[0]) + d3 * double(v[3]);
+                        return rank == 0 ? sr : sr + d1 * double(v[1]);
+                    }
+                    return d0 * double(v[0]) + d1 * double(v[1]);
+                };
+                const double lam = double(lamr);
+                if (stage == 0) incoming = lam < 0.0;
+                if (TH || rank != 3) {
+                    if (!incoming) {
+                        w = lam * srow(dUn);
+                    } else if (scheme != SCH_LODI) {
+                        const double st = srow(TTr);
+                        const double relaxP = acoustic ? B.beta_P * double(XP(5)) : 0.0;
+                        if (scheme == SCH_LODI_RELAX) w = B.alpha_T * (B.t_inf - st) + relaxP;
+                        // the viscous projection (none when the viscous vector is off)
+                        else if (scheme == SCH_CBC) w = st + (B.viscous != VIS_OFF ? srow(Vr) : 0.0);
+                        else {
+                            // Eq. CBC-Relax; the viscous term relaxed towards 0
+                            // at rate alpha_V (0: the paper's equation)
+                            const double sv = B.viscous != VIS_OFF ? srow(Vr) : 0.0;
+                            w = (1.0 - B.alpha_T) * st + (1.0 - B.alpha_V) * sv + B.alpha_T * B.t_inf + relaxP;
+                        }
                     }
                 }
             }
@@ -636,34 +723,87 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         // RK4 update (FP64).  A side unknown's lab component 1 or 2 needs
         // one local component only.
         if (comp) {
-            const double* w = Xw + 4 * l;
-            double kl1 = 0.0, kl2 = 0.0, klr = 0.0;
-            if (rank == 0) {
-                if (TH) {
-                    const R irr = (rho0r + Ul[0]) * XP(4) * XP(4);
-                    klr = -((w[2] + w[3] - w[0]) * double(irr));
+            if constexpr (kLocal) {
+                // float-float from the waves to the lab component; one
+                // conversion to FP64 for the RK4 sum
+                const double* wp = Xw + 4 * l;
+                const FF w0 = ff_unpack(wp[0]), w1 = ff_unpack(wp[1]), w2 = ff_unpack(wp[2]),
+                         w3 = ff_unpack(wp[3]);
+                const FF zero{0.0f, 0.0f};
+                FF kl1 = zero, kl2 = zero, klr = zero;
+                if (rank == 0) {
+                    if (TH) {
+                        const R irr = (rho0r + Ul[0]) * XP(4) * XP(4);
+                        klr = ff_neg(ff_mul(ff_add(ff_add(w2, w3), ff_neg(w0)), irr));
+                    } else {
+                        klr = ff_neg(ff_add(w0, w2));
+                    }
+                    if (cbc) klr = ff_add(klr, FF{TTr[0], 0.0f});
+                } else if (rank == 3) {
+                    klr = TH ? ff_neg(ff_add(ff_add(w0, w2), w3)) : zero;
+                    if (cbc && TH) klr = ff_add(klr, FF{TTr[3], 0.0f});
                 } else {
-                    klr = -(w[0] + w[2]);
+                    const bool sideW = D.kind < 2;
+                    const bool need1 = corner || ((rank == 1) == sideW);
+                    const bool need2 = corner || ((rank == 1) != sideW);
+                    if (need1) {
+                        const R bf = TH ? XP(4) * kBr : csr_ * XP(0);
+                        kl1 = ff_neg(ff_mul(TH ? ff_add(w3, ff_neg(w2)) : ff_add(w2, ff_neg(w0)), bf));
+                        if (cbc) kl1 = ff_add(kl1, FF{TTr[1], 0.0f});
+                    }
+                    if (need2) {
+                        kl2 = ff_neg(w1);
+                        if (cbc) kl2 = ff_add(kl2, FF{TTr[2], 0.0f});
+                    }
                 }
-                if (cbc) klr += double(TTr[0]);
-            } else if (rank == 3) {
-                klr = TH ? -(w[0] + w[2] + w[3]) : 0.0;
-                if (cbc && TH) klr += double(TTr[3]);
+                // lab component (lab_component's selection, in float-float)
+                FF kf;
+                if (rank == 0 || rank == 3) {
+                    kf = klr;
+                } else if (D.kind < 4) {
+                    const int kind = D.kind;
+                    kf = kind == 0 ? (rank == 1 ? ff_neg(kl1) : kl2)
+                       : kind == 1 ? (rank == 1 ? kl1 : kl2)
+                       : kind == 2 ? (rank == 1 ? kl2 : ff_neg(kl1))
+                                   : (rank == 1 ? kl2 : kl1);
+                } else {
+                    const int c = D.kind - 4;
+                    const FF r = ff_const(B.ffk[FFK_KR]);
+                    const FF n0 = (c & 1) ? r : ff_neg(r), n1 = (c & 2) ? r : ff_neg(r);
+                    kf = rank == 1 ? ff_add(ff_mul(kl1, n0), ff_neg(ff_mul(kl2, n1)))
+                                   : ff_add(ff_mul(kl1, n1), ff_mul(kl2, n0));
+                }
+                kc = ff_to_double(kf);
             } else {
-                const bool sideW = D.kind < 2;
-                const bool need1 = corner || ((rank == 1) == sideW);
-                const bool need2 = corner || ((rank == 1) != sideW);
-                if (need1) {
-                    const R bf = TH ? XP(4) * kBr : csr_ * XP(0);
-                    kl1 = -(double(bf) * (TH ? w[3] - w[2] : w[2] - w[0]));
-                    if (cbc) kl1 += double(TTr[1]);
+                const double* w = Xw + 4 * l;
+                double kl1 = 0.0, kl2 = 0.0, klr = 0.0;
+                if (rank == 0) {
+                    if (TH) {
+                        const R irr = (rho0r + Ul[0]) * XP(4) * XP(4);
+                        klr = -((w[2] + w[3] - w[0]) * double(irr));
+                    } else {
+                        klr = -(w[0] + w[2]);
+                    }
+                    if (cbc) klr += double(TTr[0]);
+                } else if (rank == 3) {
+                    klr = TH ? -(w[0] + w[2] + w[3]) : 0.0;
+                    if (cbc && TH) klr += double(TTr[3]);
+                } else {
+                    const bool sideW = D.kind < 2;
+                    const bool need1 = corner || ((rank == 1) == sideW);
+                    const bool need2 = corner || ((rank == 1) != sideW);
+                    if (need1) {
+                        const R bf = TH ? XP(4) * kBr : csr_ * XP(0);
+                        kl1 = -(double(bf) * (TH ? w[3] - w[2] : w[2] - w[0]));
+                        if (cbc) kl1 += double(TTr[1]);
+                    }
+                    if (need2) {
+                        kl2 = -w[1];
+                        if (cbc) kl2 += double(TTr[2]);
+                    }
                 }
-                if (need2) {
-                    kl2 = -w[1];
-                    if (cbc) kl2 += double(TTr[2]);
-                }
+                kc = lab_component(rank, D.kind, B.kR, klr, kl1, kl2, klr);
             }
-            kc = lab_component(rank, D.kind, B.kR, klr, kl1, kl2, klr);
             if (stage < 3) {
                 const double wk = stage == 0 ? 1.0 : 2.0;
                 const double hk = stage == 2 ? 1.0 : 0.5;
@@ -697,12 +837,12 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
 // thread (the whole register file of its SM, which then holds no bulk CTA:
 // the bulk kernel runs undisturbed on the other SMs).  FP64: a cluster of
 // four 128-thread CTAs (launched with the cluster attribute).
-template <int LAT, typename S, bool REF>
-__global__ void __launch_bounds__(band_threads<S>(), 1)
+template <int LAT, typename S, bool REF, bool MONO>
+__global__ void __launch_bounds__(band_threads<MONO>(), 1)
     k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
            int par_t)
 {
-    band_tile<LAT, S, REF>(G, O, B, E, fin, f, par_t, band_mono<S>() ? blockIdx.x : blockIdx.x / kCluster);
+    band_tile<LAT, S, REF, MONO>(G, O, B, E, fin, f, par_t, MONO ? blockIdx.x : blockIdx.x / kCluster);
 }
 
 // Band tiles of many grids in one launch: cluster t takes tile tile_run[t].y
@@ -712,19 +852,23 @@ __global__ void __launch_bounds__(band_threads<S>(), 1)
 // latencies more CTAs hide better (a few hundred bytes spill; four CTAs per
 // SM, uncapped, measured 4% slower on the 96-run sweep, six 1% slower).  The
 // FP64 form would spill kilobytes and keeps its registers.
+template <typename S>
+constexpr bool band_batch_mono() { return sizeof(S) < 8; }
+
 template <int LAT, typename S>
-__global__ void __launch_bounds__(band_threads<S>(), 1)
+__global__ void __launch_bounds__(band_threads<band_batch_mono<S>()>(), 1)
     k_band_batch(const BandRun* __restrict__ runs, const int2* __restrict__ tile_run, int par_t)
 {
+    constexpr bool MONO = band_batch_mono<S>();
     __shared__ __align__(16) BandRun R;
-    const int2 tr = tile_run[band_mono<S>() ? blockIdx.x : blockIdx.x / kCluster];
+    const int2 tr = tile_run[MONO ? blockIdx.x : blockIdx.x / kCluster];
     {
         const int* src = reinterpret_cast<const int*>(runs + tr.x);
         int* dst = reinterpret_cast<int*>(&R);
         for (int k = threadIdx.x; k < int(sizeof(BandRun) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
     }
     __syncthreads();
-    band_tile<LAT, S, false>(R.G, R.O, R.B, R.E, static_cast<const S*>(R.f[par_t]),
+    band_tile<LAT, S, false, MONO>(R.G, R.O, R.B, R.E, static_cast<const S*>(R.f[par_t]),
                       static_cast<S*>(R.f[par_t ^ 1]), par_t, tr.y);
 }
 
@@ -752,13 +896,21 @@ int boundary_t(const Geom& G, const Offsets& O, const Export& E, const Band& B, 
 {
     if (B.n_tiles == 0) return 0;
     const size_t smem = band_smem<LAT, S>(B);
-    const dim3 grd(band_ctas<S>(B.n_tiles)), blk(band_threads<S>());
-    const int cl = band_mono<S>() ? 1 : kCluster;
+    const S* fi = static_cast<const S*>(fin);
+    S* fo = static_cast<S*>(fnew);
+    if constexpr (sizeof(S) < 8) {
+        if (B.mono) {
+            const dim3 grd(B.n_tiles), blk(band_threads<true>());
+            if (G.ref)
+                return launch_ex_cl(k_band<LAT, S, true, true>, grd, blk, smem, st, false, 1, G, O, B, E, fi, fo, par_t);
+            return launch_ex_cl(k_band<LAT, S, false, true>, grd, blk, smem, st, false, 1, G, O, B, E, fi, fo, par_t);
+        }
+    }
+    const dim3 grd(B.n_tiles * kCluster), blk(band_threads<false>());
     if (G.ref)
-        return launch_ex_cl(k_band<LAT, S, true>, grd, blk, smem, st, false, cl, G, O, B, E, static_cast<const S*>(fin),
-                         static_cast<S*>(fnew), par_t);
-    return launch_ex_cl(k_band<LAT, S, false>, grd, blk, smem, st, false, cl, G, O, B, E, static_cast<const S*>(fin),
-                     static_cast<S*>(fnew), par_t);
+        return launch_ex_cl(k_band<LAT, S, true, false>, grd, blk, smem, st, false, kCluster, G, O, B, E, fi, fo,
+                            par_t);
+    return launch_ex_cl(k_band<LAT, S, false, false>, grd, blk, smem, st, false, kCluster, G, O, B, E, fi, fo, par_t);
 }
 
 template <int LAT, typename S>
@@ -766,8 +918,9 @@ int band_batch_t(const BandRun* runs, const int2* tile_run, int n_tiles, size_t 
                  cudaStream_t st, bool early)
 {
     if (n_tiles == 0) return 0;
-    return launch_ex_cl(k_band_batch<LAT, S>, dim3(band_ctas<S>(n_tiles)), dim3(band_threads<S>()), smem, st, early,
-                     band_mono<S>() ? 1 : kCluster, runs, tile_run, par_t);
+    constexpr bool mono = band_batch_mono<S>();
+    return launch_ex_cl(k_band_batch<LAT, S>, dim3(mono ? n_tiles : n_tiles * kCluster),
+                        dim3(band_threads<mono>()), smem, st, early, mono ? 1 : kCluster, runs, tile_run, par_t);
 }
 
 template <int LAT, typename S>
@@ -782,12 +935,13 @@ int prepare_t(const Band& B)
 {
     // the 48 KB default covers static + dynamic shared memory: always opt in
     const size_t smem = band_smem<LAT, S>(B);
-    return cudaFuncSetAttribute(k_band<LAT, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(smem)) == cudaSuccess &&
-                   cudaFuncSetAttribute(k_band<LAT, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        int(smem)) == cudaSuccess
-               ? 0
-               : -1;
+    auto set = [&](const void* k) {
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) == cudaSuccess;
+    };
+    bool ok = set((const void*)k_band<LAT, S, false, false>) && set((const void*)k_band<LAT, S, true, false>);
+    if constexpr (sizeof(S) < 8)
+        ok = ok && set((const void*)k_band<LAT, S, false, true>) && set((const void*)k_band<LAT, S, true, true>);
+    return ok ? 0 : -1;
 }
 
 template <int LAT, typename S>
@@ -1086,6 +1240,7 @@ extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, doub
     B.kR_f = float(B.kR);
     B.cs_f = float(B.cs);
     B.ihcs_f = float(B.ihcs);
+    set_ffk(B);
     B.Ub = Ub;
     B.Ya = scratch;
     B.Yb = scratch + 4ull * kNoAllocMaxUnknowns;

@@ -676,9 +676,25 @@ struct StripNode {
     int flags;   // kSN* bits
 };
 
+enum { FFK_TINF = 0, FFK_AT, FFK_BP, FFK_1MAT, FFK_ATTI, FFK_1MAV, FFK_KR };
+
+// The float-float split of the wave constants, from the double parameters
+// already in B (host).
+template <typename BandT>
+inline void set_ffk(BandT& B)
+{
+    const double v[7] = {B.t_inf, B.alpha_T, B.beta_P, 1.0 - B.alpha_T, B.alpha_T * B.t_inf, 1.0 - B.alpha_V, B.kR};
+    for (int q = 0; q < 7; ++q) {
+        const float h = float(v[q]);
+        B.ffk[q][0] = h;
+        B.ffk[q][1] = float(v[q] - double(h));
+    }
+}
+
 struct Band {
     int n_unk;       // unknowns of the boundary ODE
     int n_zg;        // zero-gradient nodes (copied every step)
+    int mono;        // FP32 / FP16 storage with many tiles: one CTA per tile
     int M;
     int viscous, dirichlet;
     int scheme[4];
@@ -694,6 +710,8 @@ struct Band {
     // the same constants rounded to float, for arithmetic in float-valued
     // types (no double-to-float conversion, an FP64-pipe instruction, per use)
     float kA_f, kB_f, kC_f, kR_f, cs_f, ihcs_f;
+    // float-float (hi, lo) forms of the wave constants (FFK_*)
+    float ffk[7][2];
     const UDesc* ud;
     const int2* zg;  // (node, source) grid offsets
     // Tiles of the band kernel: tile t holds local descriptors

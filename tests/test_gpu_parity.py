@@ -247,12 +247,44 @@ def test_d2q37_pulse_256_full_2000_steps_f64(alpha):
     assert_parity(cfg, f, 2000, "f64", ("pulse256", alpha, 2000))
 
 
-def test_d2q37_pulse_256_full_2000_steps_f32_continuous_scheme():
-    """FP32 storage to 1e-5 of the oracle after 2000 steps with alpha_T = 1,
-    where the incoming-wave treatment is continuous at Lambda = u_n = 0."""
+def _conditioning(cfg, f, steps):
+    """The oracle's end state, max |u| over its run, and the FP64 GPU run
+    from fields perturbed by 1e-10 (seeded) against it."""
+    o = oracle.Sim(cfg).init(*f)
+    umax_run = 0.0
+    for _ in range(steps // 50):
+        o.step(50)
+        m = o.macros()
+        umax_run = max(umax_run, np.abs(m[1]).max(), np.abs(m[2]).max())
+    ref = o.macros()
+    rng = np.random.default_rng(5)
+    fp = tuple(a * (1.0 + 1e-10 * rng.standard_normal(a.shape)) if i in (0, 3) else a
+               for i, a in enumerate(f))
+    return ref, umax_run, rel_errors(gpu_run(cfg, fp, steps), ref)
+
+
+def test_d2q37_pulse_256_full_2000_steps_f32_continuous_scheme(capsys):
+    """alpha_T = 1 (the incoming-wave treatment continuous at Lambda = u_n =
+    0), FP32 storage, 2000 steps.  By then the pulse has left and max |u| has
+    fallen to ~5e-3 of its peak, so rel_u of the end state measures the
+    problem's conditioning: the FP64 run from fields perturbed by 1e-10 lies
+    1.4e-3 from the oracle there.  FP32 is held to 1e-5 in rho and T, to
+    1e-5 of max |u| over the run in u (measured 4.9e-8), and its end-state
+    rel_u (measured ~1e-5) below the conditioning figure; both are printed."""
     cfg, f = W.pulse_d2q37(256, alpha_T=1.0, steps=2000, storage="f64")
     cfg["viscous"] = "off"
-    assert_parity(cfg, f, 2000, "f32", ("pulse256", 1.0, 2000))
+    assert_parity(cfg, f, 150, "f32", ("pulse256", 1.0, 150))
+    ref, umax_run, econd = _conditioning(cfg, f, 2000)
+    got32 = gpu_run(dict(cfg, storage="f32"), f, 2000)
+    e32 = rel_errors(got32, ref)
+    du32 = max(np.abs(got32[1] - ref[1]).max(), np.abs(got32[2] - ref[2]).max())
+    with capsys.disabled():
+        print("\nalpha_T = 1, 2000 steps: FP32 rel errors", {k: "%.2e" % v for k, v in e32.items()},
+              "| FP64 with 1e-10 perturbed fields", {k: "%.2e" % v for k, v in econd.items()},
+              "| FP32 |du| / max|u| over the run %.2e" % (du32 / umax_run))
+    assert e32["rho"] < 1e-5 and e32["T"] < 1e-5, e32
+    assert du32 / umax_run < 1e-5, du32 / umax_run
+    assert e32["u"] < econd["u"], (e32, econd)
 
 
 def test_d2q37_pulse_256_f32_switching_scheme(capsys):
@@ -269,20 +301,9 @@ def test_d2q37_pulse_256_f32_switching_scheme(capsys):
     cfg, f = W.pulse_d2q37(256, alpha_T=0.5, steps=2000, storage="f64")
     cfg["viscous"] = "off"
     assert_parity(cfg, f, 150, "f32", ("pulse256", 0.5, 150))
-    # oracle history: max |u| over the run
-    o = oracle.Sim(cfg).init(*f)
-    umax_run = 0.0
-    for _ in range(40):
-        o.step(50)
-        m = o.macros()
-        umax_run = max(umax_run, np.abs(m[1]).max(), np.abs(m[2]).max())
-    ref = o.macros()
+    ref, umax_run, econd = _conditioning(cfg, f, 2000)
     got32 = gpu_run(dict(cfg, storage="f32"), f, 2000)
-    rng = np.random.default_rng(5)
-    fp = tuple(a * (1.0 + 1e-10 * rng.standard_normal(a.shape)) if i in (0, 3) else a
-               for i, a in enumerate(f))
-    got64p = gpu_run(cfg, fp, 2000)
-    e32, econd = rel_errors(got32, ref), rel_errors(got64p, ref)
+    e32 = rel_errors(got32, ref)
     du32 = max(np.abs(got32[1] - ref[1]).max(), np.abs(got32[2] - ref[2]).max())
     with capsys.disabled():
         print("\nalpha_T = 0.5, 2000 steps: FP32 rel errors", {k: "%.2e" % v for k, v in e32.items()},
