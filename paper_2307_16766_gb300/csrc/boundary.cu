@@ -837,8 +837,14 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
 // thread (the whole register file of its SM, which then holds no bulk CTA:
 // the bulk kernel runs undisturbed on the other SMs).  FP64: a cluster of
 // four 128-thread CTAs (launched with the cluster attribute).
+// The cluster form with FP32 / FP16 storage: at most 128 registers, so that
+// a band CTA leaves room for five two-row bulk CTAs on its SM
+// (5 x 128 x 72 + 128 x 128 registers).  The one-CTA form: 512 x 128.
+template <typename S, bool MONO>
+constexpr int band_min_blocks() { return (!MONO && sizeof(S) < 8) ? 4 : 1; }
+
 template <int LAT, typename S, bool REF, bool MONO>
-__global__ void __launch_bounds__(band_threads<MONO>(), 1)
+__global__ void __launch_bounds__(band_threads<MONO>(), band_min_blocks<S, MONO>())
     k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
            int par_t)
 {
