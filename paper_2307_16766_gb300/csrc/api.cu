@@ -241,6 +241,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     G.omega = 1.0 / tau;
     G.omega_f = float(1.0 / tau);
     G.rho0_f = float(p->rho0);
+    G.tau_f = float(tau);
     G.wait_ns = 1000000000ull;
     G.ref = p->u_ref[0] != 0.0 || p->u_ref[1] != 0.0;
     for (int k = 0; k < 2; ++k) {
@@ -532,26 +533,13 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
                       pl.snp.begin() + (size_t)t * B.max_nodes);
         }
     }
-    // With FP32 / FP16 storage, tiles whose clusters would not fit the GPU
-    // at once (four CTAs each) run as one CTA per tile: each then holds a
-    // whole SM and the bulk kernel keeps the others, and the waves of many
-    // tiles are not bound by FP64 issue.  A few tiles keep the cluster form,
-    // whose band is shorter on an otherwise busy GPU.
-    {
-        int sms = 0, dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
-            cudaGetLastError();
-            sms = 152;
-        }
-        B.mono = p->storage != LBM_F64 && B.n_tiles * 4 > sms;
-    }
     B.viscous = p->viscous;
     B.dirichlet = p->dirichlet;
     for (int s = 0; s < 4; ++s) {
         B.scheme[s] = p->scheme[s];
         const double pinf = p->p_inf[s] != 0.0 ? p->p_inf[s] : cs2 * p->rho0;
         B.pdev[s] = pinf - cs2 * p->rho0;
+        B.pdev_f[s] = float(B.pdev[s]);
     }
     B.alpha_T = p->alpha_T;
     B.beta_P = p->beta_P;

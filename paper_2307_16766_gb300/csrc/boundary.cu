@@ -75,7 +75,7 @@ __device__ R vis_meso_c(int c, const Geom& G, const R* SU, const R* SN, const UD
         return R(D.tmode) * R(0.5) * (R(3) * h(0, m) - R(4) * h(3, m) + h(4, m));
     };
     if (c == 3) {
-        const R nu = (R(G.tau) - R(0.5)) * cs2;
+        const R nu = (bconst<R>(G.tau, G.tau_f) - R(0.5)) * cs2;
         const R e1 = dn(5) - dt(6), e2 = dn(6) + dt(5);
         return nu * (R(1) / cs2) * (e1 * e1 + e2 * e2);
     }
@@ -114,7 +114,7 @@ __device__ R vis_fd_c(int c, const Geom& G, const Band& B, const CtxT<R>& X0, co
             d1n[m] = R(0.5) * (A[m] - Bv[m]);
         }
     }
-    const R nu = (R(G.tau) - R(0.5)) * cs2;
+    const R nu = (bconst<R>(G.tau, G.tau_f) - R(0.5)) * cs2;
     if (c == 1) return nu * (dnn[1] + (Tp[1] - R(2) * U[1] + Tm[1]));
     if (c == 2) return nu * (dnn[2] + (Tp[2] - R(2) * U[2] + Tm[2]));
     if (c == 0) return R(2) * nu * (dnn[3] + (Tp[3] - R(2) * U[3] + Tm[3]));
@@ -226,6 +226,12 @@ __device__ __forceinline__ FF ff_unpack(double v)
     return {__int_as_float(__double2hiint(v)), __int_as_float(__double2loint(v))};
 }
 __device__ __forceinline__ FF ff_const(const float (&c)[2]) { return {c[0], c[1]}; }
+__device__ __forceinline__ FF ff_scale(FF x, float p2) { return {x.h * p2, x.l * p2}; }   // p2: a power of 2
+__device__ __forceinline__ FF ff_split(double d)
+{
+    const float h = float(d);
+    return {h, float(d - double(h))};
+}
 
 // v into slot p of every CTA of the cluster, counted on barrier `bar` there
 template <typename T>
@@ -311,8 +317,17 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     // CTAs.  The arithmetic of a group or CTA is the same in both forms, so
     // their results are identical.
     static_assert(!MONO || sizeof(S) < 8, "FP64 storage keeps the cluster form");
-    const int rank = MONO ? int(threadIdx.x / kTileThreads) : int(cg::this_cluster().block_rank());
+    const int grp = MONO ? int(threadIdx.x / kTileThreads) : int(cg::this_cluster().block_rank());
     const int l = int(threadIdx.x % kTileThreads);
+    // MONO: groups 0 and 1 do the strip phase for the tile; meanwhile the
+    // eight warps of groups 2 and 3 run one stage and the Dirichlet write
+    // without effect (no stores, no waits), each warp one part of that code
+    // with its lanes in all four roles, so that the code is in the SM's
+    // instruction caches when the tile reaches it (measured: the first
+    // stage otherwise waits several microseconds on instruction fetch under
+    // the bulk kernel's traffic, and one warp fetching it all in sequence
+    // takes longer than the strip phase).
+    const bool puller = !MONO || grp < 2;
     __shared__ __align__(16) R Ys[kTileThreads * 4];        // stage values, lab frame
     __shared__ __align__(16) R Xp[kTileThreads * 8];        // shares of the system's inputs
     __shared__ __align__(16) double Xw[kTileThreads * 4];   // wave amplitudes
@@ -356,27 +371,35 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     // dependent global round trip costs microseconds.
     const int ns = B.max_nodes;
     const StripNode* snt = B.sn + (long long)tile * ns;
-    // the strip node this thread pulls: node k goes to CTA k % 4, and the
-    // nodes of a CTA are dealt round the four warps
-    const int kp = rank + kCluster * (4 * (l % 32) + l / 32);
-    StripNode Nb{-1, -1, 0, -1, -1, 0};
-    if (kp < ns) Nb = snt[kp];
+    // the strip node this thread pulls: node k goes to CTA k % 4 (MONO:
+    // group k % 2), and the nodes of a CTA (group) are dealt round its four
+    // warps
+    constexpr int kPullStride = MONO ? 2 * kTileThreads : kCluster * kTileThreads;
+    const int kp = MONO ? (grp & 1) + 2 * (4 * (l % 32) + l / 32) : grp + kCluster * (4 * (l % 32) + l / 32);
     // the time-t slots this thread loads: nodes tl, tl + tstride, ...
     // (descriptors of the first kLT issued here, the rest in a loop); every
     // CTA of a cluster loads all of them into its own shared memory
     constexpr int kLT = 3;
-    constexpr int tstride = MONO ? kTileThreads * kCluster : kTileThreads;
+    constexpr int tstride = MONO ? 2 * kTileThreads : kTileThreads;
     const int tl = MONO ? int(threadIdx.x) : l;
-    int tsl[kLT];
+    auto load_desc = [&](StripNode& Nb, int* tsl) {
+        Nb = StripNode{-1, -1, 0, -1, -1, 0};
+        if (puller && kp < ns) Nb = snt[kp];
 #pragma unroll
-    for (int j = 0; j < kLT; ++j) {
-        const int k = tl + j * tstride;
-        tsl[j] = -1;
-        if (k < ns) {
-            const StripNode& N = snt[k];
-            if (N.x >= 0 && (N.flags & kSNLoadT)) tsl[j] = N.tslot;
+        for (int j = 0; j < kLT; ++j) {
+            const int k = tl + j * tstride;
+            tsl[j] = -1;
+            if (puller && k < ns) {
+                const StripNode& N = snt[k];
+                if (N.x >= 0 && (N.flags & kSNLoadT)) tsl[j] = N.tslot;
+            }
         }
-    }
+    };
+    // the cluster form issues them before its cluster barrier; the one-CTA
+    // form at the start of the strip phase (they are dead after it)
+    StripNode NbC;
+    int tslC[kLT];
+    if constexpr (!MONO) load_desc(NbC, tslC);
     const UDesc D = B.ld[(long long)tile * kTileUnknowns + l];
     int nc0 = 0, nc1 = 0, nc2 = 0, nc3 = 0;
     if constexpr (!MONO) {
@@ -392,7 +415,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         nc2 = __syncthreads_count(D.level <= 1);
         nc3 = __syncthreads_count(D.level <= 0);
     }
-    sync_all();                         // every CTA of the cluster runs before any remote store
+    if constexpr (!MONO) sync_all();    // every CTA of the cluster runs before any remote store
 
     // 1. strip nodes: macros of t and moments of t for every CTA; macros of
     //    t + 1 (pull and Eq. macro) by CTA k % kCluster for node k, shared
@@ -449,423 +472,458 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         const double2 a = p[0], b = p[1];
         U0[0] = a.x; U0[1] = a.y; U0[2] = b.x; U0[3] = b.y;
     }
+    // component grp of U(t) (the warm-up pass uses it for any role)
+    const double u0g = grp == 0 ? U0[0] : grp == 1 ? U0[1] : grp == 2 ? U0[2] : U0[3];
+    auto strip = [&](const StripNode& Nb, const int* tsl) {
 #pragma unroll
-    for (int j = 0; j < kLT; ++j)
-        if (tsl[j] >= 0) load_t(tl + j * tstride, tsl[j]);
-    if (Nb.x >= 0 && (Nb.flags & kSNPull)) pull_t1(kp, Nb);
-    for (int k = tl + kLT * tstride; k < ns; k += tstride) {
-        const StripNode N = snt[k];
-        if (N.x >= 0 && (N.flags & kSNLoadT)) load_t(k, N.tslot);
-    }
-    for (int k = kp + kCluster * kTileThreads; k < ns; k += kCluster * kTileThreads) {
-        const StripNode N = snt[k];
-        if (N.x >= 0 && (N.flags & kSNPull)) pull_t1(k, N);
-    }
-    if (lev <= 4 && (!MONO || rank == 0)) {
-#pragma unroll
-        for (int m = 0; m < 4; ++m) Ys[4 * l + m] = R(U0[m]);
-    }
-    sync_all();
-
-    // 2. RK4, component rank of every unknown
-    CtxT<R> X;
-    X.Y = Ys;
-    X.St = SUt;
-    X.St1 = SUt1;
-    const R rho0r = rho0_of<R>(G), cs2r = R(L::CS2), kr = bconst<R>(B.kR, B.kR_f);
-    const R kAr = bconst<R>(B.kA, B.kA_f), kBr = bconst<R>(B.kB, B.kB_f), ihcsr = bconst<R>(B.ihcs, B.ihcs_f),
-            csr_ = bconst<R>(B.cs, B.cs_f);
-    const bool corner = lev <= 4 && D.kind >= 4;
-    const int scheme = corner ? SCH_LODI : (lev <= 4 ? B.scheme[D.kind] : 0);
-    const bool cbc = scheme == SCH_CBC || scheme == SCH_CBC_RELAX;
-    double acc = 0.0, kc = 0.0;         // lab component rank of sum k and of the last k
-    const double u0r = rank == 0 ? U0[0] : rank == 1 ? U0[1] : rank == 2 ? U0[2] : U0[3];
-    bool incoming = false;              // wave rank incoming at time t
-    // In FP32 every CTA forms all inputs of the system itself; in FP64 each
-    // CTA forms a share and the shares are exchanged (FP64 issue is slow).
-    constexpr bool kLocal = sizeof(R) == 4;
-    R xs[8] = {0, 0, 0, 0, 0, 0, 0, 0}; // the inputs, kLocal
-    R Vs[4] = {0, 0, 0, 0};             // viscous vector (local frame, frozen), kLocal
-    bool xok = true;                    // every exchange so far completed in time
-    for (int stage = 0; stage < 4; ++stage) {
-        const bool comp = lev <= 3 - stage;
-        if (!MONO && l == 0) {          // bytes of this stage's two exchanges
-            const unsigned ncomp = unsigned(stage == 0 ? nc0 : stage == 1 ? nc1 : stage == 2 ? nc2 : nc3);
-            expect_bytes(&xbar[stage & 1], unsigned(kCluster * sizeof(double)) * ncomp);
-            expect_bytes(&xbar[2 + (stage & 1)], unsigned(kCluster * sizeof(R)) * ncomp);
+        for (int j = 0; j < kLT; ++j)
+            if (tsl[j] >= 0) load_t(tl + j * tstride, tsl[j]);
+        if (Nb.x >= 0 && (Nb.flags & kSNPull)) pull_t1(kp, Nb);
+        for (int k = tl + kLT * tstride; k < ns; k += tstride) {
+            const StripNode N = snt[k];
+            if (N.x >= 0 && (N.flags & kSNLoadT)) load_t(k, N.tslot);
         }
-        X.frac = stage == 0 ? R(0) : (stage == 3 ? R(1) : R(0.5));
-        R Ul[4] = {0, 0, 0, 0}, dUn[4] = {0, 0, 0, 0};
-        R d_ut = 0;
-        // A: inputs of the system, type R: 1/rho, the transversal terms,
-        // sqrt(theta), 1/sqrt(theta), P - P_inf and d(rho T)/dt (thermal) or
-        // d rho/dt (isothermal)
-        if (comp) {
-            const int kind = D.kind;
-            R A[4], Bv[4], Up[4], Um[4];
-            fetch_local(X, l, kind, kr, Ul);
-            if (corner) {
-                // LODI along the outward diagonal, one-sided difference of
-                // spacing sqrt(2) through the two diagonal bulk nodes
-                fetch_local(X, D.nb[0], kind, kr, A);
-                fetch_local(X, D.nb[1], kind, kr, Bv);
-                const R kC = R(B.kC);
+        for (int k = kp + kPullStride; k < ns; k += kPullStride) {
+            const StripNode N = snt[k];
+            if (N.x >= 0 && (N.flags & kSNPull)) pull_t1(k, N);
+        }
+        if (lev <= 4 && (!MONO || grp == 0)) {
 #pragma unroll
-                for (int m = 0; m < 4; ++m) dUn[m] = (R(3) * Ul[m] - R(4) * A[m] + Bv[m]) * kC;
-#pragma unroll
-                for (int m = 0; m < 4; ++m) Up[m] = Um[m] = R(0);
-            } else {
-                if (D.j == B.M) {        // Eq. FD-dx-bw at the outermost layer
-                    fetch_local(X, D.nb[1], kind, kr, A);
-                    fetch_local(X, D.nb[2], kind, kr, Bv);
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) dUn[m] = R(0.5) * (R(3) * Ul[m] - R(4) * A[m] + Bv[m]);
-                } else {                 // Eq. FD-dx-center at inner layers
+            for (int m = 0; m < 4; ++m) Ys[4 * l + m] = R(U0[m]);
+        }
+    };
+    if constexpr (!MONO) {
+        strip(NbC, tslC);
+        sync_all();
+    }
+
+    // 2. RK4, component rank of every unknown, and 3. the Dirichlet write
+    // (pass 1).  MONO: pass 0 is the strip phase in groups 0 and 1 and the
+    // warm-up in groups 2 and 3, which runs the one copy of this code.
+    static_assert(!MONO || sizeof(R) == 4, "the one-CTA form keeps every input local");
+#pragma unroll 1
+    for (int pass = MONO ? 0 : 1; pass < 2; ++pass) {
+      const bool dry = pass == 0;
+      if (dry && puller) {
+        StripNode Nb;
+        int tsl[kLT];
+        load_desc(Nb, tsl);
+        strip(Nb, tsl);
+      } else {
+        // warm-up: lane roles 0-3, warp parts A, B, C, Dirichlet (4: all)
+        const int rank = dry ? int(threadIdx.x % 4) : grp;
+        const int part = dry ? int(threadIdx.x / 32) % 4 : 4;
+        CtxT<R> X;
+        X.Y = Ys;
+        X.St = SUt;
+        X.St1 = SUt1;
+        const R rho0r = rho0_of<R>(G), cs2r = R(L::CS2), kr = bconst<R>(B.kR, B.kR_f);
+        const R kAr = bconst<R>(B.kA, B.kA_f), kBr = bconst<R>(B.kB, B.kB_f), ihcsr = bconst<R>(B.ihcs, B.ihcs_f),
+                csr_ = bconst<R>(B.cs, B.cs_f);
+        const bool corner = lev <= 4 && D.kind >= 4;
+        const int scheme = corner ? SCH_LODI : (lev <= 4 ? B.scheme[D.kind] : 0);
+        const bool cbc = scheme == SCH_CBC || scheme == SCH_CBC_RELAX;
+        double acc = 0.0, kc = 0.0;         // lab component rank of sum k and of the last k
+        const double u0r = u0g;
+        FF accf{0.0f, 0.0f};                // the same sum in float-float (FP32 / FP16 storage)
+        const FF u0f = ff_split(u0g);
+        bool incoming = false;              // wave rank incoming at time t
+        // In FP32 every CTA forms all inputs of the system itself; in FP64 each
+        // CTA forms a share and the shares are exchanged (FP64 issue is slow).
+        constexpr bool kLocal = sizeof(R) == 4;
+        R xs[8] = {0, 0, 0, 0, 0, 0, 0, 0}; // the inputs, kLocal
+        R Vs[4] = {0, 0, 0, 0};             // viscous vector (local frame, frozen), kLocal
+        bool xok = true;                    // every exchange so far completed in time
+        for (int stage = 0; stage < (dry ? 1 : 4); ++stage) {
+            const bool comp = lev <= 3 - stage;
+            if (!MONO && l == 0) {          // bytes of this stage's two exchanges
+                const unsigned ncomp = unsigned(stage == 0 ? nc0 : stage == 1 ? nc1 : stage == 2 ? nc2 : nc3);
+                expect_bytes(&xbar[stage & 1], unsigned(kCluster * sizeof(double)) * ncomp);
+                expect_bytes(&xbar[2 + (stage & 1)], unsigned(kCluster * sizeof(R)) * ncomp);
+            }
+            X.frac = stage == 0 ? R(0) : (stage == 3 ? R(1) : R(0.5));
+            R Ul[4] = {0, 0, 0, 0}, dUn[4] = {0, 0, 0, 0};
+            R d_ut = 0;
+            // A: inputs of the system, type R: 1/rho, the transversal terms,
+            // sqrt(theta), 1/sqrt(theta), P - P_inf and d(rho T)/dt (thermal) or
+            // d rho/dt (isothermal)
+            if (comp && (part == 4 || part == 0)) {
+                const int kind = D.kind;
+                R A[4], Bv[4], Up[4], Um[4];
+                fetch_local(X, l, kind, kr, Ul);
+                if (corner) {
+                    // LODI along the outward diagonal, one-sided difference of
+                    // spacing sqrt(2) through the two diagonal bulk nodes
                     fetch_local(X, D.nb[0], kind, kr, A);
                     fetch_local(X, D.nb[1], kind, kr, Bv);
+                    const R kC = bconst<R>(B.kC, B.kC_f);
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) dUn[m] = R(0.5) * (A[m] - Bv[m]);
+                    for (int m = 0; m < 4; ++m) dUn[m] = (R(3) * Ul[m] - R(4) * A[m] + Bv[m]) * kC;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) Up[m] = Um[m] = R(0);
+                } else {
+                    if (D.j == B.M) {        // Eq. FD-dx-bw at the outermost layer
+                        fetch_local(X, D.nb[1], kind, kr, A);
+                        fetch_local(X, D.nb[2], kind, kr, Bv);
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) dUn[m] = R(0.5) * (R(3) * Ul[m] - R(4) * A[m] + Bv[m]);
+                    } else {                 // Eq. FD-dx-center at inner layers
+                        fetch_local(X, D.nb[0], kind, kr, A);
+                        fetch_local(X, D.nb[1], kind, kr, Bv);
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) dUn[m] = R(0.5) * (A[m] - Bv[m]);
+                    }
+                    fetch_local(X, D.nb[4], kind, kr, Up);
+                    fetch_local(X, D.nb[5], kind, kr, Um);
                 }
-                fetch_local(X, D.nb[4], kind, kr, Up);
-                fetch_local(X, D.nb[5], kind, kr, Um);
-            }
-            d_ut = R(0.5) * (Up[2] - Um[2]);
-            // share q of the inputs (q = 0..3: entries {0,1}, {2,3},
-            // {4,5,6 isothermal}, {6,7 thermal})
-            auto input = [&](int i) -> R {
-                switch (i) {
-                case 0: return R(1) / (rho0r + Ul[0]);
-                case 1: return corner ? R(0) : R(-0.5) * ((rho0r + Up[0]) * Up[2] - (rho0r + Um[0]) * Um[2]);
-                case 2: return TH ? sqrt_r(R(1) + Ul[3]) : R(0);
-                case 3: return corner ? R(0) : -Ul[2] * (R(0.5) * (Up[1] - Um[1]));
-                case 4: return TH ? rsqrt_r(R(1) + Ul[3]) : R(0);
-                case 5: {
-                    const R dP = TH ? cs2r * (Ul[0] + rho0r * Ul[3] + Ul[0] * Ul[3]) : cs2r * Ul[0];
-                    return corner ? R(0) : dP - R(B.pdev[kind]);
-                }
-                case 6:
-                    // rho T - rho0 = drho + rho0 dT + drho dT
-                    return TH ? R(0.5) * ((Up[0] + rho0r * Up[3] + Up[0] * Up[3]) -
-                                          (Um[0] + rho0r * Um[3] + Um[0] * Um[3]))
-                              : R(0.5) * (Up[0] - Um[0]);
-                default:
-                    return (TH && !corner) ? R(-0.5) * ((R(1) + Up[3]) * Up[2] - (R(1) + Um[3]) * Um[2]) : R(0);
-                }
-            };
-            if constexpr (kLocal) {
+                d_ut = R(0.5) * (Up[2] - Um[2]);
+                // share q of the inputs (q = 0..3: entries {0,1}, {2,3},
+                // {4,5,6 isothermal}, {6,7 thermal})
+                auto input = [&](int i) -> R {
+                    switch (i) {
+                    case 0: return R(1) / (rho0r + Ul[0]);
+                    case 1: return corner ? R(0) : R(-0.5) * ((rho0r + Up[0]) * Up[2] - (rho0r + Um[0]) * Um[2]);
+                    case 2: return TH ? sqrt_r(R(1) + Ul[3]) : R(0);
+                    case 3: return corner ? R(0) : -Ul[2] * (R(0.5) * (Up[1] - Um[1]));
+                    case 4: return TH ? rsqrt_r(R(1) + Ul[3]) : R(0);
+                    case 5: {
+                        const R dP = TH ? cs2r * (Ul[0] + rho0r * Ul[3] + Ul[0] * Ul[3]) : cs2r * Ul[0];
+                        return corner ? R(0) : dP - bconst<R>(B.pdev[kind], B.pdev_f[kind]);
+                    }
+                    case 6:
+                        // rho T - rho0 = drho + rho0 dT + drho dT
+                        return TH ? R(0.5) * ((Up[0] + rho0r * Up[3] + Up[0] * Up[3]) -
+                                              (Um[0] + rho0r * Um[3] + Um[0] * Um[3]))
+                                  : R(0.5) * (Up[0] - Um[0]);
+                    default:
+                        return (TH && !corner) ? R(-0.5) * ((R(1) + Up[3]) * Up[2] - (R(1) + Um[3]) * Um[2]) : R(0);
+                    }
+                };
+                if constexpr (kLocal) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) xs[i] = input(i);
-                if (stage == 0 && !corner) {
-                    if (B.viscous == VIS_FD) {
+                    for (int i = 0; i < 8; ++i) xs[i] = input(i);
+                    if (stage == 0 && !corner) {
+                        if (B.viscous == VIS_FD) {
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) Vs[c] = vis_fd_c<TH, R>(c, G, B, X, D, l, cs2r);
-                    } else if (B.viscous == VIS_MESO) {
+                            for (int c = 0; c < 4; ++c) Vs[c] = vis_fd_c<TH, R>(c, G, B, X, D, l, cs2r);
+                        } else if (B.viscous == VIS_MESO) {
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) Vs[c] = vis_meso_c<TH, R>(c, G, SUt, SNt, D, cs2r);
+                            for (int c = 0; c < 4; ++c) Vs[c] = vis_meso_c<TH, R>(c, G, SUt, SNt, D, cs2r);
+                        }
+                    }
+                } else {
+                    R* xp = Xp + 8 * l;
+                    if (rank == 0) {
+                        bcast(xp + 0, input(0));
+                        bcast(xp + 1, input(1));
+                    } else if (rank == 1) {
+                        if (TH) bcast(xp + 2, input(2));
+                        bcast(xp + 3, input(3));
+                    } else if (rank == 2) {
+                        if (TH) bcast(xp + 4, input(4));
+                        bcast(xp + 5, input(5));
+                        if (!TH) bcast(xp + 6, input(6));
+                    } else if (TH) {
+                        bcast(xp + 6, input(6));
+                        bcast(xp + 7, input(7));
+                    }
+                    if (stage == 0) {
+                        R v = R(0);
+                        if (!corner && B.viscous == VIS_FD) v = vis_fd_c<TH, R>(rank, G, B, X, D, l, cs2r);
+                        else if (!corner && B.viscous == VIS_MESO) v = vis_meso_c<TH, R>(rank, G, SUt, SNt, D, cs2r);
+                        bcast(Xv + 4 * l + rank, v);
                     }
                 }
-            } else {
-                R* xp = Xp + 8 * l;
-                if (rank == 0) {
-                    bcast(xp + 0, input(0));
-                    bcast(xp + 1, input(1));
-                } else if (rank == 1) {
-                    if (TH) bcast(xp + 2, input(2));
-                    bcast(xp + 3, input(3));
-                } else if (rank == 2) {
-                    if (TH) bcast(xp + 4, input(4));
-                    bcast(xp + 5, input(5));
-                    if (!TH) bcast(xp + 6, input(6));
-                } else if (TH) {
-                    bcast(xp + 6, input(6));
-                    bcast(xp + 7, input(7));
+            }
+            if constexpr (!kLocal) sync_all();
+            // B: wave rank, FP64.  Row rank of S (see apply_S) applied to dU/dn,
+            // T and V, with Lambda_rank.
+            auto XP = [&](int i) -> R {
+                if constexpr (kLocal) return xs[i];
+                else return Xp[8 * l + i];
+            };
+            R TTr[4] = {0, 0, 0, 0};        // transversal terms, local frame
+            R Vr[4] = {0, 0, 0, 0};
+            if (comp && (part == 4 || part == 1)) {
+                if (!corner) {
+                    TTr[0] = XP(1);
+                    TTr[1] = XP(3);
+                    TTr[2] = -cs2r * XP(0) * XP(6) - Ul[2] * d_ut;
+                    TTr[3] = TH ? XP(7) : R(0);
                 }
-                if (stage == 0) {
-                    R v = R(0);
-                    if (!corner && B.viscous == VIS_FD) v = vis_fd_c<TH, R>(rank, G, B, X, D, l, cs2r);
-                    else if (!corner && B.viscous == VIS_MESO) v = vis_meso_c<TH, R>(rank, G, SUt, SNt, D, cs2r);
-                    bcast(Xv + 4 * l + rank, v);
+                if constexpr (kLocal) {
+                    Vr[1] = Vs[1];
+                    Vr[2] = Vs[2];
+                    Vr[3] = TH ? Vs[0] + Vs[3] : R(0);      // V0 = 0; V3 from two shares
+                } else {
+                    const R* xv = Xv + 4 * l;
+                    Vr[1] = xv[1];
+                    Vr[2] = xv[2];
+                    Vr[3] = TH ? xv[0] + xv[3] : R(0);
                 }
-            }
-        }
-        if constexpr (!kLocal) sync_all();
-        // B: wave rank, FP64.  Row rank of S (see apply_S) applied to dU/dn,
-        // T and V, with Lambda_rank.
-        auto XP = [&](int i) -> R {
-            if constexpr (kLocal) return xs[i];
-            else return Xp[8 * l + i];
-        };
-        R TTr[4] = {0, 0, 0, 0};        // transversal terms, local frame
-        R Vr[4] = {0, 0, 0, 0};
-        if (comp) {
-            if (!corner) {
-                TTr[0] = XP(1);
-                TTr[1] = XP(3);
-                TTr[2] = -cs2r * XP(0) * XP(6) - Ul[2] * d_ut;
-                TTr[3] = TH ? XP(7) : R(0);
-            }
-            if constexpr (kLocal) {
-                Vr[1] = Vs[1];
-                Vr[2] = Vs[2];
-                Vr[3] = TH ? Vs[0] + Vs[3] : R(0);      // V0 = 0; V3 from two shares
-            } else {
-                const R* xv = Xv + 4 * l;
-                Vr[1] = xv[1];
-                Vr[2] = xv[2];
-                Vr[3] = TH ? xv[0] + xv[3] : R(0);
-            }
-            // Row `rank` of S (see apply_S) and Lambda_rank.  Their entries
-            // are formed from the inputs in type R (the inputs' own
-            // precision) and only the non-zero ones enter the FP64
-            // projections: thermal rows (-r/2, 0, 0, 1/2), (0, 0, 1, 0),
-            // (r/4, -+a, 0, 1/4); isothermal rows (1/2, -+h, 0), (0, 0, 1).
-            R c0 = R(0), c1 = R(0), c3 = R(0), lamr = Ul[1];
-            bool acoustic = false;
-            if (TH) {
-                const R rr = (R(1) + Ul[3]) * XP(0);
-                if (rank == 0) {
-                    c0 = R(-0.5) * rr;
-                    c3 = R(0.5);
-                } else if (rank >= 2) {
-                    const R sg = rank == 2 ? R(-1) : R(1);
-                    c0 = R(0.25) * rr;
-                    c1 = sg * XP(2) * kAr;
-                    c3 = R(0.25);
-                    lamr = Ul[1] + sg * XP(2) * kBr;
+                // Row `rank` of S (see apply_S) and Lambda_rank.  Their entries
+                // are formed from the inputs in type R (the inputs' own
+                // precision) and only the non-zero ones enter the FP64
+                // projections: thermal rows (-r/2, 0, 0, 1/2), (0, 0, 1, 0),
+                // (r/4, -+a, 0, 1/4); isothermal rows (1/2, -+h, 0), (0, 0, 1).
+                R c0 = R(0), c1 = R(0), c3 = R(0), lamr = Ul[1];
+                bool acoustic = false;
+                if (TH) {
+                    const R rr = (R(1) + Ul[3]) * XP(0);
+                    if (rank == 0) {
+                        c0 = R(-0.5) * rr;
+                        c3 = R(0.5);
+                    } else if (rank >= 2) {
+                        const R sg = rank == 2 ? R(-1) : R(1);
+                        c0 = R(0.25) * rr;
+                        c1 = sg * XP(2) * kAr;
+                        c3 = R(0.25);
+                        lamr = Ul[1] + sg * XP(2) * kBr;
+                        acoustic = true;
+                    }
+                } else if (rank == 0 || rank == 2) {
+                    const R sg = rank == 0 ? R(-1) : R(1);
+                    c0 = R(0.5);
+                    c1 = sg * (rho0r + Ul[0]) * ihcsr;
+                    lamr = Ul[1] + sg * csr_;
                     acoustic = true;
                 }
-            } else if (rank == 0 || rank == 2) {
-                const R sg = rank == 0 ? R(-1) : R(1);
-                c0 = R(0.5);
-                c1 = sg * (rho0r + Ul[0]) * ihcsr;
-                lamr = Ul[1] + sg * csr_;
-                acoustic = true;
-            }
-            double w = 0.0;
-            if constexpr (kLocal) {
-                // the wave in float-float; every product of two inputs is
-                // exact in it, as in FP64
-                auto srow = [&](const R* v) -> FF {
-                    if (rank == 1) return FF{v[2], 0.0f};
-                    if (TH) {
-                        const FF sr = ff_add(ff_prod(c0, v[0]), ff_prod(c3, v[3]));
-                        return rank == 0 ? sr : ff_add(sr, ff_prod(c1, v[1]));
+                double w = 0.0;
+                if constexpr (kLocal) {
+                    // the wave in float-float; every product of two inputs is
+                    // exact in it, as in FP64
+                    auto srow = [&](const R* v) -> FF {
+                        if (rank == 1) return FF{v[2], 0.0f};
+                        if (TH) {
+                            const FF sr = ff_add(ff_prod(c0, v[0]), ff_prod(c3, v[3]));
+                            return rank == 0 ? sr : ff_add(sr, ff_prod(c1, v[1]));
+                        }
+                        return ff_add(ff_prod(c0, v[0]), ff_prod(c1, v[1]));
+                    };
+                    if (stage == 0) incoming = lamr < R(0);
+                    FF wf{0.0f, 0.0f};
+                    if (TH || rank != 3) {
+                        if (!incoming) {
+                            wf = ff_mul(srow(dUn), lamr);
+                        } else if (scheme != SCH_LODI) {
+                            const FF st = srow(TTr);
+                            const FF relaxP = acoustic ? ff_mul(ff_const(B.ffk[FFK_BP]), XP(5)) : FF{0.0f, 0.0f};
+                            if (scheme == SCH_LODI_RELAX) {
+                                wf = ff_add(ff_mul(ff_add(ff_const(B.ffk[FFK_TINF]), ff_neg(st)),
+                                                   ff_const(B.ffk[FFK_AT])),
+                                            relaxP);
+                            } else if (scheme == SCH_CBC) {
+                                wf = B.viscous != VIS_OFF ? ff_add(st, srow(Vr)) : st;
+                            } else {
+                                // Eq. CBC-Relax; the viscous term relaxed towards 0
+                                // at rate alpha_V (0: the paper's equation)
+                                wf = ff_add(ff_mul(st, ff_const(B.ffk[FFK_1MAT])), ff_const(B.ffk[FFK_ATTI]));
+                                if (B.viscous != VIS_OFF) wf = ff_add(wf, ff_mul(srow(Vr), ff_const(B.ffk[FFK_1MAV])));
+                                wf = ff_add(wf, relaxP);
+                            }
+                        }
                     }
-                    return ff_add(ff_prod(c0, v[0]), ff_prod(c1, v[1]));
-                };
-                if (stage == 0) incoming = lamr < R(0);
-                FF wf{0.0f, 0.0f};
-                if (TH || rank != 3) {
-                    if (!incoming) {
-                        wf = ff_mul(srow(dUn), lamr);
-                    } else if (scheme != SCH_LODI) {
-                        const FF st = srow(TTr);
-                        const FF relaxP = acoustic ? ff_mul(ff_const(B.ffk[FFK_BP]), XP(5)) : FF{0.0f, 0.0f};
-                        if (scheme == SCH_LODI_RELAX) {
-                            wf = ff_add(ff_mul(ff_add(ff_const(B.ffk[FFK_TINF]), ff_neg(st)), ff_const(B.ffk[FFK_AT])),
-                                        relaxP);
-                        } else if (scheme == SCH_CBC) {
-                            wf = B.viscous != VIS_OFF ? ff_add(st, srow(Vr)) : st;
+                    w = ff_pack(wf);
+                } else {
+                    const double d0 = double(c0), d1 = double(c1), d3 = double(c3);
+                    auto srow = [&](const R* v) -> double {
+                        if (rank == 1) return double(v[2]);
+                        if (TH) {
+                            const double sr = d0 * double(v[0]) + d3 * double(v[3]);
+                            return rank == 0 ? sr : sr + d1 * double(v[1]);
+                        }
+                        return d0 * double(v[0]) + d1 * double(v[1]);
+                    };
+                    const double lam = double(lamr);
+                    if (stage == 0) incoming = lam < 0.0;
+                    if (TH || rank != 3) {
+                        if (!incoming) {
+                            w = lam * srow(dUn);
+                        } else if (scheme != SCH_LODI) {
+                            const double st = srow(TTr);
+                            const double relaxP = acoustic ? B.beta_P * double(XP(5)) : 0.0;
+                            if (scheme == SCH_LODI_RELAX) w = B.alpha_T * (B.t_inf - st) + relaxP;
+                            // the viscous projection (none when the viscous vector is off)
+                            else if (scheme == SCH_CBC) w = st + (B.viscous != VIS_OFF ? srow(Vr) : 0.0);
+                            else {
+                                // Eq. CBC-Relax; the viscous term relaxed towards 0
+                                // at rate alpha_V (0: the paper's equation)
+                                const double sv = B.viscous != VIS_OFF ? srow(Vr) : 0.0;
+                                w = (1.0 - B.alpha_T) * st + (1.0 - B.alpha_V) * sv + B.alpha_T * B.t_inf + relaxP;
+                            }
+                        }
+                    }
+                }
+                if (!dry) xput(Xw + 4 * l + rank, w, &xbar[stage & 1]);
+                // the transversal and viscous terms this CTA adds in step C
+                if (cbc) {
+                    if (rank == 3) {
+                        TTr[3] += Vr[3];
+                    } else if (rank != 0) {         // V0 = 0
+                        TTr[1] += Vr[1];
+                        TTr[2] += Vr[2];
+                    }
+                }
+            }
+            if (xok && !dry) xok = xwait(&xbar[stage & 1], (stage >> 1) & 1);
+            // C: lab component rank of the right-hand side (S^-1 of the waves,
+            // with r^-1 = rho / theta, b = sqrt(2 c_s^4 / T~) formed in type R);
+            // RK4 update (FP64).  A side unknown's lab component 1 or 2 needs
+            // one local component only.
+            if (comp && (part == 4 || part == 2)) {
+                if constexpr (kLocal) {
+                    // float-float from the waves to the lab component; one
+                    // conversion to FP64 for the RK4 sum
+                    const double* wp = Xw + 4 * l;
+                    const FF w0 = ff_unpack(wp[0]), w1 = ff_unpack(wp[1]), w2 = ff_unpack(wp[2]),
+                             w3 = ff_unpack(wp[3]);
+                    const FF zero{0.0f, 0.0f};
+                    FF kl1 = zero, kl2 = zero, klr = zero;
+                    if (rank == 0) {
+                        if (TH) {
+                            const R irr = (rho0r + Ul[0]) * XP(4) * XP(4);
+                            klr = ff_neg(ff_mul(ff_add(ff_add(w2, w3), ff_neg(w0)), irr));
                         } else {
-                            // Eq. CBC-Relax; the viscous term relaxed towards 0
-                            // at rate alpha_V (0: the paper's equation)
-                            wf = ff_add(ff_mul(st, ff_const(B.ffk[FFK_1MAT])), ff_const(B.ffk[FFK_ATTI]));
-                            if (B.viscous != VIS_OFF) wf = ff_add(wf, ff_mul(srow(Vr), ff_const(B.ffk[FFK_1MAV])));
-                            wf = ff_add(wf, relaxP);
+                            klr = ff_neg(ff_add(w0, w2));
+                        }
+                        if (cbc) klr = ff_add(klr, FF{TTr[0], 0.0f});
+                    } else if (rank == 3) {
+                        klr = TH ? ff_neg(ff_add(ff_add(w0, w2), w3)) : zero;
+                        if (cbc && TH) klr = ff_add(klr, FF{TTr[3], 0.0f});
+                    } else {
+                        const bool sideW = D.kind < 2;
+                        const bool need1 = corner || ((rank == 1) == sideW);
+                        const bool need2 = corner || ((rank == 1) != sideW);
+                        if (need1) {
+                            const R bf = TH ? XP(4) * kBr : csr_ * XP(0);
+                            kl1 = ff_neg(ff_mul(TH ? ff_add(w3, ff_neg(w2)) : ff_add(w2, ff_neg(w0)), bf));
+                            if (cbc) kl1 = ff_add(kl1, FF{TTr[1], 0.0f});
+                        }
+                        if (need2) {
+                            kl2 = ff_neg(w1);
+                            if (cbc) kl2 = ff_add(kl2, FF{TTr[2], 0.0f});
+                        }
+                    }
+                    // lab component (lab_component's selection, in float-float)
+                    FF kf;
+                    if (rank == 0 || rank == 3) {
+                        kf = klr;
+                    } else if (D.kind < 4) {
+                        const int kind = D.kind;
+                        kf = kind == 0 ? (rank == 1 ? ff_neg(kl1) : kl2)
+                           : kind == 1 ? (rank == 1 ? kl1 : kl2)
+                           : kind == 2 ? (rank == 1 ? kl2 : ff_neg(kl1))
+                                       : (rank == 1 ? kl2 : kl1);
+                    } else {
+                        const int c = D.kind - 4;
+                        const FF r = ff_const(B.ffk[FFK_KR]);
+                        const FF n0 = (c & 1) ? r : ff_neg(r), n1 = (c & 2) ? r : ff_neg(r);
+                        kf = rank == 1 ? ff_add(ff_mul(kl1, n0), ff_neg(ff_mul(kl2, n1)))
+                                       : ff_add(ff_mul(kl1, n1), ff_mul(kl2, n0));
+                    }
+                    // RK4 (sum and stage value) in float-float as well: no
+                    // FP64 instruction in the stage loop
+                    if (stage < 3) {
+                        const FF k2 = stage == 0 ? kf : ff_scale(kf, 2.0f);
+                        accf = stage == 0 ? k2 : ff_add(accf, k2);
+                        const FF y = ff_add(u0f, ff_scale(kf, stage == 2 ? 1.0f : 0.5f));
+                        if (!dry) xput(Ys + 4 * l + rank, y.h, &xbar[2 + (stage & 1)]);
+                    } else {
+                        // RK4: U(t + 1) = U(t) + (k1 + 2 k2 + 2 k3 + k4) / 6
+                        const FF un = ff_add(u0f, ff_mul(ff_add(accf, kf), ff_const(B.ffk[FFK_SIXTH])));
+                        if (!dry) {
+                            B.Ub[((long long)(par_t ^ 1) * B.n_unk + D.gid) * 4 + rank] = ff_to_double(un);
+                            xput(Ys + 4 * l + rank, un.h, &xbar[2 + (stage & 1)]);
+                        }
+                    }
+                } else {
+                    const double* w = Xw + 4 * l;
+                    double kl1 = 0.0, kl2 = 0.0, klr = 0.0;
+                    if (rank == 0) {
+                        if (TH) {
+                            const R irr = (rho0r + Ul[0]) * XP(4) * XP(4);
+                            klr = -((w[2] + w[3] - w[0]) * double(irr));
+                        } else {
+                            klr = -(w[0] + w[2]);
+                        }
+                        if (cbc) klr += double(TTr[0]);
+                    } else if (rank == 3) {
+                        klr = TH ? -(w[0] + w[2] + w[3]) : 0.0;
+                        if (cbc && TH) klr += double(TTr[3]);
+                    } else {
+                        const bool sideW = D.kind < 2;
+                        const bool need1 = corner || ((rank == 1) == sideW);
+                        const bool need2 = corner || ((rank == 1) != sideW);
+                        if (need1) {
+                            const R bf = TH ? XP(4) * kBr : csr_ * XP(0);
+                            kl1 = -(double(bf) * (TH ? w[3] - w[2] : w[2] - w[0]));
+                            if (cbc) kl1 += double(TTr[1]);
+                        }
+                        if (need2) {
+                            kl2 = -w[1];
+                            if (cbc) kl2 += double(TTr[2]);
+                        }
+                    }
+                    kc = lab_component(rank, D.kind, B.kR, klr, kl1, kl2, klr);
+                    if (stage < 3) {
+                        const double wk = stage == 0 ? 1.0 : 2.0;
+                        const double hk = stage == 2 ? 1.0 : 0.5;
+                        acc = (stage == 0 ? 0.0 : acc) + wk * kc;
+                        if (!dry) xput(Ys + 4 * l + rank, R(u0r + hk * kc), &xbar[2 + (stage & 1)]);
+                    } else {
+                        // RK4: U(t + 1) = U(t) + (k1 + 2 k2 + 2 k3 + k4) / 6
+                        const double un = u0r + (acc + kc) * (1.0 / 6.0);
+                        if (!dry) {
+                            B.Ub[((long long)(par_t ^ 1) * B.n_unk + D.gid) * 4 + rank] = un;
+                            xput(Ys + 4 * l + rank, R(un), &xbar[2 + (stage & 1)]);
                         }
                     }
                 }
-                w = ff_pack(wf);
-            } else {
-                const double d0 = double(c0), d1 = double(c1), d3 = double(c3);
-                auto srow = [&](const R* v) -> double {
-                    if (rank == 1) return double(v[2]);
-                    if (TH) {
-                        const double sr = d0 * double(v[0]) + d3 * double(v[3]);
-                        return rank == 0 ? sr : sr + d1 * double(v[1]);
-                    }
-                    return d0 * double(v[0]) + d1 * double(v[1]);
-                };
-                const double lam = double(lamr);
-                if (stage == 0) incoming = lam < 0.0;
-                if (TH || rank != 3) {
-                    if (!incoming) {
-                        w = lam * srow(dUn);
-                    } else if (scheme != SCH_LODI) {
-                        const double st = srow(TTr);
-                        const double relaxP = acoustic ? B.beta_P * double(XP(5)) : 0.0;
-                        if (scheme == SCH_LODI_RELAX) w = B.alpha_T * (B.t_inf - st) + relaxP;
-                        // the viscous projection (none when the viscous vector is off)
-                        else if (scheme == SCH_CBC) w = st + (B.viscous != VIS_OFF ? srow(Vr) : 0.0);
-                        else {
-                            // Eq. CBC-Relax; the viscous term relaxed towards 0
-                            // at rate alpha_V (0: the paper's equation)
-                            const double sv = B.viscous != VIS_OFF ? srow(Vr) : 0.0;
-                            w = (1.0 - B.alpha_T) * st + (1.0 - B.alpha_V) * sv + B.alpha_T * B.t_inf + relaxP;
-                        }
-                    }
-                }
             }
-            xput(Xw + 4 * l + rank, w, &xbar[stage & 1]);
-            // the transversal and viscous terms this CTA adds in step C
-            if (cbc) {
-                if (rank == 3) {
-                    TTr[3] += Vr[3];
-                } else if (rank != 0) {         // V0 = 0
-                    TTr[1] += Vr[1];
-                    TTr[2] += Vr[2];
-                }
-            }
+            if (xok && !dry) xok = xwait(&xbar[2 + (stage & 1)], (stage >> 1) & 1);
         }
-        if (xok) xok = xwait(&xbar[stage & 1], (stage >> 1) & 1);
-        // C: lab component rank of the right-hand side (S^-1 of the waves,
-        // with r^-1 = rho / theta, b = sqrt(2 c_s^4 / T~) formed in type R);
-        // RK4 update (FP64).  A side unknown's lab component 1 or 2 needs
-        // one local component only.
-        if (comp) {
-            if constexpr (kLocal) {
-                // float-float from the waves to the lab component; one
-                // conversion to FP64 for the RK4 sum
-                const double* wp = Xw + 4 * l;
-                const FF w0 = ff_unpack(wp[0]), w1 = ff_unpack(wp[1]), w2 = ff_unpack(wp[2]),
-                         w3 = ff_unpack(wp[3]);
-                const FF zero{0.0f, 0.0f};
-                FF kl1 = zero, kl2 = zero, klr = zero;
-                if (rank == 0) {
-                    if (TH) {
-                        const R irr = (rho0r + Ul[0]) * XP(4) * XP(4);
-                        klr = ff_neg(ff_mul(ff_add(ff_add(w2, w3), ff_neg(w0)), irr));
-                    } else {
-                        klr = ff_neg(ff_add(w0, w2));
-                    }
-                    if (cbc) klr = ff_add(klr, FF{TTr[0], 0.0f});
-                } else if (rank == 3) {
-                    klr = TH ? ff_neg(ff_add(ff_add(w0, w2), w3)) : zero;
-                    if (cbc && TH) klr = ff_add(klr, FF{TTr[3], 0.0f});
-                } else {
-                    const bool sideW = D.kind < 2;
-                    const bool need1 = corner || ((rank == 1) == sideW);
-                    const bool need2 = corner || ((rank == 1) != sideW);
-                    if (need1) {
-                        const R bf = TH ? XP(4) * kBr : csr_ * XP(0);
-                        kl1 = ff_neg(ff_mul(TH ? ff_add(w3, ff_neg(w2)) : ff_add(w2, ff_neg(w0)), bf));
-                        if (cbc) kl1 = ff_add(kl1, FF{TTr[1], 0.0f});
-                    }
-                    if (need2) {
-                        kl2 = ff_neg(w1);
-                        if (cbc) kl2 = ff_add(kl2, FF{TTr[2], 0.0f});
-                    }
-                }
-                // lab component (lab_component's selection, in float-float)
-                FF kf;
-                if (rank == 0 || rank == 3) {
-                    kf = klr;
-                } else if (D.kind < 4) {
-                    const int kind = D.kind;
-                    kf = kind == 0 ? (rank == 1 ? ff_neg(kl1) : kl2)
-                       : kind == 1 ? (rank == 1 ? kl1 : kl2)
-                       : kind == 2 ? (rank == 1 ? kl2 : ff_neg(kl1))
-                                   : (rank == 1 ? kl2 : kl1);
-                } else {
-                    const int c = D.kind - 4;
-                    const FF r = ff_const(B.ffk[FFK_KR]);
-                    const FF n0 = (c & 1) ? r : ff_neg(r), n1 = (c & 2) ? r : ff_neg(r);
-                    kf = rank == 1 ? ff_add(ff_mul(kl1, n0), ff_neg(ff_mul(kl2, n1)))
-                                   : ff_add(ff_mul(kl1, n1), ff_mul(kl2, n0));
-                }
-                kc = ff_to_double(kf);
-            } else {
-                const double* w = Xw + 4 * l;
-                double kl1 = 0.0, kl2 = 0.0, klr = 0.0;
-                if (rank == 0) {
-                    if (TH) {
-                        const R irr = (rho0r + Ul[0]) * XP(4) * XP(4);
-                        klr = -((w[2] + w[3] - w[0]) * double(irr));
-                    } else {
-                        klr = -(w[0] + w[2]);
-                    }
-                    if (cbc) klr += double(TTr[0]);
-                } else if (rank == 3) {
-                    klr = TH ? -(w[0] + w[2] + w[3]) : 0.0;
-                    if (cbc && TH) klr += double(TTr[3]);
-                } else {
-                    const bool sideW = D.kind < 2;
-                    const bool need1 = corner || ((rank == 1) == sideW);
-                    const bool need2 = corner || ((rank == 1) != sideW);
-                    if (need1) {
-                        const R bf = TH ? XP(4) * kBr : csr_ * XP(0);
-                        kl1 = -(double(bf) * (TH ? w[3] - w[2] : w[2] - w[0]));
-                        if (cbc) kl1 += double(TTr[1]);
-                    }
-                    if (need2) {
-                        kl2 = -w[1];
-                        if (cbc) kl2 += double(TTr[2]);
-                    }
-                }
-                kc = lab_component(rank, D.kind, B.kR, klr, kl1, kl2, klr);
-            }
-            if (stage < 3) {
-                const double wk = stage == 0 ? 1.0 : 2.0;
-                const double hk = stage == 2 ? 1.0 : 0.5;
-                acc = (stage == 0 ? 0.0 : acc) + wk * kc;
-                xput(Ys + 4 * l + rank, R(u0r + hk * kc), &xbar[2 + (stage & 1)]);
-            } else {
-                // RK4: U(t + 1) = U(t) + (k1 + 2 k2 + 2 k3 + k4) / 6
-                const double un = u0r + (acc + kc) * (1.0 / 6.0);
-                B.Ub[((long long)(par_t ^ 1) * B.n_unk + D.gid) * 4 + rank] = un;
-                xput(Ys + 4 * l + rank, R(un), &xbar[2 + (stage & 1)]);
-            }
-        }
-        if (xok) xok = xwait(&xbar[2 + (stage & 1)], (stage >> 1) & 1);
-    }
 
-    // 3. Dirichlet populations of unknown l, on CTA l % kCluster
-    if (lev == 0 && l % kCluster == rank) {
-        const R Unew[4] = {Ys[4 * l], Ys[4 * l + 1], Ys[4 * l + 2], Ys[4 * l + 3]};
-        const bool neep = B.dirichlet >= 1;     // needs x_f: NEEP or regularised NEEP
-        const S* fs = nullptr;
-        if (neep) {
-            if constexpr (MONO) fs = Fx + D.wsrc * L::Q;
-            else fs = cg::this_cluster().map_shared_rank(Fx + D.wsrc * L::Q, D.wslot % kCluster);
+        // 3. Dirichlet populations of unknown l, on CTA l % kCluster
+        if (lev == 0 && l % kCluster == rank && (part == 4 || part == 3)) {
+            const R Unew[4] = {Ys[4 * l], Ys[4 * l + 1], Ys[4 * l + 2], Ys[4 * l + 3]};
+            const bool neep = B.dirichlet >= 1;     // needs x_f: NEEP or regularised NEEP
+            const S* fs = nullptr;
+            if (neep) {
+                if constexpr (MONO) fs = Fx + D.wsrc * L::Q;
+                else fs = cg::this_cluster().map_shared_rank(Fx + D.wsrc * L::Q, D.wslot % kCluster);
+            }
+            dirichlet<LAT, S, R, REF>(G, B, f, neep ? SUt1 + 4 * D.wslot : nullptr, fs, D, Unew, dry);
         }
-        dirichlet<LAT, S, R, REF>(G, B, f, neep ? SUt1 + 4 * D.wslot : nullptr, fs, D, Unew);
+      }
+      if (dry) sync_all();              // the strip phase (and the warm-up) are complete
     }
     if constexpr (!MONO) cg::this_cluster().sync();   // no CTA leaves while its Fx may be read
 }
 
-// FP32 / FP16 storage: one 512-thread CTA per tile, at most 128 registers a
-// thread (the whole register file of its SM, which then holds no bulk CTA:
-// the bulk kernel runs undisturbed on the other SMs).  FP64: a cluster of
-// four 128-thread CTAs (launched with the cluster attribute).
-// The cluster form with FP32 / FP16 storage: at most 128 registers, so that
-// a band CTA leaves room for five two-row bulk CTAs on its SM
-// (5 x 128 x 72 + 128 x 128 registers).  The one-CTA form: 512 x 128.
-template <typename S, bool MONO>
-constexpr int band_min_blocks() { return (!MONO && sizeof(S) < 8) ? 4 : 1; }
+// The tile form by storage.  FP32 / FP16: one 512-thread CTA per tile, at
+// most 128 registers a thread (the whole register file of its SM, which
+// then holds no bulk CTA: the bulk kernel runs undisturbed on the other
+// SMs).  FP64: a cluster of four 128-thread CTAs (launched with the cluster
+// attribute), its FP64 wave arithmetic spread over four SMs.
+template <typename S>
+constexpr bool band_mono() { return sizeof(S) < 8; }
 
 template <int LAT, typename S, bool REF, bool MONO>
-__global__ void __launch_bounds__(band_threads<MONO>(), band_min_blocks<S, MONO>())
+__global__ void __launch_bounds__(band_threads<MONO>(), 1)
     k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
            int par_t)
 {
     band_tile<LAT, S, REF, MONO>(G, O, B, E, fin, f, par_t, MONO ? blockIdx.x : blockIdx.x / kCluster);
 }
 
-// Band tiles of many grids in one launch: cluster t takes tile tile_run[t].y
-// of run tile_run[t].x, whose structures it copies to shared memory first.
-// With FP32 / FP16 storage its registers are capped so that five CTAs share
-// an SM: a batch's many tiles run in waves whose FP64 issue and exchange
-// latencies more CTAs hide better (a few hundred bytes spill; four CTAs per
-// SM, uncapped, measured 4% slower on the 96-run sweep, six 1% slower).  The
-// FP64 form would spill kilobytes and keeps its registers.
-template <typename S>
-constexpr bool band_batch_mono() { return sizeof(S) < 8; }
-
+// Band tiles of many grids in one launch: CTA (cluster) t takes tile
+// tile_run[t].y of run tile_run[t].x, whose structures it copies to shared
+// memory first; the tile form as in k_band.
 template <int LAT, typename S>
-__global__ void __launch_bounds__(band_threads<band_batch_mono<S>()>(), 1)
+__global__ void __launch_bounds__(band_threads<band_mono<S>()>(), 1)
     k_band_batch(const BandRun* __restrict__ runs, const int2* __restrict__ tile_run, int par_t)
 {
-    constexpr bool MONO = band_batch_mono<S>();
+    constexpr bool MONO = band_mono<S>();
     __shared__ __align__(16) BandRun R;
     const int2 tr = tile_run[MONO ? blockIdx.x : blockIdx.x / kCluster];
     {
@@ -904,19 +962,12 @@ int boundary_t(const Geom& G, const Offsets& O, const Export& E, const Band& B, 
     const size_t smem = band_smem<LAT, S>(B);
     const S* fi = static_cast<const S*>(fin);
     S* fo = static_cast<S*>(fnew);
-    if constexpr (sizeof(S) < 8) {
-        if (B.mono) {
-            const dim3 grd(B.n_tiles), blk(band_threads<true>());
-            if (G.ref)
-                return launch_ex_cl(k_band<LAT, S, true, true>, grd, blk, smem, st, false, 1, G, O, B, E, fi, fo, par_t);
-            return launch_ex_cl(k_band<LAT, S, false, true>, grd, blk, smem, st, false, 1, G, O, B, E, fi, fo, par_t);
-        }
-    }
-    const dim3 grd(B.n_tiles * kCluster), blk(band_threads<false>());
+    constexpr bool mono = band_mono<S>();
+    constexpr int ncl = mono ? 1 : kCluster;
+    const dim3 grd(B.n_tiles * ncl), blk(band_threads<mono>());
     if (G.ref)
-        return launch_ex_cl(k_band<LAT, S, true, false>, grd, blk, smem, st, false, kCluster, G, O, B, E, fi, fo,
-                            par_t);
-    return launch_ex_cl(k_band<LAT, S, false, false>, grd, blk, smem, st, false, kCluster, G, O, B, E, fi, fo, par_t);
+        return launch_ex_cl(k_band<LAT, S, true, mono>, grd, blk, smem, st, false, ncl, G, O, B, E, fi, fo, par_t);
+    return launch_ex_cl(k_band<LAT, S, false, mono>, grd, blk, smem, st, false, ncl, G, O, B, E, fi, fo, par_t);
 }
 
 template <int LAT, typename S>
@@ -924,7 +975,7 @@ int band_batch_t(const BandRun* runs, const int2* tile_run, int n_tiles, size_t 
                  cudaStream_t st, bool early)
 {
     if (n_tiles == 0) return 0;
-    constexpr bool mono = band_batch_mono<S>();
+    constexpr bool mono = band_mono<S>();
     return launch_ex_cl(k_band_batch<LAT, S>, dim3(mono ? n_tiles : n_tiles * kCluster),
                         dim3(band_threads<mono>()), smem, st, early, mono ? 1 : kCluster, runs, tile_run, par_t);
 }
@@ -944,9 +995,8 @@ int prepare_t(const Band& B)
     auto set = [&](const void* k) {
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) == cudaSuccess;
     };
-    bool ok = set((const void*)k_band<LAT, S, false, false>) && set((const void*)k_band<LAT, S, true, false>);
-    if constexpr (sizeof(S) < 8)
-        ok = ok && set((const void*)k_band<LAT, S, false, true>) && set((const void*)k_band<LAT, S, true, true>);
+    constexpr bool mono = band_mono<S>();
+    const bool ok = set((const void*)k_band<LAT, S, false, mono>) && set((const void*)k_band<LAT, S, true, mono>);
     return ok ? 0 : -1;
 }
 
@@ -1220,6 +1270,7 @@ extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, doub
     G.tau = tau;
     G.rho0 = p->rho0;
     G.rho0_f = float(p->rho0);
+    G.tau_f = float(tau);
     G.wait_ns = 1000000000ull;
     G.omega = 1.0 / tau;
     G.omega_f = float(G.omega);
@@ -1234,6 +1285,7 @@ extern "C" int lbm_cbc_side_step_noalloc(int lattice, int side, int length, doub
     B.alpha_V = p->alpha_V;
     const double pinf = p->p_inf[side] != 0.0 ? p->p_inf[side] : cs2 * p->rho0;
     B.pdev[side] = pinf - cs2 * p->rho0;
+    B.pdev_f[side] = float(B.pdev[side]);
     B.kA = 1.0 / std::sqrt(8.0 * cs2);
     B.kB = std::sqrt(2.0 * cs2);
     B.kC = 1.0 / (2.0 * std::sqrt(2.0));

@@ -434,8 +434,10 @@ __device__ void unknown_rhs(const Geom& G, const Band& B, const Relax<T>& P, con
 // Computed in the arithmetic type of the storage.
 template <int LAT, typename S, typename R, bool REF = true>
 __device__ void dirichlet(const Geom& G, const Band& B, S* f, const R* Us, const S* fsrc,
-                          const UDesc& D, const R* Unew)
+                          const UDesc& D, const R* Unew, bool dry = false)
 {
+    // dry: the same instructions without the stores (instruction-cache
+    // warm-up)
     // Us: macros of x_f at t + 1; fsrc: its stored post-collision
     // populations, indexed by velocity (both read only for Eq. NEEP)
     using L = Lat<LAT>;
@@ -523,7 +525,7 @@ __device__ void dirichlet(const Geom& G, const Band& B, S* f, const R* Us, const
             for (int i = 0; i < L::Q; ++i) {
                 Cm v = ge[i];
                 if (Store<S>::SCALED) v *= Cm(1.0 / L::w(i));
-                Store<S>::put(f + L::plane_of(i) * G.plane + node, v);
+                if (!dry) Store<S>::put(f + L::plane_of(i) * G.plane + node, v);
             }
         }
 }

@@ -544,7 +544,7 @@ struct Geom {
     int bx0, bx1, by0, by1;     // bulk nodes: [bx0, bx1) x [by0, by1)
     long long plane;            // ny * nxp
     double tau, rho0, omega;    // omega = 1 / tau
-    float omega_f, rho0_f;
+    float omega_f, rho0_f, tau_f;
     unsigned long long wait_ns; // limit of the bulk kernel's first wait for a tensor copy
     // populations held relative to f^eq(rho0, uref, T0) (ref != 0) instead
     // of w rho0; uref rounded to float for float-valued arithmetic
@@ -676,15 +676,16 @@ struct StripNode {
     int flags;   // kSN* bits
 };
 
-enum { FFK_TINF = 0, FFK_AT, FFK_BP, FFK_1MAT, FFK_ATTI, FFK_1MAV, FFK_KR };
+enum { FFK_TINF = 0, FFK_AT, FFK_BP, FFK_1MAT, FFK_ATTI, FFK_1MAV, FFK_KR, FFK_SIXTH, FFK_N };
 
 // The float-float split of the wave constants, from the double parameters
 // already in B (host).
 template <typename BandT>
 inline void set_ffk(BandT& B)
 {
-    const double v[7] = {B.t_inf, B.alpha_T, B.beta_P, 1.0 - B.alpha_T, B.alpha_T * B.t_inf, 1.0 - B.alpha_V, B.kR};
-    for (int q = 0; q < 7; ++q) {
+    const double v[FFK_N] = {B.t_inf, B.alpha_T, B.beta_P, 1.0 - B.alpha_T, B.alpha_T * B.t_inf, 1.0 - B.alpha_V,
+                             B.kR, 1.0 / 6.0};
+    for (int q = 0; q < FFK_N; ++q) {
         const float h = float(v[q]);
         B.ffk[q][0] = h;
         B.ffk[q][1] = float(v[q] - double(h));
@@ -694,7 +695,6 @@ inline void set_ffk(BandT& B)
 struct Band {
     int n_unk;       // unknowns of the boundary ODE
     int n_zg;        // zero-gradient nodes (copied every step)
-    int mono;        // FP32 / FP16 storage with many tiles: one CTA per tile
     int M;
     int viscous, dirichlet;
     int scheme[4];
@@ -710,8 +710,9 @@ struct Band {
     // the same constants rounded to float, for arithmetic in float-valued
     // types (no double-to-float conversion, an FP64-pipe instruction, per use)
     float kA_f, kB_f, kC_f, kR_f, cs_f, ihcs_f;
+    float pdev_f[4];
     // float-float (hi, lo) forms of the wave constants (FFK_*)
-    float ffk[7][2];
+    float ffk[FFK_N][2];
     const UDesc* ud;
     const int2* zg;  // (node, source) grid offsets
     // Tiles of the band kernel: tile t holds local descriptors
@@ -834,6 +835,7 @@ int launch_bulk_persistent(int lat, int storage, const BulkRun* runs, int n_runs
 int prepare_bulk_persistent(int lat, int storage);
 // Opt the band kernel in to its dynamic shared memory (once, at creation).
 int prepare_boundary(int lat, int storage, const Band& B);
+
 // Zero-gradient copies (Eq. zg-bc) in fnew, after the bulk update of x_f.
 int launch_zg(int lat, int storage, const Geom& G, const Band& B, void* fnew, cudaStream_t st);
 
