@@ -11,7 +11,7 @@
 // planes [Q][ny][nxp].  A bulk node pulls g*_i(x - c_i) for every i.  Away
 // from periodic wrap-around the 37 shifted source rows of a 128-node row
 // segment are staged through shared memory by tensor copies (TMA), two row
-// segments per CTA with FP32 / FP16 storage; stores
+// segments per CTA with plain FP32 storage and one otherwise; stores
 // go straight to global memory at fixed plane offsets (Offsets, in the
 // kernel parameter bank).  The FP32/FP16 paths do all of their arithmetic in
 // FP32; the FP64 path in FP64.
@@ -148,20 +148,21 @@ __device__ __forceinline__ void collide_store(const Geom& G, const Offsets& O, S
 
 // Row segments per CTA of k_bulk: the tensor copies of every row are issued
 // at once (one transaction barrier each), so the copies of later rows land
-// while earlier rows are computed.  With two rows a CTA keeps 40 KB (FP32)
-// in flight with the registers of one row: five CTAs per SM, by shared
-// memory, carry more bytes in flight than seven one-row CTAs and leave the
-// registers of a band CTA free beside them, so the band kernel costs the
-// bulk kernel no CTAs when both share an SM.  FP64 storage (ALU-bound on
-// GB300, twice the staging) keeps one row.
-template <typename S>
-constexpr int bulk_rows() { return sizeof(S) == 8 ? 1 : 2; }
+// while earlier rows are computed.  Plain FP32: two rows, a CTA keeping
+// 40 KB in flight with the registers of one row (five CTAs per SM by shared
+// memory; measured at 1024x512 beside the one-CTA band tiles: step 31.9-32.3
+// us against 33.0 with one row).  With the reference equilibrium (89
+// registers) and with FP16 storage one row measured faster (the 1024x512
+// step: 12.1k -> 13.2k and 17.2k -> 17.8k MLUPS); FP64 storage (ALU-bound
+// on GB300, twice the staging) keeps one row.
+template <typename S, bool REF>
+constexpr int bulk_rows() { return (sizeof(S) == 4 && !REF) ? 2 : 1; }
 
 template <int LAT, typename S, bool REF>
 __device__ __forceinline__ void bulk_body(const Maps& tm, const Geom& G, const Offsets& O, const Region& R,
                                           const S* __restrict__ fin, S* __restrict__ fout, int* status)
 {
-    constexpr int ROWS = bulk_rows<S>();
+    constexpr int ROWS = bulk_rows<S, REF>();
     using L = Lat<LAT>;
     using C = typename Store<S>::C;
     using BX = Stage<LAT, S>;
@@ -520,21 +521,25 @@ int bulk_t(const Geom& G, const Offsets& O, const Region& R, const CUtensorMap* 
     const int h = R.y1 - R.y0;
     if (R.x1 <= R.x0 || h <= 0) return 0;
     const int t0 = R.x0 / kBulkThreads, t1 = (R.x1 + kBulkThreads - 1) / kBulkThreads;
-    constexpr int ROWS = bulk_rows<S>();
-    constexpr size_t smem = ROWS * Stage<LAT, S>::TOTAL;
-    static_assert(smem <= 48 * 1024, "bulk staging above the default dynamic shared memory");
     Maps tm;
     tm.m7 = tmaps[0];
     tm.m5 = tmaps[1];
     tm.m3 = tmaps[2];
     tm.m2 = tmaps[3];
     tm.m1 = tmaps[4];
-    dim3 blk(kBulkThreads), grd(t1 - t0, (h + ROWS - 1) / ROWS);
-    if (G.ref)
-        return launch_ex(k_bulk_ref<LAT, S>, grd, blk, smem, st, early, tm, G, O, R, static_cast<const S*>(fin),
-                         static_cast<S*>(fout), status);
-    return launch_ex(k_bulk<LAT, S>, grd, blk, smem, st, early, tm, G, O, R, static_cast<const S*>(fin),
-                     static_cast<S*>(fout), status);
+    const dim3 blk(kBulkThreads);
+    if (G.ref) {
+        constexpr int ROWS = bulk_rows<S, true>();
+        constexpr size_t smem = ROWS * Stage<LAT, S>::TOTAL;
+        static_assert(smem <= 48 * 1024, "bulk staging above the default dynamic shared memory");
+        return launch_ex(k_bulk_ref<LAT, S>, dim3(t1 - t0, (h + ROWS - 1) / ROWS), blk, smem, st, early, tm, G, O,
+                         R, static_cast<const S*>(fin), static_cast<S*>(fout), status);
+    }
+    constexpr int ROWS = bulk_rows<S, false>();
+    constexpr size_t smem = ROWS * Stage<LAT, S>::TOTAL;
+    static_assert(smem <= 48 * 1024, "bulk staging above the default dynamic shared memory");
+    return launch_ex(k_bulk<LAT, S>, dim3(t1 - t0, (h + ROWS - 1) / ROWS), blk, smem, st, early, tm, G, O, R,
+                     static_cast<const S*>(fin), static_cast<S*>(fout), status);
 }
 
 template <int LAT, typename S>
