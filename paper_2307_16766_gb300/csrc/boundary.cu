@@ -147,7 +147,8 @@ __device__ __forceinline__ double lab_component(int m, int kind, double r, doubl
 // with FP64 storage, FP32 otherwise.  The characteristic decomposition
 // (projection on the waves, wave amplitudes with their relaxation towards
 // the targets, and back to the lab frame) and the RK4 update of the
-// boundary state are FP64 for every storage.
+// boundary state are FP64 with FP64 storage and float-float (below)
+// otherwise; the boundary state is kept in FP64 between steps.
 
 // Exchanges inside a cluster without a cluster barrier: a CTA stores a
 // value into the shared memory of every CTA of its cluster with st.async,
@@ -165,12 +166,6 @@ __device__ __forceinline__ void put_async(unsigned a, double v, unsigned bar)
 {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
                  ::"r"(a), "l"(__double_as_longlong(v)), "r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void put_async(unsigned a, float v, unsigned bar)
-{
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
-                 ::"r"(a), "r"(__float_as_uint(v)), "r"(bar) : "memory");
 }
 
 // Unevaluated sums hi + lo of two floats ("float-float"), built from the
@@ -277,27 +272,29 @@ __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
-// One tile of the boundary band per cluster: a run of positions of one
-// characteristic side (all M layers, and the corner next to it on a W/E
-// side), plus the halo its four RK4 stages need (Sec. 3.3).
+// One tile of the boundary band: a run of positions of one characteristic
+// side (all M layers, and the corner next to it on a W/E side), plus the
+// halo its four RK4 stages need (Sec. 3.3).  Four groups of 128 threads
+// (MONO: one CTA; FP64: a cluster of four CTAs), group r forming wave r and
+// lab component r of every local unknown.
 //
-// 1. Strip nodes: the cluster pulls the bulk nodes at depths 0..2 next to
-//    the side that its stencils read (Eq. lbe) for their macros at t + 1
+// 1. Strip nodes: the tile pulls the bulk nodes at depths 0..2 next to the
+//    side that its stencils read (Eq. lbe) for their macros at t + 1
 //    (Eq. macro), and keeps them with the stored macros and moments of t in
-//    every CTA's shared memory; for its own positions it also writes the
-//    macros and non-equilibrium moments of t + 1 for the next step.  (The
-//    bulk kernel updates the populations of these nodes.)
+//    shared memory (every CTA of a cluster); for its own positions it also
+//    writes the macros and non-equilibrium moments of t + 1 for the next
+//    step.  (The bulk kernel updates the populations of these nodes.)
 // 2. RK4 (Sec. 3.3, "Time integration"): the local table lists the tile's
 //    unknowns by level: level 0 are owned, level l computes the first 4 - l
-//    stages, level 4 only supplies U(t).  Per stage, CTA r computes its
-//    share of the inputs of the characteristic system (1/rho,
-//    sqrt(theta), 1/sqrt(theta), P - P_inf and the transversal terms; in
-//    type R), then wave r (FP64), then lab component r of the right-hand
-//    side and of the stage value (FP64; stage values are shared in type R).
-//    Stage 0 freezes the viscous vector and the incoming-wave mask of
-//    time t.
+//    stages, level 4 only supplies U(t).  Per stage, the inputs of the
+//    characteristic system (1/rho, sqrt(theta), 1/sqrt(theta), P - P_inf
+//    and the transversal terms; in type R), then wave r, then lab component
+//    r of the right-hand side and of the stage value (float-float with
+//    FP32 / FP16 storage, FP64 with FP64 storage; stage values are shared in
+//    type R).  Stage 0 freezes the viscous vector and the incoming-wave
+//    mask of time t.
 // 3. The owners write U(t + 1) and the mesoscopic Dirichlet populations
-//    (equilibrium or Eq. NEEP), shared out over the four CTAs.
+//    (equilibrium or Eq. NEEP), shared out over the four groups.
 template <int LAT, typename S, bool REF, bool MONO>
 __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const Band& B,
                                           const Export& E, const S* __restrict__ fin,
@@ -464,17 +461,20 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
             }
         }
     };
-    // U(t) of the tile's unknowns: every CTA loads its own copy
+    // U(t) of the tile's unknowns, loaded with the strip's own loads: in the
+    // cluster form by every CTA, which keeps its component grp (u0g); in
+    // the one-CTA form by group 0, which leaves it in shared memory for all
+    // groups (Ys in R, U0s in FP64)
     const int lev = D.level;            // > 4: no unknown on this thread
-    double U0[4] = {0.0, 0.0, 0.0, 0.0};
-    if (lev <= 4) {
-        const double2* p = reinterpret_cast<const double2*>(B.Ub + ((long long)par_t * B.n_unk + D.gid) * 4);
-        const double2 a = p[0], b = p[1];
-        U0[0] = a.x; U0[1] = a.y; U0[2] = b.x; U0[3] = b.y;
-    }
-    // component grp of U(t) (the warm-up pass uses it for any role)
-    const double u0g = grp == 0 ? U0[0] : grp == 1 ? U0[1] : grp == 2 ? U0[2] : U0[3];
+    __shared__ __align__(16) double U0s[MONO ? 4 * kTileThreads : 1];
+    double u0g = 0.0;
     auto strip = [&](const StripNode& Nb, const int* tsl) {
+        double U0[4] = {0.0, 0.0, 0.0, 0.0};
+        if (lev <= 4 && (!MONO || grp == 0)) {
+            const double2* p = reinterpret_cast<const double2*>(B.Ub + ((long long)par_t * B.n_unk + D.gid) * 4);
+            const double2 a = p[0], b = p[1];
+            U0[0] = a.x; U0[1] = a.y; U0[2] = b.x; U0[3] = b.y;
+        }
 #pragma unroll
         for (int j = 0; j < kLT; ++j)
             if (tsl[j] >= 0) load_t(tl + j * tstride, tsl[j]);
@@ -489,8 +489,12 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         }
         if (lev <= 4 && (!MONO || grp == 0)) {
 #pragma unroll
-            for (int m = 0; m < 4; ++m) Ys[4 * l + m] = R(U0[m]);
+            for (int m = 0; m < 4; ++m) {
+                Ys[4 * l + m] = R(U0[m]);
+                if constexpr (MONO) U0s[4 * l + m] = U0[m];
+            }
         }
+        if constexpr (!MONO) u0g = grp == 0 ? U0[0] : grp == 1 ? U0[1] : grp == 2 ? U0[2] : U0[3];
     };
     if constexpr (!MONO) {
         strip(NbC, tslC);
@@ -510,9 +514,14 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         load_desc(Nb, tsl);
         strip(Nb, tsl);
       } else {
-        // warm-up: lane roles 0-3, warp parts A, B, C, Dirichlet (4: all)
-        const int rank = dry ? int(threadIdx.x % 4) : grp;
-        const int part = dry ? int(threadIdx.x / 32) % 4 : 4;
+        // warm-up: eight warps, one code part each (0: A's stencils and
+        // inputs, 1: A's viscous vector, 2: B, 3 and 4: C in roles 0-1 and
+        // 2-3, 5: the Dirichlet write, 6 and 7: none) with their lanes in
+        // every role of the part; the real pass: part 8, all of it
+        const int part = dry ? int(threadIdx.x / 32) % 8 : 8;
+        const int rank = !dry ? grp
+                       : part == 3 ? int(threadIdx.x % 2)
+                       : part == 4 ? 2 + int(threadIdx.x % 2) : int(threadIdx.x % 4);
         CtxT<R> X;
         X.Y = Ys;
         X.St = SUt;
@@ -524,9 +533,9 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         const int scheme = corner ? SCH_LODI : (lev <= 4 ? B.scheme[D.kind] : 0);
         const bool cbc = scheme == SCH_CBC || scheme == SCH_CBC_RELAX;
         double acc = 0.0, kc = 0.0;         // lab component rank of sum k and of the last k
-        const double u0r = u0g;
+        const double u0r = MONO ? U0s[4 * l + grp] : u0g;   // component grp of U(t)
         FF accf{0.0f, 0.0f};                // the same sum in float-float (FP32 / FP16 storage)
-        const FF u0f = ff_split(u0g);
+        const FF u0f = ff_split(u0r);
         bool incoming = false;              // wave rank incoming at time t
         // In FP32 every CTA forms all inputs of the system itself; in FP64 each
         // CTA forms a share and the shares are exchanged (FP64 issue is slow).
@@ -547,36 +556,38 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
             // A: inputs of the system, type R: 1/rho, the transversal terms,
             // sqrt(theta), 1/sqrt(theta), P - P_inf and d(rho T)/dt (thermal) or
             // d rho/dt (isothermal)
-            if (comp && (part == 4 || part == 0)) {
+            if (comp && (part == 8 || part <= 1)) {
                 const int kind = D.kind;
                 R A[4], Bv[4], Up[4], Um[4];
-                fetch_local(X, l, kind, kr, Ul);
-                if (corner) {
-                    // LODI along the outward diagonal, one-sided difference of
-                    // spacing sqrt(2) through the two diagonal bulk nodes
-                    fetch_local(X, D.nb[0], kind, kr, A);
-                    fetch_local(X, D.nb[1], kind, kr, Bv);
-                    const R kC = bconst<R>(B.kC, B.kC_f);
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) dUn[m] = (R(3) * Ul[m] - R(4) * A[m] + Bv[m]) * kC;
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) Up[m] = Um[m] = R(0);
-                } else {
-                    if (D.j == B.M) {        // Eq. FD-dx-bw at the outermost layer
-                        fetch_local(X, D.nb[1], kind, kr, A);
-                        fetch_local(X, D.nb[2], kind, kr, Bv);
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) dUn[m] = R(0.5) * (R(3) * Ul[m] - R(4) * A[m] + Bv[m]);
-                    } else {                 // Eq. FD-dx-center at inner layers
+                if (part != 1) {             // (the warm-up's part 1: the viscous vector only)
+                    fetch_local(X, l, kind, kr, Ul);
+                    if (corner) {
+                        // LODI along the outward diagonal, one-sided difference of
+                        // spacing sqrt(2) through the two diagonal bulk nodes
                         fetch_local(X, D.nb[0], kind, kr, A);
                         fetch_local(X, D.nb[1], kind, kr, Bv);
+                        const R kC = bconst<R>(B.kC, B.kC_f);
 #pragma unroll
-                        for (int m = 0; m < 4; ++m) dUn[m] = R(0.5) * (A[m] - Bv[m]);
+                        for (int m = 0; m < 4; ++m) dUn[m] = (R(3) * Ul[m] - R(4) * A[m] + Bv[m]) * kC;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) Up[m] = Um[m] = R(0);
+                    } else {
+                        if (D.j == B.M) {        // Eq. FD-dx-bw at the outermost layer
+                            fetch_local(X, D.nb[1], kind, kr, A);
+                            fetch_local(X, D.nb[2], kind, kr, Bv);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) dUn[m] = R(0.5) * (R(3) * Ul[m] - R(4) * A[m] + Bv[m]);
+                        } else {                 // Eq. FD-dx-center at inner layers
+                            fetch_local(X, D.nb[0], kind, kr, A);
+                            fetch_local(X, D.nb[1], kind, kr, Bv);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) dUn[m] = R(0.5) * (A[m] - Bv[m]);
+                        }
+                        fetch_local(X, D.nb[4], kind, kr, Up);
+                        fetch_local(X, D.nb[5], kind, kr, Um);
                     }
-                    fetch_local(X, D.nb[4], kind, kr, Up);
-                    fetch_local(X, D.nb[5], kind, kr, Um);
+                    d_ut = R(0.5) * (Up[2] - Um[2]);
                 }
-                d_ut = R(0.5) * (Up[2] - Um[2]);
                 // share q of the inputs (q = 0..3: entries {0,1}, {2,3},
                 // {4,5,6 isothermal}, {6,7 thermal})
                 auto input = [&](int i) -> R {
@@ -600,9 +611,11 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
                     }
                 };
                 if constexpr (kLocal) {
+                    if (part != 1) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) xs[i] = input(i);
-                    if (stage == 0 && !corner) {
+                        for (int i = 0; i < 8; ++i) xs[i] = input(i);
+                    }
+                    if (stage == 0 && !corner && part != 0) {
                         if (B.viscous == VIS_FD) {
 #pragma unroll
                             for (int c = 0; c < 4; ++c) Vs[c] = vis_fd_c<TH, R>(c, G, B, X, D, l, cs2r);
@@ -644,7 +657,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
             };
             R TTr[4] = {0, 0, 0, 0};        // transversal terms, local frame
             R Vr[4] = {0, 0, 0, 0};
-            if (comp && (part == 4 || part == 1)) {
+            if (comp && (part == 8 || part == 2)) {
                 if (!corner) {
                     TTr[0] = XP(1);
                     TTr[1] = XP(3);
@@ -770,7 +783,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
             // with r^-1 = rho / theta, b = sqrt(2 c_s^4 / T~) formed in type R);
             // RK4 update (FP64).  A side unknown's lab component 1 or 2 needs
             // one local component only.
-            if (comp && (part == 4 || part == 2)) {
+            if (comp && (part == 8 || part == 3 || part == 4)) {
                 if constexpr (kLocal) {
                     // float-float from the waves to the lab component; one
                     // conversion to FP64 for the RK4 sum
@@ -884,7 +897,7 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         }
 
         // 3. Dirichlet populations of unknown l, on CTA l % kCluster
-        if (lev == 0 && l % kCluster == rank && (part == 4 || part == 3)) {
+        if (lev == 0 && l % kCluster == rank && (part == 8 || part == 5)) {
             const R Unew[4] = {Ys[4 * l], Ys[4 * l + 1], Ys[4 * l + 2], Ys[4 * l + 3]};
             const bool neep = B.dirichlet >= 1;     // needs x_f: NEEP or regularised NEEP
             const S* fs = nullptr;
