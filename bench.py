@@ -93,17 +93,20 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    PERIOD_MS = 20      # the timed region of the default run is ~60 ms
+
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
         self.thread = None
+        self.first = 0      # samples before the timed region (not counted)
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -113,6 +116,14 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def ready(self, timeout=5.0):
+        """Wait until nvidia-smi delivers samples, then count only the
+        samples from now on (those of the timed region)."""
+        end = time.perf_counter() + timeout
+        while self.proc is not None and not self.lines and time.perf_counter() < end:
+            time.sleep(0.01)
+        self.first = len(self.lines)
 
     def stop(self):
         if self.proc is None:
@@ -126,7 +137,7 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in self.lines[self.first:]:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -254,6 +265,7 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True, reference=Fal
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(local_rank)
     sampler.start()
+    sampler.ready()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for k in range(K):

@@ -56,3 +56,24 @@ def test_cpu_baseline_reports_one_thread_and_restores_threads():
     assert oracle.threads() == n
     assert r["cores"] == n and r["kind"] == "oracle" and r["value"] > 0 and r["single_thread_value"] > 0
     assert isinstance(r["cpu"], str) and r["cpu"]
+
+
+def test_clock_sampler_counts_only_the_timed_region():
+    """Samples taken before ready() (nvidia-smi start-up, warm-up) are not
+    counted; throttle reasons of the counted samples are reported."""
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.proc = FakeProc()
+    s.lines = ["0, 1200, 2070, 500, 0x4, Active, Not Active, Not Active, Not Active"]
+    s.ready(timeout=0.0)
+    s.lines += ["0, 2070, 2070, 900, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "0, 2060, 2070, 950, 0x4, Not Active, Not Active, Not Active, Active"]
+    c = s.stop()
+    assert c["samples"] == 2 and c["sm_mhz"] == 2065.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
