@@ -565,6 +565,16 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
 
     pl.Q = Q;
     pl.esize = p->storage == LBM_F64 ? 8 : (p->storage == LBM_F32 ? 4 : 2);
+    // One-CTA band tiles hold whole SMs, which the bulk kernel beside them
+    // then lacks.  The band launch gets as few CTAs as keep it, at ~25 us
+    // per tile, within half the bulk kernel's time at ~6 TB/s; each CTA
+    // takes every grid-th tile (measured on the 4096^2 pulse, 484 tiles:
+    // 32 CTAs 22.5k MLUPS, 48 22.4k, 64 22.1k, 96 21.6k, one per tile 21.2k).
+    {
+        const double bulk_us = double(G.bx1 - G.bx0) * double(G.by1 - G.by0) * 2.0 * Q * double(pl.esize) / 6.0e6;
+        const double want = std::ceil(2.0 * 25.0 * B.n_tiles / std::max(bulk_us, 1.0));
+        B.grid = std::max(1, std::min(B.n_tiles, int(std::min(want, 1.0e9))));
+    }
     pl.f_bytes = (size_t)Q * (size_t)G.plane * pl.esize;
     pl.stripU_n = 2ull * E.nslots * 4;
     pl.stripN_n = 2ull * E.nslots * 5;

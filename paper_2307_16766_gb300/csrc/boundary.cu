@@ -16,6 +16,7 @@
 // and t + 1 (interpolated linearly at the stage time, Sec. 3.3).
 #include "charsys.cuh"
 
+#include <algorithm>
 #include <cooperative_groups.h>
 
 namespace cg = cooperative_groups;
@@ -926,7 +927,14 @@ __global__ void __launch_bounds__(band_threads<MONO>(), 1)
     k_band(Geom G, Offsets O, Band B, Export E, const S* __restrict__ fin, S* __restrict__ f,
            int par_t)
 {
-    band_tile<LAT, S, REF, MONO>(G, O, B, E, fin, f, par_t, MONO ? blockIdx.x : blockIdx.x / kCluster);
+    if constexpr (MONO) {
+        for (int t = blockIdx.x; t < B.n_tiles; t += gridDim.x) {
+            band_tile<LAT, S, REF, MONO>(G, O, B, E, fin, f, par_t, t);
+            __syncthreads();            // the next tile reuses the shared memory
+        }
+    } else {
+        band_tile<LAT, S, REF, MONO>(G, O, B, E, fin, f, par_t, blockIdx.x / kCluster);
+    }
 }
 
 // Band tiles of many grids in one launch: CTA (cluster) t takes tile
@@ -977,7 +985,7 @@ int boundary_t(const Geom& G, const Offsets& O, const Export& E, const Band& B, 
     S* fo = static_cast<S*>(fnew);
     constexpr bool mono = band_mono<S>();
     constexpr int ncl = mono ? 1 : kCluster;
-    const dim3 grd(B.n_tiles * ncl), blk(band_threads<mono>());
+    const dim3 grd(mono ? std::max(1, std::min(B.grid, B.n_tiles)) : B.n_tiles * ncl), blk(band_threads<mono>());
     if (G.ref)
         return launch_ex_cl(k_band<LAT, S, true, mono>, grd, blk, smem, st, false, ncl, G, O, B, E, fi, fo, par_t);
     return launch_ex_cl(k_band<LAT, S, false, mono>, grd, blk, smem, st, false, ncl, G, O, B, E, fi, fo, par_t);

@@ -723,6 +723,7 @@ struct Band {
     // (fx).
     int n_tiles;
     int max_nodes, max_fx;   // per tile, to size shared memory
+    int grid;                // CTAs of the one-CTA band launch; CTA c takes tiles c, c + grid, ...
     const UDesc* ld;
     const StripNode* sn;
     double* Ub;      // boundary state [parity][n_unk][4] (the fused kernel); [n_unk][4]
