@@ -348,9 +348,22 @@ def run_gpu(args, rank, world, local_rank, storage, want_e2e=True, reference=Fal
             lbm.lbm_get_macros(sim.handle, *[t.data_ptr() for t in host_out], 0)
         torch.cuda.synchronize(dev)
         e2e_s = time.perf_counter() - t1
+        # The same with one step per call (fields in, one step, macros out):
+        # the cost of the host copies when nothing amortises them.
+        calls = 20
+        t2 = time.perf_counter()
+        for _ in range(calls):
+            lbm.lbm_init_fields(sim.handle, n, *[t.numpy() for t in host_in])
+            lbm.lbm_step(sim.handle, 1)
+            lbm.lbm_get_macros(sim.handle, *[t.data_ptr() for t in host_out], 0)
+        torch.cuda.synchronize(dev)
+        n1_s = time.perf_counter() - t2
         res["e2e"] = {"value": n * S * segs / e2e_s / 1e6, "unit": "MLUPS",
                       "h2d_bytes_per_step": 4 * 8 * n / S, "d2h_bytes_per_step": 4 * 8 * n / S,
-                      "segment_steps": S, "segments": segs}
+                      "segment_steps": S, "segments": segs,
+                      "one_step_per_call": {"value": n * calls / n1_s / 1e6, "unit": "MLUPS",
+                                            "ms_per_call": n1_s / calls * 1e3, "calls": calls,
+                                            "h2d_bytes_per_step": 4 * 8 * n, "d2h_bytes_per_step": 4 * 8 * n}}
     sim.close()
     return res
 
