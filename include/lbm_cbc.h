@@ -184,8 +184,8 @@ int lbm_set_kernel_events(lbm_handle* h, void* const* events, int n);
  * the copies still in flight, so that none lands in the shared memory of a
  * CTA that has left, and leaves that row segment unwritten; the next
  * lbm_get_macros returns LBM_ERR_TIMEOUT.  The band kernel's cluster
- * exchanges keep their fixed 1 s limit: a CTA that gave up on one could still
- * receive other CTAs' stores after leaving.  A batch (lbm_batch_create)
+ * exchanges (FP64 storage) keep their fixed 1 s limit: a CTA that gave up on
+ * one could still receive other CTAs' stores after leaving.  A batch (lbm_batch_create)
  * takes the limit its runs have when it is created.  Synchronises the
  * stream. */
 int lbm_set_wait_limit(lbm_handle* h, double seconds);

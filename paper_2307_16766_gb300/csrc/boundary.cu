@@ -26,26 +26,26 @@ namespace lbmgb {
 namespace {
 
 constexpr int kBandThreads = 32;   // allocation-free path: one thread per unknown
-// Fused band kernel: at most one warp per SM sub-partition, because FP64
-// issue (one warp instruction per 64 cycles on each sub-partition) bounds
-// the characteristic arithmetic; the host sizes tiles to fit.
+// Fused band kernel: a group of kTileThreads threads per characteristic
+// component, one thread per local unknown of the tile.
 constexpr int kTileThreads = kTileUnknowns;
 constexpr int kCluster = 4;         // groups per band tile: one per characteristic component
 
-// A band tile is a cluster of kCluster CTAs of kTileThreads (one SM per
-// characteristic component) or, with FP32 / FP16 storage and MONO, one CTA
-// of kCluster such groups (the whole tile on one SM).
+// A band tile is, with FP32 / FP16 storage (MONO), one CTA of kCluster
+// groups (the whole tile on one SM), and with FP64 storage a cluster of
+// kCluster CTAs of one group each (one SM per characteristic component).
 template <bool MONO>
 constexpr int band_threads() { return MONO ? kCluster * kTileThreads : kTileThreads; }
 
 // ---------------------------------------------------------------------------
-// The band kernel: one cluster of four CTAs per tile
+// The band kernel: four component groups per tile
 // ---------------------------------------------------------------------------
-// FP64 issues at one warp instruction per 64 cycles on each SM
-// sub-partition, so the characteristic arithmetic of an unknown is split
-// over the four CTAs of a cluster (four SMs): CTA r owns component / wave r
-// of every unknown of the tile, and the CTAs exchange their shares through
-// distributed shared memory between cluster barriers.
+// Group r owns component / wave r of every unknown of the tile.  With FP64
+// storage (one warp instruction of FP64 per 64 cycles on each SM
+// sub-partition) the groups are the four CTAs of a cluster on four SMs,
+// exchanging their shares through distributed shared memory; with FP32 /
+// FP16 storage the wave arithmetic is float-float and the four groups share
+// one CTA and its shared memory.
 
 // Share c of the mesoscopic viscous vector (see vis_meso), in arithmetic
 // type R: V1 for c = 1, V2 for c = 2; V3 is split, its conductive part for
@@ -308,12 +308,10 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     // a kernel launched after this one for early start (the bulk update,
     // which reads only the old buffer) may begin now
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    // MONO (FP32 / FP16 storage, many tiles): one CTA of four 128-thread
-    // groups per tile, group r in the role of cluster rank r, exchanging
-    // through its own shared memory (the tile then holds one SM and leaves
-    // the others to the bulk kernel); otherwise a cluster of four 128-thread
-    // CTAs.  The arithmetic of a group or CTA is the same in both forms, so
-    // their results are identical.
+    // MONO (FP32 / FP16 storage): one CTA of four 128-thread groups per
+    // tile, group r in the role of cluster rank r, exchanging through its
+    // own shared memory (the tile then holds one SM and leaves the others to
+    // the bulk kernel); FP64 storage: a cluster of four 128-thread CTAs.
     static_assert(!MONO || sizeof(S) < 8, "FP64 storage keeps the cluster form");
     const int grp = MONO ? int(threadIdx.x / kTileThreads) : int(cg::this_cluster().block_rank());
     const int l = int(threadIdx.x % kTileThreads);
