@@ -109,6 +109,12 @@ typedef struct lbm_cbc_params {
                            FP32/FP16 rounding, small.  (0, 0): the plain shift.  Not
                            supported by the gradient calls or in batches; a saved state
                            restores only into a solver with the same u_ref.         */
+    int    band_ctas;   /* CTAs of the band launch with FP32 / FP16 storage, each taking
+                           every band_ctas-th boundary tile (a tile holds a whole SM,
+                           which the bulk kernel beside it then lacks).  0: as few as
+                           keep the band within about half the bulk kernel's expected
+                           time; above the tile count: one per tile.  Results do not
+                           depend on it.  Ignored with FP64 storage and in batches.  */
 } lbm_cbc_params;
 
 typedef struct lbm_handle lbm_handle;

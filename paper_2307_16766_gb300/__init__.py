@@ -57,7 +57,7 @@ class LbmCbcParams(C.Structure):
         ("dirichlet", C.c_int), ("alpha_T", C.c_double), ("beta_P", C.c_double),
         ("t_inf", C.c_double), ("p_inf", C.c_double * 4), ("inflow", C.c_double * 4),
         ("storage", C.c_int), ("rho0", C.c_double), ("alpha_V", C.c_double),
-        ("u_ref", C.c_double * 2),
+        ("u_ref", C.c_double * 2), ("band_ctas", C.c_int),
     ]
 
 
@@ -151,6 +151,7 @@ def params_from_run(cfg) -> LbmCbcParams:
     p.rho0 = float(cfg.get("rho0", 1.0))
     for i, v in enumerate(cfg.get("u_ref", [0.0, 0.0])):
         p.u_ref[i] = float(v)
+    p.band_ctas = int(cfg.get("band_ctas", 0))
     return p
 
 

@@ -175,6 +175,7 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
         err = "relaxation parameters must be finite";
         return LBM_ERR_ARG;
     }
+    if (p->band_ctas < 0) { err = "band_ctas must be >= 0"; return LBM_ERR_ARG; }
     {
         const double ur2 = p->u_ref[0] * p->u_ref[0] + p->u_ref[1] * p->u_ref[1];
         if (!std::isfinite(ur2) || !(ur2 < lattice_cs2(lattice))) {
@@ -570,7 +571,9 @@ int make_plan(int lattice, int nx, int ny, double tau, const lbm_cbc_params* p, 
     // per tile, within half the bulk kernel's time at ~6 TB/s; each CTA
     // takes every grid-th tile (measured on the 4096^2 pulse, 484 tiles:
     // 32 CTAs 22.5k MLUPS, 48 22.4k, 64 22.1k, 96 21.6k, one per tile 21.2k).
-    {
+    if (p->band_ctas > 0) {
+        B.grid = std::max(1, std::min(B.n_tiles, p->band_ctas));
+    } else {
         const double bulk_us = double(G.bx1 - G.bx0) * double(G.by1 - G.by0) * 2.0 * Q * double(pl.esize) / 6.0e6;
         const double want = std::ceil(2.0 * 25.0 * B.n_tiles / std::max(bulk_us, 1.0));
         B.grid = std::max(1, std::min(B.n_tiles, int(std::min(want, 1.0e9))));

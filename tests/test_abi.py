@@ -104,6 +104,9 @@ def test_defaults_and_workspace_size():
     (lbm.LBM_D2Q37, 16, 16, dict(u_ref=[0.8, 0.3]), False),         # |u_ref| >= c_s
     (lbm.LBM_D2Q37, 16, 16, dict(u_ref=[float("nan"), 0.0]), False),
     (lbm.LBM_D2Q9, 16, 16, dict(u_ref=[0.5, 0.3]), False),          # c_s^2 = 1/3 on D2Q9
+    (lbm.LBM_D2Q37, 64, 64, dict(side=[1, 1, 1, 1], band_ctas=3), True),
+    (lbm.LBM_D2Q37, 64, 64, dict(side=[1, 1, 1, 1], band_ctas=10 ** 6), True),
+    (lbm.LBM_D2Q37, 16, 16, dict(band_ctas=-1), False),
     (3, 16, 16, dict(), False),                                    # unknown lattice
     (-1, 16, 16, dict(), False),
 ])

@@ -661,3 +661,20 @@ def test_step_replays_under_cuda_graph_capture():
     sim.close()
     for x, y in zip(want, got):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("storage,dirichlet", [("f32", "eq"), ("f16", "neep"), ("f32", "reg")])
+def test_band_launch_width_does_not_change_results(storage, dirichlet):
+    """With FP32 / FP16 storage each band CTA takes every band_ctas-th tile
+    in turn (shared memory reused from tile to tile); one CTA for all tiles,
+    three, and one per tile give the same bits.  A 160x128 pulse on four
+    characteristic sides (corners included; over a dozen tiles) with the
+    mesoscopic viscous vector."""
+    cfg, f = W.pulse_d2q37(160, storage=storage)
+    cfg = dict(cfg, ny=128, dirichlet=dirichlet)
+    f = tuple(a[:128, :] for a in f)
+    res = [gpu_run(dict(cfg, band_ctas=k), f, 40) for k in (0, 1, 3)]
+    for other in res[1:]:
+        for x, y in zip(res[0], other):
+            assert np.array_equal(x, y)
+    assert all(np.isfinite(a).all() for a in res[0])
