@@ -414,8 +414,9 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
     if constexpr (!MONO) sync_all();    // every CTA of the cluster runs before any remote store
 
     // 1. strip nodes: macros of t and moments of t for every CTA; macros of
-    //    t + 1 (pull and Eq. macro) by CTA k % kCluster for node k, shared
-    //    out; post-collision populations of Eq. NEEP sources kept locally
+    //    t + 1 (pull and Eq. macro) by CTA k % kCluster (MONO: group k % 2)
+    //    for node k, shared out; post-collision populations of Eq. NEEP
+    //    sources kept locally
     const R* gU = static_cast<const R*>(E.stripU) + (long long)par_t * E.nslots * 4;
     const R* gN = static_cast<const R*>(E.stripN) + (long long)par_t * E.nslots * 5;
     const bool meso = B.viscous == VIS_MESO;
