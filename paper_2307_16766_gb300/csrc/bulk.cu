@@ -11,7 +11,8 @@
 // planes [Q][ny][nxp].  A bulk node pulls g*_i(x - c_i) for every i.  Away
 // from periodic wrap-around the 37 shifted source rows of a 128-node row
 // segment are staged through shared memory by tensor copies (TMA), two row
-// segments per CTA with plain FP32 storage and one otherwise; stores
+// segments per CTA with FP32 / FP16 storage (one with the reference
+// equilibrium and with FP64 storage); stores
 // go straight to global memory at fixed plane offsets (Offsets, in the
 // kernel parameter bank).  The FP32/FP16 paths do all of their arithmetic in
 // FP32; the FP64 path in FP64.
@@ -148,15 +149,15 @@ __device__ __forceinline__ void collide_store(const Geom& G, const Offsets& O, S
 
 // Row segments per CTA of k_bulk: the tensor copies of every row are issued
 // at once (one transaction barrier each), so the copies of later rows land
-// while earlier rows are computed.  Plain FP32: two rows, a CTA keeping
-// 40 KB in flight with the registers of one row (five CTAs per SM by shared
-// memory; measured at 1024x512 beside the one-CTA band tiles: step 31.9-32.3
-// us against 33.0 with one row).  With the reference equilibrium (89
-// registers) and with FP16 storage one row measured faster (the 1024x512
-// step: 12.1k -> 13.2k and 17.2k -> 17.8k MLUPS); FP64 storage (ALU-bound
-// on GB300, twice the staging) keeps one row.
+// while earlier rows are computed.  Plain FP32 and FP16: two rows, a CTA
+// keeping 40 KB (FP32) in flight with the registers of one row (measured
+// beside the one-CTA band tiles: FP32 1024x512 step 31.9-32.3 us against
+// 33.0 with one row; FP16 4096^2 36.5k against 32.1k MLUPS).  With the
+// reference equilibrium (89 registers) one row measured faster (1024x512:
+// 12.1k -> 13.2k MLUPS); FP64 storage (ALU-bound on GB300, twice the
+// staging) keeps one row.
 template <typename S, bool REF>
-constexpr int bulk_rows() { return (sizeof(S) == 4 && !REF) ? 2 : 1; }
+constexpr int bulk_rows() { return (sizeof(S) <= 4 && !REF) ? 2 : 1; }
 
 template <int LAT, typename S, bool REF>
 __device__ __forceinline__ void bulk_body(const Maps& tm, const Geom& G, const Offsets& O, const Region& R,
