@@ -533,7 +533,10 @@ __device__ __forceinline__ void band_tile(const Geom& G, const Offsets& O, const
         const int scheme = corner ? SCH_LODI : (lev <= 4 ? B.scheme[D.kind] : 0);
         const bool cbc = scheme == SCH_CBC || scheme == SCH_CBC_RELAX;
         double acc = 0.0, kc = 0.0;         // lab component rank of sum k and of the last k
-        const double u0r = MONO ? U0s[4 * l + grp] : u0g;   // component grp of U(t)
+        const double u0r = [&] {            // component grp of U(t)
+            if constexpr (MONO) return U0s[4 * l + grp];
+            else return u0g;
+        }();
         FF accf{0.0f, 0.0f};                // the same sum in float-float (FP32 / FP16 storage)
         const FF u0f = ff_split(u0r);
         bool incoming = false;              // wave rank incoming at time t
